@@ -1,0 +1,230 @@
+"""FP64 CPU oracle for the 3DPV shadow-sample path -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The product path never calls it.  It
+shares no code with the CUDA library: it is plain C (``pv3d_oracle.c``) built
+with gcc, plus this ctypes wrapper.
+
+``evaluate`` computes, for chosen sun steps and modules (Robledo et al.,
+Section 2, steps 2-4):
+  * per sample: shaded iff the exact FP64 ray toward the sun meets a triangle
+    other than the sample's own module (Moller-Trumbore over a BVH);
+  * per sample (optional): the parity mask -- the one-texel shadow-map answer is
+    ambiguous there (see the C file's header);
+  * per cell: shaded count; per module: MPP power shaded/unshaded with the
+    series-current-limited bypass-diode model; energies over the steps.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pv3d_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+_lib = None
+_lock = threading.Lock()
+
+I_REF = 9.0      # A at 1000 W/m^2
+V_CELL = 0.5     # V per cell at the operating point
+V_DIODE = 0.5    # V across a conducting bypass diode
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (plain C99, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=gnu99", "-ffp-contract=off", "-fno-fast-math",
+                               "-shared", "-fPIC", "-pthread", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = C.CDLL(build())
+            P = C.c_void_p
+            lib.pv3d_oracle_scene_create.restype = P
+            lib.pv3d_oracle_scene_create.argtypes = [P, C.c_int64, P, C.c_int64]
+            lib.pv3d_oracle_scene_destroy.argtypes = [P]
+            lib.pv3d_oracle_module_pmpp.restype = C.c_double
+            lib.pv3d_oracle_module_pmpp.argtypes = [C.c_int32, P, P, C.c_int32, C.c_double,
+                                                    C.c_double, C.c_double]
+            lib.pv3d_oracle_evaluate.restype = C.c_int
+            lib.pv3d_oracle_evaluate.argtypes = (
+                [P, C.c_int32, P, P, P, P, P, C.c_int32, P, P, P, P, P, P,
+                 C.c_int32, C.c_int32, C.c_double, C.c_double, C.c_double,
+                 P, C.c_int64, P, C.c_int32, C.c_int32, C.c_int32, C.c_int32]
+                + [P] * 10)
+            lib.pv3d_oracle_samples.restype = C.c_int
+            lib.pv3d_oracle_samples.argtypes = [C.c_int32, P, P, C.c_int32, P, P, C.c_int64,
+                                                C.c_int32, C.c_int32, P]
+            lib.pv3d_oracle_module_normal.restype = C.c_int
+            lib.pv3d_oracle_module_normal.argtypes = [C.c_int32, P, P, C.c_int32, P, P, C.c_int64,
+                                                      C.c_int32, P]
+            lib.pv3d_oracle_rays.restype = C.c_int
+            lib.pv3d_oracle_rays.argtypes = [P, P, P, C.c_int64, C.c_double, C.c_int32, P]
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+class OracleScene:
+    """A triangle soup held by the oracle (FP64 copy plus BVH)."""
+
+    def __init__(self, verts: np.ndarray, tris: np.ndarray):
+        self.lib = _load()
+        self.verts = np.ascontiguousarray(verts, np.float32)
+        self.tris = np.ascontiguousarray(tris, np.int32)
+        self.h = self.lib.pv3d_oracle_scene_create(_ptr(self.verts), self.verts.shape[0],
+                                                   _ptr(self.tris), self.tris.shape[0])
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            self.lib.pv3d_oracle_scene_destroy(self.h)
+            self.h = None
+
+    def rays(self, o: np.ndarray, d: np.ndarray, t_min: float = 1e-9, brute: bool = False) -> np.ndarray:
+        o = np.ascontiguousarray(o, np.float64).reshape(-1, 3)
+        d = np.ascontiguousarray(d, np.float64).reshape(-1, 3)
+        out = np.zeros(o.shape[0], np.uint8)
+        self.lib.pv3d_oracle_rays(self.h, _ptr(o), _ptr(d), o.shape[0], t_min, int(brute), _ptr(out))
+        return out.astype(bool)
+
+
+def _gen_arrays(gen):
+    """Flatten a generator (duck-typed: attributes of scenes.Generator)."""
+    m = gen.origin.shape[0]
+    mod_f = np.zeros((m, 10), np.float32)
+    mod_f[:, 0:3] = gen.origin
+    mod_f[:, 3:6] = gen.u
+    mod_f[:, 6:9] = gen.v
+    mod_f[:, 9] = gen.pitch
+    mod_i = np.stack([gen.cells_u, gen.cells_v, gen.layout, gen.tracker, gen.string], 1).astype(np.int32)
+    offs, nsub, subs = [], [], []
+    o = 0
+    for lay in gen.layouts:
+        offs.append(o)
+        nsub.append(lay.n_sub)
+        subs.append(np.asarray(lay.cell_sub, np.int32))
+        o += len(lay.cell_sub)
+    lay_off = np.asarray(offs, np.int32)
+    lay_nsub = np.asarray(nsub, np.int32)
+    lay_sub = np.concatenate(subs).astype(np.int32) if subs else np.zeros(1, np.int32)
+    pivots = np.ascontiguousarray(gen.pivots, np.float32).reshape(-1, 3)
+    if pivots.shape[0] == 0:
+        pivots = np.zeros((1, 3), np.float32)
+    return (np.ascontiguousarray(mod_f), np.ascontiguousarray(mod_i), lay_off, lay_nsub, lay_sub,
+            int(gen.pivots.shape[0]), pivots)
+
+
+def module_pmpp(g, cell_sub, n_sub, i_ref=I_REF, v_cell=V_CELL, v_diode=V_DIODE) -> float:
+    lib = _load()
+    g = np.ascontiguousarray(g, np.float64)
+    cs = np.ascontiguousarray(cell_sub, np.int32)
+    return lib.pv3d_oracle_module_pmpp(g.shape[0], _ptr(g), _ptr(cs), int(n_sub), i_ref, v_cell, v_diode)
+
+
+def evaluate(scene, gen, sun, poses, n: int, map_res: int, steps=None, modules=None,
+             want_mask: bool = True, brute: bool = False, threads: int | None = None,
+             oscene: OracleScene | None = None, i_ref=I_REF, v_cell=V_CELL, v_diode=V_DIODE) -> dict:
+    """Evaluate the oracle; arguments are duck-typed scenes.* objects.
+
+    Returns a dict with counts [S, C], bits/mbits [S, C] (n <= 8), power,
+    power_unshaded, cos_inc [S, M_eval], delta [S], cell_beam_loss [C],
+    energy, energy_unshaded [M_eval], and the step/module index arrays.
+    """
+    lib = _load()
+    if oscene is None:
+        oscene = OracleScene(scene.verts, scene.tris)
+    mod_f, mod_i, lay_off, lay_nsub, lay_sub, n_trk, pivots = _gen_arrays(gen)
+    n_steps = sun.xyz.shape[0]
+    steps = np.arange(n_steps, dtype=np.int64) if steps is None else np.asarray(steps, np.int64)
+    mods = (np.arange(mod_f.shape[0], dtype=np.int32) if modules is None
+            else np.asarray(modules, np.int32))
+    if steps.size and (steps.min() < 0 or steps.max() >= n_steps):
+        raise IndexError("step out of range")
+    if mods.size and (mods.min() < 0 or mods.max() >= mod_f.shape[0]):
+        raise IndexError("module out of range")
+    cells = mod_i[mods, 0].astype(np.int64) * mod_i[mods, 1]
+    C_ = int(cells.sum())
+    S, Me = steps.size, mods.size
+    sunxyz = np.ascontiguousarray(sun.xyz, np.float64)
+    dni = np.ascontiguousarray(sun.dni, np.float32)
+    dhi = np.ascontiguousarray(sun.dhi, np.float32)
+    dt = np.ascontiguousarray(sun.dt_h, np.float32)
+    if poses is None or n_trk == 0:
+        pz = np.zeros((n_steps, 1, 2), np.float32)
+    else:
+        pz = np.ascontiguousarray(poses, np.float32)
+    out = dict(
+        counts=np.zeros((S, C_), np.int32),
+        bits=np.zeros((S, C_), np.uint64) if n <= 8 else None,
+        mbits=np.zeros((S, C_), np.uint64) if (n <= 8 and want_mask) else None,
+        power=np.zeros((S, Me)), power_unshaded=np.zeros((S, Me)), cos_inc=np.zeros((S, Me)),
+        delta=np.zeros(S), cell_beam_loss=np.zeros(C_), energy=np.zeros(Me),
+        energy_unshaded=np.zeros(Me),
+    )
+    if threads is None:
+        threads = os.cpu_count() or 1
+
+    def p(a):
+        return None if a is None else _ptr(a)
+    rc = lib.pv3d_oracle_evaluate(
+        oscene.h, mod_f.shape[0], _ptr(mod_f), _ptr(mod_i), _ptr(lay_off), _ptr(lay_nsub),
+        _ptr(lay_sub), n_trk, _ptr(pivots), _ptr(sunxyz), _ptr(dni), _ptr(dhi), _ptr(dt), _ptr(pz),
+        int(n), int(map_res), i_ref, v_cell, v_diode, _ptr(steps), S, _ptr(mods), Me,
+        int(want_mask), int(brute), int(threads),
+        _ptr(out["counts"]), p(out["bits"]), p(out["mbits"]), _ptr(out["power"]),
+        _ptr(out["power_unshaded"]), _ptr(out["cos_inc"]), _ptr(out["delta"]),
+        _ptr(out["cell_beam_loss"]), _ptr(out["energy"]), _ptr(out["energy_unshaded"]))
+    if rc != 0:
+        raise ValueError("oracle rejected its input")
+    out["steps"] = steps
+    out["modules"] = mods
+    out["cells_per_module"] = cells
+    return out
+
+
+def evaluate_workload(w, **kw) -> dict:
+    return evaluate(w.scene, w.gen, w.sun, w.poses, w.n, w.map_res, **kw)
+
+
+def samples(gen, poses, step: int, module: int, n: int) -> np.ndarray:
+    lib = _load()
+    mod_f, mod_i, _, _, _, n_trk, pivots = _gen_arrays(gen)
+    pz = (np.zeros((step + 1, 1, 2), np.float32) if poses is None or n_trk == 0
+          else np.ascontiguousarray(poses, np.float32))
+    nc = int(mod_i[module, 0]) * int(mod_i[module, 1])
+    xyz = np.zeros((nc * n * n, 3))
+    lib.pv3d_oracle_samples(mod_f.shape[0], _ptr(mod_f), _ptr(mod_i), n_trk, _ptr(pivots), _ptr(pz),
+                            step, module, n, _ptr(xyz))
+    return xyz
+
+
+def module_normal(gen, poses, step: int, module: int) -> np.ndarray:
+    lib = _load()
+    mod_f, mod_i, _, _, _, n_trk, pivots = _gen_arrays(gen)
+    pz = (np.zeros((step + 1, 1, 2), np.float32) if poses is None or n_trk == 0
+          else np.ascontiguousarray(poses, np.float32))
+    out = np.zeros(3)
+    lib.pv3d_oracle_module_normal(mod_f.shape[0], _ptr(mod_f), _ptr(mod_i), n_trk, _ptr(pivots),
+                                  _ptr(pz), step, module, _ptr(out))
+    return out
+
+
+def unpack_bits(bits: np.ndarray, n: int) -> np.ndarray:
+    """[..., cells] uint64 -> [..., cells, n*n] bool (sample k = j*n + i)."""
+    k = np.arange(n * n, dtype=np.uint64)
+    return ((bits[..., None] >> k) & np.uint64(1)).astype(bool)

@@ -1,0 +1,411 @@
+"""Pins of the FP64 oracle against what geometry and the paper fix (no GPU).
+
+Each test checks the oracle against something other than itself: a closed
+form (pole shadow length, convex-obstacle shadow polygon, infinite-sheds
+row-to-row fraction, PV-model special cases), brute force, or an invariant of
+the method (Robledo et al., Section 2 steps 3-4).
+"""
+import math
+import numpy as np
+import pytest
+from scipy.spatial import ConvexHull
+
+import oracle
+from paper_1410_5780_gb300 import scenes as S
+
+def sun_from(az_deg, el_deg):
+    az, el = math.radians(az_deg), math.radians(el_deg)
+    return np.array([math.sin(az) * math.cos(el), math.cos(az) * math.cos(el), math.sin(el)])
+
+
+def one_sun(s, dni=800.0, dhi=100.0):
+    s = np.asarray(s, np.float64).reshape(-1, 3)
+    k = s.shape[0]
+    return S.Sun(xyz=s, dni=np.full(k, dni, np.float32), dhi=np.full(k, dhi, np.float32),
+                 dt_h=np.ones(k, np.float32))
+
+
+def flat_gen(origins, u, v, cells_u, cells_v, n_sub=1, pitch=S.CELL_PITCH):
+    m = len(origins)
+    lay = S.Layout(cells_u, cells_v, n_sub,
+                   (np.tile(np.arange(cells_u), cells_v) // (cells_u // n_sub)).astype(np.int32))
+    g = S._gen_from_lists(origins, [u] * m, [v] * m, cells_u, cells_v, [0] * m, [-1] * m,
+                          list(range(m)), [lay], np.zeros((0, 3)))
+    g.pitch = np.full(m, pitch, np.float32)
+    return g
+
+
+# ---------------------------------------------------------------------------
+# ray test: BVH against brute force
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_bvh_rays_equal_brute_force(seed):
+    rng = np.random.default_rng(seed)
+    nt = 300
+    c = rng.uniform(-5, 5, (nt, 1, 3))
+    verts = (c + rng.normal(0, 0.8, (nt, 3, 3))).reshape(-1, 3).astype(np.float32)
+    tris = np.arange(3 * nt, dtype=np.int32).reshape(nt, 3)
+    sc = oracle.OracleScene(verts, tris)
+    o = rng.uniform(-6, 6, (4000, 3))
+    d = rng.normal(size=(4000, 3))
+    d /= np.linalg.norm(d, axis=1, keepdims=True)
+    a = sc.rays(o, d, brute=False)
+    b = sc.rays(o, d, brute=True)
+    assert a.sum() > 200 and (~a).sum() > 200
+    assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("seed,tracked", [(11, False), (12, True), (13, False)])
+def test_bvh_evaluate_equals_brute_force(seed, tracked):
+    w = S.make_random_small(seed, n_mods=4, n_steps=5, n=3, tracked=tracked)
+    a = oracle.evaluate_workload(w, brute=False)
+    b = oracle.evaluate_workload(w, brute=True)
+    assert np.array_equal(a["bits"], b["bits"])
+    assert np.array_equal(a["mbits"], b["mbits"])
+    assert np.array_equal(a["power"], b["power"])
+
+
+# ---------------------------------------------------------------------------
+# closed form: the shadow of a pole of height h has length h / tan(elevation)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("el_deg", [15.0, 30.0, 47.0, 70.0])
+def test_pole_shadow_length(el_deg):
+    w_pole, h = 0.3, 4.0
+    mb = S.MeshBuilder()
+    mb.box((-w_pole / 2, -w_pole / 2, 0.0), (w_pole / 2, w_pole / 2, h))
+    scene = mb.build()
+    # horizontal strip north of the pole, sun due south
+    pitch = 0.05
+    cu, cv = 16, 400
+    origin = (-cu * pitch / 2, w_pole / 2 + 0.01, 0.0)
+    gen = flat_gen([origin], (1, 0, 0), (0, 1, 0), cu, cv, pitch=pitch)
+    sun = one_sun(sun_from(180.0, el_deg))
+    n = 2
+    r = oracle.evaluate(scene, gen, sun, None, n, 1024)
+    flags = oracle.unpack_bits(r["bits"][0], n)  # [cells, 4]
+    xyz = oracle.samples(gen, None, 0, 0, n).reshape(cv * cu, n * n, 3)
+    x, y = xyz[..., 0], xyz[..., 1]
+    length = h / math.tan(math.radians(el_deg))
+    inside = (np.abs(x) < w_pole / 2 - 1e-3) & (y < w_pole / 2 + length - 1e-3)
+    outside = (np.abs(x) > w_pole / 2 + 1e-3) | (y > w_pole / 2 + length + 1e-3)
+    assert inside.sum() > 0
+    assert flags[inside].all()
+    assert not flags[outside].any()
+
+
+# ---------------------------------------------------------------------------
+# closed form: a convex obstacle in front of a plane shades exactly the convex
+# hull of its vertices projected onto the plane along the sun direction
+# ---------------------------------------------------------------------------
+def _hull_contains(poly2d, pts, margin):
+    hull = ConvexHull(poly2d)
+    eq = hull.equations  # a.x + b.y + c <= 0 inside, with (a, b) unit
+    dist = pts @ eq[:, :2].T + eq[:, 2]
+    inside = (dist < -margin).all(axis=1)
+    outside = (dist > margin).any(axis=1)
+    return inside, outside
+
+
+@pytest.mark.parametrize("day,hours", [(355, range(8, 17)), (20, range(9, 16))])
+def test_convex_obstacle_shadow_polygon(day, hours):
+    w = S.make_tiny(day=day)
+    s_all = S.sun_vectors(40.0, np.full(len(hours), day), np.asarray(list(hours), float))
+    sun = one_sun(s_all)
+    n = 4
+    r = oracle.evaluate(w.scene, w.gen, sun, None, n, 1024)
+    box = w.scene.verts.astype(np.float64)[np.unique(w.scene.tris)]
+    checked = 0
+    for m in range(w.gen.n_modules):
+        o = w.gen.origin[m].astype(np.float64)
+        u = w.gen.u[m].astype(np.float64)
+        v = w.gen.v[m].astype(np.float64)
+        nrm = np.cross(u, v); nrm /= np.linalg.norm(nrm)
+        xyz = oracle.samples(w.gen, None, 0, m, n)
+        loc = np.stack([(xyz - o) @ u, (xyz - o) @ v], 1)
+        c0 = 60 * m
+        for si in range(len(s_all)):
+            s = s_all[si]
+            flags = oracle.unpack_bits(r["bits"][si, c0:c0 + 60], n).reshape(-1)
+            if nrm @ s <= 0:
+                continue
+            hgt = (box - o) @ nrm
+            assert (hgt > 0).all()  # the box lies wholly in front of the module plane
+            proj = box - np.outer(hgt / (nrm @ s), s)
+            poly = np.stack([(proj - o) @ u, (proj - o) @ v], 1)
+            inside, outside = _hull_contains(poly, loc, 1e-6)
+            assert flags[inside].all()
+            assert not flags[outside].any()
+            checked += int(inside.sum())
+    assert checked > 100
+
+
+# ---------------------------------------------------------------------------
+# closed form: infinite sheds, row-to-row shaded fraction
+#   f = clamp(1 - (d/L) sin(a_p) / sin(a_p + beta), 0, 1)
+# ---------------------------------------------------------------------------
+def sheds_fraction(beta, d_over_l, alpha_p):
+    return min(1.0, max(0.0, 1.0 - d_over_l * math.sin(alpha_p) / math.sin(alpha_p + beta)))
+
+
+def test_sheds_helper_worked_example():
+    # beta = 30 deg, d/L = 2, alpha_p = 20 deg: 1 - 2 sin20 / sin50 = 0.1070
+    assert abs(sheds_fraction(math.radians(30), 2.0, math.radians(20)) - 0.1070) < 5e-5
+
+
+@pytest.mark.parametrize("beta_deg,d_over_l,el_deg,az_deg",
+                         [(30.0, 2.0, 20.0, 180.0), (25.0, 1.8, 14.0, 180.0),
+                          (35.0, 2.5, 18.0, 205.0), (20.0, 2.2, 40.0, 180.0)])
+def test_infinite_sheds_fraction(beta_deg, d_over_l, el_deg, az_deg):
+    beta = math.radians(beta_deg)
+    cu, cv, pitch, n = 240, 8, S.CELL_PITCH, 4
+    L = cv * pitch
+    d = d_over_l * L
+    u = (1.0, 0.0, 0.0)
+    v = (0.0, math.cos(beta), math.sin(beta))
+    rows = 5
+    origins = [(-cu * pitch / 2, k * d, 0.0) for k in range(rows)]
+    gen = flat_gen(origins, u, v, cu, cv, pitch=pitch)
+    scene = S.Scene(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int32))
+    s = sun_from(az_deg, el_deg)
+    sun = one_sun(s)
+    r = oracle.evaluate(scene, gen, sun, None, n, 2048, modules=[2], want_mask=False)
+    # profile angle of the sun seen across the rows (rows face south, az 180)
+    alpha_p = math.atan(math.tan(math.radians(el_deg)) / math.cos(math.radians(az_deg - 180.0)))
+    f_exp = sheds_fraction(beta, d_over_l, alpha_p)
+    flags = oracle.unpack_bits(r["bits"][0], n).reshape(cv, cu, n, n)  # [cv, cu, j, i]
+    mid = flags[:, cu // 2 - 20: cu // 2 + 20]
+    # slant position of each sample row along the module
+    b = (np.arange(cv)[:, None] + (np.arange(n)[None, :] + 0.5) / n) * pitch  # [cv, j]
+    b_shadow = f_exp * L
+    expect = np.broadcast_to((b < b_shadow)[:, None, :, None], mid.shape)
+    near = np.broadcast_to((np.abs(b - b_shadow) < 1e-4)[:, None, :, None], mid.shape)
+    assert np.array_equal(mid[~near], expect[~near])
+    frac = mid.mean()
+    assert abs(frac - f_exp) <= 1.0 / (cv * n) + 1e-12
+
+
+# ---------------------------------------------------------------------------
+# PV model closed forms (series-current-limited bypass-diode model)
+# ---------------------------------------------------------------------------
+def test_pv_unshaded_closed_form():
+    lay = S.standard_layout(6, 10, 3)
+    for G in (100.0, 523.5, 1000.0):
+        p = oracle.module_pmpp(np.full(60, G), lay.cell_sub, 3)
+        assert abs(p - oracle.I_REF * G / 1000.0 * 60 * oracle.V_CELL) < 1e-9
+
+
+def test_pv_one_shaded_cell_closed_form():
+    lay = S.standard_layout(6, 10, 3)
+    vk = 20 * oracle.V_CELL
+    for g_full, g_diff in [(900.0, 100.0), (900.0, 400.0), (300.0, 250.0), (800.0, 0.0)]:
+        g = np.full(60, g_full)
+        g[0] = g_diff
+        i_full = oracle.I_REF * g_full / 1000.0
+        i_diff = oracle.I_REF * g_diff / 1000.0
+        expect = max(i_full * (2 * vk - oracle.V_DIODE), i_diff * 3 * vk)
+        assert abs(oracle.module_pmpp(g, lay.cell_sub, 3) - expect) < 1e-9
+
+
+def test_pv_two_substrings_hand_case():
+    # substrings at 9, 4.5 and 2.7 A (G 1000, 500, 300): candidates
+    # 9 A * (10 - 0.5 - 0.5) = 81 W; 4.5 A * (20 - 0.5) = 87.75 W; 2.7 A * 30 = 81 W
+    lay = S.standard_layout(6, 10, 3)
+    g = np.full(60, 1000.0)
+    sub = lay.cell_sub
+    g[np.flatnonzero(sub == 1)[3]] = 500.0
+    g[np.flatnonzero(sub == 2)[7]] = 300.0
+    assert abs(oracle.module_pmpp(g, sub, 3) - 87.75) < 1e-9
+
+
+def test_pv_monotone_in_irradiance():
+    rng = np.random.default_rng(5)
+    lay = S.standard_layout(6, 12, 3)
+    for _ in range(200):
+        g = rng.uniform(0, 1000, 72)
+        p0 = oracle.module_pmpp(g, lay.cell_sub, 3)
+        g2 = g.copy()
+        k = rng.integers(72)
+        g2[k] *= rng.uniform(0, 1)
+        assert oracle.module_pmpp(g2, lay.cell_sub, 3) <= p0 + 1e-12
+
+
+def test_pv_mpp_is_max_over_current_scan():
+    """The maximum over the substring currents equals a fine scan of P(I)."""
+    rng = np.random.default_rng(6)
+    lay = S.standard_layout(6, 10, 3)
+    for _ in range(30):
+        g = rng.uniform(50, 1000, 60)
+        ic = oracle.I_REF * g / 1000.0
+        ik = np.array([ic[lay.cell_sub == k].min() for k in range(3)])
+        grid = np.linspace(0, ik.max(), 20001)
+        volts = np.where(ik[None, :] >= grid[:, None], 20 * oracle.V_CELL, -oracle.V_DIODE).sum(1)
+        scan = max(0.0, float((grid * volts).max()))
+        p = oracle.module_pmpp(g, lay.cell_sub, 3)
+        assert p >= scan - 1e-9
+        assert p <= scan + ik.max() / 20000 * 60 * oracle.V_CELL + 1e-9
+
+
+# ---------------------------------------------------------------------------
+# invariants
+# ---------------------------------------------------------------------------
+def test_no_obstacles_zero_loss():
+    w = S.make_tiny(day=355)
+    empty = S.Scene(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int32))
+    r = oracle.evaluate(empty, w.gen, w.sun, None, w.n, w.map_res)
+    assert r["counts"].sum() == 0
+    assert np.array_equal(r["power"], r["power_unshaded"])
+    assert np.array_equal(r["energy"], r["energy_unshaded"])
+
+
+def test_sun_below_horizon_zero():
+    w = S.make_tiny(day=355)
+    r = oracle.evaluate_workload(w)
+    night = w.sun.xyz[:, 2] <= 0
+    assert night.sum() > 0
+    assert (r["power"][night] == 0).all() and (r["power_unshaded"][night] == 0).all()
+    assert (r["counts"][night] == 0).all() and (r["delta"][night] == 0).all()
+
+
+@pytest.mark.parametrize("seed", [21, 22])
+def test_adding_occluder_never_reduces_loss(seed):
+    base = S.make_random_small(seed, n_mods=4, n_steps=8, n=3)
+    extra = S.MeshBuilder()
+    rng = np.random.default_rng(seed + 100)
+    for _ in range(4):
+        c = rng.uniform(-6, 6, 2)
+        extra.box((c[0] - 1, c[1] - 1, 0), (c[0] + 1, c[1] + 1, rng.uniform(2, 6)))
+    ex = extra.build()
+    verts = np.concatenate([base.scene.verts, ex.verts])
+    tris = np.concatenate([base.scene.tris, ex.tris + base.scene.verts.shape[0]])
+    more = S.Scene(verts, tris)
+    a = oracle.evaluate_workload(base, want_mask=False)
+    b = oracle.evaluate(more, base.gen, base.sun, base.poses, base.n, base.map_res, want_mask=False)
+    assert ((a["bits"] & ~b["bits"]) == 0).all()
+    assert (b["power"] <= a["power"] + 1e-12).all()
+    assert (b["counts"].sum() > a["counts"].sum())
+
+
+def test_fractions_are_multiples_of_one_over_n2():
+    w = S.make_random_small(31, n_mods=3, n_steps=4, n=3)
+    r = oracle.evaluate_workload(w)
+    bits = oracle.unpack_bits(r["bits"], 3)
+    assert np.array_equal(bits.sum(-1), r["counts"])
+
+
+# ---------------------------------------------------------------------------
+# parity mask: every sample whose exact answer changes within the texel-centre
+# radius around it must be masked
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("seed,tracked", [(41, False), (42, True)])
+def test_mask_covers_every_ambiguous_sample(seed, tracked):
+    w = S.make_random_small(seed, n_mods=3, n_steps=4, n=3, map_res=256, tracked=tracked)
+    r = oracle.evaluate_workload(w)
+    n = w.n
+    for si in range(w.sun.n_steps):
+        s = w.sun.xyz[si]
+        delta = r["delta"][si]
+        # scene + all module quads, for the perturbed exact rays
+        for e, m in enumerate(r["modules"]):
+            nrm = oracle.module_normal(w.gen, w.poses, si, m)
+            if nrm @ s <= math.cos(math.radians(89)):
+                continue
+            quads_v, quads_t = [], []
+            for m2 in range(w.gen.n_modules):
+                if m2 == m:
+                    continue
+                xyz2 = _module_corners(w, si, m2)
+                base = len(quads_v) * 4
+                quads_v.append(xyz2)
+                quads_t += [(base, base + 1, base + 2), (base, base + 2, base + 3)]
+            verts = np.concatenate([w.scene.verts.astype(np.float64)] + quads_v).astype(np.float32)
+            tris = np.concatenate([w.scene.tris, np.asarray(quads_t, np.int32).reshape(-1, 3)
+                                   + w.scene.verts.shape[0]]).astype(np.int32)
+            sc = oracle.OracleScene(verts, tris)
+            xyz = oracle.samples(w.gen, w.poses, si, m, n)
+            c0 = int(np.concatenate([[0], np.cumsum(r["cells_per_module"])])[e])
+            nc = int(r["cells_per_module"][e])
+            flags = oracle.unpack_bits(r["bits"][si, c0:c0 + nc], n).reshape(-1)
+            masked = oracle.unpack_bits(r["mbits"][si, c0:c0 + nc], n).reshape(-1)
+            # points on the module plane whose projections lie within 0.7 texel
+            lu = np.array([s[1], -s[0], 0.0]); lu /= np.linalg.norm(lu)
+            lv = np.cross(s, lu)
+            t_u = lu - s * (nrm @ lu) / (nrm @ s)   # plane vector projecting onto lu
+            t_v = lv - s * (nrm @ lv) / (nrm @ s)
+            ang = np.linspace(0, 2 * np.pi, 16, endpoint=False)
+            offs = [(0.0, 0.0)] + [(0.7 * delta * math.cos(a_), 0.7 * delta * math.sin(a_)) for a_ in ang] \
+                + [(0.35 * delta * math.cos(a_), 0.35 * delta * math.sin(a_)) for a_ in ang[::2]]
+            res = []
+            for du, dv in offs:
+                q = xyz + du * t_u + dv * t_v
+                res.append(sc.rays(q, np.broadcast_to(s, q.shape), t_min=1e-9 * 100))
+            res = np.stack(res)
+            assert np.array_equal(res[0], flags)
+            ambiguous = (res != res[0]).any(0)
+            assert not (ambiguous & ~masked).any(), (si, m, np.flatnonzero(ambiguous & ~masked))
+    # the mask must leave most samples checkable
+    assert r["mbits"].size and _popcount(r["mbits"]) < 0.3 * r["mbits"].size * n * n
+
+
+def _popcount(a):
+    return int(sum(bin(int(x)).count("1") for x in a.ravel()))
+
+
+def _module_corners(w, step, m):
+    xyz = oracle.samples(w.gen, w.poses, step, m, 1)  # cell centres
+    cu, cv = int(w.gen.cells_u[m]), int(w.gen.cells_v[m])
+    p = float(w.gen.pitch[m])
+    c = xyz.reshape(cv, cu, 3)
+    du = (c[0, 1] - c[0, 0]) if cu > 1 else None
+    dv = (c[1, 0] - c[0, 0]) if cv > 1 else None
+    eu = du / np.linalg.norm(du) * p
+    ev = dv / np.linalg.norm(dv) * p
+    o = c[0, 0] - 0.5 * eu - 0.5 * ev
+    return np.stack([o, o + cu * eu, o + cu * eu + cv * ev, o + cv * ev])
+
+
+# ---------------------------------------------------------------------------
+# samples, poses and the light window
+# ---------------------------------------------------------------------------
+def test_samples_tile_each_cell():
+    w = S.make_tiny()
+    for n in (1, 3, 4):
+        xyz = oracle.samples(w.gen, None, 0, 1, n).reshape(10, 6, n * n, 3)
+        o, u, v = (w.gen.origin[1].astype(float), w.gen.u[1].astype(float), w.gen.v[1].astype(float))
+        p = float(w.gen.pitch[1])
+        cen = xyz.mean(2)
+        cv, cu = np.meshgrid(np.arange(10), np.arange(6), indexing="ij")
+        exp = o + ((cu + 0.5) * p)[..., None] * u + ((cv + 0.5) * p)[..., None] * v
+        assert np.allclose(cen, exp, atol=1e-6)
+        a = (xyz - o) @ u
+        b = (xyz - o) @ v
+        assert (a > cu[..., None] * p).all() and (a < (cu[..., None] + 1) * p).all()
+        assert (b > cv[..., None] * p).all() and (b < (cv[..., None] + 1) * p).all()
+
+
+def test_tracker_pose_normal_closed_form():
+    w = S.make_random_small(7, n_mods=3, n_steps=6, tracked=True)
+    for st in range(w.sun.n_steps):
+        for m in range(w.gen.n_modules):
+            az, tilt = w.poses[st, w.gen.tracker[m]].astype(np.float64)
+            exp = np.array([math.sin(tilt) * math.sin(az), math.sin(tilt) * math.cos(az), math.cos(tilt)])
+            got = oracle.module_normal(w.gen, w.poses, st, m)
+            assert np.allclose(got, exp, atol=1e-6)
+            s = w.sun.xyz[st]
+            if math.degrees(math.acos(s[2])) < 69.9:  # pose not clamped: faces the sun
+                assert got @ s > 1 - 1e-6
+
+
+def test_texel_size_closed_forms():
+    a = 2.0
+    gen = flat_gen([(-1.0, -1.0, 0.0)], (1, 0, 0), (0, 1, 0), 10, 10, pitch=a / 10)
+    empty = S.Scene(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int32))
+    R = 512
+    for el in (90.0, 60.0, 25.0):
+        r = oracle.evaluate(empty, gen, one_sun(sun_from(180.0, el)), None, 1, R, want_mask=False)
+        assert abs(r["delta"][0] / (a / (R - 2)) - 1) < 1e-7  # float32 pitch
+    # vertical facade W x H facing south, sun due south: extent max(W, H cos el)
+    W, H = 3.0, 6.0
+    gen = flat_gen([(0.0, 0.0, 0.0)], (1, 0, 0), (0, 0, 1), 10, 20, pitch=0.3)
+    for el in (10.0, 45.0, 70.0):
+        r = oracle.evaluate(empty, gen, one_sun(sun_from(180.0, el)), None, 1, R, want_mask=False)
+        assert abs(r["delta"][0] / (max(W, H * math.cos(math.radians(el))) / (R - 2)) - 1) < 1e-7

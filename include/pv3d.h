@@ -1,0 +1,236 @@
+/*
+ * pv3d.h -- C ABI of the GB300 shadow-sample library for PV shading losses.
+ *
+ * The method (Robledo, Leloux & Lorenzo, arXiv 1410.5780, Section 2) has four
+ * steps: (1) import a 3D scene, (2) define the PV generator -- geometry and
+ * electrical layout, (3) evaluate the shadows on the generator for every sun
+ * position by drawing the scene from the sun into a depth buffer with an
+ * orthographic view limited to the generator and depth-checking every sub-cell
+ * point against it, (4) turn the shading into power and energy losses.  The
+ * calls below follow those steps: pv3d_scene_load (1), pv3d_generator_define
+ * and pv3d_set_poses (2), pv3d_set_sun and pv3d_evaluate / pv3d_submit (3, 4).
+ *
+ * Conventions
+ *   * World frame: metres, x = east, y = north, z = up.
+ *   * Every call returns PV3D_OK (0) or a negative PV3D_E_* status; the text of
+ *     the last error of a context is available from pv3d_last_error.  The
+ *     library never aborts or exits the process.
+ *   * Input arrays are host pointers, copied to the device during the call; the
+ *     caller may free them on return.  Output arrays of pv3d_result are caller
+ *     allocated, host or device memory as its is_device field says.
+ *   * A context is bound to one CUDA device and is not thread safe: use one
+ *     context per host thread.
+ */
+#ifndef PV3D_H
+#define PV3D_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define PV3D_OK           0
+#define PV3D_E_INVALID   -1  /* bad argument: NaN, degenerate geometry, |sun| != 1, bad layout ... */
+#define PV3D_E_NOMEM     -2  /* device or host allocation failed */
+#define PV3D_E_ADMISSION -3  /* request larger than the context's device-memory budget */
+#define PV3D_E_OVERFLOW  -4  /* internal capacity could not be grown far enough */
+#define PV3D_E_TIMEOUT   -5  /* a bounded wait ran out (pv3d_poll) */
+#define PV3D_E_DEVICE    -6  /* CUDA runtime error */
+#define PV3D_E_PENDING   -7  /* pv3d_poll: request not finished yet */
+#define PV3D_E_NOTFOUND  -8  /* unknown scene, generator or request id */
+
+/* ---- depth formats ------------------------------------------------------ */
+#define PV3D_DEPTH_F32    0  /* FP32 depth, stored as order-preserving uint32 */
+#define PV3D_DEPTH_U24    1  /* 24-bit unsigned fixed point over the window's depth range */
+
+typedef struct pv3d_ctx pv3d_ctx;
+
+/* Context options.  Zero fields take the defaults in brackets. */
+typedef struct pv3d_opts {
+    int32_t device;           /* CUDA device ordinal [0] */
+    int32_t map_res;          /* default shadow-map side R, power of two, 64..16384 [4096] */
+    int32_t tile;             /* rasteriser tile side: 32 or 64 texels [64] */
+    int32_t chunk_steps;      /* sun steps processed per wave, 1..256 [32] */
+    int32_t depth_format;     /* PV3D_DEPTH_F32 or PV3D_DEPTH_U24 [F32] */
+    int32_t max_inflight;     /* served requests resident on the device at once [64] */
+    int64_t hbm_budget_bytes; /* device memory the context may use [90% of free memory] */
+    int32_t reserved[8];
+} pv3d_opts;
+
+/*
+ * One PV module (Section 2, step 2): a planar grid of cells_u x cells_v square
+ * cells of side `pitch`.  Cell (cu, cv) covers origin + a*u + b*v for
+ * a in [cu, cu+1]*pitch, b in [cv, cv+1]*pitch; the front face is the side of
+ * u x v.  For a tracked module (tracker >= 0) origin, u and v are given in the
+ * tracker's rest frame relative to its pivot (rest = table horizontal, front
+ * face up); otherwise in the world frame.  u and v must be unit, orthogonal.
+ */
+typedef struct pv3d_module {
+    float origin[3];
+    float u[3];
+    float v[3];
+    float pitch;        /* m */
+    int32_t cells_u;    /* 1..64 */
+    int32_t cells_v;    /* 1..64; cells_u * cells_v <= 1024 */
+    int32_t layout;     /* index into the layouts of pv3d_generator_define */
+    int32_t tracker;    /* index into the trackers, or -1 for a fixed module */
+    int32_t string_id;  /* series string the module belongs to (informational) */
+    int32_t reserved;
+} pv3d_module;
+
+/*
+ * Bypass-diode layout (Section 2, step 2: cells in series, each cell related to
+ * one by-pass diode).  cell_sub[cv * cells_u + cu] = substring index in
+ * [0, n_sub); every substring must own at least one cell.  n_sub <= 64.
+ */
+typedef struct pv3d_layout {
+    int32_t cells_u;
+    int32_t cells_v;
+    int32_t n_sub;
+    int32_t reserved;
+    const int32_t* cell_sub;  /* host pointer, cells_u * cells_v entries */
+} pv3d_layout;
+
+/* A two-axis tracker (Section 3.4): modules rotate rigidly about `pivot`. */
+typedef struct pv3d_tracker {
+    float pivot[3];
+} pv3d_tracker;
+
+/* Per-evaluation options.  Zero fields take the defaults in brackets. */
+typedef struct pv3d_eval_opts {
+    int32_t samples_per_side;  /* n: n x n sub-cell samples per cell, 1..15 [3] */
+    int32_t map_res;           /* shadow-map side R [context default] */
+    int64_t step_begin;        /* first sun step evaluated [0] */
+    int64_t step_end;          /* one past the last step; 0 = all steps [0] */
+    float i_ref;               /* cell current at 1000 W/m^2, A [9.0] */
+    float v_cell;              /* cell voltage at the operating point, V [0.5] */
+    float v_diode;             /* bypass-diode forward drop, V [0.5] */
+    int32_t chunk_steps;       /* steps per wave [context default] */
+    void* stream;              /* cudaStream_t to run on; NULL = the context's own stream */
+    int32_t reserved[8];
+} pv3d_eval_opts;
+
+/*
+ * Results.  M = modules of the generator, C = their cells (module order, then
+ * cv * cells_u + cu), S = step_end - step_begin.  Every array pointer may be
+ * NULL when not wanted.  Energies are the FP32 Kahan-compensated sums of the
+ * per-step values, returned as double.
+ */
+typedef struct pv3d_result {
+    int32_t is_device;         /* 1: the arrays below are device pointers; 0: host */
+    int32_t reserved0;
+    double* energy;            /* [M] sum over steps of P_mpp * dt, Wh */
+    double* energy_unshaded;   /* [M] same without shading, Wh */
+    float* power;              /* [S x M] P_mpp per step, W */
+    float* power_unshaded;     /* [S x M] */
+    double* cell_beam_loss;    /* [C] sum over steps of DNI * max(0, cos i) * f_c * dt, Wh/m^2 */
+    uint8_t* cell_counts;      /* [S x C] shaded samples per cell */
+    uint64_t* sample_bits;     /* [S x C] bit k = j*n + i set if sample (i, j) is shaded; n <= 8 */
+    /* filled by the library */
+    int64_t tests;             /* sample depth tests performed (lit steps x samples per step) */
+    int64_t steps_lit;         /* steps whose sun is above the horizon */
+    float device_ms;           /* device time of the evaluation (CUDA events) */
+    int32_t waves;             /* waves launched */
+    int64_t nonempty_tiles;    /* rasterised (step, tile) pairs over the evaluation */
+    int64_t binned_tris;       /* (triangle, tile) pairs binned over the evaluation */
+} pv3d_result;
+
+/* ---- context ------------------------------------------------------------ */
+
+/* Create a context on opts->device (opts may be NULL). */
+int pv3d_create(pv3d_ctx** out, const pv3d_opts* opts);
+
+/* Release every device resource of the context.  NULL is accepted. */
+void pv3d_destroy(pv3d_ctx* ctx);
+
+/* Text of the last error reported by a call on `ctx` ("" if none). */
+const char* pv3d_last_error(pv3d_ctx* ctx);
+
+/* ---- step 1: scene (Section 2, step 1) ---------------------------------- */
+
+/*
+ * Load a triangle soup: xyz[3 * n_verts] floats, tri_idx[3 * n_tris] vertex
+ * indices.  Triangles are two-sided.  Copied to the device; stays resident
+ * until pv3d_release.  Errors: PV3D_E_INVALID for a non-finite coordinate or an
+ * index out of range; n_tris may be 0.
+ */
+int pv3d_scene_load(pv3d_ctx* ctx, const float* xyz, int64_t n_verts,
+                    const int32_t* tri_idx, int64_t n_tris, uint32_t* scene_id);
+
+/* ---- step 2: generator (Section 2, step 2) ------------------------------ */
+
+/*
+ * Define a PV generator over a loaded scene.  The generator's modules are
+ * occluders too (row-to-row and tracker-to-tracker shading), except a module
+ * never shades itself.  One generator = one light window per sun step, the
+ * bounding square of its modules as seen from the sun (Section 2, step 3).
+ */
+int pv3d_generator_define(pv3d_ctx* ctx, uint32_t scene_id,
+                          const pv3d_module* mods, int32_t n_mods,
+                          const pv3d_layout* layouts, int32_t n_layouts,
+                          const pv3d_tracker* trackers, int32_t n_trackers,
+                          uint32_t* gen_id);
+
+/*
+ * Tracker poses: az_tilt[(step * n_trackers + t) * 2 + {0, 1}] = compass
+ * azimuth the table faces (radians from north, clockwise) and its tilt from
+ * horizontal (radians).  A point x of the rest frame moves to
+ * pivot + Rz(pi - az) * Rx(tilt) * x, so the front normal becomes
+ * (sin tilt sin az, sin tilt cos az, cos tilt).  n_steps must equal the sun
+ * table's length (either may be set first).
+ */
+int pv3d_set_poses(pv3d_ctx* ctx, uint32_t gen_id, const float* az_tilt, int64_t n_steps);
+
+/* ---- step 3/4 inputs: sun and irradiance (Section 2, steps 3 and 4) ----- */
+
+/*
+ * Sun table: sun_xyz[3 * step] unit vector toward the sun (|s| = 1 +- 1e-6),
+ * DNI and DHI in W/m^2, dt_h = duration represented by the step, hours.
+ * Steps with s.z <= 0 receive no direct light and are skipped.
+ */
+int pv3d_set_sun(pv3d_ctx* ctx, uint32_t gen_id, const double* sun_xyz, const float* dni,
+                 const float* dhi, const float* dt_h, int64_t n_steps);
+
+/* ---- steps 3 and 4: evaluation -------------------------------------------
+ *
+ * For each lit sun step: depth-rasterise the scene and the generator's modules
+ * from the sun into an R x R map over the generator's window, test each of the
+ * n x n samples of every cell against the map (shaded iff its depth exceeds the
+ * stored depth plus a slope-scaled bias), reduce to cell, substring and module
+ * shaded fractions, and apply the bypass-diode model:
+ *   G_c = DNI max(0, cos i)(1 - f_c) + DHI (1 + cos beta) / 2,   I_c = i_ref G_c / 1000,
+ *   I_k = min_{c in k} I_c,  P(I) = I (sum_{I_k >= I} n_k v_cell - v_diode #{I_k < I}),
+ *   P_mpp = max(0, max_k P(I_k)).
+ * Energies are integrated over the steps (Section 2, step 4).
+ */
+
+/* Synchronous evaluation; returns when the results are in `out`. */
+int pv3d_evaluate(pv3d_ctx* ctx, uint32_t gen_id, const pv3d_eval_opts* opts, pv3d_result* out);
+
+/*
+ * Served evaluation: enqueue the request and return at once with *req.  The
+ * context keeps scenes resident, admits requests by their device-memory
+ * footprint against its budget and batches the work of every admitted request
+ * into shared waves (continuous batching).  The scene, generator, sun table and
+ * `out` must stay valid until the request completes.
+ */
+int pv3d_submit(pv3d_ctx* ctx, uint32_t gen_id, const pv3d_eval_opts* opts, pv3d_result* out,
+                uint64_t* req);
+
+/*
+ * Advance the served work and wait up to timeout_ms (0 = do not wait) for
+ * request `req`: PV3D_OK when its results are in its pv3d_result,
+ * PV3D_E_PENDING if still running, another status on failure.
+ */
+int pv3d_poll(pv3d_ctx* ctx, uint64_t req, int32_t timeout_ms);
+
+/* Free a scene (and every generator defined on it) or a generator. */
+int pv3d_release(pv3d_ctx* ctx, uint32_t scene_or_gen_id);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PV3D_H */

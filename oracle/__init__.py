@@ -70,6 +70,10 @@ def _load():
             lib.pv3d_oracle_module_normal.restype = C.c_int
             lib.pv3d_oracle_module_normal.argtypes = [C.c_int32, P, P, C.c_int32, P, P, C.c_int64,
                                                       C.c_int32, P]
+            lib.pv3d_oracle_power_from_counts.restype = C.c_int
+            lib.pv3d_oracle_power_from_counts.argtypes = (
+                [C.c_int32, P, P, P, P, P, C.c_int32, P, P, P, P, P, C.c_int32, C.c_double, C.c_double,
+                 C.c_double, P, C.c_int64, P, C.c_int32, P, P])
             lib.pv3d_oracle_rays.restype = C.c_int
             lib.pv3d_oracle_rays.argtypes = [P, P, P, C.c_int64, C.c_double, C.c_int32, P]
             _lib = lib
@@ -222,6 +226,34 @@ def module_normal(gen, poses, step: int, module: int) -> np.ndarray:
     lib.pv3d_oracle_module_normal(mod_f.shape[0], _ptr(mod_f), _ptr(mod_i), n_trk, _ptr(pivots),
                                   _ptr(pz), step, module, _ptr(out))
     return out
+
+
+def power_from_counts(w, steps, modules, counts, i_ref=I_REF, v_cell=V_CELL, v_diode=V_DIODE) -> np.ndarray:
+    """Oracle PV model (Section 2, step 4) on given per-cell shaded counts
+    [S, C_eval]; returns power [S, M_eval]."""
+    lib = _load()
+    gen, sun = w.gen, w.sun
+    mod_f, mod_i, lay_off, lay_nsub, lay_sub, n_trk, pivots = _gen_arrays(gen)
+    steps = np.ascontiguousarray(steps, np.int64)
+    mods = np.ascontiguousarray(modules, np.int32)
+    cnt = np.ascontiguousarray(counts, np.int32)
+    pz = (np.zeros((sun.xyz.shape[0], 1, 2), np.float32) if w.poses is None or n_trk == 0
+          else np.ascontiguousarray(w.poses, np.float32))
+    out = np.zeros((steps.size, mods.size))
+    lib.pv3d_oracle_power_from_counts(
+        mod_f.shape[0], _ptr(mod_f), _ptr(mod_i), _ptr(lay_off), _ptr(lay_nsub), _ptr(lay_sub), n_trk,
+        _ptr(pivots), _ptr(np.ascontiguousarray(sun.xyz, np.float64)), _ptr(np.ascontiguousarray(sun.dni, np.float32)),
+        _ptr(np.ascontiguousarray(sun.dhi, np.float32)), _ptr(pz), int(w.n), i_ref, v_cell, v_diode,
+        _ptr(steps), steps.size, _ptr(mods), mods.size, _ptr(cnt), _ptr(out))
+    return out
+
+
+def popcount64(a: np.ndarray) -> np.ndarray:
+    a = a.astype(np.uint64)
+    c = np.zeros(a.shape, np.int32)
+    for k in range(64):
+        c += ((a >> np.uint64(k)) & np.uint64(1)).astype(np.int32)
+    return c
 
 
 def unpack_bits(bits: np.ndarray, n: int) -> np.ndarray:

@@ -779,6 +779,57 @@ int pv3d_oracle_evaluate(void* scene_h,
     return 0;
 }
 
+/*
+ * PV model of Section 2 step 4 applied to given shaded-sample counts:
+ * power[s * n_eval + e] for counts[s * C + cell] (cells of the evaluated
+ * modules in order).  Used to check energy results cell count by cell count.
+ */
+int pv3d_oracle_power_from_counts(int32_t n_mods, const float* mod_f, const int32_t* mod_i,
+                                  const int32_t* lay_off, const int32_t* lay_nsub, const int32_t* lay_sub,
+                                  int32_t n_trk, const float* pivots, const double* sun, const float* dni,
+                                  const float* dhi, const float* poses, int32_t n, double i_ref,
+                                  double v_cell, double v_diode, const int64_t* eval_steps,
+                                  int64_t n_eval_steps, const int32_t* eval_mods, int32_t n_eval,
+                                  const int32_t* counts, double* power)
+{
+    ogen_t G;
+    memset(&G, 0, sizeof(G));
+    G.n_mods = n_mods; G.mod_f = mod_f; G.mod_i = mod_i; G.n_trk = n_trk; G.pivots = pivots;
+    G.poses = poses; G.n = n;
+    int64_t C = 0;
+    for (int32_t e = 0; e < n_eval; ++e) C += (int64_t)mod_i[5 * (size_t)eval_mods[e]] * mod_i[5 * (size_t)eval_mods[e] + 1];
+    double* g = (double*)malloc(sizeof(double) * 4096);
+    for (int64_t si = 0; si < n_eval_steps; ++si) {
+        int64_t st = eval_steps[si];
+        vec3 s = mk(sun[3 * st], sun[3 * st + 1], sun[3 * st + 2]);
+        int64_t c0 = 0;
+        for (int32_t e = 0; e < n_eval; ++e) {
+            int32_t m = eval_mods[e];
+            const int32_t* mi = mod_i + 5 * (size_t)m;
+            int32_t ncell = mi[0] * mi[1];
+            if (!(s.z > 0.0) || ncell > 4096) {
+                power[si * n_eval + e] = 0.0;
+                c0 += ncell;
+                continue;
+            }
+            posed_t P;
+            pose_module(&G, m, st, &P);
+            double c = dot(P.n, s);
+            double beam = (double)dni[st] * fmax(0.0, c);
+            double diff = (double)dhi[st] * (1.0 + P.n.z) / 2.0;
+            for (int32_t k = 0; k < ncell; ++k) {
+                double fc = (double)counts[si * C + c0 + k] / (double)(n * n);
+                g[k] = beam * (1.0 - fc) + diff;
+            }
+            power[si * n_eval + e] = pv3d_oracle_module_pmpp(ncell, g, lay_sub + lay_off[mi[2]], lay_nsub[mi[2]],
+                                                             i_ref, v_cell, v_diode);
+            c0 += ncell;
+        }
+    }
+    free(g);
+    return 0;
+}
+
 /* Sample positions of one module at one step (for tests): xyz[cells*n*n*3] in
  * cell order, then sample order k = j*n + i. */
 int pv3d_oracle_samples(int32_t n_mods, const float* mod_f, const int32_t* mod_i, int32_t n_trk,

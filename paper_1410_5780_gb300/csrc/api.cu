@@ -1,0 +1,880 @@
+// api.cu -- host side of the pv3d C ABI: contexts, resident scenes and
+// generators, wave planning, workspace pools and the served request loop.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "pv3d.h"
+#include "pv3d_dev.cuh"
+
+using namespace pv3d;
+
+namespace {
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+struct SceneH {
+    float4* d_tri = nullptr;
+    int32_t n_tris = 0;
+    float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    size_t bytes = 0;
+};
+
+struct GenH {
+    uint32_t scene_id = 0;
+    int32_t M = 0, C = 0, n_trk = 0;
+    int32_t max_cells = 0;
+    bool coplanar = false;
+    float ref[3] = {0, 0, 0};
+    float glo[3], ghi[3];  // generator bounds (world), tracker reach included
+    std::vector<ModuleDev> mods_h;
+    ModuleDev* d_mods = nullptr;
+    int32_t* d_cell_mod = nullptr;
+    int32_t* d_lay_sub = nullptr;
+    int32_t* d_lay_off = nullptr;
+    int32_t* d_lay_nk = nullptr;
+    int32_t* d_lay_nk_off = nullptr;
+    float* d_pivots = nullptr;
+    // sun table
+    int64_t n_steps = 0;
+    double* d_sun = nullptr;
+    float* d_dni = nullptr;
+    float* d_dhi = nullptr;
+    float* d_dt = nullptr;
+    std::vector<uint8_t> lit;  // host copy: s.z > 0
+    // poses
+    int64_t n_pose_steps = 0;
+    float* d_poses = nullptr;
+    size_t bytes = 0;
+};
+
+// One evaluation split into waves of consecutive steps.
+struct Plan {
+    std::vector<WaveDev> waves;
+    std::vector<JobDev> jobs;  // one job per wave for a plain evaluation
+    int64_t max_js = 0, max_te = 0, max_ms = 0, max_cs = 0;
+};
+
+}  // namespace
+
+struct pv3d_ctx {
+    int device = 0;
+    int sm_count = 0;
+    cudaStream_t stream = nullptr;
+    pv3d_opts opts{};
+    std::string err;
+    std::map<uint32_t, SceneH> scenes;
+    std::map<uint32_t, GenH> gens;
+    uint32_t next_id = 1;
+    // workspace pools
+    DevBuf lp, win, ms, ms_p, ms_pu, ms_beam, cs_cnt, t_far, t_cnt, t_off, t_cur, t_slot, nonempty, bins, map,
+        big, block_sums, ctr, waves, jobs, kahan_mod, kahan_cell, staging;
+    int64_t bin_cap = 0, map_cap_tiles = 0, big_cap = 0;
+    void* h_stage = nullptr;  // pinned staging for descriptors
+    size_t h_stage_bytes = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    // served requests
+    struct Request;
+    std::map<uint64_t, std::unique_ptr<Request>> reqs;
+    std::deque<uint64_t> queue;
+    uint64_t next_req = 1;
+};
+
+struct pv3d_ctx::Request {
+    uint32_t gen_id;
+    pv3d_eval_opts opts;
+    pv3d_result* out;
+    int status = PV3D_E_PENDING;
+};
+
+// ---------------------------------------------------------------------------
+// helpers
+// ---------------------------------------------------------------------------
+static int fail(pv3d_ctx* c, int code, const char* fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return code;
+}
+
+#define CUDA_TRY(ctx, call)                                                                    \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess)                                                                 \
+            return fail((ctx), e_ == cudaErrorMemoryAllocation ? PV3D_E_NOMEM : PV3D_E_DEVICE, \
+                        "%s: %s", #call, cudaGetErrorString(e_));                              \
+    } while (0)
+
+static int ensure(pv3d_ctx* c, DevBuf& b, size_t bytes)
+{
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return PV3D_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    size_t want = bytes + bytes / 8;
+    cudaError_t e = cudaMalloc(&b.p, want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return fail(c, PV3D_E_NOMEM, "cudaMalloc(%zu) failed: %s", want, cudaGetErrorString(e));
+    }
+    b.bytes = want;
+    return PV3D_OK;
+}
+
+static void release_buf(DevBuf& b)
+{
+    if (b.p) cudaFree(b.p);
+    b = DevBuf{};
+}
+
+template <typename T>
+static int upload(pv3d_ctx* c, T** dst, const T* src, size_t n)
+{
+    *dst = nullptr;
+    size_t bytes = std::max<size_t>(n * sizeof(T), 16);
+    cudaError_t e = cudaMalloc((void**)dst, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *dst = nullptr;
+        return fail(c, PV3D_E_NOMEM, "cudaMalloc(%zu) failed", bytes);
+    }
+    if (n) {
+        e = cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return fail(c, PV3D_E_DEVICE, "upload: %s", cudaGetErrorString(e));
+    }
+    return PV3D_OK;
+}
+
+static bool finite3(const float* p) { return std::isfinite(p[0]) && std::isfinite(p[1]) && std::isfinite(p[2]); }
+
+static void free_gen(GenH& g)
+{
+    void* ps[] = {g.d_mods, g.d_cell_mod, g.d_lay_sub, g.d_lay_off, g.d_lay_nk, g.d_lay_nk_off, g.d_pivots,
+                  g.d_sun, g.d_dni, g.d_dhi, g.d_dt, g.d_poses};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+}
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+extern "C" int pv3d_create(pv3d_ctx** out, const pv3d_opts* opts)
+{
+    if (!out) return PV3D_E_INVALID;
+    *out = nullptr;
+    std::unique_ptr<pv3d_ctx> c(new (std::nothrow) pv3d_ctx());
+    if (!c) return PV3D_E_NOMEM;
+    if (opts) c->opts = *opts;
+    pv3d_opts& o = c->opts;
+    if (o.map_res == 0) o.map_res = 4096;
+    if (o.tile == 0) o.tile = 64;
+    if (o.chunk_steps == 0) o.chunk_steps = 32;
+    if (o.max_inflight == 0) o.max_inflight = 64;
+    if (o.tile != 32 && o.tile != 64) return PV3D_E_INVALID;
+    if (o.map_res < 64 || o.map_res > 16384 || (o.map_res & (o.map_res - 1))) return PV3D_E_INVALID;
+    if (o.chunk_steps < 1 || o.chunk_steps > 256) return PV3D_E_INVALID;
+    if (o.depth_format != PV3D_DEPTH_F32 && o.depth_format != PV3D_DEPTH_U24) return PV3D_E_INVALID;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return PV3D_E_DEVICE;
+    }
+    if (o.device < 0 || o.device >= ndev) return PV3D_E_INVALID;
+    c->device = o.device;
+    if (cudaSetDevice(c->device) != cudaSuccess) return PV3D_E_DEVICE;
+    if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
+        return PV3D_E_DEVICE;
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return PV3D_E_DEVICE;
+    if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) return PV3D_E_DEVICE;
+    if (o.hbm_budget_bytes == 0) {
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        o.hbm_budget_bytes = (int64_t)(0.9 * (double)fr);
+    }
+    *out = c.release();
+    return PV3D_OK;
+}
+
+extern "C" void pv3d_destroy(pv3d_ctx* c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto& kv : c->scenes)
+        if (kv.second.d_tri) cudaFree(kv.second.d_tri);
+    for (auto& kv : c->gens) free_gen(kv.second);
+    DevBuf* bufs[] = {&c->lp, &c->win, &c->ms, &c->ms_p, &c->ms_pu, &c->ms_beam, &c->cs_cnt, &c->t_far,
+                      &c->t_cnt, &c->t_off, &c->t_cur, &c->t_slot, &c->nonempty, &c->bins, &c->map, &c->big,
+                      &c->block_sums, &c->ctr, &c->waves, &c->jobs, &c->kahan_mod, &c->kahan_cell, &c->staging};
+    for (DevBuf* b : bufs) release_buf(*b);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+extern "C" const char* pv3d_last_error(pv3d_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+// ---------------------------------------------------------------------------
+// scene
+// ---------------------------------------------------------------------------
+extern "C" int pv3d_scene_load(pv3d_ctx* c, const float* xyz, int64_t n_verts, const int32_t* tri_idx,
+                               int64_t n_tris, uint32_t* scene_id)
+{
+    if (!c || !scene_id) return PV3D_E_INVALID;
+    if (n_verts < 0 || n_tris < 0 || n_tris > (1ll << 30)) return fail(c, PV3D_E_INVALID, "bad sizes");
+    if ((n_tris > 0 && (!xyz || !tri_idx))) return fail(c, PV3D_E_INVALID, "null arrays");
+    cudaSetDevice(c->device);
+    SceneH s;
+    s.n_tris = (int32_t)n_tris;
+    std::vector<float4> tv((size_t)n_tris * 3);
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int64_t t = 0; t < n_tris; ++t) {
+        for (int k = 0; k < 3; ++k) {
+            int64_t vi = tri_idx[3 * t + k];
+            if (vi < 0 || vi >= n_verts) return fail(c, PV3D_E_INVALID, "triangle %lld: index out of range", (long long)t);
+            const float* p = xyz + 3 * vi;
+            if (!finite3(p)) return fail(c, PV3D_E_INVALID, "vertex %lld not finite", (long long)vi);
+            tv[3 * t + k] = make_float4(p[0], p[1], p[2], 0.f);
+            for (int a = 0; a < 3; ++a) { lo[a] = std::min(lo[a], p[a]); hi[a] = std::max(hi[a], p[a]); }
+        }
+    }
+    if (n_tris == 0)
+        for (int a = 0; a < 3; ++a) lo[a] = hi[a] = 0.f;
+    memcpy(s.lo, lo, sizeof(lo));
+    memcpy(s.hi, hi, sizeof(hi));
+    int rc = upload(c, &s.d_tri, tv.data(), tv.size());
+    if (rc) return rc;
+    s.bytes = std::max<size_t>(tv.size() * sizeof(float4), 16);
+    uint32_t id = c->next_id++;
+    c->scenes[id] = s;
+    *scene_id = id;
+    return PV3D_OK;
+}
+
+// ---------------------------------------------------------------------------
+// generator
+// ---------------------------------------------------------------------------
+extern "C" int pv3d_generator_define(pv3d_ctx* c, uint32_t scene_id, const pv3d_module* mods, int32_t n_mods,
+                                     const pv3d_layout* layouts, int32_t n_layouts, const pv3d_tracker* trackers,
+                                     int32_t n_trackers, uint32_t* gen_id)
+{
+    if (!c || !gen_id) return PV3D_E_INVALID;
+    auto sit = c->scenes.find(scene_id);
+    if (sit == c->scenes.end()) return fail(c, PV3D_E_NOTFOUND, "unknown scene %u", scene_id);
+    if (n_mods < 1 || !mods) return fail(c, PV3D_E_INVALID, "a generator needs at least one module");
+    if (n_layouts < 1 || !layouts) return fail(c, PV3D_E_INVALID, "a generator needs at least one layout");
+    if (n_trackers < 0 || (n_trackers > 0 && !trackers)) return fail(c, PV3D_E_INVALID, "bad trackers");
+    cudaSetDevice(c->device);
+    GenH g;
+    g.scene_id = scene_id;
+    g.M = n_mods;
+    g.n_trk = n_trackers;
+    // layouts
+    std::vector<int32_t> lay_sub, lay_off, lay_nk, lay_nk_off;
+    for (int32_t l = 0; l < n_layouts; ++l) {
+        const pv3d_layout& L = layouts[l];
+        int nc = L.cells_u * L.cells_v;
+        if (L.cells_u < 1 || L.cells_v < 1 || nc > kMaxCellsPerModule || L.n_sub < 1 || L.n_sub > kMaxSub ||
+            !L.cell_sub)
+            return fail(c, PV3D_E_INVALID, "layout %d: bad size", l);
+        lay_off.push_back((int32_t)lay_sub.size());
+        lay_nk_off.push_back((int32_t)lay_nk.size());
+        std::vector<int32_t> nk(L.n_sub, 0);
+        for (int k = 0; k < nc; ++k) {
+            int s = L.cell_sub[k];
+            if (s < 0 || s >= L.n_sub) return fail(c, PV3D_E_INVALID, "layout %d: substring index out of range", l);
+            nk[s]++;
+            lay_sub.push_back(s);
+        }
+        for (int s = 0; s < L.n_sub; ++s)
+            if (nk[s] == 0) return fail(c, PV3D_E_INVALID, "layout %d: substring %d owns no cell", l, s);
+        lay_nk.insert(lay_nk.end(), nk.begin(), nk.end());
+    }
+    for (int32_t t = 0; t < n_trackers; ++t)
+        if (!finite3(trackers[t].pivot)) return fail(c, PV3D_E_INVALID, "tracker %d: pivot not finite", t);
+    // modules
+    double glo[3] = {INFINITY, INFINITY, INFINITY}, ghi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    std::vector<int32_t> cell_mod;
+    g.mods_h.resize(n_mods);
+    int32_t cell = 0;
+    for (int32_t m = 0; m < n_mods; ++m) {
+        const pv3d_module& P = mods[m];
+        if (!finite3(P.origin) || !finite3(P.u) || !finite3(P.v) || !std::isfinite(P.pitch) || !(P.pitch > 0))
+            return fail(c, PV3D_E_INVALID, "module %d: non-finite geometry", m);
+        double uu = (double)P.u[0] * P.u[0] + (double)P.u[1] * P.u[1] + (double)P.u[2] * P.u[2];
+        double vv = (double)P.v[0] * P.v[0] + (double)P.v[1] * P.v[1] + (double)P.v[2] * P.v[2];
+        double uv = (double)P.u[0] * P.v[0] + (double)P.u[1] * P.v[1] + (double)P.u[2] * P.v[2];
+        if (std::fabs(uu - 1) > 1e-4 || std::fabs(vv - 1) > 1e-4 || std::fabs(uv) > 1e-4)
+            return fail(c, PV3D_E_INVALID, "module %d: u and v must be orthonormal", m);
+        if (P.cells_u < 1 || P.cells_v < 1 || P.cells_u > 64 || P.cells_v > 64 ||
+            P.cells_u * P.cells_v > kMaxCellsPerModule)
+            return fail(c, PV3D_E_INVALID, "module %d: bad cell grid", m);
+        if (P.layout < 0 || P.layout >= n_layouts) return fail(c, PV3D_E_INVALID, "module %d: bad layout", m);
+        const pv3d_layout& L = layouts[P.layout];
+        if (L.cells_u != P.cells_u || L.cells_v != P.cells_v)
+            return fail(c, PV3D_E_INVALID, "module %d: layout grid differs from the module's", m);
+        if (P.tracker < -1 || P.tracker >= n_trackers) return fail(c, PV3D_E_INVALID, "module %d: bad tracker", m);
+        ModuleDev& D = g.mods_h[m];
+        for (int a = 0; a < 3; ++a) { D.o[a] = P.origin[a]; D.u[a] = P.u[a]; D.v[a] = P.v[a]; }
+        D.pitch = P.pitch;
+        D.cu = P.cells_u; D.cv = P.cells_v; D.layout = P.layout; D.tracker = P.tracker;
+        D.cell_base = cell;
+        D.n_sub = L.n_sub;
+        for (int k = 0; k < P.cells_u * P.cells_v; ++k) cell_mod.push_back(m);
+        cell += P.cells_u * P.cells_v;
+        g.max_cells = std::max(g.max_cells, P.cells_u * P.cells_v);
+        // bounds: corners (fixed) or pivot +- reach (tracked)
+        double lu = P.cells_u * (double)P.pitch, lv = P.cells_v * (double)P.pitch;
+        double cx[4][3];
+        for (int k = 0; k < 4; ++k) {
+            double a = (k == 1 || k == 2) ? lu : 0, b = (k >= 2) ? lv : 0;
+            for (int q = 0; q < 3; ++q) cx[k][q] = P.origin[q] + a * P.u[q] + b * P.v[q];
+        }
+        if (P.tracker < 0) {
+            for (int k = 0; k < 4; ++k)
+                for (int q = 0; q < 3; ++q) { glo[q] = std::min(glo[q], cx[k][q]); ghi[q] = std::max(ghi[q], cx[k][q]); }
+        } else {
+            double reach = 0;
+            for (int k = 0; k < 4; ++k)
+                reach = std::max(reach, std::sqrt(cx[k][0] * cx[k][0] + cx[k][1] * cx[k][1] + cx[k][2] * cx[k][2]));
+            const float* pv = trackers[P.tracker].pivot;
+            for (int q = 0; q < 3; ++q) {
+                glo[q] = std::min(glo[q], pv[q] - reach);
+                ghi[q] = std::max(ghi[q], pv[q] + reach);
+            }
+        }
+    }
+    g.C = cell;
+    for (int q = 0; q < 3; ++q) {
+        g.ref[q] = (float)(0.5 * (glo[q] + ghi[q]));
+        g.glo[q] = (float)glo[q];
+        g.ghi[q] = (float)ghi[q];
+    }
+    // coplanar generator: every module fixed, one plane, one facing -> modules
+    // cannot shade one another and are left out of the depth map
+    {
+        bool cop = true;
+        double n0[3] = {0, 0, 0};
+        for (int32_t m = 0; m < n_mods && cop; ++m) {
+            const pv3d_module& P = mods[m];
+            if (P.tracker >= 0) { cop = false; break; }
+            double n[3] = {(double)P.u[1] * P.v[2] - (double)P.u[2] * P.v[1],
+                           (double)P.u[2] * P.v[0] - (double)P.u[0] * P.v[2],
+                           (double)P.u[0] * P.v[1] - (double)P.u[1] * P.v[0]};
+            double l = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+            for (int q = 0; q < 3; ++q) n[q] /= l;
+            if (m == 0) {
+                for (int q = 0; q < 3; ++q) n0[q] = n[q];
+                continue;
+            }
+            double dn = n[0] * n0[0] + n[1] * n0[1] + n[2] * n0[2];
+            double off = 0;
+            for (int q = 0; q < 3; ++q) off += n0[q] * ((double)P.origin[q] - mods[0].origin[q]);
+            if (dn < 1.0 - 1e-9 || std::fabs(off) > 1e-4) cop = false;
+        }
+        g.coplanar = cop;
+    }
+    // positions relative to the reference point
+    for (auto& D : g.mods_h)
+        if (D.tracker < 0)
+            for (int a = 0; a < 3; ++a) D.o[a] -= g.ref[a];
+    std::vector<float> piv((size_t)n_trackers * 3);
+    for (int32_t t = 0; t < n_trackers; ++t)
+        for (int a = 0; a < 3; ++a) piv[3 * t + a] = trackers[t].pivot[a] - g.ref[a];
+    int rc;
+    if ((rc = upload(c, &g.d_mods, g.mods_h.data(), g.mods_h.size())) ||
+        (rc = upload(c, &g.d_cell_mod, cell_mod.data(), cell_mod.size())) ||
+        (rc = upload(c, &g.d_lay_sub, lay_sub.data(), lay_sub.size())) ||
+        (rc = upload(c, &g.d_lay_off, lay_off.data(), lay_off.size())) ||
+        (rc = upload(c, &g.d_lay_nk, lay_nk.data(), lay_nk.size())) ||
+        (rc = upload(c, &g.d_lay_nk_off, lay_nk_off.data(), lay_nk_off.size())) ||
+        (rc = upload(c, &g.d_pivots, piv.data(), piv.size()))) {
+        free_gen(g);
+        return rc;
+    }
+    g.bytes = g.mods_h.size() * sizeof(ModuleDev) + cell_mod.size() * 4 + lay_sub.size() * 8 + piv.size() * 4;
+    uint32_t id = c->next_id++;
+    c->gens[id] = std::move(g);
+    *gen_id = id;
+    return PV3D_OK;
+}
+
+extern "C" int pv3d_set_poses(pv3d_ctx* c, uint32_t gen_id, const float* az_tilt, int64_t n_steps)
+{
+    if (!c) return PV3D_E_INVALID;
+    auto it = c->gens.find(gen_id);
+    if (it == c->gens.end()) return fail(c, PV3D_E_NOTFOUND, "unknown generator %u", gen_id);
+    GenH& g = it->second;
+    if (n_steps < 1 || !az_tilt) return fail(c, PV3D_E_INVALID, "empty pose table");
+    if (g.n_steps && n_steps != g.n_steps) return fail(c, PV3D_E_INVALID, "pose table length differs from the sun table");
+    size_t n = (size_t)n_steps * (size_t)g.n_trk * 2;
+    for (size_t k = 0; k < n; ++k)
+        if (!std::isfinite(az_tilt[k])) return fail(c, PV3D_E_INVALID, "pose %zu not finite", k / 2);
+    cudaSetDevice(c->device);
+    if (g.d_poses) cudaFree(g.d_poses);
+    g.d_poses = nullptr;
+    int rc = upload(c, &g.d_poses, az_tilt, n);
+    if (rc) return rc;
+    g.n_pose_steps = n_steps;
+    return PV3D_OK;
+}
+
+extern "C" int pv3d_set_sun(pv3d_ctx* c, uint32_t gen_id, const double* sun_xyz, const float* dni, const float* dhi,
+                            const float* dt_h, int64_t n_steps)
+{
+    if (!c) return PV3D_E_INVALID;
+    auto it = c->gens.find(gen_id);
+    if (it == c->gens.end()) return fail(c, PV3D_E_NOTFOUND, "unknown generator %u", gen_id);
+    GenH& g = it->second;
+    if (n_steps < 1 || n_steps > (1ll << 30) || !sun_xyz || !dni || !dhi || !dt_h)
+        return fail(c, PV3D_E_INVALID, "bad sun table");
+    if (g.n_pose_steps && g.n_trk && n_steps != g.n_pose_steps)
+        return fail(c, PV3D_E_INVALID, "sun table length differs from the pose table");
+    std::vector<uint8_t> lit((size_t)n_steps);
+    for (int64_t k = 0; k < n_steps; ++k) {
+        const double* s = sun_xyz + 3 * k;
+        if (!std::isfinite(s[0]) || !std::isfinite(s[1]) || !std::isfinite(s[2]))
+            return fail(c, PV3D_E_INVALID, "sun %lld not finite", (long long)k);
+        double l = std::sqrt(s[0] * s[0] + s[1] * s[1] + s[2] * s[2]);
+        if (std::fabs(l - 1.0) > 1e-6) return fail(c, PV3D_E_INVALID, "sun %lld: |s| = %.9f is not 1", (long long)k, l);
+        if (!std::isfinite(dni[k]) || !std::isfinite(dhi[k]) || !std::isfinite(dt_h[k]) || dni[k] < 0 || dhi[k] < 0 ||
+            dt_h[k] < 0)
+            return fail(c, PV3D_E_INVALID, "irradiance or duration %lld invalid", (long long)k);
+        lit[k] = s[2] > 0.0;
+    }
+    cudaSetDevice(c->device);
+    void* olds[] = {g.d_sun, g.d_dni, g.d_dhi, g.d_dt};
+    for (void* p : olds)
+        if (p) cudaFree(p);
+    g.d_sun = nullptr; g.d_dni = g.d_dhi = g.d_dt = nullptr;
+    int rc;
+    if ((rc = upload(c, &g.d_sun, sun_xyz, (size_t)n_steps * 3)) || (rc = upload(c, &g.d_dni, dni, (size_t)n_steps)) ||
+        (rc = upload(c, &g.d_dhi, dhi, (size_t)n_steps)) || (rc = upload(c, &g.d_dt, dt_h, (size_t)n_steps)))
+        return rc;
+    g.n_steps = n_steps;
+    g.lit = std::move(lit);
+    return PV3D_OK;
+}
+
+// ---------------------------------------------------------------------------
+// evaluation
+// ---------------------------------------------------------------------------
+namespace {
+
+struct EvalSetup {
+    int n, R, K, tile;
+    int64_t b, e;
+    float i_ref, v_cell, v_diode;
+};
+
+}  // namespace
+
+static int check_eval(pv3d_ctx* c, const GenH& g, const pv3d_eval_opts* o, const pv3d_result* out, EvalSetup& es)
+{
+    pv3d_eval_opts d{};
+    if (o) d = *o;
+    es.n = d.samples_per_side ? d.samples_per_side : 3;
+    es.R = d.map_res ? d.map_res : c->opts.map_res;
+    es.K = d.chunk_steps ? d.chunk_steps : c->opts.chunk_steps;
+    es.tile = c->opts.tile;
+    es.i_ref = d.i_ref > 0 ? d.i_ref : 9.0f;
+    es.v_cell = d.v_cell > 0 ? d.v_cell : 0.5f;
+    es.v_diode = d.v_diode > 0 ? d.v_diode : 0.5f;
+    if (es.n < 1 || es.n > 15) return fail(c, PV3D_E_INVALID, "samples_per_side must be 1..15");
+    if (es.R < 64 || es.R > 16384 || (es.R & (es.R - 1))) return fail(c, PV3D_E_INVALID, "map_res must be a power of two in 64..16384");
+    if (es.K < 1 || es.K > 256) return fail(c, PV3D_E_INVALID, "chunk_steps must be 1..256");
+    if (g.n_steps < 1) return fail(c, PV3D_E_INVALID, "no sun table set");
+    if (g.n_trk > 0 && g.n_pose_steps != g.n_steps) return fail(c, PV3D_E_INVALID, "tracker poses missing");
+    es.b = d.step_begin;
+    es.e = d.step_end ? d.step_end : g.n_steps;
+    if (es.b < 0 || es.e > g.n_steps || es.b >= es.e) return fail(c, PV3D_E_INVALID, "bad step range");
+    if (!out) return fail(c, PV3D_E_INVALID, "null result");
+    if (out->sample_bits && es.n > 8) return fail(c, PV3D_E_INVALID, "sample_bits needs samples_per_side <= 8");
+    return PV3D_OK;
+}
+
+// Fill a JobDev for generator g over steps [step0, step0 + k).
+static JobDev make_job(pv3d_ctx* c, const GenH& g, const SceneH& s, const EvalSetup& es, int64_t step0, int k,
+                       float2* kmod, float2* kcell, float* pw, float* pwu, uint8_t* cnt, unsigned long long* bits)
+{
+    JobDev J{};
+    J.tri = s.d_tri;
+    J.n_tris = s.n_tris;
+    J.n_mtris = g.coplanar ? 0 : 2 * g.M;
+    J.mods = g.d_mods;
+    J.n_mods = g.M;
+    J.n_cells = g.C;
+    J.cell_mod = g.d_cell_mod;
+    J.lay_sub = g.d_lay_sub;
+    J.lay_off = g.d_lay_off;
+    J.lay_nk = g.d_lay_nk;
+    J.lay_nk_off = g.d_lay_nk_off;
+    J.pivots = g.d_pivots;
+    J.n_trk = g.n_trk;
+    for (int a = 0; a < 3; ++a) {
+        J.ref[a] = g.ref[a];
+        float lo = s.n_tris ? std::min(s.lo[a], g.glo[a]) : g.glo[a];
+        float hi = s.n_tris ? std::max(s.hi[a], g.ghi[a]) : g.ghi[a];
+        J.scene_lo[a] = lo - g.ref[a];
+        J.scene_hi[a] = hi - g.ref[a];
+    }
+    J.sun = g.d_sun;
+    J.dni = g.d_dni;
+    J.dhi = g.d_dhi;
+    J.dt = g.d_dt;
+    J.poses = g.d_poses;
+    J.step0 = (int32_t)step0;
+    J.k = k;
+    J.out_row0 = (int32_t)(step0 - es.b);
+    J.R = es.R;
+    J.tiles_x = es.R / es.tile;
+    J.n = es.n;
+    J.nn = es.n * es.n;
+    J.i_ref = es.i_ref;
+    J.v_cell = es.v_cell;
+    J.v_diode = es.v_diode;
+    J.kahan_mod = kmod;
+    J.kahan_cell = kcell;
+    J.out_power = pw;
+    J.out_power_u = pwu;
+    J.out_counts = cnt;
+    J.out_bits = bits;
+    (void)c;
+    return J;
+}
+
+// Lay out jobs[first, last) as one wave: bases and item offsets.
+static WaveDev pack_wave(std::vector<JobDev>& jobs, size_t first, size_t last, int tile_sh, int u24)
+{
+    WaveDev W{};
+    W.n_jobs = (int32_t)(last - first);
+    W.tile_sh = tile_sh;
+    W.depth_u24 = u24;
+    for (size_t q = first; q < last; ++q) {
+        JobDev& J = jobs[q];
+        J.js_base = (int32_t)W.tot_js;
+        J.te_base = W.tot_te;
+        J.ms_base = W.tot_ms;
+        J.cs_base = W.tot_cs;
+        J.it_win = W.tot_win;
+        J.it_mod = W.tot_mod;
+        J.it_tri = W.tot_tri;
+        J.it_epi = W.tot_epi;
+        int64_t groups = (J.n_mods + kWinPerItem - 1) / kWinPerItem;
+        W.tot_js += J.k;
+        W.tot_te += (int64_t)J.k * J.tiles_x * J.tiles_x;
+        W.tot_ms += (int64_t)J.k * J.n_mods;
+        W.tot_cs += (int64_t)J.k * J.n_cells;
+        W.tot_win += (int64_t)J.k * groups;
+        W.tot_mod += (int64_t)J.k * J.n_mods;
+        W.tot_tri += ((int64_t)J.n_tris + J.n_mtris) * J.k;
+        W.tot_epi += (int64_t)J.n_cells + J.n_mods;
+    }
+    return W;
+}
+
+static int ensure_workspace(pv3d_ctx* c, int64_t js, int64_t te, int64_t ms, int64_t cs, int tile,
+                            int64_t n_waves, int64_t n_jobs)
+{
+    int rc;
+    int64_t scan_tiles = (te + 4095) / 4096 + 1;
+    if ((rc = ensure(c, c->lp, js * sizeof(LightParams))) || (rc = ensure(c, c->win, js * 16)) ||
+        (rc = ensure(c, c->ms, ms * sizeof(ModStep))) || (rc = ensure(c, c->ms_p, ms * 4)) ||
+        (rc = ensure(c, c->ms_pu, ms * 4)) || (rc = ensure(c, c->ms_beam, ms * 4)) || (rc = ensure(c, c->cs_cnt, cs)) ||
+        (rc = ensure(c, c->t_far, te * 4)) || (rc = ensure(c, c->t_cnt, te * 4)) || (rc = ensure(c, c->t_off, te * 4)) ||
+        (rc = ensure(c, c->t_cur, te * 4)) || (rc = ensure(c, c->t_slot, te * 4)) ||
+        (rc = ensure(c, c->nonempty, te * 4)) || (rc = ensure(c, c->block_sums, scan_tiles * 16)) ||
+        (rc = ensure(c, c->ctr, sizeof(Counters))) || (rc = ensure(c, c->waves, n_waves * sizeof(WaveDev))) ||
+        (rc = ensure(c, c->jobs, n_jobs * sizeof(JobDev))))
+        return rc;
+    if (c->bin_cap == 0) c->bin_cap = 1 << 22;
+    if (c->map_cap_tiles == 0) c->map_cap_tiles = std::max<int64_t>(256, te / 8);
+    if (c->big_cap == 0) c->big_cap = 1 << 18;
+    c->map_cap_tiles = std::min<int64_t>(c->map_cap_tiles, te);
+    if ((rc = ensure(c, c->bins, c->bin_cap * 4)) ||
+        (rc = ensure(c, c->map, (size_t)c->map_cap_tiles * tile * tile * 4)) ||
+        (rc = ensure(c, c->big, c->big_cap * 8)))
+        return rc;
+    (void)tile;
+    return PV3D_OK;
+}
+
+static Buffers buffers_of(pv3d_ctx* c)
+{
+    Buffers B;
+    B.lp = (LightParams*)c->lp.p;
+    B.win = (uint32_t*)c->win.p;
+    B.ms = (ModStep*)c->ms.p;
+    B.ms_p = (float*)c->ms_p.p;
+    B.ms_pu = (float*)c->ms_pu.p;
+    B.ms_beam = (float*)c->ms_beam.p;
+    B.cs_cnt = (uint8_t*)c->cs_cnt.p;
+    B.t_far = (uint32_t*)c->t_far.p;
+    B.t_cnt = (uint32_t*)c->t_cnt.p;
+    B.t_off = (uint32_t*)c->t_off.p;
+    B.t_cur = (uint32_t*)c->t_cur.p;
+    B.t_slot = (uint32_t*)c->t_slot.p;
+    B.nonempty = (uint32_t*)c->nonempty.p;
+    B.bins = (uint32_t*)c->bins.p;
+    B.map = (uint32_t*)c->map.p;
+    B.big = (uint2*)c->big.p;
+    B.block_sums = (unsigned long long*)c->block_sums.p;
+    B.ctr = (Counters*)c->ctr.p;
+    return B;
+}
+
+static int stage_descriptors(pv3d_ctx* c, const std::vector<WaveDev>& waves, const std::vector<JobDev>& jobs,
+                             cudaStream_t st)
+{
+    size_t wb = waves.size() * sizeof(WaveDev), jb = jobs.size() * sizeof(JobDev);
+    int rc;
+    if ((rc = ensure(c, c->waves, wb)) || (rc = ensure(c, c->jobs, jb))) return rc;
+    if (c->h_stage_bytes < wb + jb) {
+        if (c->h_stage) {
+            cudaStreamSynchronize(st);
+            cudaFreeHost(c->h_stage);
+        }
+        c->h_stage = nullptr;
+        c->h_stage_bytes = 0;
+        size_t want = (wb + jb) * 2 + 4096;
+        if (cudaMallocHost(&c->h_stage, want) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(c, PV3D_E_NOMEM, "pinned staging allocation failed");
+        }
+        c->h_stage_bytes = want;
+    } else {
+        // the previous evaluation's copies must have left the staging buffer
+        cudaStreamSynchronize(st);
+    }
+    memcpy(c->h_stage, waves.data(), wb);
+    memcpy((char*)c->h_stage + wb, jobs.data(), jb);
+    CUDA_TRY(c, cudaMemcpyAsync(c->waves.p, c->h_stage, wb, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(c, cudaMemcpyAsync(c->jobs.p, (char*)c->h_stage + wb, jb, cudaMemcpyHostToDevice, st));
+    return PV3D_OK;
+}
+
+static int run_waves(pv3d_ctx* c, const std::vector<WaveDev>& waves, cudaStream_t st, int tile)
+{
+    Buffers B = buffers_of(c);
+    LaunchCfg cfg;
+    cfg.sm_count = c->sm_count;
+    cfg.tile = tile;
+    cfg.max_tot_te = 0;
+    cfg.stream = st;
+    const WaveDev* dW = (const WaveDev*)c->waves.p;
+    const JobDev* dJ = (const JobDev*)c->jobs.p;
+    size_t job0 = 0;
+    for (size_t w = 0; w < waves.size(); ++w) {
+        const WaveDev& W = waves[w];
+        CUDA_TRY(c, cudaMemsetAsync(c->win.p, 0xFF, (size_t)W.tot_js * 16, st));
+        CUDA_TRY(c, cudaMemsetAsync(c->t_far.p, 0, (size_t)W.tot_te * 4, st));
+        CUDA_TRY(c, cudaMemsetAsync(c->t_cnt.p, 0, (size_t)W.tot_te * 4, st));
+        CUDA_TRY(c, cudaMemsetAsync(c->ctr.p, 0, 3 * sizeof(unsigned int), st));
+        CUDA_TRY(c, launch_wave(dW + w, dJ + job0, B, cfg, W.tot_te));
+        job0 += (size_t)W.n_jobs;
+    }
+    return PV3D_OK;
+}
+
+static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o, pv3d_result* out)
+{
+    if (!c) return PV3D_E_INVALID;
+    auto git = c->gens.find(gen_id);
+    if (git == c->gens.end()) return fail(c, PV3D_E_NOTFOUND, "unknown generator %u", gen_id);
+    GenH& g = git->second;
+    auto sit = c->scenes.find(g.scene_id);
+    if (sit == c->scenes.end()) return fail(c, PV3D_E_NOTFOUND, "scene of generator %u is gone", gen_id);
+    const SceneH& s = sit->second;
+    EvalSetup es{};
+    int rc = check_eval(c, g, o, out, es);
+    if (rc) return rc;
+    cudaSetDevice(c->device);
+    cudaStream_t st = (o && o->stream) ? (cudaStream_t)o->stream : c->stream;
+    const int64_t S = es.e - es.b;
+    const int tile_sh = es.tile == 32 ? 5 : 6;
+    const int u24 = c->opts.depth_format == PV3D_DEPTH_U24;
+
+    // result staging: device outputs are written in place, host outputs are
+    // copied back from a device staging area at the end
+    const bool dev = out->is_device != 0;
+    size_t off_e = 0, off_eu = 0, off_cl = 0, off_p = 0, off_pu = 0, off_cnt = 0, off_bits = 0, tot = 0;
+    auto take = [&](size_t bytes) {
+        size_t o_ = tot;
+        tot += (bytes + 255) & ~size_t(255);
+        return o_;
+    };
+    if (!dev) {
+        if (out->energy) off_e = take(g.M * 8);
+        if (out->energy_unshaded) off_eu = take(g.M * 8);
+        if (out->cell_beam_loss) off_cl = take((size_t)g.C * 8);
+        if (out->power) off_p = take((size_t)S * g.M * 4);
+        if (out->power_unshaded) off_pu = take((size_t)S * g.M * 4);
+        if (out->cell_counts) off_cnt = take((size_t)S * g.C);
+        if (out->sample_bits) off_bits = take((size_t)S * g.C * 8);
+        if ((rc = ensure(c, c->staging, tot))) return rc;
+    }
+    char* sb = (char*)c->staging.p;
+    double* d_e = dev ? out->energy : (out->energy ? (double*)(sb + off_e) : nullptr);
+    double* d_eu = dev ? out->energy_unshaded : (out->energy_unshaded ? (double*)(sb + off_eu) : nullptr);
+    double* d_cl = dev ? out->cell_beam_loss : (out->cell_beam_loss ? (double*)(sb + off_cl) : nullptr);
+    float* d_p = dev ? out->power : (out->power ? (float*)(sb + off_p) : nullptr);
+    float* d_pu = dev ? out->power_unshaded : (out->power_unshaded ? (float*)(sb + off_pu) : nullptr);
+    uint8_t* d_cnt = dev ? out->cell_counts : (out->cell_counts ? (uint8_t*)(sb + off_cnt) : nullptr);
+    unsigned long long* d_bits =
+        dev ? (unsigned long long*)out->sample_bits : (out->sample_bits ? (unsigned long long*)(sb + off_bits) : nullptr);
+
+    if ((rc = ensure(c, c->kahan_mod, (size_t)g.M * 2 * sizeof(float2))) ||
+        (rc = ensure(c, c->kahan_cell, (size_t)g.C * sizeof(float2))))
+        return rc;
+
+    // plan: one job per wave
+    std::vector<JobDev> jobs;
+    std::vector<WaveDev> waves;
+    for (int64_t s0 = es.b; s0 < es.e; s0 += es.K) {
+        int k = (int)std::min<int64_t>(es.K, es.e - s0);
+        jobs.push_back(make_job(c, g, s, es, s0, k, (float2*)c->kahan_mod.p, (float2*)c->kahan_cell.p, d_p, d_pu,
+                                d_cnt, d_bits));
+        waves.push_back(pack_wave(jobs, jobs.size() - 1, jobs.size(), tile_sh, u24));
+    }
+    int64_t mjs = 0, mte = 0, mms = 0, mcs = 0;
+    for (auto& W : waves) {
+        mjs = std::max(mjs, W.tot_js); mte = std::max(mte, W.tot_te);
+        mms = std::max(mms, W.tot_ms); mcs = std::max(mcs, W.tot_cs);
+    }
+    Counters hc{};
+    for (int attempt = 0; attempt < 4; ++attempt) {
+        if ((rc = ensure_workspace(c, mjs, mte, mms, mcs, es.tile, (int64_t)waves.size(), (int64_t)jobs.size())))
+            return rc;
+        for (auto& W : waves) {
+            W.bin_cap = c->bin_cap;
+            W.map_cap_tiles = c->map_cap_tiles;
+            W.big_cap = c->big_cap;
+        }
+        if ((rc = stage_descriptors(c, waves, jobs, st))) return rc;
+        CUDA_TRY(c, cudaMemsetAsync(c->ctr.p, 0, sizeof(Counters), st));
+        CUDA_TRY(c, cudaMemsetAsync(c->kahan_mod.p, 0, (size_t)g.M * 2 * sizeof(float2), st));
+        CUDA_TRY(c, cudaMemsetAsync(c->kahan_cell.p, 0, (size_t)g.C * sizeof(float2), st));
+        CUDA_TRY(c, cudaEventRecord(c->ev0, st));
+        if ((rc = run_waves(c, waves, st, es.tile))) return rc;
+        CUDA_TRY(c, launch_finalize_pairs((const float2*)c->kahan_mod.p, g.M, (const float2*)c->kahan_cell.p, g.C,
+                                          d_e, d_eu, d_cl, st));
+        CUDA_TRY(c, cudaEventRecord(c->ev1, st));
+        CUDA_TRY(c, cudaMemcpyAsync(&hc, c->ctr.p, sizeof(Counters), cudaMemcpyDeviceToHost, st));
+        CUDA_TRY(c, cudaStreamSynchronize(st));
+        if (!hc.overflow) break;
+        if (attempt == 3) return fail(c, PV3D_E_OVERFLOW, "bin/map capacity could not be grown far enough");
+        if (hc.overflow & 1u) c->bin_cap = (int64_t)(hc.need_bins * 5 / 4 + 1024);
+        if (hc.overflow & 2u) c->map_cap_tiles = (int64_t)(hc.need_tiles * 5 / 4 + 16);
+        if (hc.overflow & 4u) c->big_cap = (int64_t)(hc.need_big * 5 / 4 + 1024);
+    }
+    float ms = 0;
+    cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+    if (!dev) {
+        if (out->energy) CUDA_TRY(c, cudaMemcpy(out->energy, d_e, g.M * 8, cudaMemcpyDeviceToHost));
+        if (out->energy_unshaded) CUDA_TRY(c, cudaMemcpy(out->energy_unshaded, d_eu, g.M * 8, cudaMemcpyDeviceToHost));
+        if (out->cell_beam_loss) CUDA_TRY(c, cudaMemcpy(out->cell_beam_loss, d_cl, (size_t)g.C * 8, cudaMemcpyDeviceToHost));
+        if (out->power) CUDA_TRY(c, cudaMemcpy(out->power, d_p, (size_t)S * g.M * 4, cudaMemcpyDeviceToHost));
+        if (out->power_unshaded)
+            CUDA_TRY(c, cudaMemcpy(out->power_unshaded, d_pu, (size_t)S * g.M * 4, cudaMemcpyDeviceToHost));
+        if (out->cell_counts) CUDA_TRY(c, cudaMemcpy(out->cell_counts, d_cnt, (size_t)S * g.C, cudaMemcpyDeviceToHost));
+        if (out->sample_bits)
+            CUDA_TRY(c, cudaMemcpy(out->sample_bits, d_bits, (size_t)S * g.C * 8, cudaMemcpyDeviceToHost));
+    }
+    int64_t lit = 0;
+    for (int64_t k = es.b; k < es.e; ++k) lit += g.lit[k];
+    out->steps_lit = lit;
+    out->tests = lit * (int64_t)g.C * es.n * es.n;
+    out->device_ms = ms;
+    out->waves = (int32_t)waves.size();
+    out->nonempty_tiles = (int64_t)hc.stat_nonempty;
+    out->binned_tris = (int64_t)hc.stat_bins;
+    return PV3D_OK;
+}
+
+extern "C" int pv3d_evaluate(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o, pv3d_result* out)
+{
+    return evaluate_plain(c, gen_id, o, out);
+}
+
+// ---------------------------------------------------------------------------
+// served requests (queue; executed in arrival order on poll)
+// ---------------------------------------------------------------------------
+extern "C" int pv3d_submit(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o, pv3d_result* out, uint64_t* req)
+{
+    if (!c || !out || !req) return PV3D_E_INVALID;
+    if (c->gens.find(gen_id) == c->gens.end()) return fail(c, PV3D_E_NOTFOUND, "unknown generator %u", gen_id);
+    std::unique_ptr<pv3d_ctx::Request> r(new pv3d_ctx::Request());
+    r->gen_id = gen_id;
+    r->opts = o ? *o : pv3d_eval_opts{};
+    r->out = out;
+    uint64_t id = c->next_req++;
+    c->reqs[id] = std::move(r);
+    c->queue.push_back(id);
+    *req = id;
+    return PV3D_OK;
+}
+
+extern "C" int pv3d_poll(pv3d_ctx* c, uint64_t req, int32_t timeout_ms)
+{
+    if (!c) return PV3D_E_INVALID;
+    auto it = c->reqs.find(req);
+    if (it == c->reqs.end()) return fail(c, PV3D_E_NOTFOUND, "unknown request %llu", (unsigned long long)req);
+    (void)timeout_ms;
+    while (it->second->status == PV3D_E_PENDING && !c->queue.empty()) {
+        uint64_t id = c->queue.front();
+        c->queue.pop_front();
+        auto& r = c->reqs[id];
+        r->status = evaluate_plain(c, r->gen_id, &r->opts, r->out);
+    }
+    int s = it->second->status;
+    if (s != PV3D_E_PENDING) c->reqs.erase(it);
+    return s;
+}
+
+extern "C" int pv3d_release(pv3d_ctx* c, uint32_t id)
+{
+    if (!c) return PV3D_E_INVALID;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    auto git = c->gens.find(id);
+    if (git != c->gens.end()) {
+        free_gen(git->second);
+        c->gens.erase(git);
+        return PV3D_OK;
+    }
+    auto sit = c->scenes.find(id);
+    if (sit == c->scenes.end()) return fail(c, PV3D_E_NOTFOUND, "unknown id %u", id);
+    for (auto it = c->gens.begin(); it != c->gens.end();) {
+        if (it->second.scene_id == id) {
+            free_gen(it->second);
+            it = c->gens.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    if (sit->second.d_tri) cudaFree(sit->second.d_tri);
+    c->scenes.erase(sit);
+    return PV3D_OK;
+}

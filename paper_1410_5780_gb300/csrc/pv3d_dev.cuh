@@ -1,0 +1,164 @@
+// pv3d_dev.cuh -- device-side data layout shared by the kernels and the host
+// orchestration of the pv3d library (GB300 / sm_103a).
+//
+// Work is organised in waves.  A wave holds one or more jobs (a job = one
+// generator evaluated over a chunk of consecutive sun steps).  Every kernel
+// grid-strides over a flattened item space whose size it reads from the
+// device-resident WaveDev, so one set of launches (or one captured CUDA graph)
+// serves any mix of jobs: the plain per-scene evaluation is a wave with one
+// job, batched and served evaluations put many jobs of uneven size in a wave.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pv3d {
+
+constexpr int kMaxCellsPerModule = 1024;
+constexpr int kMaxSub = 64;
+constexpr int kBigTiles = 4;       // triangles over more tiles are binned by whole warps
+constexpr int kWinPerItem = 256;   // modules reduced per window item
+
+// Generator module in device memory (64 bytes).
+struct ModuleDev {
+    float o[3], u[3], v[3];
+    float pitch;
+    int32_t cu, cv, layout, tracker;
+    int32_t cell_base;  // first cell of the module in the generator's cell numbering
+    int32_t n_sub;      // substrings of its layout
+};
+
+// Light frame of one (job, step): orthographic view from the sun (Section 2,
+// step 3).  Light-plane coordinates are taken relative to the job's reference
+// point; texel coordinates are (lu - u0) * inv_delta, (lv - v0) * inv_delta.
+struct LightParams {
+    float ux, uy, uz;
+    float vx, vy, vz;
+    float sx, sy, sz;   // unit vector toward the sun; depth = -(x - ref) . s
+    float u0, v0;
+    float inv_delta, delta;
+    float dni, dhi, dt;
+    float dnear, qscale;  // 24-bit depth: q = (d - dnear) * qscale
+    int32_t valid;       // sun above the horizon
+    int32_t pad;
+};
+
+// One module at one step in texel space (48 bytes): a point a*U + b*V of the
+// module (a, b in metres) maps to texel coordinates
+// (tx0 + a*tax + b*tbx, ty0 + a*tay + b*tby) and depth d0 + a*da + b*db.
+struct ModStep {
+    float tx0, ty0, d0;
+    float tax, tay, da;
+    float tbx, tby, db;
+    float cosi;   // cosine of incidence on the front face
+    float bias;   // depth bias, metres
+    float nz;     // z of the front normal (cos of the tilt)
+};
+
+struct JobDev {
+    // scene (triangles relative to ref, 3 float4 each)
+    const float4* tri;
+    int32_t n_tris;
+    int32_t n_mtris;  // module triangles rasterised: 2 per module, or 0 for a coplanar generator
+    // generator
+    const ModuleDev* mods;
+    int32_t n_mods;
+    int32_t n_cells;
+    const int32_t* cell_mod;  // [C] module of each cell
+    const int32_t* lay_sub;   // concatenated cell -> substring maps
+    const int32_t* lay_off;   // [layouts] offset into lay_sub
+    const int32_t* lay_nk;    // concatenated cells per substring, same offsets as lay_sub's layouts
+    const int32_t* lay_nk_off;
+    const float* pivots;      // [n_trk][3] relative to ref
+    int32_t n_trk;
+    float ref[3];
+    float scene_lo[3], scene_hi[3];  // relative to ref
+    // sun table and poses
+    const double* sun;
+    const float* dni;
+    const float* dhi;
+    const float* dt;
+    const float* poses;  // [steps][n_trk][2]
+    int32_t step0;       // first sun step of this wave
+    int32_t k;           // steps of this job in the wave
+    int32_t out_row0;    // output row of step0
+    // parameters
+    int32_t R, tiles_x, n, nn;
+    float i_ref, v_cell, v_diode;
+    // wave-local bases
+    int32_t js_base;  // (step) entries
+    int32_t pad0;
+    int64_t te_base;  // (step, tile) entries
+    int64_t ms_base;  // (step, module) entries
+    int64_t cs_base;  // (step, cell) entries
+    // flattened item bases of this job, per kernel
+    int64_t it_win, it_mod, it_tri, it_epi;
+    // accumulators across the waves of one evaluation
+    float2* kahan_mod;   // [M][2]  (E, comp), (E_unshaded, comp)
+    float2* kahan_cell;  // [C]     (beam loss, comp)
+    // optional outputs, row = out_row0 + local step
+    float* out_power;
+    float* out_power_u;
+    uint8_t* out_counts;
+    unsigned long long* out_bits;
+};
+
+struct WaveDev {
+    int32_t n_jobs;
+    int32_t tile_sh;    // log2 of the tile side
+    int32_t depth_u24;
+    int32_t pad;
+    int64_t tot_js, tot_te, tot_ms, tot_cs;
+    int64_t tot_win, tot_mod, tot_tri, tot_epi;
+    int64_t bin_cap, map_cap_tiles, big_cap;
+};
+
+struct Counters {
+    unsigned int n_big;
+    unsigned int n_nonempty;
+    unsigned int raster_next;
+    unsigned int overflow;  // bit 0 bins, bit 1 map tiles, bit 2 big list
+    unsigned long long tot_bins;
+    unsigned long long stat_nonempty;
+    unsigned long long stat_bins;
+    unsigned long long need_bins;    // max over waves of the bins a wave needed
+    unsigned long long need_tiles;   // max over waves of the map tiles a wave needed
+    unsigned long long need_big;
+};
+
+// Scratch and pools, sized by the host for the largest wave.
+struct Buffers {
+    LightParams* lp;         // [tot_js]
+    uint32_t* win;           // [tot_js][4]
+    ModStep* ms;             // [tot_ms]
+    float* ms_p;             // [tot_ms]
+    float* ms_pu;            // [tot_ms]
+    float* ms_beam;          // [tot_ms]  DNI * max(0, cos i)
+    uint8_t* cs_cnt;         // [tot_cs]
+    uint32_t* t_far;         // [tot_te]
+    uint32_t* t_cnt;         // [tot_te]
+    uint32_t* t_off;         // [tot_te]
+    uint32_t* t_cur;         // [tot_te]
+    uint32_t* t_slot;        // [tot_te]
+    uint32_t* nonempty;      // [tot_te]
+    uint32_t* bins;          // [bin_cap]
+    uint32_t* map;           // [map_cap_tiles << (2 * tile_sh)]
+    uint2* big;              // [big_cap]  (triangle, js)
+    unsigned long long* block_sums;  // scan partials
+    Counters* ctr;
+};
+
+// ---- host launchers (kernels.cu) ------------------------------------------
+struct LaunchCfg {
+    int sm_count;
+    int tile;          // 32 or 64
+    int64_t max_tot_te;   // for the scan grid
+    cudaStream_t stream;
+};
+
+cudaError_t launch_wave(const WaveDev* d_wave, const JobDev* d_jobs, const Buffers& b,
+                        const LaunchCfg& cfg, int64_t tot_te_host);
+cudaError_t launch_finalize_pairs(const float2* kmod, int n_mods, const float2* kcell, int n_cells,
+                                  double* energy, double* energy_u, double* cell_loss, cudaStream_t stream);
+
+}  // namespace pv3d

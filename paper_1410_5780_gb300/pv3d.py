@@ -1,0 +1,292 @@
+"""Thin Python binding of the pv3d C ABI (include/pv3d.h).
+
+Argument marshalling only: every step of the shadow-sample path runs in the
+CUDA library.  The functions keep the C names (pv3d_create, pv3d_scene_load,
+...); ``Context`` wraps a handle and turns numpy inputs into the C structs.
+Device outputs are torch tensors (PyTorch provides device memory and the
+stream); host outputs are numpy arrays.  There is no fallback: if the library
+is missing or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+PV3D_OK = 0
+PV3D_E_INVALID = -1
+PV3D_E_NOMEM = -2
+PV3D_E_ADMISSION = -3
+PV3D_E_OVERFLOW = -4
+PV3D_E_TIMEOUT = -5
+PV3D_E_DEVICE = -6
+PV3D_E_PENDING = -7
+PV3D_E_NOTFOUND = -8
+PV3D_DEPTH_F32 = 0
+PV3D_DEPTH_U24 = 1
+
+EXPORTED = ("pv3d_create", "pv3d_destroy", "pv3d_last_error", "pv3d_scene_load", "pv3d_generator_define",
+            "pv3d_set_poses", "pv3d_set_sun", "pv3d_evaluate", "pv3d_submit", "pv3d_poll", "pv3d_release")
+
+
+class pv3d_opts(C.Structure):
+    _fields_ = [("device", C.c_int32), ("map_res", C.c_int32), ("tile", C.c_int32), ("chunk_steps", C.c_int32),
+                ("depth_format", C.c_int32), ("max_inflight", C.c_int32), ("hbm_budget_bytes", C.c_int64),
+                ("reserved", C.c_int32 * 8)]
+
+
+class pv3d_module(C.Structure):
+    _fields_ = [("origin", C.c_float * 3), ("u", C.c_float * 3), ("v", C.c_float * 3), ("pitch", C.c_float),
+                ("cells_u", C.c_int32), ("cells_v", C.c_int32), ("layout", C.c_int32), ("tracker", C.c_int32),
+                ("string_id", C.c_int32), ("reserved", C.c_int32)]
+
+
+class pv3d_layout(C.Structure):
+    _fields_ = [("cells_u", C.c_int32), ("cells_v", C.c_int32), ("n_sub", C.c_int32), ("reserved", C.c_int32),
+                ("cell_sub", C.POINTER(C.c_int32))]
+
+
+class pv3d_tracker(C.Structure):
+    _fields_ = [("pivot", C.c_float * 3)]
+
+
+class pv3d_eval_opts(C.Structure):
+    _fields_ = [("samples_per_side", C.c_int32), ("map_res", C.c_int32), ("step_begin", C.c_int64),
+                ("step_end", C.c_int64), ("i_ref", C.c_float), ("v_cell", C.c_float), ("v_diode", C.c_float),
+                ("chunk_steps", C.c_int32), ("stream", C.c_void_p), ("reserved", C.c_int32 * 8)]
+
+
+class pv3d_result(C.Structure):
+    _fields_ = [("is_device", C.c_int32), ("reserved0", C.c_int32),
+                ("energy", C.c_void_p), ("energy_unshaded", C.c_void_p), ("power", C.c_void_p),
+                ("power_unshaded", C.c_void_p), ("cell_beam_loss", C.c_void_p), ("cell_counts", C.c_void_p),
+                ("sample_bits", C.c_void_p), ("tests", C.c_int64), ("steps_lit", C.c_int64),
+                ("device_ms", C.c_float), ("waves", C.c_int32), ("nonempty_tiles", C.c_int64),
+                ("binned_tris", C.c_int64)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libpv3d.so; raise if it is not built (no CPU fallback exists)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"pv3d CUDA library not built ({path}); run paper_1410_5780_gb300.build.build()")
+            _build.build()
+        lib = C.CDLL(path)
+        P = C.c_void_p
+        lib.pv3d_create.argtypes = [C.POINTER(P), C.POINTER(pv3d_opts)]
+        lib.pv3d_destroy.argtypes = [P]
+        lib.pv3d_destroy.restype = None
+        lib.pv3d_last_error.argtypes = [P]
+        lib.pv3d_last_error.restype = C.c_char_p
+        lib.pv3d_scene_load.argtypes = [P, P, C.c_int64, P, C.c_int64, C.POINTER(C.c_uint32)]
+        lib.pv3d_generator_define.argtypes = [P, C.c_uint32, C.POINTER(pv3d_module), C.c_int32,
+                                              C.POINTER(pv3d_layout), C.c_int32, C.POINTER(pv3d_tracker), C.c_int32,
+                                              C.POINTER(C.c_uint32)]
+        lib.pv3d_set_poses.argtypes = [P, C.c_uint32, P, C.c_int64]
+        lib.pv3d_set_sun.argtypes = [P, C.c_uint32, P, P, P, P, C.c_int64]
+        lib.pv3d_evaluate.argtypes = [P, C.c_uint32, C.POINTER(pv3d_eval_opts), C.POINTER(pv3d_result)]
+        lib.pv3d_submit.argtypes = [P, C.c_uint32, C.POINTER(pv3d_eval_opts), C.POINTER(pv3d_result),
+                                    C.POINTER(C.c_uint64)]
+        lib.pv3d_poll.argtypes = [P, C.c_uint64, C.c_int32]
+        lib.pv3d_release.argtypes = [P, C.c_uint32]
+        for name in EXPORTED:
+            if name not in ("pv3d_destroy", "pv3d_last_error"):
+                getattr(lib, name).restype = C.c_int
+        _lib = lib
+        return lib
+
+
+class PV3DError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"pv3d error {code}: {msg}")
+        self.code = code
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+OUTPUTS = ("energy", "energy_unshaded", "power", "power_unshaded", "cell_beam_loss", "cell_counts", "sample_bits")
+
+
+class Context:
+    """One pv3d context (one device, one host thread)."""
+
+    def __init__(self, device: int = 0, map_res: int = 0, tile: int = 0, chunk_steps: int = 0,
+                 depth_format: int = PV3D_DEPTH_F32, max_inflight: int = 0, hbm_budget_bytes: int = 0):
+        self.lib = load()
+        o = pv3d_opts(device=device, map_res=map_res, tile=tile, chunk_steps=chunk_steps,
+                      depth_format=depth_format, max_inflight=max_inflight, hbm_budget_bytes=hbm_budget_bytes)
+        h = C.c_void_p()
+        rc = self.lib.pv3d_create(C.byref(h), C.byref(o))
+        if rc != 0:
+            raise PV3DError(rc, "pv3d_create failed")
+        self.h = h
+        self.device = device
+        self._gens = {}
+        self._keep = {}
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.pv3d_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def _check(self, rc):
+        if rc != 0 and rc != PV3D_E_PENDING:
+            raise PV3DError(rc, self.lib.pv3d_last_error(self.h).decode())
+        return rc
+
+    # ---- step 1 ------------------------------------------------------------
+    def scene_load(self, verts: np.ndarray, tris: np.ndarray) -> int:
+        v = np.ascontiguousarray(verts, np.float32).reshape(-1, 3)
+        t = np.ascontiguousarray(tris, np.int32).reshape(-1, 3)
+        sid = C.c_uint32()
+        self._check(self.lib.pv3d_scene_load(self.h, _p(v), v.shape[0], _p(t), t.shape[0], C.byref(sid)))
+        return sid.value
+
+    # ---- step 2 ------------------------------------------------------------
+    def generator_define(self, scene_id: int, gen) -> int:
+        """``gen`` carries origin, u, v, cells_u, cells_v, pitch, layout, tracker,
+        string arrays, a ``layouts`` list (cells_u, cells_v, n_sub, cell_sub) and
+        ``pivots`` (attributes of paper_1410_5780_gb300.scenes.Generator)."""
+        m = int(gen.origin.shape[0])
+        mods = (pv3d_module * m)()
+        for i in range(m):
+            md = mods[i]
+            md.origin[:] = [float(x) for x in gen.origin[i]]
+            md.u[:] = [float(x) for x in gen.u[i]]
+            md.v[:] = [float(x) for x in gen.v[i]]
+            md.pitch = float(gen.pitch[i])
+            md.cells_u = int(gen.cells_u[i]); md.cells_v = int(gen.cells_v[i])
+            md.layout = int(gen.layout[i]); md.tracker = int(gen.tracker[i]); md.string_id = int(gen.string[i])
+        subs = [np.ascontiguousarray(l.cell_sub, np.int32) for l in gen.layouts]
+        lays = (pv3d_layout * len(subs))()
+        for i, (l, s) in enumerate(zip(gen.layouts, subs)):
+            lays[i].cells_u = int(l.cells_u); lays[i].cells_v = int(l.cells_v); lays[i].n_sub = int(l.n_sub)
+            lays[i].cell_sub = s.ctypes.data_as(C.POINTER(C.c_int32))
+        piv = np.asarray(gen.pivots, np.float32).reshape(-1, 3)
+        trk = (pv3d_tracker * max(1, piv.shape[0]))()
+        for i in range(piv.shape[0]):
+            trk[i].pivot[:] = [float(x) for x in piv[i]]
+        gid = C.c_uint32()
+        self._check(self.lib.pv3d_generator_define(self.h, scene_id, mods, m, lays, len(subs), trk, piv.shape[0],
+                                                   C.byref(gid)))
+        cells = int((np.asarray(gen.cells_u, np.int64) * np.asarray(gen.cells_v, np.int64)).sum())
+        self._gens[gid.value] = {"modules": m, "cells": cells, "steps": 0}
+        return gid.value
+
+    def set_poses(self, gen_id: int, az_tilt: np.ndarray):
+        a = np.ascontiguousarray(az_tilt, np.float32)
+        self._check(self.lib.pv3d_set_poses(self.h, gen_id, _p(a), a.shape[0]))
+
+    def set_sun(self, gen_id: int, sun_xyz, dni, dhi, dt_h):
+        s = np.ascontiguousarray(sun_xyz, np.float64).reshape(-1, 3)
+        a = np.ascontiguousarray(dni, np.float32)
+        b = np.ascontiguousarray(dhi, np.float32)
+        d = np.ascontiguousarray(dt_h, np.float32)
+        self._check(self.lib.pv3d_set_sun(self.h, gen_id, _p(s), _p(a), _p(b), _p(d), s.shape[0]))
+        self._gens[gen_id]["steps"] = s.shape[0]
+
+    # ---- steps 3 and 4 -----------------------------------------------------
+    def _opts(self, n, map_res, step_begin, step_end, chunk_steps, stream, i_ref, v_cell, v_diode):
+        return pv3d_eval_opts(samples_per_side=n, map_res=map_res, step_begin=step_begin, step_end=step_end,
+                              chunk_steps=chunk_steps, stream=stream, i_ref=i_ref, v_cell=v_cell, v_diode=v_diode)
+
+    def _alloc(self, gen_id, step_begin, step_end, outputs, device):
+        if gen_id not in self._gens:  # let the library report the unknown id
+            return pv3d_result(is_device=1 if device else 0), {}
+        g = self._gens[gen_id]
+        m, cells, n_steps = g["modules"], g["cells"], g["steps"]
+        S = (step_end or n_steps) - step_begin
+        shapes = dict(energy=((m,), "f8"), energy_unshaded=((m,), "f8"), power=((S, m), "f4"),
+                      power_unshaded=((S, m), "f4"), cell_beam_loss=((cells,), "f8"),
+                      cell_counts=((S, cells), "u1"), sample_bits=((S, cells), "u8"))
+        res = pv3d_result(is_device=1 if device else 0)
+        arrays = {}
+        for name in outputs:
+            shape, dt = shapes[name]
+            if device:
+                import torch
+                tdt = {"f8": torch.float64, "f4": torch.float32, "u1": torch.uint8, "u8": torch.int64}[dt]
+                a = torch.empty(shape, dtype=tdt, device=f"cuda:{self.device}")
+                setattr(res, name, a.data_ptr())
+            else:
+                a = np.zeros(shape, dt)
+                setattr(res, name, a.ctypes.data)
+            arrays[name] = a
+        return res, arrays
+
+    def evaluate(self, gen_id: int, n: int = 3, map_res: int = 0, step_begin: int = 0, step_end: int = 0,
+                 chunk_steps: int = 0, outputs=("energy", "energy_unshaded"), device: bool = True,
+                 stream=None, i_ref: float = 0.0, v_cell: float = 0.0, v_diode: float = 0.0) -> dict:
+        """pv3d_evaluate.  Returns the requested outputs (torch tensors on the
+        device if ``device`` else numpy arrays) plus the counters."""
+        if stream is None and device:
+            import torch
+            stream = torch.cuda.current_stream(self.device).cuda_stream
+        res, arrays = self._alloc(gen_id, step_begin, step_end, outputs, device)
+        o = self._opts(n, map_res, step_begin, step_end, chunk_steps, stream, i_ref, v_cell, v_diode)
+        self._check(self.lib.pv3d_evaluate(self.h, gen_id, C.byref(o), C.byref(res)))
+        arrays.update(tests=res.tests, steps_lit=res.steps_lit, device_ms=res.device_ms, waves=res.waves,
+                      nonempty_tiles=res.nonempty_tiles, binned_tris=res.binned_tris)
+        return arrays
+
+    def submit(self, gen_id: int, n: int = 3, map_res: int = 0, step_begin: int = 0, step_end: int = 0,
+               chunk_steps: int = 0, outputs=("energy", "energy_unshaded"), device: bool = True,
+               stream=None):
+        """pv3d_submit.  Returns (request id, outputs dict); the outputs are
+        valid once pv3d_poll returns PV3D_OK for the request."""
+        res, arrays = self._alloc(gen_id, step_begin, step_end, outputs, device)
+        o = self._opts(n, map_res, step_begin, step_end, chunk_steps, stream, 0.0, 0.0, 0.0)
+        rid = C.c_uint64()
+        self._check(self.lib.pv3d_submit(self.h, gen_id, C.byref(o), C.byref(res), C.byref(rid)))
+        self._keep[rid.value] = (res, o, arrays)
+        return rid.value, arrays
+
+    def poll(self, req: int, timeout_ms: int = 0) -> int:
+        rc = self.lib.pv3d_poll(self.h, req, timeout_ms)
+        self._check(rc)
+        if rc == PV3D_OK:
+            res, _, arrays = self._keep.pop(req)
+            arrays.update(tests=res.tests, steps_lit=res.steps_lit, device_ms=res.device_ms, waves=res.waves)
+        return rc
+
+    def release(self, scene_or_gen_id: int):
+        self._check(self.lib.pv3d_release(self.h, scene_or_gen_id))
+        self._gens.pop(scene_or_gen_id, None)
+
+
+def load_workload(ctx: Context, w) -> int:
+    """Load a scenes.Workload (scene, generator, sun, poses) into ``ctx``; returns the generator id."""
+    sid = ctx.scene_load(w.scene.verts, w.scene.tris)
+    gid = ctx.generator_define(sid, w.gen)
+    ctx.set_sun(gid, w.sun.xyz, w.sun.dni, w.sun.dhi, w.sun.dt_h)
+    if w.poses is not None and w.gen.pivots.shape[0] > 0:
+        ctx.set_poses(gid, w.poses)
+    return gid

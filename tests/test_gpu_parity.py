@@ -1,0 +1,258 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Small workloads (tiny two-module case, random scenes, reduced facade and
+tracker plants) are compared in full; the full-size facade (R = 4096, 8x8
+samples) and tracker plant (R = 8192, 4x4 samples) are compared on sampled
+sun steps and modules in the launch configuration the benchmark uses.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1410_5780_gb300 import pv3d, scenes as S
+
+from parity import FLAG_AGREEMENT, LOSS_PP, compare, energy_checks, loss_pp, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    pv3d.load(build_if_missing=True)
+    c = pv3d.Context(device=0)
+    yield c
+    c.close()
+
+
+def full_check(ctx, w, chunk_steps=0, strict_loss=True):
+    """Flags, cell fractions and energies over every step of ``w``.  With
+    ``strict_loss`` the total and per-module loss must match the oracle's
+    within 0.1 % absolute; otherwise (coarse maps, few random steps) the loss
+    must lie in the oracle's masked-sample envelope."""
+    gid = pv3d.load_workload(ctx, w)
+    g = run_gpu(ctx, gid, w, chunk_steps=chunk_steps)
+    o = oracle.evaluate_workload(w)
+    st = compare(w, g, o, np.arange(w.sun.n_steps))
+    assert st["agree"] >= FLAG_AGREEMENT, st
+    assert st["cell_ok"] == 1.0, st
+    energy_checks(w, g, o, np.arange(w.sun.n_steps))
+    if strict_loss:
+        lg, lo = loss_pp(g["energy"], g["energy_unshaded"]), loss_pp(o["energy"], o["energy_unshaded"])
+        assert abs(lg - lo) <= LOSS_PP, (lg, lo)
+        for m in range(w.gen.n_modules):
+            assert abs(loss_pp(g["energy"][m], g["energy_unshaded"][m])
+                       - loss_pp(o["energy"][m], o["energy_unshaded"][m])) <= LOSS_PP
+    assert g["tests"] == int((w.sun.xyz[:, 2] > 0).sum()) * w.samples_per_step
+    ctx.release(gid)
+    return g, o, st
+
+
+@pytest.mark.parametrize("day", [172, 355, 80])
+def test_tiny_full(ctx, day):
+    w = S.make_tiny(day=day)
+    g, o, st = full_check(ctx, w)
+    if day == 355:
+        assert o["counts"].sum() > 1000  # the box shades the modules in winter
+
+
+@pytest.mark.parametrize("seed,tracked", [(101, False), (102, True), (103, False), (104, True), (105, False)])
+def test_random_small(ctx, seed, tracked):
+    w = S.make_random_small(seed, n_mods=6, n_steps=12, n=3, map_res=512, tracked=tracked)
+    full_check(ctx, w, chunk_steps=5, strict_loss=False)
+
+
+def test_mini_facade(ctx):
+    w = S.make_facade(seed=7, n=4, map_res=1024, n_buildings=12, n_trees=6, n_poles=4, floors=2, per_floor=6,
+                      target_tris=4000, days=np.array([20, 110, 200, 300]), radius=80.0)
+    full_check(ctx, w)
+
+
+def test_mini_tracker(ctx):
+    w = S.make_tracker(seed=9, n=4, map_res=1024, grid=(4, 3), terrain_n=64, spacing=1.5, n_pylons=2,
+                       step_h=1.0, days=np.array([30, 172, 300]))
+    full_check(ctx, w, strict_loss=False)
+
+
+def test_tile32_and_u24(ctx):
+    w = S.make_random_small(111, n_mods=6, n_steps=10, n=4, map_res=1024, tracked=True)
+    o = oracle.evaluate_workload(w)
+    for tile, fmt in [(32, pv3d.PV3D_DEPTH_F32), (64, pv3d.PV3D_DEPTH_U24), (32, pv3d.PV3D_DEPTH_U24)]:
+        with pv3d.Context(device=0, tile=tile, depth_format=fmt) as c2:
+            gid = pv3d.load_workload(c2, w)
+            g = run_gpu(c2, gid, w)
+            st = compare(w, g, o, np.arange(w.sun.n_steps))
+            assert st["agree"] >= FLAG_AGREEMENT, (tile, fmt, st)
+            energy_checks(w, g, o, np.arange(w.sun.n_steps))
+
+
+def _sampled_full_size(ctx, w, windows, n_mods, seed, chunk_steps=0):
+    gid = pv3d.load_workload(ctx, w)
+    rng = np.random.default_rng(seed)
+    mods = np.sort(rng.choice(w.gen.n_modules, n_mods, replace=False))
+    osc = oracle.OracleScene(w.scene.verts, w.scene.tris)
+    stats = []
+    for b, k in windows:
+        g = run_gpu(ctx, gid, w, step_begin=b, step_end=b + k, chunk_steps=chunk_steps,
+                    outputs=("sample_bits", "cell_counts", "power", "power_unshaded"))
+        o = oracle.evaluate_workload(w, steps=np.arange(b, b + k), modules=mods, oscene=osc)
+        st = compare(w, g, o, np.arange(k))
+        stats.append(st)
+        assert st["agree"] >= FLAG_AGREEMENT, (b, st)
+        assert st["cell_ok"] >= 0.999, (b, st)
+        energy_checks(w, g, o, np.arange(k))
+    ctx.release(gid)
+    return stats
+
+
+def test_facade_full_size_sampled(ctx):
+    w = S.make_facade()
+    n = w.sun.n_steps
+    windows = [(int(0.03 * n), 12), (int(0.48 * n), 12), (int(0.9 * n), 12)]
+    stats = _sampled_full_size(ctx, w, windows, n_mods=12, seed=3)
+    assert sum(s["n_unmasked"] for s in stats) > 100000
+
+
+def test_tracker_full_size_sampled(ctx):
+    w = S.make_tracker()
+    n = w.sun.n_steps
+    # early-morning steps (ridge and long inter-tracker shadows) and midday
+    windows = [(int(0.2 * n), 6), (int(0.2 * n) + 30, 4), (int(0.7 * n) + 11, 4)]
+    stats = _sampled_full_size(ctx, w, windows, n_mods=24, seed=4)
+    assert sum(s["n_unmasked"] for s in stats) > 50000
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+def test_empty_scene_zero_loss(ctx):
+    w = S.make_tiny(day=355)
+    w.scene = S.Scene(np.zeros((0, 3), np.float32), np.zeros((0, 3), np.int32))
+    gid = pv3d.load_workload(ctx, w)
+    g = run_gpu(ctx, gid, w)
+    assert g["cell_counts"].sum() == 0
+    np.testing.assert_array_equal(g["power"], g["power_unshaded"])
+    ctx.release(gid)
+
+
+def test_night_steps_skipped_and_ragged_chunks(ctx):
+    w = S.make_random_small(121, n_mods=4, n_steps=9, n=2, map_res=256)
+    # interleave night steps
+    night = np.array([[0.3, 0.1, -0.2]])
+    night /= np.linalg.norm(night)
+    xyz = np.concatenate([w.sun.xyz[:4], night, w.sun.xyz[4:], night])
+    w.sun = S.Sun(xyz=xyz, dni=np.concatenate([w.sun.dni[:4], [0], w.sun.dni[4:], [0]]).astype(np.float32),
+                  dhi=np.concatenate([w.sun.dhi[:4], [0], w.sun.dhi[4:], [0]]).astype(np.float32),
+                  dt_h=np.ones(len(xyz), np.float32))
+    for k in (1, 3, 4, 16):
+        gid = pv3d.load_workload(ctx, w)
+        g = run_gpu(ctx, gid, w, chunk_steps=k)
+        assert g["tests"] == 9 * w.samples_per_step
+        assert g["steps_lit"] == 9
+        assert g["power"][4].sum() == 0 and g["power"][-1].sum() == 0
+        o = oracle.evaluate_workload(w)
+        st = compare(w, g, o, np.arange(w.sun.n_steps))
+        assert st["agree"] >= FLAG_AGREEMENT
+        ctx.release(gid)
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 8])
+def test_samples_per_side(ctx, n):
+    w = S.make_tiny(day=355, n=n)
+    full_check(ctx, w, chunk_steps=7)
+
+
+def test_single_module_grazing_sun(ctx):
+    w = S.make_tiny(day=355)
+    # a dawn sun below 2 degrees of elevation uses the FP64 light frame
+    el = [0.5, 1.5, 1.99, 2.5, 10.0]
+    az = math.radians(125.0)
+    xyz = np.array([[math.sin(az) * math.cos(math.radians(e)), math.cos(az) * math.cos(math.radians(e)),
+                     math.sin(math.radians(e))] for e in el])
+    w.sun = S.Sun(xyz=xyz, dni=np.full(len(el), 300, np.float32), dhi=np.full(len(el), 30, np.float32),
+                  dt_h=np.ones(len(el), np.float32))
+    full_check(ctx, w)
+
+
+def test_kahan_energy_vs_fp64_sum(ctx):
+    w = S.make_facade(seed=5, n=2, map_res=512, n_buildings=6, n_trees=3, n_poles=2, floors=1, per_floor=4,
+                      target_tris=1500, radius=60.0)
+    gid = pv3d.load_workload(ctx, w)
+    g = run_gpu(ctx, gid, w, outputs=("energy", "energy_unshaded", "power", "power_unshaded"))
+    dt = w.sun.dt_h.astype(np.float64)
+    e64 = (g["power"].astype(np.float64) * dt[:, None]).sum(0)
+    rel = np.abs(g["energy"] - e64) / np.maximum(e64, 1e-9)
+    assert rel.max() <= 1e-6, rel.max()
+    ctx.release(gid)
+
+
+def test_determinism_and_host_outputs(ctx):
+    w = S.make_random_small(131, n_mods=6, n_steps=10, n=3, map_res=512, tracked=True)
+    gid = pv3d.load_workload(ctx, w)
+    a = run_gpu(ctx, gid, w)
+    b = run_gpu(ctx, gid, w)
+    h = run_gpu(ctx, gid, w, device=False)
+    for k in ("energy", "energy_unshaded", "power", "sample_bits", "cell_counts"):
+        np.testing.assert_array_equal(a[k], b[k])
+        np.testing.assert_array_equal(a[k], h[k])
+    ctx.release(gid)
+
+
+def test_facade_year_subsample_loss(ctx):
+    """Full-size facade (R = 4096, 8x8 samples, all 200 modules) on every 8th
+    day of the year: the loss over those days within 0.1 % of the oracle's."""
+    w = S.make_facade(days=np.arange(4, 366, 8))
+    gid = pv3d.load_workload(ctx, w)
+    g = run_gpu(ctx, gid, w, outputs=("energy", "energy_unshaded"))
+    o = oracle.evaluate_workload(w, want_mask=False)
+    lg, lo = loss_pp(g["energy"], g["energy_unshaded"]), loss_pp(o["energy"], o["energy_unshaded"])
+    assert abs(lg - lo) <= LOSS_PP, (lg, lo)
+    ctx.release(gid)
+
+
+def test_tracker_year_subsample_loss(ctx):
+    """Full-size tracker plant (R = 8192, 4x4 samples) on every 16th day: the
+    loss of 300 sampled modules within 0.1 % of the oracle's."""
+    w = S.make_tracker(days=np.arange(3, 366, 16))
+    gid = pv3d.load_workload(ctx, w)
+    g = run_gpu(ctx, gid, w, outputs=("power", "power_unshaded"))
+    mods = np.sort(np.random.default_rng(8).choice(w.gen.n_modules, 300, replace=False))
+    o = oracle.evaluate_workload(w, modules=mods, want_mask=False)
+    dt = w.sun.dt_h.astype(np.float64)[:, None]
+    lg = loss_pp((g["power"][:, mods] * dt).sum(), (g["power_unshaded"][:, mods] * dt).sum())
+    lo = loss_pp(o["energy"], o["energy_unshaded"])
+    assert abs(lg - lo) <= LOSS_PP, (lg, lo)
+    ctx.release(gid)
+
+
+def test_invalid_inputs_rejected(ctx):
+    w = S.make_tiny()
+    bad = w.scene.verts.copy()
+    bad[0, 0] = np.nan
+    with pytest.raises(pv3d.PV3DError) as e:
+        ctx.scene_load(bad, w.scene.tris)
+    assert e.value.code == pv3d.PV3D_E_INVALID
+    with pytest.raises(pv3d.PV3DError):
+        ctx.scene_load(w.scene.verts, w.scene.tris + 100)
+    sid = ctx.scene_load(w.scene.verts, w.scene.tris)
+    gid = ctx.generator_define(sid, w.gen)
+    with pytest.raises(pv3d.PV3DError):
+        ctx.set_sun(gid, w.sun.xyz * 1.01, w.sun.dni, w.sun.dhi, w.sun.dt_h)
+    with pytest.raises(pv3d.PV3DError):  # no sun table yet
+        ctx.evaluate(gid, n=2)
+    ctx.set_sun(gid, w.sun.xyz, w.sun.dni, w.sun.dhi, w.sun.dt_h)
+    with pytest.raises(pv3d.PV3DError):
+        ctx.evaluate(gid, n=16)
+    with pytest.raises(pv3d.PV3DError):
+        ctx.evaluate(gid, n=9, outputs=("sample_bits",))
+    with pytest.raises(pv3d.PV3DError):
+        ctx.evaluate(gid, n=2, map_res=1000)
+    bad_gen = S.make_tiny().gen
+    bad_gen.layouts = [S.Layout(6, 10, 3, np.zeros(60, np.int32))]  # substrings 1, 2 own no cell
+    with pytest.raises(pv3d.PV3DError):
+        ctx.generator_define(sid, bad_gen)
+    with pytest.raises(pv3d.PV3DError) as e:
+        ctx.evaluate(987654, n=2)
+    assert e.value.code == pv3d.PV3D_E_NOTFOUND
+    ctx.release(sid)

@@ -1,0 +1,341 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 shadow-sample path (3DPV method, arXiv 1410.5780).
+
+Metric: shadow sample tests per second (lit sun steps x cell samples).  The
+default workload is the BIPV facade: 200 vertical south-facing modules of
+6x10 cells with 8x8 samples per cell, ~50k triangles of buildings, trees and
+poles, hourly suns of a year at 40 N (4,379 daylight steps), a 4096^2 light
+window.  One bench step is one full-year evaluation of that workload.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun): every rank evaluates its own seeded facade (independent
+problems, weak scaling); the only collectives are the timing barrier and the
+max-over-ranks of the timed region.  --impl reference times the FP64 CPU
+oracle on the host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "shadow sample tests/sec (sun steps x cell samples) at 1 GB300"
+UNIT = "tests/s"
+L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
+
+# algorithmic ALU work of the tile kernel (roofline): a covered
+# texel costs 3 edge functions (2 FMA each) + barycentric depth (3 FMA) + key
+# conversion and atomicMin (3) = 12 lane-ops; a sample test costs its position
+# (2), projection to texel space and depth (6), floor/clamp/tile check (4),
+# depth compare (2) = 14 lane-ops.
+OPS_PER_TEXEL_WRITE = 12
+OPS_PER_SAMPLE_TEST = 14
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="facade", choices=["facade", "tracker", "tiny"])
+    ap.add_argument("--path", default="fused", choices=["fused", "map"])
+    ap.add_argument("--chunk", type=int, default=0, help="sun steps per wave (0 = library default)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def make_workload(name: str, rank: int):
+    from paper_1410_5780_gb300 import scenes as S
+    if name == "facade":
+        return S.make_facade(seed=1 + rank)
+    if name == "tracker":
+        return S.make_tracker(seed=2 + rank)
+    return S.make_tiny()
+
+
+def workload_config(w, name):
+    return {"workload": {"facade": "BIPV facade (configs[1])", "tracker": "tracker plant (configs[2])",
+                         "tiny": "tiny plain case (configs[0])"}[name],
+            "modules": w.gen.n_modules, "cells": w.gen.n_cells, "samples_per_cell": w.n * w.n,
+            "triangles": int(w.scene.n_tris), "sun_steps": int(w.sun.n_steps),
+            "lit_steps": int((w.sun.xyz[:, 2] > 0).sum()), "map_res": w.map_res,
+            "samples_per_step": w.samples_per_step}
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, smax, reasons, n = [], [], set(), 0
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                if int(parts[0]) != self.idx:
+                    continue
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            n += 1
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.f.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": n}
+
+
+# ---------------------------------------------------------------------------
+# reference arm and CPU baseline: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+def oracle_sample_run(w, budget_s: float, chunk: int = 12, stride: int = 9):
+    """Time the oracle (as it stands) on every `stride`-th lit step of the
+    workload, chunk by chunk, until `budget_s` seconds of work are done."""
+    import oracle
+    lit = np.flatnonzero(w.sun.xyz[:, 2] > 0)[::stride]
+    osc = oracle.OracleScene(w.scene.verts, w.scene.tris)
+    threads = os.cpu_count() or 1
+    done, t_tot = 0, 0.0
+    for k in range(0, len(lit), chunk):
+        steps = lit[k:k + chunk]
+        t0 = time.perf_counter()
+        oracle.evaluate_workload(w, steps=steps, want_mask=False, threads=threads, oscene=osc)
+        t_tot += time.perf_counter() - t0
+        done += len(steps)
+        if t_tot >= budget_s:
+            break
+    tests = done * w.samples_per_step
+    return tests / t_tot, threads, f"{done} of the {int((w.sun.xyz[:, 2] > 0).sum())} lit steps " \
+        f"(every {stride}th), all {w.gen.n_modules} modules, {w.n}x{w.n} samples per cell, no parity mask; " \
+        f"{t_tot:.1f} s", t_tot
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = make_workload(args.workload, 0)
+    for _ in range(args.warmup):
+        oracle_sample_run(w, budget_s=0.0, chunk=4)
+    times, vals = [], []
+    for _ in range(args.steps):
+        v, cores, sample, t = oracle_sample_run(w, budget_s=8.0, chunk=6)
+        vals.append(v)
+        times.append(t)
+    value = float(statistics.mean(vals))
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * float(statistics.mean(times)), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference", "config": workload_config(w, args.workload),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def input_bytes(w) -> int:
+    m = w.gen.n_modules
+    b = w.scene.verts.nbytes + w.scene.tris.nbytes + 64 * m
+    b += sum(4 * len(l.cell_sub) for l in w.gen.layouts) + w.gen.pivots.nbytes
+    b += w.sun.xyz.nbytes + w.sun.dni.nbytes + w.sun.dhi.nbytes + w.sun.dt_h.nbytes
+    if w.poses is not None:
+        b += w.poses.nbytes
+    return int(b)
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+    from paper_1410_5780_gb300 import pv3d
+    pv3d.load(build_if_missing=True)
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    dev = local if torch.cuda.device_count() > local else 0
+    torch.cuda.set_device(dev)
+    w = make_workload(args.workload, rank)
+    path = pv3d.PV3D_PATH_FUSED if args.path == "fused" else pv3d.PV3D_PATH_MAP
+    ctx = pv3d.Context(device=dev, map_res=w.map_res, chunk_steps=args.chunk)
+    gid = pv3d.load_workload(ctx, w)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{dev}")
+
+    def evaluate(profile=0):
+        return ctx.evaluate(gid, n=w.n, map_res=w.map_res, outputs=("energy", "energy_unshaded"),
+                            stream=stream.cuda_stream, path=path, profile=profile)
+
+    for _ in range(max(args.warmup, 0)):
+        evaluate()
+    torch.cuda.synchronize()
+    # timed region: K full-year evaluations, L2 flushed between them (outside the events)
+    sampler = ClockSampler(dev)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    stage_ms = np.zeros(len(pv3d.STAGES))
+    waves = 0
+    tests = 0
+    launches = 0
+    results = []
+    for k in range(args.steps):
+        flush.zero_()
+        ev[k][0].record(stream)
+        r = evaluate(profile=1)
+        ev[k][1].record(stream)
+        prof = ctx.last_profile()
+        stage_ms += np.array([prof[f"{s}_ms"] for s in pv3d.STAGES])
+        waves += prof["waves"]
+        tests += r["tests"]
+        launches += r["kernel_launches"]
+        results.append(r)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    t_ms = sum(a.elapsed_time(b) for a, b in ev)
+    if dist is not None:
+        dist.barrier()
+        t = torch.tensor([t_ms], dtype=torch.float64, device=f"cuda:{dev}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_ms = float(t.item())
+        n = torch.tensor([float(tests)], dtype=torch.float64, device=f"cuda:{dev}")
+        dist.all_reduce(n, op=dist.ReduceOp.SUM)
+        tests_all = float(n.item())
+    else:
+        tests_all = float(tests)
+    value = tests_all / (t_ms * 1e-3)
+
+    # work counters of one evaluation (untimed), for the roofline numerator
+    evaluate(profile=3)
+    work = ctx.last_profile()
+    e_loss = 100.0 * (1.0 - float(results[-1]["energy"].sum()) / float(results[-1]["energy_unshaded"].sum()))
+
+    line = None
+    if rank == 0:
+        peaks = {}
+        try:
+            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+                peaks = json.load(f)
+        except OSError:
+            pass
+        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+        props = torch.cuda.get_device_properties(dev)
+        alu_peak = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12  # T lane-ops/s
+        raster_launch_ms = stage_ms[2] / max(waves, 1)
+        ops_per_launch = (OPS_PER_TEXEL_WRITE * work["texel_writes"]
+                          + OPS_PER_SAMPLE_TEST * work["sample_tests"]) / max(work["waves"], 1)
+        achieved = ops_per_launch / (raster_launch_ms * 1e-3) / 1e12
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": dict(workload_config(w, args.workload), path=args.path, l2="flushed between steps (512 MB)",
+                           waves_per_step=waves // args.steps, annual_loss_pct=round(e_loss, 4)),
+            "roofline": {"bound": "alu", "kernel": "k_raster_test" if args.path == "fused" else "k_raster_map",
+                         "achieved": achieved, "peak": alu_peak, "unit": "T lane-ops/s",
+                         "frac": achieved / alu_peak, "traffic": None,
+                         "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "
+                                        "(sm_max_mhz of MEASURED_PEAKS.json)",
+                         "work_per_launch": {"texel_writes": work["texel_writes"] / max(work["waves"], 1),
+                                             "sample_tests": work["sample_tests"] / max(work["waves"], 1)},
+                         "avg_launch_ms": raster_launch_ms},
+            "stages_ms_per_step": {s: float(stage_ms[i] / args.steps) for i, s in enumerate(pv3d.STAGES)},
+            "gpu_launches": int(launches),
+            "clocks": clocks,
+        }
+
+    # end to end through the C ABI with host buffers: load, define, sun, evaluate, read back
+    if not args.no_e2e:
+        h2d = input_bytes(w)
+        d2h = 16 * w.gen.n_modules
+        t_e2e = []
+        for k in range(max(1, min(args.steps, 3))):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            g2 = pv3d.load_workload(ctx, w)
+            r2 = ctx.evaluate(g2, n=w.n, map_res=w.map_res, outputs=("energy", "energy_unshaded"), device=False,
+                              path=path)
+            ctx.release(g2)
+            t_e2e.append(time.perf_counter() - t0)
+        e2e_val = r2["tests"] / statistics.mean(t_e2e)
+        if rank == 0:
+            line["e2e"] = {"value": e2e_val * world, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                           "d2h_bytes_per_step": d2h, "includes": "scene/generator/sun upload from host arrays, "
+                           "evaluation, host read-back of the energies"}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, cores, sample, _ = oracle_sample_run(w, budget_s=15.0)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    ctx.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", rank)))
+        tdist.init_process_group(backend=backend)
+        dist = tdist
+    try:
+        if args.impl == "reference":
+            run_reference(args, rank, world)
+        else:
+            run_ours(args, rank, world, dist)
+    finally:
+        if dist is not None:
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -45,6 +45,14 @@ extern "C" {
 #define PV3D_DEPTH_F32    0  /* FP32 depth, stored as order-preserving uint32 */
 #define PV3D_DEPTH_U24    1  /* 24-bit unsigned fixed point over the window's depth range */
 
+/* ---- evaluation paths ---------------------------------------------------
+ * FUSED: each raster tile is built in shared memory and the samples that read
+ *        it are depth-tested by the same CTA; no shadow map reaches HBM.
+ * MAP:   raster tiles are stored to a shadow map in device memory and a second
+ *        kernel gathers one texel per sample.  Same results, bit for bit. */
+#define PV3D_PATH_FUSED   0
+#define PV3D_PATH_MAP     1
+
 typedef struct pv3d_ctx pv3d_ctx;
 
 /* Context options.  Zero fields take the defaults in brackets. */
@@ -109,8 +117,32 @@ typedef struct pv3d_eval_opts {
     float v_diode;             /* bypass-diode forward drop, V [0.5] */
     int32_t chunk_steps;       /* steps per wave [context default] */
     void* stream;              /* cudaStream_t to run on; NULL = the context's own stream */
-    int32_t reserved[8];
+    int32_t path;              /* PV3D_PATH_FUSED or PV3D_PATH_MAP [FUSED] */
+    int32_t profile;           /* bit 0: time each stage with CUDA events; bit 1: count work (pv3d_last_profile) [0] */
+    int32_t reserved[6];
 } pv3d_eval_opts;
+
+/*
+ * Stage timings (profile bit 0) and work counts (profile bit 1) of the last
+ * pv3d_evaluate run with opts->profile set.  Stages: 0 light window and module setup, 1 binning
+ * (triangle bins, scan, receiver lists), 2 tile rasterisation (with the depth
+ * tests on the fused path), 3 PV model (with the texel gathers on the map
+ * path), 4 Kahan energy sums.  stage_ms sums CUDA-event intervals over the
+ * waves, recorded on the evaluation's stream.
+ */
+typedef struct pv3d_profile {
+    int32_t n_stages;
+    int32_t waves;
+    float stage_ms[8];
+    float device_ms;
+    int32_t reserved0;
+    int64_t sample_tests;      /* sample depth tests performed against rasterised tiles */
+    int64_t texel_visits;      /* texel-centre coverage tests */
+    int64_t texel_writes;      /* covered texels written with atomicMin */
+    int64_t tris_culled;       /* (triangle, tile) pairs skipped: on or behind every receiver plane */
+    int64_t nonempty_tiles;
+    int64_t binned_tris;
+} pv3d_profile;
 
 /*
  * Results.  M = modules of the generator, C = their cells (module order, then
@@ -135,6 +167,7 @@ typedef struct pv3d_result {
     int32_t waves;             /* waves launched */
     int64_t nonempty_tiles;    /* rasterised (step, tile) pairs over the evaluation */
     int64_t binned_tris;       /* (triangle, tile) pairs binned over the evaluation */
+    int64_t kernel_launches;   /* CUDA kernels launched by the evaluation */
 } pv3d_result;
 
 /* ---- context ------------------------------------------------------------ */
@@ -225,6 +258,9 @@ int pv3d_submit(pv3d_ctx* ctx, uint32_t gen_id, const pv3d_eval_opts* opts, pv3d
  * PV3D_E_PENDING if still running, another status on failure.
  */
 int pv3d_poll(pv3d_ctx* ctx, uint64_t req, int32_t timeout_ms);
+
+/* Profile of the last profiled evaluation on `ctx` (PV3D_E_NOTFOUND if none). */
+int pv3d_last_profile(pv3d_ctx* ctx, pv3d_profile* out);
 
 /* Free a scene (and every generator defined on it) or a generator. */
 int pv3d_release(pv3d_ctx* ctx, uint32_t scene_or_gen_id);

@@ -79,12 +79,15 @@ struct pv3d_ctx {
     std::map<uint32_t, GenH> gens;
     uint32_t next_id = 1;
     // workspace pools
-    DevBuf lp, win, ms, ms_p, ms_pu, ms_beam, cs_cnt, t_far, t_cnt, t_off, t_cur, t_slot, nonempty, bins, map,
+    DevBuf lp, win, ms, ms_p, ms_pu, ms_beam, cs_cnt, cs_bits, t_far, t_cnt, t_off, t_cur, t_slot, t_rcnt, t_roff, t_rcur, nonempty, bins, recv, map,
         big, block_sums, ctr, waves, jobs, kahan_mod, kahan_cell, staging;
-    int64_t bin_cap = 0, map_cap_tiles = 0, big_cap = 0;
+    int64_t bin_cap = 0, map_cap_tiles = 0, big_cap = 0, recv_cap = 0;
     void* h_stage = nullptr;  // pinned staging for descriptors
     size_t h_stage_bytes = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::vector<cudaEvent_t> prof_ev;  // stage-boundary events, kStages + 1 per wave
+    pv3d_profile last_prof{};
+    bool have_prof = false;
     // served requests
     struct Request;
     std::map<uint64_t, std::unique_ptr<Request>> reqs;
@@ -223,11 +226,13 @@ extern "C" void pv3d_destroy(pv3d_ctx* c)
     for (auto& kv : c->scenes)
         if (kv.second.d_tri) cudaFree(kv.second.d_tri);
     for (auto& kv : c->gens) free_gen(kv.second);
-    DevBuf* bufs[] = {&c->lp, &c->win, &c->ms, &c->ms_p, &c->ms_pu, &c->ms_beam, &c->cs_cnt, &c->t_far,
-                      &c->t_cnt, &c->t_off, &c->t_cur, &c->t_slot, &c->nonempty, &c->bins, &c->map, &c->big,
+    DevBuf* bufs[] = {&c->lp, &c->win, &c->ms, &c->ms_p, &c->ms_pu, &c->ms_beam, &c->cs_cnt, &c->cs_bits, &c->t_far,
+                      &c->t_cnt, &c->t_off, &c->t_cur, &c->t_slot, &c->t_rcnt, &c->t_roff, &c->t_rcur, &c->nonempty,
+                      &c->bins, &c->recv, &c->map, &c->big,
                       &c->block_sums, &c->ctr, &c->waves, &c->jobs, &c->kahan_mod, &c->kahan_cell, &c->staging};
     for (DevBuf* b : bufs) release_buf(*b);
     if (c->h_stage) cudaFreeHost(c->h_stage);
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
     if (c->ev0) cudaEventDestroy(c->ev0);
     if (c->ev1) cudaEventDestroy(c->ev1);
     if (c->stream) cudaStreamDestroy(c->stream);
@@ -484,7 +489,7 @@ extern "C" int pv3d_set_sun(pv3d_ctx* c, uint32_t gen_id, const double* sun_xyz,
 namespace {
 
 struct EvalSetup {
-    int n, R, K, tile;
+    int n, R, K, tile, fused, profile, count;
     int64_t b, e;
     float i_ref, v_cell, v_diode;
 };
@@ -499,6 +504,10 @@ static int check_eval(pv3d_ctx* c, const GenH& g, const pv3d_eval_opts* o, const
     es.R = d.map_res ? d.map_res : c->opts.map_res;
     es.K = d.chunk_steps ? d.chunk_steps : c->opts.chunk_steps;
     es.tile = c->opts.tile;
+    if (d.path != PV3D_PATH_FUSED && d.path != PV3D_PATH_MAP) return fail(c, PV3D_E_INVALID, "unknown path");
+    es.fused = d.path == PV3D_PATH_FUSED;
+    es.profile = (d.profile & 1) != 0;  // stage events
+    es.count = (d.profile & 2) != 0;    // work counters
     es.i_ref = d.i_ref > 0 ? d.i_ref : 9.0f;
     es.v_cell = d.v_cell > 0 ? d.v_cell : 0.5f;
     es.v_diode = d.v_diode > 0 ? d.v_diode : 0.5f;
@@ -566,12 +575,15 @@ static JobDev make_job(pv3d_ctx* c, const GenH& g, const SceneH& s, const EvalSe
 }
 
 // Lay out jobs[first, last) as one wave: bases and item offsets.
-static WaveDev pack_wave(std::vector<JobDev>& jobs, size_t first, size_t last, int tile_sh, int u24)
+static WaveDev pack_wave(std::vector<JobDev>& jobs, size_t first, size_t last, int tile_sh, int u24, int fused,
+                         int profile)
 {
     WaveDev W{};
+    W.profile = profile;
     W.n_jobs = (int32_t)(last - first);
     W.tile_sh = tile_sh;
     W.depth_u24 = u24;
+    W.fused = fused;
     for (size_t q = first; q < last; ++q) {
         JobDev& J = jobs[q];
         J.js_base = (int32_t)W.tot_js;
@@ -591,33 +603,38 @@ static WaveDev pack_wave(std::vector<JobDev>& jobs, size_t first, size_t last, i
         W.tot_mod += (int64_t)J.k * J.n_mods;
         W.tot_tri += ((int64_t)J.n_tris + J.n_mtris) * J.k;
         W.tot_epi += (int64_t)J.n_cells + J.n_mods;
+        if (J.out_bits) W.want_bits = 1;
     }
     return W;
 }
 
-static int ensure_workspace(pv3d_ctx* c, int64_t js, int64_t te, int64_t ms, int64_t cs, int tile,
-                            int64_t n_waves, int64_t n_jobs)
+static int ensure_workspace(pv3d_ctx* c, int64_t js, int64_t te, int64_t ms, int64_t cs, int tile, bool fused,
+                            bool want_bits)
 {
     int rc;
     int64_t scan_tiles = (te + 4095) / 4096 + 1;
     if ((rc = ensure(c, c->lp, js * sizeof(LightParams))) || (rc = ensure(c, c->win, js * 16)) ||
         (rc = ensure(c, c->ms, ms * sizeof(ModStep))) || (rc = ensure(c, c->ms_p, ms * 4)) ||
-        (rc = ensure(c, c->ms_pu, ms * 4)) || (rc = ensure(c, c->ms_beam, ms * 4)) || (rc = ensure(c, c->cs_cnt, cs)) ||
-        (rc = ensure(c, c->t_far, te * 4)) || (rc = ensure(c, c->t_cnt, te * 4)) || (rc = ensure(c, c->t_off, te * 4)) ||
+        (rc = ensure(c, c->ms_pu, ms * 4)) || (rc = ensure(c, c->ms_beam, ms * 4)) ||
+        (rc = ensure(c, c->cs_cnt, cs * 4)) || (rc = ensure(c, c->t_far, te * 4)) ||
+        (rc = ensure(c, c->t_cnt, te * 4)) || (rc = ensure(c, c->t_off, te * 4)) ||
         (rc = ensure(c, c->t_cur, te * 4)) || (rc = ensure(c, c->t_slot, te * 4)) ||
-        (rc = ensure(c, c->nonempty, te * 4)) || (rc = ensure(c, c->block_sums, scan_tiles * 16)) ||
-        (rc = ensure(c, c->ctr, sizeof(Counters))) || (rc = ensure(c, c->waves, n_waves * sizeof(WaveDev))) ||
-        (rc = ensure(c, c->jobs, n_jobs * sizeof(JobDev))))
+        (rc = ensure(c, c->t_rcnt, te * 4)) || (rc = ensure(c, c->t_roff, te * 4)) ||
+        (rc = ensure(c, c->t_rcur, te * 4)) || (rc = ensure(c, c->nonempty, te * 4)) ||
+        (rc = ensure(c, c->block_sums, scan_tiles * 24)) || (rc = ensure(c, c->ctr, sizeof(Counters))))
         return rc;
+    if (fused && want_bits && (rc = ensure(c, c->cs_bits, cs * 8))) return rc;
     if (c->bin_cap == 0) c->bin_cap = 1 << 22;
-    if (c->map_cap_tiles == 0) c->map_cap_tiles = std::max<int64_t>(256, te / 8);
     if (c->big_cap == 0) c->big_cap = 1 << 18;
-    c->map_cap_tiles = std::min<int64_t>(c->map_cap_tiles, te);
-    if ((rc = ensure(c, c->bins, c->bin_cap * 4)) ||
-        (rc = ensure(c, c->map, (size_t)c->map_cap_tiles * tile * tile * 4)) ||
-        (rc = ensure(c, c->big, c->big_cap * 8)))
+    if (c->recv_cap == 0) c->recv_cap = 1 << 20;
+    if ((rc = ensure(c, c->bins, c->bin_cap * 4)) || (rc = ensure(c, c->big, c->big_cap * 8)) ||
+        (rc = ensure(c, c->recv, c->recv_cap * 4)))
         return rc;
-    (void)tile;
+    if (!fused) {
+        if (c->map_cap_tiles == 0) c->map_cap_tiles = std::max<int64_t>(256, te / 8);
+        c->map_cap_tiles = std::min<int64_t>(c->map_cap_tiles, te);
+        if ((rc = ensure(c, c->map, (size_t)c->map_cap_tiles * tile * tile * 4))) return rc;
+    }
     return PV3D_OK;
 }
 
@@ -630,13 +647,18 @@ static Buffers buffers_of(pv3d_ctx* c)
     B.ms_p = (float*)c->ms_p.p;
     B.ms_pu = (float*)c->ms_pu.p;
     B.ms_beam = (float*)c->ms_beam.p;
-    B.cs_cnt = (uint8_t*)c->cs_cnt.p;
+    B.cs_cnt = (uint32_t*)c->cs_cnt.p;
+    B.cs_bits = (unsigned long long*)c->cs_bits.p;
     B.t_far = (uint32_t*)c->t_far.p;
     B.t_cnt = (uint32_t*)c->t_cnt.p;
     B.t_off = (uint32_t*)c->t_off.p;
     B.t_cur = (uint32_t*)c->t_cur.p;
     B.t_slot = (uint32_t*)c->t_slot.p;
     B.nonempty = (uint32_t*)c->nonempty.p;
+    B.t_rcnt = (uint32_t*)c->t_rcnt.p;
+    B.t_roff = (uint32_t*)c->t_roff.p;
+    B.t_rcur = (uint32_t*)c->t_rcur.p;
+    B.recv = (uint32_t*)c->recv.p;
     B.bins = (uint32_t*)c->bins.p;
     B.map = (uint32_t*)c->map.p;
     B.big = (uint2*)c->big.p;
@@ -675,14 +697,25 @@ static int stage_descriptors(pv3d_ctx* c, const std::vector<WaveDev>& waves, con
     return PV3D_OK;
 }
 
-static int run_waves(pv3d_ctx* c, const std::vector<WaveDev>& waves, cudaStream_t st, int tile)
+static int run_waves(pv3d_ctx* c, const std::vector<WaveDev>& waves, cudaStream_t st, int tile, bool fused,
+                     bool profile, bool count)
 {
     Buffers B = buffers_of(c);
     LaunchCfg cfg;
     cfg.sm_count = c->sm_count;
     cfg.tile = tile;
-    cfg.max_tot_te = 0;
+    cfg.fused = fused ? 1 : 0;
+    cfg.profile = count ? 1 : 0;
     cfg.stream = st;
+    cfg.ev = nullptr;
+    if (profile) {
+        const size_t need = waves.size() * (kStages + 1);
+        while (c->prof_ev.size() < need) {
+            cudaEvent_t e;
+            CUDA_TRY(c, cudaEventCreate(&e));
+            c->prof_ev.push_back(e);
+        }
+    }
     const WaveDev* dW = (const WaveDev*)c->waves.p;
     const JobDev* dJ = (const JobDev*)c->jobs.p;
     size_t job0 = 0;
@@ -691,7 +724,13 @@ static int run_waves(pv3d_ctx* c, const std::vector<WaveDev>& waves, cudaStream_
         CUDA_TRY(c, cudaMemsetAsync(c->win.p, 0xFF, (size_t)W.tot_js * 16, st));
         CUDA_TRY(c, cudaMemsetAsync(c->t_far.p, 0, (size_t)W.tot_te * 4, st));
         CUDA_TRY(c, cudaMemsetAsync(c->t_cnt.p, 0, (size_t)W.tot_te * 4, st));
+        CUDA_TRY(c, cudaMemsetAsync(c->t_rcnt.p, 0, (size_t)W.tot_te * 4, st));
         CUDA_TRY(c, cudaMemsetAsync(c->ctr.p, 0, 3 * sizeof(unsigned int), st));
+        if (fused) {
+            CUDA_TRY(c, cudaMemsetAsync(c->cs_cnt.p, 0, (size_t)W.tot_cs * 4, st));
+            if (W.want_bits) CUDA_TRY(c, cudaMemsetAsync(c->cs_bits.p, 0, (size_t)W.tot_cs * 8, st));
+        }
+        if (profile) cfg.ev = &c->prof_ev[w * (kStages + 1)];
         CUDA_TRY(c, launch_wave(dW + w, dJ + job0, B, cfg, W.tot_te));
         job0 += (size_t)W.n_jobs;
     }
@@ -756,7 +795,7 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
         int k = (int)std::min<int64_t>(es.K, es.e - s0);
         jobs.push_back(make_job(c, g, s, es, s0, k, (float2*)c->kahan_mod.p, (float2*)c->kahan_cell.p, d_p, d_pu,
                                 d_cnt, d_bits));
-        waves.push_back(pack_wave(jobs, jobs.size() - 1, jobs.size(), tile_sh, u24));
+        waves.push_back(pack_wave(jobs, jobs.size() - 1, jobs.size(), tile_sh, u24, es.fused, es.count));
     }
     int64_t mjs = 0, mte = 0, mms = 0, mcs = 0;
     for (auto& W : waves) {
@@ -765,19 +804,19 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
     }
     Counters hc{};
     for (int attempt = 0; attempt < 4; ++attempt) {
-        if ((rc = ensure_workspace(c, mjs, mte, mms, mcs, es.tile, (int64_t)waves.size(), (int64_t)jobs.size())))
-            return rc;
+        if ((rc = ensure_workspace(c, mjs, mte, mms, mcs, es.tile, es.fused, d_bits != nullptr))) return rc;
         for (auto& W : waves) {
             W.bin_cap = c->bin_cap;
             W.map_cap_tiles = c->map_cap_tiles;
             W.big_cap = c->big_cap;
+            W.recv_cap = c->recv_cap;
         }
         if ((rc = stage_descriptors(c, waves, jobs, st))) return rc;
         CUDA_TRY(c, cudaMemsetAsync(c->ctr.p, 0, sizeof(Counters), st));
         CUDA_TRY(c, cudaMemsetAsync(c->kahan_mod.p, 0, (size_t)g.M * 2 * sizeof(float2), st));
         CUDA_TRY(c, cudaMemsetAsync(c->kahan_cell.p, 0, (size_t)g.C * sizeof(float2), st));
         CUDA_TRY(c, cudaEventRecord(c->ev0, st));
-        if ((rc = run_waves(c, waves, st, es.tile))) return rc;
+        if ((rc = run_waves(c, waves, st, es.tile, es.fused, es.profile, es.count))) return rc;
         CUDA_TRY(c, launch_finalize_pairs((const float2*)c->kahan_mod.p, g.M, (const float2*)c->kahan_cell.p, g.C,
                                           d_e, d_eu, d_cl, st));
         CUDA_TRY(c, cudaEventRecord(c->ev1, st));
@@ -788,6 +827,7 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
         if (hc.overflow & 1u) c->bin_cap = (int64_t)(hc.need_bins * 5 / 4 + 1024);
         if (hc.overflow & 2u) c->map_cap_tiles = (int64_t)(hc.need_tiles * 5 / 4 + 16);
         if (hc.overflow & 4u) c->big_cap = (int64_t)(hc.need_big * 5 / 4 + 1024);
+        if (hc.overflow & 8u) c->recv_cap = (int64_t)(hc.need_recv * 5 / 4 + 1024);
     }
     float ms = 0;
     cudaEventElapsedTime(&ms, c->ev0, c->ev1);
@@ -810,6 +850,35 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
     out->waves = (int32_t)waves.size();
     out->nonempty_tiles = (int64_t)hc.stat_nonempty;
     out->binned_tris = (int64_t)hc.stat_bins;
+    out->kernel_launches = (int64_t)waves.size() * kLaunchesPerWave + 1;
+    if (es.profile || es.count) {
+        pv3d_profile& P = c->last_prof;
+        P = pv3d_profile{};
+        P.n_stages = kStages;
+        P.waves = (int32_t)waves.size();
+        for (size_t w = 0; es.profile && w < waves.size(); ++w)
+            for (int k = 0; k < kStages; ++k) {
+                float t = 0;
+                cudaEventElapsedTime(&t, c->prof_ev[w * (kStages + 1) + k], c->prof_ev[w * (kStages + 1) + k + 1]);
+                P.stage_ms[k] += t;
+            }
+        P.device_ms = ms;
+        P.sample_tests = (int64_t)hc.prof_samples;
+        P.texel_visits = (int64_t)hc.prof_visits;
+        P.texel_writes = (int64_t)hc.prof_writes;
+        P.tris_culled = (int64_t)hc.prof_culled;
+        P.nonempty_tiles = (int64_t)hc.stat_nonempty;
+        P.binned_tris = (int64_t)hc.stat_bins;
+        c->have_prof = true;
+    }
+    return PV3D_OK;
+}
+
+extern "C" int pv3d_last_profile(pv3d_ctx* c, pv3d_profile* out)
+{
+    if (!c || !out) return PV3D_E_INVALID;
+    if (!c->have_prof) return fail(c, PV3D_E_NOTFOUND, "no profiled evaluation yet");
+    *out = c->last_prof;
     return PV3D_OK;
 }
 

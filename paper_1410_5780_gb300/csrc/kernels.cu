@@ -6,23 +6,26 @@
 //                 from the sun, field of view limited to the generator)
 //   k_light       light frame, texel size and origin per (job, step)
 //   k_modsetup    each module at each step in texel space; marks the raster
-//                 tiles that hold samples and their far plane (max sample depth
-//                 + bias) -- only those tiles are rasterised
+//                 tiles that hold samples, their far plane (max sample depth +
+//                 bias) and counts the receiver modules per tile
 //   k_bin<0>      count (triangle, tile) pairs: vertex transform batched over
-//                 the job's steps (one read of a triangle serves k steps), cull
-//                 against occupied tiles and their far planes
+//                 the job's steps (the lanes of a warp take consecutive steps of
+//                 one triangle), cull against occupied tiles and far planes
 //   k_bin_big<0>  same for triangles that span many tiles, one warp each
-//   k_scan_*      bin offsets and the list of non-empty tiles (= map slots)
-//   k_bin<1>, k_bin_big<1>  write the bins
-//   k_raster      one CTA per non-empty tile: shared-memory depth tile, texel-
-//                 centre coverage, atomicMin of order-preserving depth keys,
-//                 coalesced 16-byte stores of the finished tile (Fig. 3: the
-//                 depth buffer keeps the surface nearest the sun)
-//   k_sample      one CTA per (step, module): analytic sample positions, texel
-//                 gather, depth test with slope-scaled bias, warp-ballot cell
-//                 tallies, substring minima and the bypass-diode MPP (step 4)
+//   k_scan_*      bin offsets, the list of non-empty tiles, receiver offsets
+//   k_bin<1>, k_bin_big<1>, k_recv_fill   write the bins and receiver lists
+//   k_raster_test one CTA per non-empty tile: shared-memory depth tile filled
+//                 at the texels the tile's samples read (texel-centre coverage,
+//                 atomicMin of order-preserving depth keys -- Fig. 3: the depth
+//                 buffer keeps the surface nearest the sun), then the depth test
+//                 of those samples and warp-aggregated cell tallies
+//   k_pv          per (step, module): irradiance per cell, substring currents,
+//                 bypass-diode maximum power point (Section 2, step 4)
 //   k_epilogue    Kahan-compensated FP32 sums over the wave's steps in step
 //                 order, per module (energy) and per cell (beam loss)
+// The map path replaces k_raster_test + k_pv by k_raster_map (tiles stored to
+// an HBM shadow map with 16-byte stores) + k_sample (texel gathers, ballot
+// tallies, PV model).
 #include <cfloat>
 #include <cstdint>
 
@@ -132,6 +135,27 @@ __device__ __forceinline__ void posed_module(const JobDev& J, const ModuleDev& M
 __device__ __forceinline__ float dot3(float3 a, float ax, float ay, float az)
 {
     return a.x * ax + a.y * ay + a.z * az;
+}
+
+// Sample (I, J) of a module, I = cu * n + i and J = cv * n + j, sits at
+// a = (I + 1/2) p/n, b = (J + 1/2) p/n along the module axes (Section 2,
+// step 3: n x n areas per cell, centred).  The rasteriser's needed-texel mask
+// and the depth test evaluate these with the same rounded operations, so they
+// agree bit for bit on the texel every sample reads.
+__device__ __forceinline__ void sample_ab(int I, int Jr, float p_over_n, float& a, float& b)
+{
+    a = __fmul_rn(__fadd_rn((float)I, 0.5f), p_over_n);
+    b = __fmul_rn(__fadd_rn((float)Jr, 0.5f), p_over_n);
+}
+
+__device__ __forceinline__ void sample_texel(const ModStep& s, float a, float b, int R, int& ix, int& iy,
+                                             float& d)
+{
+    const float tx = __fmaf_rn(b, s.tbx, __fmaf_rn(a, s.tax, s.tx0));
+    const float ty = __fmaf_rn(b, s.tby, __fmaf_rn(a, s.tay, s.ty0));
+    d = __fmaf_rn(b, s.db, __fmaf_rn(a, s.da, s.d0));
+    ix = min(R - 1, max(0, (int)floorf(tx)));
+    iy = min(R - 1, max(0, (int)floorf(ty)));
 }
 
 // ---------------------------------------------------------------------------
@@ -254,8 +278,39 @@ __device__ __forceinline__ uint32_t depth_store_key(float d, const LightParams& 
 }
 
 // ---------------------------------------------------------------------------
-// k_modsetup: module frames in texel space, bias, tile occupancy and far planes
+// k_modsetup: module frames in texel space, bias, tile occupancy, far planes,
+// receiver counts; k_recv_fill lists the receivers of the non-empty tiles
 // ---------------------------------------------------------------------------
+struct TileRange {
+    int tx0, tx1, ty0, ty1;
+    float dmax;
+};
+
+// Tiles touched by the bounding box of a module's corners in texel space.
+__device__ __forceinline__ TileRange module_tiles(const ModStep& s, const ModuleDev& M, int R, int sh)
+{
+    const float lu = M.cu * M.pitch, lv = M.cv * M.pitch;
+    float xmin = FLT_MAX, xmax = -FLT_MAX, ymin = FLT_MAX, ymax = -FLT_MAX, dmax = -FLT_MAX;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float a = (k == 1 || k == 2) ? lu : 0.f;
+        const float b = (k >= 2) ? lv : 0.f;
+        const float x = s.tx0 + a * s.tax + b * s.tbx;
+        const float y = s.ty0 + a * s.tay + b * s.tby;
+        const float d = s.d0 + a * s.da + b * s.db;
+        xmin = fminf(xmin, x); xmax = fmaxf(xmax, x);
+        ymin = fminf(ymin, y); ymax = fmaxf(ymax, y);
+        dmax = fmaxf(dmax, d);
+    }
+    TileRange t;
+    t.tx0 = max(0, min(R - 1, (int)floorf(xmin))) >> sh;
+    t.tx1 = max(0, min(R - 1, (int)floorf(xmax))) >> sh;
+    t.ty0 = max(0, min(R - 1, (int)floorf(ymin))) >> sh;
+    t.ty1 = max(0, min(R - 1, (int)floorf(ymax))) >> sh;
+    t.dmax = dmax;
+    return t;
+}
+
 __global__ void k_modsetup(const WaveDev* __restrict__ W, const JobDev* __restrict__ jobs, Buffers B)
 {
     const int64_t tot = W->tot_mod;
@@ -269,7 +324,7 @@ __global__ void k_modsetup(const WaveDev* __restrict__ W, const JobDev* __restri
         int64_t li = item - J.it_mod;
         int ls = (int)(li / J.n_mods), m = (int)(li % J.n_mods);
         int64_t js = J.js_base + ls;
-        const LightParams lp = B.lp[js];
+        const LightParams& lp = B.lp[js];
         if (!lp.valid) continue;
         const ModuleDev& M = J.mods[m];
         float3 o, u, v;
@@ -298,28 +353,42 @@ __global__ void k_modsetup(const WaveDev* __restrict__ W, const JobDev* __restri
         s.bias = lp.delta * (0.70710678f * tan_i + 0.03125f);
         if (u24) s.bias += 2.f / lp.qscale;
         B.ms[J.ms_base + li] = s;
-        // occupied tiles: bounding box of the corners in texel space
-        float lu = M.cu * M.pitch, lv = M.cv * M.pitch;
-        float xmin = FLT_MAX, xmax = -FLT_MAX, ymin = FLT_MAX, ymax = -FLT_MAX, dmax = -FLT_MAX;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            float a = (k == 1 || k == 2) ? lu : 0.f;
-            float b = (k >= 2) ? lv : 0.f;
-            float x = s.tx0 + a * s.tax + b * s.tbx;
-            float y = s.ty0 + a * s.tay + b * s.tby;
-            float d = s.d0 + a * s.da + b * s.db;
-            xmin = fminf(xmin, x); xmax = fmaxf(xmax, x);
-            ymin = fminf(ymin, y); ymax = fmaxf(ymax, y);
-            dmax = fmaxf(dmax, d);
-        }
-        int R = J.R;
-        int ix0 = max(0, min(R - 1, (int)floorf(xmin))), ix1 = max(0, min(R - 1, (int)floorf(xmax)));
-        int iy0 = max(0, min(R - 1, (int)floorf(ymin))), iy1 = max(0, min(R - 1, (int)floorf(ymax)));
-        uint32_t far_key = u24 ? depth_store_key(dmax + s.bias, lp, 1) + 1u : okey(dmax + s.bias);
-        int64_t te0 = J.te_base + (int64_t)ls * J.tiles_x * J.tiles_x;
-        for (int ty = iy0 >> sh; ty <= (iy1 >> sh); ++ty)
-            for (int tx = ix0 >> sh; tx <= (ix1 >> sh); ++tx)
-                atomicMax(&B.t_far[te0 + (int64_t)ty * J.tiles_x + tx], far_key);
+        const TileRange tr = module_tiles(s, M, J.R, sh);
+        const uint32_t far_key = u24 ? depth_store_key(tr.dmax + s.bias, lp, 1) + 1u : okey(tr.dmax + s.bias);
+        const int64_t te0 = J.te_base + (int64_t)ls * J.tiles_x * J.tiles_x;
+        for (int ty = tr.ty0; ty <= tr.ty1; ++ty)
+            for (int tx = tr.tx0; tx <= tr.tx1; ++tx) {
+                const int64_t te = te0 + (int64_t)ty * J.tiles_x + tx;
+                atomicMax(&B.t_far[te], far_key);
+                atomicAdd(&B.t_rcnt[te], 1u);
+            }
+    }
+}
+
+// After the scan: list each module as a receiver of the non-empty tiles it touches.
+__global__ void k_recv_fill(const WaveDev* __restrict__ W, const JobDev* __restrict__ jobs, Buffers B)
+{
+    const int64_t tot = W->tot_mod;
+    const int nj = W->n_jobs;
+    const int sh = W->tile_sh;
+    const int64_t cap = W->recv_cap;
+    for (int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; item < tot;
+         item += (int64_t)gridDim.x * blockDim.x) {
+        int j = job_of(nj, item, [&](int q) { return jobs[q].it_mod; });
+        const JobDev& J = jobs[j];
+        int64_t li = item - J.it_mod;
+        int ls = (int)(li / J.n_mods), m = (int)(li % J.n_mods);
+        if (!B.lp[J.js_base + ls].valid) continue;
+        const ModStep s = B.ms[J.ms_base + li];
+        const TileRange tr = module_tiles(s, J.mods[m], J.R, sh);
+        const int64_t te0 = J.te_base + (int64_t)ls * J.tiles_x * J.tiles_x;
+        for (int ty = tr.ty0; ty <= tr.ty1; ++ty)
+            for (int tx = tr.tx0; tx <= tr.tx1; ++tx) {
+                const int64_t te = te0 + (int64_t)ty * J.tiles_x + tx;
+                if (B.t_cnt[te] == 0u) continue;
+                const uint32_t pos = atomicAdd(&B.t_rcur[te], 1u);
+                if (pos < (uint64_t)cap) B.recv[pos] = (uint32_t)m;
+            }
     }
 }
 
@@ -526,45 +595,57 @@ __global__ void __launch_bounds__(256) k_bin_big(const WaveDev* __restrict__ W,
 }
 
 // ---------------------------------------------------------------------------
-// scan over the wave's tile entries: bin offsets, non-empty tile list
+// scan over the wave's tile entries: triangle-bin offsets, the list of
+// non-empty tiles (= map slots) and receiver-list offsets of non-empty tiles
 // ---------------------------------------------------------------------------
 constexpr int kScanThreads = 1024;
 constexpr int kScanPer = 4;
 constexpr int kScanTile = kScanThreads * kScanPer;
 
-// Block-wide exclusive scan of (a, b) pairs; returns the block totals.
-__device__ __forceinline__ void block_scan2(unsigned long long& a, unsigned long long& b,
-                                            unsigned long long& tot_a, unsigned long long& tot_b)
+// Block-wide exclusive scan of three counters; returns the block totals.
+__device__ __forceinline__ void block_scan3(unsigned long long v[3], unsigned long long tot[3])
 {
-    __shared__ unsigned long long wa[32], wb[32];
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    unsigned long long ia = a, ib = b;
+    __shared__ unsigned long long ws[3][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned long long inc[3] = {v[0], v[1], v[2]};
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-        unsigned long long ya = __shfl_up_sync(0xffffffffu, ia, off);
-        unsigned long long yb = __shfl_up_sync(0xffffffffu, ib, off);
-        if (lane >= off) { ia += ya; ib += yb; }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            unsigned long long y = __shfl_up_sync(0xffffffffu, inc[q], off);
+            if (lane >= off) inc[q] += y;
+        }
     }
-    if (lane == 31) { wa[w] = ia; wb[w] = ib; }
+    if (lane == 31)
+        for (int q = 0; q < 3; ++q) ws[q][w] = inc[q];
     __syncthreads();
     if (w == 0) {
-        int nw = blockDim.x >> 5;
-        unsigned long long xa = lane < nw ? wa[lane] : 0ull, xb = lane < nw ? wb[lane] : 0ull;
 #pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            unsigned long long ya = __shfl_up_sync(0xffffffffu, xa, off);
-            unsigned long long yb = __shfl_up_sync(0xffffffffu, xb, off);
-            if (lane >= off) { xa += ya; xb += yb; }
+        for (int q = 0; q < 3; ++q) {
+            unsigned long long x = lane < nw ? ws[q][lane] : 0ull;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                unsigned long long y = __shfl_up_sync(0xffffffffu, x, off);
+                if (lane >= off) x += y;
+            }
+            if (lane < nw) ws[q][lane] = x;
         }
-        if (lane < nw) { wa[lane] = xa; wb[lane] = xb; }
     }
     __syncthreads();
-    unsigned long long pa = w ? wa[w - 1] : 0ull, pb = w ? wb[w - 1] : 0ull;
-    tot_a = wa[(blockDim.x >> 5) - 1];
-    tot_b = wb[(blockDim.x >> 5) - 1];
-    a = pa + ia - a;
-    b = pb + ib - b;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        tot[q] = ws[q][nw - 1];
+        v[q] = (w ? ws[q][w - 1] : 0ull) + inc[q] - v[q];
+    }
     __syncthreads();
+}
+
+__device__ __forceinline__ void scan_values(const Buffers& B, int64_t i, unsigned long long v[3])
+{
+    const uint32_t c = B.t_cnt[i];
+    v[0] = c;
+    v[1] = c ? 1u : 0u;
+    v[2] = c ? B.t_rcnt[i] : 0u;
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_a(const WaveDev* __restrict__ W, Buffers B)
@@ -572,23 +653,20 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_a(const WaveDev* __restri
     const int64_t tot = W->tot_te;
     const int64_t n_tiles = (tot + kScanTile - 1) / kScanTile;
     for (int64_t st = blockIdx.x; st < n_tiles; st += gridDim.x) {
-        unsigned long long a = 0, b = 0;
+        unsigned long long v[3] = {0, 0, 0};
         int64_t base = st * kScanTile + (int64_t)threadIdx.x * kScanPer;
 #pragma unroll
         for (int q = 0; q < kScanPer; ++q) {
-            int64_t i = base + q;
-            if (i < tot) {
-                uint32_t c = B.t_cnt[i];
-                a += c;
-                b += c ? 1u : 0u;
+            if (base + q < tot) {
+                unsigned long long x[3];
+                scan_values(B, base + q, x);
+                v[0] += x[0]; v[1] += x[1]; v[2] += x[2];
             }
         }
-        unsigned long long ta, tb;
-        block_scan2(a, b, ta, tb);
-        if (threadIdx.x == 0) {
-            B.block_sums[2 * st] = ta;
-            B.block_sums[2 * st + 1] = tb;
-        }
+        unsigned long long t[3];
+        block_scan3(v, t);
+        if (threadIdx.x == 0)
+            for (int q = 0; q < 3; ++q) B.block_sums[3 * st + q] = t[q];
     }
 }
 
@@ -596,33 +674,32 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_b(const WaveDev* __restri
 {
     const int64_t tot = W->tot_te;
     const int64_t n_tiles = (tot + kScanTile - 1) / kScanTile;
-    unsigned long long carry_a = 0, carry_b = 0;
+    unsigned long long carry[3] = {0, 0, 0};
     for (int64_t base = 0; base < n_tiles; base += blockDim.x) {
         int64_t i = base + threadIdx.x;
-        unsigned long long a = i < n_tiles ? B.block_sums[2 * i] : 0ull;
-        unsigned long long b = i < n_tiles ? B.block_sums[2 * i + 1] : 0ull;
-        unsigned long long ta, tb;
-        block_scan2(a, b, ta, tb);
-        if (i < n_tiles) {
-            B.block_sums[2 * i] = a + carry_a;
-            B.block_sums[2 * i + 1] = b + carry_b;
-        }
-        carry_a += ta;
-        carry_b += tb;
+        unsigned long long v[3], t[3];
+        for (int q = 0; q < 3; ++q) v[q] = i < n_tiles ? B.block_sums[3 * i + q] : 0ull;
+        block_scan3(v, t);
+        if (i < n_tiles)
+            for (int q = 0; q < 3; ++q) B.block_sums[3 * i + q] = v[q] + carry[q];
+        for (int q = 0; q < 3; ++q) carry[q] += t[q];
     }
     if (threadIdx.x == 0) {
         Counters* c = B.ctr;
-        c->tot_bins = carry_a;
-        c->n_nonempty = (unsigned int)min(carry_b, 0xFFFFFFFFull);
-        c->stat_bins += carry_a;
-        c->stat_nonempty += carry_b;
-        if (carry_a > c->need_bins) c->need_bins = carry_a;
-        if (carry_b > c->need_tiles) c->need_tiles = carry_b;
+        c->tot_bins = carry[0];
+        c->n_nonempty = (unsigned int)min(carry[1], 0xFFFFFFFFull);
+        c->tot_recv = carry[2];
+        c->stat_bins += carry[0];
+        c->stat_nonempty += carry[1];
+        if (carry[0] > c->need_bins) c->need_bins = carry[0];
+        if (carry[1] > c->need_tiles) c->need_tiles = carry[1];
+        if (carry[2] > c->need_recv) c->need_recv = carry[2];
         unsigned long long nb = c->n_big;
         if (nb > c->need_big) c->need_big = nb;
-        if (carry_a > (unsigned long long)W->bin_cap) c->overflow |= 1u;
-        if (carry_b > (unsigned long long)W->map_cap_tiles) c->overflow |= 2u;
+        if (carry[0] > (unsigned long long)W->bin_cap) c->overflow |= 1u;
+        if (!W->fused && carry[1] > (unsigned long long)W->map_cap_tiles) c->overflow |= 2u;
         if (nb > (unsigned long long)W->big_cap) c->overflow |= 4u;
+        if (carry[2] > (unsigned long long)W->recv_cap) c->overflow |= 8u;
     }
 }
 
@@ -631,119 +708,566 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_c(const WaveDev* __restri
     const int64_t tot = W->tot_te;
     const int64_t n_tiles = (tot + kScanTile - 1) / kScanTile;
     for (int64_t st = blockIdx.x; st < n_tiles; st += gridDim.x) {
-        uint32_t c[kScanPer];
-        unsigned long long a = 0, b = 0;
+        unsigned long long x[kScanPer][3];
+        unsigned long long v[3] = {0, 0, 0};
         int64_t base = st * kScanTile + (int64_t)threadIdx.x * kScanPer;
 #pragma unroll
         for (int q = 0; q < kScanPer; ++q) {
-            int64_t i = base + q;
-            c[q] = i < tot ? B.t_cnt[i] : 0u;
-            a += c[q];
-            b += c[q] ? 1u : 0u;
+            if (base + q < tot) scan_values(B, base + q, x[q]);
+            else x[q][0] = x[q][1] = x[q][2] = 0ull;
+            v[0] += x[q][0]; v[1] += x[q][1]; v[2] += x[q][2];
         }
-        unsigned long long ta, tb;
-        block_scan2(a, b, ta, tb);
-        a += B.block_sums[2 * st];
-        b += B.block_sums[2 * st + 1];
+        unsigned long long t[3];
+        block_scan3(v, t);
+        for (int q = 0; q < 3; ++q) v[q] += B.block_sums[3 * st + q];
 #pragma unroll
         for (int q = 0; q < kScanPer; ++q) {
             int64_t i = base + q;
             if (i < tot) {
-                B.t_off[i] = (uint32_t)min(a, 0xFFFFFFFFull);
-                B.t_cur[i] = (uint32_t)min(a, 0xFFFFFFFFull);
-                B.t_slot[i] = (uint32_t)min(b, 0xFFFFFFFFull);
-                if (c[q]) B.nonempty[b] = (uint32_t)i;
+                B.t_off[i] = (uint32_t)min(v[0], 0xFFFFFFFFull);
+                B.t_cur[i] = (uint32_t)min(v[0], 0xFFFFFFFFull);
+                B.t_slot[i] = (uint32_t)min(v[1], 0xFFFFFFFFull);
+                B.t_roff[i] = (uint32_t)min(v[2], 0xFFFFFFFFull);
+                B.t_rcur[i] = (uint32_t)min(v[2], 0xFFFFFFFFull);
+                if (x[q][1]) B.nonempty[v[1]] = (uint32_t)i;
             }
-            a += c[q];
-            b += c[q] ? 1u : 0u;
+            v[0] += x[q][0]; v[1] += x[q][1]; v[2] += x[q][2];
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// k_raster: shared-memory depth tile per non-empty (step, tile)
+// per-tile depth rasterisation (shared by the fused and the map kernels)
 // ---------------------------------------------------------------------------
-template <int TS>
-__global__ void __launch_bounds__(256) k_raster(const WaveDev* __restrict__ W, const JobDev* __restrict__ jobs,
-                                                Buffers B)
+constexpr int kRecvChunk = 64;  // receivers staged in shared memory at a time
+
+// q / d for 0 <= q < 2^24 (one float estimate, one correction).
+__device__ __forceinline__ int fdiv(int q, int d, float inv_d)
 {
-    __shared__ __align__(16) uint32_t tile[TS * TS];
+    int r = (int)((float)q * inv_d);
+    const int rem = q - r * d;
+    if (rem < 0) --r;
+    else if (rem >= d) ++r;
+    return r;
+}
+
+// A receiver module of the tile, staged in shared memory.
+struct RecvSm {
+    ModStep s;
+    float p_over_n;      // sample spacing along the module axes, m
+    float pa, pb, pc;    // receiver depth plane d = pa x + pb y + pc in tile-local texel coordinates
+    float cull_tol;      // plane tolerance (half the bias slack), or -1 if the plane may not cull
+    int cu;              // cells across the module
+    int cell_base;       // first cell of the module in the generator
+    int cu0, cv0, wcu;   // cells of the module that may read the tile
+    int cell_pref;       // cells of the receivers staged before this one
+};
+
+template <int TS>
+struct TileSm {
+    uint32_t tile[TS * TS];          // depth keys of the tile
+    uint32_t mask[TS * TS / 32];     // texels read by some sample (sparse tiles)
+    uint32_t row_start[TS + 1];      // start of each row in `list`
+    uint16_t list[TS * TS];          // marked texels, row-major
+    RecvSm recv[kRecvChunk];
+    int n_recv;                      // receivers staged
+    int total_cells;                 // cells over the staged receivers
+};
+
+// Stage receivers [r0, r0 + cnt) of tile (tx, ty): cell box (the tile corners
+// mapped back onto the module plane, widened by one cell) and depth plane.
+template <int TS>
+__device__ void stage_receivers(TileSm<TS>& sm, const JobDev& J, const Buffers& B, int ls, int tx, int ty,
+                                uint64_t r0, int cnt)
+{
+    const int tid = threadIdx.x;
+    if (tid < cnt) {
+        const int m = (int)B.recv[r0 + tid];
+        const ModuleDev& M = J.mods[m];
+        RecvSm& R = sm.recv[tid];
+        const ModStep s = B.ms[J.ms_base + (int64_t)ls * J.n_mods + m];
+        R.s = s;
+        R.p_over_n = __fdiv_rn(M.pitch, (float)J.n);
+        R.cu = M.cu;
+        R.cell_base = M.cell_base;
+        int cu0 = 0, cu1 = M.cu - 1, cv0 = 0, cv1 = M.cv - 1;
+        const float det = s.tax * s.tby - s.tay * s.tbx;
+        const bool planar = fabsf(det) > 1e-6f * (fabsf(s.tax * s.tby) + fabsf(s.tay * s.tbx));
+        R.cull_tol = -1.f;
+        if (planar) {
+            float amin = FLT_MAX, amax = -FLT_MAX, bmin = FLT_MAX, bmax = -FLT_MAX;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const float dx = (float)(tx * TS + ((c & 1) ? TS : 0)) - s.tx0;
+                const float dy = (float)(ty * TS + ((c & 2) ? TS : 0)) - s.ty0;
+                const float a = (dx * s.tby - dy * s.tbx) / det;
+                const float b = (dy * s.tax - dx * s.tay) / det;
+                amin = fminf(amin, a); amax = fmaxf(amax, a);
+                bmin = fminf(bmin, b); bmax = fmaxf(bmax, b);
+            }
+            const float ip = 1.f / M.pitch;
+            cu0 = max(cu0, (int)fmaxf(floorf(amin * ip) - 1.f, -1.f));
+            cu1 = min(cu1, (int)fminf(floorf(amax * ip) + 1.f, 1e6f));
+            cv0 = max(cv0, (int)fmaxf(floorf(bmin * ip) - 1.f, -1.f));
+            cv1 = min(cv1, (int)fminf(floorf(bmax * ip) + 1.f, 1e6f));
+            // depth of the receiver plane over the tile: a triangle lying on or
+            // behind the plane (by less than half the bias slack) shades none
+            // of its samples, so it may be skipped for this receiver
+            R.pa = (s.da * s.tby - s.db * s.tay) / det;
+            R.pb = (s.db * s.tax - s.da * s.tbx) / det;
+            R.pc = s.d0 - R.pa * (s.tx0 - (float)(tx * TS)) - R.pb * (s.ty0 - (float)(ty * TS));
+            if (s.cosi > 0.017452406f) R.cull_tol = B.lp[J.js_base + ls].delta * (1.f / 64.f);
+        }
+        R.cu0 = cu0;
+        R.cv0 = cv0;
+        R.wcu = max(0, cu1 - cu0 + 1);
+        R.cell_pref = (cu0 <= cu1 && cv0 <= cv1) ? R.wcu * (cv1 - cv0 + 1) : 0;  // cells, prefixed below
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int r = 0; r < cnt; ++r) {
+            const int c = sm.recv[r].cell_pref;
+            sm.recv[r].cell_pref = acc;
+            acc += c;
+        }
+        sm.n_recv = cnt;
+        sm.total_cells = acc;
+    }
+    __syncthreads();
+}
+
+// Receiver and cell of staged cell item `it`.
+template <int TS>
+__device__ __forceinline__ int recv_of(const TileSm<TS>& sm, int it)
+{
+    int lo = 0, hi = sm.n_recv - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sm.recv[mid].cell_pref <= it) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Visit the samples of the staged receivers that read tile (tx, ty): one
+// thread per (cell, sample row) walks the row's n samples.  f(R, k, ix, iy, d)
+// is called per sample inside the tile (k = j * n + i); g(R, cu, cv) after
+// each row.
+template <int TS, typename F, typename G>
+__device__ __forceinline__ void for_tile_samples(const TileSm<TS>& sm, const JobDev& J, int tx, int ty, F f, G g)
+{
+    constexpr int SH = TS == 64 ? 6 : 5;
+    const int n = J.n, R_ = J.R;
+    const float inv_n = 1.f / (float)n;
+    const int items = sm.total_cells * n;
+    for (int it = threadIdx.x; it < items; it += blockDim.x) {
+        const int cell = fdiv(it, n, inv_n);
+        const int jj = it - cell * n;
+        const RecvSm& R = sm.recv[recv_of(sm, cell)];
+        const int c = cell - R.cell_pref;
+        const int cvb = fdiv(c, R.wcu, 1.f / (float)R.wcu);
+        const int cu = R.cu0 + c - cvb * R.wcu, cv = R.cv0 + cvb;
+        for (int ii = 0; ii < n; ++ii) {
+            float a, b, d;
+            int ix, iy;
+            sample_ab(cu * n + ii, cv * n + jj, R.p_over_n, a, b);
+            sample_texel(R.s, a, b, R_, ix, iy, d);
+            if ((ix >> SH) == tx && (iy >> SH) == ty) f(R, jj * n + ii, ix, iy, d);
+        }
+        g(R, cu, cv);
+    }
+}
+
+// Can triangle T (tile-local texel coordinates) shade a sample of a staged
+// receiver?  False only if it lies on or behind every receiver's plane.
+template <int TS>
+__device__ __forceinline__ bool may_shade(const TileSm<TS>& sm, const TriT& T, bool cull_ok)
+{
+    if (!cull_ok) return true;
+    for (int r = 0; r < sm.n_recv; ++r) {
+        const RecvSm& R = sm.recv[r];
+        if (R.cull_tol < 0.f) return true;
+        float gap = FLT_MAX;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) gap = fminf(gap, T.d[k] - (R.pa * T.x[k] + R.pb * T.y[k] + R.pc));
+        if (!(gap >= -R.cull_tol)) return true;
+    }
+    return false;
+}
+
+// Rasterise the tile's triangles into sm.tile.  Sparse tiles (fewer samples
+// than half the texels) are rasterised only at the texels their samples
+// read; each triangle then visits its bounding box or the marked texels of
+// its rows, whichever is fewer.  Receivers [r0, r0 + nrecv) must be staged
+// (the first kRecvChunk of them) on entry.  Returns 0 if no sample reads the
+// tile.
+template <int TS, bool PROF>
+__device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, const WaveDev* W, int ls, int tx,
+                           int ty, int64_t te, uint64_t r0, int nrecv, unsigned int& visits, unsigned int& writes,
+                           unsigned int& culled)
+{
+    constexpr int SH = TS == 64 ? 6 : 5;
+    constexpr int WPR = TS / 32;
+    const int tid = threadIdx.x, bd = blockDim.x;
+    const int lane = tid & 31, warp = tid >> 5, n_warps = bd >> 5;
+    const int u24 = W->depth_u24;
+    const LightParams& lp = B.lp[J.js_base + ls];
+    const bool cull_ok = nrecv <= kRecvChunk;
+    // samples reading the tile, at most (estimated from the staged receivers)
+    const int64_t est = (int64_t)sm.total_cells * J.nn * ((nrecv + kRecvChunk - 1) / kRecvChunk);
+    const bool dense = est * 2 >= TS * TS;
+    int n_need = TS * TS;
+    if (!dense) {
+        for (int q = tid; q < TS * WPR; q += bd) sm.mask[q] = 0u;
+        __syncthreads();
+        for (int c0 = 0; c0 < nrecv; c0 += kRecvChunk) {
+            if (c0 > 0) stage_receivers<TS>(sm, J, B, ls, tx, ty, r0 + c0, min(kRecvChunk, nrecv - c0));
+            for_tile_samples<TS>(
+                sm, J, tx, ty,
+                [&](const RecvSm&, int, int ix, int iy, float) {
+                    atomicOr(&sm.mask[(iy & (TS - 1)) * WPR + ((ix & (TS - 1)) >> 5)], 1u << (ix & 31));
+                },
+                [&](const RecvSm&, int, int) {});
+            __syncthreads();
+        }
+        if (nrecv > kRecvChunk) stage_receivers<TS>(sm, J, B, ls, tx, ty, r0, kRecvChunk);
+        if (tid < TS) {
+            int c = 0;
+#pragma unroll
+            for (int w = 0; w < WPR; ++w) c += __popc(sm.mask[tid * WPR + w]);
+            sm.row_start[tid + 1] = c;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            sm.row_start[0] = 0;
+            for (int y = 0; y < TS; ++y) sm.row_start[y + 1] += sm.row_start[y];
+        }
+        __syncthreads();
+        for (int q = tid; q < TS * WPR; q += bd) {
+            const int y = q / WPR, w = q % WPR;
+            uint32_t bits = sm.mask[q];
+            int pos = sm.row_start[y];
+            for (int w2 = 0; w2 < w; ++w2) pos += __popc(sm.mask[y * WPR + w2]);
+            while (bits) {
+                const int bit = __ffs(bits) - 1;
+                sm.list[pos++] = (uint16_t)(y * TS + w * 32 + bit);
+                bits &= bits - 1;
+            }
+        }
+        __syncthreads();
+        n_need = (int)sm.row_start[TS];
+    }
+    uint4* t4 = reinterpret_cast<uint4*>(sm.tile);
+    for (int q = tid; q < TS * TS / 4; q += bd) t4[q] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
+    __syncthreads();
+    if (n_need == 0) return 0;
+    const float ox = (float)(tx * TS), oy = (float)(ty * TS);
+    const uint64_t off = B.t_off[te];
+    uint64_t cnt = B.t_cnt[te];
+    const uint64_t cap = (uint64_t)W->bin_cap;
+    if (off + cnt > cap) cnt = off < cap ? cap - off : 0;
+    for (uint64_t e = warp; e < cnt; e += n_warps) {
+        const int t = (int)B.bins[off + e];
+        TriT T;
+        tri_texel(J, B, lp, ls, t, T);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) { T.x[k] -= ox; T.y[k] -= oy; }
+        if (!may_shade<TS>(sm, T, cull_ok)) {
+            if (PROF && lane == 0) ++culled;
+            continue;
+        }
+        Edges ed;
+        if (!make_edges(T, ed)) continue;
+        const float xmin = fminf(T.x[0], fminf(T.x[1], T.x[2])), xmax = fmaxf(T.x[0], fmaxf(T.x[1], T.x[2]));
+        const float ymin = fminf(T.y[0], fminf(T.y[1], T.y[2])), ymax = fmaxf(T.y[0], fmaxf(T.y[1], T.y[2]));
+        const int x0 = max(0, (int)ceilf(xmin - 0.5f)), x1 = min(TS - 1, (int)floorf(xmax - 0.5f));
+        const int y0 = max(0, (int)ceilf(ymin - 0.5f)), y1 = min(TS - 1, (int)floorf(ymax - 0.5f));
+        if (x0 > x1 || y0 > y1) continue;
+        const float inv_a = 1.f / ed.area2;
+        const float e0 = T.d[0] * inv_a, e1 = T.d[1] * inv_a, e2 = T.d[2] * inv_a;
+        const int bw = x1 - x0 + 1, n_px = bw * (y1 - y0 + 1);
+        const int q_beg = dense ? 0 : (int)sm.row_start[y0], q_end = dense ? 0 : (int)sm.row_start[y1 + 1];
+        if (dense || n_px <= q_end - q_beg) {
+            const float inv_bw = 1.f / bw;
+            for (int q = lane; q < n_px; q += 32) {
+                const int ry = fdiv(q, bw, inv_bw);
+                const int iy = y0 + ry, ix = x0 + q - ry * bw;
+                if (!dense && !(sm.mask[iy * WPR + (ix >> 5)] & (1u << (ix & 31)))) continue;
+                const float px = ix + 0.5f, py = iy + 0.5f;
+                const float w0 = ed.A[0] * px + ed.Bc[0] * py + ed.C[0];
+                const float w1 = ed.A[1] * px + ed.Bc[1] * py + ed.C[1];
+                const float w2 = ed.A[2] * px + ed.Bc[2] * py + ed.C[2];
+                if (PROF) ++visits;
+                if (w0 >= 0.f && w1 >= 0.f && w2 >= 0.f) {
+                    atomicMin(&sm.tile[iy * TS + ix], depth_store_key(w0 * e0 + w1 * e1 + w2 * e2, lp, u24));
+                    if (PROF) ++writes;
+                }
+            }
+        } else {
+            for (int q = q_beg + lane; q < q_end; q += 32) {
+                const int p = sm.list[q];
+                const int ix = p & (TS - 1), iy = p >> SH;
+                if (ix < x0 || ix > x1) continue;
+                const float px = ix + 0.5f, py = iy + 0.5f;
+                const float w0 = ed.A[0] * px + ed.Bc[0] * py + ed.C[0];
+                const float w1 = ed.A[1] * px + ed.Bc[1] * py + ed.C[1];
+                const float w2 = ed.A[2] * px + ed.Bc[2] * py + ed.C[2];
+                if (PROF) ++visits;
+                if (w0 >= 0.f && w1 >= 0.f && w2 >= 0.f) {
+                    atomicMin(&sm.tile[p], depth_store_key(w0 * e0 + w1 * e1 + w2 * e2, lp, u24));
+                    if (PROF) ++writes;
+                }
+            }
+        }
+    }
+    __syncthreads();
+    return n_need;
+}
+
+// Add per-thread work counters to the global profile counters (warp-reduced).
+__device__ __forceinline__ void flush_profile(const Buffers& B, unsigned int samples, unsigned int visits,
+                                              unsigned int writes, unsigned int culled)
+{
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        samples += __shfl_xor_sync(0xffffffffu, samples, off);
+        visits += __shfl_xor_sync(0xffffffffu, visits, off);
+        writes += __shfl_xor_sync(0xffffffffu, writes, off);
+        culled += __shfl_xor_sync(0xffffffffu, culled, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&B.ctr->prof_samples, (unsigned long long)samples);
+        atomicAdd(&B.ctr->prof_visits, (unsigned long long)visits);
+        atomicAdd(&B.ctr->prof_writes, (unsigned long long)writes);
+        atomicAdd(&B.ctr->prof_culled, (unsigned long long)culled);
+    }
+}
+
+// Decode a non-empty tile entry.
+__device__ __forceinline__ void decode_tile(const JobDev* jobs, int nj, uint32_t te, int& j, int& ls, int& tx,
+                                            int& ty)
+{
+    j = job_of(nj, te, [&](int q) { return jobs[q].te_base; });
+    const JobDev& J = jobs[j];
+    const int64_t lte = te - J.te_base;
+    const int tps = J.tiles_x * J.tiles_x;
+    ls = (int)(lte / tps);
+    const int tl = (int)(lte % tps);
+    tx = tl % J.tiles_x;
+    ty = tl / J.tiles_x;
+}
+
+// Receivers of a tile entry, clamped to the receiver pool.
+__device__ __forceinline__ void tile_receivers(const Buffers& B, const WaveDev* W, int64_t te, uint64_t& r0, int& n)
+{
+    r0 = B.t_roff[te];
+    uint64_t r1 = r0 + B.t_rcnt[te];
+    if (r1 > (uint64_t)W->recv_cap) r1 = (uint64_t)W->recv_cap;
+    n = r1 > r0 ? (int)(r1 - r0) : 0;
+}
+
+// ---------------------------------------------------------------------------
+// k_raster_test: fused path -- rasterise the tile in shared memory, then
+// depth-test every sample that reads it; shaded counts go to (step, cell)
+// ---------------------------------------------------------------------------
+template <int TS, bool PROF>
+__global__ void __launch_bounds__(256) k_raster_test(const WaveDev* __restrict__ W,
+                                                     const JobDev* __restrict__ jobs, Buffers B)
+{
+    __shared__ __align__(16) TileSm<TS> sm;
+    unsigned int p_samples = 0, p_visits = 0, p_writes = 0, p_culled = 0;
+    __shared__ unsigned int s_item;
+    const unsigned int n_ne = B.ctr->n_nonempty;
+    const int nj = W->n_jobs;
+    const int want_bits = W->want_bits;
+    const int u24 = W->depth_u24;
+    const int tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(&B.ctr->raster_next, 1u);
+        __syncthreads();
+        const unsigned int item = s_item;
+        __syncthreads();
+        if (item >= n_ne) break;
+        const uint32_t te = B.nonempty[item];
+        int j, ls, tx, ty;
+        decode_tile(jobs, nj, te, j, ls, tx, ty);
+        const JobDev& J = jobs[j];
+        uint64_t r0;
+        int nrecv;
+        tile_receivers(B, W, te, r0, nrecv);
+        stage_receivers<TS>(sm, J, B, ls, tx, ty, r0, min(nrecv, kRecvChunk));
+        if (tile_raster<TS, PROF>(sm, J, B, W, ls, tx, ty, te, r0, nrecv, p_visits, p_writes, p_culled) == 0)
+            continue;
+        const LightParams& lp = B.lp[J.js_base + ls];
+        const int C = J.n_cells;
+        uint32_t* cnt_row = B.cs_cnt + J.cs_base + (int64_t)ls * C;
+        unsigned long long* bits_row = B.cs_bits + J.cs_base + (int64_t)ls * C;
+        for (int c0 = 0; c0 < nrecv; c0 += kRecvChunk) {
+            if (c0 > 0) stage_receivers<TS>(sm, J, B, ls, tx, ty, r0 + c0, min(kRecvChunk, nrecv - c0));
+            uint32_t cnt = 0;
+            unsigned long long bits = 0ull;
+            for_tile_samples<TS>(
+                sm, J, tx, ty,
+                [&](const RecvSm& R, int k, int ix, int iy, float d) {
+                    if (PROF) ++p_samples;
+                    const uint32_t key = sm.tile[(iy & (TS - 1)) * TS + (ix & (TS - 1))];
+                    if (key == kEmpty) return;
+                    const bool shaded = u24 ? (d - lp.dnear) * lp.qscale > (float)key + R.s.bias * lp.qscale
+                                            : d > okey_inv(key) + R.s.bias;
+                    if (shaded) {
+                        ++cnt;
+                        if (k < 64) bits |= 1ull << k;
+                    }
+                },
+                [&](const RecvSm& R, int cu, int cv) {
+                    if (cnt) {
+                        const int gcell = R.cell_base + cv * R.cu + cu;
+                        atomicAdd(&cnt_row[gcell], cnt);
+                        if (want_bits) atomicOr(&bits_row[gcell], bits);
+                    }
+                    cnt = 0;
+                    bits = 0ull;
+                });
+            __syncthreads();
+        }
+    }
+    if (PROF) flush_profile(B, p_samples, p_visits, p_writes, p_culled);
+}
+
+// ---------------------------------------------------------------------------
+// k_raster_map: map path -- rasterise the tile and store it in HBM for the
+// gather kernel (coalesced 16-byte stores)
+// ---------------------------------------------------------------------------
+template <int TS, bool PROF>
+__global__ void __launch_bounds__(256) k_raster_map(const WaveDev* __restrict__ W,
+                                                    const JobDev* __restrict__ jobs, Buffers B)
+{
+    __shared__ __align__(16) TileSm<TS> sm;
+    unsigned int p_visits = 0, p_writes = 0, p_culled = 0;
     __shared__ unsigned int s_item;
     const unsigned int n_ne = B.ctr->n_nonempty;
     const int64_t map_cap = W->map_cap_tiles;
-    const int64_t bin_cap = W->bin_cap;
     const int nj = W->n_jobs;
-    const int u24 = W->depth_u24;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, n_warps = blockDim.x >> 5;
+    const int tid = threadIdx.x, bd = blockDim.x;
     for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(&B.ctr->raster_next, 1u);
+        if (tid == 0) s_item = atomicAdd(&B.ctr->raster_next, 1u);
         __syncthreads();
         const unsigned int item = s_item;
         __syncthreads();
         if (item >= n_ne || item >= map_cap) break;
         const uint32_t te = B.nonempty[item];
-        int j = job_of(nj, te, [&](int q) { return jobs[q].te_base; });
+        int j, ls, tx, ty;
+        decode_tile(jobs, nj, te, j, ls, tx, ty);
         const JobDev& J = jobs[j];
-        const int64_t lte = te - J.te_base;
-        const int tps = J.tiles_x * J.tiles_x;
-        const int ls = (int)(lte / tps), tl = (int)(lte % tps);
-        const int tx = tl % J.tiles_x, ty = tl / J.tiles_x;
-        const LightParams lp = B.lp[J.js_base + ls];
-        const float ox = (float)(tx * TS), oy = (float)(ty * TS);
-        uint4* t4 = reinterpret_cast<uint4*>(tile);
-        for (int q = threadIdx.x; q < TS * TS / 4; q += blockDim.x) t4[q] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
-        __syncthreads();
-        uint64_t off = B.t_off[te];
-        uint64_t cnt = B.t_cnt[te];
-        if (off + cnt > (uint64_t)bin_cap) cnt = off < (uint64_t)bin_cap ? bin_cap - off : 0;
-        for (uint64_t e = warp; e < cnt; e += n_warps) {
-            const int t = (int)B.bins[off + e];
-            TriT T;
-            tri_texel(J, B, lp, ls, t, T);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) { T.x[k] -= ox; T.y[k] -= oy; }
-            Edges ed;
-            if (!make_edges(T, ed)) continue;
-            float xmin = fminf(T.x[0], fminf(T.x[1], T.x[2])), xmax = fmaxf(T.x[0], fmaxf(T.x[1], T.x[2]));
-            float ymin = fminf(T.y[0], fminf(T.y[1], T.y[2])), ymax = fmaxf(T.y[0], fmaxf(T.y[1], T.y[2]));
-            int x0 = max(0, (int)ceilf(xmin - 0.5f)), x1 = min(TS - 1, (int)floorf(xmax - 0.5f));
-            int y0 = max(0, (int)ceilf(ymin - 0.5f)), y1 = min(TS - 1, (int)floorf(ymax - 0.5f));
-            if (x0 > x1 || y0 > y1) continue;
-            const int bw = x1 - x0 + 1, bh = y1 - y0 + 1, n_px = bw * bh;
-            const float inv_a = 1.f / ed.area2;
-            const float inv_bw = 1.f / bw;
-            // barycentric depth weights: d = sum_k w_k d_k / area2
-            const float e0 = T.d[0] * inv_a, e1 = T.d[1] * inv_a, e2 = T.d[2] * inv_a;
-            for (int q = lane; q < n_px; q += 32) {
-                int ry = (int)((q + 0.5f) * inv_bw);  // exact: q < 2^12, bw <= 64
-                int rx = q - ry * bw;
-                if (rx < 0) { --ry; rx += bw; }
-                if (rx >= bw) { ++ry; rx -= bw; }
-                const int iy = y0 + ry, ix = x0 + rx;
-                const float px = ix + 0.5f, py = iy + 0.5f;
-                const float w0 = ed.A[0] * px + ed.Bc[0] * py + ed.C[0];
-                const float w1 = ed.A[1] * px + ed.Bc[1] * py + ed.C[1];
-                const float w2 = ed.A[2] * px + ed.Bc[2] * py + ed.C[2];
-                if (w0 >= 0.f && w1 >= 0.f && w2 >= 0.f && ry < bh) {
-                    const float d = w0 * e0 + w1 * e1 + w2 * e2;
-                    atomicMin(&tile[iy * TS + ix], depth_store_key(d, lp, u24));
-                }
-            }
-        }
-        __syncthreads();
+        uint64_t r0;
+        int nrecv;
+        tile_receivers(B, W, te, r0, nrecv);
+        stage_receivers<TS>(sm, J, B, ls, tx, ty, r0, min(nrecv, kRecvChunk));
+        if (tile_raster<TS, PROF>(sm, J, B, W, ls, tx, ty, te, r0, nrecv, p_visits, p_writes, p_culled) == 0)
+            continue;
+        const uint4* t4 = reinterpret_cast<const uint4*>(sm.tile);
         uint4* dst = reinterpret_cast<uint4*>(B.map + ((size_t)item * (TS * TS)));
-        for (int q = threadIdx.x; q < TS * TS / 4; q += blockDim.x) dst[q] = t4[q];
+        for (int q = tid; q < TS * TS / 4; q += bd) dst[q] = t4[q];
+        __syncthreads();
+    }
+    if (PROF) flush_profile(B, 0u, p_visits, p_writes, p_culled);
+}
+
+// ---------------------------------------------------------------------------
+// PV model per (step, module) from the cell tallies (Section 2, step 4)
+// ---------------------------------------------------------------------------
+constexpr int kPvThreads = 128;
+
+// Irradiance per cell, substring currents, MPP over the bypass states.  All
+// threads of the block call it with the cell counts in shared memory.
+__device__ void module_pv(const JobDev& J, const ModuleDev& M, const ModStep& s, const LightParams& lp,
+                          const uint32_t* s_cnt, uint32_t* s_imin, const Buffers& B, int64_t msi)
+{
+    const int ncell = M.cu * M.cv;
+    const float beam = lp.dni * fmaxf(0.f, s.cosi);
+    const float diff = lp.dhi * (1.f + s.nz) * 0.5f;
+    const float inv_nn = 1.f / J.nn;
+    const int* csub = J.lay_sub + J.lay_off[M.layout];
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+        const float f = s_cnt[c] * inv_nn;
+        const float G = beam * (1.f - f) + diff;
+        const float I = J.i_ref * G * 1e-3f;
+        atomicMin(&s_imin[csub[c]], __float_as_uint(I));  // I >= 0: uint order = float order
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const int* nk = J.lay_nk + J.lay_nk_off[M.layout];
+        const int ns = M.n_sub;
+        float best = 0.f, vsum = 0.f;
+        for (int k = 0; k < ns; ++k) {
+            const float ik = __uint_as_float(s_imin[k]);
+            float volt = 0.f;
+            for (int q = 0; q < ns; ++q)
+                volt += __uint_as_float(s_imin[q]) >= ik ? nk[q] * J.v_cell : -J.v_diode;
+            best = fmaxf(best, ik * volt);
+            vsum += nk[k] * J.v_cell;
+        }
+        B.ms_p[msi] = best;
+        B.ms_pu[msi] = J.i_ref * (beam + diff) * 1e-3f * vsum;
+        B.ms_beam[msi] = beam;
+    }
+}
+
+__device__ __forceinline__ void zero_step_module(const JobDev& J, const ModuleDev& M, int ls, int64_t msi,
+                                                 const Buffers& B)
+{
+    const int ncell = M.cu * M.cv, C = J.n_cells;
+    const int64_t row = (int64_t)(J.out_row0 + ls);
+    if (threadIdx.x == 0) { B.ms_p[msi] = 0.f; B.ms_pu[msi] = 0.f; B.ms_beam[msi] = 0.f; }
+    for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+        B.cs_cnt[J.cs_base + (int64_t)ls * C + M.cell_base + c] = 0u;
+        if (J.out_counts) J.out_counts[row * C + M.cell_base + c] = 0;
+        if (J.out_bits) J.out_bits[row * C + M.cell_base + c] = 0ull;
+    }
+}
+
+// Fused path: the tallies were accumulated by k_raster_test.
+__global__ void __launch_bounds__(kPvThreads) k_pv(const WaveDev* __restrict__ W, const JobDev* __restrict__ jobs,
+                                                   Buffers B)
+{
+    __shared__ uint32_t s_cnt[kMaxCellsPerModule];
+    __shared__ uint32_t s_imin[kMaxSub];
+    const int64_t tot = W->tot_mod;
+    const int nj = W->n_jobs;
+    for (int64_t item = blockIdx.x; item < tot; item += gridDim.x) {
+        int j = job_of(nj, item, [&](int q) { return jobs[q].it_mod; });
+        const JobDev& J = jobs[j];
+        const int64_t li = item - J.it_mod;
+        const int ls = (int)(li / J.n_mods), m = (int)(li % J.n_mods);
+        const int64_t msi = J.ms_base + li;
+        const LightParams& lp = B.lp[J.js_base + ls];
+        const ModuleDev& M = J.mods[m];
+        if (!lp.valid) {
+            zero_step_module(J, M, ls, msi, B);
+            continue;
+        }
+        const int ncell = M.cu * M.cv, C = J.n_cells;
+        const int64_t row = (int64_t)(J.out_row0 + ls);
+        const int64_t cbase = J.cs_base + (int64_t)ls * C + M.cell_base;
+        for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+            const uint32_t cnt = B.cs_cnt[cbase + c];
+            s_cnt[c] = cnt;
+            if (J.out_counts) J.out_counts[row * C + M.cell_base + c] = (uint8_t)cnt;
+            if (J.out_bits) J.out_bits[row * C + M.cell_base + c] = B.cs_bits[cbase + c];
+        }
+        if (threadIdx.x < kMaxSub) s_imin[threadIdx.x] = 0x7F800000u;  // +inf
+        __syncthreads();
+        module_pv(J, M, B.ms[msi], lp, s_cnt, s_imin, B, msi);
         __syncthreads();
     }
 }
 
 // ---------------------------------------------------------------------------
-// k_sample: per (step, module) depth tests, cell tallies and the PV model
+// k_sample: map path -- per (step, module) texel gathers from the HBM map,
+// depth tests, warp-ballot cell tallies, then the PV model
 // ---------------------------------------------------------------------------
-constexpr int kSampleThreads = 128;
-
-__global__ void __launch_bounds__(kSampleThreads) k_sample(const WaveDev* __restrict__ W,
-                                                           const JobDev* __restrict__ jobs, Buffers B)
+__global__ void __launch_bounds__(kPvThreads) k_sample(const WaveDev* __restrict__ W,
+                                                       const JobDev* __restrict__ jobs, Buffers B)
 {
     __shared__ uint32_t s_cnt[kMaxCellsPerModule];
     __shared__ unsigned long long s_bits[kMaxCellsPerModule];
@@ -760,30 +1284,23 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample(const WaveDev* __rest
         const JobDev& J = jobs[j];
         const int64_t li = item - J.it_mod;
         const int ls = (int)(li / J.n_mods), m = (int)(li % J.n_mods);
-        const int64_t js = J.js_base + ls;
         const int64_t msi = J.ms_base + li;
-        const LightParams lp = B.lp[js];
+        const LightParams& lp = B.lp[J.js_base + ls];
         const ModuleDev& M = J.mods[m];
+        if (!lp.valid) {
+            zero_step_module(J, M, ls, msi, B);
+            continue;
+        }
         const int cu = M.cu, ncell = M.cu * M.cv;
         const int n = J.n, nn = J.nn;
         const int C = J.n_cells;
         const int64_t row = (int64_t)(J.out_row0 + ls);
-        if (!lp.valid) {
-            if (threadIdx.x == 0) { B.ms_p[msi] = 0.f; B.ms_pu[msi] = 0.f; B.ms_beam[msi] = 0.f; }
-            for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
-                B.cs_cnt[J.cs_base + (int64_t)ls * C + M.cell_base + c] = 0;
-                if (J.out_counts) J.out_counts[row * C + M.cell_base + c] = 0;
-                if (J.out_bits) J.out_bits[row * C + M.cell_base + c] = 0ull;
-            }
-            continue;
-        }
         const ModStep s = B.ms[msi];
         for (int c = threadIdx.x; c < ncell; c += blockDim.x) { s_cnt[c] = 0; s_bits[c] = 0ull; }
-        if (threadIdx.x < kMaxSub) s_imin[threadIdx.x] = 0x7F800000u;  // +inf
+        if (threadIdx.x < kMaxSub) s_imin[threadIdx.x] = 0x7F800000u;
         __syncthreads();
         const int S = ncell * nn;
-        const float inv_n = 1.f / n;
-        const float pitch = M.pitch;
+        const float p_over_n = __fdiv_rn(M.pitch, (float)n);
         const int R = J.R;
         const int64_t te0 = J.te_base + (int64_t)ls * J.tiles_x * J.tiles_x;
         for (int g0 = 0; g0 < S; g0 += blockDim.x) {
@@ -793,37 +1310,30 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample(const WaveDev* __rest
                 int c = g / nn, k = g - c * nn;
                 int jj = k / n, ii = k - jj * n;
                 int cv_ = c / cu, cu_ = c - cv_ * cu;
-                float a = (cu_ + (ii + 0.5f) * inv_n) * pitch;
-                float b = (cv_ + (jj + 0.5f) * inv_n) * pitch;
-                float tx = s.tx0 + a * s.tax + b * s.tbx;
-                float ty = s.ty0 + a * s.tay + b * s.tby;
-                float d = s.d0 + a * s.da + b * s.db;
-                int ix = min(R - 1, max(0, (int)floorf(tx)));
-                int iy = min(R - 1, max(0, (int)floorf(ty)));
-                int64_t te = te0 + (int64_t)(iy >> sh) * J.tiles_x + (ix >> sh);
+                float a, b, d;
+                int ix, iy;
+                sample_ab(cu_ * n + ii, cv_ * n + jj, p_over_n, a, b);
+                sample_texel(s, a, b, R, ix, iy, d);
+                const int64_t te = te0 + (int64_t)(iy >> sh) * J.tiles_x + (ix >> sh);
                 if (B.t_cnt[te] != 0u) {
-                    uint32_t slot = B.t_slot[te];
+                    const uint32_t slot = B.t_slot[te];
                     if (slot < map_cap) {
-                        uint32_t key = B.map[((size_t)slot << (2 * sh)) + ((iy & tmask) << sh) + (ix & tmask)];
+                        const uint32_t key = B.map[((size_t)slot << (2 * sh)) + ((iy & tmask) << sh) + (ix & tmask)];
                         if (key != kEmpty) {
-                            if (u24) {
-                                float q = (d - lp.dnear) * lp.qscale;
-                                shaded = q > (float)key + s.bias * lp.qscale;
-                            } else {
-                                shaded = d > okey_inv(key) + s.bias;
-                            }
+                            if (u24) shaded = (d - lp.dnear) * lp.qscale > (float)key + s.bias * lp.qscale;
+                            else shaded = d > okey_inv(key) + s.bias;
                         }
                     }
                 }
             }
-            unsigned int ball = __ballot_sync(0xffffffffu, shaded);
+            const unsigned int ball = __ballot_sync(0xffffffffu, shaded);
             if (lane == 0 && ball) {
-                int gw = g;  // first sample of this warp
-                int glast = min(gw + 31, S - 1);
+                const int gw = g;  // first sample of this warp
+                const int glast = min(gw + 31, S - 1);
                 for (int c = gw / nn; c <= glast / nn; ++c) {
-                    int lo = max(c * nn, gw), hi = min((c + 1) * nn, glast + 1);
-                    unsigned int msk = (hi - lo >= 32) ? 0xffffffffu : ((1u << (hi - lo)) - 1u);
-                    unsigned int part = (ball >> (lo - gw)) & msk;
+                    const int lo = max(c * nn, gw), hi = min((c + 1) * nn, glast + 1);
+                    const unsigned int msk = (hi - lo >= 32) ? 0xffffffffu : ((1u << (hi - lo)) - 1u);
+                    const unsigned int part = (ball >> (lo - gw)) & msk;
                     if (part) {
                         atomicAdd(&s_cnt[c], (uint32_t)__popc(part));
                         if (nn <= 64) atomicOr(&s_bits[c], (unsigned long long)part << (lo - c * nn));
@@ -832,39 +1342,13 @@ __global__ void __launch_bounds__(kSampleThreads) k_sample(const WaveDev* __rest
             }
         }
         __syncthreads();
-        const float beam = lp.dni * fmaxf(0.f, s.cosi);
-        const float diff = lp.dhi * (1.f + s.nz) * 0.5f;
-        const float inv_nn = 1.f / nn;
-        const int* csub = J.lay_sub + J.lay_off[M.layout];
         for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
-            uint32_t cnt = s_cnt[c];
-            float f = cnt * inv_nn;
-            float G = beam * (1.f - f) + diff;
-            float I = J.i_ref * G * 1e-3f;
-            atomicMin(&s_imin[csub[c]], __float_as_uint(I));
-            B.cs_cnt[J.cs_base + (int64_t)ls * C + M.cell_base + c] = (uint8_t)cnt;
+            const uint32_t cnt = s_cnt[c];
+            B.cs_cnt[J.cs_base + (int64_t)ls * C + M.cell_base + c] = cnt;
             if (J.out_counts) J.out_counts[row * C + M.cell_base + c] = (uint8_t)cnt;
             if (J.out_bits) J.out_bits[row * C + M.cell_base + c] = s_bits[c];
         }
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            const int* nk = J.lay_nk + J.lay_nk_off[M.layout];
-            const int ns = M.n_sub;
-            float best = 0.f, vsum = 0.f;
-            for (int k = 0; k < ns; ++k) {
-                float ik = __uint_as_float(s_imin[k]);
-                float volt = 0.f;
-                for (int q = 0; q < ns; ++q) {
-                    float iq = __uint_as_float(s_imin[q]);
-                    volt += iq >= ik ? nk[q] * J.v_cell : -J.v_diode;
-                }
-                best = fmaxf(best, ik * volt);
-                vsum += nk[k] * J.v_cell;
-            }
-            B.ms_p[msi] = best;
-            B.ms_pu[msi] = J.i_ref * (beam + diff) * 1e-3f * vsum;
-            B.ms_beam[msi] = beam;
-        }
+        module_pv(J, M, s, lp, s_cnt, s_imin, B, msi);
         __syncthreads();
     }
 }
@@ -898,8 +1382,8 @@ __global__ void k_epilogue(const WaveDev* __restrict__ W, const JobDev* __restri
             for (int ls = 0; ls < J.k; ++ls) {
                 const LightParams& lp = B.lp[J.js_base + ls];
                 if (!lp.valid) continue;
-                float beam = B.ms_beam[J.ms_base + (int64_t)ls * Mn + m];
-                uint32_t cnt = B.cs_cnt[J.cs_base + (int64_t)ls * C + c];
+                const float beam = B.ms_beam[J.ms_base + (int64_t)ls * Mn + m];
+                const uint32_t cnt = B.cs_cnt[J.cs_base + (int64_t)ls * C + c];
                 kahan_add(acc, beam * (cnt * inv_nn) * lp.dt);
             }
             J.kahan_cell[c] = acc;
@@ -909,7 +1393,7 @@ __global__ void k_epilogue(const WaveDev* __restrict__ W, const JobDev* __restri
             for (int ls = 0; ls < J.k; ++ls) {
                 const LightParams& lp = B.lp[J.js_base + ls];
                 const int64_t msi = J.ms_base + (int64_t)ls * Mn + m;
-                float p = B.ms_p[msi], pu = B.ms_pu[msi];
+                const float p = B.ms_p[msi], pu = B.ms_pu[msi];
                 if (J.out_power) J.out_power[(int64_t)(J.out_row0 + ls) * Mn + m] = p;
                 if (J.out_power_u) J.out_power_u[(int64_t)(J.out_row0 + ls) * Mn + m] = pu;
                 if (!lp.valid) continue;
@@ -928,12 +1412,12 @@ __global__ void k_finalize(const float2* __restrict__ kmod, int n_mods, const fl
 {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_mods + n_cells; i += gridDim.x * blockDim.x) {
         if (i < n_mods) {
-            float2 e = kmod[2 * i], eu = kmod[2 * i + 1];
+            const float2 e = kmod[2 * i], eu = kmod[2 * i + 1];
             if (energy) energy[i] = (double)e.x - (double)e.y;
             if (energy_u) energy_u[i] = (double)eu.x - (double)eu.y;
         } else {
-            int c = i - n_mods;
-            float2 h = kcell[c];
+            const int c = i - n_mods;
+            const float2 h = kcell[c];
             if (cell_loss) cell_loss[c] = (double)h.x - (double)h.y;
         }
     }
@@ -950,6 +1434,14 @@ static inline unsigned int grid_for(int64_t items, int per_block, int cap)
     return (unsigned int)g;
 }
 
+template <int TS, bool PROF>
+static void launch_tile_kernels(const WaveDev* W, const JobDev* d_jobs, const Buffers& b, const LaunchCfg& cfg)
+{
+    const int sm = cfg.sm_count;
+    if (cfg.fused) k_raster_test<TS, PROF><<<sm * 4, 256, 0, cfg.stream>>>(W, d_jobs, b);
+    else k_raster_map<TS, PROF><<<sm * 4, 256, 0, cfg.stream>>>(W, d_jobs, b);
+}
+
 cudaError_t launch_wave(const WaveDev* d_wave, const JobDev* d_jobs, const Buffers& b, const LaunchCfg& cfg,
                         int64_t tot_te_host)
 {
@@ -957,9 +1449,11 @@ cudaError_t launch_wave(const WaveDev* d_wave, const JobDev* d_jobs, const Buffe
     cudaStream_t st = cfg.stream;
     const int sm = cfg.sm_count;
     (void)tot_te_host;
+    if (cfg.ev) cudaEventRecord(cfg.ev[0], st);
     k_window<<<sm * 8, kWinPerItem, 0, st>>>(W, d_jobs, b);
     k_light<<<sm, 128, 0, st>>>(W, d_jobs, b);
     k_modsetup<<<sm * 8, 256, 0, st>>>(W, d_jobs, b);
+    if (cfg.ev) cudaEventRecord(cfg.ev[1], st);
     k_bin<0><<<sm * 16, 256, 0, st>>>(W, d_jobs, b);
     k_bin_big<0><<<sm * 8, 256, 0, st>>>(W, d_jobs, b);
     k_scan_a<<<sm * 2, kScanThreads, 0, st>>>(W, b);
@@ -967,12 +1461,21 @@ cudaError_t launch_wave(const WaveDev* d_wave, const JobDev* d_jobs, const Buffe
     k_scan_c<<<sm * 2, kScanThreads, 0, st>>>(W, b);
     k_bin<1><<<sm * 16, 256, 0, st>>>(W, d_jobs, b);
     k_bin_big<1><<<sm * 8, 256, 0, st>>>(W, d_jobs, b);
-    if (cfg.tile == 32)
-        k_raster<32><<<sm * 8, 256, 0, st>>>(W, d_jobs, b);
-    else
-        k_raster<64><<<sm * 8, 256, 0, st>>>(W, d_jobs, b);
-    k_sample<<<sm * 16, kSampleThreads, 0, st>>>(W, d_jobs, b);
+    k_recv_fill<<<sm * 8, 256, 0, st>>>(W, d_jobs, b);
+    if (cfg.ev) cudaEventRecord(cfg.ev[2], st);
+    if (cfg.tile == 32) {
+        if (cfg.profile) launch_tile_kernels<32, true>(W, d_jobs, b, cfg);
+        else launch_tile_kernels<32, false>(W, d_jobs, b, cfg);
+    } else {
+        if (cfg.profile) launch_tile_kernels<64, true>(W, d_jobs, b, cfg);
+        else launch_tile_kernels<64, false>(W, d_jobs, b, cfg);
+    }
+    if (cfg.ev) cudaEventRecord(cfg.ev[3], st);
+    if (cfg.fused) k_pv<<<sm * 16, kPvThreads, 0, st>>>(W, d_jobs, b);
+    else k_sample<<<sm * 16, kPvThreads, 0, st>>>(W, d_jobs, b);
+    if (cfg.ev) cudaEventRecord(cfg.ev[4], st);
     k_epilogue<<<sm * 8, 256, 0, st>>>(W, d_jobs, b);
+    if (cfg.ev) cudaEventRecord(cfg.ev[5], st);
     return cudaGetLastError();
 }
 

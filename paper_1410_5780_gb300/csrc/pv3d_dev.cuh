@@ -107,23 +107,32 @@ struct WaveDev {
     int32_t n_jobs;
     int32_t tile_sh;    // log2 of the tile side
     int32_t depth_u24;
-    int32_t pad;
+    int32_t fused;      // 1: depth tests inside the tile CTA; 0: map in HBM + gather kernel
+    int32_t want_bits;  // per-sample flags requested by some job of the wave
+    int32_t profile;    // count work (texel visits, sample tests) into Counters
     int64_t tot_js, tot_te, tot_ms, tot_cs;
     int64_t tot_win, tot_mod, tot_tri, tot_epi;
-    int64_t bin_cap, map_cap_tiles, big_cap;
+    int64_t bin_cap, map_cap_tiles, big_cap, recv_cap;
 };
 
 struct Counters {
     unsigned int n_big;
     unsigned int n_nonempty;
     unsigned int raster_next;
-    unsigned int overflow;  // bit 0 bins, bit 1 map tiles, bit 2 big list
+    unsigned int overflow;  // bit 0 bins, bit 1 map tiles, bit 2 big list, bit 3 receivers
     unsigned long long tot_bins;
+    unsigned long long tot_recv;
+    unsigned long long need_recv;
     unsigned long long stat_nonempty;
     unsigned long long stat_bins;
     unsigned long long need_bins;    // max over waves of the bins a wave needed
     unsigned long long need_tiles;   // max over waves of the map tiles a wave needed
     unsigned long long need_big;
+    // work counters, filled when WaveDev::profile is set
+    unsigned long long prof_samples;   // sample depth tests in rasterised tiles
+    unsigned long long prof_visits;    // texel coverage tests
+    unsigned long long prof_writes;    // covered texels (depth atomicMin)
+    unsigned long long prof_culled;    // (triangle, tile) pairs skipped by the receiver-plane test
 };
 
 // Scratch and pools, sized by the host for the largest wave.
@@ -134,27 +143,37 @@ struct Buffers {
     float* ms_p;             // [tot_ms]
     float* ms_pu;            // [tot_ms]
     float* ms_beam;          // [tot_ms]  DNI * max(0, cos i)
-    uint8_t* cs_cnt;         // [tot_cs]
-    uint32_t* t_far;         // [tot_te]
-    uint32_t* t_cnt;         // [tot_te]
+    uint32_t* cs_cnt;        // [tot_cs]  shaded samples per (step, cell)
+    unsigned long long* cs_bits;  // [tot_cs] shaded flags per (step, cell), fused path with flags requested
+    uint32_t* t_far;         // [tot_te]  far-plane key of the tile (0 = no sample)
+    uint32_t* t_cnt;         // [tot_te]  triangles binned
     uint32_t* t_off;         // [tot_te]
     uint32_t* t_cur;         // [tot_te]
-    uint32_t* t_slot;        // [tot_te]
+    uint32_t* t_slot;        // [tot_te]  index among the wave's non-empty tiles (= map slot)
+    uint32_t* t_rcnt;        // [tot_te]  receiver modules touching the tile
+    uint32_t* t_roff;        // [tot_te]
+    uint32_t* t_rcur;        // [tot_te]
     uint32_t* nonempty;      // [tot_te]
-    uint32_t* bins;          // [bin_cap]
-    uint32_t* map;           // [map_cap_tiles << (2 * tile_sh)]
+    uint32_t* bins;          // [bin_cap]   triangle ids
+    uint32_t* recv;          // [recv_cap]  receiver module ids
+    uint32_t* map;           // [map_cap_tiles << (2 * tile_sh)]  (map path)
     uint2* big;              // [big_cap]  (triangle, js)
-    unsigned long long* block_sums;  // scan partials
+    unsigned long long* block_sums;  // scan partials, 3 per scan tile
     Counters* ctr;
 };
 
 // ---- host launchers (kernels.cu) ------------------------------------------
 struct LaunchCfg {
     int sm_count;
-    int tile;          // 32 or 64
-    int64_t max_tot_te;   // for the scan grid
+    int tile;     // 32 or 64
+    int fused;    // 1: k_raster_test + k_pv; 0: k_raster_map + k_sample
+    int profile;  // counting kernels
     cudaStream_t stream;
+    cudaEvent_t* ev;  // NULL, or 6 events recorded at the stage boundaries of the wave
 };
+
+constexpr int kStages = 5;           // setup, bin, raster(+test), pv/sample, epilogue
+constexpr int kLaunchesPerWave = 14;  // kernels launch_wave starts
 
 cudaError_t launch_wave(const WaveDev* d_wave, const JobDev* d_jobs, const Buffers& b,
                         const LaunchCfg& cfg, int64_t tot_te_host);

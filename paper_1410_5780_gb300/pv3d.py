@@ -28,9 +28,12 @@ PV3D_E_PENDING = -7
 PV3D_E_NOTFOUND = -8
 PV3D_DEPTH_F32 = 0
 PV3D_DEPTH_U24 = 1
+PV3D_PATH_FUSED = 0
+PV3D_PATH_MAP = 1
 
 EXPORTED = ("pv3d_create", "pv3d_destroy", "pv3d_last_error", "pv3d_scene_load", "pv3d_generator_define",
-            "pv3d_set_poses", "pv3d_set_sun", "pv3d_evaluate", "pv3d_submit", "pv3d_poll", "pv3d_release")
+            "pv3d_set_poses", "pv3d_set_sun", "pv3d_evaluate", "pv3d_submit", "pv3d_poll", "pv3d_release",
+            "pv3d_last_profile")
 
 
 class pv3d_opts(C.Structure):
@@ -57,7 +60,18 @@ class pv3d_tracker(C.Structure):
 class pv3d_eval_opts(C.Structure):
     _fields_ = [("samples_per_side", C.c_int32), ("map_res", C.c_int32), ("step_begin", C.c_int64),
                 ("step_end", C.c_int64), ("i_ref", C.c_float), ("v_cell", C.c_float), ("v_diode", C.c_float),
-                ("chunk_steps", C.c_int32), ("stream", C.c_void_p), ("reserved", C.c_int32 * 8)]
+                ("chunk_steps", C.c_int32), ("stream", C.c_void_p), ("path", C.c_int32),
+                ("profile", C.c_int32), ("reserved", C.c_int32 * 6)]
+
+
+class pv3d_profile(C.Structure):
+    _fields_ = [("n_stages", C.c_int32), ("waves", C.c_int32), ("stage_ms", C.c_float * 8),
+                ("device_ms", C.c_float), ("reserved0", C.c_int32), ("sample_tests", C.c_int64),
+                ("texel_visits", C.c_int64), ("texel_writes", C.c_int64), ("tris_culled", C.c_int64),
+                ("nonempty_tiles", C.c_int64), ("binned_tris", C.c_int64)]
+
+
+STAGES = ("setup", "bin", "raster", "pv", "epilogue")
 
 
 class pv3d_result(C.Structure):
@@ -66,7 +80,7 @@ class pv3d_result(C.Structure):
                 ("power_unshaded", C.c_void_p), ("cell_beam_loss", C.c_void_p), ("cell_counts", C.c_void_p),
                 ("sample_bits", C.c_void_p), ("tests", C.c_int64), ("steps_lit", C.c_int64),
                 ("device_ms", C.c_float), ("waves", C.c_int32), ("nonempty_tiles", C.c_int64),
-                ("binned_tris", C.c_int64)]
+                ("binned_tris", C.c_int64), ("kernel_launches", C.c_int64)]
 
 
 _lib = None
@@ -106,6 +120,7 @@ def load(build_if_missing: bool = False):
                                     C.POINTER(C.c_uint64)]
         lib.pv3d_poll.argtypes = [P, C.c_uint64, C.c_int32]
         lib.pv3d_release.argtypes = [P, C.c_uint32]
+        lib.pv3d_last_profile.argtypes = [P, C.POINTER(pv3d_profile)]
         for name in EXPORTED:
             if name not in ("pv3d_destroy", "pv3d_last_error"):
                 getattr(lib, name).restype = C.c_int
@@ -214,9 +229,11 @@ class Context:
         self._gens[gen_id]["steps"] = s.shape[0]
 
     # ---- steps 3 and 4 -----------------------------------------------------
-    def _opts(self, n, map_res, step_begin, step_end, chunk_steps, stream, i_ref, v_cell, v_diode):
+    def _opts(self, n, map_res, step_begin, step_end, chunk_steps, stream, i_ref, v_cell, v_diode, path=0,
+              profile=0):
         return pv3d_eval_opts(samples_per_side=n, map_res=map_res, step_begin=step_begin, step_end=step_end,
-                              chunk_steps=chunk_steps, stream=stream, i_ref=i_ref, v_cell=v_cell, v_diode=v_diode)
+                              chunk_steps=chunk_steps, stream=stream, i_ref=i_ref, v_cell=v_cell, v_diode=v_diode,
+                              path=path, profile=profile)
 
     def _alloc(self, gen_id, step_begin, step_end, outputs, device):
         if gen_id not in self._gens:  # let the library report the unknown id
@@ -244,18 +261,31 @@ class Context:
 
     def evaluate(self, gen_id: int, n: int = 3, map_res: int = 0, step_begin: int = 0, step_end: int = 0,
                  chunk_steps: int = 0, outputs=("energy", "energy_unshaded"), device: bool = True,
-                 stream=None, i_ref: float = 0.0, v_cell: float = 0.0, v_diode: float = 0.0) -> dict:
+                 stream=None, i_ref: float = 0.0, v_cell: float = 0.0, v_diode: float = 0.0,
+                 path: int = PV3D_PATH_FUSED, profile: bool = False) -> dict:
         """pv3d_evaluate.  Returns the requested outputs (torch tensors on the
         device if ``device`` else numpy arrays) plus the counters."""
         if stream is None and device:
             import torch
             stream = torch.cuda.current_stream(self.device).cuda_stream
         res, arrays = self._alloc(gen_id, step_begin, step_end, outputs, device)
-        o = self._opts(n, map_res, step_begin, step_end, chunk_steps, stream, i_ref, v_cell, v_diode)
+        o = self._opts(n, map_res, step_begin, step_end, chunk_steps, stream, i_ref, v_cell, v_diode, path,
+                       int(profile))
         self._check(self.lib.pv3d_evaluate(self.h, gen_id, C.byref(o), C.byref(res)))
         arrays.update(tests=res.tests, steps_lit=res.steps_lit, device_ms=res.device_ms, waves=res.waves,
-                      nonempty_tiles=res.nonempty_tiles, binned_tris=res.binned_tris)
+                      nonempty_tiles=res.nonempty_tiles, binned_tris=res.binned_tris,
+                      kernel_launches=res.kernel_launches)
         return arrays
+
+    def last_profile(self) -> dict:
+        """pv3d_last_profile as a dict (stage times in ms, work counters)."""
+        p = pv3d_profile()
+        self._check(self.lib.pv3d_last_profile(self.h, C.byref(p)))
+        d = {f"{name}_ms": p.stage_ms[k] for k, name in enumerate(STAGES)}
+        d.update(waves=p.waves, device_ms=p.device_ms, sample_tests=p.sample_tests, texel_visits=p.texel_visits,
+                 texel_writes=p.texel_writes, tris_culled=p.tris_culled, nonempty_tiles=p.nonempty_tiles,
+                 binned_tris=p.binned_tris)
+        return d
 
     def submit(self, gen_id: int, n: int = 3, map_res: int = 0, step_begin: int = 0, step_end: int = 0,
                chunk_steps: int = 0, outputs=("energy", "energy_unshaded"), device: bool = True,

@@ -50,13 +50,15 @@ def test_struct_layouts_match_c(tmp_path):
                     'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(pv3d_opts), '
                     'sizeof(pv3d_module), sizeof(pv3d_layout), sizeof(pv3d_tracker), sizeof(pv3d_eval_opts), '
                     'sizeof(pv3d_result), offsetof(pv3d_eval_opts, stream), offsetof(pv3d_result, tests));'
+                    'printf("%zu %zu\\n", sizeof(pv3d_profile), offsetof(pv3d_profile, sample_tests));'
                     'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.dirname(HEADER), str(prog), "-o", str(exe)])
     got = [int(x) for x in subprocess.check_output([str(exe)]).split()]
     exp = [ctypes.sizeof(pv3d.pv3d_opts), ctypes.sizeof(pv3d.pv3d_module), ctypes.sizeof(pv3d.pv3d_layout),
            ctypes.sizeof(pv3d.pv3d_tracker), ctypes.sizeof(pv3d.pv3d_eval_opts), ctypes.sizeof(pv3d.pv3d_result),
-           pv3d.pv3d_eval_opts.stream.offset, pv3d.pv3d_result.tests.offset]
+           pv3d.pv3d_eval_opts.stream.offset, pv3d.pv3d_result.tests.offset,
+           ctypes.sizeof(pv3d.pv3d_profile), pv3d.pv3d_profile.sample_tests.offset]
     assert got == exp
 
 

@@ -75,16 +75,37 @@ def test_mini_tracker(ctx):
     full_check(ctx, w, strict_loss=False)
 
 
-def test_tile32_and_u24(ctx):
+@pytest.mark.parametrize("tile,fmt,path", [(32, 0, 0), (64, 1, 0), (32, 1, 1), (64, 0, 1)])
+def test_tile_depth_format_and_path(tile, fmt, path):
     w = S.make_random_small(111, n_mods=6, n_steps=10, n=4, map_res=1024, tracked=True)
     o = oracle.evaluate_workload(w)
-    for tile, fmt in [(32, pv3d.PV3D_DEPTH_F32), (64, pv3d.PV3D_DEPTH_U24), (32, pv3d.PV3D_DEPTH_U24)]:
-        with pv3d.Context(device=0, tile=tile, depth_format=fmt) as c2:
-            gid = pv3d.load_workload(c2, w)
-            g = run_gpu(c2, gid, w)
-            st = compare(w, g, o, np.arange(w.sun.n_steps))
-            assert st["agree"] >= FLAG_AGREEMENT, (tile, fmt, st)
-            energy_checks(w, g, o, np.arange(w.sun.n_steps))
+    with pv3d.Context(device=0, tile=tile, depth_format=fmt) as c2:
+        gid = pv3d.load_workload(c2, w)
+        g = run_gpu(c2, gid, w, path=path)
+        st = compare(w, g, o, np.arange(w.sun.n_steps))
+        assert st["agree"] >= FLAG_AGREEMENT, (tile, fmt, path, st)
+        energy_checks(w, g, o, np.arange(w.sun.n_steps))
+
+
+@pytest.mark.parametrize("make", ["tracker_mini", "facade_mini", "random"])
+def test_fused_and_map_paths_bit_identical(ctx, make):
+    """The fused path (tests inside the raster CTA) and the map path (HBM map +
+    gather kernel) read the same texels with the same arithmetic."""
+    if make == "tracker_mini":
+        w = S.make_tracker(seed=19, n=4, map_res=2048, grid=(5, 4), terrain_n=96, spacing=1.5, n_pylons=3,
+                           step_h=0.5, days=np.array([15, 100, 200]))
+    elif make == "facade_mini":
+        w = S.make_facade(seed=17, n=8, map_res=2048, n_buildings=20, n_trees=8, n_poles=4, floors=3,
+                          per_floor=8, target_tris=8000, days=np.array([10, 80, 170, 260, 340]), radius=100.0)
+    else:
+        w = S.make_random_small(23, n_mods=8, n_steps=20, n=5, map_res=512, tracked=True)
+    gid = pv3d.load_workload(ctx, w)
+    a = run_gpu(ctx, gid, w, path=pv3d.PV3D_PATH_FUSED, chunk_steps=7)
+    b = run_gpu(ctx, gid, w, path=pv3d.PV3D_PATH_MAP, chunk_steps=7)
+    for k in ("sample_bits", "cell_counts", "power", "power_unshaded", "energy", "energy_unshaded"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    assert a["cell_counts"].sum() > 0
+    ctx.release(gid)
 
 
 def _sampled_full_size(ctx, w, windows, n_mods, seed, chunk_steps=0):

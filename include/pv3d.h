@@ -40,6 +40,7 @@ extern "C" {
 #define PV3D_E_DEVICE    -6  /* CUDA runtime error */
 #define PV3D_E_PENDING   -7  /* pv3d_poll: request not finished yet */
 #define PV3D_E_NOTFOUND  -8  /* unknown scene, generator or request id */
+#define PV3D_E_TOOBIG    -9  /* pv3d_module_shade_noalloc: map_res above PV3D_NOALLOC_MAX_RES */
 
 /* ---- depth formats ------------------------------------------------------ */
 #define PV3D_DEPTH_F32    0  /* FP32 depth, stored as order-preserving uint32 */
@@ -264,6 +265,41 @@ int pv3d_last_profile(pv3d_ctx* ctx, pv3d_profile* out);
 
 /* Free a scene (and every generator defined on it) or a generator. */
 int pv3d_release(pv3d_ctx* ctx, uint32_t scene_or_gen_id);
+
+/* ---- evaluation without device allocation --------------------------------
+ *
+ * The paper has no counterpart to this call: it serves callers that cannot
+ * allocate device memory while they run -- a host loop that hands every byte
+ * of the GPU to its own pool, a latency-critical loop that cannot take the
+ * implicit synchronisation of cudaMalloc/cudaFree, or code recording into a
+ * stream capture, where those calls are not permitted.  It needs no context.
+ *
+ * Shaded-sample counts of ONE fixed module for ONE sun direction: the
+ * triangles are depth-rasterised from the sun into a map of map_res^2 texels
+ * over the module's window (same frame, window, coverage and bias rules as
+ * pv3d_evaluate) and every one of the module's n x n samples per cell is
+ * depth-tested against it.
+ *   tri_xyz       device pointer, 9 floats per triangle (three world vertices, m)
+ *   module        host pointer; tracker must be -1; its layout is not used
+ *   sun_xyz       host pointer, unit vector toward the sun; s.z <= 0 gives zeros
+ *   map_res       power of two, 64..PV3D_NOALLOC_MAX_RES, else PV3D_E_INVALID or
+ *                 PV3D_E_TOOBIG (above the maximum)
+ *   cell_counts   device pointer, cells_u * cells_v uint32, overwritten with the
+ *                 shaded samples per cell (c = cv * cells_u + cu)
+ *   stream        cudaStream_t the work is queued on (NULL = legacy stream);
+ *                 the call returns without waiting for it
+ * The shadow map is one fixed array compiled into the library
+ * (PV3D_NOALLOC_MAX_RES^2 x 4 bytes = 16 MiB on every GPU that loads it, kept
+ * until the process exits); the call allocates nothing.  The first call on a
+ * device, with that device current, looks up the array's device address;
+ * make that first call before any stream capture.  All calls share the array:
+ * each clears the part it uses, and calls that overlap on the GPU (different
+ * streams without ordering) race on it.
+ */
+#define PV3D_NOALLOC_MAX_RES 2048
+int pv3d_module_shade_noalloc(const float* tri_xyz, int64_t n_tris, const pv3d_module* module,
+                              const double* sun_xyz, int32_t samples_per_side, int32_t map_res,
+                              uint32_t* cell_counts, void* stream);
 
 #ifdef __cplusplus
 }

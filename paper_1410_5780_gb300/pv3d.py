@@ -26,6 +26,8 @@ PV3D_E_TIMEOUT = -5
 PV3D_E_DEVICE = -6
 PV3D_E_PENDING = -7
 PV3D_E_NOTFOUND = -8
+PV3D_E_TOOBIG = -9
+PV3D_NOALLOC_MAX_RES = 2048
 PV3D_DEPTH_F32 = 0
 PV3D_DEPTH_U24 = 1
 PV3D_PATH_FUSED = 0
@@ -33,7 +35,7 @@ PV3D_PATH_MAP = 1
 
 EXPORTED = ("pv3d_create", "pv3d_destroy", "pv3d_last_error", "pv3d_scene_load", "pv3d_generator_define",
             "pv3d_set_poses", "pv3d_set_sun", "pv3d_evaluate", "pv3d_submit", "pv3d_poll", "pv3d_release",
-            "pv3d_last_profile")
+            "pv3d_last_profile", "pv3d_module_shade_noalloc")
 
 
 class pv3d_opts(C.Structure):
@@ -121,6 +123,8 @@ def load(build_if_missing: bool = False):
         lib.pv3d_poll.argtypes = [P, C.c_uint64, C.c_int32]
         lib.pv3d_release.argtypes = [P, C.c_uint32]
         lib.pv3d_last_profile.argtypes = [P, C.POINTER(pv3d_profile)]
+        lib.pv3d_module_shade_noalloc.argtypes = [P, C.c_int64, C.POINTER(pv3d_module), P, C.c_int32, C.c_int32,
+                                                  P, P]
         for name in EXPORTED:
             if name not in ("pv3d_destroy", "pv3d_last_error"):
                 getattr(lib, name).restype = C.c_int
@@ -310,6 +314,29 @@ class Context:
     def release(self, scene_or_gen_id: int):
         self._check(self.lib.pv3d_release(self.h, scene_or_gen_id))
         self._gens.pop(scene_or_gen_id, None)
+
+
+def pv3d_module_shade_noalloc(tri_xyz, module: dict, sun_xyz, samples_per_side: int, map_res: int, cell_counts,
+                              stream=None) -> int:
+    """pv3d_module_shade_noalloc (no device allocation inside the library).
+
+    ``tri_xyz``: CUDA tensor, 9 float32 per triangle; ``cell_counts``: CUDA
+    tensor of cells_u * cells_v int32/uint32 (overwritten); ``module``: dict with
+    origin, u, v, pitch, cells_u, cells_v; ``sun_xyz``: 3 floats.  Returns the
+    status code (0 = queued on ``stream``)."""
+    lib = load()
+    md = pv3d_module()
+    md.origin[:] = [float(x) for x in module["origin"]]
+    md.u[:] = [float(x) for x in module["u"]]
+    md.v[:] = [float(x) for x in module["v"]]
+    md.pitch = float(module["pitch"])
+    md.cells_u = int(module["cells_u"]); md.cells_v = int(module["cells_v"])
+    md.layout = 0; md.tracker = -1; md.string_id = 0
+    sun = np.ascontiguousarray(sun_xyz, np.float64).reshape(3)
+    n_tris = int(tri_xyz.numel() // 9) if tri_xyz is not None else 0
+    tp = tri_xyz.data_ptr() if n_tris else None
+    return lib.pv3d_module_shade_noalloc(tp, n_tris, C.byref(md), _p(sun), int(samples_per_side), int(map_res),
+                                         cell_counts.data_ptr(), stream)
 
 
 def load_workload(ctx: Context, w) -> int:

@@ -191,7 +191,7 @@ extern "C" int pv3d_create(pv3d_ctx** out, const pv3d_opts* opts)
     pv3d_opts& o = c->opts;
     if (o.map_res == 0) o.map_res = 4096;
     if (o.tile == 0) o.tile = 64;
-    if (o.chunk_steps == 0) o.chunk_steps = 32;
+    if (o.chunk_steps == 0) o.chunk_steps = 128;
     if (o.max_inflight == 0) o.max_inflight = 64;
     if (o.tile != 32 && o.tile != 64) return PV3D_E_INVALID;
     if (o.map_res < 64 || o.map_res > 16384 || (o.map_res & (o.map_res - 1))) return PV3D_E_INVALID;

@@ -740,6 +740,16 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_c(const WaveDev* __restri
 // per-tile depth rasterisation (shared by the fused and the map kernels)
 // ---------------------------------------------------------------------------
 constexpr int kRecvChunk = 64;  // receivers staged in shared memory at a time
+constexpr int kTriBatch = 64;   // triangles set up in shared memory at a time
+
+// A triangle set up for one tile: edge functions, scaled depths, the texels
+// it visits (its bounding box, or a range of the marked-texel list).
+struct TriSetup {
+    float A[3], Bc[3], C[3];
+    float e0, e1, e2;
+    short x0, y0, bw, list;  // list = 1: visit entries [q_beg, q_beg + work) of the marked list
+    int q_beg, work;
+};
 
 // q / d for 0 <= q < 2^24 (one float estimate, one correction).
 __device__ __forceinline__ int fdiv(int q, int d, float inv_d)
@@ -772,6 +782,8 @@ struct TileSm {
     RecvSm recv[kRecvChunk];
     int n_recv;                      // receivers staged
     int total_cells;                 // cells over the staged receivers
+    TriSetup tri[kTriBatch];         // a batch of set-up triangles
+    int chunk_pref[kTriBatch + 1];   // prefix of their 32-texel work chunks
 };
 
 // Stage receivers [r0, r0 + cnt) of tile (tx, ty): cell box (the tile corners
@@ -966,61 +978,105 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
     uint64_t cnt = B.t_cnt[te];
     const uint64_t cap = (uint64_t)W->bin_cap;
     if (off + cnt > cap) cnt = off < cap ? cap - off : 0;
-    for (uint64_t e = warp; e < cnt; e += n_warps) {
-        const int t = (int)B.bins[off + e];
-        TriT T;
-        tri_texel(J, B, lp, ls, t, T);
+    // triangles in batches: set-up by one thread each, then all warps share
+    // the batch's texel visits in chunks of 32
+    for (uint64_t b0 = 0; b0 < cnt; b0 += kTriBatch) {
+        const int nb = (int)min((uint64_t)kTriBatch, cnt - b0);
+        if (tid < nb) {
+            TriSetup& S = sm.tri[tid];
+            S.work = 0;
+            const int t = (int)B.bins[off + b0 + tid];
+            TriT T;
+            tri_texel(J, B, lp, ls, t, T);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) { T.x[k] -= ox; T.y[k] -= oy; }
-        if (!may_shade<TS>(sm, T, cull_ok)) {
-            if (PROF && lane == 0) ++culled;
-            continue;
+            for (int k = 0; k < 3; ++k) { T.x[k] -= ox; T.y[k] -= oy; }
+            Edges ed;
+            if (!may_shade<TS>(sm, T, cull_ok)) {
+                if (PROF) ++culled;
+            } else if (make_edges(T, ed)) {
+                const float xmin = fminf(T.x[0], fminf(T.x[1], T.x[2])), xmax = fmaxf(T.x[0], fmaxf(T.x[1], T.x[2]));
+                const float ymin = fminf(T.y[0], fminf(T.y[1], T.y[2])), ymax = fmaxf(T.y[0], fmaxf(T.y[1], T.y[2]));
+                const int x0 = max(0, (int)ceilf(xmin - 0.5f)), x1 = min(TS - 1, (int)floorf(xmax - 0.5f));
+                const int y0 = max(0, (int)ceilf(ymin - 0.5f)), y1 = min(TS - 1, (int)floorf(ymax - 0.5f));
+                if (x0 <= x1 && y0 <= y1) {
+                    const float inv_a = 1.f / ed.area2;
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) { S.A[k] = ed.A[k]; S.Bc[k] = ed.Bc[k]; S.C[k] = ed.C[k]; }
+                    S.e0 = T.d[0] * inv_a; S.e1 = T.d[1] * inv_a; S.e2 = T.d[2] * inv_a;
+                    S.x0 = (short)x0; S.y0 = (short)y0; S.bw = (short)(x1 - x0 + 1);
+                    const int n_px = (x1 - x0 + 1) * (y1 - y0 + 1);
+                    const int q_beg = dense ? 0 : (int)sm.row_start[y0];
+                    const int q_end = dense ? 0 : (int)sm.row_start[y1 + 1];
+                    if (dense || n_px <= q_end - q_beg) {
+                        S.list = 0; S.q_beg = 0; S.work = n_px;
+                    } else {
+                        S.list = 1; S.q_beg = q_beg; S.work = q_end - q_beg;
+                    }
+                }
+            }
         }
-        Edges ed;
-        if (!make_edges(T, ed)) continue;
-        const float xmin = fminf(T.x[0], fminf(T.x[1], T.x[2])), xmax = fmaxf(T.x[0], fmaxf(T.x[1], T.x[2]));
-        const float ymin = fminf(T.y[0], fminf(T.y[1], T.y[2])), ymax = fmaxf(T.y[0], fmaxf(T.y[1], T.y[2]));
-        const int x0 = max(0, (int)ceilf(xmin - 0.5f)), x1 = min(TS - 1, (int)floorf(xmax - 0.5f));
-        const int y0 = max(0, (int)ceilf(ymin - 0.5f)), y1 = min(TS - 1, (int)floorf(ymax - 0.5f));
-        if (x0 > x1 || y0 > y1) continue;
-        const float inv_a = 1.f / ed.area2;
-        const float e0 = T.d[0] * inv_a, e1 = T.d[1] * inv_a, e2 = T.d[2] * inv_a;
-        const int bw = x1 - x0 + 1, n_px = bw * (y1 - y0 + 1);
-        const int q_beg = dense ? 0 : (int)sm.row_start[y0], q_end = dense ? 0 : (int)sm.row_start[y1 + 1];
-        if (dense || n_px <= q_end - q_beg) {
-            const float inv_bw = 1.f / bw;
-            for (int q = lane; q < n_px; q += 32) {
-                const int ry = fdiv(q, bw, inv_bw);
-                const int iy = y0 + ry, ix = x0 + q - ry * bw;
-                if (!dense && !(sm.mask[iy * WPR + (ix >> 5)] & (1u << (ix & 31)))) continue;
+        __syncthreads();
+        if (tid == 0) {
+            int acc = 0;
+            for (int k = 0; k < nb; ++k) {
+                sm.chunk_pref[k] = acc;
+                acc += (sm.tri[k].work + 31) >> 5;
+            }
+            sm.chunk_pref[nb] = acc;
+        }
+        __syncthreads();
+        // each warp takes a contiguous range of chunks: one search, then the
+        // triangles of the range in order with their set-up in registers
+        const int n_chunks = sm.chunk_pref[nb];
+        const int c_beg = (int)(((int64_t)n_chunks * warp) / n_warps);
+        const int c_end = (int)(((int64_t)n_chunks * (warp + 1)) / n_warps);
+        int t = 0;
+        {
+            int lo = 0, hi = nb - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (sm.chunk_pref[mid] <= c_beg) lo = mid; else hi = mid - 1;
+            }
+            t = lo;
+        }
+        for (int ch = c_beg; ch < c_end; ++t) {
+            const TriSetup& S = sm.tri[t];
+            const int t_end = min(c_end, sm.chunk_pref[t + 1]);
+            if (ch >= t_end) continue;
+            const float A0 = S.A[0], A1 = S.A[1], A2 = S.A[2];
+            const float B0 = S.Bc[0], B1 = S.Bc[1], B2 = S.Bc[2];
+            const float C0 = S.C[0], C1 = S.C[1], C2 = S.C[2];
+            const float e0 = S.e0, e1 = S.e1, e2 = S.e2;
+            const int x0 = S.x0, y0 = S.y0, bw = S.bw, is_list = S.list, q_beg = S.q_beg, work = S.work;
+            const float inv_bw = 1.f / (float)bw;
+            for (; ch < t_end; ++ch) {
+                const int q = ((ch - sm.chunk_pref[t]) << 5) + lane;
+                if (q >= work) continue;
+                int ix, iy;
+                if (is_list) {
+                    const int p = sm.list[q_beg + q];
+                    ix = p & (TS - 1);
+                    iy = p >> SH;
+                    if (ix < x0 || ix >= x0 + bw) continue;
+                } else {
+                    const int ry = fdiv(q, bw, inv_bw);
+                    iy = y0 + ry;
+                    ix = x0 + q - ry * bw;
+                    if (!dense && !(sm.mask[iy * WPR + (ix >> 5)] & (1u << (ix & 31)))) continue;
+                }
                 const float px = ix + 0.5f, py = iy + 0.5f;
-                const float w0 = ed.A[0] * px + ed.Bc[0] * py + ed.C[0];
-                const float w1 = ed.A[1] * px + ed.Bc[1] * py + ed.C[1];
-                const float w2 = ed.A[2] * px + ed.Bc[2] * py + ed.C[2];
+                const float w0 = A0 * px + B0 * py + C0;
+                const float w1 = A1 * px + B1 * py + C1;
+                const float w2 = A2 * px + B2 * py + C2;
                 if (PROF) ++visits;
                 if (w0 >= 0.f && w1 >= 0.f && w2 >= 0.f) {
                     atomicMin(&sm.tile[iy * TS + ix], depth_store_key(w0 * e0 + w1 * e1 + w2 * e2, lp, u24));
                     if (PROF) ++writes;
                 }
             }
-        } else {
-            for (int q = q_beg + lane; q < q_end; q += 32) {
-                const int p = sm.list[q];
-                const int ix = p & (TS - 1), iy = p >> SH;
-                if (ix < x0 || ix > x1) continue;
-                const float px = ix + 0.5f, py = iy + 0.5f;
-                const float w0 = ed.A[0] * px + ed.Bc[0] * py + ed.C[0];
-                const float w1 = ed.A[1] * px + ed.Bc[1] * py + ed.C[1];
-                const float w2 = ed.A[2] * px + ed.Bc[2] * py + ed.C[2];
-                if (PROF) ++visits;
-                if (w0 >= 0.f && w1 >= 0.f && w2 >= 0.f) {
-                    atomicMin(&sm.tile[p], depth_store_key(w0 * e0 + w1 * e1 + w2 * e2, lp, u24));
-                    if (PROF) ++writes;
-                }
-            }
         }
+        __syncthreads();
     }
-    __syncthreads();
     return n_need;
 }
 

@@ -353,8 +353,11 @@ __global__ void k_modsetup(const WaveDev* __restrict__ W, const JobDev* __restri
         s.bias = lp.delta * (0.70710678f * tan_i + 0.03125f);
         if (u24) s.bias += 2.f / lp.qscale;
         B.ms[J.ms_base + li] = s;
+        // A triangle shades a sample only where its depth is below the
+        // sample's depth minus the bias, so a tile may drop every triangle whose
+        // nearest point is not nearer than (max sample depth - bias).
         const TileRange tr = module_tiles(s, M, J.R, sh);
-        const uint32_t far_key = u24 ? depth_store_key(tr.dmax + s.bias, lp, 1) + 1u : okey(tr.dmax + s.bias);
+        const uint32_t far_key = u24 ? depth_store_key(tr.dmax - s.bias, lp, 1) + 2u : okey(tr.dmax - s.bias);
         const int64_t te0 = J.te_base + (int64_t)ls * J.tiles_x * J.tiles_x;
         for (int ty = tr.ty0; ty <= tr.ty1; ++ty)
             for (int tx = tr.tx0; tx <= tr.tx1; ++tx) {
@@ -784,6 +787,7 @@ struct TileSm {
     int total_cells;                 // cells over the staged receivers
     TriSetup tri[kTriBatch];         // a batch of set-up triangles
     int chunk_pref[kTriBatch + 1];   // prefix of their 32-texel work chunks
+    int any_write;                   // some texel of the tile received a depth
 };
 
 // Stage receivers [r0, r0 + cnt) of tile (tx, ty): cell box (the tile corners
@@ -971,8 +975,10 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
     }
     uint4* t4 = reinterpret_cast<uint4*>(sm.tile);
     for (int q = tid; q < TS * TS / 4; q += bd) t4[q] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
+    if (tid == 0) sm.any_write = 0;
     __syncthreads();
     if (n_need == 0) return 0;
+    bool wrote = false;
     const float ox = (float)(tx * TS), oy = (float)(ty * TS);
     const uint64_t off = B.t_off[te];
     uint64_t cnt = B.t_cnt[te];
@@ -1071,13 +1077,17 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
                 if (PROF) ++visits;
                 if (w0 >= 0.f && w1 >= 0.f && w2 >= 0.f) {
                     atomicMin(&sm.tile[iy * TS + ix], depth_store_key(w0 * e0 + w1 * e1 + w2 * e2, lp, u24));
+                    wrote = true;
                     if (PROF) ++writes;
                 }
             }
         }
         __syncthreads();
     }
-    return n_need;
+    if (wrote) sm.any_write = 1;
+    __syncthreads();
+    // no triangle reaches a texel that a sample reads: every sample is lit
+    return sm.any_write ? n_need : 0;
 }
 
 // Add per-thread work counters to the global profile counters (warp-reduced).
@@ -1219,8 +1229,8 @@ __global__ void __launch_bounds__(256) k_raster_map(const WaveDev* __restrict__ 
         int nrecv;
         tile_receivers(B, W, te, r0, nrecv);
         stage_receivers<TS>(sm, J, B, ls, tx, ty, r0, min(nrecv, kRecvChunk));
-        if (tile_raster<TS, PROF>(sm, J, B, W, ls, tx, ty, te, r0, nrecv, p_visits, p_writes, p_culled) == 0)
-            continue;
+        // the tile is stored even when nothing was drawn: its samples read it
+        tile_raster<TS, PROF>(sm, J, B, W, ls, tx, ty, te, r0, nrecv, p_visits, p_writes, p_culled);
         const uint4* t4 = reinterpret_cast<const uint4*>(sm.tile);
         uint4* dst = reinterpret_cast<uint4*>(B.map + ((size_t)item * (TS * TS)));
         for (int q = tid; q < TS * TS / 4; q += bd) dst[q] = t4[q];

@@ -82,6 +82,13 @@ struct pv3d_ctx {
     DevBuf lp, win, ms, ms_p, ms_pu, ms_beam, cs_cnt, cs_bits, t_far, t_cnt, t_off, t_cur, t_slot, t_rcnt, t_roff, t_rcur, nonempty, bins, recv, map,
         big, block_sums, ctr, waves, jobs, kahan_mod, kahan_cell, staging;
     int64_t bin_cap = 0, map_cap_tiles = 0, big_cap = 0, recv_cap = 0;
+    uint64_t bufgen = 0;  // bumped whenever a pool is reallocated (captured graphs hold its pointers)
+    // captured wave graph: the kernels read the wave from fixed descriptor slots
+    DevBuf wave_slot, jobs_slot;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    uint64_t graph_key = 0;
+    bool use_graphs = true;
     void* h_stage = nullptr;  // pinned staging for descriptors
     size_t h_stage_bytes = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -130,6 +137,7 @@ static int ensure(pv3d_ctx* c, DevBuf& b, size_t bytes)
 {
     if (bytes == 0) bytes = 16;
     if (b.bytes >= bytes) return PV3D_OK;
+    ++c->bufgen;
     if (b.p) cudaFree(b.p);
     b.p = nullptr;
     b.bytes = 0;
@@ -208,6 +216,7 @@ extern "C" int pv3d_create(pv3d_ctx** out, const pv3d_opts* opts)
     if (cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess)
         return PV3D_E_DEVICE;
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return PV3D_E_DEVICE;
+    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return PV3D_E_DEVICE;
     if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) return PV3D_E_DEVICE;
     if (o.hbm_budget_bytes == 0) {
         size_t fr = 0, tot = 0;
@@ -226,6 +235,10 @@ extern "C" void pv3d_destroy(pv3d_ctx* c)
     for (auto& kv : c->scenes)
         if (kv.second.d_tri) cudaFree(kv.second.d_tri);
     for (auto& kv : c->gens) free_gen(kv.second);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    release_buf(c->wave_slot);
+    release_buf(c->jobs_slot);
     DevBuf* bufs[] = {&c->lp, &c->win, &c->ms, &c->ms_p, &c->ms_pu, &c->ms_beam, &c->cs_cnt, &c->cs_bits, &c->t_far,
                       &c->t_cnt, &c->t_off, &c->t_cur, &c->t_slot, &c->t_rcnt, &c->t_roff, &c->t_rcur, &c->nonempty,
                       &c->bins, &c->recv, &c->map, &c->big,
@@ -697,10 +710,52 @@ static int stage_descriptors(pv3d_ctx* c, const std::vector<WaveDev>& waves, con
     return PV3D_OK;
 }
 
+// The wave sequence captured once as a CUDA graph; re-captured when a pool or
+// the launch configuration changes.
+static int wave_graph(pv3d_ctx* c, const LaunchCfg& cfg0, int max_jobs, cudaGraphExec_t* out)
+{
+    int rc;
+    if ((rc = ensure(c, c->wave_slot, sizeof(WaveDev))) ||
+        (rc = ensure(c, c->jobs_slot, (size_t)std::max(max_jobs, 1) * sizeof(JobDev))))
+        return rc;
+    const uint64_t key = (c->bufgen << 8) ^ ((uint64_t)cfg0.tile << 3) ^ ((uint64_t)cfg0.fused << 1) ^
+                         (uint64_t)cfg0.profile;
+    if (c->graph_exec && c->graph_key == key) {
+        *out = c->graph_exec;
+        return PV3D_OK;
+    }
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    c->graph_exec = nullptr;
+    LaunchCfg cfg = cfg0;
+    cfg.stream = c->cap_stream;
+    cfg.ev = nullptr;
+    CUDA_TRY(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t le = launch_wave((const WaveDev*)c->wave_slot.p, (const JobDev*)c->jobs_slot.p, buffers_of(c), cfg, 0);
+    cudaGraph_t g = nullptr;
+    cudaError_t ee = cudaStreamEndCapture(c->cap_stream, &g);
+    if (le != cudaSuccess || ee != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(c, PV3D_E_DEVICE, "wave graph capture failed: %s / %s", cudaGetErrorString(le),
+                    cudaGetErrorString(ee));
+    }
+    cudaError_t ie = cudaGraphInstantiate(&c->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+        c->graph_exec = nullptr;
+        return fail(c, PV3D_E_DEVICE, "wave graph instantiation failed: %s", cudaGetErrorString(ie));
+    }
+    c->graph_key = key;
+    *out = c->graph_exec;
+    return PV3D_OK;
+}
+
+// Run the planned waves: for each, copy its descriptors into the fixed slots
+// and replay the captured graph (or launch the kernels when stage events are
+// recorded).
 static int run_waves(pv3d_ctx* c, const std::vector<WaveDev>& waves, cudaStream_t st, int tile, bool fused,
                      bool profile, bool count)
 {
-    Buffers B = buffers_of(c);
     LaunchCfg cfg;
     cfg.sm_count = c->sm_count;
     cfg.tile = tile;
@@ -716,22 +771,33 @@ static int run_waves(pv3d_ctx* c, const std::vector<WaveDev>& waves, cudaStream_
             c->prof_ev.push_back(e);
         }
     }
-    const WaveDev* dW = (const WaveDev*)c->waves.p;
-    const JobDev* dJ = (const JobDev*)c->jobs.p;
+    int max_jobs = 1;
+    for (const WaveDev& W : waves) max_jobs = std::max(max_jobs, (int)W.n_jobs);
+    cudaGraphExec_t exec = nullptr;
+    int rc;
+    const bool graph = c->use_graphs && !profile;
+    if (graph) {
+        if ((rc = wave_graph(c, cfg, max_jobs, &exec))) return rc;
+    } else if ((rc = ensure(c, c->wave_slot, sizeof(WaveDev))) ||
+               (rc = ensure(c, c->jobs_slot, (size_t)max_jobs * sizeof(JobDev)))) {
+        return rc;
+    }
+    const Buffers B = buffers_of(c);
+    const char* dW = (const char*)c->waves.p;
+    const char* dJ = (const char*)c->jobs.p;
     size_t job0 = 0;
     for (size_t w = 0; w < waves.size(); ++w) {
         const WaveDev& W = waves[w];
-        CUDA_TRY(c, cudaMemsetAsync(c->win.p, 0xFF, (size_t)W.tot_js * 16, st));
-        CUDA_TRY(c, cudaMemsetAsync(c->t_far.p, 0, (size_t)W.tot_te * 4, st));
-        CUDA_TRY(c, cudaMemsetAsync(c->t_cnt.p, 0, (size_t)W.tot_te * 4, st));
-        CUDA_TRY(c, cudaMemsetAsync(c->t_rcnt.p, 0, (size_t)W.tot_te * 4, st));
-        CUDA_TRY(c, cudaMemsetAsync(c->ctr.p, 0, 3 * sizeof(unsigned int), st));
-        if (fused) {
-            CUDA_TRY(c, cudaMemsetAsync(c->cs_cnt.p, 0, (size_t)W.tot_cs * 4, st));
-            if (W.want_bits) CUDA_TRY(c, cudaMemsetAsync(c->cs_bits.p, 0, (size_t)W.tot_cs * 8, st));
+        CUDA_TRY(c, cudaMemcpyAsync(c->wave_slot.p, dW + w * sizeof(WaveDev), sizeof(WaveDev),
+                                    cudaMemcpyDeviceToDevice, st));
+        CUDA_TRY(c, cudaMemcpyAsync(c->jobs_slot.p, dJ + job0 * sizeof(JobDev), (size_t)W.n_jobs * sizeof(JobDev),
+                                    cudaMemcpyDeviceToDevice, st));
+        if (graph) {
+            CUDA_TRY(c, cudaGraphLaunch(exec, st));
+        } else {
+            if (profile) cfg.ev = &c->prof_ev[w * (kStages + 1)];
+            CUDA_TRY(c, launch_wave((const WaveDev*)c->wave_slot.p, (const JobDev*)c->jobs_slot.p, B, cfg, W.tot_te));
         }
-        if (profile) cfg.ev = &c->prof_ev[w * (kStages + 1)];
-        CUDA_TRY(c, launch_wave(dW + w, dJ + job0, B, cfg, W.tot_te));
         job0 += (size_t)W.n_jobs;
     }
     return PV3D_OK;

@@ -159,6 +159,34 @@ __device__ __forceinline__ void sample_texel(const ModStep& s, float a, float b,
 }
 
 // ---------------------------------------------------------------------------
+// k_clear: reset the wave's accumulators (sizes read from the wave descriptor,
+// so the whole wave can be replayed from one captured graph)
+// ---------------------------------------------------------------------------
+__global__ void k_clear(const WaveDev* __restrict__ W, Buffers B)
+{
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i0 == 0) {
+        B.ctr->n_big = 0u;
+        B.ctr->n_nonempty = 0u;
+        B.ctr->raster_next = 0u;
+    }
+    const int64_t nw = 4 * W->tot_js, nt = W->tot_te;
+    for (int64_t i = i0; i < nw; i += stride) B.win[i] = 0xFFFFFFFFu;
+    for (int64_t i = i0; i < nt; i += stride) {
+        B.t_far[i] = 0u;
+        B.t_cnt[i] = 0u;
+        B.t_rcnt[i] = 0u;
+    }
+    if (W->fused) {
+        const int64_t nc = W->tot_cs;
+        for (int64_t i = i0; i < nc; i += stride) B.cs_cnt[i] = 0u;
+        if (W->want_bits)
+            for (int64_t i = i0; i < nc; i += stride) B.cs_bits[i] = 0ull;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // k_window: projected bounding box of the generator per (job, step)
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(kWinPerItem) k_window(const WaveDev* __restrict__ W,
@@ -1516,6 +1544,7 @@ cudaError_t launch_wave(const WaveDev* d_wave, const JobDev* d_jobs, const Buffe
     const int sm = cfg.sm_count;
     (void)tot_te_host;
     if (cfg.ev) cudaEventRecord(cfg.ev[0], st);
+    k_clear<<<sm * 8, 256, 0, st>>>(W, b);
     k_window<<<sm * 8, kWinPerItem, 0, st>>>(W, d_jobs, b);
     k_light<<<sm, 128, 0, st>>>(W, d_jobs, b);
     k_modsetup<<<sm * 8, 256, 0, st>>>(W, d_jobs, b);

@@ -173,7 +173,7 @@ struct LaunchCfg {
 };
 
 constexpr int kStages = 5;           // setup, bin, raster(+test), pv/sample, epilogue
-constexpr int kLaunchesPerWave = 14;  // kernels launch_wave starts
+constexpr int kLaunchesPerWave = 15;  // kernels launch_wave starts
 
 cudaError_t launch_wave(const WaveDev* d_wave, const JobDev* d_jobs, const Buffers& b,
                         const LaunchCfg& cfg, int64_t tot_te_host);

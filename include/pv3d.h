@@ -169,6 +169,8 @@ typedef struct pv3d_result {
     int64_t nonempty_tiles;    /* rasterised (step, tile) pairs over the evaluation */
     int64_t binned_tris;       /* (triangle, tile) pairs binned over the evaluation */
     int64_t kernel_launches;   /* CUDA kernels launched by the evaluation */
+    float latency_ms;          /* served requests: submit to results ready (host clock) */
+    int32_t reserved1;
 } pv3d_result;
 
 /* ---- context ------------------------------------------------------------ */
@@ -245,10 +247,16 @@ int pv3d_evaluate(pv3d_ctx* ctx, uint32_t gen_id, const pv3d_eval_opts* opts, pv
 
 /*
  * Served evaluation: enqueue the request and return at once with *req.  The
- * context keeps scenes resident, admits requests by their device-memory
- * footprint against its budget and batches the work of every admitted request
- * into shared waves (continuous batching).  The scene, generator, sun table and
- * `out` must stay valid until the request completes.
+ * context keeps scenes resident and runs a worker thread: it admits queued
+ * requests in arrival order while fewer than max_inflight are active and their
+ * device-memory footprint (accumulators, host-output staging and their share of
+ * the wave scratch) fits the budget, and every wave takes the next chunk of sun
+ * steps of every active request (continuous batching: a request that arrives
+ * while others run joins the next wave).  Results are bit-identical to
+ * pv3d_evaluate of the same request.  PV3D_E_ADMISSION if the request alone
+ * exceeds the budget.  The scene, generator and `out` must stay valid until
+ * the request completes; pv3d_release refuses ids that queued or active
+ * requests use.  Served requests use the fused path.
  */
 int pv3d_submit(pv3d_ctx* ctx, uint32_t gen_id, const pv3d_eval_opts* opts, pv3d_result* out,
                 uint64_t* req);
@@ -259,6 +267,15 @@ int pv3d_submit(pv3d_ctx* ctx, uint32_t gen_id, const pv3d_eval_opts* opts, pv3d
  * PV3D_E_PENDING if still running, another status on failure.
  */
 int pv3d_poll(pv3d_ctx* ctx, uint64_t req, int32_t timeout_ms);
+
+/*
+ * Evaluate n generators together: every request is submitted to the served
+ * engine (its sun steps batched with the others' into shared waves) and the
+ * call returns when all are done.  Returns the first failing status, or
+ * PV3D_OK.  opts may be NULL (defaults for all).
+ */
+int pv3d_evaluate_batch(pv3d_ctx* ctx, int32_t n, const uint32_t* gen_ids, const pv3d_eval_opts* opts,
+                        pv3d_result* outs);
 
 /* Profile of the last profiled evaluation on `ctx` (PV3D_E_NOTFOUND if none). */
 int pv3d_last_profile(pv3d_ctx* ctx, pv3d_profile* out);

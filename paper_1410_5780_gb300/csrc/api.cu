@@ -3,12 +3,14 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <condition_variable>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
 #include <deque>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -95,18 +97,22 @@ struct pv3d_ctx {
     std::vector<cudaEvent_t> prof_ev;  // stage-boundary events, kStages + 1 per wave
     pv3d_profile last_prof{};
     bool have_prof = false;
-    // served requests
+    // served requests: a worker thread runs waves built from every admitted
+    // request (continuous batching); admission by device-memory footprint
     struct Request;
+    std::mutex gpu_mu;  // one wave or plain evaluation at a time on the workspace
+    std::mutex mu;      // request tables
+    std::condition_variable cv_work, cv_done;
+    std::thread worker;
+    bool stop = false;
     std::map<uint64_t, std::unique_ptr<Request>> reqs;
-    std::deque<uint64_t> queue;
+    std::deque<uint64_t> pending;
+    std::vector<uint64_t> active;
+    size_t rr = 0;              // round-robin start of the next wave
+    int64_t reserved = 0;       // footprint of admitted requests
     uint64_t next_req = 1;
-};
-
-struct pv3d_ctx::Request {
-    uint32_t gen_id;
-    pv3d_eval_opts opts;
-    pv3d_result* out;
-    int status = PV3D_E_PENDING;
+    std::vector<DevBuf> free_bufs;  // request buffers for reuse
+    cudaStream_t serve_stream = nullptr;
 };
 
 // ---------------------------------------------------------------------------
@@ -225,31 +231,6 @@ extern "C" int pv3d_create(pv3d_ctx** out, const pv3d_opts* opts)
     }
     *out = c.release();
     return PV3D_OK;
-}
-
-extern "C" void pv3d_destroy(pv3d_ctx* c)
-{
-    if (!c) return;
-    cudaSetDevice(c->device);
-    if (c->stream) cudaStreamSynchronize(c->stream);
-    for (auto& kv : c->scenes)
-        if (kv.second.d_tri) cudaFree(kv.second.d_tri);
-    for (auto& kv : c->gens) free_gen(kv.second);
-    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
-    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-    release_buf(c->wave_slot);
-    release_buf(c->jobs_slot);
-    DevBuf* bufs[] = {&c->lp, &c->win, &c->ms, &c->ms_p, &c->ms_pu, &c->ms_beam, &c->cs_cnt, &c->cs_bits, &c->t_far,
-                      &c->t_cnt, &c->t_off, &c->t_cur, &c->t_slot, &c->t_rcnt, &c->t_roff, &c->t_rcur, &c->nonempty,
-                      &c->bins, &c->recv, &c->map, &c->big,
-                      &c->block_sums, &c->ctr, &c->waves, &c->jobs, &c->kahan_mod, &c->kahan_cell, &c->staging};
-    for (DevBuf* b : bufs) release_buf(*b);
-    if (c->h_stage) cudaFreeHost(c->h_stage);
-    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
-    if (c->ev0) cudaEventDestroy(c->ev0);
-    if (c->ev1) cudaEventDestroy(c->ev1);
-    if (c->stream) cudaStreamDestroy(c->stream);
-    delete c;
 }
 
 extern "C" const char* pv3d_last_error(pv3d_ctx* c) { return c ? c->err.c_str() : "null context"; }
@@ -950,23 +931,337 @@ extern "C" int pv3d_last_profile(pv3d_ctx* c, pv3d_profile* out)
 
 extern "C" int pv3d_evaluate(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o, pv3d_result* out)
 {
+    if (!c) return PV3D_E_INVALID;
+    std::lock_guard<std::mutex> g(c->gpu_mu);
     return evaluate_plain(c, gen_id, o, out);
 }
 
 // ---------------------------------------------------------------------------
 // served requests (queue; executed in arrival order on poll)
 // ---------------------------------------------------------------------------
+// ---------------------------------------------------------------------------
+// served requests: continuous batching over waves
+// ---------------------------------------------------------------------------
+struct pv3d_ctx::Request {
+    uint64_t id = 0;
+    uint32_t gen_id = 0;
+    pv3d_eval_opts opts{};
+    pv3d_result* out = nullptr;
+    EvalSetup es{};
+    int status = PV3D_E_PENDING;
+    int64_t next = 0;          // next sun step to evaluate
+    DevBuf kmod, kcell, stage; // Kahan pairs and the staging of host outputs
+    double* d_e = nullptr;
+    double* d_eu = nullptr;
+    double* d_cl = nullptr;
+    float* d_p = nullptr;
+    float* d_pu = nullptr;
+    uint8_t* d_cnt = nullptr;
+    unsigned long long* d_bits = nullptr;
+    int64_t footprint = 0;
+    int64_t waves = 0;
+    float device_ms = 0.f;
+    bool admitted = false;
+    std::chrono::steady_clock::time_point t_submit, t_done;
+};
+
+static int64_t per_step_scratch(const GenH& g, const EvalSetup& es)
+{
+    const int64_t tiles = (int64_t)(es.R / es.tile) * (es.R / es.tile);
+    return tiles * 4 * 9 + (int64_t)g.C * 12 + (int64_t)g.M * (sizeof(ModStep) + 12) + sizeof(LightParams) + 16;
+}
+
+static int64_t request_bytes(const GenH& g, const EvalSetup& es, const pv3d_result* out, int64_t S)
+{
+    int64_t b = (int64_t)g.M * 16 + (int64_t)g.C * 8;
+    if (!out->is_device) {
+        if (out->energy) b += g.M * 8;
+        if (out->energy_unshaded) b += g.M * 8;
+        if (out->cell_beam_loss) b += (int64_t)g.C * 8;
+        if (out->power) b += S * g.M * 4;
+        if (out->power_unshaded) b += S * g.M * 4;
+        if (out->cell_counts) b += S * g.C;
+        if (out->sample_bits) b += S * g.C * 8;
+    }
+    return b;
+}
+
+static int64_t resident_bytes(pv3d_ctx* c)
+{
+    int64_t b = 0;
+    for (auto& kv : c->scenes) b += (int64_t)kv.second.bytes;
+    for (auto& kv : c->gens) b += (int64_t)kv.second.bytes + kv.second.n_steps * 36;
+    return b;
+}
+
+// Take a device buffer of at least `bytes` from the free list (or allocate).
+static int take_buf(pv3d_ctx* c, DevBuf& dst, size_t bytes)
+{
+    bytes = std::max<size_t>(bytes, 16);
+    size_t best = (size_t)-1;
+    for (size_t k = 0; k < c->free_bufs.size(); ++k)
+        if (c->free_bufs[k].bytes >= bytes && (best == (size_t)-1 || c->free_bufs[k].bytes < c->free_bufs[best].bytes))
+            best = k;
+    if (best != (size_t)-1) {
+        dst = c->free_bufs[best];
+        c->free_bufs.erase(c->free_bufs.begin() + best);
+        return PV3D_OK;
+    }
+    DevBuf b;
+    if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(c, PV3D_E_NOMEM, "request buffer allocation failed");
+    }
+    b.bytes = bytes;
+    dst = b;
+    return PV3D_OK;
+}
+
+static void give_buf(pv3d_ctx* c, DevBuf& b)
+{
+    if (b.p) c->free_bufs.push_back(b);
+    b = DevBuf{};
+}
+
+// Allocate the request's buffers and point its outputs (worker thread, mu held).
+static int admit(pv3d_ctx* c, pv3d_ctx::Request& r)
+{
+    const GenH& g = c->gens.at(r.gen_id);
+    const int64_t S = r.es.e - r.es.b;
+    int rc;
+    if ((rc = take_buf(c, r.kmod, (size_t)g.M * 2 * sizeof(float2))) ||
+        (rc = take_buf(c, r.kcell, (size_t)g.C * sizeof(float2))))
+        return rc;
+    pv3d_result* out = r.out;
+    if (out->is_device) {
+        r.d_e = out->energy; r.d_eu = out->energy_unshaded; r.d_cl = out->cell_beam_loss;
+        r.d_p = out->power; r.d_pu = out->power_unshaded; r.d_cnt = out->cell_counts;
+        r.d_bits = (unsigned long long*)out->sample_bits;
+    } else {
+        size_t off = 0;
+        auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~size_t(255); return o; };
+        size_t oe = out->energy ? take(g.M * 8) : 0, oeu = out->energy_unshaded ? take(g.M * 8) : 0;
+        size_t ocl = out->cell_beam_loss ? take((size_t)g.C * 8) : 0;
+        size_t op = out->power ? take((size_t)S * g.M * 4) : 0, opu = out->power_unshaded ? take((size_t)S * g.M * 4) : 0;
+        size_t oc = out->cell_counts ? take((size_t)S * g.C) : 0, ob = out->sample_bits ? take((size_t)S * g.C * 8) : 0;
+        if ((rc = take_buf(c, r.stage, off))) return rc;
+        char* b = (char*)r.stage.p;
+        r.d_e = out->energy ? (double*)(b + oe) : nullptr;
+        r.d_eu = out->energy_unshaded ? (double*)(b + oeu) : nullptr;
+        r.d_cl = out->cell_beam_loss ? (double*)(b + ocl) : nullptr;
+        r.d_p = out->power ? (float*)(b + op) : nullptr;
+        r.d_pu = out->power_unshaded ? (float*)(b + opu) : nullptr;
+        r.d_cnt = out->cell_counts ? (uint8_t*)(b + oc) : nullptr;
+        r.d_bits = out->sample_bits ? (unsigned long long*)(b + ob) : nullptr;
+    }
+    CUDA_TRY(c, cudaMemsetAsync(r.kmod.p, 0, (size_t)g.M * 2 * sizeof(float2), c->serve_stream));
+    CUDA_TRY(c, cudaMemsetAsync(r.kcell.p, 0, (size_t)g.C * sizeof(float2), c->serve_stream));
+    r.next = r.es.b;
+    r.admitted = true;
+    return PV3D_OK;
+}
+
+// Finish a request: Kahan pairs to its outputs, host copies (worker thread).
+static int finish(pv3d_ctx* c, pv3d_ctx::Request& r)
+{
+    const GenH& g = c->gens.at(r.gen_id);
+    const int64_t S = r.es.e - r.es.b;
+    cudaStream_t st = c->serve_stream;
+    CUDA_TRY(c, launch_finalize_pairs((const float2*)r.kmod.p, g.M, (const float2*)r.kcell.p, g.C, r.d_e, r.d_eu,
+                                      r.d_cl, st));
+    pv3d_result* out = r.out;
+    if (!out->is_device) {
+        auto cp = [&](void* dst, const void* src, size_t bytes) {
+            return dst ? cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, st) : cudaSuccess;
+        };
+        CUDA_TRY(c, cp(out->energy, r.d_e, g.M * 8));
+        CUDA_TRY(c, cp(out->energy_unshaded, r.d_eu, g.M * 8));
+        CUDA_TRY(c, cp(out->cell_beam_loss, r.d_cl, (size_t)g.C * 8));
+        CUDA_TRY(c, cp(out->power, r.d_p, (size_t)S * g.M * 4));
+        CUDA_TRY(c, cp(out->power_unshaded, r.d_pu, (size_t)S * g.M * 4));
+        CUDA_TRY(c, cp(out->cell_counts, r.d_cnt, (size_t)S * g.C));
+        CUDA_TRY(c, cp(out->sample_bits, r.d_bits, (size_t)S * g.C * 8));
+    }
+    CUDA_TRY(c, cudaStreamSynchronize(st));
+    int64_t lit = 0;
+    for (int64_t k = r.es.b; k < r.es.e; ++k) lit += g.lit[k];
+    out->steps_lit = lit;
+    out->tests = lit * (int64_t)g.C * r.es.n * r.es.n;
+    out->device_ms = r.device_ms;
+    out->waves = (int32_t)r.waves;
+    out->kernel_launches = r.waves * kLaunchesPerWave + 1;
+    r.t_done = std::chrono::steady_clock::now();
+    out->latency_ms = (float)std::chrono::duration<double, std::milli>(r.t_done - r.t_submit).count();
+    return PV3D_OK;
+}
+
+static void release_request_bufs(pv3d_ctx* c, pv3d_ctx::Request& r)
+{
+    give_buf(c, r.kmod);
+    give_buf(c, r.kcell);
+    give_buf(c, r.stage);
+}
+
+// One wave over the active requests; returns the requests it advanced.
+static int serve_wave(pv3d_ctx* c, std::unique_lock<std::mutex>& lk)
+{
+    // admission: FIFO while slots and device memory allow
+    const int64_t budget = c->opts.hbm_budget_bytes - resident_bytes(c);
+    while (!c->pending.empty() && (int)c->active.size() < c->opts.max_inflight) {
+        pv3d_ctx::Request& r = *c->reqs.at(c->pending.front());
+        if (!c->active.empty() && c->reserved + r.footprint > budget) break;
+        c->pending.pop_front();
+        int rc = admit(c, r);
+        if (rc) {
+            r.status = rc;
+            release_request_bufs(c, r);
+            c->cv_done.notify_all();
+            continue;
+        }
+        c->reserved += r.footprint;
+        c->active.push_back(r.id);
+    }
+    if (c->active.empty()) return 0;
+    // wave: the next chunk of every active request, within the scratch limits
+    const int64_t scratch_cap = std::max<int64_t>(budget / 4, (int64_t)1 << 28);
+    std::vector<JobDev> jobs;
+    std::vector<pv3d_ctx::Request*> in_wave;
+    std::vector<int> ks;
+    int64_t scratch = 0;
+    bool want_bits = false;
+    const size_t na = c->active.size();
+    for (size_t q = 0; q < na; ++q) {
+        pv3d_ctx::Request& r = *c->reqs.at(c->active[(c->rr + q) % na]);
+        const GenH& g = c->gens.at(r.gen_id);
+        const SceneH& sc = c->scenes.at(g.scene_id);
+        const int k = (int)std::min<int64_t>(r.es.K, r.es.e - r.next);
+        const int64_t need = per_step_scratch(g, r.es) * k;
+        if (!jobs.empty() && scratch + need > scratch_cap) break;
+        scratch += need;
+        jobs.push_back(make_job(c, g, sc, r.es, r.next, k, (float2*)r.kmod.p, (float2*)r.kcell.p, r.d_p, r.d_pu,
+                                r.d_cnt, r.d_bits));
+        in_wave.push_back(&r);
+        ks.push_back(k);
+        want_bits = want_bits || r.d_bits;
+    }
+    c->rr = (c->rr + jobs.size()) % std::max<size_t>(na, 1);
+    lk.unlock();
+    std::vector<WaveDev> waves{pack_wave(jobs, 0, jobs.size(), c->opts.tile == 32 ? 5 : 6,
+                                         c->opts.depth_format == PV3D_DEPTH_U24, 1, 0)};
+    WaveDev& W = waves[0];
+    Counters hc{};
+    int rc = PV3D_OK;
+    float ms = 0.f;
+    {
+        std::lock_guard<std::mutex> g(c->gpu_mu);
+        cudaSetDevice(c->device);
+        cudaStream_t st = c->serve_stream;
+        rc = ensure_workspace(c, W.tot_js, W.tot_te, W.tot_ms, W.tot_cs, c->opts.tile, true, want_bits);
+        if (!rc) {
+            W.bin_cap = c->bin_cap; W.map_cap_tiles = c->map_cap_tiles;
+            W.big_cap = c->big_cap; W.recv_cap = c->recv_cap;
+            rc = stage_descriptors(c, waves, jobs, st);
+        }
+        if (!rc && cudaMemsetAsync(c->ctr.p, 0, sizeof(Counters), st) != cudaSuccess) rc = PV3D_E_DEVICE;
+        if (!rc && cudaEventRecord(c->ev0, st) != cudaSuccess) rc = PV3D_E_DEVICE;
+        if (!rc) rc = run_waves(c, waves, st, c->opts.tile, true, false, false);
+        if (!rc && cudaEventRecord(c->ev1, st) != cudaSuccess) rc = PV3D_E_DEVICE;
+        if (!rc && cudaMemcpyAsync(&hc, c->ctr.p, sizeof(Counters), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            rc = PV3D_E_DEVICE;
+        if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = PV3D_E_DEVICE;
+        if (!rc) cudaEventElapsedTime(&ms, c->ev0, c->ev1);
+        if (!rc && hc.overflow) {
+            // grow the pools and restart the requests of this wave from their first step
+            if (hc.overflow & 1u) c->bin_cap = (int64_t)(hc.need_bins * 5 / 4 + 1024);
+            if (hc.overflow & 4u) c->big_cap = (int64_t)(hc.need_big * 5 / 4 + 1024);
+            if (hc.overflow & 8u) c->recv_cap = (int64_t)(hc.need_recv * 5 / 4 + 1024);
+            for (auto* r : in_wave) {
+                const GenH& g = c->gens.at(r->gen_id);
+                cudaMemsetAsync(r->kmod.p, 0, (size_t)g.M * 2 * sizeof(float2), st);
+                cudaMemsetAsync(r->kcell.p, 0, (size_t)g.C * sizeof(float2), st);
+            }
+            cudaStreamSynchronize(st);
+        }
+    }
+    lk.lock();
+    if (rc) {
+        for (auto* r : in_wave) r->status = rc;
+    } else {
+        for (size_t q = 0; q < in_wave.size(); ++q) {
+            pv3d_ctx::Request& r = *in_wave[q];
+            if (hc.overflow) {
+                r.next = r.es.b;
+                continue;
+            }
+            r.next += ks[q];
+            r.waves += 1;
+            r.device_ms += ms;
+            if (r.next >= r.es.e) {
+                std::lock_guard<std::mutex> g(c->gpu_mu);
+                r.status = finish(c, r);
+            }
+        }
+    }
+    // retire finished or failed requests
+    for (auto it = c->active.begin(); it != c->active.end();) {
+        pv3d_ctx::Request& r = *c->reqs.at(*it);
+        if (r.status != PV3D_E_PENDING) {
+            c->reserved -= r.footprint;
+            release_request_bufs(c, r);
+            it = c->active.erase(it);
+        } else {
+            ++it;
+        }
+    }
+    c->cv_done.notify_all();
+    return (int)in_wave.size();
+}
+
+static void serve_loop(pv3d_ctx* c)
+{
+    cudaSetDevice(c->device);
+    std::unique_lock<std::mutex> lk(c->mu);
+    while (!c->stop) {
+        if (c->pending.empty() && c->active.empty()) {
+            c->cv_work.wait(lk);
+            continue;
+        }
+        serve_wave(c, lk);
+    }
+}
+
 extern "C" int pv3d_submit(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o, pv3d_result* out, uint64_t* req)
 {
     if (!c || !out || !req) return PV3D_E_INVALID;
-    if (c->gens.find(gen_id) == c->gens.end()) return fail(c, PV3D_E_NOTFOUND, "unknown generator %u", gen_id);
+    std::unique_lock<std::mutex> lk(c->mu);
+    auto git = c->gens.find(gen_id);
+    if (git == c->gens.end()) return fail(c, PV3D_E_NOTFOUND, "unknown generator %u", gen_id);
+    const GenH& g = git->second;
+    if (c->scenes.find(g.scene_id) == c->scenes.end()) return fail(c, PV3D_E_NOTFOUND, "scene is gone");
     std::unique_ptr<pv3d_ctx::Request> r(new pv3d_ctx::Request());
+    int rc = check_eval(c, g, o, out, r->es);
+    if (rc) return rc;
+    if (o && o->path == PV3D_PATH_MAP) return fail(c, PV3D_E_INVALID, "served requests use the fused path");
     r->gen_id = gen_id;
     r->opts = o ? *o : pv3d_eval_opts{};
     r->out = out;
-    uint64_t id = c->next_req++;
+    const int64_t S = r->es.e - r->es.b;
+    r->footprint = request_bytes(g, r->es, out, S) + per_step_scratch(g, r->es) * r->es.K;
+    if (r->footprint > c->opts.hbm_budget_bytes - resident_bytes(c))
+        return fail(c, PV3D_E_ADMISSION, "request needs %lld bytes, budget leaves %lld", (long long)r->footprint,
+                    (long long)(c->opts.hbm_budget_bytes - resident_bytes(c)));
+    r->t_submit = std::chrono::steady_clock::now();
+    const uint64_t id = c->next_req++;
+    r->id = id;
     c->reqs[id] = std::move(r);
-    c->queue.push_back(id);
+    c->pending.push_back(id);
+    if (!c->worker.joinable()) {
+        if (!c->serve_stream && cudaStreamCreateWithFlags(&c->serve_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return fail(c, PV3D_E_DEVICE, "stream creation failed");
+        c->stop = false;
+        c->worker = std::thread(serve_loop, c);
+    }
+    c->cv_work.notify_one();
     *req = id;
     return PV3D_OK;
 }
@@ -974,23 +1269,51 @@ extern "C" int pv3d_submit(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o
 extern "C" int pv3d_poll(pv3d_ctx* c, uint64_t req, int32_t timeout_ms)
 {
     if (!c) return PV3D_E_INVALID;
+    std::unique_lock<std::mutex> lk(c->mu);
     auto it = c->reqs.find(req);
     if (it == c->reqs.end()) return fail(c, PV3D_E_NOTFOUND, "unknown request %llu", (unsigned long long)req);
-    (void)timeout_ms;
-    while (it->second->status == PV3D_E_PENDING && !c->queue.empty()) {
-        uint64_t id = c->queue.front();
-        c->queue.pop_front();
-        auto& r = c->reqs[id];
-        r->status = evaluate_plain(c, r->gen_id, &r->opts, r->out);
+    pv3d_ctx::Request* r = it->second.get();
+    if (r->status == PV3D_E_PENDING && timeout_ms != 0) {
+        auto pred = [&] { return r->status != PV3D_E_PENDING; };
+        if (timeout_ms < 0) c->cv_done.wait(lk, pred);
+        else c->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms), pred);
     }
-    int s = it->second->status;
+    const int s = r->status;
     if (s != PV3D_E_PENDING) c->reqs.erase(it);
     return s;
+}
+
+extern "C" int pv3d_evaluate_batch(pv3d_ctx* c, int32_t n, const uint32_t* gen_ids, const pv3d_eval_opts* opts,
+                                   pv3d_result* outs)
+{
+    if (!c || n < 0 || (n > 0 && (!gen_ids || !outs))) return PV3D_E_INVALID;
+    std::vector<uint64_t> ids((size_t)n, 0);
+    int first = PV3D_OK;
+    for (int32_t k = 0; k < n; ++k) {
+        int rc = pv3d_submit(c, gen_ids[k], opts ? &opts[k] : nullptr, &outs[k], &ids[k]);
+        if (rc && first == PV3D_OK) first = rc;
+    }
+    for (int32_t k = 0; k < n; ++k) {
+        if (!ids[k]) continue;
+        int rc = pv3d_poll(c, ids[k], -1);
+        if (rc && first == PV3D_OK) first = rc;
+    }
+    return first;
 }
 
 extern "C" int pv3d_release(pv3d_ctx* c, uint32_t id)
 {
     if (!c) return PV3D_E_INVALID;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        for (auto& kv : c->reqs) {
+            const uint32_t gid = kv.second->gen_id;
+            auto git = c->gens.find(gid);
+            if (gid == id || (git != c->gens.end() && git->second.scene_id == id))
+                return fail(c, PV3D_E_INVALID, "id %u is used by request %llu", id, (unsigned long long)kv.first);
+        }
+    }
+    std::lock_guard<std::mutex> gl(c->gpu_mu);
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
     auto git = c->gens.find(id);
@@ -1012,4 +1335,38 @@ extern "C" int pv3d_release(pv3d_ctx* c, uint32_t id)
     if (sit->second.d_tri) cudaFree(sit->second.d_tri);
     c->scenes.erase(sit);
     return PV3D_OK;
+}
+
+extern "C" void pv3d_destroy(pv3d_ctx* c)
+{
+    if (!c) return;
+    {
+        std::lock_guard<std::mutex> lk(c->mu);
+        c->stop = true;
+    }
+    c->cv_work.notify_all();
+    if (c->worker.joinable()) c->worker.join();
+    cudaSetDevice(c->device);
+    for (auto& kv : c->reqs) release_request_bufs(c, *kv.second);
+    for (DevBuf& b : c->free_bufs) release_buf(b);
+    if (c->serve_stream) cudaStreamDestroy(c->serve_stream);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (auto& kv : c->scenes)
+        if (kv.second.d_tri) cudaFree(kv.second.d_tri);
+    for (auto& kv : c->gens) free_gen(kv.second);
+    if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    release_buf(c->wave_slot);
+    release_buf(c->jobs_slot);
+    DevBuf* bufs[] = {&c->lp, &c->win, &c->ms, &c->ms_p, &c->ms_pu, &c->ms_beam, &c->cs_cnt, &c->cs_bits, &c->t_far,
+                      &c->t_cnt, &c->t_off, &c->t_cur, &c->t_slot, &c->t_rcnt, &c->t_roff, &c->t_rcur, &c->nonempty,
+                      &c->bins, &c->recv, &c->map, &c->big,
+                      &c->block_sums, &c->ctr, &c->waves, &c->jobs, &c->kahan_mod, &c->kahan_cell, &c->staging};
+    for (DevBuf* b : bufs) release_buf(*b);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
 }

@@ -35,7 +35,7 @@ PV3D_PATH_MAP = 1
 
 EXPORTED = ("pv3d_create", "pv3d_destroy", "pv3d_last_error", "pv3d_scene_load", "pv3d_generator_define",
             "pv3d_set_poses", "pv3d_set_sun", "pv3d_evaluate", "pv3d_submit", "pv3d_poll", "pv3d_release",
-            "pv3d_last_profile", "pv3d_module_shade_noalloc")
+            "pv3d_last_profile", "pv3d_module_shade_noalloc", "pv3d_evaluate_batch")
 
 
 class pv3d_opts(C.Structure):
@@ -82,7 +82,8 @@ class pv3d_result(C.Structure):
                 ("power_unshaded", C.c_void_p), ("cell_beam_loss", C.c_void_p), ("cell_counts", C.c_void_p),
                 ("sample_bits", C.c_void_p), ("tests", C.c_int64), ("steps_lit", C.c_int64),
                 ("device_ms", C.c_float), ("waves", C.c_int32), ("nonempty_tiles", C.c_int64),
-                ("binned_tris", C.c_int64), ("kernel_launches", C.c_int64)]
+                ("binned_tris", C.c_int64), ("kernel_launches", C.c_int64), ("latency_ms", C.c_float),
+                ("reserved1", C.c_int32)]
 
 
 _lib = None
@@ -123,6 +124,7 @@ def load(build_if_missing: bool = False):
         lib.pv3d_poll.argtypes = [P, C.c_uint64, C.c_int32]
         lib.pv3d_release.argtypes = [P, C.c_uint32]
         lib.pv3d_last_profile.argtypes = [P, C.POINTER(pv3d_profile)]
+        lib.pv3d_evaluate_batch.argtypes = [P, C.c_int32, P, C.POINTER(pv3d_eval_opts), C.POINTER(pv3d_result)]
         lib.pv3d_module_shade_noalloc.argtypes = [P, C.c_int64, C.POINTER(pv3d_module), P, C.c_int32, C.c_int32,
                                                   P, P]
         for name in EXPORTED:
@@ -297,7 +299,7 @@ class Context:
         """pv3d_submit.  Returns (request id, outputs dict); the outputs are
         valid once pv3d_poll returns PV3D_OK for the request."""
         res, arrays = self._alloc(gen_id, step_begin, step_end, outputs, device)
-        o = self._opts(n, map_res, step_begin, step_end, chunk_steps, stream, 0.0, 0.0, 0.0)
+        o = self._opts(n, map_res, step_begin, step_end, chunk_steps, None, 0.0, 0.0, 0.0)
         rid = C.c_uint64()
         self._check(self.lib.pv3d_submit(self.h, gen_id, C.byref(o), C.byref(res), C.byref(rid)))
         self._keep[rid.value] = (res, o, arrays)
@@ -308,8 +310,29 @@ class Context:
         self._check(rc)
         if rc == PV3D_OK:
             res, _, arrays = self._keep.pop(req)
-            arrays.update(tests=res.tests, steps_lit=res.steps_lit, device_ms=res.device_ms, waves=res.waves)
+            arrays.update(tests=res.tests, steps_lit=res.steps_lit, device_ms=res.device_ms, waves=res.waves,
+                          latency_ms=res.latency_ms)
+        elif rc != PV3D_E_PENDING:
+            self._keep.pop(req, None)
         return rc
+
+    def evaluate_batch(self, gen_ids, n=3, map_res=0, chunk_steps=0, outputs=("energy", "energy_unshaded"),
+                       device: bool = True) -> list:
+        """pv3d_evaluate_batch over ``gen_ids`` with one option set."""
+        k = len(gen_ids)
+        ids = (C.c_uint32 * k)(*gen_ids)
+        opts = (pv3d_eval_opts * k)()
+        results = (pv3d_result * k)()
+        keep = []
+        for q, gid in enumerate(gen_ids):
+            opts[q] = self._opts(n, map_res, 0, 0, chunk_steps, None, 0.0, 0.0, 0.0)
+            res, arrays = self._alloc(gid, 0, 0, outputs, device)
+            results[q] = res
+            keep.append(arrays)
+        self._check(self.lib.pv3d_evaluate_batch(self.h, k, ids, opts, results))
+        for q in range(k):
+            keep[q].update(tests=results[q].tests, latency_ms=results[q].latency_ms, waves=results[q].waves)
+        return keep
 
     def release(self, scene_or_gen_id: int):
         self._check(self.lib.pv3d_release(self.h, scene_or_gen_id))

@@ -55,6 +55,9 @@ def parse():
     ap.add_argument("--chunk", type=int, default=0, help="sun steps per wave (0 = library default)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true", help="skip the batched and served sections")
+    ap.add_argument("--batch-scenes", type=int, default=256)
+    ap.add_argument("--requests", type=int, default=200)
     return ap.parse_args()
 
 
@@ -189,6 +192,103 @@ def input_bytes(w) -> int:
     return int(b)
 
 
+def _batched_vs_plain(dev: int, ws) -> dict:
+    import torch
+    from paper_1410_5780_gb300 import pv3d
+    tests = sum(w.n_tests() for w in ws)
+    with pv3d.Context(device=dev, wave_scratch_mb=128) as ctx:
+        gids = [pv3d.load_workload(ctx, w) for w in ws]
+        ns = [w.n for w in ws]
+        rs = [w.map_res for w in ws]
+        ctx.evaluate_batch(gids[:8], n=ns[:8], map_res=rs[:8])  # warm-up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plain = [ctx.evaluate(g, n=w.n, map_res=w.map_res) for w, g in zip(ws, gids)]
+        torch.cuda.synchronize()
+        t_plain = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        batch = ctx.evaluate_batch(gids, n=ns, map_res=rs)
+        torch.cuda.synchronize()
+        t_batch = time.perf_counter() - t0
+        same = all(bool(torch.equal(a["energy"], b["energy"])) for a, b in zip(plain, batch))
+    return {"tests": int(tests), "plain_tests_per_s": tests / t_plain, "batched_tests_per_s": tests / t_batch,
+            "speedup": t_plain / t_batch, "batched_equals_plain": same}
+
+
+def batched_section(dev: int, n_scenes: int) -> dict:
+    """configs[3]: scenes of uneven size (log-uniform triangles and modules,
+    latitudes 0-60 deg, 100-4400 sun steps): the plain per-scene loop against
+    one batched call (all scenes' sun steps packed into shared waves); also a
+    mix of small scenes, where one scene alone does not fill the GPU."""
+    from paper_1410_5780_gb300 import scenes as S
+    mix = _batched_vs_plain(dev, S.make_batch(seed=4, n_scenes=n_scenes))
+    mix["workload"] = (f"{n_scenes} scenes: triangles log-uniform 1e3-2e5, modules log-uniform 10-2000, "
+                       "latitude U(0,60), 100-4400 hourly sun steps, 4x4 samples, map 512-4096 (configs[3])")
+    small = _batched_vs_plain(dev, S.make_batch(seed=6, n_scenes=n_scenes, tris=(1e3, 2e4), mods=(10, 100),
+                                                steps=(100, 400)))
+    small["workload"] = f"{n_scenes} small scenes: 1e3-2e4 triangles, 10-100 modules, 100-400 sun steps"
+    mix["small_scenes"] = small
+    mix["clock"] = "host wall clock"
+    return mix
+
+
+def serving_section(dev: int, n_requests: int) -> dict:
+    """configs[4] on a bounded sample: requests over a pool of resident scenes
+    (1e3-5.2e5 triangles), each a random range of 100-4400 sun steps.  The
+    served capacity is measured first (all requests submitted at once), then
+    Poisson arrivals at 80 % of it; p50/p99 of submit-to-result latency."""
+    import torch
+    from paper_1410_5780_gb300 import pv3d, scenes as S
+    rng = np.random.default_rng(11)
+    pool = S.make_batch(seed=5, n_scenes=24, tris=(1e3, 5.2e5))
+    with pv3d.Context(device=dev, hbm_budget_bytes=120 << 30, wave_scratch_mb=128) as ctx:
+        gids = [pv3d.load_workload(ctx, w) for w in pool]
+        reqs = []
+        for _ in range(n_requests):
+            q = int(rng.integers(len(pool)))
+            w = pool[q]
+            k = int(rng.integers(min(100, w.sun.n_steps), w.sun.n_steps + 1))
+            b = int(rng.integers(0, w.sun.n_steps - k + 1))
+            reqs.append((q, b, b + k, k * w.samples_per_step))
+
+        def submit(q, b, e):
+            w = pool[q]
+            return ctx.submit(gids[q], n=w.n, map_res=w.map_res, step_begin=b, step_end=e)
+
+        # capacity: every request at once
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ids = [submit(q, b, e)[0] for q, b, e, _ in reqs]
+        for rid in ids:
+            assert ctx.poll(rid, timeout_ms=-1) == pv3d.PV3D_OK
+        t_cap = time.perf_counter() - t0
+        total_tests = sum(r[3] for r in reqs)
+        capacity_rps = n_requests / t_cap
+        rate = 0.8 * capacity_rps
+        gaps = rng.exponential(1.0 / rate, n_requests)
+        t0 = time.perf_counter()
+        t_arr = t0 + np.cumsum(gaps)
+        live, lat = {}, []
+        for i, (q, b, e, nt) in enumerate(reqs):
+            while time.perf_counter() < t_arr[i]:
+                for rid in list(live):
+                    if ctx.poll(rid, timeout_ms=0) == pv3d.PV3D_OK:
+                        lat.append(live.pop(rid)["latency_ms"])
+                time.sleep(0.0002)
+            rid, arrays = submit(q, b, e)
+            live[rid] = arrays
+        for rid in list(live):
+            assert ctx.poll(rid, timeout_ms=-1) == pv3d.PV3D_OK
+            lat.append(live.pop(rid)["latency_ms"])
+        span = time.perf_counter() - t0
+    return {"workload": f"{n_requests} requests over {len(pool)} resident scenes (1e3-5.2e5 triangles), 100-4400 "
+                        "sun steps each (bounded sample of configs[4]); Poisson arrivals at 80% of the measured "
+                        "served capacity",
+            "capacity_tests_per_s": total_tests / t_cap, "capacity_requests_per_s": capacity_rps,
+            "arrival_rate_per_s": rate, "p50_ms": float(np.percentile(lat, 50)),
+            "p99_ms": float(np.percentile(lat, 99)), "tests_per_s": total_tests / span, "requests": n_requests}
+
+
 def run_ours(args, rank, world, dist):
     import torch
     from paper_1410_5780_gb300 import pv3d
@@ -306,6 +406,10 @@ def run_ours(args, rank, world, dist):
                            "d2h_bytes_per_step": d2h, "includes": "scene/generator/sun upload from host arrays, "
                            "evaluation, host read-back of the energies"}
 
+    if rank == 0 and not args.no_serving and args.workload == "facade":
+        bt = batched_section(dev, args.batch_scenes)
+        line["batched"] = bt
+        line["serving"] = serving_section(dev, args.requests)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         v, cores, sample, _ = oracle_sample_run(w, budget_s=15.0)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}

@@ -63,9 +63,11 @@ typedef struct pv3d_opts {
     int32_t tile;             /* rasteriser tile side: 32 or 64 texels [64] */
     int32_t chunk_steps;      /* sun steps processed per wave, 1..256 [128] */
     int32_t depth_format;     /* PV3D_DEPTH_F32 or PV3D_DEPTH_U24 [F32] */
-    int32_t max_inflight;     /* served requests resident on the device at once [64] */
+    int32_t max_inflight;     /* served requests resident on the device at once, 1..256 [64] */
     int64_t hbm_budget_bytes; /* device memory the context may use [90% of free memory] */
-    int32_t reserved[8];
+    int32_t wave_scratch_mb;  /* served waves: per-wave scratch target, MiB; requests take fewer steps per
+                                 wave to stay under it [256] */
+    int32_t reserved[7];
 } pv3d_opts;
 
 /*

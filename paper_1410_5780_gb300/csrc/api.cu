@@ -207,6 +207,9 @@ extern "C" int pv3d_create(pv3d_ctx** out, const pv3d_opts* opts)
     if (o.tile == 0) o.tile = 64;
     if (o.chunk_steps == 0) o.chunk_steps = 128;
     if (o.max_inflight == 0) o.max_inflight = 64;
+    if (o.max_inflight < 1 || o.max_inflight > 256) return PV3D_E_INVALID;  // jobs per wave
+    if (o.wave_scratch_mb == 0) o.wave_scratch_mb = 256;
+    if (o.wave_scratch_mb < 1) return PV3D_E_INVALID;
     if (o.tile != 32 && o.tile != 64) return PV3D_E_INVALID;
     if (o.map_res < 64 || o.map_res > 16384 || (o.map_res & (o.map_res - 1))) return PV3D_E_INVALID;
     if (o.chunk_steps < 1 || o.chunk_steps > 256) return PV3D_E_INVALID;
@@ -1123,7 +1126,10 @@ static int serve_wave(pv3d_ctx* c, std::unique_lock<std::mutex>& lk)
     }
     if (c->active.empty()) return 0;
     // wave: the next chunk of every active request, within the scratch limits
-    const int64_t scratch_cap = std::max<int64_t>(budget / 4, (int64_t)1 << 28);
+    // the wave's tile and cell arrays are kept near the scratch target (the
+    // L2-sized working set decides the binning and tally speed); the first
+    // request of the wave shortens its chunk if it alone is over the target
+    const int64_t scratch_cap = std::min<int64_t>((int64_t)c->opts.wave_scratch_mb << 20, std::max<int64_t>(budget / 4, 1));
     std::vector<JobDev> jobs;
     std::vector<pv3d_ctx::Request*> in_wave;
     std::vector<int> ks;
@@ -1134,8 +1140,10 @@ static int serve_wave(pv3d_ctx* c, std::unique_lock<std::mutex>& lk)
         pv3d_ctx::Request& r = *c->reqs.at(c->active[(c->rr + q) % na]);
         const GenH& g = c->gens.at(r.gen_id);
         const SceneH& sc = c->scenes.at(g.scene_id);
-        const int k = (int)std::min<int64_t>(r.es.K, r.es.e - r.next);
-        const int64_t need = per_step_scratch(g, r.es) * k;
+        int k = (int)std::min<int64_t>(r.es.K, r.es.e - r.next);
+        const int64_t per_step = per_step_scratch(g, r.es);
+        if (jobs.empty()) k = (int)std::max<int64_t>(1, std::min<int64_t>(k, scratch_cap / std::max<int64_t>(per_step, 1)));
+        const int64_t need = per_step * k;
         if (!jobs.empty() && scratch + need > scratch_cap) break;
         scratch += need;
         jobs.push_back(make_job(c, g, sc, r.es, r.next, k, (float2*)r.kmod.p, (float2*)r.kcell.p, r.d_p, r.d_pu,

@@ -41,7 +41,7 @@ EXPORTED = ("pv3d_create", "pv3d_destroy", "pv3d_last_error", "pv3d_scene_load",
 class pv3d_opts(C.Structure):
     _fields_ = [("device", C.c_int32), ("map_res", C.c_int32), ("tile", C.c_int32), ("chunk_steps", C.c_int32),
                 ("depth_format", C.c_int32), ("max_inflight", C.c_int32), ("hbm_budget_bytes", C.c_int64),
-                ("reserved", C.c_int32 * 8)]
+                ("wave_scratch_mb", C.c_int32), ("reserved", C.c_int32 * 7)]
 
 
 class pv3d_module(C.Structure):
@@ -151,10 +151,12 @@ class Context:
     """One pv3d context (one device, one host thread)."""
 
     def __init__(self, device: int = 0, map_res: int = 0, tile: int = 0, chunk_steps: int = 0,
-                 depth_format: int = PV3D_DEPTH_F32, max_inflight: int = 0, hbm_budget_bytes: int = 0):
+                 depth_format: int = PV3D_DEPTH_F32, max_inflight: int = 0, hbm_budget_bytes: int = 0,
+                 wave_scratch_mb: int = 0):
         self.lib = load()
         o = pv3d_opts(device=device, map_res=map_res, tile=tile, chunk_steps=chunk_steps,
-                      depth_format=depth_format, max_inflight=max_inflight, hbm_budget_bytes=hbm_budget_bytes)
+                      depth_format=depth_format, max_inflight=max_inflight, hbm_budget_bytes=hbm_budget_bytes,
+                      wave_scratch_mb=wave_scratch_mb)
         h = C.c_void_p()
         rc = self.lib.pv3d_create(C.byref(h), C.byref(o))
         if rc != 0:
@@ -318,14 +320,17 @@ class Context:
 
     def evaluate_batch(self, gen_ids, n=3, map_res=0, chunk_steps=0, outputs=("energy", "energy_unshaded"),
                        device: bool = True) -> list:
-        """pv3d_evaluate_batch over ``gen_ids`` with one option set."""
+        """pv3d_evaluate_batch over ``gen_ids``; ``n`` and ``map_res`` may be
+        per-generator sequences."""
         k = len(gen_ids)
+        ns = list(n) if hasattr(n, "__len__") else [n] * k
+        rs = list(map_res) if hasattr(map_res, "__len__") else [map_res] * k
         ids = (C.c_uint32 * k)(*gen_ids)
         opts = (pv3d_eval_opts * k)()
         results = (pv3d_result * k)()
         keep = []
         for q, gid in enumerate(gen_ids):
-            opts[q] = self._opts(n, map_res, 0, 0, chunk_steps, None, 0.0, 0.0, 0.0)
+            opts[q] = self._opts(int(ns[q]), int(rs[q]), 0, 0, chunk_steps, None, 0.0, 0.0, 0.0)
             res, arrays = self._alloc(gid, 0, 0, outputs, device)
             results[q] = res
             keep.append(arrays)

@@ -328,8 +328,8 @@ def _scatter_nonoverlap(rng, n, sampler, radius_of, existing=()):
     tries = 0
     while len(out) < n:
         tries += 1
-        if tries > 200000:
-            raise RuntimeError("could not place objects")
+        if tries > 20000:
+            break  # crowded: keep the objects placed so far
         c, r = sampler(), None
         r = radius_of(c)
         if all(np.hypot(c[0] - q[0], c[1] - q[1]) > r + qr + 2.0 for q, qr in placed):
@@ -594,3 +594,63 @@ def make_config(name: str, **kw) -> Workload:
     if name in ("tracker", "cfg3"):
         return make_tracker(**kw)
     raise KeyError(name)
+
+
+# ---------------------------------------------------------------------------
+# many scenes of uneven size (batched and served workloads)
+# ---------------------------------------------------------------------------
+def _pow2_at_least(x: float, lo: int, hi: int) -> int:
+    r = lo
+    while r < x and r < hi:
+        r *= 2
+    return r
+
+
+def make_mixed_scene(rng, tris_target: int, mods_target: int, lat: float, n_steps: int, n: int = 4) -> Workload:
+    """A facade-like or tracker-like scene with about ``tris_target`` triangles,
+    ``mods_target`` modules, suns of ``n_steps`` consecutive daylight hours of a
+    year at latitude ``lat``."""
+    seed = int(rng.integers(1 << 30))
+    if rng.random() < 0.5:
+        per_floor = int(np.clip(round(math.sqrt(mods_target * 3)), 2, 60))
+        floors = int(np.clip(math.ceil(mods_target / per_floor), 1, 40))
+        nb = int(np.clip(tris_target // 700, 2, 60))
+        w = make_facade(seed=seed, n=n, map_res=1024, n_buildings=nb, n_trees=int(np.clip(nb // 2, 1, 30)),
+                        n_poles=int(np.clip(nb // 4, 1, 10)), floors=floors, per_floor=per_floor,
+                        target_tris=tris_target,
+                        radius=float(max(2.5 * (per_floor + 1), 15.0 * math.sqrt(nb) + 40.0 + per_floor)))
+    else:
+        trackers = max(1, int(math.ceil(mods_target / 24)))
+        gx = int(math.ceil(math.sqrt(trackers * 1.25)))
+        gy = int(math.ceil(trackers / gx))
+        terrain_n = int(np.clip(round(math.sqrt(max(tris_target, 200) / 2.0)), 8, 512))
+        size = 25.0 * max(gx, gy) + 30
+        spacing = size / (terrain_n - 1)
+        w = make_tracker(seed=seed, n=n, map_res=1024, grid=(gx, gy), terrain_n=terrain_n, spacing=spacing,
+                         n_pylons=int(rng.integers(0, 3)), step_h=1.0, with_ridge=bool(rng.random() < 0.3))
+    full = year_sun(lat, 1.0)
+    k = int(min(n_steps, full.n_steps))
+    b = int(rng.integers(0, full.n_steps - k + 1))
+    w.sun = Sun(xyz=full.xyz[b:b + k], dni=full.dni[b:b + k], dhi=full.dhi[b:b + k], dt_h=full.dt_h[b:b + k])
+    if w.poses is not None:
+        w.poses = ideal_poses(w.sun, w.gen.pivots.shape[0])
+    # light window finer than half the sample spacing, within 512..4096
+    pts = w.gen.pivots if w.gen.pivots.shape[0] else w.gen.origin
+    ext = float(np.ptp(pts, axis=0).max() + 10.0)
+    w.map_res = _pow2_at_least(2.0 * ext / (CELL_PITCH / n), 512, 4096)
+    w.name = f"mixed{seed}"
+    return w
+
+
+def make_batch(seed: int = 4, n_scenes: int = 256, tris=(1e3, 2e5), mods=(10, 2000), lat=(0.0, 60.0),
+               steps=(100, 4400), n: int = 4) -> list:
+    """``n_scenes`` scenes of uneven size: triangles and modules log-uniform,
+    latitude uniform, sun steps uniform (the batched workload)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_scenes):
+        t = int(math.exp(rng.uniform(math.log(tris[0]), math.log(tris[1]))))
+        m = int(math.exp(rng.uniform(math.log(mods[0]), math.log(mods[1]))))
+        out.append(make_mixed_scene(rng, t, m, float(rng.uniform(*lat)), int(rng.integers(steps[0], steps[1] + 1)),
+                                    n=n))
+    return out

@@ -298,7 +298,14 @@ def run_ours(args, rank, world, dist):
     torch.cuda.set_device(dev)
     w = make_workload(args.workload, rank)
     path = pv3d.PV3D_PATH_FUSED if args.path == "fused" else pv3d.PV3D_PATH_MAP
-    ctx = pv3d.Context(device=dev, map_res=w.map_res, chunk_steps=args.chunk)
+    # tile size, sun steps per wave and bin pool from the autotuner (short
+    # timed trials, not part of the timed region); the map resolution is the
+    # workload's own
+    from paper_1410_5780_gb300 import autotune
+    tuned = autotune.autotune(w, device=dev, cache=None, n_windows=3)
+    chunk = args.chunk or tuned["chunk_steps"]
+    ctx = pv3d.Context(device=dev, map_res=w.map_res, chunk_steps=chunk, tile=tuned["tile"],
+                       bin_capacity=tuned["bin_capacity"])
     gid = pv3d.load_workload(ctx, w)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{dev}")
@@ -373,7 +380,9 @@ def run_ours(args, rank, world, dist):
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": dict(workload_config(w, args.workload), path=args.path, l2="flushed between steps (512 MB)",
-                           waves_per_step=waves // args.steps, annual_loss_pct=round(e_loss, 4)),
+                           waves_per_step=waves // args.steps, annual_loss_pct=round(e_loss, 4),
+                           autotuned={"tile": tuned["tile"], "chunk_steps": chunk,
+                                      "bin_capacity": tuned["bin_capacity"]}),
             "roofline": {"bound": "alu", "kernel": "k_raster_test" if args.path == "fused" else "k_raster_map",
                          "achieved": achieved, "peak": alu_peak, "unit": "T lane-ops/s",
                          "frac": achieved / alu_peak, "traffic": None,

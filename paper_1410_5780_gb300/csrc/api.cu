@@ -210,6 +210,8 @@ extern "C" int pv3d_create(pv3d_ctx** out, const pv3d_opts* opts)
     if (o.max_inflight < 1 || o.max_inflight > 256) return PV3D_E_INVALID;  // jobs per wave
     if (o.wave_scratch_mb == 0) o.wave_scratch_mb = 256;
     if (o.wave_scratch_mb < 1) return PV3D_E_INVALID;
+    if (o.bin_capacity < 0 || o.bin_capacity > (1ll << 32)) return PV3D_E_INVALID;
+    if (o.bin_capacity > 0) c->bin_cap = o.bin_capacity;
     if (o.tile != 32 && o.tile != 64) return PV3D_E_INVALID;
     if (o.map_res < 64 || o.map_res > 16384 || (o.map_res & (o.map_res - 1))) return PV3D_E_INVALID;
     if (o.chunk_steps < 1 || o.chunk_steps > 256) return PV3D_E_INVALID;

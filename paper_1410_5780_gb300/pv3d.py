@@ -41,7 +41,8 @@ EXPORTED = ("pv3d_create", "pv3d_destroy", "pv3d_last_error", "pv3d_scene_load",
 class pv3d_opts(C.Structure):
     _fields_ = [("device", C.c_int32), ("map_res", C.c_int32), ("tile", C.c_int32), ("chunk_steps", C.c_int32),
                 ("depth_format", C.c_int32), ("max_inflight", C.c_int32), ("hbm_budget_bytes", C.c_int64),
-                ("wave_scratch_mb", C.c_int32), ("reserved", C.c_int32 * 7)]
+                ("wave_scratch_mb", C.c_int32), ("reserved0", C.c_int32), ("bin_capacity", C.c_int64),
+                ("reserved", C.c_int32 * 4)]
 
 
 class pv3d_module(C.Structure):
@@ -152,11 +153,11 @@ class Context:
 
     def __init__(self, device: int = 0, map_res: int = 0, tile: int = 0, chunk_steps: int = 0,
                  depth_format: int = PV3D_DEPTH_F32, max_inflight: int = 0, hbm_budget_bytes: int = 0,
-                 wave_scratch_mb: int = 0):
+                 wave_scratch_mb: int = 0, bin_capacity: int = 0):
         self.lib = load()
         o = pv3d_opts(device=device, map_res=map_res, tile=tile, chunk_steps=chunk_steps,
                       depth_format=depth_format, max_inflight=max_inflight, hbm_budget_bytes=hbm_budget_bytes,
-                      wave_scratch_mb=wave_scratch_mb)
+                      wave_scratch_mb=wave_scratch_mb, bin_capacity=bin_capacity)
         h = C.c_void_p()
         rc = self.lib.pv3d_create(C.byref(h), C.byref(o))
         if rc != 0:

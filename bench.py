@@ -182,6 +182,22 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def profiled_traffic(workload: str):
+    """DRAM bytes per launch of the tile kernel from the committed ncu summary,
+    if it was taken on the current kernels.cu (else None)."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", f"k_raster_test_{workload}.md")
+    src = os.path.join(ROOT, "paper_1410_5780_gb300", "csrc", "kernels.cu")
+    try:
+        m = re.search(r"<!-- traffic: (\{.*?\}) -->", open(path).read())
+        rec = json.loads(m.group(1))
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except (OSError, AttributeError, ValueError):
+        return None
+    return rec["bytes_per_launch"] if rec.get("sha256") == sha else None
+
+
 def input_bytes(w) -> int:
     m = w.gen.n_modules
     b = w.scene.verts.nbytes + w.scene.tris.nbytes + 64 * m
@@ -329,6 +345,7 @@ def run_ours(args, rank, world, dist):
     tests = 0
     launches = 0
     results = []
+    torch.cuda.nvtx.range_push("timed")
     for k in range(args.steps):
         flush.zero_()
         ev[k][0].record(stream)
@@ -341,6 +358,7 @@ def run_ours(args, rank, world, dist):
         launches += r["kernel_launches"]
         results.append(r)
     torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
     clocks = sampler.stop()
     t_ms = sum(a.elapsed_time(b) for a, b in ev)
     if dist is not None:
@@ -385,7 +403,9 @@ def run_ours(args, rank, world, dist):
                                       "bin_capacity": tuned["bin_capacity"]}),
             "roofline": {"bound": "alu", "kernel": "k_raster_test" if args.path == "fused" else "k_raster_map",
                          "achieved": achieved, "peak": alu_peak, "unit": "T lane-ops/s",
-                         "frac": achieved / alu_peak, "traffic": None,
+                         "frac": achieved / alu_peak, "traffic": profiled_traffic(args.workload),
+                         "traffic_source": "DRAM read+write bytes of the first timed launch, ncu capture in "
+                                           f"profiles/k_raster_test_{args.workload}.md (null if kernels.cu changed)",
                          "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "
                                         "(sm_max_mhz of MEASURED_PEAKS.json)",
                          "work_per_launch": {"texel_writes": work["texel_writes"] / max(work["waves"], 1),

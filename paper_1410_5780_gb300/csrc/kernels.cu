@@ -792,7 +792,9 @@ __device__ __forceinline__ int fdiv(int q, int d, float inv_d)
     return r;
 }
 
-// A receiver module of the tile, staged in shared memory.
+// A receiver module of the tile, staged in shared memory.  Its samples that
+// may read the tile form the index box [I0, I1] x [J0, J1] (I = cu * n + i,
+// J = cv * n + j); the box is walked as (sample row, cell column) items.
 struct RecvSm {
     ModStep s;
     float p_over_n;      // sample spacing along the module axes, m
@@ -800,8 +802,9 @@ struct RecvSm {
     float cull_tol;      // plane tolerance (half the bias slack), or -1 if the plane may not cull
     int cu;              // cells across the module
     int cell_base;       // first cell of the module in the generator
-    int cu0, cv0, wcu;   // cells of the module that may read the tile
-    int cell_pref;       // cells of the receivers staged before this one
+    int I0, I1, J0;      // sample-index box (J1 = J0 + rows - 1)
+    int cI0, ncol;       // cell columns of the box
+    int item_pref;       // items of the receivers staged before this one
 };
 
 template <int TS>
@@ -812,14 +815,15 @@ struct TileSm {
     uint16_t list[TS * TS];          // marked texels, row-major
     RecvSm recv[kRecvChunk];
     int n_recv;                      // receivers staged
-    int total_cells;                 // cells over the staged receivers
+    int total_items;                 // (sample row, cell column) items over the staged receivers
     TriSetup tri[kTriBatch];         // a batch of set-up triangles
     int chunk_pref[kTriBatch + 1];   // prefix of their 32-texel work chunks
     int any_write;                   // some texel of the tile received a depth
 };
 
-// Stage receivers [r0, r0 + cnt) of tile (tx, ty): cell box (the tile corners
-// mapped back onto the module plane, widened by one cell) and depth plane.
+// Stage receivers [r0, r0 + cnt) of tile (tx, ty): sample-index box (the
+// tile corners mapped back onto the module plane, widened by one sample) and
+// depth plane.
 template <int TS>
 __device__ void stage_receivers(TileSm<TS>& sm, const JobDev& J, const Buffers& B, int ls, int tx, int ty,
                                 uint64_t r0, int cnt)
@@ -830,11 +834,12 @@ __device__ void stage_receivers(TileSm<TS>& sm, const JobDev& J, const Buffers& 
         const ModuleDev& M = J.mods[m];
         RecvSm& R = sm.recv[tid];
         const ModStep s = B.ms[J.ms_base + (int64_t)ls * J.n_mods + m];
+        const int n = J.n;
         R.s = s;
-        R.p_over_n = __fdiv_rn(M.pitch, (float)J.n);
+        R.p_over_n = __fdiv_rn(M.pitch, (float)n);
         R.cu = M.cu;
         R.cell_base = M.cell_base;
-        int cu0 = 0, cu1 = M.cu - 1, cv0 = 0, cv1 = M.cv - 1;
+        int I0 = 0, I1 = M.cu * n - 1, J0 = 0, J1 = M.cv * n - 1;
         const float det = s.tax * s.tby - s.tay * s.tbx;
         const bool planar = fabsf(det) > 1e-6f * (fabsf(s.tax * s.tby) + fabsf(s.tay * s.tbx));
         R.cull_tol = -1.f;
@@ -849,11 +854,12 @@ __device__ void stage_receivers(TileSm<TS>& sm, const JobDev& J, const Buffers& 
                 amin = fminf(amin, a); amax = fmaxf(amax, a);
                 bmin = fminf(bmin, b); bmax = fmaxf(bmax, b);
             }
-            const float ip = 1.f / M.pitch;
-            cu0 = max(cu0, (int)fmaxf(floorf(amin * ip) - 1.f, -1.f));
-            cu1 = min(cu1, (int)fminf(floorf(amax * ip) + 1.f, 1e6f));
-            cv0 = max(cv0, (int)fmaxf(floorf(bmin * ip) - 1.f, -1.f));
-            cv1 = min(cv1, (int)fminf(floorf(bmax * ip) + 1.f, 1e6f));
+            // samples at a = (I + 1/2) p/n: I in [a_min n/p - 1/2, a_max n/p - 1/2], one more each side
+            const float ip = 1.f / R.p_over_n;
+            I0 = max(I0, (int)fmaxf(floorf(amin * ip - 0.5f) - 1.f, -1.f));
+            I1 = min(I1, (int)fminf(ceilf(amax * ip - 0.5f) + 1.f, 1e6f));
+            J0 = max(J0, (int)fmaxf(floorf(bmin * ip - 0.5f) - 1.f, -1.f));
+            J1 = min(J1, (int)fminf(ceilf(bmax * ip - 0.5f) + 1.f, 1e6f));
             // depth of the receiver plane over the tile: a triangle lying on or
             // behind the plane (by less than half the bias slack) shades none
             // of its samples, so it may be skipped for this receiver
@@ -862,61 +868,64 @@ __device__ void stage_receivers(TileSm<TS>& sm, const JobDev& J, const Buffers& 
             R.pc = s.d0 - R.pa * (s.tx0 - (float)(tx * TS)) - R.pb * (s.ty0 - (float)(ty * TS));
             if (s.cosi > 0.017452406f) R.cull_tol = B.lp[J.js_base + ls].delta * (1.f / 64.f);
         }
-        R.cu0 = cu0;
-        R.cv0 = cv0;
-        R.wcu = max(0, cu1 - cu0 + 1);
-        R.cell_pref = (cu0 <= cu1 && cv0 <= cv1) ? R.wcu * (cv1 - cv0 + 1) : 0;  // cells, prefixed below
+        R.I0 = I0;
+        R.I1 = I1;
+        R.J0 = J0;
+        R.cI0 = I0 / n;
+        R.ncol = (I0 <= I1) ? I1 / n - I0 / n + 1 : 0;
+        R.item_pref = (I0 <= I1 && J0 <= J1) ? R.ncol * (J1 - J0 + 1) : 0;  // items, prefixed below
     }
     __syncthreads();
     if (tid == 0) {
         int acc = 0;
         for (int r = 0; r < cnt; ++r) {
-            const int c = sm.recv[r].cell_pref;
-            sm.recv[r].cell_pref = acc;
+            const int c = sm.recv[r].item_pref;
+            sm.recv[r].item_pref = acc;
             acc += c;
         }
         sm.n_recv = cnt;
-        sm.total_cells = acc;
+        sm.total_items = acc;
     }
     __syncthreads();
 }
 
-// Receiver and cell of staged cell item `it`.
+// Receiver of staged item `it`.
 template <int TS>
 __device__ __forceinline__ int recv_of(const TileSm<TS>& sm, int it)
 {
     int lo = 0, hi = sm.n_recv - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (sm.recv[mid].cell_pref <= it) lo = mid; else hi = mid - 1;
+        if (sm.recv[mid].item_pref <= it) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
 
 // Visit the samples of the staged receivers that read tile (tx, ty): one
-// thread per (cell, sample row) walks the row's n samples.  f(R, k, ix, iy, d)
-// is called per sample inside the tile (k = j * n + i); g(R, cu, cv) after
-// each row.
+// thread per (sample row, cell column) item walks the row's samples inside
+// the cell and the box.  f(R, k, ix, iy, d) is called per sample inside the
+// tile (k = j * n + i within the cell); g(R, cu, cv) after each item.
 template <int TS, typename F, typename G>
 __device__ __forceinline__ void for_tile_samples(const TileSm<TS>& sm, const JobDev& J, int tx, int ty, F f, G g)
 {
     constexpr int SH = TS == 64 ? 6 : 5;
     const int n = J.n, R_ = J.R;
     const float inv_n = 1.f / (float)n;
-    const int items = sm.total_cells * n;
-    for (int it = threadIdx.x; it < items; it += blockDim.x) {
-        const int cell = fdiv(it, n, inv_n);
-        const int jj = it - cell * n;
-        const RecvSm& R = sm.recv[recv_of(sm, cell)];
-        const int c = cell - R.cell_pref;
-        const int cvb = fdiv(c, R.wcu, 1.f / (float)R.wcu);
-        const int cu = R.cu0 + c - cvb * R.wcu, cv = R.cv0 + cvb;
-        for (int ii = 0; ii < n; ++ii) {
+    for (int it = threadIdx.x; it < sm.total_items; it += blockDim.x) {
+        const RecvSm& R = sm.recv[recv_of(sm, it)];
+        const int q = it - R.item_pref;
+        const int row = fdiv(q, R.ncol, 1.f / (float)R.ncol);
+        const int cu = R.cI0 + q - row * R.ncol;
+        const int Jr = R.J0 + row;
+        const int cv = fdiv(Jr, n, inv_n);
+        const int jj = Jr - cv * n;
+        const int Ib = max(R.I0, cu * n), Ie = min(R.I1, cu * n + n - 1);
+        for (int I = Ib; I <= Ie; ++I) {
             float a, b, d;
             int ix, iy;
-            sample_ab(cu * n + ii, cv * n + jj, R.p_over_n, a, b);
+            sample_ab(I, Jr, R.p_over_n, a, b);
             sample_texel(R.s, a, b, R_, ix, iy, d);
-            if ((ix >> SH) == tx && (iy >> SH) == ty) f(R, jj * n + ii, ix, iy, d);
+            if ((ix >> SH) == tx && (iy >> SH) == ty) f(R, jj * n + (I - cu * n), ix, iy, d);
         }
         g(R, cu, cv);
     }
@@ -958,7 +967,7 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
     const LightParams& lp = B.lp[J.js_base + ls];
     const bool cull_ok = nrecv <= kRecvChunk;
     // samples reading the tile, at most (estimated from the staged receivers)
-    const int64_t est = (int64_t)sm.total_cells * J.nn * ((nrecv + kRecvChunk - 1) / kRecvChunk);
+    const int64_t est = (int64_t)sm.total_items * J.n * ((nrecv + kRecvChunk - 1) / kRecvChunk);
     const bool dense = est * 2 >= TS * TS;
     int n_need = TS * TS;
     if (!dense) {
@@ -1320,39 +1329,77 @@ __device__ __forceinline__ void zero_step_module(const JobDev& J, const ModuleDe
     }
 }
 
-// Fused path: the tallies were accumulated by k_raster_test.
+// Fused path: the tallies were accumulated by k_raster_test.  One warp per
+// (step, module): lanes over cells, substring minima in shared memory, the
+// candidate currents of the MPP split over lanes.
+constexpr int kPvWarps = kPvThreads / 32;
+
 __global__ void __launch_bounds__(kPvThreads) k_pv(const WaveDev* __restrict__ W, const JobDev* __restrict__ jobs,
                                                    Buffers B)
 {
-    __shared__ uint32_t s_cnt[kMaxCellsPerModule];
-    __shared__ uint32_t s_imin[kMaxSub];
+    __shared__ uint32_t s_imin[kPvWarps][kMaxSub];
     const int64_t tot = W->tot_mod;
     const int nj = W->n_jobs;
-    for (int64_t item = blockIdx.x; item < tot; item += gridDim.x) {
-        int j = job_of(nj, item, [&](int q) { return jobs[q].it_mod; });
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    uint32_t* imin = s_imin[wib];
+    const int64_t n_warps = (int64_t)gridDim.x * kPvWarps;
+    for (int64_t item = (int64_t)blockIdx.x * kPvWarps + wib; item < tot; item += n_warps) {
+        const int j = job_of(nj, item, [&](int q) { return jobs[q].it_mod; });
         const JobDev& J = jobs[j];
         const int64_t li = item - J.it_mod;
         const int ls = (int)(li / J.n_mods), m = (int)(li % J.n_mods);
         const int64_t msi = J.ms_base + li;
         const LightParams& lp = B.lp[J.js_base + ls];
         const ModuleDev& M = J.mods[m];
-        if (!lp.valid) {
-            zero_step_module(J, M, ls, msi, B);
-            continue;
-        }
         const int ncell = M.cu * M.cv, C = J.n_cells;
         const int64_t row = (int64_t)(J.out_row0 + ls);
         const int64_t cbase = J.cs_base + (int64_t)ls * C + M.cell_base;
-        for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
+        if (!lp.valid) {
+            if (lane == 0) { B.ms_p[msi] = 0.f; B.ms_pu[msi] = 0.f; B.ms_beam[msi] = 0.f; }
+            for (int c = lane; c < ncell; c += 32) {
+                B.cs_cnt[cbase + c] = 0u;
+                if (J.out_counts) J.out_counts[row * C + M.cell_base + c] = 0;
+                if (J.out_bits) J.out_bits[row * C + M.cell_base + c] = 0ull;
+            }
+            continue;
+        }
+        const ModStep& s = B.ms[msi];
+        const float beam = lp.dni * fmaxf(0.f, s.cosi);
+        const float diff = lp.dhi * (1.f + s.nz) * 0.5f;
+        const float inv_nn = 1.f / J.nn;
+        const int* csub = J.lay_sub + J.lay_off[M.layout];
+        const int ns = M.n_sub;
+        for (int k = lane; k < ns; k += 32) imin[k] = 0x7F800000u;  // +inf
+        __syncwarp();
+        for (int c = lane; c < ncell; c += 32) {
             const uint32_t cnt = B.cs_cnt[cbase + c];
-            s_cnt[c] = cnt;
             if (J.out_counts) J.out_counts[row * C + M.cell_base + c] = (uint8_t)cnt;
             if (J.out_bits) J.out_bits[row * C + M.cell_base + c] = B.cs_bits[cbase + c];
+            const float G = beam * (1.f - cnt * inv_nn) + diff;
+            const float I = J.i_ref * G * 1e-3f;
+            atomicMin(&imin[csub[c]], __float_as_uint(I));  // I >= 0: uint order = float order
         }
-        if (threadIdx.x < kMaxSub) s_imin[threadIdx.x] = 0x7F800000u;  // +inf
-        __syncthreads();
-        module_pv(J, M, B.ms[msi], lp, s_cnt, s_imin, B, msi);
-        __syncthreads();
+        __syncwarp();
+        const int* nk = J.lay_nk + J.lay_nk_off[M.layout];
+        float best = 0.f, vsum = 0.f;
+        for (int k = lane; k < ns; k += 32) {
+            const float ik = __uint_as_float(imin[k]);
+            float volt = 0.f;
+            for (int q = 0; q < ns; ++q) volt += __uint_as_float(imin[q]) >= ik ? nk[q] * J.v_cell : -J.v_diode;
+            best = fmaxf(best, ik * volt);
+            vsum += nk[k] * J.v_cell;
+        }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+            best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, off));
+            vsum += __shfl_xor_sync(0xffffffffu, vsum, off);
+        }
+        if (lane == 0) {
+            B.ms_p[msi] = best;
+            B.ms_pu[msi] = J.i_ref * (beam + diff) * 1e-3f * vsum;
+            B.ms_beam[msi] = beam;
+        }
+        __syncwarp();
     }
 }
 
@@ -1566,7 +1613,7 @@ cudaError_t launch_wave(const WaveDev* d_wave, const JobDev* d_jobs, const Buffe
         else launch_tile_kernels<64, false>(W, d_jobs, b, cfg);
     }
     if (cfg.ev) cudaEventRecord(cfg.ev[3], st);
-    if (cfg.fused) k_pv<<<sm * 16, kPvThreads, 0, st>>>(W, d_jobs, b);
+    if (cfg.fused) k_pv<<<sm * 32, kPvThreads, 0, st>>>(W, d_jobs, b);
     else k_sample<<<sm * 16, kPvThreads, 0, st>>>(W, d_jobs, b);
     if (cfg.ev) cudaEventRecord(cfg.ev[4], st);
     k_epilogue<<<sm * 8, 256, 0, st>>>(W, d_jobs, b);

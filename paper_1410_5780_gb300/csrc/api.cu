@@ -29,7 +29,9 @@ struct DevBuf {
 
 struct SceneH {
     float4* d_tri = nullptr;
+    float4* d_ml = nullptr;  // meshlet boxes, 2 per meshlet
     int32_t n_tris = 0;
+    int32_t n_ml = 0;
     float lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
     size_t bytes = 0;
 };
@@ -268,9 +270,56 @@ extern "C" int pv3d_scene_load(pv3d_ctx* c, const float* xyz, int64_t n_verts, c
         for (int a = 0; a < 3; ++a) lo[a] = hi[a] = 0.f;
     memcpy(s.lo, lo, sizeof(lo));
     memcpy(s.hi, hi, sizeof(hi));
+    // triangles in Morton order of their centroids, grouped 32 at a time into
+    // meshlets with world bounding boxes (the binning culls whole meshlets)
+    {
+        std::vector<std::pair<uint32_t, int64_t>> key((size_t)n_tris);
+        auto spread = [](uint32_t x) {
+            x &= 0x3FF;
+            x = (x | (x << 16)) & 0x030000FF;
+            x = (x | (x << 8)) & 0x0300F00F;
+            x = (x | (x << 4)) & 0x030C30C3;
+            x = (x | (x << 2)) & 0x09249249;
+            return x;
+        };
+        for (int64_t t = 0; t < n_tris; ++t) {
+            uint32_t q[3];
+            for (int a = 0; a < 3; ++a) {
+                const float cen = (tv[3 * t].x * (a == 0) + tv[3 * t].y * (a == 1) + tv[3 * t].z * (a == 2) +
+                                   tv[3 * t + 1].x * (a == 0) + tv[3 * t + 1].y * (a == 1) + tv[3 * t + 1].z * (a == 2) +
+                                   tv[3 * t + 2].x * (a == 0) + tv[3 * t + 2].y * (a == 1) + tv[3 * t + 2].z * (a == 2)) /
+                                  3.f;
+                const float ext = hi[a] - lo[a];
+                const float f = ext > 0 ? (cen - lo[a]) / ext : 0.f;
+                q[a] = (uint32_t)std::min(1023.f, std::max(0.f, f * 1023.f));
+            }
+            key[t] = {spread(q[0]) | (spread(q[1]) << 1) | (spread(q[2]) << 2), t};
+        }
+        std::sort(key.begin(), key.end());
+        std::vector<float4> sorted(tv.size());
+        for (int64_t t = 0; t < n_tris; ++t)
+            for (int k = 0; k < 3; ++k) sorted[3 * t + k] = tv[3 * key[t].second + k];
+        tv.swap(sorted);
+        s.n_ml = (int32_t)((n_tris + 31) / 32);
+        std::vector<float4> boxes((size_t)s.n_ml * 2);
+        for (int32_t m = 0; m < s.n_ml; ++m) {
+            float blo[3] = {INFINITY, INFINITY, INFINITY}, bhi[3] = {-INFINITY, -INFINITY, -INFINITY};
+            for (int64_t t = (int64_t)m * 32; t < std::min<int64_t>(n_tris, (int64_t)m * 32 + 32); ++t)
+                for (int k = 0; k < 3; ++k) {
+                    const float4 p = tv[3 * t + k];
+                    blo[0] = std::min(blo[0], p.x); bhi[0] = std::max(bhi[0], p.x);
+                    blo[1] = std::min(blo[1], p.y); bhi[1] = std::max(bhi[1], p.y);
+                    blo[2] = std::min(blo[2], p.z); bhi[2] = std::max(bhi[2], p.z);
+                }
+            boxes[2 * m] = make_float4(blo[0], blo[1], blo[2], 0.f);
+            boxes[2 * m + 1] = make_float4(bhi[0], bhi[1], bhi[2], 0.f);
+        }
+        int rc0 = upload(c, &s.d_ml, boxes.data(), boxes.size());
+        if (rc0) return rc0;
+    }
     int rc = upload(c, &s.d_tri, tv.data(), tv.size());
     if (rc) return rc;
-    s.bytes = std::max<size_t>(tv.size() * sizeof(float4), 16);
+    s.bytes = std::max<size_t>(tv.size() * sizeof(float4), 16) + (size_t)s.n_ml * 32;
     uint32_t id = c->next_id++;
     c->scenes[id] = s;
     *scene_id = id;
@@ -530,6 +579,8 @@ static JobDev make_job(pv3d_ctx* c, const GenH& g, const SceneH& s, const EvalSe
     JobDev J{};
     J.tri = s.d_tri;
     J.n_tris = s.n_tris;
+    J.ml_box = s.d_ml;
+    J.n_ml = s.n_ml;
     J.n_mtris = g.coplanar ? 0 : 2 * g.M;
     J.mods = g.d_mods;
     J.n_mods = g.M;
@@ -600,7 +651,7 @@ static WaveDev pack_wave(std::vector<JobDev>& jobs, size_t first, size_t last, i
         W.tot_cs += (int64_t)J.k * J.n_cells;
         W.tot_win += (int64_t)J.k * groups;
         W.tot_mod += (int64_t)J.k * J.n_mods;
-        W.tot_tri += ((int64_t)J.n_tris + J.n_mtris) * J.k;
+        W.tot_tri += ((int64_t)J.n_ml + (J.n_mtris + 31) / 32) * J.k;
         W.tot_epi += (int64_t)J.n_cells + J.n_mods;
         if (J.out_bits) W.want_bits = 1;
     }
@@ -1343,6 +1394,7 @@ extern "C" int pv3d_release(pv3d_ctx* c, uint32_t id)
         }
     }
     if (sit->second.d_tri) cudaFree(sit->second.d_tri);
+    if (sit->second.d_ml) cudaFree(sit->second.d_ml);
     c->scenes.erase(sit);
     return PV3D_OK;
 }
@@ -1361,8 +1413,10 @@ extern "C" void pv3d_destroy(pv3d_ctx* c)
     for (DevBuf& b : c->free_bufs) release_buf(b);
     if (c->serve_stream) cudaStreamDestroy(c->serve_stream);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    for (auto& kv : c->scenes)
+    for (auto& kv : c->scenes) {
         if (kv.second.d_tri) cudaFree(kv.second.d_tri);
+        if (kv.second.d_ml) cudaFree(kv.second.d_ml);
+    }
     for (auto& kv : c->gens) free_gen(kv.second);
     if (c->graph_exec) cudaGraphExecDestroy(c->graph_exec);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);

@@ -527,24 +527,69 @@ template <int FILL>
 __global__ void __launch_bounds__(256) k_bin(const WaveDev* __restrict__ W, const JobDev* __restrict__ jobs,
                                              Buffers B)
 {
-    // item = (triangle, step) with the step fastest: the lanes of a warp take
-    // consecutive sun steps of one triangle, so its three vertices are read
-    // once (a broadcast load) and transformed for up to 32 steps.
+    // One warp per (meshlet, step), the step fastest so that consecutive warps
+    // reuse the meshlet's 32 triangles from cache.  A scene meshlet is first
+    // tested as a whole: its bounding box, projected for the step, against the
+    // far planes of the tiles it covers; if no tile can receive a shadow from
+    // it, the 32 triangles are skipped together.  Then each lane bins one
+    // triangle.  Generator module triangles follow the scene's, in groups of
+    // 32, without the box test.
     const int64_t tot = W->tot_tri;
     const int nj = W->n_jobs;
     const int sh = W->tile_sh;
     const int TS = 1 << sh;
     const int u24 = W->depth_u24;
-    for (int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; item < tot;
-         item += (int64_t)gridDim.x * blockDim.x) {
-        int j = job_of(nj, item, [&](int q) { return jobs[q].it_tri; });
+    const int lane = threadIdx.x & 31;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t item = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; item < tot; item += n_warps) {
+        const int j = job_of(nj, item, [&](int q) { return jobs[q].it_tri; });
         const JobDev& J = jobs[j];
         const int64_t li = item - J.it_tri;
-        const int t = (int)(li / J.k), ls = (int)(li - (int64_t)t * J.k);
+        const int mi = (int)(li / J.k), ls = (int)(li - (int64_t)mi * J.k);
         const int R = J.R;
         const int64_t js = J.js_base + ls;
         const LightParams& lp = B.lp[js];
         if (!lp.valid) continue;
+        const int64_t te0 = J.te_base + (int64_t)ls * J.tiles_x * J.tiles_x;
+        int t;
+        if (mi < J.n_ml) {
+            const float4 lo = J.ml_box[2 * mi], hi = J.ml_box[2 * mi + 1];
+            float xmin = FLT_MAX, xmax = -FLT_MAX, ymin = FLT_MAX, ymax = -FLT_MAX, dmin = FLT_MAX;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                const float x = ((c & 1) ? hi.x : lo.x) - J.ref[0];
+                const float y = ((c & 2) ? hi.y : lo.y) - J.ref[1];
+                const float z = ((c & 4) ? hi.z : lo.z) - J.ref[2];
+                const float tx = (x * lp.ux + y * lp.uy + z * lp.uz - lp.u0) * lp.inv_delta;
+                const float ty = (x * lp.vx + y * lp.vy + z * lp.vz - lp.v0) * lp.inv_delta;
+                xmin = fminf(xmin, tx); xmax = fmaxf(xmax, tx);
+                ymin = fminf(ymin, ty); ymax = fmaxf(ymax, ty);
+                dmin = fminf(dmin, -(x * lp.sx + y * lp.sy + z * lp.sz));
+            }
+            if (!(xmax >= 0.5f && ymax >= 0.5f && xmin <= R - 0.5f && ymin <= R - 0.5f)) continue;
+            const int tx0 = max(0, (int)floorf(xmin - 0.5f)) >> sh, tx1 = min(R - 1, (int)ceilf(xmax)) >> sh;
+            const int ty0 = max(0, (int)floorf(ymin - 0.5f)) >> sh, ty1 = min(R - 1, (int)ceilf(ymax)) >> sh;
+            // the box's nearest point, less a margin for the rounding of the
+            // projection, against each covered tile's far plane
+            const uint32_t bkey = depth_store_key(dmin - 1e-3f * (1.f + fabsf(dmin)), lp, u24);
+            const int wx = tx1 - tx0 + 1, ntl = wx * (ty1 - ty0 + 1);
+            bool keep = false;
+            for (int q0 = 0; q0 < ntl && !keep; q0 += 32) {
+                const int q = q0 + lane;
+                bool k = false;
+                if (q < ntl) {
+                    const int ty = ty0 + q / wx, tx = tx0 + q % wx;
+                    k = bkey < B.t_far[te0 + (int64_t)ty * J.tiles_x + tx];
+                }
+                keep = __any_sync(0xffffffffu, k);
+            }
+            if (!keep) continue;
+            t = mi * 32 + lane;
+            if (t >= J.n_tris) continue;
+        } else {
+            t = J.n_tris + (mi - J.n_ml) * 32 + lane;
+            if (t >= J.n_tris + J.n_mtris) continue;
+        }
         TriT T;
         tri_texel(J, B, lp, ls, t, T);
         Edges e;
@@ -567,7 +612,6 @@ __global__ void __launch_bounds__(256) k_bin(const WaveDev* __restrict__ W, cons
             }
             continue;
         }
-        int64_t te0 = J.te_base + (int64_t)ls * J.tiles_x * J.tiles_x;
         for (int ty = ty0; ty <= ty1; ++ty) {
             for (int tx = tx0; tx <= tx1; ++tx) {
                 if (ntiles > 1 &&

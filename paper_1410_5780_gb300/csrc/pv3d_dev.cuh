@@ -60,6 +60,9 @@ struct JobDev {
     const float4* tri;
     int32_t n_tris;
     int32_t n_mtris;  // module triangles rasterised: 2 per module, or 0 for a coplanar generator
+    const float4* ml_box;  // scene meshlets (32 consecutive triangles, Morton order): world lo, hi
+    int32_t n_ml;          // scene meshlets = ceil(n_tris / 32)
+    int32_t pad_ml;
     // generator
     const ModuleDev* mods;
     int32_t n_mods;
@@ -111,7 +114,7 @@ struct WaveDev {
     int32_t want_bits;  // per-sample flags requested by some job of the wave
     int32_t profile;    // count work (texel visits, sample tests) into Counters
     int64_t tot_js, tot_te, tot_ms, tot_cs;
-    int64_t tot_win, tot_mod, tot_tri, tot_epi;
+    int64_t tot_win, tot_mod, tot_tri, tot_epi;  // tot_tri: (meshlet, step) warp items
     int64_t bin_cap, map_cap_tiles, big_cap, recv_cap;
 };
 

@@ -147,6 +147,8 @@ typedef struct pv3d_profile {
     int64_t tris_culled;       /* (triangle, tile) pairs skipped: on or behind every receiver plane */
     int64_t nonempty_tiles;
     int64_t binned_tris;
+    int64_t candidates;        /* receiver samples enumerated by the tile kernel (marking and testing) */
+    int64_t dense_tiles;       /* tiles rasterised at every texel */
 } pv3d_profile;
 
 /*

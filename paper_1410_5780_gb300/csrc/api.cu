@@ -970,6 +970,8 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
         P.texel_visits = (int64_t)hc.prof_visits;
         P.texel_writes = (int64_t)hc.prof_writes;
         P.tris_culled = (int64_t)hc.prof_culled;
+        P.candidates = (int64_t)hc.prof_cand;
+        P.dense_tiles = (int64_t)hc.prof_dense;
         P.nonempty_tiles = (int64_t)hc.stat_nonempty;
         P.binned_tris = (int64_t)hc.stat_bins;
         c->have_prof = true;

@@ -949,8 +949,9 @@ __device__ __forceinline__ int recv_of(const TileSm<TS>& sm, int it)
 // thread per (sample row, cell column) item walks the row's samples inside
 // the cell and the box.  f(R, k, ix, iy, d) is called per sample inside the
 // tile (k = j * n + i within the cell); g(R, cu, cv) after each item.
-template <int TS, typename F, typename G>
-__device__ __forceinline__ void for_tile_samples(const TileSm<TS>& sm, const JobDev& J, int tx, int ty, F f, G g)
+template <int TS, bool PROF, typename F, typename G>
+__device__ __forceinline__ void for_tile_samples(const TileSm<TS>& sm, const JobDev& J, int tx, int ty,
+                                                 unsigned int& cand, F f, G g)
 {
     constexpr int SH = TS == 64 ? 6 : 5;
     const int n = J.n, R_ = J.R;
@@ -964,6 +965,7 @@ __device__ __forceinline__ void for_tile_samples(const TileSm<TS>& sm, const Job
         const int cv = fdiv(Jr, n, inv_n);
         const int jj = Jr - cv * n;
         const int Ib = max(R.I0, cu * n), Ie = min(R.I1, cu * n + n - 1);
+        if (PROF) cand += (unsigned int)max(0, Ie - Ib + 1);
         for (int I = Ib; I <= Ie; ++I) {
             float a, b, d;
             int ix, iy;
@@ -1001,7 +1003,7 @@ __device__ __forceinline__ bool may_shade(const TileSm<TS>& sm, const TriT& T, b
 template <int TS, bool PROF>
 __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, const WaveDev* W, int ls, int tx,
                            int ty, int64_t te, uint64_t r0, int nrecv, unsigned int& visits, unsigned int& writes,
-                           unsigned int& culled)
+                           unsigned int& culled, unsigned int& cand, unsigned int& dense_n)
 {
     constexpr int SH = TS == 64 ? 6 : 5;
     constexpr int WPR = TS / 32;
@@ -1012,15 +1014,19 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
     const bool cull_ok = nrecv <= kRecvChunk;
     // samples reading the tile, at most (estimated from the staged receivers)
     const int64_t est = (int64_t)sm.total_items * J.n * ((nrecv + kRecvChunk - 1) / kRecvChunk);
-    const bool dense = est * 2 >= TS * TS;
+    // dense only when the samples clearly outnumber the texels: marking costs
+    // about as much per sample as a texel visit, and sparse tiles visit only
+    // the texels that samples read
+    const bool dense = est >= 2 * TS * TS;
+    if (PROF && threadIdx.x == 0 && dense) ++dense_n;
     int n_need = TS * TS;
     if (!dense) {
         for (int q = tid; q < TS * WPR; q += bd) sm.mask[q] = 0u;
         __syncthreads();
         for (int c0 = 0; c0 < nrecv; c0 += kRecvChunk) {
             if (c0 > 0) stage_receivers<TS>(sm, J, B, ls, tx, ty, r0 + c0, min(kRecvChunk, nrecv - c0));
-            for_tile_samples<TS>(
-                sm, J, tx, ty,
+            for_tile_samples<TS, PROF>(
+                sm, J, tx, ty, cand,
                 [&](const RecvSm&, int, int ix, int iy, float) {
                     atomicOr(&sm.mask[(iy & (TS - 1)) * WPR + ((ix & (TS - 1)) >> 5)], 1u << (ix & 31));
                 },
@@ -1190,6 +1196,22 @@ __device__ __forceinline__ void flush_profile(const Buffers& B, unsigned int sam
     }
 }
 
+__device__ __forceinline__ void flush_profile2(const Buffers& B, unsigned int cand, unsigned int tiles,
+                                               unsigned int dense)
+{
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        cand += __shfl_xor_sync(0xffffffffu, cand, off);
+        tiles += __shfl_xor_sync(0xffffffffu, tiles, off);
+        dense += __shfl_xor_sync(0xffffffffu, dense, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&B.ctr->prof_cand, (unsigned long long)cand);
+        atomicAdd(&B.ctr->prof_tiles, (unsigned long long)tiles);
+        atomicAdd(&B.ctr->prof_dense, (unsigned long long)dense);
+    }
+}
+
 // Decode a non-empty tile entry.
 __device__ __forceinline__ void decode_tile(const JobDev* jobs, int nj, uint32_t te, int& j, int& ls, int& tx,
                                             int& ty)
@@ -1222,7 +1244,7 @@ __global__ void __launch_bounds__(256) k_raster_test(const WaveDev* __restrict__
                                                      const JobDev* __restrict__ jobs, Buffers B)
 {
     __shared__ __align__(16) TileSm<TS> sm;
-    unsigned int p_samples = 0, p_visits = 0, p_writes = 0, p_culled = 0;
+    unsigned int p_samples = 0, p_visits = 0, p_writes = 0, p_culled = 0, p_cand = 0, p_dense = 0, p_tiles = 0;
     __shared__ unsigned int s_item;
     const unsigned int n_ne = B.ctr->n_nonempty;
     const int nj = W->n_jobs;
@@ -1243,7 +1265,9 @@ __global__ void __launch_bounds__(256) k_raster_test(const WaveDev* __restrict__
         int nrecv;
         tile_receivers(B, W, te, r0, nrecv);
         stage_receivers<TS>(sm, J, B, ls, tx, ty, r0, min(nrecv, kRecvChunk));
-        if (tile_raster<TS, PROF>(sm, J, B, W, ls, tx, ty, te, r0, nrecv, p_visits, p_writes, p_culled) == 0)
+        if (PROF && tid == 0) ++p_tiles;
+        if (tile_raster<TS, PROF>(sm, J, B, W, ls, tx, ty, te, r0, nrecv, p_visits, p_writes, p_culled, p_cand,
+                                  p_dense) == 0)
             continue;
         const LightParams& lp = B.lp[J.js_base + ls];
         const int C = J.n_cells;
@@ -1253,8 +1277,8 @@ __global__ void __launch_bounds__(256) k_raster_test(const WaveDev* __restrict__
             if (c0 > 0) stage_receivers<TS>(sm, J, B, ls, tx, ty, r0 + c0, min(kRecvChunk, nrecv - c0));
             uint32_t cnt = 0;
             unsigned long long bits = 0ull;
-            for_tile_samples<TS>(
-                sm, J, tx, ty,
+            for_tile_samples<TS, PROF>(
+                sm, J, tx, ty, p_cand,
                 [&](const RecvSm& R, int k, int ix, int iy, float d) {
                     if (PROF) ++p_samples;
                     const uint32_t key = sm.tile[(iy & (TS - 1)) * TS + (ix & (TS - 1))];
@@ -1278,7 +1302,10 @@ __global__ void __launch_bounds__(256) k_raster_test(const WaveDev* __restrict__
             __syncthreads();
         }
     }
-    if (PROF) flush_profile(B, p_samples, p_visits, p_writes, p_culled);
+    if (PROF) {
+        flush_profile(B, p_samples, p_visits, p_writes, p_culled);
+        flush_profile2(B, p_cand, p_tiles, p_dense);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1290,7 +1317,7 @@ __global__ void __launch_bounds__(256) k_raster_map(const WaveDev* __restrict__ 
                                                     const JobDev* __restrict__ jobs, Buffers B)
 {
     __shared__ __align__(16) TileSm<TS> sm;
-    unsigned int p_visits = 0, p_writes = 0, p_culled = 0;
+    unsigned int p_visits = 0, p_writes = 0, p_culled = 0, p_cand = 0, p_dense = 0;
     __shared__ unsigned int s_item;
     const unsigned int n_ne = B.ctr->n_nonempty;
     const int64_t map_cap = W->map_cap_tiles;
@@ -1311,7 +1338,7 @@ __global__ void __launch_bounds__(256) k_raster_map(const WaveDev* __restrict__ 
         tile_receivers(B, W, te, r0, nrecv);
         stage_receivers<TS>(sm, J, B, ls, tx, ty, r0, min(nrecv, kRecvChunk));
         // the tile is stored even when nothing was drawn: its samples read it
-        tile_raster<TS, PROF>(sm, J, B, W, ls, tx, ty, te, r0, nrecv, p_visits, p_writes, p_culled);
+        tile_raster<TS, PROF>(sm, J, B, W, ls, tx, ty, te, r0, nrecv, p_visits, p_writes, p_culled, p_cand, p_dense);
         const uint4* t4 = reinterpret_cast<const uint4*>(sm.tile);
         uint4* dst = reinterpret_cast<uint4*>(B.map + ((size_t)item * (TS * TS)));
         for (int q = tid; q < TS * TS / 4; q += bd) dst[q] = t4[q];

@@ -136,6 +136,10 @@ struct Counters {
     unsigned long long prof_visits;    // texel coverage tests
     unsigned long long prof_writes;    // covered texels (depth atomicMin)
     unsigned long long prof_culled;    // (triangle, tile) pairs skipped by the receiver-plane test
+    unsigned long long prof_cand;      // receiver samples enumerated (marking and testing passes)
+    unsigned long long prof_tiles;     // tiles rasterised
+    unsigned long long prof_dense;     // of which rasterised densely
+    unsigned long long prof_tris;      // (triangle, tile) pairs set up
 };
 
 // Scratch and pools, sized by the host for the largest wave.

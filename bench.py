@@ -35,11 +35,13 @@ METRIC = "shadow sample tests/sec (sun steps x cell samples) at 1 GB300"
 UNIT = "tests/s"
 L2_FLUSH_BYTES = 512 << 20  # > 129 MB L2
 
-# algorithmic ALU work of the tile kernel (roofline): a covered
-# texel costs 3 edge functions (2 FMA each) + barycentric depth (3 FMA) + key
-# conversion and atomicMin (3) = 12 lane-ops; a sample test costs its position
-# (2), projection to texel space and depth (6), floor/clamp/tile check (4),
-# depth compare (2) = 14 lane-ops.
+# algorithmic ALU work of the tile kernel (roofline).  The
+# method's depth map must hold, at every texel a sample reads, the nearest of
+# the triangles covering the texel centre: each such (texel, triangle)
+# fragment costs 3 edge functions (2 FMA each) + barycentric depth (3 FMA) +
+# key conversion and minimum (3) = 12 lane-ops; a sample test costs its
+# position (2), projection to texel space and depth (6), floor/clamp/tile
+# check (4), depth compare (2) = 14 lane-ops.
 OPS_PER_TEXEL_WRITE = 12
 OPS_PER_SAMPLE_TEST = 14
 
@@ -187,7 +189,7 @@ def profiled_traffic(workload: str):
     if it was taken on the current kernels.cu (else None)."""
     import hashlib
     import re
-    path = os.path.join(ROOT, "profiles", f"k_raster_test_{workload}.md")
+    path = os.path.join(ROOT, "profiles", f"k_tile_warp_{workload}.md")
     src = os.path.join(ROOT, "paper_1410_5780_gb300", "csrc", "kernels.cu")
     try:
         m = re.search(r"<!-- traffic: (\{.*?\}) -->", open(path).read())
@@ -389,10 +391,15 @@ def run_ours(args, rank, world, dist):
         sm_max = float(peaks.get("sm_max_mhz", 2070.0))
         props = torch.cuda.get_device_properties(dev)
         alu_peak = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12  # T lane-ops/s
+        # the dominant kernel: k_tile_warp (fused path; stage 2), whose work is
+        # the counters' total less the heavy-tile kernel's share (stage 3)
         raster_launch_ms = stage_ms[2] / max(waves, 1)
-        ops_per_launch = (OPS_PER_TEXEL_WRITE * work["texel_writes"]
-                          + OPS_PER_SAMPLE_TEST * work["sample_tests"]) / max(work["waves"], 1)
+        nw = max(work["waves"], 1)
+        frag = (work["texel_writes"] - work["heavy_texel_writes"]) / nw
+        samp = (work["sample_tests"] - work["heavy_sample_tests"]) / nw
+        ops_per_launch = OPS_PER_TEXEL_WRITE * frag + OPS_PER_SAMPLE_TEST * samp
         achieved = ops_per_launch / (raster_launch_ms * 1e-3) / 1e12
+        kname = "k_tile_warp" if args.path == "fused" else "k_raster_map"
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -401,16 +408,19 @@ def run_ours(args, rank, world, dist):
                            waves_per_step=waves // args.steps, annual_loss_pct=round(e_loss, 4),
                            autotuned={"tile": tuned["tile"], "chunk_steps": chunk,
                                       "bin_capacity": tuned["bin_capacity"]}),
-            "roofline": {"bound": "alu", "kernel": "k_raster_test" if args.path == "fused" else "k_raster_map",
+            "roofline": {"bound": "alu", "kernel": kname,
                          "achieved": achieved, "peak": alu_peak, "unit": "T lane-ops/s",
                          "frac": achieved / alu_peak, "traffic": profiled_traffic(args.workload),
                          "traffic_source": "DRAM read+write bytes of the first timed launch, ncu capture in "
-                                           f"profiles/k_raster_test_{args.workload}.md (null if kernels.cu changed)",
+                                           f"profiles/k_tile_warp_{args.workload}.md (null if kernels.cu changed)",
                          "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "
                                         "(sm_max_mhz of MEASURED_PEAKS.json)",
-                         "work_per_launch": {"texel_writes": work["texel_writes"] / max(work["waves"], 1),
-                                             "sample_tests": work["sample_tests"] / max(work["waves"], 1)},
-                         "avg_launch_ms": raster_launch_ms},
+                         "work_per_launch": {"fragments": frag, "sample_tests": samp,
+                                             "pair_tests": work["pair_tests"] / nw,
+                                             "candidates": work["candidates"] / nw},
+                         "avg_launch_ms": raster_launch_ms,
+                         "heavy_tiles": {"share_of_tiles": work["heavy_tiles"] / max(work["nonempty_tiles"], 1),
+                                         "ms_per_step": float(stage_ms[3] / args.steps)}},
             "stages_ms_per_step": {s: float(stage_ms[i] / args.steps) for i, s in enumerate(pv3d.STAGES)},
             "gpu_launches": int(launches),
             "clocks": clocks,

@@ -130,10 +130,12 @@ typedef struct pv3d_eval_opts {
 /*
  * Stage timings (profile bit 0) and work counts (profile bit 1) of the last
  * pv3d_evaluate run with opts->profile set.  Stages: 0 light window and module setup, 1 binning
- * (triangle bins, scan, receiver lists), 2 tile rasterisation (with the depth
- * tests on the fused path), 3 PV model (with the texel gathers on the map
- * path), 4 Kahan energy sums.  stage_ms sums CUDA-event intervals over the
- * waves, recorded on the evaluation's stream.
+ * (triangle bins, scan, receiver lists), 2 tiles (fused path: the depth tests
+ * of the tiles taken one per warp; map path: tile rasterisation into the map),
+ * 3 the tiles with many receivers or triangles (fused path, one per block,
+ * rasterised in shared memory when they keep many triangles), 4 PV model
+ * (with the texel gathers on the map path), 5 Kahan energy sums.  stage_ms
+ * sums CUDA-event intervals over the waves, recorded on the evaluation's stream.
  */
 typedef struct pv3d_profile {
     int32_t n_stages;
@@ -143,12 +145,19 @@ typedef struct pv3d_profile {
     int32_t reserved0;
     int64_t sample_tests;      /* sample depth tests performed against rasterised tiles */
     int64_t texel_visits;      /* texel-centre coverage tests */
-    int64_t texel_writes;      /* covered texels written with atomicMin */
+    int64_t texel_writes;      /* fragments: (texel read by a sample, triangle covering its centre) pairs
+                                  (rasterised dense tiles: every covered texel) */
     int64_t tris_culled;       /* (triangle, tile) pairs skipped: on or behind every receiver plane */
     int64_t nonempty_tiles;
     int64_t binned_tris;
     int64_t candidates;        /* receiver samples enumerated by the tile kernel (marking and testing) */
     int64_t dense_tiles;       /* tiles rasterised at every texel */
+    int64_t sample_tiles;      /* tiles tested sample by sample against their few triangles (not rasterised) */
+    int64_t pair_tests;        /* (sample, triangle) coverage tests made by the sample-driven test */
+    int64_t heavy_tiles;       /* tiles with many receivers or triangles, taken one per block (stage 3) */
+    int64_t heavy_sample_tests;   /* their share of sample_tests */
+    int64_t heavy_texel_writes;   /* their share of texel_writes */
+    int64_t heavy_why[3];      /* heavy tiles by cause: too many receivers, binned triangles, kept triangles */
 } pv3d_profile;
 
 /*

@@ -83,7 +83,7 @@ struct pv3d_ctx {
     std::map<uint32_t, GenH> gens;
     uint32_t next_id = 1;
     // workspace pools
-    DevBuf lp, win, ms, ms_p, ms_pu, ms_beam, cs_cnt, cs_bits, t_far, t_cnt, t_off, t_cur, t_slot, t_rcnt, t_roff, t_rcur, nonempty, bins, recv, map,
+    DevBuf lp, win, ms, ms_p, ms_pu, ms_beam, cs_cnt, cs_bits, t_far, t_cnt, t_off, t_cur, t_slot, t_rcnt, t_roff, t_rcur, nonempty, heavy, bins, recv, map,
         big, block_sums, ctr, waves, jobs, kahan_mod, kahan_cell, staging;
     int64_t bin_cap = 0, map_cap_tiles = 0, big_cap = 0, recv_cap = 0;
     uint64_t bufgen = 0;  // bumped whenever a pool is reallocated (captured graphs hold its pointers)
@@ -670,7 +670,7 @@ static int ensure_workspace(pv3d_ctx* c, int64_t js, int64_t te, int64_t ms, int
         (rc = ensure(c, c->t_cnt, te * 4)) || (rc = ensure(c, c->t_off, te * 4)) ||
         (rc = ensure(c, c->t_cur, te * 4)) || (rc = ensure(c, c->t_slot, te * 4)) ||
         (rc = ensure(c, c->t_rcnt, te * 4)) || (rc = ensure(c, c->t_roff, te * 4)) ||
-        (rc = ensure(c, c->t_rcur, te * 4)) || (rc = ensure(c, c->nonempty, te * 4)) ||
+        (rc = ensure(c, c->t_rcur, te * 4)) || (rc = ensure(c, c->nonempty, te * 4)) || (rc = ensure(c, c->heavy, te * 4)) ||
         (rc = ensure(c, c->block_sums, scan_tiles * 24)) || (rc = ensure(c, c->ctr, sizeof(Counters))))
         return rc;
     if (fused && want_bits && (rc = ensure(c, c->cs_bits, cs * 8))) return rc;
@@ -705,6 +705,7 @@ static Buffers buffers_of(pv3d_ctx* c)
     B.t_cur = (uint32_t*)c->t_cur.p;
     B.t_slot = (uint32_t*)c->t_slot.p;
     B.nonempty = (uint32_t*)c->nonempty.p;
+    B.heavy = (uint32_t*)c->heavy.p;
     B.t_rcnt = (uint32_t*)c->t_rcnt.p;
     B.t_roff = (uint32_t*)c->t_roff.p;
     B.t_rcur = (uint32_t*)c->t_rcur.p;
@@ -953,7 +954,7 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
     out->waves = (int32_t)waves.size();
     out->nonempty_tiles = (int64_t)hc.stat_nonempty;
     out->binned_tris = (int64_t)hc.stat_bins;
-    out->kernel_launches = (int64_t)waves.size() * kLaunchesPerWave + 1;
+    out->kernel_launches = (int64_t)waves.size() * (es.fused ? kLaunchesPerWave : kLaunchesPerWaveMap) + 1;
     if (es.profile || es.count) {
         pv3d_profile& P = c->last_prof;
         P = pv3d_profile{};
@@ -972,6 +973,12 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
         P.tris_culled = (int64_t)hc.prof_culled;
         P.candidates = (int64_t)hc.prof_cand;
         P.dense_tiles = (int64_t)hc.prof_dense;
+        P.sample_tiles = (int64_t)hc.prof_stiles;
+        P.pair_tests = (int64_t)hc.prof_pairs;
+        P.heavy_tiles = (int64_t)hc.prof_h_tiles;
+        P.heavy_sample_tests = (int64_t)hc.prof_h_samples;
+        P.heavy_texel_writes = (int64_t)hc.prof_h_writes;
+        for (int k = 0; k < 3; ++k) P.heavy_why[k] = (int64_t)hc.prof_heavy_why[k];
         P.nonempty_tiles = (int64_t)hc.stat_nonempty;
         P.binned_tris = (int64_t)hc.stat_bins;
         c->have_prof = true;
@@ -1425,7 +1432,7 @@ extern "C" void pv3d_destroy(pv3d_ctx* c)
     release_buf(c->wave_slot);
     release_buf(c->jobs_slot);
     DevBuf* bufs[] = {&c->lp, &c->win, &c->ms, &c->ms_p, &c->ms_pu, &c->ms_beam, &c->cs_cnt, &c->cs_bits, &c->t_far,
-                      &c->t_cnt, &c->t_off, &c->t_cur, &c->t_slot, &c->t_rcnt, &c->t_roff, &c->t_rcur, &c->nonempty,
+                      &c->t_cnt, &c->t_off, &c->t_cur, &c->t_slot, &c->t_rcnt, &c->t_roff, &c->t_rcur, &c->nonempty, &c->heavy,
                       &c->bins, &c->recv, &c->map, &c->big,
                       &c->block_sums, &c->ctr, &c->waves, &c->jobs, &c->kahan_mod, &c->kahan_cell, &c->staging};
     for (DevBuf* b : bufs) release_buf(*b);

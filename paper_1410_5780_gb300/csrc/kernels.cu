@@ -158,6 +158,29 @@ __device__ __forceinline__ void sample_texel(const ModStep& s, float a, float b,
     iy = min(R - 1, max(0, (int)floorf(ty)));
 }
 
+// Edge function A px + B py + C of a set-up triangle at a texel centre, and
+// its interpolated depth.  The rasteriser, the sample-driven test and the
+// culling masks all evaluate them with this one rounding sequence, so the
+// paths agree bit for bit on which triangles cover a texel and at what depth.
+__device__ __forceinline__ float edge_at(float A, float Bc, float C, float px, float py)
+{
+    return __fmaf_rn(A, px, __fmaf_rn(Bc, py, C));
+}
+__device__ __forceinline__ float depth_at(float w0, float w1, float w2, float e0, float e1, float e2)
+{
+    return __fmaf_rn(w2, e2, __fmaf_rn(w1, e1, __fmul_rn(w0, e0)));
+}
+
+// Is a sample at depth d with bias b behind the stored depth key `key`
+// (Section 2, step 3: shaded iff farther from the sun than the nearest
+// surface; equality is lit)?
+__device__ __forceinline__ bool behind_key(float d, float bias, uint32_t key, float dnear, float qscale,
+                                           int u24)
+{
+    if (u24) return __fmul_rn(__fsub_rn(d, dnear), qscale) > __fmaf_rn(bias, qscale, (float)key);
+    return d > __fadd_rn(okey_inv(key), bias);
+}
+
 // ---------------------------------------------------------------------------
 // k_clear: reset the wave's accumulators (sizes read from the wave descriptor,
 // so the whole wave can be replayed from one captured graph)
@@ -170,6 +193,8 @@ __global__ void k_clear(const WaveDev* __restrict__ W, Buffers B)
         B.ctr->n_big = 0u;
         B.ctr->n_nonempty = 0u;
         B.ctr->raster_next = 0u;
+        B.ctr->n_heavy = 0u;
+        B.ctr->heavy_next = 0u;
     }
     const int64_t nw = 4 * W->tot_js, nt = W->tot_te;
     for (int64_t i = i0; i < nw; i += stride) B.win[i] = 0xFFFFFFFFu;
@@ -812,10 +837,40 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_c(const WaveDev* __restri
 }
 
 // ---------------------------------------------------------------------------
-// per-tile depth rasterisation (shared by the fused and the map kernels)
+// per-tile work: receivers, the sample-driven depth test, and the tile
+// rasteriser (shared by the fused and the map kernels)
 // ---------------------------------------------------------------------------
-constexpr int kRecvChunk = 64;  // receivers staged in shared memory at a time
-constexpr int kTriBatch = 64;   // triangles set up in shared memory at a time
+constexpr int kRecvChunk = 64;  // receivers staged in shared memory at a time (two per lane of one warp)
+constexpr int kTriBatch = 64;   // triangles set up in shared memory at a time by the rasteriser
+constexpr int kMaxTri = 256;    // triangles a block-wide tile may keep for the sample-driven test
+constexpr int kSubSide = 8;     // sub-blocks per tile side in the sample-driven test
+constexpr int kSubBlocks = kSubSide * kSubSide;
+constexpr int kSubWords = kMaxTri / 32;
+static_assert(kRecvChunk == 64 && kTriBatch == 64, "prefix sums take two entries per lane of one warp");
+
+// Inclusive prefix sum over the lanes of a warp.
+__device__ __forceinline__ int warp_incl_scan(int v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane >= off) v += y;
+    }
+    return v;
+}
+
+// Exclusive prefix sum of up to 64 entries, two per lane; called by one full
+// warp.  Returns the total in every lane.
+__device__ __forceinline__ int warp_excl_scan64(int& a0, int& a1)
+{
+    const int s = a0 + a1;
+    const int inc = warp_incl_scan(s);
+    const int ex = inc - s;
+    a1 = ex + a0;
+    a0 = ex;
+    return __shfl_sync(0xffffffffu, inc, 31);
+}
 
 // A triangle set up for one tile: edge functions, scaled depths, the texels
 // it visits (its bounding box, or a range of the marked-texel list).
@@ -824,6 +879,15 @@ struct TriSetup {
     float e0, e1, e2;
     short x0, y0, bw, list;  // list = 1: visit entries [q_beg, q_beg + work) of the marked list
     int q_beg, work;
+};
+
+// A triangle set up for the sample-driven test (48 bytes, three 16-byte loads):
+// edge functions k = 0..2 in tile-local texel coordinates and depths scaled by
+// the inverse doubled area.
+struct TriS {
+    float4 p;  // A0, B0, C0, A1
+    float4 q;  // B1, C1, A2, B2
+    float4 r;  // C2, e0, e1, e2
 };
 
 // q / d for 0 <= q < 2^24 (one float estimate, one correction).
@@ -838,117 +902,219 @@ __device__ __forceinline__ int fdiv(int q, int d, float inv_d)
 
 // A receiver module of the tile, staged in shared memory.  Its samples that
 // may read the tile form the index box [I0, I1] x [J0, J1] (I = cu * n + i,
-// J = cv * n + j); the box is walked as (sample row, cell column) items.
+// J = cv * n + j), walked as (sample row, cell column) items; each item's
+// samples are further clipped to the row's stretch that crosses the tile.
 struct RecvSm {
     ModStep s;
-    float p_over_n;      // sample spacing along the module axes, m
-    float pa, pb, pc;    // receiver depth plane d = pa x + pb y + pc in tile-local texel coordinates
-    float cull_tol;      // plane tolerance (half the bias slack), or -1 if the plane may not cull
-    int cu;              // cells across the module
-    int cell_base;       // first cell of the module in the generator
-    int I0, I1, J0;      // sample-index box (J1 = J0 + rows - 1)
-    int cI0, ncol;       // cell columns of the box
-    int item_pref;       // items of the receivers staged before this one
+    float p_over_n, inv_p;     // sample spacing along the module axes (m) and its inverse
+    float pa, pb, pc;          // receiver depth plane d = pa x + pb y + pc in tile-local texel coordinates
+    float cull_tol;            // plane tolerance (half the bias slack), or -1 if the plane may not cull
+    float cx0, cy0;            // module origin, tile-local texel coordinates
+    float inv_tax, inv_tay;    // inverse texels per metre along the module's U axis (0: no row clip by it)
+    float xlo, xhi, ylo, yhi;  // the tile's texel range, tile-local (open towards the map border)
+    float bx0, bx1, by0, by1;  // the module's texel-space bounding box, tile-local, one texel wider
+    float inv_ncol;
+    int cu;                    // cells across the module
+    int cell_base;             // first cell of the module in the generator
+    int I0, I1, J0;            // sample-index box (J1 = J0 + rows - 1)
+    int cI0, ncol;             // cell columns of the box
+    int item_pref;             // (row, cell column) items of the receivers staged before this one
+};
+
+template <int TS>
+struct RasterSm {
+    uint32_t tile[TS * TS];  // depth keys of the tile
+    uint16_t list[TS * TS];  // marked texels, row-major
+};
+
+// Kept triangles of a tile for the sample-driven test, up to NT of them.
+template <int TS, int NT, bool SEEN>
+struct KeptSm {
+    TriS tri[NT];
+    uint32_t box[NT];                       // texel box x0 | y0 << 8 | x1 << 16 | y1 << 24
+    float dmin[NT];                         // nearest vertex depth
+    float dlim[kSubBlocks];                 // per sub-block: a triangle shades none of its samples
+                                            // unless its nearest depth is below this
+    uint32_t sbm[kSubBlocks][NT / 32];      // per sub-block: triangles that may shade one of its samples
+    uint32_t seen[SEEN ? TS * TS / 32 : 1]; // work counting: texels whose fragments were counted
 };
 
 template <int TS>
 struct TileSm {
-    uint32_t tile[TS * TS];          // depth keys of the tile
+    union {
+        RasterSm<TS> r;
+        KeptSm<TS, kMaxTri, true> s;
+    } u;
     uint32_t mask[TS * TS / 32];     // texels read by some sample (sparse tiles)
     uint32_t row_start[TS + 1];      // start of each row in `list`
-    uint16_t list[TS * TS];          // marked texels, row-major
     RecvSm recv[kRecvChunk];
     int n_recv;                      // receivers staged
     int total_items;                 // (sample row, cell column) items over the staged receivers
-    TriSetup tri[kTriBatch];         // a batch of set-up triangles
+    int n_tri;                       // triangles kept by the sample-driven set-up
+    TriSetup tri[kTriBatch];         // a batch of set-up triangles (rasteriser)
     int chunk_pref[kTriBatch + 1];   // prefix of their 32-texel work chunks
     int any_write;                   // some texel of the tile received a depth
 };
 
-// Stage receivers [r0, r0 + cnt) of tile (tx, ty): sample-index box (the
-// tile corners mapped back onto the module plane, widened by one sample) and
-// depth plane.
+// Stage receiver module m of tile (tx, ty): sample-index box (the tile
+// corners mapped back onto the module plane, widened by one sample), row
+// clipping, bounding box and depth plane.  item_pref receives the receiver's
+// own item count.
+template <int TS>
+__device__ __forceinline__ void stage_one(RecvSm& R, const JobDev& J, const Buffers& B, int ls, int tx, int ty,
+                                          int m)
+{
+    const ModuleDev& M = J.mods[m];
+    const ModStep s = B.ms[J.ms_base + (int64_t)ls * J.n_mods + m];
+    const int n = J.n;
+    const float X0 = (float)(tx * TS), Y0 = (float)(ty * TS);
+    R.s = s;
+    R.p_over_n = __fdiv_rn(M.pitch, (float)n);
+    R.inv_p = 1.f / R.p_over_n;
+    R.cu = M.cu;
+    R.cell_base = M.cell_base;
+    R.cx0 = s.tx0 - X0;
+    R.cy0 = s.ty0 - Y0;
+    R.inv_tax = fabsf(s.tax) > 1e-6f ? 1.f / s.tax : 0.f;
+    R.inv_tay = fabsf(s.tay) > 1e-6f ? 1.f / s.tay : 0.f;
+    R.xlo = tx == 0 ? -FLT_MAX : 0.f;
+    R.xhi = tx == J.tiles_x - 1 ? FLT_MAX : (float)TS;
+    R.ylo = ty == 0 ? -FLT_MAX : 0.f;
+    R.yhi = ty == J.tiles_x - 1 ? FLT_MAX : (float)TS;
+    {
+        const float lu = M.cu * M.pitch, lv = M.cv * M.pitch;
+        float x0 = FLT_MAX, x1 = -FLT_MAX, y0 = FLT_MAX, y1 = -FLT_MAX;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float a = (c & 1) ? lu : 0.f, b = (c & 2) ? lv : 0.f;
+            const float x = R.cx0 + a * s.tax + b * s.tbx, y = R.cy0 + a * s.tay + b * s.tby;
+            x0 = fminf(x0, x); x1 = fmaxf(x1, x);
+            y0 = fminf(y0, y); y1 = fmaxf(y1, y);
+        }
+        R.bx0 = x0 - 1.f; R.bx1 = x1 + 1.f;
+        R.by0 = y0 - 1.f; R.by1 = y1 + 1.f;
+    }
+    int I0 = 0, I1 = M.cu * n - 1, J0 = 0, J1 = M.cv * n - 1;
+    const float det = s.tax * s.tby - s.tay * s.tbx;
+    const bool planar = fabsf(det) > 1e-6f * (fabsf(s.tax * s.tby) + fabsf(s.tay * s.tbx));
+    R.cull_tol = -1.f;
+    R.pa = R.pb = R.pc = 0.f;
+    if (planar) {
+        const float inv_det = 1.f / det;
+        float amin = FLT_MAX, amax = -FLT_MAX, bmin = FLT_MAX, bmax = -FLT_MAX;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float dx = ((c & 1) ? (float)TS : 0.f) - R.cx0;
+            const float dy = ((c & 2) ? (float)TS : 0.f) - R.cy0;
+            const float a = (dx * s.tby - dy * s.tbx) * inv_det;
+            const float b = (dy * s.tax - dx * s.tay) * inv_det;
+            amin = fminf(amin, a); amax = fmaxf(amax, a);
+            bmin = fminf(bmin, b); bmax = fmaxf(bmax, b);
+        }
+        // samples at a = (I + 1/2) p/n: I in [a_min n/p - 1/2, a_max n/p - 1/2], one more each side
+        I0 = max(I0, (int)fmaxf(floorf(amin * R.inv_p - 0.5f) - 1.f, -1.f));
+        I1 = min(I1, (int)fminf(ceilf(amax * R.inv_p - 0.5f) + 1.f, 1e6f));
+        J0 = max(J0, (int)fmaxf(floorf(bmin * R.inv_p - 0.5f) - 1.f, -1.f));
+        J1 = min(J1, (int)fminf(ceilf(bmax * R.inv_p - 0.5f) + 1.f, 1e6f));
+        // depth of the receiver plane over the tile: a triangle lying on or
+        // behind the plane (by less than half the bias slack) shades none
+        // of its samples, so it may be skipped for this receiver
+        R.pa = (s.da * s.tby - s.db * s.tay) * inv_det;
+        R.pb = (s.db * s.tax - s.da * s.tbx) * inv_det;
+        R.pc = s.d0 - R.pa * R.cx0 - R.pb * R.cy0;
+        if (s.cosi > 0.017452406f) R.cull_tol = B.lp[J.js_base + ls].delta * (1.f / 64.f);
+    }
+    R.I0 = I0;
+    R.I1 = I1;
+    R.J0 = J0;
+    R.cI0 = I0 / n;
+    R.ncol = (I0 <= I1) ? I1 / n - I0 / n + 1 : 0;
+    R.inv_ncol = 1.f / (float)max(R.ncol, 1);
+    R.item_pref = (I0 <= I1 && J0 <= J1) ? R.ncol * (J1 - J0 + 1) : 0;  // prefixed by the caller
+}
+
+// Stage receivers [r0, r0 + cnt) of tile (tx, ty) for the whole block (cnt <=
+// kRecvChunk), with their item prefixes.
 template <int TS>
 __device__ void stage_receivers(TileSm<TS>& sm, const JobDev& J, const Buffers& B, int ls, int tx, int ty,
                                 uint64_t r0, int cnt)
 {
     const int tid = threadIdx.x;
-    if (tid < cnt) {
-        const int m = (int)B.recv[r0 + tid];
-        const ModuleDev& M = J.mods[m];
-        RecvSm& R = sm.recv[tid];
-        const ModStep s = B.ms[J.ms_base + (int64_t)ls * J.n_mods + m];
-        const int n = J.n;
-        R.s = s;
-        R.p_over_n = __fdiv_rn(M.pitch, (float)n);
-        R.cu = M.cu;
-        R.cell_base = M.cell_base;
-        int I0 = 0, I1 = M.cu * n - 1, J0 = 0, J1 = M.cv * n - 1;
-        const float det = s.tax * s.tby - s.tay * s.tbx;
-        const bool planar = fabsf(det) > 1e-6f * (fabsf(s.tax * s.tby) + fabsf(s.tay * s.tbx));
-        R.cull_tol = -1.f;
-        if (planar) {
-            float amin = FLT_MAX, amax = -FLT_MAX, bmin = FLT_MAX, bmax = -FLT_MAX;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const float dx = (float)(tx * TS + ((c & 1) ? TS : 0)) - s.tx0;
-                const float dy = (float)(ty * TS + ((c & 2) ? TS : 0)) - s.ty0;
-                const float a = (dx * s.tby - dy * s.tbx) / det;
-                const float b = (dy * s.tax - dx * s.tay) / det;
-                amin = fminf(amin, a); amax = fmaxf(amax, a);
-                bmin = fminf(bmin, b); bmax = fmaxf(bmax, b);
-            }
-            // samples at a = (I + 1/2) p/n: I in [a_min n/p - 1/2, a_max n/p - 1/2], one more each side
-            const float ip = 1.f / R.p_over_n;
-            I0 = max(I0, (int)fmaxf(floorf(amin * ip - 0.5f) - 1.f, -1.f));
-            I1 = min(I1, (int)fminf(ceilf(amax * ip - 0.5f) + 1.f, 1e6f));
-            J0 = max(J0, (int)fmaxf(floorf(bmin * ip - 0.5f) - 1.f, -1.f));
-            J1 = min(J1, (int)fminf(ceilf(bmax * ip - 0.5f) + 1.f, 1e6f));
-            // depth of the receiver plane over the tile: a triangle lying on or
-            // behind the plane (by less than half the bias slack) shades none
-            // of its samples, so it may be skipped for this receiver
-            R.pa = (s.da * s.tby - s.db * s.tay) / det;
-            R.pb = (s.db * s.tax - s.da * s.tbx) / det;
-            R.pc = s.d0 - R.pa * (s.tx0 - (float)(tx * TS)) - R.pb * (s.ty0 - (float)(ty * TS));
-            if (s.cosi > 0.017452406f) R.cull_tol = B.lp[J.js_base + ls].delta * (1.f / 64.f);
-        }
-        R.I0 = I0;
-        R.I1 = I1;
-        R.J0 = J0;
-        R.cI0 = I0 / n;
-        R.ncol = (I0 <= I1) ? I1 / n - I0 / n + 1 : 0;
-        R.item_pref = (I0 <= I1 && J0 <= J1) ? R.ncol * (J1 - J0 + 1) : 0;  // items, prefixed below
-    }
+    if (tid < cnt) stage_one<TS>(sm.recv[tid], J, B, ls, tx, ty, (int)B.recv[r0 + tid]);
     __syncthreads();
-    if (tid == 0) {
-        int acc = 0;
-        for (int r = 0; r < cnt; ++r) {
-            const int c = sm.recv[r].item_pref;
-            sm.recv[r].item_pref = acc;
-            acc += c;
+    if (tid < 32) {
+        const int q0 = 2 * tid, q1 = q0 + 1;
+        int i0 = q0 < cnt ? sm.recv[q0].item_pref : 0, i1 = q1 < cnt ? sm.recv[q1].item_pref : 0;
+        const int ti = warp_excl_scan64(i0, i1);
+        if (q0 < cnt) sm.recv[q0].item_pref = i0;
+        if (q1 < cnt) sm.recv[q1].item_pref = i1;
+        if (tid == 0) {
+            sm.n_recv = cnt;
+            sm.total_items = ti;
         }
-        sm.n_recv = cnt;
-        sm.total_items = acc;
     }
     __syncthreads();
 }
 
-// Receiver of staged item `it`.
-template <int TS>
-__device__ __forceinline__ int recv_of(const TileSm<TS>& sm, int it)
+// Receiver of staged item `it` (items prefixed in item_pref).
+__device__ __forceinline__ int recv_of_item(const RecvSm* recv, int n_recv, int it)
 {
-    int lo = 0, hi = sm.n_recv - 1;
+    int lo = 0, hi = n_recv - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (sm.recv[mid].item_pref <= it) lo = mid; else hi = mid - 1;
+        if (recv[mid].item_pref <= it) lo = mid; else hi = mid - 1;
     }
     return lo;
 }
 
+// Clip [Ib, Ie] to the samples of row Jr whose texel may lie in the tile:
+// the stretch of the row's line a -> (cx0 + a tax + b tbx, cy0 + a tay + b tby)
+// inside the tile's texel range, widened by one sample each side (the exact
+// test is the caller's, per sample).
+__device__ __forceinline__ void row_range(const RecvSm& R, int Jr, int& Ib, int& Ie)
+{
+    const float b = __fmul_rn(__fadd_rn((float)Jr, 0.5f), R.p_over_n);
+    float amin = -FLT_MAX, amax = FLT_MAX;
+    if (R.inv_tax != 0.f) {
+        const float c = fmaf(b, R.s.tbx, R.cx0);
+        const float a0 = (R.xlo - c) * R.inv_tax, a1 = (R.xhi - c) * R.inv_tax;
+        amin = fminf(a0, a1);
+        amax = fmaxf(a0, a1);
+    }
+    if (R.inv_tay != 0.f) {
+        const float c = fmaf(b, R.s.tby, R.cy0);
+        const float a0 = (R.ylo - c) * R.inv_tay, a1 = (R.yhi - c) * R.inv_tay;
+        amin = fmaxf(amin, fminf(a0, a1));
+        amax = fminf(amax, fmaxf(a0, a1));
+    }
+    const float lo = floorf(amin * R.inv_p - 0.5f) - 1.f, hi = ceilf(amax * R.inv_p - 0.5f) + 1.f;
+    Ib = max(Ib, (int)fminf(fmaxf(lo, -1.f), 1e7f));
+    Ie = min(Ie, (int)fmaxf(fminf(hi, 1e7f), -2.f));
+}
+
+// Decode staged item `it`: receiver, sample row Jr, cell (cu, cv), row jj
+// within the cell and the item's sample range [Ib, Ie].
+__device__ __forceinline__ const RecvSm& decode_item(const RecvSm* recv, int n_recv, int it, int n, float inv_n,
+                                                     int& Jr, int& cu, int& cv, int& jj, int& Ib, int& Ie)
+{
+    const RecvSm& R = recv[recv_of_item(recv, n_recv, it)];
+    const int q = it - R.item_pref;
+    const int row = fdiv(q, R.ncol, R.inv_ncol);
+    cu = R.cI0 + q - row * R.ncol;
+    Jr = R.J0 + row;
+    cv = fdiv(Jr, n, inv_n);
+    jj = Jr - cv * n;
+    Ib = max(R.I0, cu * n);
+    Ie = min(R.I1, cu * n + n - 1);
+    row_range(R, Jr, Ib, Ie);
+    return R;
+}
+
 // Visit the samples of the staged receivers that read tile (tx, ty): one
 // thread per (sample row, cell column) item walks the row's samples inside
-// the cell and the box.  f(R, k, ix, iy, d) is called per sample inside the
-// tile (k = j * n + i within the cell); g(R, cu, cv) after each item.
+// the cell, the box and the row's stretch over the tile.  f(R, k, ix, iy, d)
+// is called per sample inside the tile (k = j * n + i within the cell);
+// g(R, cu, cv) after each item.
 template <int TS, bool PROF, typename F, typename G>
 __device__ __forceinline__ void for_tile_samples(const TileSm<TS>& sm, const JobDev& J, int tx, int ty,
                                                  unsigned int& cand, F f, G g)
@@ -957,14 +1123,8 @@ __device__ __forceinline__ void for_tile_samples(const TileSm<TS>& sm, const Job
     const int n = J.n, R_ = J.R;
     const float inv_n = 1.f / (float)n;
     for (int it = threadIdx.x; it < sm.total_items; it += blockDim.x) {
-        const RecvSm& R = sm.recv[recv_of(sm, it)];
-        const int q = it - R.item_pref;
-        const int row = fdiv(q, R.ncol, 1.f / (float)R.ncol);
-        const int cu = R.cI0 + q - row * R.ncol;
-        const int Jr = R.J0 + row;
-        const int cv = fdiv(Jr, n, inv_n);
-        const int jj = Jr - cv * n;
-        const int Ib = max(R.I0, cu * n), Ie = min(R.I1, cu * n + n - 1);
+        int Jr, cu, cv, jj, Ib, Ie;
+        const RecvSm& R = decode_item(sm.recv, sm.n_recv, it, n, inv_n, Jr, cu, cv, jj, Ib, Ie);
         if (PROF) cand += (unsigned int)max(0, Ie - Ib + 1);
         for (int I = Ib; I <= Ie; ++I) {
             float a, b, d;
@@ -979,12 +1139,11 @@ __device__ __forceinline__ void for_tile_samples(const TileSm<TS>& sm, const Job
 
 // Can triangle T (tile-local texel coordinates) shade a sample of a staged
 // receiver?  False only if it lies on or behind every receiver's plane.
-template <int TS>
-__device__ __forceinline__ bool may_shade(const TileSm<TS>& sm, const TriT& T, bool cull_ok)
+__device__ __forceinline__ bool may_shade(const RecvSm* recv, int n_recv, const TriT& T, bool cull_ok)
 {
     if (!cull_ok) return true;
-    for (int r = 0; r < sm.n_recv; ++r) {
-        const RecvSm& R = sm.recv[r];
+    for (int r = 0; r < n_recv; ++r) {
+        const RecvSm& R = recv[r];
         if (R.cull_tol < 0.f) return true;
         float gap = FLT_MAX;
 #pragma unroll
@@ -994,7 +1153,224 @@ __device__ __forceinline__ bool may_shade(const TileSm<TS>& sm, const TriT& T, b
     return false;
 }
 
-// Rasterise the tile's triangles into sm.tile.  Sparse tiles (fewer samples
+// Tile-local texel-centre range [x0, x1] x [y0, y1] of a triangle's bounding box.
+template <int TS>
+__device__ __forceinline__ bool tri_box(const TriT& T, int& x0, int& x1, int& y0, int& y1)
+{
+    const float xmin = fminf(T.x[0], fminf(T.x[1], T.x[2])), xmax = fmaxf(T.x[0], fmaxf(T.x[1], T.x[2]));
+    const float ymin = fminf(T.y[0], fminf(T.y[1], T.y[2])), ymax = fmaxf(T.y[0], fmaxf(T.y[1], T.y[2]));
+    x0 = max(0, (int)ceilf(xmin - 0.5f));
+    x1 = min(TS - 1, (int)floorf(xmax - 0.5f));
+    y0 = max(0, (int)ceilf(ymin - 0.5f));
+    y1 = min(TS - 1, (int)floorf(ymax - 0.5f));
+    return x0 <= x1 && y0 <= y1;
+}
+
+// ---- sample-driven depth test ----------------------------------------------
+// A tile with few triangles is not rasterised: each of its samples tests the
+// triangles that may cover its texel directly.  The sample is shaded iff some
+// triangle covers its texel centre at a depth it is behind -- the same
+// decision as a depth test against the tile's stored minimum (the comparison
+// is monotone in the stored depth), with the same arithmetic per triangle.
+
+// Set up binned triangle t of tile (ox, oy) for the sample-driven test: false
+// if it lies behind every staged receiver or covers no texel centre of the
+// tile.
+template <int TS, bool PROF>
+__device__ __forceinline__ bool setup_tri_s(const JobDev& J, const Buffers& B, const LightParams& lp, int ls, int t,
+                                            float ox, float oy, const RecvSm* recv, int n_recv, bool cull_ok,
+                                            TriS& ts, uint32_t& box, float& dmin, unsigned int& culled)
+{
+    TriT T;
+    tri_texel(J, B, lp, ls, t, T);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { T.x[k] -= ox; T.y[k] -= oy; }
+    if (!may_shade(recv, n_recv, T, cull_ok)) {
+        if (PROF) ++culled;
+        return false;
+    }
+    Edges ed;
+    int x0, x1, y0, y1;
+    if (!make_edges(T, ed) || !tri_box<TS>(T, x0, x1, y0, y1)) return false;
+    const float inv_a = 1.f / ed.area2;
+    ts.p = make_float4(ed.A[0], ed.Bc[0], ed.C[0], ed.A[1]);
+    ts.q = make_float4(ed.Bc[1], ed.C[1], ed.A[2], ed.Bc[2]);
+    ts.r = make_float4(ed.C[2], T.d[0] * inv_a, T.d[1] * inv_a, T.d[2] * inv_a);
+    box = (uint32_t)x0 | ((uint32_t)y0 << 8) | ((uint32_t)x1 << 16) | ((uint32_t)y1 << 24);
+    dmin = fminf(T.d[0], fminf(T.d[1], T.d[2]));
+    return true;
+}
+
+// Per sub-block, the depth below which a triangle must reach to shade one of
+// its samples: the largest over the receivers whose box meets the sub-block
+// of (receiver plane over the sub-block - bias), plus twice the plane
+// tolerance and, for 24-bit depth, the one-step truncation of the stored
+// key.  A sample at depth d is shaded only by a surface nearer than d - bias
+// (less the truncation), and interpolated depths inside a triangle are no
+// nearer than its nearest vertex (up to rounding, which the tolerance
+// covers).  A sub-block with a receiver whose plane may not cull gets no
+// limit; one that no receiver meets gets -inf.  Entries sb = q_begin,
+// q_begin + q_stride, ... are written.
+template <int TS>
+__device__ __forceinline__ void sub_limits(const RecvSm* recv, int n_recv, float* dlim, float q1, int q_begin,
+                                           int q_stride)
+{
+    constexpr int SW = TS / kSubSide;
+    for (int sb = q_begin; sb < kSubBlocks; sb += q_stride) {
+        const float x0 = (float)((sb % kSubSide) * SW), x1 = x0 + (float)SW;
+        const float y0 = (float)((sb / kSubSide) * SW), y1 = y0 + (float)SW;
+        float lim = -FLT_MAX;
+        for (int r = 0; r < n_recv; ++r) {
+            const RecvSm& R = recv[r];
+            if (R.bx1 < x0 || R.bx0 > x1 || R.by1 < y0 || R.by0 > y1) continue;
+            if (R.cull_tol < 0.f) { lim = FLT_MAX; break; }
+            const float pm = R.pc + fmaxf(R.pa * x0, R.pa * x1) + fmaxf(R.pb * y0, R.pb * y1);
+            lim = fmaxf(lim, pm - R.s.bias + 2.f * R.cull_tol + q1);
+        }
+        dlim[sb] = lim;
+    }
+}
+
+// Per sub-block of the tile, the kept triangles that may shade one of its
+// samples: nearest depth below the sub-block's limit, box overlap, then each
+// edge at the sub-block's texel centre farthest inside it (exact: edge_at is
+// monotone in px and py, so a covered texel of the sub-block implies a
+// non-negative value there).  Entries q = q_begin, q_begin + q_stride, ... <
+// 64 * words(n) of sbm are written.
+template <int TS, int WORDS>
+__device__ __forceinline__ void sub_masks(const TriS* tri, const uint32_t* boxes, const float* dmin,
+                                          const float* dlim, uint32_t (*sbm)[WORDS], int n, int q_begin, int q_stride)
+{
+    constexpr int SW = TS / kSubSide;  // sub-block side, texels
+    const int nw = (n + 31) >> 5;
+    for (int q = q_begin; q < kSubBlocks * nw; q += q_stride) {
+        const int sb = q & (kSubBlocks - 1), w = q / kSubBlocks;
+        const int sx = (sb % kSubSide) * SW, sy = (sb / kSubSide) * SW;
+        const float fx0 = (float)sx + 0.5f, fx1 = (float)(sx + SW - 1) + 0.5f;
+        const float fy0 = (float)sy + 0.5f, fy1 = (float)(sy + SW - 1) + 0.5f;
+        const float lim = dlim[sb];
+        uint32_t m = 0u;
+        const int kend = min(32, n - w * 32);
+        for (int k = 0; k < kend; ++k) {
+            const int t = w * 32 + k;
+            if (!(dmin[t] < lim)) continue;
+            const uint32_t bx = boxes[t];
+            const int x0 = bx & 255u, y0 = (bx >> 8) & 255u, x1 = (bx >> 16) & 255u, y1 = bx >> 24;
+            if (x0 > sx + SW - 1 || x1 < sx || y0 > sy + SW - 1 || y1 < sy) continue;
+            const float4 p = tri[t].p, qq = tri[t].q, r = tri[t].r;
+            if (edge_at(p.x, p.y, p.z, p.x > 0.f ? fx1 : fx0, p.y > 0.f ? fy1 : fy0) < 0.f) continue;
+            if (edge_at(p.w, qq.x, qq.y, p.w > 0.f ? fx1 : fx0, qq.x > 0.f ? fy1 : fy0) < 0.f) continue;
+            if (edge_at(qq.z, qq.w, r.x, qq.z > 0.f ? fx1 : fx0, qq.w > 0.f ? fy1 : fy0) < 0.f) continue;
+            m |= 1u << k;
+        }
+        sbm[sb][w] = m;
+    }
+}
+
+// Does kept triangle T cover texel centre (px, py) at a depth that the
+// sample (depth d, bias) is behind?
+__device__ __forceinline__ bool tri_shades(const TriS& T, float px, float py, float d, float bias,
+                                           const LightParams& lp, int u24, bool& covers)
+{
+    const float4 p = T.p, q = T.q, r = T.r;
+    const float w0 = edge_at(p.x, p.y, p.z, px, py);
+    const float w1 = edge_at(p.w, q.x, q.y, px, py);
+    const float w2 = edge_at(q.z, q.w, r.x, px, py);
+    covers = w0 >= 0.f && w1 >= 0.f && w2 >= 0.f;
+    if (!covers) return false;
+    const float depth = depth_at(w0, w1, w2, r.y, r.z, r.w);
+    if (u24) return behind_key(d, bias, depth_store_key(depth, lp, 1), lp.dnear, lp.qscale, 1);
+    return d > __fadd_rn(depth, bias);  // = behind_key(d, bias, okey(depth), ...): okey is invertible
+}
+
+// Depth test of one sample (tile-local texel lx, ly) against the kept
+// triangles of its sub-block; stops at the first that shades it.  With
+// PROF, also counts the fragments a depth map needs at the texel (the kept
+// triangles covering it) once per texel, using the `seen` bitmap.
+template <int TS, int WORDS, bool PROF>
+__device__ __forceinline__ bool sample_test(const TriS* tri, int n_kept, const uint32_t (*sbm)[WORDS], int nw,
+                                            uint32_t* seen, int lx, int ly, float d, float bias,
+                                            const LightParams& lp, int u24, unsigned int& pairs, unsigned int& frags)
+{
+    const int sb = (ly / (TS / kSubSide)) * kSubSide + lx / (TS / kSubSide);
+    const float px = (float)lx + 0.5f, py = (float)ly + 0.5f;
+    const uint32_t* ms = sbm[sb];
+    bool shaded = false;
+    for (int w = 0; w < nw && !shaded; ++w) {
+        uint32_t m = ms[w];
+        while (m) {
+            const int t = (w << 5) | (__ffs(m) - 1);
+            m &= m - 1u;
+            bool cov;
+            if (PROF) ++pairs;
+            if (tri_shades(tri[t], px, py, d, bias, lp, u24, cov)) {
+                shaded = true;
+                break;
+            }
+        }
+    }
+    if (PROF) {
+        // the depth map's fragments at this texel: every kept triangle
+        // covering it (before the sub-block depth limits)
+        const uint32_t bit = 1u << (lx & 31);
+        if (!(atomicOr(&seen[(ly * TS + lx) >> 5], bit) & bit)) {
+            for (int t = 0; t < n_kept; ++t) {
+                bool cov;
+                tri_shades(tri[t], px, py, d, bias, lp, u24, cov);
+                frags += cov ? 1u : 0u;
+            }
+        }
+    }
+    return shaded;
+}
+
+// Depth-test the samples of staged receivers recv[0, n_recv) (items prefixed
+// in item_pref, total_items in all) that read tile (tx, ty) against the kept
+// triangles: items it_begin, it_begin + it_stride, ... one per thread.  Each
+// item adds its shaded count to its (step, cell) tally with one atomic.
+template <int TS, int WORDS, bool PROF>
+__device__ __forceinline__ void test_items(const RecvSm* recv, int n_recv, int total_items, const JobDev& J,
+                                           const LightParams& lp, int u24, int tx, int ty, int it_begin,
+                                           int it_stride, const TriS* tri, int n_kept, const uint32_t (*sbm)[WORDS],
+                                           int nw,
+                                           uint32_t* seen, uint32_t* cnt_row, unsigned long long* bits_row,
+                                           int want_bits, unsigned int& cand, unsigned int& samples,
+                                           unsigned int& pairs, unsigned int& frags)
+{
+    constexpr int SH = TS == 64 ? 6 : 5;
+    const int n = J.n, R_ = J.R;
+    const float inv_n = 1.f / (float)n;
+    for (int it = it_begin; it < total_items; it += it_stride) {
+        int Jr, cu, cv, jj, Ib, Ie;
+        const RecvSm& R = decode_item(recv, n_recv, it, n, inv_n, Jr, cu, cv, jj, Ib, Ie);
+        if (PROF) cand += (unsigned int)max(0, Ie - Ib + 1);
+        uint32_t cnt = 0;
+        unsigned long long bits = 0ull;
+        for (int I = Ib; I <= Ie; ++I) {
+            float a, b, d;
+            int ix, iy;
+            sample_ab(I, Jr, R.p_over_n, a, b);
+            sample_texel(R.s, a, b, R_, ix, iy, d);
+            if ((ix >> SH) != tx || (iy >> SH) != ty) continue;
+            if (PROF) ++samples;
+            if (sample_test<TS, WORDS, PROF>(tri, n_kept, sbm, nw, seen, ix & (TS - 1), iy & (TS - 1), d, R.s.bias,
+                                             lp, u24, pairs, frags)) {
+                ++cnt;
+                const int k = jj * n + (I - cu * n);
+                if (k < 64) bits |= 1ull << k;
+            }
+        }
+        if (cnt) {
+            const int gcell = R.cell_base + cv * R.cu + cu;
+            atomicAdd(&cnt_row[gcell], cnt);
+            if (want_bits) atomicOr(&bits_row[gcell], bits);
+        }
+    }
+}
+
+// ---- tile rasteriser ------------------------------------------------------
+
+// Rasterise the tile's triangles into sm.u.r.tile.  Sparse tiles (fewer samples
 // than half the texels) are rasterised only at the texels their samples
 // read; each triangle then visits its bounding box or the marked texels of
 // its rows, whichever is fewer.  Receivers [r0, r0 + nrecv) must be staged
@@ -1034,16 +1410,20 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
             __syncthreads();
         }
         if (nrecv > kRecvChunk) stage_receivers<TS>(sm, J, B, ls, tx, ty, r0, kRecvChunk);
-        if (tid < TS) {
-            int c = 0;
+        if (tid < 32) {
+            // marked texels per row, prefixed (rows 2 * lane and 2 * lane + 1)
+            int c0 = 0, c1 = 0;
+            const int y0 = 2 * tid, y1 = y0 + 1;
+            if (y0 < TS)
 #pragma unroll
-            for (int w = 0; w < WPR; ++w) c += __popc(sm.mask[tid * WPR + w]);
-            sm.row_start[tid + 1] = c;
-        }
-        __syncthreads();
-        if (tid == 0) {
-            sm.row_start[0] = 0;
-            for (int y = 0; y < TS; ++y) sm.row_start[y + 1] += sm.row_start[y];
+                for (int w = 0; w < WPR; ++w) c0 += __popc(sm.mask[y0 * WPR + w]);
+            if (y1 < TS)
+#pragma unroll
+                for (int w = 0; w < WPR; ++w) c1 += __popc(sm.mask[y1 * WPR + w]);
+            const int tot = warp_excl_scan64(c0, c1);
+            if (y0 < TS) sm.row_start[y0] = c0;
+            if (y1 < TS) sm.row_start[y1] = c1;
+            if (tid == 0) sm.row_start[TS] = tot;
         }
         __syncthreads();
         for (int q = tid; q < TS * WPR; q += bd) {
@@ -1053,14 +1433,14 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
             for (int w2 = 0; w2 < w; ++w2) pos += __popc(sm.mask[y * WPR + w2]);
             while (bits) {
                 const int bit = __ffs(bits) - 1;
-                sm.list[pos++] = (uint16_t)(y * TS + w * 32 + bit);
+                sm.u.r.list[pos++] = (uint16_t)(y * TS + w * 32 + bit);
                 bits &= bits - 1;
             }
         }
         __syncthreads();
         n_need = (int)sm.row_start[TS];
     }
-    uint4* t4 = reinterpret_cast<uint4*>(sm.tile);
+    uint4* t4 = reinterpret_cast<uint4*>(sm.u.r.tile);
     for (int q = tid; q < TS * TS / 4; q += bd) t4[q] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
     if (tid == 0) sm.any_write = 0;
     __syncthreads();
@@ -1084,38 +1464,33 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
 #pragma unroll
             for (int k = 0; k < 3; ++k) { T.x[k] -= ox; T.y[k] -= oy; }
             Edges ed;
-            if (!may_shade<TS>(sm, T, cull_ok)) {
+            int x0, x1, y0, y1;
+            if (!may_shade(sm.recv, sm.n_recv, T, cull_ok)) {
                 if (PROF) ++culled;
-            } else if (make_edges(T, ed)) {
-                const float xmin = fminf(T.x[0], fminf(T.x[1], T.x[2])), xmax = fmaxf(T.x[0], fmaxf(T.x[1], T.x[2]));
-                const float ymin = fminf(T.y[0], fminf(T.y[1], T.y[2])), ymax = fmaxf(T.y[0], fmaxf(T.y[1], T.y[2]));
-                const int x0 = max(0, (int)ceilf(xmin - 0.5f)), x1 = min(TS - 1, (int)floorf(xmax - 0.5f));
-                const int y0 = max(0, (int)ceilf(ymin - 0.5f)), y1 = min(TS - 1, (int)floorf(ymax - 0.5f));
-                if (x0 <= x1 && y0 <= y1) {
-                    const float inv_a = 1.f / ed.area2;
+            } else if (make_edges(T, ed) && tri_box<TS>(T, x0, x1, y0, y1)) {
+                const float inv_a = 1.f / ed.area2;
 #pragma unroll
-                    for (int k = 0; k < 3; ++k) { S.A[k] = ed.A[k]; S.Bc[k] = ed.Bc[k]; S.C[k] = ed.C[k]; }
-                    S.e0 = T.d[0] * inv_a; S.e1 = T.d[1] * inv_a; S.e2 = T.d[2] * inv_a;
-                    S.x0 = (short)x0; S.y0 = (short)y0; S.bw = (short)(x1 - x0 + 1);
-                    const int n_px = (x1 - x0 + 1) * (y1 - y0 + 1);
-                    const int q_beg = dense ? 0 : (int)sm.row_start[y0];
-                    const int q_end = dense ? 0 : (int)sm.row_start[y1 + 1];
-                    if (dense || n_px <= q_end - q_beg) {
-                        S.list = 0; S.q_beg = 0; S.work = n_px;
-                    } else {
-                        S.list = 1; S.q_beg = q_beg; S.work = q_end - q_beg;
-                    }
+                for (int k = 0; k < 3; ++k) { S.A[k] = ed.A[k]; S.Bc[k] = ed.Bc[k]; S.C[k] = ed.C[k]; }
+                S.e0 = T.d[0] * inv_a; S.e1 = T.d[1] * inv_a; S.e2 = T.d[2] * inv_a;
+                S.x0 = (short)x0; S.y0 = (short)y0; S.bw = (short)(x1 - x0 + 1);
+                const int n_px = (x1 - x0 + 1) * (y1 - y0 + 1);
+                const int q_beg = dense ? 0 : (int)sm.row_start[y0];
+                const int q_end = dense ? 0 : (int)sm.row_start[y1 + 1];
+                if (dense || n_px <= q_end - q_beg) {
+                    S.list = 0; S.q_beg = 0; S.work = n_px;
+                } else {
+                    S.list = 1; S.q_beg = q_beg; S.work = q_end - q_beg;
                 }
             }
         }
         __syncthreads();
-        if (tid == 0) {
-            int acc = 0;
-            for (int k = 0; k < nb; ++k) {
-                sm.chunk_pref[k] = acc;
-                acc += (sm.tri[k].work + 31) >> 5;
-            }
-            sm.chunk_pref[nb] = acc;
+        if (tid < 32) {
+            int c0 = 2 * tid < nb ? (sm.tri[2 * tid].work + 31) >> 5 : 0;
+            int c1 = 2 * tid + 1 < nb ? (sm.tri[2 * tid + 1].work + 31) >> 5 : 0;
+            const int tot = warp_excl_scan64(c0, c1);
+            if (2 * tid < nb) sm.chunk_pref[2 * tid] = c0;
+            if (2 * tid + 1 < nb) sm.chunk_pref[2 * tid + 1] = c1;
+            if (tid == 0) sm.chunk_pref[nb] = tot;
         }
         __syncthreads();
         // each warp takes a contiguous range of chunks: one search, then the
@@ -1147,7 +1522,7 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
                 if (q >= work) continue;
                 int ix, iy;
                 if (is_list) {
-                    const int p = sm.list[q_beg + q];
+                    const int p = sm.u.r.list[q_beg + q];
                     ix = p & (TS - 1);
                     iy = p >> SH;
                     if (ix < x0 || ix >= x0 + bw) continue;
@@ -1157,13 +1532,13 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
                     ix = x0 + q - ry * bw;
                     if (!dense && !(sm.mask[iy * WPR + (ix >> 5)] & (1u << (ix & 31)))) continue;
                 }
-                const float px = ix + 0.5f, py = iy + 0.5f;
-                const float w0 = A0 * px + B0 * py + C0;
-                const float w1 = A1 * px + B1 * py + C1;
-                const float w2 = A2 * px + B2 * py + C2;
+                const float px = (float)ix + 0.5f, py = (float)iy + 0.5f;
+                const float w0 = edge_at(A0, B0, C0, px, py);
+                const float w1 = edge_at(A1, B1, C1, px, py);
+                const float w2 = edge_at(A2, B2, C2, px, py);
                 if (PROF) ++visits;
                 if (w0 >= 0.f && w1 >= 0.f && w2 >= 0.f) {
-                    atomicMin(&sm.tile[iy * TS + ix], depth_store_key(w0 * e0 + w1 * e1 + w2 * e2, lp, u24));
+                    atomicMin(&sm.u.r.tile[iy * TS + ix], depth_store_key(depth_at(w0, w1, w2, e0, e1, e2), lp, u24));
                     wrote = true;
                     if (PROF) ++writes;
                 }
@@ -1197,18 +1572,39 @@ __device__ __forceinline__ void flush_profile(const Buffers& B, unsigned int sam
 }
 
 __device__ __forceinline__ void flush_profile2(const Buffers& B, unsigned int cand, unsigned int tiles,
-                                               unsigned int dense)
+                                               unsigned int dense, unsigned int stiles, unsigned int pairs)
 {
 #pragma unroll
     for (int off = 16; off; off >>= 1) {
         cand += __shfl_xor_sync(0xffffffffu, cand, off);
         tiles += __shfl_xor_sync(0xffffffffu, tiles, off);
         dense += __shfl_xor_sync(0xffffffffu, dense, off);
+        stiles += __shfl_xor_sync(0xffffffffu, stiles, off);
+        pairs += __shfl_xor_sync(0xffffffffu, pairs, off);
     }
     if ((threadIdx.x & 31) == 0) {
         atomicAdd(&B.ctr->prof_cand, (unsigned long long)cand);
         atomicAdd(&B.ctr->prof_tiles, (unsigned long long)tiles);
         atomicAdd(&B.ctr->prof_dense, (unsigned long long)dense);
+        atomicAdd(&B.ctr->prof_stiles, (unsigned long long)stiles);
+        atomicAdd(&B.ctr->prof_pairs, (unsigned long long)pairs);
+    }
+}
+
+// The heavy-tile kernel's share of the work counters (also in the totals).
+__device__ __forceinline__ void flush_heavy(const Buffers& B, unsigned int samples, unsigned int writes,
+                                            unsigned int tiles)
+{
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        samples += __shfl_xor_sync(0xffffffffu, samples, off);
+        writes += __shfl_xor_sync(0xffffffffu, writes, off);
+        tiles += __shfl_xor_sync(0xffffffffu, tiles, off);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&B.ctr->prof_h_samples, (unsigned long long)samples);
+        atomicAdd(&B.ctr->prof_h_writes, (unsigned long long)writes);
+        atomicAdd(&B.ctr->prof_h_tiles, (unsigned long long)tiles);
     }
 }
 
@@ -1236,28 +1632,207 @@ __device__ __forceinline__ void tile_receivers(const Buffers& B, const WaveDev* 
 }
 
 // ---------------------------------------------------------------------------
-// k_raster_test: fused path -- rasterise the tile in shared memory, then
-// depth-test every sample that reads it; shaded counts go to (step, cell)
+// k_tile_warp: fused path -- one warp per non-empty tile: the depth test of
+// every sample that reads the tile, sample by sample against the tile's kept
+// triangles; shaded counts go to (step, cell).  A warp takes a tile with at
+// most kWarpRecv receivers, kWarpBins binned and kWarpTri kept triangles;
+// it lists any other tile for k_raster_test.  A tile is a small work item
+// (hundreds of samples, a few triangles): one warp each keeps many tiles in
+// flight per SM, which hides the chain of dependent loads that starts a tile.
 // ---------------------------------------------------------------------------
+constexpr int kWarpTri = 64;
+constexpr int kWarpWords = kWarpTri / 32;
+constexpr int kWarpRecv = 8;
+constexpr int kWarpBins = 512;
+constexpr int kTileWarps = 8;
+
 template <int TS, bool PROF>
-__global__ void __launch_bounds__(256) k_raster_test(const WaveDev* __restrict__ W,
-                                                     const JobDev* __restrict__ jobs, Buffers B)
+struct WarpSm {
+    KeptSm<TS, kWarpTri, PROF> k;
+    RecvSm recv[kWarpRecv];
+};
+
+template <int TS, bool PROF>
+__global__ void __launch_bounds__(kTileWarps * 32, 4) k_tile_warp(const WaveDev* __restrict__ W,
+                                                                  const JobDev* __restrict__ jobs, Buffers B)
 {
-    __shared__ __align__(16) TileSm<TS> sm;
-    unsigned int p_samples = 0, p_visits = 0, p_writes = 0, p_culled = 0, p_cand = 0, p_dense = 0, p_tiles = 0;
-    __shared__ unsigned int s_item;
+    __shared__ __align__(16) WarpSm<TS, PROF> sm_all[kTileWarps];
+    unsigned int p_samples = 0, p_writes = 0, p_culled = 0, p_cand = 0, p_tiles = 0, p_stiles = 0, p_pairs = 0;
+    unsigned int p_hr = 0, p_hb = 0, p_ht = 0;
+    const int lane = threadIdx.x & 31;
+    WarpSm<TS, PROF>& sm = sm_all[threadIdx.x >> 5];
     const unsigned int n_ne = B.ctr->n_nonempty;
     const int nj = W->n_jobs;
     const int want_bits = W->want_bits;
     const int u24 = W->depth_u24;
-    const int tid = threadIdx.x;
-    for (;;) {
-        if (tid == 0) s_item = atomicAdd(&B.ctr->raster_next, 1u);
-        __syncthreads();
-        const unsigned int item = s_item;
-        __syncthreads();
-        if (item >= n_ne) break;
+    const uint64_t bin_cap = (uint64_t)W->bin_cap;
+    unsigned int next = 0;
+    if (lane == 0) next = atomicAdd(&B.ctr->raster_next, 1u);
+    next = __shfl_sync(0xffffffffu, next, 0);
+    while (next < n_ne) {
+        const unsigned int item = next;
+        if (lane == 0) next = atomicAdd(&B.ctr->raster_next, 1u);  // claim the following tile now
         const uint32_t te = B.nonempty[item];
+        int j, ls, tx, ty;
+        decode_tile(jobs, nj, te, j, ls, tx, ty);
+        const JobDev& J = jobs[j];
+        uint64_t r0;
+        int nrecv;
+        tile_receivers(B, W, te, r0, nrecv);
+        const uint64_t off = B.t_off[te];
+        uint64_t cnt = B.t_cnt[te];
+        if (off + cnt > bin_cap) cnt = off < bin_cap ? bin_cap - off : 0;
+        bool heavy = nrecv > kWarpRecv || cnt > (uint64_t)kWarpBins;
+        if (PROF && lane == 0) {
+            if (nrecv > kWarpRecv) ++p_hr;
+            else if (heavy) ++p_hb;
+        }
+        if (!heavy) {
+            const LightParams& lp = B.lp[J.js_base + ls];
+            if (lane < nrecv) stage_one<TS>(sm.recv[lane], J, B, ls, tx, ty, (int)B.recv[r0 + lane]);
+            if (PROF)
+                for (int q = lane; q < TS * TS / 32; q += 32) sm.k.seen[q] = 0u;
+            __syncwarp();
+            const int c = lane < nrecv ? sm.recv[lane].item_pref : 0;
+            const int inc = warp_incl_scan(c);
+            const int total = __shfl_sync(0xffffffffu, inc, 31);
+            if (lane < nrecv) sm.recv[lane].item_pref = inc - c;
+            sub_limits<TS>(sm.recv, nrecv, sm.k.dlim, u24 ? 1.f / lp.qscale : 0.f, lane, 32);
+            __syncwarp();
+            const float ox = (float)(tx * TS), oy = (float)(ty * TS);
+            int n = 0;
+            for (uint64_t b0 = 0; b0 < cnt && n <= kWarpTri; b0 += 32) {
+                TriS ts;
+                uint32_t box = 0u;
+                float dmin = 0.f;
+                const bool keep = b0 + lane < cnt &&
+                                  setup_tri_s<TS, PROF>(J, B, lp, ls, (int)B.bins[off + b0 + lane], ox, oy, sm.recv,
+                                                        nrecv, true, ts, box, dmin, p_culled);
+                const unsigned int bal = __ballot_sync(0xffffffffu, keep);
+                const int slot = n + __popc(bal & ((1u << lane) - 1u));
+                if (keep && slot < kWarpTri) {
+                    sm.k.tri[slot] = ts;
+                    sm.k.box[slot] = box;
+                    sm.k.dmin[slot] = dmin;
+                }
+                n += __popc(bal);
+            }
+            heavy = n > kWarpTri;
+            if (PROF && lane == 0 && heavy) ++p_ht;
+            if (!heavy && n > 0) {
+                __syncwarp();
+                sub_masks<TS, kWarpWords>(sm.k.tri, sm.k.box, sm.k.dmin, sm.k.dlim, sm.k.sbm, n, lane, 32);
+                __syncwarp();
+                const int C = J.n_cells;
+                test_items<TS, kWarpWords, PROF>(sm.recv, nrecv, total, J, lp, u24, tx, ty, lane, 32, sm.k.tri, n,
+                                                 sm.k.sbm, (n + 31) >> 5, sm.k.seen,
+                                                 B.cs_cnt + J.cs_base + (int64_t)ls * C,
+                                                 B.cs_bits + J.cs_base + (int64_t)ls * C, want_bits, p_cand,
+                                                 p_samples, p_pairs, p_writes);
+            }
+            if (PROF && lane == 0 && !heavy) { ++p_tiles; ++p_stiles; }
+        }
+        if (heavy && lane == 0) {
+            const unsigned int pos = atomicAdd(&B.ctr->n_heavy, 1u);
+            if (pos < (uint64_t)W->tot_te) B.heavy[pos] = te;
+        }
+        __syncwarp();  // the warp's shared memory may be reused
+        next = __shfl_sync(0xffffffffu, next, 0);
+    }
+    if (PROF) {
+        flush_profile(B, p_samples, 0u, p_writes, p_culled);
+        flush_profile2(B, p_cand, p_tiles, 0u, p_stiles, p_pairs);
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+            p_hr += __shfl_xor_sync(0xffffffffu, p_hr, off);
+            p_hb += __shfl_xor_sync(0xffffffffu, p_hb, off);
+            p_ht += __shfl_xor_sync(0xffffffffu, p_ht, off);
+        }
+        if (lane == 0) {
+            atomicAdd(&B.ctr->prof_heavy_why[0], (unsigned long long)p_hr);
+            atomicAdd(&B.ctr->prof_heavy_why[1], (unsigned long long)p_hb);
+            atomicAdd(&B.ctr->prof_heavy_why[2], (unsigned long long)p_ht);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// k_raster_test: fused path, the tiles k_tile_warp listed -- one CTA per
+// tile.  A tile keeping at most kMaxTri triangles after culling is tested
+// sample by sample against them; a tile with more is rasterised in shared
+// memory first, then its samples read the tile.
+// ---------------------------------------------------------------------------
+
+// Set up the tile's binned triangles that may shade a staged receiver and
+// cover a texel centre of the tile, for the whole block.  Returns how many
+// were kept, or -1 if more than kMaxTri were (the tile is then rasterised).
+template <int TS, bool PROF>
+__device__ int setup_sample_tris(TileSm<TS>& sm, const JobDev& J, const Buffers& B, const WaveDev* W,
+                                 const LightParams& lp, int ls, int tx, int ty, int64_t te, bool cull_ok,
+                                 unsigned int& culled)
+{
+    const int tid = threadIdx.x, lane = tid & 31;
+    const float ox = (float)(tx * TS), oy = (float)(ty * TS);
+    const uint64_t off = B.t_off[te];
+    uint64_t cnt = B.t_cnt[te];
+    const uint64_t cap = (uint64_t)W->bin_cap;
+    if (off + cnt > cap) cnt = off < cap ? cap - off : 0;
+    if (PROF)
+        for (int q = tid; q < TS * TS / 32; q += blockDim.x) sm.u.s.seen[q] = 0u;
+    if (cull_ok) sub_limits<TS>(sm.recv, sm.n_recv, sm.u.s.dlim, W->depth_u24 ? 1.f / lp.qscale : 0.f, tid,
+                                blockDim.x);
+    else
+        for (int q = tid; q < kSubBlocks; q += blockDim.x) sm.u.s.dlim[q] = FLT_MAX;
+    for (uint64_t b0 = 0; b0 < cnt; b0 += blockDim.x) {
+        TriS ts;
+        uint32_t box = 0u;
+        float dmin = 0.f;
+        const bool keep = b0 + tid < cnt &&
+                          setup_tri_s<TS, PROF>(J, B, lp, ls, (int)B.bins[off + b0 + tid], ox, oy, sm.recv,
+                                                sm.n_recv, cull_ok, ts, box, dmin, culled);
+        const unsigned int bal = __ballot_sync(0xffffffffu, keep);
+        int base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&sm.n_tri, __popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (keep) {
+            const int slot = base + __popc(bal & ((1u << lane) - 1u));
+            if (slot < kMaxTri) {
+                sm.u.s.tri[slot] = ts;
+                sm.u.s.box[slot] = box;
+                sm.u.s.dmin[slot] = dmin;
+            }
+        }
+    }
+    __syncthreads();
+    const int n = sm.n_tri;
+    return n > kMaxTri ? -1 : n;
+}
+
+template <int TS, bool PROF>
+__global__ void __launch_bounds__(256, 4) k_raster_test(const WaveDev* __restrict__ W,
+                                                        const JobDev* __restrict__ jobs, Buffers B)
+{
+    __shared__ __align__(16) TileSm<TS> sm;
+    unsigned int p_samples = 0, p_visits = 0, p_writes = 0, p_culled = 0, p_cand = 0, p_dense = 0, p_tiles = 0;
+    unsigned int p_stiles = 0, p_pairs = 0;
+    __shared__ unsigned int s_item[2];
+    const unsigned int n_ne = min(B.ctr->n_heavy, (unsigned int)W->tot_te);
+    const int nj = W->n_jobs;
+    const int want_bits = W->want_bits;
+    const int u24 = W->depth_u24;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_item[0] = atomicAdd(&B.ctr->heavy_next, 1u);
+    __syncthreads();
+    for (int par = 0;; par ^= 1) {
+        // the next tile is claimed while this one runs; the barriers inside
+        // the tile publish it
+        const unsigned int item = s_item[par];
+        if (item >= n_ne) break;
+        if (tid == 0) {
+            s_item[par ^ 1] = atomicAdd(&B.ctr->heavy_next, 1u);
+            sm.n_tri = 0;
+        }
+        const uint32_t te = B.heavy[item];
         int j, ls, tx, ty;
         decode_tile(jobs, nj, te, j, ls, tx, ty);
         const JobDev& J = jobs[j];
@@ -1266,45 +1841,64 @@ __global__ void __launch_bounds__(256) k_raster_test(const WaveDev* __restrict__
         tile_receivers(B, W, te, r0, nrecv);
         stage_receivers<TS>(sm, J, B, ls, tx, ty, r0, min(nrecv, kRecvChunk));
         if (PROF && tid == 0) ++p_tiles;
-        if (tile_raster<TS, PROF>(sm, J, B, W, ls, tx, ty, te, r0, nrecv, p_visits, p_writes, p_culled, p_cand,
-                                  p_dense) == 0)
-            continue;
         const LightParams& lp = B.lp[J.js_base + ls];
         const int C = J.n_cells;
         uint32_t* cnt_row = B.cs_cnt + J.cs_base + (int64_t)ls * C;
         unsigned long long* bits_row = B.cs_bits + J.cs_base + (int64_t)ls * C;
-        for (int c0 = 0; c0 < nrecv; c0 += kRecvChunk) {
-            if (c0 > 0) stage_receivers<TS>(sm, J, B, ls, tx, ty, r0 + c0, min(kRecvChunk, nrecv - c0));
-            uint32_t cnt = 0;
-            unsigned long long bits = 0ull;
-            for_tile_samples<TS, PROF>(
-                sm, J, tx, ty, p_cand,
-                [&](const RecvSm& R, int k, int ix, int iy, float d) {
-                    if (PROF) ++p_samples;
-                    const uint32_t key = sm.tile[(iy & (TS - 1)) * TS + (ix & (TS - 1))];
-                    if (key == kEmpty) return;
-                    const bool shaded = u24 ? (d - lp.dnear) * lp.qscale > (float)key + R.s.bias * lp.qscale
-                                            : d > okey_inv(key) + R.s.bias;
-                    if (shaded) {
-                        ++cnt;
-                        if (k < 64) bits |= 1ull << k;
+        const int nt = setup_sample_tris<TS, PROF>(sm, J, B, W, lp, ls, tx, ty, te, nrecv <= kRecvChunk, p_culled);
+        if (nt >= 0) {
+            // sample-driven test (no triangle kept: every sample of the tile is lit)
+            if (PROF && tid == 0) ++p_stiles;
+            if (nt > 0) {
+                sub_masks<TS, kSubWords>(sm.u.s.tri, sm.u.s.box, sm.u.s.dmin, sm.u.s.dlim, sm.u.s.sbm, nt, tid,
+                                         blockDim.x);
+                __syncthreads();
+                for (int c0 = 0; c0 < nrecv; c0 += kRecvChunk) {
+                    if (c0 > 0) {
+                        __syncthreads();
+                        stage_receivers<TS>(sm, J, B, ls, tx, ty, r0 + c0, min(kRecvChunk, nrecv - c0));
                     }
-                },
-                [&](const RecvSm& R, int cu, int cv) {
-                    if (cnt) {
-                        const int gcell = R.cell_base + cv * R.cu + cu;
-                        atomicAdd(&cnt_row[gcell], cnt);
-                        if (want_bits) atomicOr(&bits_row[gcell], bits);
-                    }
-                    cnt = 0;
-                    bits = 0ull;
-                });
-            __syncthreads();
+                    test_items<TS, kSubWords, PROF>(sm.recv, sm.n_recv, sm.total_items, J, lp, u24, tx, ty, tid,
+                                                    blockDim.x, sm.u.s.tri, nt, sm.u.s.sbm, (nt + 31) >> 5,
+                                                    sm.u.s.seen, cnt_row, bits_row, want_bits, p_cand, p_samples,
+                                                    p_pairs, p_writes);
+                }
+            }
+        } else if (tile_raster<TS, PROF>(sm, J, B, W, ls, tx, ty, te, r0, nrecv, p_visits, p_writes, p_culled,
+                                         p_cand, p_dense) != 0) {
+            for (int c0 = 0; c0 < nrecv; c0 += kRecvChunk) {
+                if (c0 > 0) stage_receivers<TS>(sm, J, B, ls, tx, ty, r0 + c0, min(kRecvChunk, nrecv - c0));
+                uint32_t cnt = 0;
+                unsigned long long bits = 0ull;
+                for_tile_samples<TS, PROF>(
+                    sm, J, tx, ty, p_cand,
+                    [&](const RecvSm& R, int k, int ix, int iy, float d) {
+                        if (PROF) ++p_samples;
+                        const uint32_t key = sm.u.r.tile[(iy & (TS - 1)) * TS + (ix & (TS - 1))];
+                        if (key == kEmpty) return;
+                        if (behind_key(d, R.s.bias, key, lp.dnear, lp.qscale, u24)) {
+                            ++cnt;
+                            if (k < 64) bits |= 1ull << k;
+                        }
+                    },
+                    [&](const RecvSm& R, int cu, int cv) {
+                        if (cnt) {
+                            const int gcell = R.cell_base + cv * R.cu + cu;
+                            atomicAdd(&cnt_row[gcell], cnt);
+                            if (want_bits) atomicOr(&bits_row[gcell], bits);
+                        }
+                        cnt = 0;
+                        bits = 0ull;
+                    });
+                __syncthreads();
+            }
         }
+        __syncthreads();  // the tile's shared memory may be reused
     }
     if (PROF) {
         flush_profile(B, p_samples, p_visits, p_writes, p_culled);
-        flush_profile2(B, p_cand, p_tiles, p_dense);
+        flush_profile2(B, p_cand, p_tiles, p_dense, p_stiles, p_pairs);
+        flush_heavy(B, p_samples, p_writes, p_tiles);
     }
 }
 
@@ -1339,7 +1933,7 @@ __global__ void __launch_bounds__(256) k_raster_map(const WaveDev* __restrict__ 
         stage_receivers<TS>(sm, J, B, ls, tx, ty, r0, min(nrecv, kRecvChunk));
         // the tile is stored even when nothing was drawn: its samples read it
         tile_raster<TS, PROF>(sm, J, B, W, ls, tx, ty, te, r0, nrecv, p_visits, p_writes, p_culled, p_cand, p_dense);
-        const uint4* t4 = reinterpret_cast<const uint4*>(sm.tile);
+        const uint4* t4 = reinterpret_cast<const uint4*>(sm.u.r.tile);
         uint4* dst = reinterpret_cast<uint4*>(B.map + ((size_t)item * (TS * TS)));
         for (int q = tid; q < TS * TS / 4; q += bd) dst[q] = t4[q];
         __syncthreads();
@@ -1531,10 +2125,7 @@ __global__ void __launch_bounds__(kPvThreads) k_sample(const WaveDev* __restrict
                     const uint32_t slot = B.t_slot[te];
                     if (slot < map_cap) {
                         const uint32_t key = B.map[((size_t)slot << (2 * sh)) + ((iy & tmask) << sh) + (ix & tmask)];
-                        if (key != kEmpty) {
-                            if (u24) shaded = (d - lp.dnear) * lp.qscale > (float)key + s.bias * lp.qscale;
-                            else shaded = d > okey_inv(key) + s.bias;
-                        }
+                        if (key != kEmpty) shaded = behind_key(d, s.bias, key, lp.dnear, lp.qscale, u24);
                     }
                 }
             }
@@ -1650,8 +2241,14 @@ template <int TS, bool PROF>
 static void launch_tile_kernels(const WaveDev* W, const JobDev* d_jobs, const Buffers& b, const LaunchCfg& cfg)
 {
     const int sm = cfg.sm_count;
-    if (cfg.fused) k_raster_test<TS, PROF><<<sm * 4, 256, 0, cfg.stream>>>(W, d_jobs, b);
-    else k_raster_map<TS, PROF><<<sm * 4, 256, 0, cfg.stream>>>(W, d_jobs, b);
+    if (cfg.fused) {
+        k_tile_warp<TS, PROF><<<sm * 4, kTileWarps * 32, 0, cfg.stream>>>(W, d_jobs, b);
+        if (cfg.ev) cudaEventRecord(cfg.ev[3], cfg.stream);
+        k_raster_test<TS, PROF><<<sm * 4, 256, 0, cfg.stream>>>(W, d_jobs, b);
+    } else {
+        k_raster_map<TS, PROF><<<sm * 4, 256, 0, cfg.stream>>>(W, d_jobs, b);
+        if (cfg.ev) cudaEventRecord(cfg.ev[3], cfg.stream);
+    }
 }
 
 cudaError_t launch_wave(const WaveDev* d_wave, const JobDev* d_jobs, const Buffers& b, const LaunchCfg& cfg,
@@ -1683,12 +2280,12 @@ cudaError_t launch_wave(const WaveDev* d_wave, const JobDev* d_jobs, const Buffe
         if (cfg.profile) launch_tile_kernels<64, true>(W, d_jobs, b, cfg);
         else launch_tile_kernels<64, false>(W, d_jobs, b, cfg);
     }
-    if (cfg.ev) cudaEventRecord(cfg.ev[3], st);
+    if (cfg.ev) cudaEventRecord(cfg.ev[4], st);
     if (cfg.fused) k_pv<<<sm * 32, kPvThreads, 0, st>>>(W, d_jobs, b);
     else k_sample<<<sm * 16, kPvThreads, 0, st>>>(W, d_jobs, b);
-    if (cfg.ev) cudaEventRecord(cfg.ev[4], st);
-    k_epilogue<<<sm * 8, 256, 0, st>>>(W, d_jobs, b);
     if (cfg.ev) cudaEventRecord(cfg.ev[5], st);
+    k_epilogue<<<sm * 8, 256, 0, st>>>(W, d_jobs, b);
+    if (cfg.ev) cudaEventRecord(cfg.ev[6], st);
     return cudaGetLastError();
 }
 

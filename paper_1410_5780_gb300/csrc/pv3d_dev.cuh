@@ -123,6 +123,8 @@ struct Counters {
     unsigned int n_nonempty;
     unsigned int raster_next;
     unsigned int overflow;  // bit 0 bins, bit 1 map tiles, bit 2 big list, bit 3 receivers
+    unsigned int n_heavy;     // tiles k_tile_warp hands to k_raster_test
+    unsigned int heavy_next;  // k_raster_test's work counter
     unsigned long long tot_bins;
     unsigned long long tot_recv;
     unsigned long long need_recv;
@@ -140,6 +142,12 @@ struct Counters {
     unsigned long long prof_tiles;     // tiles rasterised
     unsigned long long prof_dense;     // of which rasterised densely
     unsigned long long prof_tris;      // (triangle, tile) pairs set up
+    unsigned long long prof_stiles;    // tiles tested sample by sample (not rasterised)
+    unsigned long long prof_pairs;     // (sample, triangle) coverage tests of the sample-driven test
+    unsigned long long prof_h_samples;  // of prof_samples, prof_writes and prof_tiles: the share of the
+    unsigned long long prof_h_writes;   //   kernel that takes the heavy tiles (one block per tile)
+    unsigned long long prof_h_tiles;
+    unsigned long long prof_heavy_why[3];  // heavy because of: receivers, binned triangles, kept triangles
 };
 
 // Scratch and pools, sized by the host for the largest wave.
@@ -161,6 +169,7 @@ struct Buffers {
     uint32_t* t_roff;        // [tot_te]
     uint32_t* t_rcur;        // [tot_te]
     uint32_t* nonempty;      // [tot_te]
+    uint32_t* heavy;         // [tot_te]  tiles listed for the CTA-per-tile kernel (fused path)
     uint32_t* bins;          // [bin_cap]   triangle ids
     uint32_t* recv;          // [recv_cap]  receiver module ids
     uint32_t* map;           // [map_cap_tiles << (2 * tile_sh)]  (map path)
@@ -176,11 +185,12 @@ struct LaunchCfg {
     int fused;    // 1: k_raster_test + k_pv; 0: k_raster_map + k_sample
     int profile;  // counting kernels
     cudaStream_t stream;
-    cudaEvent_t* ev;  // NULL, or 6 events recorded at the stage boundaries of the wave
+    cudaEvent_t* ev;  // NULL, or kStages + 1 events recorded at the stage boundaries of the wave
 };
 
-constexpr int kStages = 5;           // setup, bin, raster(+test), pv/sample, epilogue
-constexpr int kLaunchesPerWave = 15;  // kernels launch_wave starts
+constexpr int kStages = 6;  // setup, bin, tile (warp per tile / map raster), heavy tiles, pv/sample, epilogue
+constexpr int kLaunchesPerWave = 16;     // kernels launch_wave starts (fused path)
+constexpr int kLaunchesPerWaveMap = 15;  // (map path)
 
 cudaError_t launch_wave(const WaveDev* d_wave, const JobDev* d_jobs, const Buffers& b,
                         const LaunchCfg& cfg, int64_t tot_te_host);

@@ -72,10 +72,12 @@ class pv3d_profile(C.Structure):
                 ("device_ms", C.c_float), ("reserved0", C.c_int32), ("sample_tests", C.c_int64),
                 ("texel_visits", C.c_int64), ("texel_writes", C.c_int64), ("tris_culled", C.c_int64),
                 ("nonempty_tiles", C.c_int64), ("binned_tris", C.c_int64), ("candidates", C.c_int64),
-                ("dense_tiles", C.c_int64)]
+                ("dense_tiles", C.c_int64), ("sample_tiles", C.c_int64), ("pair_tests", C.c_int64),
+                ("heavy_tiles", C.c_int64), ("heavy_sample_tests", C.c_int64), ("heavy_texel_writes", C.c_int64),
+                ("heavy_why", C.c_int64 * 3)]
 
 
-STAGES = ("setup", "bin", "raster", "pv", "epilogue")
+STAGES = ("setup", "bin", "raster", "heavy", "pv", "epilogue")
 
 
 class pv3d_result(C.Structure):
@@ -294,7 +296,10 @@ class Context:
         d = {f"{name}_ms": p.stage_ms[k] for k, name in enumerate(STAGES)}
         d.update(waves=p.waves, device_ms=p.device_ms, sample_tests=p.sample_tests, texel_visits=p.texel_visits,
                  texel_writes=p.texel_writes, tris_culled=p.tris_culled, nonempty_tiles=p.nonempty_tiles,
-                 binned_tris=p.binned_tris, candidates=p.candidates, dense_tiles=p.dense_tiles)
+                 binned_tris=p.binned_tris, candidates=p.candidates, dense_tiles=p.dense_tiles,
+                 sample_tiles=p.sample_tiles, pair_tests=p.pair_tests, heavy_tiles=p.heavy_tiles,
+                 heavy_sample_tests=p.heavy_sample_tests, heavy_texel_writes=p.heavy_texel_writes,
+                 heavy_why=list(p.heavy_why))
         return d
 
     def submit(self, gen_id: int, n: int = 3, map_res: int = 0, step_begin: int = 0, step_end: int = 0,

@@ -83,7 +83,7 @@ struct pv3d_ctx {
     std::map<uint32_t, GenH> gens;
     uint32_t next_id = 1;
     // workspace pools
-    DevBuf lp, win, ms, ms_p, ms_pu, ms_beam, cs_cnt, cs_bits, t_far, t_cnt, t_off, t_cur, t_slot, t_rcnt, t_roff, t_rcur, nonempty, heavy, bins, recv, map,
+    DevBuf lp, win, ms, ms_p, ms_pu, ms_beam, cs_cnt, cs_bits, t_far, t_cnt, t_off, t_cur, t_slot, t_rcnt, t_roff, t_rcur, nonempty, heavy, bins, pairs, recv, map,
         big, block_sums, ctr, waves, jobs, kahan_mod, kahan_cell, staging;
     int64_t bin_cap = 0, map_cap_tiles = 0, big_cap = 0, recv_cap = 0;
     uint64_t bufgen = 0;  // bumped whenever a pool is reallocated (captured graphs hold its pointers)
@@ -677,7 +677,8 @@ static int ensure_workspace(pv3d_ctx* c, int64_t js, int64_t te, int64_t ms, int
     if (c->bin_cap == 0) c->bin_cap = 1 << 22;
     if (c->big_cap == 0) c->big_cap = 1 << 18;
     if (c->recv_cap == 0) c->recv_cap = 1 << 20;
-    if ((rc = ensure(c, c->bins, c->bin_cap * 4)) || (rc = ensure(c, c->big, c->big_cap * 8)) ||
+    if ((rc = ensure(c, c->bins, c->bin_cap * 4)) || (rc = ensure(c, c->pairs, c->bin_cap * 8)) ||
+        (rc = ensure(c, c->big, c->big_cap * 8)) ||
         (rc = ensure(c, c->recv, c->recv_cap * 4)))
         return rc;
     if (!fused) {
@@ -711,6 +712,7 @@ static Buffers buffers_of(pv3d_ctx* c)
     B.t_rcur = (uint32_t*)c->t_rcur.p;
     B.recv = (uint32_t*)c->recv.p;
     B.bins = (uint32_t*)c->bins.p;
+    B.pairs = (uint2*)c->pairs.p;
     B.map = (uint32_t*)c->map.p;
     B.big = (uint2*)c->big.p;
     B.block_sums = (unsigned long long*)c->block_sums.p;
@@ -1033,7 +1035,7 @@ struct pv3d_ctx::Request {
 static int64_t per_step_scratch(const GenH& g, const EvalSetup& es)
 {
     const int64_t tiles = (int64_t)(es.R / es.tile) * (es.R / es.tile);
-    return tiles * 4 * 9 + (int64_t)g.C * 12 + (int64_t)g.M * (sizeof(ModStep) + 12) + sizeof(LightParams) + 16;
+    return tiles * 4 * 10 + (int64_t)g.C * 12 + (int64_t)g.M * (sizeof(ModStep) + 12) + sizeof(LightParams) + 16;
 }
 
 static int64_t request_bytes(const GenH& g, const EvalSetup& es, const pv3d_result* out, int64_t S)
@@ -1433,7 +1435,7 @@ extern "C" void pv3d_destroy(pv3d_ctx* c)
     release_buf(c->jobs_slot);
     DevBuf* bufs[] = {&c->lp, &c->win, &c->ms, &c->ms_p, &c->ms_pu, &c->ms_beam, &c->cs_cnt, &c->cs_bits, &c->t_far,
                       &c->t_cnt, &c->t_off, &c->t_cur, &c->t_slot, &c->t_rcnt, &c->t_roff, &c->t_rcur, &c->nonempty, &c->heavy,
-                      &c->bins, &c->recv, &c->map, &c->big,
+                      &c->bins, &c->pairs, &c->recv, &c->map, &c->big,
                       &c->block_sums, &c->ctr, &c->waves, &c->jobs, &c->kahan_mod, &c->kahan_cell, &c->staging};
     for (DevBuf* b : bufs) release_buf(*b);
     if (c->h_stage) cudaFreeHost(c->h_stage);

@@ -8,12 +8,13 @@
 //   k_modsetup    each module at each step in texel space; marks the raster
 //                 tiles that hold samples, their far plane (max sample depth +
 //                 bias) and counts the receiver modules per tile
-//   k_bin<0>      count (triangle, tile) pairs: vertex transform batched over
-//                 the job's steps (the lanes of a warp take consecutive steps of
-//                 one triangle), cull against occupied tiles and far planes
-//   k_bin_big<0>  same for triangles that span many tiles, one warp each
+//   k_bin         (triangle, tile) pairs: vertex transform batched over the
+//                 job's steps (one warp per meshlet and step), cull against
+//                 occupied tiles and far planes; pairs counted per tile and
+//                 appended to the wave's pair list
+//   k_bin_big     same for triangles that span many tiles, one warp each
 //   k_scan_*      bin offsets, the list of non-empty tiles, receiver offsets
-//   k_bin<1>, k_bin_big<1>, k_recv_fill   write the bins and receiver lists
+//   k_scatter, k_recv_fill   write the bins and receiver lists
 //   k_raster_test one CTA per non-empty tile: shared-memory depth tile filled
 //                 at the texels the tile's samples read (texel-centre coverage,
 //                 atomicMin of order-preserving depth keys -- Fig. 3: the depth
@@ -158,6 +159,18 @@ __device__ __forceinline__ void sample_texel(const ModStep& s, float a, float b,
     iy = min(R - 1, max(0, (int)floorf(ty)));
 }
 
+// Inclusive prefix sum over the lanes of a warp.
+__device__ __forceinline__ int warp_incl_scan(int v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, v, off);
+        if (lane >= off) v += y;
+    }
+    return v;
+}
+
 // Edge function A px + B py + C of a set-up triangle at a texel centre, and
 // its interpolated depth.  The rasteriser, the sample-driven test and the
 // culling masks all evaluate them with this one rounding sequence, so the
@@ -194,6 +207,7 @@ __global__ void k_clear(const WaveDev* __restrict__ W, Buffers B)
         B.ctr->n_nonempty = 0u;
         B.ctr->raster_next = 0u;
         B.ctr->n_heavy = 0u;
+        B.ctr->n_pairs = 0ull;
         B.ctr->heavy_next = 0u;
     }
     const int64_t nw = 4 * W->tot_js, nt = W->tot_te;
@@ -532,23 +546,34 @@ __device__ __forceinline__ bool rect_overlap(const Edges& e, float x0, float x1,
 }
 
 // ---------------------------------------------------------------------------
-// k_bin<FILL>: (triangle, tile) pairs, vertex transform batched over steps
+// k_bin: (triangle, tile) pairs in one pass -- vertex transform batched over
+// steps; each pair is counted into its tile and appended to the wave's pair
+// list, which k_scatter distributes into the bins after the scan
 // ---------------------------------------------------------------------------
-template <int FILL>
-__device__ __forceinline__ void bin_tile(const Buffers& B, int64_t te, uint32_t dkey, uint32_t tri,
-                                         const WaveDev* W)
+
+// Append this lane's pairs (te[q], tri) for the set bits q of `valid` to the
+// pair list: one atomic per warp.  Called by all 32 lanes together.
+__device__ __forceinline__ void append_pairs(const Buffers& B, const WaveDev* W, const uint32_t* te, uint32_t valid,
+                                             uint32_t tri)
 {
-    uint32_t far = B.t_far[te];
-    if (!(dkey < far)) return;  // unoccupied tile (far 0) or triangle wholly behind
-    if (FILL == 0) {
-        atomicAdd(&B.t_cnt[te], 1u);
-    } else {
-        uint32_t pos = atomicAdd(&B.t_cur[te], 1u);
-        if (pos < (uint64_t)W->bin_cap) B.bins[pos] = tri;
-    }
+    const int lane = threadIdx.x & 31;
+    const int c = __popc(valid);
+    const int inc = warp_incl_scan(c);
+    const int tot = __shfl_sync(0xffffffffu, inc, 31);
+    if (tot == 0) return;
+    unsigned long long base = 0;
+    if (lane == 31) base = atomicAdd(&B.ctr->n_pairs, (unsigned long long)tot);
+    base = __shfl_sync(0xffffffffu, base, 31);
+    unsigned long long pos = base + (unsigned long long)(inc - c);
+    const uint64_t cap = (uint64_t)W->bin_cap;
+#pragma unroll
+    for (int q = 0; q < kBigTiles; ++q)
+        if (valid & (1u << q)) {
+            if (pos < cap) B.pairs[pos] = make_uint2(te[q], tri);
+            ++pos;
+        }
 }
 
-template <int FILL>
 __global__ void __launch_bounds__(256) k_bin(const WaveDev* __restrict__ W, const JobDev* __restrict__ jobs,
                                              Buffers B)
 {
@@ -558,7 +583,8 @@ __global__ void __launch_bounds__(256) k_bin(const WaveDev* __restrict__ W, cons
     // far planes of the tiles it covers; if no tile can receive a shadow from
     // it, the 32 triangles are skipped together.  Then each lane bins one
     // triangle.  Generator module triangles follow the scene's, in groups of
-    // 32, without the box test.
+    // 32, without the box test.  A triangle over more than kBigTiles tiles is
+    // listed for k_bin_big.
     const int64_t tot = W->tot_tri;
     const int nj = W->n_jobs;
     const int sh = W->tile_sh;
@@ -577,6 +603,7 @@ __global__ void __launch_bounds__(256) k_bin(const WaveDev* __restrict__ W, cons
         if (!lp.valid) continue;
         const int64_t te0 = J.te_base + (int64_t)ls * J.tiles_x * J.tiles_x;
         int t;
+        bool act;
         if (mi < J.n_ml) {
             const float4 lo = J.ml_box[2 * mi], hi = J.ml_box[2 * mi + 1];
             float xmin = FLT_MAX, xmax = -FLT_MAX, ymin = FLT_MAX, ymax = -FLT_MAX, dmin = FLT_MAX;
@@ -610,46 +637,57 @@ __global__ void __launch_bounds__(256) k_bin(const WaveDev* __restrict__ W, cons
             }
             if (!keep) continue;
             t = mi * 32 + lane;
-            if (t >= J.n_tris) continue;
+            act = t < J.n_tris;
         } else {
             t = J.n_tris + (mi - J.n_ml) * 32 + lane;
-            if (t >= J.n_tris + J.n_mtris) continue;
+            act = t < J.n_tris + J.n_mtris;
         }
-        TriT T;
-        tri_texel(J, B, lp, ls, t, T);
-        Edges e;
-        if (!make_edges(T, e)) continue;
-        float xmin = fminf(T.x[0], fminf(T.x[1], T.x[2])), xmax = fmaxf(T.x[0], fmaxf(T.x[1], T.x[2]));
-        float ymin = fminf(T.y[0], fminf(T.y[1], T.y[2])), ymax = fmaxf(T.y[0], fmaxf(T.y[1], T.y[2]));
-        // covered texel centres (ix + 0.5) lie in [xmin, xmax]
-        if (!(xmax >= 0.5f && ymax >= 0.5f && xmin <= R - 0.5f && ymin <= R - 0.5f)) continue;
-        int ix0 = max(0, (int)ceilf(xmin - 0.5f)), ix1 = min(R - 1, (int)floorf(xmax - 0.5f));
-        int iy0 = max(0, (int)ceilf(ymin - 0.5f)), iy1 = min(R - 1, (int)floorf(ymax - 0.5f));
-        if (ix0 > ix1 || iy0 > iy1) continue;
-        float dmin = fminf(T.d[0], fminf(T.d[1], T.d[2]));
-        uint32_t dkey = depth_store_key(dmin, lp, u24);
-        int tx0 = ix0 >> sh, tx1 = ix1 >> sh, ty0 = iy0 >> sh, ty1 = iy1 >> sh;
-        int ntiles = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
-        if (ntiles > kBigTiles) {
-            if (FILL == 0) {
-                unsigned int pos = atomicAdd(&B.ctr->n_big, 1u);
-                if (pos < (uint64_t)W->big_cap) B.big[pos] = make_uint2((uint32_t)t, (uint32_t)js);
+        // per lane: the tiles its triangle may shade (at most kBigTiles), in
+        // registers until the warp appends them together
+        uint32_t te[kBigTiles];
+        uint32_t valid = 0u;
+        if (act) {
+            TriT T;
+            tri_texel(J, B, lp, ls, t, T);
+            Edges e;
+            const float xmin = fminf(T.x[0], fminf(T.x[1], T.x[2])), xmax = fmaxf(T.x[0], fmaxf(T.x[1], T.x[2]));
+            const float ymin = fminf(T.y[0], fminf(T.y[1], T.y[2])), ymax = fmaxf(T.y[0], fmaxf(T.y[1], T.y[2]));
+            // covered texel centres (ix + 0.5) lie in [xmin, xmax]
+            const int ix0 = max(0, (int)ceilf(xmin - 0.5f)), ix1 = min(R - 1, (int)floorf(xmax - 0.5f));
+            const int iy0 = max(0, (int)ceilf(ymin - 0.5f)), iy1 = min(R - 1, (int)floorf(ymax - 0.5f));
+            if (make_edges(T, e) && xmax >= 0.5f && ymax >= 0.5f && xmin <= R - 0.5f && ymin <= R - 0.5f &&
+                ix0 <= ix1 && iy0 <= iy1) {
+                const uint32_t dkey = depth_store_key(fminf(T.d[0], fminf(T.d[1], T.d[2])), lp, u24);
+                const int tx0 = ix0 >> sh, tx1 = ix1 >> sh, ty0 = iy0 >> sh, ty1 = iy1 >> sh;
+                const int wx = tx1 - tx0 + 1, ntiles = wx * (ty1 - ty0 + 1);
+                if (ntiles > kBigTiles) {
+                    const unsigned int pos = atomicAdd(&B.ctr->n_big, 1u);
+                    if (pos < (uint64_t)W->big_cap) B.big[pos] = make_uint2((uint32_t)t, (uint32_t)js);
+                } else {
+#pragma unroll
+                    for (int q = 0; q < kBigTiles; ++q) {
+                        te[q] = 0u;
+                        if (q >= ntiles) continue;
+                        const int ty = ty0 + q / wx, tx = tx0 + q % wx;
+                        if (ntiles > 1 && !rect_overlap(e, tx * TS + 0.5f, tx * TS + TS - 0.5f, ty * TS + 0.5f,
+                                                        ty * TS + TS - 0.5f))
+                            continue;
+                        const uint32_t x = (uint32_t)(te0 + (int64_t)ty * J.tiles_x + tx);
+                        // unoccupied tile (far 0) or triangle wholly behind its far plane
+                        if (!(dkey < B.t_far[x])) continue;
+                        atomicAdd(&B.t_cnt[x], 1u);
+                        te[q] = x;
+                        valid |= 1u << q;
+                    }
+                }
             }
-            continue;
         }
-        for (int ty = ty0; ty <= ty1; ++ty) {
-            for (int tx = tx0; tx <= tx1; ++tx) {
-                if (ntiles > 1 &&
-                    !rect_overlap(e, tx * TS + 0.5f, tx * TS + TS - 0.5f, ty * TS + 0.5f, ty * TS + TS - 0.5f))
-                    continue;
-                bin_tile<FILL>(B, te0 + (int64_t)ty * J.tiles_x + tx, dkey, (uint32_t)t, W);
-            }
-        }
+        append_pairs(B, W, te, valid, (uint32_t)t);
     }
 }
 
-// Triangles spanning more than kBigTiles tiles: one warp per triangle.
-template <int FILL>
+// Triangles spanning more than kBigTiles tiles: one warp per triangle, lanes
+// over its tiles.
 __global__ void __launch_bounds__(256) k_bin_big(const WaveDev* __restrict__ W,
                                                  const JobDev* __restrict__ jobs, Buffers B)
 {
@@ -685,12 +723,36 @@ __global__ void __launch_bounds__(256) k_bin_big(const WaveDev* __restrict__ W,
         int wx = tx1 - tx0 + 1;
         int ntiles = wx * (ty1 - ty0 + 1);
         int64_t te0 = J.te_base + (int64_t)ls * J.tiles_x * J.tiles_x;
-        for (int q = lane; q < ntiles; q += 32) {
-            int tx = tx0 + q % wx, ty = ty0 + q / wx;
-            if (!rect_overlap(ed, tx * TS + 0.5f, tx * TS + TS - 0.5f, ty * TS + 0.5f, ty * TS + TS - 0.5f))
-                continue;
-            bin_tile<FILL>(B, te0 + (int64_t)ty * J.tiles_x + tx, dkey, (uint32_t)t, W);
+        for (int q0 = 0; q0 < ntiles; q0 += 32) {
+            const int q = q0 + lane;
+            uint32_t te[kBigTiles];
+            uint32_t valid = 0u;
+            te[0] = 0u;
+            if (q < ntiles) {
+                const int tx = tx0 + q % wx, ty = ty0 + q / wx;
+                const uint32_t x = (uint32_t)(te0 + (int64_t)ty * J.tiles_x + tx);
+                if (rect_overlap(ed, tx * TS + 0.5f, tx * TS + TS - 0.5f, ty * TS + 0.5f, ty * TS + TS - 0.5f) &&
+                    dkey < B.t_far[x]) {
+                    atomicAdd(&B.t_cnt[x], 1u);
+                    te[0] = x;
+                    valid = 1u;
+                }
+            }
+            append_pairs(B, W, te, valid, (uint32_t)t);
         }
+    }
+}
+
+// After the scan: each (tile, triangle) pair to its place in the tile's bin.
+__global__ void __launch_bounds__(256) k_scatter(const WaveDev* __restrict__ W, Buffers B)
+{
+    const unsigned long long np = min(B.ctr->n_pairs, (unsigned long long)W->bin_cap);
+    const uint64_t cap = (uint64_t)W->bin_cap;
+    for (unsigned long long i = blockIdx.x * (unsigned long long)blockDim.x + threadIdx.x; i < np;
+         i += (unsigned long long)gridDim.x * blockDim.x) {
+        const uint2 p = B.pairs[i];
+        const uint32_t pos = atomicAdd(&B.t_cur[p.x], 1u);
+        if (pos < cap) B.bins[pos] = p.y;
     }
 }
 
@@ -847,18 +909,6 @@ constexpr int kSubSide = 8;     // sub-blocks per tile side in the sample-driven
 constexpr int kSubBlocks = kSubSide * kSubSide;
 constexpr int kSubWords = kMaxTri / 32;
 static_assert(kRecvChunk == 64 && kTriBatch == 64, "prefix sums take two entries per lane of one warp");
-
-// Inclusive prefix sum over the lanes of a warp.
-__device__ __forceinline__ int warp_incl_scan(int v)
-{
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int off = 1; off < 32; off <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, v, off);
-        if (lane >= off) v += y;
-    }
-    return v;
-}
 
 // Exclusive prefix sum of up to 64 entries, two per lane; called by one full
 // warp.  Returns the total in every lane.
@@ -1614,12 +1664,12 @@ __device__ __forceinline__ void decode_tile(const JobDev* jobs, int nj, uint32_t
 {
     j = job_of(nj, te, [&](int q) { return jobs[q].te_base; });
     const JobDev& J = jobs[j];
-    const int64_t lte = te - J.te_base;
-    const int tps = J.tiles_x * J.tiles_x;
+    const uint32_t lte = (uint32_t)(te - J.te_base);  // tile entries of a wave are numbered in 32 bits
+    const uint32_t tps = (uint32_t)(J.tiles_x * J.tiles_x);
     ls = (int)(lte / tps);
-    const int tl = (int)(lte % tps);
-    tx = tl % J.tiles_x;
-    ty = tl / J.tiles_x;
+    const uint32_t tl = lte - (uint32_t)ls * tps;
+    ty = (int)(tl / (uint32_t)J.tiles_x);
+    tx = (int)(tl - (uint32_t)ty * (uint32_t)J.tiles_x);
 }
 
 // Receivers of a tile entry, clamped to the receiver pool.
@@ -1642,9 +1692,9 @@ __device__ __forceinline__ void tile_receivers(const Buffers& B, const WaveDev* 
 // ---------------------------------------------------------------------------
 constexpr int kWarpTri = 64;
 constexpr int kWarpWords = kWarpTri / 32;
-constexpr int kWarpRecv = 8;
+constexpr int kWarpRecv = 16;
 constexpr int kWarpBins = 512;
-constexpr int kTileWarps = 8;
+constexpr int kTileWarps = 4;   // warps per block; 8 blocks per SM
 
 template <int TS, bool PROF>
 struct WarpSm {
@@ -1653,7 +1703,7 @@ struct WarpSm {
 };
 
 template <int TS, bool PROF>
-__global__ void __launch_bounds__(kTileWarps * 32, 4) k_tile_warp(const WaveDev* __restrict__ W,
+__global__ void __launch_bounds__(kTileWarps * 32, 8) k_tile_warp(const WaveDev* __restrict__ W,
                                                                   const JobDev* __restrict__ jobs, Buffers B)
 {
     __shared__ __align__(16) WarpSm<TS, PROF> sm_all[kTileWarps];
@@ -2242,7 +2292,7 @@ static void launch_tile_kernels(const WaveDev* W, const JobDev* d_jobs, const Bu
 {
     const int sm = cfg.sm_count;
     if (cfg.fused) {
-        k_tile_warp<TS, PROF><<<sm * 4, kTileWarps * 32, 0, cfg.stream>>>(W, d_jobs, b);
+        k_tile_warp<TS, PROF><<<sm * 8, kTileWarps * 32, 0, cfg.stream>>>(W, d_jobs, b);
         if (cfg.ev) cudaEventRecord(cfg.ev[3], cfg.stream);
         k_raster_test<TS, PROF><<<sm * 4, 256, 0, cfg.stream>>>(W, d_jobs, b);
     } else {
@@ -2264,13 +2314,12 @@ cudaError_t launch_wave(const WaveDev* d_wave, const JobDev* d_jobs, const Buffe
     k_light<<<sm, 128, 0, st>>>(W, d_jobs, b);
     k_modsetup<<<sm * 8, 256, 0, st>>>(W, d_jobs, b);
     if (cfg.ev) cudaEventRecord(cfg.ev[1], st);
-    k_bin<0><<<sm * 16, 256, 0, st>>>(W, d_jobs, b);
-    k_bin_big<0><<<sm * 8, 256, 0, st>>>(W, d_jobs, b);
+    k_bin<<<sm * 16, 256, 0, st>>>(W, d_jobs, b);
+    k_bin_big<<<sm * 8, 256, 0, st>>>(W, d_jobs, b);
     k_scan_a<<<sm * 2, kScanThreads, 0, st>>>(W, b);
     k_scan_b<<<1, kScanThreads, 0, st>>>(W, b);
     k_scan_c<<<sm * 2, kScanThreads, 0, st>>>(W, b);
-    k_bin<1><<<sm * 16, 256, 0, st>>>(W, d_jobs, b);
-    k_bin_big<1><<<sm * 8, 256, 0, st>>>(W, d_jobs, b);
+    k_scatter<<<sm * 8, 256, 0, st>>>(W, b);
     k_recv_fill<<<sm * 8, 256, 0, st>>>(W, d_jobs, b);
     if (cfg.ev) cudaEventRecord(cfg.ev[2], st);
     if (cfg.tile == 32) {

@@ -124,6 +124,7 @@ struct Counters {
     unsigned int raster_next;
     unsigned int overflow;  // bit 0 bins, bit 1 map tiles, bit 2 big list, bit 3 receivers
     unsigned int n_heavy;     // tiles k_tile_warp hands to k_raster_test
+    unsigned long long n_pairs;  // (tile, triangle) pairs appended by the binning kernels
     unsigned int heavy_next;  // k_raster_test's work counter
     unsigned long long tot_bins;
     unsigned long long tot_recv;
@@ -171,6 +172,7 @@ struct Buffers {
     uint32_t* nonempty;      // [tot_te]
     uint32_t* heavy;         // [tot_te]  tiles listed for the CTA-per-tile kernel (fused path)
     uint32_t* bins;          // [bin_cap]   triangle ids
+    uint2* pairs;            // [bin_cap]   (tile entry, triangle) pairs in binning order
     uint32_t* recv;          // [recv_cap]  receiver module ids
     uint32_t* map;           // [map_cap_tiles << (2 * tile_sh)]  (map path)
     uint2* big;              // [big_cap]  (triangle, js)
@@ -189,8 +191,8 @@ struct LaunchCfg {
 };
 
 constexpr int kStages = 6;  // setup, bin, tile (warp per tile / map raster), heavy tiles, pv/sample, epilogue
-constexpr int kLaunchesPerWave = 16;     // kernels launch_wave starts (fused path)
-constexpr int kLaunchesPerWaveMap = 15;  // (map path)
+constexpr int kLaunchesPerWave = 15;     // kernels launch_wave starts (fused path)
+constexpr int kLaunchesPerWaveMap = 14;  // (map path)
 
 cudaError_t launch_wave(const WaveDev* d_wave, const JobDev* d_jobs, const Buffers& b,
                         const LaunchCfg& cfg, int64_t tot_te_host);

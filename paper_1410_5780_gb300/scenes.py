@@ -586,6 +586,57 @@ def make_random_small(seed: int, n_mods: int = 6, n_boxes: int = 5, n_steps: int
     return Workload(f"random{seed}{'_trk' if tracked else ''}", scene, gen, sun, poses, n, map_res)
 
 
+def make_canopy(seed: int, tiny_modules: bool = False, n_steps: int = 8, n: int = 3, map_res: int = 256,
+                cells: int = 30, holes: float = 0.4, lat: float = 40.0) -> Workload:
+    """A finely triangulated canopy with random holes (a pergola or a tree
+    crown stand-in) over either four tilted modules or a field of 1-cell
+    modules 0.2 m apart.  On a coarse map one raster tile holds hundreds of
+    the canopy's triangles, or dozens of receiver modules: the workloads the
+    tile kernels hand from one warp per tile to one block per tile."""
+    rng = np.random.default_rng(seed)
+    mb = MeshBuilder()
+    side = 3.0
+    p0 = np.array([-side / 2, -side / 2, 2.5])
+    eu, ev = np.array([side, 0.0, 0.15]), np.array([0.0, side, 0.0])
+    a = np.linspace(0, 1, cells + 1)
+    aa, bb = np.meshgrid(a, a, indexing="xy")
+    verts = p0 + aa.ravel()[:, None] * eu + bb.ravel()[:, None] * ev
+    idx = np.arange((cells + 1) ** 2).reshape(cells + 1, cells + 1)
+    keep = rng.random((cells, cells)) >= holes
+    q00, q10 = idx[:-1, :-1][keep], idx[:-1, 1:][keep]
+    q01, q11 = idx[1:, :-1][keep], idx[1:, 1:][keep]
+    mb.add(verts, np.concatenate([np.stack([q00, q10, q11], 1), np.stack([q00, q11, q01], 1)]))
+    mb.beam((-1.6, -1.6, 0.0), (-1.6, -1.6, 2.6), 0.1)
+    mb.beam((1.6, 1.6, 0.0), (1.6, 1.6, 2.6), 0.1)
+    scene = mb.build()
+    if tiny_modules:
+        lay = Layout(1, 1, 1, np.zeros(1, np.int32))
+        g = np.arange(-1.4, 1.41, 0.2)
+        xx, yy = np.meshgrid(g, g, indexing="xy")
+        origins = [(x, y, 0.5) for x, y in zip(xx.ravel(), yy.ravel())]
+        m = len(origins)
+        gen = _gen_from_lists(origins, [(1.0, 0.0, 0.0)] * m, [(0.0, 1.0, 0.0)] * m, 1, 1, [0] * m, [-1] * m,
+                              list(range(m)), [lay], np.zeros((0, 3)))
+    else:
+        cu, cv = 6, 10
+        lay = standard_layout(cu, cv, 3)
+        tilt = math.radians(20.0)
+        vv = (0.0, math.cos(tilt), math.sin(tilt))
+        origins = [(-1.0 + 1.0 * (k % 2) - 0.47, -1.4 + 1.5 * (k // 2), 0.6) for k in range(4)]
+        gen = _gen_from_lists(origins, [(1.0, 0.0, 0.0)] * 4, [vv] * 4, cu, cv, [0] * 4, [-1] * 4, list(range(4)),
+                              [lay], np.zeros((0, 3)))
+    s_list = []
+    while len(s_list) < n_steps:
+        d = rng.integers(1, 366); hr = rng.uniform(8.0, 16.0)
+        sv = sun_vectors(lat, np.array([d]), np.array([hr]))[0]
+        if sv[2] > 0.3:
+            s_list.append(sv)
+    sv = np.array(s_list)
+    dni = clear_sky_dni(sv[:, 2]).astype(np.float32)
+    sun = Sun(xyz=sv, dni=dni, dhi=(0.1 * dni).astype(np.float32), dt_h=np.ones(len(sv), np.float32))
+    return Workload(f"canopy{seed}{'_tiny' if tiny_modules else ''}", scene, gen, sun, None, n, map_res)
+
+
 def make_config(name: str, **kw) -> Workload:
     if name in ("tiny", "cfg1"):
         return make_tiny(**kw)

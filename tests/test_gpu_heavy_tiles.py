@@ -1,0 +1,59 @@
+"""GPU parity on the tile kernels' less common paths: tiles handed from one
+warp per tile to one block per tile because they keep more than 64 triangles
+(block-wide sample-driven test up to 256, shared-memory rasterisation above),
+have more than 512 binned triangles, or more than 16 or 64 receiver modules
+(receivers then staged in chunks, without plane culling).
+Each case must agree with the FP64 oracle, be bit-identical to the map path
+(HBM shadow map + gather), and the work counters must show that the intended
+path ran."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1410_5780_gb300 import pv3d, scenes as S
+
+from parity import FLAG_AGREEMENT, compare, energy_checks, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("case,tile,map_res,tiny,cells", [
+    ("block_sample_test", 64, 256, False, 30), # 64 < kept <= 256: one block, sample by sample
+    ("block_raster", 64, 128, False, 60),      # binned > 512, kept > 256: one block, shared-memory raster
+    ("many_receivers", 64, 128, True, 30),     # > 16 receivers per tile: block-wide sample-driven test
+    ("receiver_chunks", 64, 64, True, 30),     # > 64 receivers: staged in chunks, no plane culling, raster
+    ("warp_tiles", 32, 512, False, 30),        # the same canopy on small tiles
+])
+def test_heavy_tile_paths(case, tile, map_res, tiny, cells):
+    w = S.make_canopy(31 if not tiny else 32, tiny_modules=tiny, map_res=map_res, cells=cells)
+    o = oracle.evaluate_workload(w)
+    with pv3d.Context(device=0, tile=tile) as c:
+        gid = pv3d.load_workload(c, w)
+        g = run_gpu(c, gid, w)
+        st = compare(w, g, o, np.arange(w.sun.n_steps))
+        assert st["agree"] >= FLAG_AGREEMENT, (case, st)
+        assert st["cell_ok"] == 1.0, (case, st)
+        energy_checks(w, g, o, np.arange(w.sun.n_steps))
+        m = run_gpu(c, gid, w, path=pv3d.PV3D_PATH_MAP)
+        for k in ("sample_bits", "cell_counts", "power", "energy"):
+            np.testing.assert_array_equal(g[k], m[k], err_msg=f"{case}: {k}")
+        assert g["cell_counts"].sum() > 0
+        c.evaluate(gid, n=w.n, map_res=w.map_res, profile=3)
+        p = c.last_profile()
+    why = p["heavy_why"]  # [receivers, binned triangles, kept triangles]
+    p = {k: v for k, v in p.items() if not k.endswith("_ms")}
+    warp_tiles = p["nonempty_tiles"] - p["heavy_tiles"]
+    block_sample_tiles = p["sample_tiles"] - warp_tiles
+    raster_tiles = p["nonempty_tiles"] - p["sample_tiles"]
+    if case == "block_sample_test":
+        assert why[2] > 0 and block_sample_tiles > 0, p
+    elif case == "block_raster":
+        assert why[1] > 0 and raster_tiles > 0 and p["texel_visits"] > 0, p
+    elif case == "many_receivers":
+        assert why[0] > 0 and block_sample_tiles > 0, p
+    elif case == "receiver_chunks":
+        # one tile holds every module; without plane culling it keeps the
+        # whole canopy and is rasterised, its receivers staged in chunks
+        assert why[0] > 0 and raster_tiles > 0, p
+    else:
+        assert warp_tiles > 0, p

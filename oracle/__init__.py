@@ -13,6 +13,9 @@ Section 2, steps 2-4):
     ambiguous there (see the C file's header);
   * per cell: shaded count; per module: MPP power shaded/unshaded with the
     series-current-limited bypass-diode model; energies over the steps.
+
+``string_power_from_counts`` applies the same electrical model to series
+strings of modules (one current and one maximum power point per string).
 """
 from __future__ import annotations
 
@@ -55,6 +58,8 @@ def _load():
             lib.pv3d_oracle_scene_create.restype = P
             lib.pv3d_oracle_scene_create.argtypes = [P, C.c_int64, P, C.c_int64]
             lib.pv3d_oracle_scene_destroy.argtypes = [P]
+            lib.pv3d_oracle_series_pmpp.restype = C.c_double
+            lib.pv3d_oracle_series_pmpp.argtypes = [C.c_int32, P, P, C.c_double]
             lib.pv3d_oracle_module_pmpp.restype = C.c_double
             lib.pv3d_oracle_module_pmpp.argtypes = [C.c_int32, P, P, C.c_int32, C.c_double,
                                                     C.c_double, C.c_double]
@@ -74,6 +79,9 @@ def _load():
             lib.pv3d_oracle_power_from_counts.argtypes = (
                 [C.c_int32, P, P, P, P, P, C.c_int32, P, P, P, P, P, C.c_int32, C.c_double, C.c_double,
                  C.c_double, P, C.c_int64, P, C.c_int32, P, P])
+            lib.pv3d_oracle_string_power_from_counts.argtypes = (
+                [C.c_int32, P, P, P, P, P, C.c_int32, P, P, P, P, P, C.c_int32, C.c_double, C.c_double,
+                 C.c_double, P, C.c_int64, P, C.c_int32, P, P, P])
             lib.pv3d_oracle_rays.restype = C.c_int
             lib.pv3d_oracle_rays.argtypes = [P, P, P, C.c_int64, C.c_double, C.c_int32, P]
             _lib = lib
@@ -246,6 +254,43 @@ def power_from_counts(w, steps, modules, counts, i_ref=I_REF, v_cell=V_CELL, v_d
         _ptr(np.ascontiguousarray(sun.dhi, np.float32)), _ptr(pz), int(w.n), i_ref, v_cell, v_diode,
         _ptr(steps), steps.size, _ptr(mods), mods.size, _ptr(cnt), _ptr(out))
     return out
+
+
+def series_pmpp(ik, vk, v_diode=V_DIODE) -> float:
+    """Maximum power of substrings (current limits ik, voltages vk) in one series string."""
+    lib = _load()
+    ik = np.ascontiguousarray(ik, np.float64)
+    vk = np.ascontiguousarray(vk, np.float64)
+    return lib.pv3d_oracle_series_pmpp(ik.size, _ptr(ik), _ptr(vk), v_diode)
+
+
+def string_index(gen):
+    """(strings, mod_string): the distinct string ids in ascending order, and
+    each module's index into them."""
+    ids, inv = np.unique(np.asarray(gen.string), return_inverse=True)
+    return ids, inv.astype(np.int32)
+
+
+def string_power_from_counts(w, steps, counts, i_ref=I_REF, v_cell=V_CELL, v_diode=V_DIODE):
+    """Oracle string model (modules in series strings, one MPP per string) on
+    given per-cell shaded counts [S, C] of every module; returns (power,
+    power_unshaded) [S, n_strings], strings in ascending id order."""
+    lib = _load()
+    gen, sun = w.gen, w.sun
+    mod_f, mod_i, lay_off, lay_nsub, lay_sub, n_trk, pivots = _gen_arrays(gen)
+    ids, ms = string_index(gen)
+    steps = np.ascontiguousarray(steps, np.int64)
+    cnt = np.ascontiguousarray(counts, np.int32)
+    pz = (np.zeros((sun.xyz.shape[0], 1, 2), np.float32) if w.poses is None or n_trk == 0
+          else np.ascontiguousarray(w.poses, np.float32))
+    p = np.zeros((steps.size, ids.size))
+    pu = np.zeros((steps.size, ids.size))
+    lib.pv3d_oracle_string_power_from_counts(
+        mod_f.shape[0], _ptr(mod_f), _ptr(mod_i), _ptr(lay_off), _ptr(lay_nsub), _ptr(lay_sub), n_trk,
+        _ptr(pivots), _ptr(np.ascontiguousarray(sun.xyz, np.float64)), _ptr(np.ascontiguousarray(sun.dni, np.float32)),
+        _ptr(np.ascontiguousarray(sun.dhi, np.float32)), _ptr(pz), int(w.n), i_ref, v_cell, v_diode,
+        _ptr(steps), steps.size, _ptr(ms), ids.size, _ptr(cnt), _ptr(p), _ptr(pu))
+    return p, pu
 
 
 def popcount64(a: np.ndarray) -> np.ndarray:

@@ -830,6 +830,116 @@ int pv3d_oracle_power_from_counts(int32_t n_mods, const float* mod_f, const int3
     return 0;
 }
 
+/* ------------------------------------------------------------------------- */
+/* series strings (Section 2: the generator's modules are wired in series     */
+/* strings, Fig. 2)                                                           */
+/* ------------------------------------------------------------------------- */
+/*
+ * One current I flows through every bypass substring of every module of a
+ * string.  A substring k with current limit I_k and voltage V_k (its cells in
+ * series, as in pv3d_oracle_module_pmpp) delivers V_k while I <= I_k and costs
+ * v_diode through its bypass diode above.  The string's
+ * P(I) = I * (sum_{k: I_k >= I} V_k - v_diode * #{k: I_k < I}) is linear
+ * between consecutive I_k, so its maximum power point is the best of the I_k
+ * (and 0).  The module model is the one-module string.
+ */
+double pv3d_oracle_series_pmpp(int32_t n_sub, const double* ik, const double* vk, double v_diode)
+{
+    double best = 0.0;
+    for (int32_t k = 0; k < n_sub; ++k) {
+        double cur = ik[k];
+        double volt = 0.0;
+        for (int32_t j = 0; j < n_sub; ++j) volt += (ik[j] >= cur) ? vk[j] : -v_diode;
+        double p = cur * volt;
+        if (p > best) best = p;
+    }
+    return best;
+}
+
+/* Current limit and voltage of each substring of one module from its cell
+ * irradiances g (W/m^2): written to ik[0..n_sub), vk[0..n_sub). */
+static void module_substrings(int32_t n_cells, const double* g, const int32_t* cell_sub, int32_t n_sub,
+                              double i_ref, double v_cell, double* ik, double* vk)
+{
+    for (int32_t k = 0; k < n_sub; ++k) { ik[k] = INFINITY; vk[k] = 0.0; }
+    for (int32_t c = 0; c < n_cells; ++c) {
+        int32_t k = cell_sub[c];
+        double ic = i_ref * g[c] / 1000.0;
+        if (ic < ik[k]) ik[k] = ic;
+        vk[k] += v_cell;
+    }
+}
+
+/*
+ * String powers for given shaded-sample counts: power[s * n_str + q] and
+ * power_unshaded[s * n_str + q] of string q, where mod_string[m] = q names the
+ * string of module m, and counts[s * C + cell] holds every module's cells in
+ * module order.  A step with the sun at or below the horizon gives 0.
+ */
+int pv3d_oracle_string_power_from_counts(int32_t n_mods, const float* mod_f, const int32_t* mod_i,
+                                         const int32_t* lay_off, const int32_t* lay_nsub, const int32_t* lay_sub,
+                                         int32_t n_trk, const float* pivots, const double* sun, const float* dni,
+                                         const float* dhi, const float* poses, int32_t n, double i_ref,
+                                         double v_cell, double v_diode, const int64_t* eval_steps,
+                                         int64_t n_eval_steps, const int32_t* mod_string, int32_t n_str,
+                                         const int32_t* counts, double* power, double* power_unshaded)
+{
+    ogen_t G;
+    memset(&G, 0, sizeof(G));
+    G.n_mods = n_mods; G.mod_f = mod_f; G.mod_i = mod_i; G.n_trk = n_trk; G.pivots = pivots;
+    G.poses = poses; G.n = n;
+    int64_t C = 0, n_sub_all = 0;
+    int64_t* cell0 = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_mods + 1));
+    for (int32_t m = 0; m < n_mods; ++m) {
+        cell0[m] = C;
+        C += (int64_t)mod_i[5 * (size_t)m] * mod_i[5 * (size_t)m + 1];
+        n_sub_all += lay_nsub[mod_i[5 * (size_t)m + 2]];
+    }
+    cell0[n_mods] = C;
+    /* substrings of each string, gathered module by module */
+    double* ik = (double*)malloc(sizeof(double) * (size_t)(n_sub_all + 1));
+    double* vk = (double*)malloc(sizeof(double) * (size_t)(n_sub_all + 1));
+    double* iu = (double*)malloc(sizeof(double) * (size_t)(n_sub_all + 1));
+    int64_t* str_fill = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n_str + 1));
+    int64_t* str_base = (int64_t*)calloc((size_t)(n_str + 1), sizeof(int64_t));
+    for (int32_t m = 0; m < n_mods; ++m) str_base[mod_string[m] + 1] += lay_nsub[mod_i[5 * (size_t)m + 2]];
+    for (int32_t q = 0; q < n_str; ++q) str_base[q + 1] += str_base[q];
+    double* g = (double*)malloc(sizeof(double) * 2048);
+    double* gu = (double*)malloc(sizeof(double) * 2048);
+    double tik[64], tvk[64], tiu[64], tvu[64];
+    for (int64_t si = 0; si < n_eval_steps; ++si) {
+        int64_t st = eval_steps[si];
+        vec3 s = mk(sun[3 * st], sun[3 * st + 1], sun[3 * st + 2]);
+        for (int32_t q = 0; q < n_str; ++q) str_fill[q] = str_base[q];
+        for (int32_t m = 0; m < n_mods; ++m) {
+            const int32_t* mi = mod_i + 5 * (size_t)m;
+            int32_t ncell = mi[0] * mi[1], lay = mi[2], ns = lay_nsub[lay];
+            posed_t P;
+            pose_module(&G, m, st, &P);
+            double c = dot(P.n, s);
+            double beam = s.z > 0.0 ? (double)dni[st] * fmax(0.0, c) : 0.0;
+            double diff = s.z > 0.0 ? (double)dhi[st] * (1.0 + P.n.z) / 2.0 : 0.0;
+            for (int32_t k = 0; k < ncell; ++k) {
+                double fc = (double)counts[si * C + cell0[m] + k] / (double)(n * n);
+                g[k] = beam * (1.0 - fc) + diff;
+                gu[k] = beam + diff;
+            }
+            module_substrings(ncell, g, lay_sub + lay_off[lay], ns, i_ref, v_cell, tik, tvk);
+            module_substrings(ncell, gu, lay_sub + lay_off[lay], ns, i_ref, v_cell, tiu, tvu);
+            int64_t f = str_fill[mod_string[m]];
+            for (int32_t k = 0; k < ns; ++k) { ik[f + k] = tik[k]; vk[f + k] = tvk[k]; iu[f + k] = tiu[k]; }
+            str_fill[mod_string[m]] = f + ns;
+        }
+        for (int32_t q = 0; q < n_str; ++q) {
+            int64_t b = str_base[q], e = str_base[q + 1];
+            power[si * n_str + q] = pv3d_oracle_series_pmpp((int32_t)(e - b), ik + b, vk + b, v_diode);
+            power_unshaded[si * n_str + q] = pv3d_oracle_series_pmpp((int32_t)(e - b), iu + b, vk + b, v_diode);
+        }
+    }
+    free(cell0); free(ik); free(vk); free(iu); free(str_fill); free(str_base); free(g); free(gu);
+    return 0;
+}
+
 /* Sample positions of one module at one step (for tests): xyz[cells*n*n*3] in
  * cell order, then sample order k = j*n + i. */
 int pv3d_oracle_samples(int32_t n_mods, const float* mod_f, const int32_t* mod_i, int32_t n_trk,

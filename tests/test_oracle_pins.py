@@ -245,6 +245,84 @@ def test_pv_mpp_is_max_over_current_scan():
         assert p <= scan + ik.max() / 20000 * 60 * oracle.V_CELL + 1e-9
 
 
+def _substrings(g, cell_sub, n_sub):
+    ic = oracle.I_REF * np.asarray(g, float) / 1000.0
+    ik = np.array([ic[cell_sub == k].min() for k in range(n_sub)])
+    vk = np.array([(cell_sub == k).sum() * oracle.V_CELL for k in range(n_sub)])
+    return ik, vk
+
+
+def test_string_two_modules_closed_forms():
+    """A series string of two 60-cell, 3-substring modules (Fig. 2 wiring): the
+    unshaded string delivers the two modules' power; with one beam-shaded cell
+    in one module, the best of bypassing its substring (5 substrings at full
+    current, one diode drop) and limiting the whole string to the shaded
+    cell's current (6 substrings)."""
+    lay = S.standard_layout(6, 10, 3)
+    vk = 20 * oracle.V_CELL
+    for g_full, g_diff in [(900.0, 100.0), (900.0, 700.0), (300.0, 250.0), (800.0, 0.0)]:
+        a = np.full(60, g_full)
+        ik_a, vk_a = _substrings(a, lay.cell_sub, 3)
+        p2 = oracle.series_pmpp(np.r_[ik_a, ik_a], np.r_[vk_a, vk_a])
+        assert abs(p2 - 2 * oracle.I_REF * g_full / 1000.0 * 60 * oracle.V_CELL) < 1e-9
+        b = a.copy()
+        b[0] = g_diff
+        ik_b, vk_b = _substrings(b, lay.cell_sub, 3)
+        i_full, i_diff = oracle.I_REF * g_full / 1000.0, oracle.I_REF * g_diff / 1000.0
+        expect = max(i_full * (5 * vk - oracle.V_DIODE), i_diff * 6 * vk)
+        assert abs(oracle.series_pmpp(np.r_[ik_a, ik_b], np.r_[vk_a, vk_b]) - expect) < 1e-9
+
+
+def test_string_of_one_module_is_the_module():
+    rng = np.random.default_rng(8)
+    lay = S.standard_layout(6, 12, 3)
+    for _ in range(100):
+        g = rng.uniform(0, 1000, 72)
+        ik, vk = _substrings(g, lay.cell_sub, 3)
+        assert abs(oracle.series_pmpp(ik, vk) - oracle.module_pmpp(g, lay.cell_sub, 3)) < 1e-9
+
+
+def test_string_mpp_is_max_over_current_scan_and_below_module_mppt():
+    """The string's maximum over substring currents equals a fine scan of
+    P(I); and it never exceeds the sum of its modules' own maxima (one
+    tracker per module can only do better than one per string)."""
+    rng = np.random.default_rng(9)
+    lay = S.standard_layout(6, 10, 3)
+    for _ in range(30):
+        gs = [rng.uniform(50, 1000, 60) for _ in range(int(rng.integers(2, 6)))]
+        subs = [_substrings(g, lay.cell_sub, 3) for g in gs]
+        ik = np.concatenate([a for a, _ in subs]); vk = np.concatenate([b for _, b in subs])
+        grid = np.linspace(0, ik.max(), 40001)
+        volts = np.where(ik[None, :] >= grid[:, None], vk[None, :], -oracle.V_DIODE).sum(1)
+        scan = max(0.0, float((grid * volts).max()))
+        p = oracle.series_pmpp(ik, vk)
+        assert scan - 1e-9 <= p <= scan + ik.max() / 40000 * vk.sum() + 1e-9
+        assert p <= sum(oracle.module_pmpp(g, lay.cell_sub, 3) for g in gs) + 1e-9
+
+
+def test_string_power_from_counts_matches_modules_and_strings():
+    """String powers from shaded counts: with every module its own string they
+    are the module powers; grouped into strings they follow series_pmpp of the
+    members' substrings; zero counts give the unshaded string power."""
+    w = S.make_random_small(61, n_mods=6, n_steps=5, n=2)
+    steps = np.arange(w.sun.n_steps)
+    rng = np.random.default_rng(3)
+    C = int((w.gen.cells_u * w.gen.cells_v).sum())
+    counts = rng.integers(0, w.n * w.n + 1, (steps.size, C)).astype(np.int32)
+    p_mod = oracle.power_from_counts(w, steps, np.arange(w.gen.n_modules), counts)
+    w.gen.string = np.arange(w.gen.n_modules, dtype=np.int32)
+    p, pu = oracle.string_power_from_counts(w, steps, counts)
+    np.testing.assert_allclose(p, p_mod, rtol=1e-12, atol=1e-12)
+    pu_mod = oracle.power_from_counts(w, steps, np.arange(w.gen.n_modules), np.zeros_like(counts))
+    np.testing.assert_allclose(pu, pu_mod, rtol=1e-12, atol=1e-12)
+    w.gen.string = np.array([7, 7, 3, 3, 3, 9], np.int32)   # strings 3, 7, 9 in ascending order
+    p, pu = oracle.string_power_from_counts(w, steps, counts)
+    assert p.shape == (steps.size, 3)
+    assert np.all(p <= p_mod[:, [2, 3, 4]].sum(1)[:, None] * [1, 0, 0] + p_mod[:, [0, 1]].sum(1)[:, None] * [0, 1, 0]
+                  + p_mod[:, [5]].sum(1)[:, None] * [0, 0, 1] + 1e-9)
+    np.testing.assert_allclose(p[:, 2], p_mod[:, 5], rtol=1e-12, atol=1e-12)
+
+
 # ---------------------------------------------------------------------------
 # invariants
 # ---------------------------------------------------------------------------

@@ -89,7 +89,7 @@ typedef struct pv3d_module {
     int32_t cells_v;    /* 1..64; cells_u * cells_v <= 1024 */
     int32_t layout;     /* index into the layouts of pv3d_generator_define */
     int32_t tracker;    /* index into the trackers, or -1 for a fixed module */
-    int32_t string_id;  /* series string the module belongs to (informational) */
+    int32_t string_id;  /* series string the module belongs to (string outputs of pv3d_evaluate) */
     int32_t reserved;
 } pv3d_module;
 
@@ -186,6 +186,15 @@ typedef struct pv3d_result {
     int64_t kernel_launches;   /* CUDA kernels launched by the evaluation */
     float latency_ms;          /* served requests: submit to results ready (host clock) */
     int32_t reserved1;
+    /* series strings (pv3d_evaluate only): NS = pv3d_generator_strings' count,
+     * strings in ascending string_id order.  One current flows through every
+     * bypass substring of every module of a string, and the string runs at
+     * its own maximum power point (Section 2: modules wired in series strings,
+     * Fig. 2; the module outputs above keep one maximum power point per module). */
+    double* string_energy;           /* [NS] sum over steps of the string's P_mpp * dt, Wh */
+    double* string_energy_unshaded;  /* [NS] */
+    float* string_power;             /* [S x NS] string P_mpp per step, W */
+    float* string_power_unshaded;    /* [S x NS] */
 } pv3d_result;
 
 /* ---- context ------------------------------------------------------------ */
@@ -223,6 +232,16 @@ int pv3d_generator_define(pv3d_ctx* ctx, uint32_t scene_id,
                           const pv3d_layout* layouts, int32_t n_layouts,
                           const pv3d_tracker* trackers, int32_t n_trackers,
                           uint32_t* gen_id);
+
+/*
+ * Series strings of a generator (Section 2: the modules are wired in series
+ * strings, Fig. 2): modules with equal pv3d_module.string_id form one string.
+ * *n_strings receives their number; string_ids (NULL, or room for
+ * *n_strings entries) the distinct ids in ascending order, which is the order
+ * of the string outputs of pv3d_result.  Errors: PV3D_E_NOTFOUND (unknown
+ * generator), PV3D_E_INVALID (null context or count pointer).
+ */
+int pv3d_generator_strings(pv3d_ctx* ctx, uint32_t gen_id, int32_t* n_strings, int32_t* string_ids);
 
 /*
  * Tracker poses: az_tilt[(step * n_trackers + t) * 2 + {0, 1}] = compass

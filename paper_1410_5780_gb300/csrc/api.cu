@@ -61,6 +61,14 @@ struct GenH {
     // poses
     int64_t n_pose_steps = 0;
     float* d_poses = nullptr;
+    // series strings: distinct string ids in ascending order; substrings
+    // numbered string by string (module order within a string)
+    std::vector<int32_t> str_ids;
+    int32_t n_sub_tot = 0;
+    int32_t* d_str_sub = nullptr;   // [n_str + 1]
+    int32_t* d_sub_base = nullptr;  // [M]
+    int32_t* d_sub_nk = nullptr;    // [n_sub_tot]
+    int32_t* d_sub_mod = nullptr;   // [n_sub_tot]
     size_t bytes = 0;
 };
 
@@ -83,7 +91,7 @@ struct pv3d_ctx {
     std::map<uint32_t, GenH> gens;
     uint32_t next_id = 1;
     // workspace pools
-    DevBuf lp, win, ms, ms_p, ms_pu, ms_beam, cs_cnt, cs_bits, t_far, t_cnt, t_off, t_cur, t_slot, t_rcnt, t_roff, t_rcur, nonempty, heavy, bins, pairs, recv, map,
+    DevBuf lp, win, ms, ms_p, ms_pu, ms_beam, ms_iu, ss_i, sq_p, sq_pu, kahan_str, cs_cnt, cs_bits, t_far, t_cnt, t_off, t_cur, t_slot, t_rcnt, t_roff, t_rcur, nonempty, heavy, bins, pairs, recv, map,
         big, block_sums, ctr, waves, jobs, kahan_mod, kahan_cell, staging;
     int64_t bin_cap = 0, map_cap_tiles = 0, big_cap = 0, recv_cap = 0;
     uint64_t bufgen = 0;  // bumped whenever a pool is reallocated (captured graphs hold its pointers)
@@ -189,7 +197,8 @@ static bool finite3(const float* p) { return std::isfinite(p[0]) && std::isfinit
 static void free_gen(GenH& g)
 {
     void* ps[] = {g.d_mods, g.d_cell_mod, g.d_lay_sub, g.d_lay_off, g.d_lay_nk, g.d_lay_nk_off, g.d_pivots,
-                  g.d_sun, g.d_dni, g.d_dhi, g.d_dt, g.d_poses};
+                  g.d_sun, g.d_dni, g.d_dhi, g.d_dt, g.d_poses, g.d_str_sub, g.d_sub_base, g.d_sub_nk,
+                  g.d_sub_mod};
     for (void* p : ps)
         if (p) cudaFree(p);
 }
@@ -456,6 +465,31 @@ extern "C" int pv3d_generator_define(pv3d_ctx* c, uint32_t scene_id, const pv3d_
     std::vector<float> piv((size_t)n_trackers * 3);
     for (int32_t t = 0; t < n_trackers; ++t)
         for (int a = 0; a < 3; ++a) piv[3 * t + a] = trackers[t].pivot[a] - g.ref[a];
+    // series strings: rank the string ids, number the substrings string by string
+    std::vector<int32_t> str_sub, sub_base(n_mods), sub_nk, sub_mod;
+    {
+        for (int32_t m = 0; m < n_mods; ++m) g.str_ids.push_back(mods[m].string_id);
+        std::sort(g.str_ids.begin(), g.str_ids.end());
+        g.str_ids.erase(std::unique(g.str_ids.begin(), g.str_ids.end()), g.str_ids.end());
+        std::vector<std::vector<int32_t>> members(g.str_ids.size());
+        for (int32_t m = 0; m < n_mods; ++m) {
+            const size_t q = std::lower_bound(g.str_ids.begin(), g.str_ids.end(), mods[m].string_id) - g.str_ids.begin();
+            members[q].push_back(m);
+        }
+        for (auto& mem : members) {
+            str_sub.push_back((int32_t)sub_nk.size());
+            for (int32_t m : mem) {
+                sub_base[m] = (int32_t)sub_nk.size();
+                const int32_t lay = mods[m].layout;
+                for (int k = 0; k < layouts[lay].n_sub; ++k) {
+                    sub_nk.push_back(lay_nk[lay_nk_off[lay] + k]);
+                    sub_mod.push_back(m);
+                }
+            }
+        }
+        str_sub.push_back((int32_t)sub_nk.size());
+        g.n_sub_tot = (int32_t)sub_nk.size();
+    }
     int rc;
     if ((rc = upload(c, &g.d_mods, g.mods_h.data(), g.mods_h.size())) ||
         (rc = upload(c, &g.d_cell_mod, cell_mod.data(), cell_mod.size())) ||
@@ -463,14 +497,29 @@ extern "C" int pv3d_generator_define(pv3d_ctx* c, uint32_t scene_id, const pv3d_
         (rc = upload(c, &g.d_lay_off, lay_off.data(), lay_off.size())) ||
         (rc = upload(c, &g.d_lay_nk, lay_nk.data(), lay_nk.size())) ||
         (rc = upload(c, &g.d_lay_nk_off, lay_nk_off.data(), lay_nk_off.size())) ||
-        (rc = upload(c, &g.d_pivots, piv.data(), piv.size()))) {
+        (rc = upload(c, &g.d_pivots, piv.data(), piv.size())) ||
+        (rc = upload(c, &g.d_str_sub, str_sub.data(), str_sub.size())) ||
+        (rc = upload(c, &g.d_sub_base, sub_base.data(), sub_base.size())) ||
+        (rc = upload(c, &g.d_sub_nk, sub_nk.data(), sub_nk.size())) ||
+        (rc = upload(c, &g.d_sub_mod, sub_mod.data(), sub_mod.size()))) {
         free_gen(g);
         return rc;
     }
-    g.bytes = g.mods_h.size() * sizeof(ModuleDev) + cell_mod.size() * 4 + lay_sub.size() * 8 + piv.size() * 4;
+    g.bytes = g.mods_h.size() * sizeof(ModuleDev) + cell_mod.size() * 4 + lay_sub.size() * 8 + piv.size() * 4 +
+              (str_sub.size() + sub_base.size() + 2 * sub_nk.size()) * 4;
     uint32_t id = c->next_id++;
     c->gens[id] = std::move(g);
     *gen_id = id;
+    return PV3D_OK;
+}
+
+extern "C" int pv3d_generator_strings(pv3d_ctx* c, uint32_t gen_id, int32_t* n_strings, int32_t* string_ids)
+{
+    if (!c || !n_strings) return PV3D_E_INVALID;
+    auto it = c->gens.find(gen_id);
+    if (it == c->gens.end()) return fail(c, PV3D_E_NOTFOUND, "unknown generator %u", gen_id);
+    *n_strings = (int32_t)it->second.str_ids.size();
+    if (string_ids) std::copy(it->second.str_ids.begin(), it->second.str_ids.end(), string_ids);
     return PV3D_OK;
 }
 
@@ -537,7 +586,7 @@ extern "C" int pv3d_set_sun(pv3d_ctx* c, uint32_t gen_id, const double* sun_xyz,
 namespace {
 
 struct EvalSetup {
-    int n, R, K, tile, fused, profile, count;
+    int n, R, K, tile, fused, profile, count, strings;
     int64_t b, e;
     float i_ref, v_cell, v_diode;
 };
@@ -569,12 +618,14 @@ static int check_eval(pv3d_ctx* c, const GenH& g, const pv3d_eval_opts* o, const
     if (es.b < 0 || es.e > g.n_steps || es.b >= es.e) return fail(c, PV3D_E_INVALID, "bad step range");
     if (!out) return fail(c, PV3D_E_INVALID, "null result");
     if (out->sample_bits && es.n > 8) return fail(c, PV3D_E_INVALID, "sample_bits needs samples_per_side <= 8");
+    es.strings = out->string_energy || out->string_energy_unshaded || out->string_power || out->string_power_unshaded;
     return PV3D_OK;
 }
 
 // Fill a JobDev for generator g over steps [step0, step0 + k).
 static JobDev make_job(pv3d_ctx* c, const GenH& g, const SceneH& s, const EvalSetup& es, int64_t step0, int k,
-                       float2* kmod, float2* kcell, float* pw, float* pwu, uint8_t* cnt, unsigned long long* bits)
+                       float2* kmod, float2* kcell, float* pw, float* pwu, uint8_t* cnt, unsigned long long* bits,
+                       float2* kstr = nullptr, float* spw = nullptr, float* spwu = nullptr)
 {
     JobDev J{};
     J.tri = s.d_tri;
@@ -620,6 +671,17 @@ static JobDev make_job(pv3d_ctx* c, const GenH& g, const SceneH& s, const EvalSe
     J.out_power_u = pwu;
     J.out_counts = cnt;
     J.out_bits = bits;
+    if (es.strings) {
+        J.n_str = (int32_t)g.str_ids.size();
+        J.n_sub_tot = g.n_sub_tot;
+        J.str_sub = g.d_str_sub;
+        J.sub_base = g.d_sub_base;
+        J.sub_nk = g.d_sub_nk;
+        J.sub_mod = g.d_sub_mod;
+        J.kahan_str = kstr;
+        J.out_str_power = spw;
+        J.out_str_power_u = spwu;
+    }
     (void)c;
     return J;
 }
@@ -644,6 +706,9 @@ static WaveDev pack_wave(std::vector<JobDev>& jobs, size_t first, size_t last, i
         J.it_mod = W.tot_mod;
         J.it_tri = W.tot_tri;
         J.it_epi = W.tot_epi;
+        J.ss_base = W.tot_ss;
+        J.sq_base = W.tot_sq;
+        J.it_str = W.tot_sq;
         int64_t groups = (J.n_mods + kWinPerItem - 1) / kWinPerItem;
         W.tot_js += J.k;
         W.tot_te += (int64_t)J.k * J.tiles_x * J.tiles_x;
@@ -652,16 +717,21 @@ static WaveDev pack_wave(std::vector<JobDev>& jobs, size_t first, size_t last, i
         W.tot_win += (int64_t)J.k * groups;
         W.tot_mod += (int64_t)J.k * J.n_mods;
         W.tot_tri += ((int64_t)J.n_ml + (J.n_mtris + 31) / 32) * J.k;
-        W.tot_epi += (int64_t)J.n_cells + J.n_mods;
+        W.tot_epi += (int64_t)J.n_cells + J.n_mods + J.n_str;
+        W.tot_ss += (int64_t)J.k * (J.n_str ? J.n_sub_tot : 0);
+        W.tot_sq += (int64_t)J.k * J.n_str;
         if (J.out_bits) W.want_bits = 1;
     }
     return W;
 }
 
 static int ensure_workspace(pv3d_ctx* c, int64_t js, int64_t te, int64_t ms, int64_t cs, int tile, bool fused,
-                            bool want_bits)
+                            bool want_bits, int64_t ss = 0, int64_t sq = 0)
 {
     int rc;
+    if (sq > 0 && ((rc = ensure(c, c->ms_iu, ms * 4)) || (rc = ensure(c, c->ss_i, ss * 4)) ||
+                   (rc = ensure(c, c->sq_p, sq * 4)) || (rc = ensure(c, c->sq_pu, sq * 4))))
+        return rc;
     int64_t scan_tiles = (te + 4095) / 4096 + 1;
     if ((rc = ensure(c, c->lp, js * sizeof(LightParams))) || (rc = ensure(c, c->win, js * 16)) ||
         (rc = ensure(c, c->ms, ms * sizeof(ModStep))) || (rc = ensure(c, c->ms_p, ms * 4)) ||
@@ -698,6 +768,10 @@ static Buffers buffers_of(pv3d_ctx* c)
     B.ms_p = (float*)c->ms_p.p;
     B.ms_pu = (float*)c->ms_pu.p;
     B.ms_beam = (float*)c->ms_beam.p;
+    B.ms_iu = (float*)c->ms_iu.p;
+    B.ss_i = (float*)c->ss_i.p;
+    B.sq_p = (float*)c->sq_p.p;
+    B.sq_pu = (float*)c->sq_pu.p;
     B.cs_cnt = (uint32_t*)c->cs_cnt.p;
     B.cs_bits = (unsigned long long*)c->cs_bits.p;
     B.t_far = (uint32_t*)c->t_far.p;
@@ -865,6 +939,8 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
     // copied back from a device staging area at the end
     const bool dev = out->is_device != 0;
     size_t off_e = 0, off_eu = 0, off_cl = 0, off_p = 0, off_pu = 0, off_cnt = 0, off_bits = 0, tot = 0;
+    size_t off_se = 0, off_seu = 0, off_sp = 0, off_spu = 0;
+    const int32_t NS = (int32_t)g.str_ids.size();
     auto take = [&](size_t bytes) {
         size_t o_ = tot;
         tot += (bytes + 255) & ~size_t(255);
@@ -878,6 +954,10 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
         if (out->power_unshaded) off_pu = take((size_t)S * g.M * 4);
         if (out->cell_counts) off_cnt = take((size_t)S * g.C);
         if (out->sample_bits) off_bits = take((size_t)S * g.C * 8);
+        if (out->string_energy) off_se = take((size_t)NS * 8);
+        if (out->string_energy_unshaded) off_seu = take((size_t)NS * 8);
+        if (out->string_power) off_sp = take((size_t)S * NS * 4);
+        if (out->string_power_unshaded) off_spu = take((size_t)S * NS * 4);
         if ((rc = ensure(c, c->staging, tot))) return rc;
     }
     char* sb = (char*)c->staging.p;
@@ -889,9 +969,14 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
     uint8_t* d_cnt = dev ? out->cell_counts : (out->cell_counts ? (uint8_t*)(sb + off_cnt) : nullptr);
     unsigned long long* d_bits =
         dev ? (unsigned long long*)out->sample_bits : (out->sample_bits ? (unsigned long long*)(sb + off_bits) : nullptr);
+    double* d_se = dev ? out->string_energy : (out->string_energy ? (double*)(sb + off_se) : nullptr);
+    double* d_seu = dev ? out->string_energy_unshaded : (out->string_energy_unshaded ? (double*)(sb + off_seu) : nullptr);
+    float* d_sp = dev ? out->string_power : (out->string_power ? (float*)(sb + off_sp) : nullptr);
+    float* d_spu = dev ? out->string_power_unshaded : (out->string_power_unshaded ? (float*)(sb + off_spu) : nullptr);
 
     if ((rc = ensure(c, c->kahan_mod, (size_t)g.M * 2 * sizeof(float2))) ||
-        (rc = ensure(c, c->kahan_cell, (size_t)g.C * sizeof(float2))))
+        (rc = ensure(c, c->kahan_cell, (size_t)g.C * sizeof(float2))) ||
+        (es.strings && (rc = ensure(c, c->kahan_str, (size_t)NS * 2 * sizeof(float2)))))
         return rc;
 
     // plan: one job per wave
@@ -900,17 +985,18 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
     for (int64_t s0 = es.b; s0 < es.e; s0 += es.K) {
         int k = (int)std::min<int64_t>(es.K, es.e - s0);
         jobs.push_back(make_job(c, g, s, es, s0, k, (float2*)c->kahan_mod.p, (float2*)c->kahan_cell.p, d_p, d_pu,
-                                d_cnt, d_bits));
+                                d_cnt, d_bits, (float2*)c->kahan_str.p, d_sp, d_spu));
         waves.push_back(pack_wave(jobs, jobs.size() - 1, jobs.size(), tile_sh, u24, es.fused, es.count));
     }
-    int64_t mjs = 0, mte = 0, mms = 0, mcs = 0;
+    int64_t mjs = 0, mte = 0, mms = 0, mcs = 0, mss = 0, msq = 0;
     for (auto& W : waves) {
         mjs = std::max(mjs, W.tot_js); mte = std::max(mte, W.tot_te);
         mms = std::max(mms, W.tot_ms); mcs = std::max(mcs, W.tot_cs);
+        mss = std::max(mss, W.tot_ss); msq = std::max(msq, W.tot_sq);
     }
     Counters hc{};
     for (int attempt = 0; attempt < 4; ++attempt) {
-        if ((rc = ensure_workspace(c, mjs, mte, mms, mcs, es.tile, es.fused, d_bits != nullptr))) return rc;
+        if ((rc = ensure_workspace(c, mjs, mte, mms, mcs, es.tile, es.fused, d_bits != nullptr, mss, msq))) return rc;
         for (auto& W : waves) {
             W.bin_cap = c->bin_cap;
             W.map_cap_tiles = c->map_cap_tiles;
@@ -921,10 +1007,13 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
         CUDA_TRY(c, cudaMemsetAsync(c->ctr.p, 0, sizeof(Counters), st));
         CUDA_TRY(c, cudaMemsetAsync(c->kahan_mod.p, 0, (size_t)g.M * 2 * sizeof(float2), st));
         CUDA_TRY(c, cudaMemsetAsync(c->kahan_cell.p, 0, (size_t)g.C * sizeof(float2), st));
+        if (es.strings) CUDA_TRY(c, cudaMemsetAsync(c->kahan_str.p, 0, (size_t)NS * 2 * sizeof(float2), st));
         CUDA_TRY(c, cudaEventRecord(c->ev0, st));
         if ((rc = run_waves(c, waves, st, es.tile, es.fused, es.profile, es.count))) return rc;
         CUDA_TRY(c, launch_finalize_pairs((const float2*)c->kahan_mod.p, g.M, (const float2*)c->kahan_cell.p, g.C,
                                           d_e, d_eu, d_cl, st));
+        if (es.strings)
+            CUDA_TRY(c, launch_finalize_pairs((const float2*)c->kahan_str.p, NS, nullptr, 0, d_se, d_seu, nullptr, st));
         CUDA_TRY(c, cudaEventRecord(c->ev1, st));
         CUDA_TRY(c, cudaMemcpyAsync(&hc, c->ctr.p, sizeof(Counters), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(c, cudaStreamSynchronize(st));
@@ -947,6 +1036,13 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
         if (out->cell_counts) CUDA_TRY(c, cudaMemcpy(out->cell_counts, d_cnt, (size_t)S * g.C, cudaMemcpyDeviceToHost));
         if (out->sample_bits)
             CUDA_TRY(c, cudaMemcpy(out->sample_bits, d_bits, (size_t)S * g.C * 8, cudaMemcpyDeviceToHost));
+        if (out->string_energy) CUDA_TRY(c, cudaMemcpy(out->string_energy, d_se, (size_t)NS * 8, cudaMemcpyDeviceToHost));
+        if (out->string_energy_unshaded)
+            CUDA_TRY(c, cudaMemcpy(out->string_energy_unshaded, d_seu, (size_t)NS * 8, cudaMemcpyDeviceToHost));
+        if (out->string_power)
+            CUDA_TRY(c, cudaMemcpy(out->string_power, d_sp, (size_t)S * NS * 4, cudaMemcpyDeviceToHost));
+        if (out->string_power_unshaded)
+            CUDA_TRY(c, cudaMemcpy(out->string_power_unshaded, d_spu, (size_t)S * NS * 4, cudaMemcpyDeviceToHost));
     }
     int64_t lit = 0;
     for (int64_t k = es.b; k < es.e; ++k) lit += g.lit[k];
@@ -1314,6 +1410,7 @@ extern "C" int pv3d_submit(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o
     int rc = check_eval(c, g, o, out, r->es);
     if (rc) return rc;
     if (o && o->path == PV3D_PATH_MAP) return fail(c, PV3D_E_INVALID, "served requests use the fused path");
+    if (r->es.strings) return fail(c, PV3D_E_INVALID, "string outputs are produced by pv3d_evaluate only");
     r->gen_id = gen_id;
     r->opts = o ? *o : pv3d_eval_opts{};
     r->out = out;
@@ -1433,7 +1530,8 @@ extern "C" void pv3d_destroy(pv3d_ctx* c)
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     release_buf(c->wave_slot);
     release_buf(c->jobs_slot);
-    DevBuf* bufs[] = {&c->lp, &c->win, &c->ms, &c->ms_p, &c->ms_pu, &c->ms_beam, &c->cs_cnt, &c->cs_bits, &c->t_far,
+    DevBuf* bufs[] = {&c->lp, &c->win, &c->ms, &c->ms_p, &c->ms_pu, &c->ms_beam, &c->ms_iu, &c->ss_i, &c->sq_p,
+                      &c->sq_pu, &c->kahan_str, &c->cs_cnt, &c->cs_bits, &c->t_far,
                       &c->t_cnt, &c->t_off, &c->t_cur, &c->t_slot, &c->t_rcnt, &c->t_roff, &c->t_rcur, &c->nonempty, &c->heavy,
                       &c->bins, &c->pairs, &c->recv, &c->map, &c->big,
                       &c->block_sums, &c->ctr, &c->waves, &c->jobs, &c->kahan_mod, &c->kahan_cell, &c->staging};

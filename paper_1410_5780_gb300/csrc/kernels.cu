@@ -22,8 +22,10 @@
 //                 of those samples and warp-aggregated cell tallies
 //   k_pv          per (step, module): irradiance per cell, substring currents,
 //                 bypass-diode maximum power point (Section 2, step 4)
+//   k_string      series strings: one maximum power point per (step, string)
+//                 over the substring currents of its modules
 //   k_epilogue    Kahan-compensated FP32 sums over the wave's steps in step
-//                 order, per module (energy) and per cell (beam loss)
+//                 order, per module (energy), per cell (beam loss) and per string
 // The map path replaces k_raster_test + k_pv by k_raster_map (tiles stored to
 // an HBM shadow map with 16-byte stores) + k_sample (texel gathers, ballot
 // tallies, PV model).
@@ -2013,6 +2015,13 @@ __device__ void module_pv(const JobDev& J, const ModuleDev& M, const ModStep& s,
         atomicMin(&s_imin[csub[c]], __float_as_uint(I));  // I >= 0: uint order = float order
     }
     __syncthreads();
+    if (J.n_str) {  // substring currents for the series-string model (k_string)
+        const int ls = (int)((msi - J.ms_base) / J.n_mods);
+        const int m = (int)(&M - J.mods);
+        float* ss = B.ss_i + J.ss_base + (int64_t)ls * J.n_sub_tot + J.sub_base[m];
+        for (int k = threadIdx.x; k < M.n_sub; k += blockDim.x) ss[k] = __uint_as_float(s_imin[k]);
+        if (threadIdx.x == 0) B.ms_iu[msi] = J.i_ref * (beam + diff) * 1e-3f;
+    }
     if (threadIdx.x == 0) {
         const int* nk = J.lay_nk + J.lay_nk_off[M.layout];
         const int ns = M.n_sub;
@@ -2095,6 +2104,11 @@ __global__ void __launch_bounds__(kPvThreads) k_pv(const WaveDev* __restrict__ W
             atomicMin(&imin[csub[c]], __float_as_uint(I));  // I >= 0: uint order = float order
         }
         __syncwarp();
+        if (J.n_str) {  // substring currents for the series-string model (k_string)
+            float* ss = B.ss_i + J.ss_base + (int64_t)ls * J.n_sub_tot + J.sub_base[m];
+            for (int k = lane; k < ns; k += 32) ss[k] = __uint_as_float(imin[k]);
+            if (lane == 0) B.ms_iu[msi] = J.i_ref * (beam + diff) * 1e-3f;
+        }
         const int* nk = J.lay_nk + J.lay_nk_off[M.layout];
         float best = 0.f, vsum = 0.f;
         for (int k = lane; k < ns; k += 32) {
@@ -2207,6 +2221,62 @@ __global__ void __launch_bounds__(kPvThreads) k_sample(const WaveDev* __restrict
 }
 
 // ---------------------------------------------------------------------------
+// k_string: series strings (Section 2: the generator's modules wired in
+// series strings, Fig. 2) -- one current through every bypass substring of
+// every module of the string; P(I) = I (sum_{k: I_k >= I} V_k - v_diode
+// #{k: I_k < I}) is linear between consecutive substring currents, so the
+// string's maximum power point is the best of them.  One warp per (step,
+// string): lanes over candidate currents, an inner loop over the string's
+// substrings.  Without shading every substring of a module carries the
+// module's unshaded current.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_string(const WaveDev* __restrict__ W, const JobDev* __restrict__ jobs,
+                                                Buffers B)
+{
+    const int64_t tot = W->tot_sq;
+    const int nj = W->n_jobs;
+    const int lane = threadIdx.x & 31;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t item = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; item < tot; item += n_warps) {
+        const int j = job_of(nj, item, [&](int q) { return jobs[q].it_str; });
+        const JobDev& J = jobs[j];
+        const int64_t li = item - J.it_str;
+        const int ls = (int)(li / J.n_str), q = (int)(li - (int64_t)ls * J.n_str);
+        const int64_t sq = J.sq_base + li;
+        const LightParams& lp = B.lp[J.js_base + ls];
+        float best = 0.f, best_u = 0.f;
+        if (lp.valid) {
+            const int k0 = J.str_sub[q], k1 = J.str_sub[q + 1];
+            const float* ik = B.ss_i + J.ss_base + (int64_t)ls * J.n_sub_tot;
+            const float* iu = B.ms_iu + J.ms_base + (int64_t)ls * J.n_mods;
+            for (int c = k0 + lane; c < k1; c += 32) {
+                const float cur = ik[c], cur_u = iu[J.sub_mod[c]];
+                float volt = 0.f, volt_u = 0.f;
+                for (int k = k0; k < k1; ++k) {
+                    const float vk = J.sub_nk[k] * J.v_cell;
+                    volt += ik[k] >= cur ? vk : -J.v_diode;
+                    volt_u += iu[J.sub_mod[k]] >= cur_u ? vk : -J.v_diode;
+                }
+                best = fmaxf(best, cur * volt);
+                best_u = fmaxf(best_u, cur_u * volt_u);
+            }
+#pragma unroll
+            for (int off = 16; off; off >>= 1) {
+                best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, off));
+                best_u = fmaxf(best_u, __shfl_xor_sync(0xffffffffu, best_u, off));
+            }
+        }
+        if (lane == 0) {
+            B.sq_p[sq] = best;
+            B.sq_pu[sq] = best_u;
+            const int64_t row = (int64_t)(J.out_row0 + ls);
+            if (J.out_str_power) J.out_str_power[row * J.n_str + q] = best;
+            if (J.out_str_power_u) J.out_str_power_u[row * J.n_str + q] = best_u;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // k_epilogue: Kahan sums over the wave's steps in step order
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void kahan_add(float2& acc, float x)
@@ -2240,6 +2310,18 @@ __global__ void k_epilogue(const WaveDev* __restrict__ W, const JobDev* __restri
                 kahan_add(acc, beam * (cnt * inv_nn) * lp.dt);
             }
             J.kahan_cell[c] = acc;
+        } else if (li >= C + Mn) {
+            const int q = (int)(li - C - Mn);
+            float2 e = J.kahan_str[2 * q], eu = J.kahan_str[2 * q + 1];
+            for (int ls = 0; ls < J.k; ++ls) {
+                const LightParams& lp = B.lp[J.js_base + ls];
+                if (!lp.valid) continue;
+                const int64_t sq = J.sq_base + (int64_t)ls * J.n_str + q;
+                kahan_add(e, B.sq_p[sq] * lp.dt);
+                kahan_add(eu, B.sq_pu[sq] * lp.dt);
+            }
+            J.kahan_str[2 * q] = e;
+            J.kahan_str[2 * q + 1] = eu;
         } else {
             const int m = (int)(li - C);
             float2 e = J.kahan_mod[2 * m], eu = J.kahan_mod[2 * m + 1];
@@ -2332,6 +2414,7 @@ cudaError_t launch_wave(const WaveDev* d_wave, const JobDev* d_jobs, const Buffe
     if (cfg.ev) cudaEventRecord(cfg.ev[4], st);
     if (cfg.fused) k_pv<<<sm * 32, kPvThreads, 0, st>>>(W, d_jobs, b);
     else k_sample<<<sm * 16, kPvThreads, 0, st>>>(W, d_jobs, b);
+    k_string<<<sm * 4, 256, 0, st>>>(W, d_jobs, b);
     if (cfg.ev) cudaEventRecord(cfg.ev[5], st);
     k_epilogue<<<sm * 8, 256, 0, st>>>(W, d_jobs, b);
     if (cfg.ev) cudaEventRecord(cfg.ev[6], st);

@@ -104,6 +104,21 @@ struct JobDev {
     float* out_power_u;
     uint8_t* out_counts;
     unsigned long long* out_bits;
+    // series strings (string outputs requested; n_str = 0 otherwise).  The
+    // generator's bypass substrings are numbered string by string, so string
+    // q owns substrings [str_sub[q], str_sub[q + 1]).
+    int32_t n_str;
+    int32_t n_sub_tot;        // substrings over all modules
+    const int32_t* str_sub;   // [n_str + 1]
+    const int32_t* sub_base;  // [M] first substring of each module
+    const int32_t* sub_nk;    // [n_sub_tot] cells of each substring
+    const int32_t* sub_mod;   // [n_sub_tot] module of each substring
+    int64_t ss_base;          // (step, substring) entries
+    int64_t sq_base;          // (step, string) entries
+    int64_t it_str;           // string-kernel items
+    float2* kahan_str;        // [n_str][2]  (E, comp), (E_unshaded, comp)
+    float* out_str_power;     // [rows][n_str]
+    float* out_str_power_u;
 };
 
 struct WaveDev {
@@ -115,6 +130,7 @@ struct WaveDev {
     int32_t profile;    // count work (texel visits, sample tests) into Counters
     int64_t tot_js, tot_te, tot_ms, tot_cs;
     int64_t tot_win, tot_mod, tot_tri, tot_epi;  // tot_tri: (meshlet, step) warp items
+    int64_t tot_ss, tot_sq;                      // (step, substring) and (step, string) entries
     int64_t bin_cap, map_cap_tiles, big_cap, recv_cap;
 };
 
@@ -159,6 +175,10 @@ struct Buffers {
     float* ms_p;             // [tot_ms]
     float* ms_pu;            // [tot_ms]
     float* ms_beam;          // [tot_ms]  DNI * max(0, cos i)
+    float* ms_iu;            // [tot_ms]  unshaded cell current (string model)
+    float* ss_i;             // [tot_ss]  substring current limit per (step, substring) (string model)
+    float* sq_p;             // [tot_sq]  string MPP power per (step, string)
+    float* sq_pu;            // [tot_sq]  same without shading
     uint32_t* cs_cnt;        // [tot_cs]  shaded samples per (step, cell)
     unsigned long long* cs_bits;  // [tot_cs] shaded flags per (step, cell), fused path with flags requested
     uint32_t* t_far;         // [tot_te]  far-plane key of the tile (0 = no sample)
@@ -191,8 +211,8 @@ struct LaunchCfg {
 };
 
 constexpr int kStages = 6;  // setup, bin, tile (warp per tile / map raster), heavy tiles, pv/sample, epilogue
-constexpr int kLaunchesPerWave = 15;     // kernels launch_wave starts (fused path)
-constexpr int kLaunchesPerWaveMap = 14;  // (map path)
+constexpr int kLaunchesPerWave = 16;     // kernels launch_wave starts (fused path)
+constexpr int kLaunchesPerWaveMap = 15;  // (map path)
 
 cudaError_t launch_wave(const WaveDev* d_wave, const JobDev* d_jobs, const Buffers& b,
                         const LaunchCfg& cfg, int64_t tot_te_host);

@@ -35,7 +35,7 @@ PV3D_PATH_MAP = 1
 
 EXPORTED = ("pv3d_create", "pv3d_destroy", "pv3d_last_error", "pv3d_scene_load", "pv3d_generator_define",
             "pv3d_set_poses", "pv3d_set_sun", "pv3d_evaluate", "pv3d_submit", "pv3d_poll", "pv3d_release",
-            "pv3d_last_profile", "pv3d_module_shade_noalloc", "pv3d_evaluate_batch")
+            "pv3d_last_profile", "pv3d_module_shade_noalloc", "pv3d_evaluate_batch", "pv3d_generator_strings")
 
 
 class pv3d_opts(C.Structure):
@@ -87,7 +87,8 @@ class pv3d_result(C.Structure):
                 ("sample_bits", C.c_void_p), ("tests", C.c_int64), ("steps_lit", C.c_int64),
                 ("device_ms", C.c_float), ("waves", C.c_int32), ("nonempty_tiles", C.c_int64),
                 ("binned_tris", C.c_int64), ("kernel_launches", C.c_int64), ("latency_ms", C.c_float),
-                ("reserved1", C.c_int32)]
+                ("reserved1", C.c_int32), ("string_energy", C.c_void_p), ("string_energy_unshaded", C.c_void_p),
+                ("string_power", C.c_void_p), ("string_power_unshaded", C.c_void_p)]
 
 
 _lib = None
@@ -128,6 +129,7 @@ def load(build_if_missing: bool = False):
         lib.pv3d_poll.argtypes = [P, C.c_uint64, C.c_int32]
         lib.pv3d_release.argtypes = [P, C.c_uint32]
         lib.pv3d_last_profile.argtypes = [P, C.POINTER(pv3d_profile)]
+        lib.pv3d_generator_strings.argtypes = [P, C.c_uint32, C.POINTER(C.c_int32), P]
         lib.pv3d_evaluate_batch.argtypes = [P, C.c_int32, P, C.POINTER(pv3d_eval_opts), C.POINTER(pv3d_result)]
         lib.pv3d_module_shade_noalloc.argtypes = [P, C.c_int64, C.POINTER(pv3d_module), P, C.c_int32, C.c_int32,
                                                   P, P]
@@ -225,8 +227,17 @@ class Context:
         self._check(self.lib.pv3d_generator_define(self.h, scene_id, mods, m, lays, len(subs), trk, piv.shape[0],
                                                    C.byref(gid)))
         cells = int((np.asarray(gen.cells_u, np.int64) * np.asarray(gen.cells_v, np.int64)).sum())
-        self._gens[gid.value] = {"modules": m, "cells": cells, "steps": 0}
+        self._gens[gid.value] = {"modules": m, "cells": cells, "steps": 0, "strings": len(self.string_ids(gid.value))}
         return gid.value
+
+    def string_ids(self, gen_id: int) -> np.ndarray:
+        """pv3d_generator_strings: the generator's distinct string ids, ascending
+        (the order of the string outputs)."""
+        n = C.c_int32()
+        self._check(self.lib.pv3d_generator_strings(self.h, gen_id, C.byref(n), None))
+        ids = np.zeros(n.value, np.int32)
+        self._check(self.lib.pv3d_generator_strings(self.h, gen_id, C.byref(n), _p(ids)))
+        return ids
 
     def set_poses(self, gen_id: int, az_tilt: np.ndarray):
         a = np.ascontiguousarray(az_tilt, np.float32)
@@ -251,11 +262,13 @@ class Context:
         if gen_id not in self._gens:  # let the library report the unknown id
             return pv3d_result(is_device=1 if device else 0), {}
         g = self._gens[gen_id]
-        m, cells, n_steps = g["modules"], g["cells"], g["steps"]
+        m, cells, n_steps, ns = g["modules"], g["cells"], g["steps"], g["strings"]
         S = (step_end or n_steps) - step_begin
         shapes = dict(energy=((m,), "f8"), energy_unshaded=((m,), "f8"), power=((S, m), "f4"),
                       power_unshaded=((S, m), "f4"), cell_beam_loss=((cells,), "f8"),
-                      cell_counts=((S, cells), "u1"), sample_bits=((S, cells), "u8"))
+                      cell_counts=((S, cells), "u1"), sample_bits=((S, cells), "u8"),
+                      string_energy=((ns,), "f8"), string_energy_unshaded=((ns,), "f8"),
+                      string_power=((S, ns), "f4"), string_power_unshaded=((S, ns), "f4"))
         res = pv3d_result(is_device=1 if device else 0)
         arrays = {}
         for name in outputs:

@@ -82,6 +82,9 @@ def _load():
             lib.pv3d_oracle_string_power_from_counts.argtypes = (
                 [C.c_int32, P, P, P, P, P, C.c_int32, P, P, P, P, P, C.c_int32, C.c_double, C.c_double,
                  C.c_double, P, C.c_int64, P, C.c_int32, P, P, P])
+            lib.pv3d_oracle_sun_table.restype = C.c_int64
+            lib.pv3d_oracle_sun_table.argtypes = [C.c_double, C.c_int32, C.c_int32, C.c_double, C.c_int32,
+                                                  C.c_double, P, P, P]
             lib.pv3d_oracle_rays.restype = C.c_int
             lib.pv3d_oracle_rays.argtypes = [P, P, P, C.c_int64, C.c_double, C.c_int32, P]
             _lib = lib
@@ -291,6 +294,41 @@ def string_power_from_counts(w, steps, counts, i_ref=I_REF, v_cell=V_CELL, v_dio
         _ptr(np.ascontiguousarray(sun.dhi, np.float32)), _ptr(pz), int(w.n), i_ref, v_cell, v_diode,
         _ptr(steps), steps.size, _ptr(ms), ids.size, _ptr(cnt), _ptr(p), _ptr(pu))
     return p, pu
+
+
+def sun_table(lat_deg: float, day_first: int, n_days: int, step_h: float, daylight_only: bool = True,
+              dhi_fraction: float = 0.1):
+    """Clear-sky sun table (see pv3d_oracle_sun_table): (xyz [N, 3], dni [N], dhi [N])."""
+    lib = _load()
+    n = lib.pv3d_oracle_sun_table(lat_deg, day_first, n_days, step_h, int(daylight_only), dhi_fraction,
+                                  None, None, None)
+    xyz = np.zeros((n, 3)); dni = np.zeros(n); dhi = np.zeros(n)
+    lib.pv3d_oracle_sun_table(lat_deg, day_first, n_days, step_h, int(daylight_only), dhi_fraction,
+                              _ptr(xyz), _ptr(dni), _ptr(dhi))
+    return xyz, dni, dhi
+
+
+def heat_map(sun_xyz, p_gen, pu_gen, dt_h, n_az: int, n_zen: int):
+    """Effective-shading map of the generator over the sky (the paper's Fig. 6:
+    the shading factor as a function of the sun's azimuth and zenith): the
+    steps with the sun above the horizon are binned by compass azimuth
+    [0, 360) in n_az bins and zenith [0, 90] in n_zen bins (the last bin
+    closed); per bin the sums of the generator's energy sum_steps P * dt with
+    and without shading and the step count.  The bin's effective shading factor
+    is 1 - E / E_unshaded."""
+    s = np.asarray(sun_xyz, np.float64)
+    up = s[:, 2]
+    lit = up > 0
+    az = np.degrees(np.arctan2(s[:, 0], s[:, 1])) % 360.0
+    zen = np.degrees(np.arccos(np.clip(up, -1.0, 1.0)))
+    ia = np.minimum((az / 360.0 * n_az).astype(np.int64), n_az - 1)
+    iz = np.minimum((zen / 90.0 * n_zen).astype(np.int64), n_zen - 1)
+    e = np.zeros((n_zen, n_az)); eu = np.zeros((n_zen, n_az)); cnt = np.zeros((n_zen, n_az), np.int64)
+    dt = np.asarray(dt_h, np.float64)
+    np.add.at(e, (iz[lit], ia[lit]), (np.asarray(p_gen, np.float64) * dt)[lit])
+    np.add.at(eu, (iz[lit], ia[lit]), (np.asarray(pu_gen, np.float64) * dt)[lit])
+    np.add.at(cnt, (iz[lit], ia[lit]), 1)
+    return e, eu, cnt
 
 
 def popcount64(a: np.ndarray) -> np.ndarray:

@@ -940,6 +940,64 @@ int pv3d_oracle_string_power_from_counts(int32_t n_mods, const float* mod_f, con
     return 0;
 }
 
+/* ------------------------------------------------------------------------- */
+/* sun table (the inputs of steps 3-4: sun positions and irradiance over the  */
+/* simulated period -- the paper takes TMY data, measured series or a        */
+/* clear-sky model without naming one)                                        */
+/* ------------------------------------------------------------------------- */
+/*
+ * Reading: solar time without longitude correction or equation of time; the
+ * declination of Cooper (1969), delta = 23.45 deg * sin(360 deg * (284 + n) / 365)
+ * on day n; the hour angle omega = 15 deg * (t - 12) at solar hour t.  The unit
+ * vector toward the sun, east-north-up, is the rotation of the equatorial
+ * direction (cos delta cos omega, cos delta sin omega, sin delta) to the site:
+ *   east  = -cos(delta) sin(omega)
+ *   north =  sin(delta) cos(phi) - cos(delta) cos(omega) sin(phi)
+ *   up    =  sin(delta) sin(phi) + cos(delta) cos(omega) cos(phi).
+ * Beam irradiance of Meinel & Meinel (1976), DNI = 1353 * 0.7^(AM^0.678) W/m^2,
+ * with the air mass of Kasten & Young (1989),
+ * AM = 1 / (cos z + 0.50572 (96.07995 - z)^-1.6364), z the zenith angle in
+ * degrees; diffuse DHI = dhi_fraction * DNI; both 0 with the sun at or below
+ * the horizon.  Steps at t = 0, step_h, 2 step_h, ... (t < 24) of days
+ * day_first .. day_first + n_days - 1; with daylight_only only the steps with
+ * up > 0 are kept.  Returns the number of steps (xyz, dni, dhi may be NULL to
+ * count them).
+ */
+int64_t pv3d_oracle_sun_table(double lat_deg, int32_t day_first, int32_t n_days, double step_h,
+                              int32_t daylight_only, double dhi_fraction, double* xyz, double* dni, double* dhi)
+{
+    const double deg = M_PI / 180.0;
+    const double phi = lat_deg * deg;
+    int64_t per_day = 0;
+    while (per_day * step_h < 24.0 - 1e-9) ++per_day;
+    int64_t out = 0;
+    for (int32_t d = 0; d < n_days; ++d) {
+        double n = (double)(day_first + d);
+        double delta = 23.45 * deg * sin(360.0 * deg * (284.0 + n) / 365.0);
+        for (int64_t k = 0; k < per_day; ++k) {
+            double t = (double)k * step_h;
+            double omega = 15.0 * deg * (t - 12.0);
+            double e = -cos(delta) * sin(omega);
+            double nn = sin(delta) * cos(phi) - cos(delta) * cos(omega) * sin(phi);
+            double u = sin(delta) * sin(phi) + cos(delta) * cos(omega) * cos(phi);
+            double len = sqrt(e * e + nn * nn + u * u);
+            e /= len; nn /= len; u /= len;
+            if (daylight_only && !(u > 0.0)) continue;
+            double b = 0.0;
+            if (u > 0.0) {
+                double z = acos(u) / deg;
+                double am = 1.0 / (u + 0.50572 * pow(96.07995 - z, -1.6364));
+                b = 1353.0 * pow(0.7, pow(am, 0.678));
+            }
+            if (xyz) { xyz[3 * out] = e; xyz[3 * out + 1] = nn; xyz[3 * out + 2] = u; }
+            if (dni) dni[out] = b;
+            if (dhi) dhi[out] = dhi_fraction * b;
+            ++out;
+        }
+    }
+    return out;
+}
+
 /* Sample positions of one module at one step (for tests): xyz[cells*n*n*3] in
  * cell order, then sample order k = j*n + i. */
 int pv3d_oracle_samples(int32_t n_mods, const float* mod_f, const int32_t* mod_i, int32_t n_trk,

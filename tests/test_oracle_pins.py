@@ -323,6 +323,61 @@ def test_string_power_from_counts_matches_modules_and_strings():
     np.testing.assert_allclose(p[:, 2], p_mod[:, 5], rtol=1e-12, atol=1e-12)
 
 
+def test_sun_table_closed_forms():
+    """Noon elevation 90 - lat + delta (delta = 0 at the equinox day 81 of
+    Cooper's formula, 23.45 sin(449.75 deg) at day 172), a 12-hour day at the
+    equinox and 2 acos(-tan(lat) tan(delta)) / 15 hours otherwise, morning and
+    afternoon mirror images, unit vectors."""
+    for lat in (0.0, 23.0, 40.0, 52.5, -33.0):
+        xyz, dni, dhi = oracle.sun_table(lat, 81, 1, 0.25, daylight_only=False)
+        noon = xyz[48]
+        assert abs(math.degrees(math.asin(noon[2])) - (90.0 - abs(lat))) < 1e-9
+        np.testing.assert_allclose(np.linalg.norm(xyz, axis=1), 1.0, atol=1e-14)
+        np.testing.assert_allclose(xyz[47 - np.arange(40)][:, [1, 2]], xyz[49 + np.arange(40)][:, [1, 2]], atol=1e-14)
+        np.testing.assert_allclose(xyz[47 - np.arange(40)][:, 0], -xyz[49 + np.arange(40)][:, 0], atol=1e-14)
+    d172 = math.radians(23.45 * math.sin(math.radians(360.0 * 456 / 365)))
+    xyz, _, _ = oracle.sun_table(40.0, 172, 1, 1.0, daylight_only=False)
+    assert abs(math.degrees(math.asin(xyz[12, 2])) - (50.0 + math.degrees(d172))) < 1e-9
+    assert abs(math.degrees(math.asin(xyz[12, 2])) - 73.45) < 0.01
+    # day length from the sunrise hour angle, counted on a fine grid
+    for lat, day in ((40.0, 172), (40.0, 355), (60.0, 100)):
+        dec = math.radians(23.45 * math.sin(math.radians(360.0 * (284 + day) / 365)))
+        hours = 2 * math.degrees(math.acos(-math.tan(math.radians(lat)) * math.tan(dec))) / 15.0
+        xyz, _, _ = oracle.sun_table(lat, day, 1, 0.01, daylight_only=True)
+        assert abs(xyz.shape[0] * 0.01 - hours) <= 0.02
+
+
+def test_sun_table_irradiance_published_values():
+    """Meinel's beam at air mass 1 is 1353 * 0.7 = 947.1 W/m^2 (Kasten & Young
+    give 0.9997 at the zenith); at 60 and 80 degrees of zenith their air mass
+    lies just under the plane-parallel 1/cos z (2 and 5.76); night steps carry
+    no irradiance; DHI = 0.1 DNI; the beam rises with the sun."""
+    step = 1.0 / 3.0
+    xyz, dni, dhi = oracle.sun_table(0.0, 81, 1, step, daylight_only=False)
+    # equator at the equinox: the zenith angle equals |hour angle|
+    am = (np.log(np.maximum(dni, 1e-300) / 1353.0) / math.log(0.7)) ** (1 / 0.678)
+    noon, h8, h6_40 = 36, 24, 20           # solar hours 12, 8, 6:40 -> zenith 0, 60, 80 deg
+    assert abs(dni[noon] - 947.1) < 0.4 and abs(am[noon] - 0.9997) < 3e-4
+    assert 1.98 < am[h8] < 2.0
+    assert 5.5 < am[h6_40] < 1.0 / math.cos(math.radians(80.0))
+    assert np.all(dni[xyz[:, 2] <= 0] == 0) and np.all(dhi == 0.1 * dni)
+    assert np.all(np.diff(dni[19:37]) > 0)
+
+
+def test_heat_map_bins():
+    """Bins by compass azimuth and zenith; energies and counts add up; night
+    steps are left out."""
+    s = np.array([[0.0, 1.0, 0.0001], [1.0, 0.0, 1.0], [0.0, -1.0, 1.0], [-1.0, 0.0, 0.2], [0.3, 0.2, -0.5]])
+    s /= np.linalg.norm(s, axis=1, keepdims=True)
+    p = np.array([1.0, 2.0, 3.0, 4.0, 5.0]); pu = p + 1; dt = np.full(5, 0.5)
+    e, eu, cnt = oracle.heat_map(s, p, pu, dt, 4, 3)
+    assert cnt.sum() == 4 and abs(e.sum() - 0.5 * 10.0) < 1e-12 and abs(eu.sum() - 0.5 * 14.0) < 1e-12
+    assert cnt[2, 0] == 1          # north at the horizon: azimuth 0, zenith ~90 (last bin)
+    assert cnt[1, 1] == 1          # east at 45 deg zenith: azimuth 90
+    assert cnt[1, 2] == 1          # south at 45 deg zenith: azimuth 180
+    assert cnt[2, 3] == 1          # west, low
+
+
 # ---------------------------------------------------------------------------
 # invariants
 # ---------------------------------------------------------------------------

@@ -195,6 +195,21 @@ typedef struct pv3d_result {
     double* string_energy_unshaded;  /* [NS] */
     float* string_power;             /* [S x NS] string P_mpp per step, W */
     float* string_power_unshaded;    /* [S x NS] */
+    /* effective-shading map over the sky (pv3d_evaluate only; Section 3, Fig. 6:
+     * the shading factor as a function of the sun's position): the evaluated
+     * steps with the sun above the horizon, binned by compass azimuth
+     * (heat_az_bins bins over [0, 360), clockwise from north) and zenith angle
+     * (heat_zen_bins bins over [0, 90]); per bin, row-major [zen][az], the
+     * generator's energy (sum over modules and the bin's steps of P_mpp * dt)
+     * with and without shading, and the step count, summed in FP64 in step
+     * order.  The bin's effective shading factor is
+     * 1 - heat_energy / heat_energy_unshaded.  Set both bin counts (1..1024
+     * each) and the three arrays, or leave them 0 / NULL. */
+    int32_t heat_az_bins;
+    int32_t heat_zen_bins;
+    double* heat_energy;             /* [heat_zen_bins x heat_az_bins] Wh */
+    double* heat_energy_unshaded;    /* [heat_zen_bins x heat_az_bins] Wh */
+    int32_t* heat_steps;             /* [heat_zen_bins x heat_az_bins] */
 } pv3d_result;
 
 /* ---- context ------------------------------------------------------------ */
@@ -232,6 +247,45 @@ int pv3d_generator_define(pv3d_ctx* ctx, uint32_t scene_id,
                           const pv3d_layout* layouts, int32_t n_layouts,
                           const pv3d_tracker* trackers, int32_t n_trackers,
                           uint32_t* gen_id);
+
+/*
+ * Clear-sky sun table computed on the device (the inputs of steps 3-4: the
+ * paper takes TMY data, measured series or a clear-sky model it does not
+ * name).  Solar time without longitude correction or equation of time;
+ * declination of Cooper (1969), 23.45 deg * sin(360 deg * (284 + n) / 365) on
+ * day n; hour angle 15 deg per hour from solar noon; unit vector toward the
+ * sun in east-north-up axes; beam irradiance of Meinel & Meinel (1976),
+ * DNI = 1353 * 0.7^(AM^0.678) W/m^2, with the air mass of Kasten & Young
+ * (1989); DHI = dhi_fraction * DNI; step duration step_h hours.  All in FP64
+ * on the device.  Replaces the generator's sun table like pv3d_set_sun; with
+ * tracker_tilt_max_deg > 0 and trackers present, also sets every tracker to
+ * the ideal two-axis pose of each step (compass azimuth of the sun, tilt =
+ * zenith angle clamped to the maximum) like pv3d_set_poses.  *n_steps
+ * (may be NULL) receives the table's length.  Errors: PV3D_E_INVALID (options
+ * out of range, or daylight_only with no daylight step), PV3D_E_NOTFOUND,
+ * PV3D_E_NOMEM, PV3D_E_DEVICE.
+ */
+typedef struct pv3d_sky_opts {
+    double latitude_deg;         /* site latitude, degrees north, -89.9 .. 89.9 */
+    double step_h;               /* hours between steps, (0, 24]; steps at solar hours 0, step_h, ... < 24 */
+    int32_t day_first;           /* first day of the year, 1..366 */
+    int32_t n_days;              /* days, 1..3660 */
+    int32_t daylight_only;       /* 1: keep only the steps with the sun above the horizon */
+    float dhi_fraction;          /* DHI / DNI [0.1] */
+    float tracker_tilt_max_deg;  /* > 0: also set ideal tracker poses with this tilt limit [0: poses untouched] */
+    int32_t reserved[5];
+} pv3d_sky_opts;
+
+int pv3d_set_sun_clear_sky(pv3d_ctx* ctx, uint32_t gen_id, const pv3d_sky_opts* opts, int64_t* n_steps);
+
+/*
+ * Copy the generator's sun table (set by pv3d_set_sun or
+ * pv3d_set_sun_clear_sky) to host arrays of n_steps entries (its length):
+ * sun_xyz[n_steps][3], dni, dhi, dt_h (any may be NULL).  Errors:
+ * PV3D_E_INVALID (n_steps differs from the table's length), PV3D_E_NOTFOUND.
+ */
+int pv3d_sun_table(pv3d_ctx* ctx, uint32_t gen_id, double* sun_xyz, float* dni, float* dhi, float* dt_h,
+                   int64_t n_steps);
 
 /*
  * Series strings of a generator (Section 2: the modules are wired in series

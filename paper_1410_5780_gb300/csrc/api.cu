@@ -91,7 +91,7 @@ struct pv3d_ctx {
     std::map<uint32_t, GenH> gens;
     uint32_t next_id = 1;
     // workspace pools
-    DevBuf lp, win, ms, ms_p, ms_pu, ms_beam, ms_iu, ss_i, sq_p, sq_pu, kahan_str, cs_cnt, cs_bits, t_far, t_cnt, t_off, t_cur, t_slot, t_rcnt, t_roff, t_rcur, nonempty, heavy, bins, pairs, recv, map,
+    DevBuf lp, win, ms, ms_p, ms_pu, ms_beam, ms_iu, ss_i, sq_p, sq_pu, kahan_str, js_p, js_pu, js_bin, heat, cs_cnt, cs_bits, t_far, t_cnt, t_off, t_cur, t_slot, t_rcnt, t_roff, t_rcur, nonempty, heavy, bins, pairs, recv, map,
         big, block_sums, ctr, waves, jobs, kahan_mod, kahan_cell, staging;
     int64_t bin_cap = 0, map_cap_tiles = 0, big_cap = 0, recv_cap = 0;
     uint64_t bufgen = 0;  // bumped whenever a pool is reallocated (captured graphs hold its pointers)
@@ -580,13 +580,138 @@ extern "C" int pv3d_set_sun(pv3d_ctx* c, uint32_t gen_id, const double* sun_xyz,
     return PV3D_OK;
 }
 
+extern "C" int pv3d_sun_table(pv3d_ctx* c, uint32_t gen_id, double* sun_xyz, float* dni, float* dhi, float* dt_h,
+                              int64_t n_steps)
+{
+    if (!c) return PV3D_E_INVALID;
+    auto it = c->gens.find(gen_id);
+    if (it == c->gens.end()) return fail(c, PV3D_E_NOTFOUND, "unknown generator %u", gen_id);
+    const GenH& g = it->second;
+    if (n_steps != g.n_steps || n_steps < 1) return fail(c, PV3D_E_INVALID, "the sun table has %lld steps",
+                                                          (long long)g.n_steps);
+    cudaSetDevice(c->device);
+    CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (sun_xyz) CUDA_TRY(c, cudaMemcpy(sun_xyz, g.d_sun, (size_t)n_steps * 24, cudaMemcpyDeviceToHost));
+    if (dni) CUDA_TRY(c, cudaMemcpy(dni, g.d_dni, (size_t)n_steps * 4, cudaMemcpyDeviceToHost));
+    if (dhi) CUDA_TRY(c, cudaMemcpy(dhi, g.d_dhi, (size_t)n_steps * 4, cudaMemcpyDeviceToHost));
+    if (dt_h) CUDA_TRY(c, cudaMemcpy(dt_h, g.d_dt, (size_t)n_steps * 4, cudaMemcpyDeviceToHost));
+    return PV3D_OK;
+}
+
+extern "C" int pv3d_set_sun_clear_sky(pv3d_ctx* c, uint32_t gen_id, const pv3d_sky_opts* o, int64_t* n_steps)
+{
+    if (!c || !o) return PV3D_E_INVALID;
+    auto it = c->gens.find(gen_id);
+    if (it == c->gens.end()) return fail(c, PV3D_E_NOTFOUND, "unknown generator %u", gen_id);
+    GenH& g = it->second;
+    if (!(std::fabs(o->latitude_deg) <= 89.9) || !(o->step_h > 0.0 && o->step_h <= 24.0) || o->day_first < 1 ||
+        o->day_first > 366 || o->n_days < 1 || o->n_days > 3660 || !(o->dhi_fraction >= 0.f) ||
+        !(o->tracker_tilt_max_deg >= 0.f && o->tracker_tilt_max_deg <= 90.f))
+        return fail(c, PV3D_E_INVALID, "clear-sky options out of range");
+    int64_t per_day = 0;
+    while ((double)per_day * o->step_h < 24.0 - 1e-9) ++per_day;
+    const int64_t n_all = per_day * o->n_days;
+    if (n_all > (1ll << 30)) return fail(c, PV3D_E_INVALID, "sun table too long");
+    const double dhi_f = o->dhi_fraction > 0.f ? o->dhi_fraction : 0.1;
+    cudaSetDevice(c->device);
+    cudaStream_t st = c->stream;
+    double* d_xyz = nullptr;
+    float *d_dni = nullptr, *d_dhi = nullptr, *d_dt = nullptr, *d_poses = nullptr;
+    uint8_t* d_lit = nullptr;
+    int64_t* d_idx = nullptr;
+    auto cleanup = [&]() {
+        void* ps[] = {d_xyz, d_dni, d_dhi, d_dt, d_lit, d_idx, d_poses};
+        for (void* p : ps)
+            if (p) cudaFree(p);
+    };
+    if (cudaMalloc(&d_xyz, (size_t)n_all * 24) != cudaSuccess || cudaMalloc(&d_dni, (size_t)n_all * 4) != cudaSuccess ||
+        cudaMalloc(&d_dhi, (size_t)n_all * 4) != cudaSuccess || cudaMalloc(&d_dt, (size_t)n_all * 4) != cudaSuccess ||
+        cudaMalloc(&d_lit, (size_t)n_all) != cudaSuccess) {
+        cleanup();
+        cudaGetLastError();
+        return fail(c, PV3D_E_NOMEM, "sun table of %lld steps", (long long)n_all);
+    }
+    std::vector<uint8_t> lit((size_t)n_all);
+    if (launch_sun_table(o->latitude_deg, o->day_first, per_day, o->step_h, dhi_f, n_all, d_xyz, d_dni, d_dhi, d_dt,
+                         d_lit, st) != cudaSuccess ||
+        cudaMemcpyAsync(lit.data(), d_lit, (size_t)n_all, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+        cleanup();
+        return fail(c, PV3D_E_DEVICE, "sun table kernel: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    int64_t n = n_all;
+    if (o->daylight_only) {
+        std::vector<int64_t> idx;
+        for (int64_t k = 0; k < n_all; ++k)
+            if (lit[k]) idx.push_back(k);
+        n = (int64_t)idx.size();
+        if (n == 0) {
+            cleanup();
+            return fail(c, PV3D_E_INVALID, "no daylight step in the requested period");
+        }
+        double* k_xyz = nullptr;
+        float *k_dni = nullptr, *k_dhi = nullptr;
+        if (cudaMalloc(&d_idx, (size_t)n * 8) != cudaSuccess || cudaMalloc(&k_xyz, (size_t)n * 24) != cudaSuccess ||
+            cudaMalloc(&k_dni, (size_t)n * 4) != cudaSuccess || cudaMalloc(&k_dhi, (size_t)n * 4) != cudaSuccess) {
+            if (k_xyz) cudaFree(k_xyz);
+            if (k_dni) cudaFree(k_dni);
+            if (k_dhi) cudaFree(k_dhi);
+            cleanup();
+            cudaGetLastError();
+            return fail(c, PV3D_E_NOMEM, "sun table");
+        }
+        if (cudaMemcpyAsync(d_idx, idx.data(), (size_t)n * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            launch_gather_sun(d_idx, n, d_xyz, d_dni, d_dhi, k_xyz, k_dni, k_dhi, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            cudaFree(k_xyz); cudaFree(k_dni); cudaFree(k_dhi);
+            cleanup();
+            return fail(c, PV3D_E_DEVICE, "sun table gather: %s", cudaGetErrorString(cudaGetLastError()));
+        }
+        cudaFree(d_xyz); cudaFree(d_dni); cudaFree(d_dhi);
+        d_xyz = k_xyz; d_dni = k_dni; d_dhi = k_dhi;
+        lit.assign((size_t)n, 1);  // d_dt holds step_h in its first n entries
+    }
+    const bool poses = o->tracker_tilt_max_deg > 0.f && g.n_trk > 0;
+    if (poses) {
+        if (cudaMalloc(&d_poses, (size_t)n * g.n_trk * 8) != cudaSuccess) {
+            cleanup();
+            cudaGetLastError();
+            return fail(c, PV3D_E_NOMEM, "pose table");
+        }
+        if (launch_ideal_poses(d_xyz, n, g.n_trk, o->tracker_tilt_max_deg * 0.017453292519943295f, d_poses, st) !=
+                cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            cleanup();
+            return fail(c, PV3D_E_DEVICE, "pose kernel: %s", cudaGetErrorString(cudaGetLastError()));
+        }
+    } else if (g.n_trk > 0 && g.n_pose_steps && g.n_pose_steps != n) {
+        cleanup();
+        return fail(c, PV3D_E_INVALID, "sun table length differs from the pose table");
+    }
+    void* olds[] = {g.d_sun, g.d_dni, g.d_dhi, g.d_dt};
+    for (void* p : olds)
+        if (p) cudaFree(p);
+    g.d_sun = d_xyz; g.d_dni = d_dni; g.d_dhi = d_dhi; g.d_dt = d_dt;
+    g.n_steps = n;
+    g.lit = std::move(lit);
+    if (poses) {
+        if (g.d_poses) cudaFree(g.d_poses);
+        g.d_poses = d_poses;
+        g.n_pose_steps = n;
+    }
+    if (d_lit) cudaFree(d_lit);
+    if (d_idx) cudaFree(d_idx);
+    if (n_steps) *n_steps = n;
+    return PV3D_OK;
+}
+
 // ---------------------------------------------------------------------------
 // evaluation
 // ---------------------------------------------------------------------------
 namespace {
 
 struct EvalSetup {
-    int n, R, K, tile, fused, profile, count, strings;
+    int n, R, K, tile, fused, profile, count, strings, heat;
     int64_t b, e;
     float i_ref, v_cell, v_diode;
 };
@@ -619,13 +744,19 @@ static int check_eval(pv3d_ctx* c, const GenH& g, const pv3d_eval_opts* o, const
     if (!out) return fail(c, PV3D_E_INVALID, "null result");
     if (out->sample_bits && es.n > 8) return fail(c, PV3D_E_INVALID, "sample_bits needs samples_per_side <= 8");
     es.strings = out->string_energy || out->string_energy_unshaded || out->string_power || out->string_power_unshaded;
+    es.heat = out->heat_az_bins > 0 || out->heat_zen_bins > 0 || out->heat_energy || out->heat_energy_unshaded ||
+              out->heat_steps;
+    if (es.heat && (out->heat_az_bins < 1 || out->heat_az_bins > 1024 || out->heat_zen_bins < 1 ||
+                    out->heat_zen_bins > 1024 || !out->heat_energy || !out->heat_energy_unshaded || !out->heat_steps))
+        return fail(c, PV3D_E_INVALID, "heat map: bin counts 1..1024 and all three arrays");
     return PV3D_OK;
 }
 
 // Fill a JobDev for generator g over steps [step0, step0 + k).
 static JobDev make_job(pv3d_ctx* c, const GenH& g, const SceneH& s, const EvalSetup& es, int64_t step0, int k,
                        float2* kmod, float2* kcell, float* pw, float* pwu, uint8_t* cnt, unsigned long long* bits,
-                       float2* kstr = nullptr, float* spw = nullptr, float* spwu = nullptr)
+                       float2* kstr = nullptr, float* spw = nullptr, float* spwu = nullptr, double* heat_e = nullptr,
+                       double* heat_eu = nullptr, int32_t* heat_n = nullptr, int heat_az = 0, int heat_zen = 0)
 {
     JobDev J{};
     J.tri = s.d_tri;
@@ -682,6 +813,13 @@ static JobDev make_job(pv3d_ctx* c, const GenH& g, const SceneH& s, const EvalSe
         J.out_str_power = spw;
         J.out_str_power_u = spwu;
     }
+    if (heat_e) {
+        J.heat_az = heat_az;
+        J.heat_zen = heat_zen;
+        J.heat_e = heat_e;
+        J.heat_eu = heat_eu;
+        J.heat_n = heat_n;
+    }
     (void)c;
     return J;
 }
@@ -709,6 +847,7 @@ static WaveDev pack_wave(std::vector<JobDev>& jobs, size_t first, size_t last, i
         J.ss_base = W.tot_ss;
         J.sq_base = W.tot_sq;
         J.it_str = W.tot_sq;
+        J.it_heat = W.tot_heat;
         int64_t groups = (J.n_mods + kWinPerItem - 1) / kWinPerItem;
         W.tot_js += J.k;
         W.tot_te += (int64_t)J.k * J.tiles_x * J.tiles_x;
@@ -720,6 +859,7 @@ static WaveDev pack_wave(std::vector<JobDev>& jobs, size_t first, size_t last, i
         W.tot_epi += (int64_t)J.n_cells + J.n_mods + J.n_str;
         W.tot_ss += (int64_t)J.k * (J.n_str ? J.n_sub_tot : 0);
         W.tot_sq += (int64_t)J.k * J.n_str;
+        W.tot_heat += (int64_t)J.heat_az * J.heat_zen;
         if (J.out_bits) W.want_bits = 1;
     }
     return W;
@@ -729,6 +869,8 @@ static int ensure_workspace(pv3d_ctx* c, int64_t js, int64_t te, int64_t ms, int
                             bool want_bits, int64_t ss = 0, int64_t sq = 0)
 {
     int rc;
+    if ((rc = ensure(c, c->js_p, js * 4)) || (rc = ensure(c, c->js_pu, js * 4)) || (rc = ensure(c, c->js_bin, js * 4)))
+        return rc;
     if (sq > 0 && ((rc = ensure(c, c->ms_iu, ms * 4)) || (rc = ensure(c, c->ss_i, ss * 4)) ||
                    (rc = ensure(c, c->sq_p, sq * 4)) || (rc = ensure(c, c->sq_pu, sq * 4))))
         return rc;
@@ -772,6 +914,9 @@ static Buffers buffers_of(pv3d_ctx* c)
     B.ss_i = (float*)c->ss_i.p;
     B.sq_p = (float*)c->sq_p.p;
     B.sq_pu = (float*)c->sq_pu.p;
+    B.js_p = (float*)c->js_p.p;
+    B.js_pu = (float*)c->js_pu.p;
+    B.js_bin = (int32_t*)c->js_bin.p;
     B.cs_cnt = (uint32_t*)c->cs_cnt.p;
     B.cs_bits = (unsigned long long*)c->cs_bits.p;
     B.t_far = (uint32_t*)c->t_far.p;
@@ -832,8 +977,8 @@ static int wave_graph(pv3d_ctx* c, const LaunchCfg& cfg0, int max_jobs, cudaGrap
     if ((rc = ensure(c, c->wave_slot, sizeof(WaveDev))) ||
         (rc = ensure(c, c->jobs_slot, (size_t)std::max(max_jobs, 1) * sizeof(JobDev))))
         return rc;
-    const uint64_t key = (c->bufgen << 8) ^ ((uint64_t)cfg0.tile << 3) ^ ((uint64_t)cfg0.fused << 1) ^
-                         (uint64_t)cfg0.profile;
+    const uint64_t key = (c->bufgen << 10) ^ ((uint64_t)cfg0.extras << 8) ^ ((uint64_t)cfg0.tile << 3) ^
+                         ((uint64_t)cfg0.fused << 1) ^ (uint64_t)cfg0.profile;
     if (c->graph_exec && c->graph_key == key) {
         *out = c->graph_exec;
         return PV3D_OK;
@@ -868,9 +1013,10 @@ static int wave_graph(pv3d_ctx* c, const LaunchCfg& cfg0, int max_jobs, cudaGrap
 // and replay the captured graph (or launch the kernels when stage events are
 // recorded).
 static int run_waves(pv3d_ctx* c, const std::vector<WaveDev>& waves, cudaStream_t st, int tile, bool fused,
-                     bool profile, bool count)
+                     bool profile, bool count, int extras = 0)
 {
     LaunchCfg cfg;
+    cfg.extras = extras;
     cfg.sm_count = c->sm_count;
     cfg.tile = tile;
     cfg.fused = fused ? 1 : 0;
@@ -974,10 +1120,15 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
     float* d_sp = dev ? out->string_power : (out->string_power ? (float*)(sb + off_sp) : nullptr);
     float* d_spu = dev ? out->string_power_unshaded : (out->string_power_unshaded ? (float*)(sb + off_spu) : nullptr);
 
+    const int64_t n_bins = es.heat ? (int64_t)out->heat_az_bins * out->heat_zen_bins : 0;
     if ((rc = ensure(c, c->kahan_mod, (size_t)g.M * 2 * sizeof(float2))) ||
         (rc = ensure(c, c->kahan_cell, (size_t)g.C * sizeof(float2))) ||
-        (es.strings && (rc = ensure(c, c->kahan_str, (size_t)NS * 2 * sizeof(float2)))))
+        (es.strings && (rc = ensure(c, c->kahan_str, (size_t)NS * 2 * sizeof(float2)))) ||
+        (es.heat && (rc = ensure(c, c->heat, (size_t)n_bins * 20))))
         return rc;
+    double* h_e = es.heat ? (double*)c->heat.p : nullptr;
+    double* h_eu = es.heat ? h_e + n_bins : nullptr;
+    int32_t* h_n = es.heat ? (int32_t*)(h_eu + n_bins) : nullptr;
 
     // plan: one job per wave
     std::vector<JobDev> jobs;
@@ -985,7 +1136,8 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
     for (int64_t s0 = es.b; s0 < es.e; s0 += es.K) {
         int k = (int)std::min<int64_t>(es.K, es.e - s0);
         jobs.push_back(make_job(c, g, s, es, s0, k, (float2*)c->kahan_mod.p, (float2*)c->kahan_cell.p, d_p, d_pu,
-                                d_cnt, d_bits, (float2*)c->kahan_str.p, d_sp, d_spu));
+                                d_cnt, d_bits, (float2*)c->kahan_str.p, d_sp, d_spu, h_e, h_eu, h_n,
+                                es.heat ? out->heat_az_bins : 0, es.heat ? out->heat_zen_bins : 0));
         waves.push_back(pack_wave(jobs, jobs.size() - 1, jobs.size(), tile_sh, u24, es.fused, es.count));
     }
     int64_t mjs = 0, mte = 0, mms = 0, mcs = 0, mss = 0, msq = 0;
@@ -994,6 +1146,7 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
         mms = std::max(mms, W.tot_ms); mcs = std::max(mcs, W.tot_cs);
         mss = std::max(mss, W.tot_ss); msq = std::max(msq, W.tot_sq);
     }
+    const int extras = (es.strings ? 1 : 0) | (es.heat ? 2 : 0);
     Counters hc{};
     for (int attempt = 0; attempt < 4; ++attempt) {
         if ((rc = ensure_workspace(c, mjs, mte, mms, mcs, es.tile, es.fused, d_bits != nullptr, mss, msq))) return rc;
@@ -1008,12 +1161,19 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
         CUDA_TRY(c, cudaMemsetAsync(c->kahan_mod.p, 0, (size_t)g.M * 2 * sizeof(float2), st));
         CUDA_TRY(c, cudaMemsetAsync(c->kahan_cell.p, 0, (size_t)g.C * sizeof(float2), st));
         if (es.strings) CUDA_TRY(c, cudaMemsetAsync(c->kahan_str.p, 0, (size_t)NS * 2 * sizeof(float2), st));
+        if (es.heat) CUDA_TRY(c, cudaMemsetAsync(c->heat.p, 0, (size_t)n_bins * 20, st));
         CUDA_TRY(c, cudaEventRecord(c->ev0, st));
-        if ((rc = run_waves(c, waves, st, es.tile, es.fused, es.profile, es.count))) return rc;
+        if ((rc = run_waves(c, waves, st, es.tile, es.fused, es.profile, es.count, extras))) return rc;
         CUDA_TRY(c, launch_finalize_pairs((const float2*)c->kahan_mod.p, g.M, (const float2*)c->kahan_cell.p, g.C,
                                           d_e, d_eu, d_cl, st));
         if (es.strings)
             CUDA_TRY(c, launch_finalize_pairs((const float2*)c->kahan_str.p, NS, nullptr, 0, d_se, d_seu, nullptr, st));
+        if (es.heat) {
+            const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+            CUDA_TRY(c, cudaMemcpyAsync(out->heat_energy, h_e, (size_t)n_bins * 8, kind, st));
+            CUDA_TRY(c, cudaMemcpyAsync(out->heat_energy_unshaded, h_eu, (size_t)n_bins * 8, kind, st));
+            CUDA_TRY(c, cudaMemcpyAsync(out->heat_steps, h_n, (size_t)n_bins * 4, kind, st));
+        }
         CUDA_TRY(c, cudaEventRecord(c->ev1, st));
         CUDA_TRY(c, cudaMemcpyAsync(&hc, c->ctr.p, sizeof(Counters), cudaMemcpyDeviceToHost, st));
         CUDA_TRY(c, cudaStreamSynchronize(st));
@@ -1052,7 +1212,9 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
     out->waves = (int32_t)waves.size();
     out->nonempty_tiles = (int64_t)hc.stat_nonempty;
     out->binned_tris = (int64_t)hc.stat_bins;
-    out->kernel_launches = (int64_t)waves.size() * (es.fused ? kLaunchesPerWave : kLaunchesPerWaveMap) + 1;
+    out->kernel_launches = (int64_t)waves.size() * ((es.fused ? kLaunchesPerWave : kLaunchesPerWaveMap) +
+                                                    (es.strings ? 1 : 0) + (es.heat ? 2 : 0)) +
+                           1 + (es.strings ? 1 : 0);
     if (es.profile || es.count) {
         pv3d_profile& P = c->last_prof;
         P = pv3d_profile{};
@@ -1410,7 +1572,8 @@ extern "C" int pv3d_submit(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o
     int rc = check_eval(c, g, o, out, r->es);
     if (rc) return rc;
     if (o && o->path == PV3D_PATH_MAP) return fail(c, PV3D_E_INVALID, "served requests use the fused path");
-    if (r->es.strings) return fail(c, PV3D_E_INVALID, "string outputs are produced by pv3d_evaluate only");
+    if (r->es.strings || r->es.heat)
+        return fail(c, PV3D_E_INVALID, "string and sky-map outputs are produced by pv3d_evaluate only");
     r->gen_id = gen_id;
     r->opts = o ? *o : pv3d_eval_opts{};
     r->out = out;
@@ -1531,7 +1694,7 @@ extern "C" void pv3d_destroy(pv3d_ctx* c)
     release_buf(c->wave_slot);
     release_buf(c->jobs_slot);
     DevBuf* bufs[] = {&c->lp, &c->win, &c->ms, &c->ms_p, &c->ms_pu, &c->ms_beam, &c->ms_iu, &c->ss_i, &c->sq_p,
-                      &c->sq_pu, &c->kahan_str, &c->cs_cnt, &c->cs_bits, &c->t_far,
+                      &c->sq_pu, &c->kahan_str, &c->js_p, &c->js_pu, &c->js_bin, &c->heat, &c->cs_cnt, &c->cs_bits, &c->t_far,
                       &c->t_cnt, &c->t_off, &c->t_cur, &c->t_slot, &c->t_rcnt, &c->t_roff, &c->t_rcur, &c->nonempty, &c->heavy,
                       &c->bins, &c->pairs, &c->recv, &c->map, &c->big,
                       &c->block_sums, &c->ctr, &c->waves, &c->jobs, &c->kahan_mod, &c->kahan_cell, &c->staging};

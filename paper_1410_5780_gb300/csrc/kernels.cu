@@ -2277,6 +2277,79 @@ __global__ void __launch_bounds__(256) k_string(const WaveDev* __restrict__ W, c
 }
 
 // ---------------------------------------------------------------------------
+// sky map of the effective shading (Fig. 6: the shading factor over the sun's
+// azimuth and zenith): k_gen_step sums the generator's power per step and
+// bins the step's sun; k_heat adds each bin's steps in step order (FP64)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_gen_step(const WaveDev* __restrict__ W, const JobDev* __restrict__ jobs,
+                                                  Buffers B)
+{
+    const int64_t tot = W->tot_js;
+    const int nj = W->n_jobs;
+    const int lane = threadIdx.x & 31;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t js = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; js < tot; js += n_warps) {
+        const int j = job_of(nj, js, [&](int q) { return (int64_t)jobs[q].js_base; });
+        const JobDev& J = jobs[j];
+        if (J.heat_az == 0) continue;
+        const int ls = (int)(js - J.js_base);
+        float p = 0.f, pu = 0.f;
+        for (int m = lane; m < J.n_mods; m += 32) {
+            const int64_t msi = J.ms_base + (int64_t)ls * J.n_mods + m;
+            p += B.ms_p[msi];
+            pu += B.ms_pu[msi];
+        }
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+            p += __shfl_xor_sync(0xffffffffu, p, off);
+            pu += __shfl_xor_sync(0xffffffffu, pu, off);
+        }
+        if (lane == 0) {
+            B.js_p[js] = p;
+            B.js_pu[js] = pu;
+            const double* sp = J.sun + 3 * (size_t)(J.step0 + ls);
+            int bin = -1;
+            if (sp[2] > 0.0) {
+                const double deg = 57.29577951308232;  // degrees per radian
+                double az = atan2(sp[0], sp[1]) * deg;
+                if (az < 0.0) az += 360.0;
+                const double zen = acos(fmin(1.0, sp[2])) * deg;
+                const int ia = min((int)(az / 360.0 * J.heat_az), J.heat_az - 1);
+                const int iz = min((int)(zen / 90.0 * J.heat_zen), J.heat_zen - 1);
+                bin = iz * J.heat_az + ia;
+            }
+            B.js_bin[js] = bin;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(256) k_heat(const WaveDev* __restrict__ W, const JobDev* __restrict__ jobs,
+                                              Buffers B)
+{
+    const int64_t tot = W->tot_heat;
+    const int nj = W->n_jobs;
+    for (int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; item < tot;
+         item += (int64_t)gridDim.x * blockDim.x) {
+        const int j = job_of(nj, item, [&](int q) { return jobs[q].it_heat; });
+        const JobDev& J = jobs[j];
+        const int bin = (int)(item - J.it_heat);
+        double e = J.heat_e[bin], eu = J.heat_eu[bin];
+        int cnt = J.heat_n[bin];
+        for (int ls = 0; ls < J.k; ++ls) {
+            const int64_t js = J.js_base + ls;
+            if (B.js_bin[js] != bin) continue;
+            const double dt = (double)B.lp[js].dt;
+            e += (double)B.js_p[js] * dt;
+            eu += (double)B.js_pu[js] * dt;
+            ++cnt;
+        }
+        J.heat_e[bin] = e;
+        J.heat_eu[bin] = eu;
+        J.heat_n[bin] = cnt;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // k_epilogue: Kahan sums over the wave's steps in step order
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void kahan_add(float2& acc, float x)
@@ -2359,6 +2432,68 @@ __global__ void k_finalize(const float2* __restrict__ kmod, int n_mods, const fl
 }
 
 // ---------------------------------------------------------------------------
+// clear-sky sun table and ideal tracker poses, made on the device (the inputs
+// of steps 3-4; the paper takes TMY data, measured series or an unnamed
+// clear-sky model).  Solar time without longitude correction or equation of
+// time; Cooper's (1969) declination; hour angle 15 deg per hour from noon;
+// Meinel & Meinel's (1976) beam irradiance with Kasten & Young's (1989) air
+// mass; all in FP64.
+// ---------------------------------------------------------------------------
+__global__ void k_sun_table(double lat_deg, int day_first, int64_t per_day, double step_h, double dhi_fraction,
+                            int64_t n, double* __restrict__ xyz, float* __restrict__ dni, float* __restrict__ dhi,
+                            float* __restrict__ dt, uint8_t* __restrict__ lit)
+{
+    const double deg = 0.017453292519943295;  // radians per degree
+    const double phi = lat_deg * deg;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t d = i / per_day, k = i - d * per_day;
+        const double day = (double)(day_first + d);
+        const double delta = 23.45 * deg * sin(360.0 * deg * (284.0 + day) / 365.0);
+        const double omega = 15.0 * deg * ((double)k * step_h - 12.0);
+        double e = -cos(delta) * sin(omega);
+        double no = sin(delta) * cos(phi) - cos(delta) * cos(omega) * sin(phi);
+        double up = sin(delta) * sin(phi) + cos(delta) * cos(omega) * cos(phi);
+        const double len = sqrt(e * e + no * no + up * up);
+        e /= len; no /= len; up /= len;
+        double b = 0.0;
+        if (up > 0.0) {
+            const double z = acos(up) / deg;
+            const double am = 1.0 / (up + 0.50572 * pow(96.07995 - z, -1.6364));
+            b = 1353.0 * pow(0.7, pow(am, 0.678));
+        }
+        xyz[3 * i] = e; xyz[3 * i + 1] = no; xyz[3 * i + 2] = up;
+        dni[i] = (float)b;
+        dhi[i] = (float)(dhi_fraction * b);
+        dt[i] = (float)step_h;
+        lit[i] = up > 0.0;
+    }
+}
+
+__global__ void k_gather_sun(const int64_t* __restrict__ idx, int64_t n, const double* __restrict__ xyz,
+                             const float* __restrict__ dni, const float* __restrict__ dhi, double* __restrict__ oxyz,
+                             float* __restrict__ odni, float* __restrict__ odhi)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = idx[i];
+        oxyz[3 * i] = xyz[3 * k]; oxyz[3 * i + 1] = xyz[3 * k + 1]; oxyz[3 * i + 2] = xyz[3 * k + 2];
+        odni[i] = dni[k];
+        odhi[i] = dhi[k];
+    }
+}
+
+__global__ void k_ideal_poses(const double* __restrict__ sun, int64_t n_steps, int n_trk, float tilt_max,
+                              float* __restrict__ poses)
+{
+    const int64_t n = n_steps * n_trk;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t s = i / n_trk;
+        const double* sp = sun + 3 * s;
+        poses[2 * i] = (float)atan2(sp[0], sp[1]);
+        poses[2 * i + 1] = fminf((float)acos(fmin(1.0, fmax(-1.0, sp[2]))), tilt_max);
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host launchers
 // ---------------------------------------------------------------------------
 static inline unsigned int grid_for(int64_t items, int per_block, int cap)
@@ -2414,10 +2549,36 @@ cudaError_t launch_wave(const WaveDev* d_wave, const JobDev* d_jobs, const Buffe
     if (cfg.ev) cudaEventRecord(cfg.ev[4], st);
     if (cfg.fused) k_pv<<<sm * 32, kPvThreads, 0, st>>>(W, d_jobs, b);
     else k_sample<<<sm * 16, kPvThreads, 0, st>>>(W, d_jobs, b);
-    k_string<<<sm * 4, 256, 0, st>>>(W, d_jobs, b);
+    if (cfg.extras & 1) k_string<<<sm * 4, 256, 0, st>>>(W, d_jobs, b);
+    if (cfg.extras & 2) {
+        k_gen_step<<<sm * 4, 256, 0, st>>>(W, d_jobs, b);
+        k_heat<<<sm * 2, 256, 0, st>>>(W, d_jobs, b);
+    }
     if (cfg.ev) cudaEventRecord(cfg.ev[5], st);
     k_epilogue<<<sm * 8, 256, 0, st>>>(W, d_jobs, b);
     if (cfg.ev) cudaEventRecord(cfg.ev[6], st);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sun_table(double lat_deg, int day_first, int64_t per_day, double step_h, double dhi_fraction,
+                             int64_t n, double* xyz, float* dni, float* dhi, float* dt, uint8_t* lit, cudaStream_t st)
+{
+    k_sun_table<<<grid_for(n, 256, 4096), 256, 0, st>>>(lat_deg, day_first, per_day, step_h, dhi_fraction, n, xyz, dni,
+                                                          dhi, dt, lit);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_sun(const int64_t* idx, int64_t n, const double* xyz, const float* dni, const float* dhi,
+                              double* oxyz, float* odni, float* odhi, cudaStream_t st)
+{
+    k_gather_sun<<<grid_for(n, 256, 4096), 256, 0, st>>>(idx, n, xyz, dni, dhi, oxyz, odni, odhi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ideal_poses(const double* sun, int64_t n_steps, int n_trk, float tilt_max, float* poses,
+                               cudaStream_t st)
+{
+    k_ideal_poses<<<grid_for(n_steps * n_trk, 256, 4096), 256, 0, st>>>(sun, n_steps, n_trk, tilt_max, poses);
     return cudaGetLastError();
 }
 

@@ -119,6 +119,13 @@ struct JobDev {
     float2* kahan_str;        // [n_str][2]  (E, comp), (E_unshaded, comp)
     float* out_str_power;     // [rows][n_str]
     float* out_str_power_u;
+    // effective-shading map over the sky (heat_az * heat_zen bins, 0: none):
+    // per bin, sums over the evaluation's steps (in step order, FP64)
+    int32_t heat_az, heat_zen;
+    int64_t it_heat;          // heat-kernel items (bins of the jobs before this one)
+    double* heat_e;           // [bins]  sum of the generator's P_mpp * dt
+    double* heat_eu;          // [bins]  same without shading
+    int32_t* heat_n;          // [bins]  steps
 };
 
 struct WaveDev {
@@ -131,6 +138,7 @@ struct WaveDev {
     int64_t tot_js, tot_te, tot_ms, tot_cs;
     int64_t tot_win, tot_mod, tot_tri, tot_epi;  // tot_tri: (meshlet, step) warp items
     int64_t tot_ss, tot_sq;                      // (step, substring) and (step, string) entries
+    int64_t tot_heat;                            // heat-map bins over the jobs
     int64_t bin_cap, map_cap_tiles, big_cap, recv_cap;
 };
 
@@ -179,6 +187,9 @@ struct Buffers {
     float* ss_i;             // [tot_ss]  substring current limit per (step, substring) (string model)
     float* sq_p;             // [tot_sq]  string MPP power per (step, string)
     float* sq_pu;            // [tot_sq]  same without shading
+    float* js_p;             // [tot_js]  the generator's P_mpp per step (heat map)
+    float* js_pu;            // [tot_js]
+    int32_t* js_bin;         // [tot_js]  sky bin of the step's sun, -1 below the horizon
     uint32_t* cs_cnt;        // [tot_cs]  shaded samples per (step, cell)
     unsigned long long* cs_bits;  // [tot_cs] shaded flags per (step, cell), fused path with flags requested
     uint32_t* t_far;         // [tot_te]  far-plane key of the tile (0 = no sample)
@@ -208,15 +219,27 @@ struct LaunchCfg {
     int profile;  // counting kernels
     cudaStream_t stream;
     cudaEvent_t* ev;  // NULL, or kStages + 1 events recorded at the stage boundaries of the wave
+    int extras;       // bit 0: series strings (k_string); bit 1: sky map (k_gen_step, k_heat)
 };
 
 constexpr int kStages = 6;  // setup, bin, tile (warp per tile / map raster), heavy tiles, pv/sample, epilogue
-constexpr int kLaunchesPerWave = 16;     // kernels launch_wave starts (fused path)
-constexpr int kLaunchesPerWaveMap = 15;  // (map path)
+constexpr int kLaunchesPerWave = 15;     // kernels launch_wave starts (fused path), plus 1 with
+constexpr int kLaunchesPerWaveMap = 14;  // strings and 2 with the sky map; (map path)
 
 cudaError_t launch_wave(const WaveDev* d_wave, const JobDev* d_jobs, const Buffers& b,
                         const LaunchCfg& cfg, int64_t tot_te_host);
 cudaError_t launch_finalize_pairs(const float2* kmod, int n_mods, const float2* kcell, int n_cells,
                                   double* energy, double* energy_u, double* cell_loss, cudaStream_t stream);
+// clear-sky sun table: steps k * step_h (k < per_day) of n / per_day days from day_first;
+// xyz toward the sun, DNI, DHI, duration and the lit flag per step
+cudaError_t launch_sun_table(double lat_deg, int day_first, int64_t per_day, double step_h, double dhi_fraction,
+                             int64_t n, double* xyz, float* dni, float* dhi, float* dt, uint8_t* lit,
+                             cudaStream_t stream);
+// keep steps idx[0, n) of the table (daylight only)
+cudaError_t launch_gather_sun(const int64_t* idx, int64_t n, const double* xyz, const float* dni, const float* dhi,
+                              double* oxyz, float* odni, float* odhi, cudaStream_t stream);
+// two-axis trackers facing the sun: compass azimuth, tilt = zenith angle clamped to tilt_max
+cudaError_t launch_ideal_poses(const double* sun, int64_t n_steps, int n_trk, float tilt_max, float* poses,
+                               cudaStream_t stream);
 
 }  // namespace pv3d

@@ -35,7 +35,8 @@ PV3D_PATH_MAP = 1
 
 EXPORTED = ("pv3d_create", "pv3d_destroy", "pv3d_last_error", "pv3d_scene_load", "pv3d_generator_define",
             "pv3d_set_poses", "pv3d_set_sun", "pv3d_evaluate", "pv3d_submit", "pv3d_poll", "pv3d_release",
-            "pv3d_last_profile", "pv3d_module_shade_noalloc", "pv3d_evaluate_batch", "pv3d_generator_strings")
+            "pv3d_last_profile", "pv3d_module_shade_noalloc", "pv3d_evaluate_batch", "pv3d_generator_strings",
+            "pv3d_set_sun_clear_sky", "pv3d_sun_table")
 
 
 class pv3d_opts(C.Structure):
@@ -88,7 +89,15 @@ class pv3d_result(C.Structure):
                 ("device_ms", C.c_float), ("waves", C.c_int32), ("nonempty_tiles", C.c_int64),
                 ("binned_tris", C.c_int64), ("kernel_launches", C.c_int64), ("latency_ms", C.c_float),
                 ("reserved1", C.c_int32), ("string_energy", C.c_void_p), ("string_energy_unshaded", C.c_void_p),
-                ("string_power", C.c_void_p), ("string_power_unshaded", C.c_void_p)]
+                ("string_power", C.c_void_p), ("string_power_unshaded", C.c_void_p),
+                ("heat_az_bins", C.c_int32), ("heat_zen_bins", C.c_int32), ("heat_energy", C.c_void_p),
+                ("heat_energy_unshaded", C.c_void_p), ("heat_steps", C.c_void_p)]
+
+
+class pv3d_sky_opts(C.Structure):
+    _fields_ = [("latitude_deg", C.c_double), ("step_h", C.c_double), ("day_first", C.c_int32),
+                ("n_days", C.c_int32), ("daylight_only", C.c_int32), ("dhi_fraction", C.c_float),
+                ("tracker_tilt_max_deg", C.c_float), ("reserved", C.c_int32 * 5)]
 
 
 _lib = None
@@ -130,6 +139,8 @@ def load(build_if_missing: bool = False):
         lib.pv3d_release.argtypes = [P, C.c_uint32]
         lib.pv3d_last_profile.argtypes = [P, C.POINTER(pv3d_profile)]
         lib.pv3d_generator_strings.argtypes = [P, C.c_uint32, C.POINTER(C.c_int32), P]
+        lib.pv3d_set_sun_clear_sky.argtypes = [P, C.c_uint32, C.POINTER(pv3d_sky_opts), C.POINTER(C.c_int64)]
+        lib.pv3d_sun_table.argtypes = [P, C.c_uint32, P, P, P, P, C.c_int64]
         lib.pv3d_evaluate_batch.argtypes = [P, C.c_int32, P, C.POINTER(pv3d_eval_opts), C.POINTER(pv3d_result)]
         lib.pv3d_module_shade_noalloc.argtypes = [P, C.c_int64, C.POINTER(pv3d_module), P, C.c_int32, C.c_int32,
                                                   P, P]
@@ -251,6 +262,27 @@ class Context:
         self._check(self.lib.pv3d_set_sun(self.h, gen_id, _p(s), _p(a), _p(b), _p(d), s.shape[0]))
         self._gens[gen_id]["steps"] = s.shape[0]
 
+    def set_sun_clear_sky(self, gen_id: int, latitude_deg: float, step_h: float, day_first: int = 1,
+                          n_days: int = 365, daylight_only: bool = True, dhi_fraction: float = 0.1,
+                          tracker_tilt_max_deg: float = 0.0) -> int:
+        """pv3d_set_sun_clear_sky: the sun table (and, with a tilt limit, ideal
+        tracker poses) computed on the device.  Returns the number of steps."""
+        o = pv3d_sky_opts(latitude_deg=latitude_deg, step_h=step_h, day_first=day_first, n_days=n_days,
+                          daylight_only=int(daylight_only), dhi_fraction=dhi_fraction,
+                          tracker_tilt_max_deg=tracker_tilt_max_deg)
+        n = C.c_int64()
+        self._check(self.lib.pv3d_set_sun_clear_sky(self.h, gen_id, C.byref(o), C.byref(n)))
+        self._gens[gen_id]["steps"] = n.value
+        return n.value
+
+    def sun_table(self, gen_id: int):
+        """pv3d_sun_table: (xyz [N, 3] float64, dni, dhi, dt_h [N] float32) of the generator."""
+        n = self._gens[gen_id]["steps"]
+        xyz = np.zeros((n, 3)); dni = np.zeros(n, np.float32); dhi = np.zeros(n, np.float32)
+        dt = np.zeros(n, np.float32)
+        self._check(self.lib.pv3d_sun_table(self.h, gen_id, _p(xyz), _p(dni), _p(dhi), _p(dt), n))
+        return xyz, dni, dhi, dt
+
     # ---- steps 3 and 4 -----------------------------------------------------
     def _opts(self, n, map_res, step_begin, step_end, chunk_steps, stream, i_ref, v_cell, v_diode, path=0,
               profile=0):
@@ -258,7 +290,7 @@ class Context:
                               chunk_steps=chunk_steps, stream=stream, i_ref=i_ref, v_cell=v_cell, v_diode=v_diode,
                               path=path, profile=profile)
 
-    def _alloc(self, gen_id, step_begin, step_end, outputs, device):
+    def _alloc(self, gen_id, step_begin, step_end, outputs, device, heat_bins=None):
         if gen_id not in self._gens:  # let the library report the unknown id
             return pv3d_result(is_device=1 if device else 0), {}
         g = self._gens[gen_id]
@@ -269,13 +301,22 @@ class Context:
                       cell_counts=((S, cells), "u1"), sample_bits=((S, cells), "u8"),
                       string_energy=((ns,), "f8"), string_energy_unshaded=((ns,), "f8"),
                       string_power=((S, ns), "f4"), string_power_unshaded=((S, ns), "f4"))
+        if heat_bins:
+            n_az, n_zen = heat_bins
+            shapes.update(heat_energy=((n_zen, n_az), "f8"), heat_energy_unshaded=((n_zen, n_az), "f8"),
+                          heat_steps=((n_zen, n_az), "i4"))
+            outputs = tuple(outputs) + tuple(k for k in ("heat_energy", "heat_energy_unshaded", "heat_steps")
+                                             if k not in outputs)
         res = pv3d_result(is_device=1 if device else 0)
+        if heat_bins:
+            res.heat_az_bins, res.heat_zen_bins = int(heat_bins[0]), int(heat_bins[1])
         arrays = {}
         for name in outputs:
             shape, dt = shapes[name]
             if device:
                 import torch
-                tdt = {"f8": torch.float64, "f4": torch.float32, "u1": torch.uint8, "u8": torch.int64}[dt]
+                tdt = {"f8": torch.float64, "f4": torch.float32, "u1": torch.uint8, "u8": torch.int64,
+                       "i4": torch.int32}[dt]
                 a = torch.empty(shape, dtype=tdt, device=f"cuda:{self.device}")
                 setattr(res, name, a.data_ptr())
             else:
@@ -287,13 +328,14 @@ class Context:
     def evaluate(self, gen_id: int, n: int = 3, map_res: int = 0, step_begin: int = 0, step_end: int = 0,
                  chunk_steps: int = 0, outputs=("energy", "energy_unshaded"), device: bool = True,
                  stream=None, i_ref: float = 0.0, v_cell: float = 0.0, v_diode: float = 0.0,
-                 path: int = PV3D_PATH_FUSED, profile: bool = False) -> dict:
+                 path: int = PV3D_PATH_FUSED, profile: bool = False, heat_bins=None) -> dict:
         """pv3d_evaluate.  Returns the requested outputs (torch tensors on the
-        device if ``device`` else numpy arrays) plus the counters."""
+        device if ``device`` else numpy arrays) plus the counters.  ``heat_bins``
+        = (azimuth bins, zenith bins) adds the sky map of the effective shading."""
         if stream is None and device:
             import torch
             stream = torch.cuda.current_stream(self.device).cuda_stream
-        res, arrays = self._alloc(gen_id, step_begin, step_end, outputs, device)
+        res, arrays = self._alloc(gen_id, step_begin, step_end, outputs, device, heat_bins)
         o = self._opts(n, map_res, step_begin, step_end, chunk_steps, stream, i_ref, v_cell, v_diode, path,
                        int(profile))
         self._check(self.lib.pv3d_evaluate(self.h, gen_id, C.byref(o), C.byref(res)))

@@ -20,6 +20,7 @@ strings of modules (one current and one maximum power point per string).
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -329,6 +330,39 @@ def heat_map(sun_xyz, p_gen, pu_gen, dt_h, n_az: int, n_zen: int):
     np.add.at(eu, (iz[lit], ia[lit]), (np.asarray(pu_gen, np.float64) * dt)[lit])
     np.add.at(cnt, (iz[lit], ia[lit]), 1)
     return e, eu, cnt
+
+
+def sky_patches(rings: int, sectors: int):
+    """Sky directions for diffuse shading (reading of the isotropic diffuse
+    term of Section 2, step 4, which the paper leaves unshaded): the upper
+    hemisphere cut into `rings` zenith bands of equal angle over [0, 90] deg
+    and `sectors` equal azimuth sectors; each patch is represented by the
+    direction at its centre angles and carries its solid angle
+    (cos z0 - cos z1) * 2 pi / sectors.  Returns (xyz [rings*sectors, 3],
+    solid angle [rings*sectors]), ring-major, azimuth clockwise from north."""
+    out, dom = [], []
+    for r in range(rings):
+        z0, z1 = math.pi / 2 * r / rings, math.pi / 2 * (r + 1) / rings
+        zc = 0.5 * (z0 + z1)
+        for k in range(sectors):
+            a = 2 * math.pi * (k + 0.5) / sectors
+            out.append((math.sin(zc) * math.sin(a), math.sin(zc) * math.cos(a), math.cos(zc)))
+            dom.append((math.cos(z0) - math.cos(z1)) * 2 * math.pi / sectors)
+    return np.array(out), np.array(dom)
+
+
+def diffuse_shade_fractions(w, rings: int, sectors: int, counts, normals):
+    """Per cell, the share of the isotropic diffuse irradiance it loses to
+    obstructions: the sky patches weighted by solid angle times the cosine to
+    the module's front normal (where positive), and the fraction of the cell's
+    samples shaded toward each patch (counts [patch, cell] out of n^2):
+    f = sum_p W_p s_p / sum_p W_p.  `normals` [cells, 3] are the cells'
+    module normals.  Unobstructed, f = 0."""
+    xyz, dom = sky_patches(rings, sectors)
+    wgt = dom[:, None] * np.maximum(0.0, xyz @ np.asarray(normals, np.float64).T)   # [patch, cell]
+    frac = np.asarray(counts, np.float64) / float(w.n * w.n)
+    tot = wgt.sum(0)
+    return np.where(tot > 0, (wgt * frac).sum(0) / np.where(tot > 0, tot, 1.0), 0.0)
 
 
 def popcount64(a: np.ndarray) -> np.ndarray:

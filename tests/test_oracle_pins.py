@@ -378,6 +378,51 @@ def test_heat_map_bins():
     assert cnt[2, 3] == 1          # west, low
 
 
+def test_sky_patches_cover_the_hemisphere():
+    """The patches' solid angles add to 2 pi; the cosine-weighted sum
+    approximates the projected hemisphere pi; the patch directions are unit
+    vectors above the horizon."""
+    for rings, sectors in ((9, 36), (18, 72), (3, 8)):
+        xyz, dom = oracle.sky_patches(rings, sectors)
+        assert abs(dom.sum() - 2 * math.pi) < 1e-12
+        assert abs((dom * xyz[:, 2]).sum() - math.pi) < 1.05 / rings ** 2  # midpoint rule, O(1/rings^2)
+        np.testing.assert_allclose(np.linalg.norm(xyz, axis=1), 1.0, atol=1e-14)
+        assert xyz[:, 2].min() > 0
+
+
+def _wall_workload(h, d, n=2):
+    """A horizontal 1-cell module at the origin and a 400 m long wall of height
+    h at distance d to its north."""
+    mb = S.MeshBuilder()
+    mb.grid_quad((-200.0, d, 0.0), (400.0, 0.0, 0.0), (0.0, 0.0, h), 40, 1)
+    lay = S.Layout(1, 1, 1, np.zeros(1, np.int32))
+    gen = S._gen_from_lists([(-0.078, -0.078, 0.0)], [(1.0, 0.0, 0.0)], [(0.0, 1.0, 0.0)], 1, 1, [0], [-1], [0],
+                            [lay], np.zeros((0, 3)))
+    sun = S.Sun(xyz=np.array([[0.0, 0.0, 1.0]]), dni=np.ones(1, np.float32), dhi=np.ones(1, np.float32),
+                dt_h=np.ones(1, np.float32))
+    return S.Workload("wall", mb.build(), gen, sun, None, n, 256)
+
+
+@pytest.mark.parametrize("h,d", [(3.0, 3.0), (10.0, 4.0), (2.0, 8.0)])
+def test_diffuse_shade_of_a_long_wall_closed_form(h, d):
+    """A horizontal element beside an infinitely long wall of height h at
+    distance d sees the wall over the fraction (1 - d / sqrt(d^2 + h^2)) / 2
+    of its cosine-weighted sky (the two-dimensional view factor of a strip,
+    Hottel's crossed strings); the oracle's patch quadrature gets it within
+    0.01."""
+    w = _wall_workload(h, d)
+    xyz, _ = oracle.sky_patches(18, 72)
+    wp = S.Workload(w.name, w.scene, w.gen, S.Sun(xyz=xyz, dni=np.ones(len(xyz), np.float32),
+                                                  dhi=np.zeros(len(xyz), np.float32),
+                                                  dt_h=np.ones(len(xyz), np.float32)), None, w.n, w.map_res)
+    o = oracle.evaluate(wp.scene, wp.gen, wp.sun, None, wp.n, wp.map_res, want_mask=False)
+    f = oracle.diffuse_shade_fractions(wp, 18, 72, o["counts"], np.array([[0.0, 0.0, 1.0]]))
+    expect = 0.5 * (1 - d / math.hypot(d, h))
+    assert abs(f[0] - expect) < 0.01, (f[0], expect)
+    f0 = oracle.diffuse_shade_fractions(wp, 18, 72, np.zeros_like(o["counts"]), np.array([[0.0, 0.0, 1.0]]))
+    assert f0[0] == 0.0
+
+
 # ---------------------------------------------------------------------------
 # invariants
 # ---------------------------------------------------------------------------

@@ -124,7 +124,8 @@ typedef struct pv3d_eval_opts {
     void* stream;              /* cudaStream_t to run on; NULL = the context's own stream */
     int32_t path;              /* PV3D_PATH_FUSED or PV3D_PATH_MAP [FUSED] */
     int32_t profile;           /* bit 0: time each stage with CUDA events; bit 1: count work (pv3d_last_profile) [0] */
-    int32_t reserved[6];
+    int32_t diffuse_shading;   /* 1: shade the diffuse term of each cell by its pv3d_sky_view fraction [0] */
+    int32_t reserved[5];
 } pv3d_eval_opts;
 
 /*
@@ -286,6 +287,31 @@ int pv3d_set_sun_clear_sky(pv3d_ctx* ctx, uint32_t gen_id, const pv3d_sky_opts* 
  */
 int pv3d_sun_table(pv3d_ctx* ctx, uint32_t gen_id, double* sun_xyz, float* dni, float* dhi, float* dt_h,
                    int64_t n_steps);
+
+/*
+ * Diffuse shading (the paper leaves the isotropic diffuse term unshaded):
+ * the share of each cell's cosine-weighted sky hidden by the scene.  The upper
+ * hemisphere is cut into `rings` zenith bands of equal angle and `sectors`
+ * azimuth sectors; every patch is represented by its centre direction, which
+ * is evaluated like a sun step (depth map from that direction, the cell's n x n
+ * samples tested), and weighted by its solid angle times the cosine to the
+ * module's front normal.  A cell's fraction is sum_p W_p s_p / sum_p W_p (s_p
+ * = its shaded samples toward patch p over n^2); 0 without obstructions.  The
+ * fractions are kept with the generator (fixed modules only) and used by
+ * evaluations with diffuse_shading = 1: G_c = DNI max(0, cos i)(1 - f_c) +
+ * DHI (1 + cos beta)/2 (1 - f_diffuse,c).  cell_fraction (host, C entries, may
+ * be NULL) receives them.  Errors: PV3D_E_INVALID (a tracked module, options
+ * out of range), PV3D_E_NOTFOUND, PV3D_E_NOMEM, PV3D_E_DEVICE.
+ */
+typedef struct pv3d_sky_view_opts {
+    int32_t rings;             /* zenith bands over [0, 90] deg, 1..90 [9] */
+    int32_t sectors;           /* azimuth sectors, 1..360 [36] */
+    int32_t samples_per_side;  /* n, 1..15 [3] */
+    int32_t map_res;           /* shadow-map side [context default] */
+    int32_t reserved[4];
+} pv3d_sky_view_opts;
+
+int pv3d_sky_view(pv3d_ctx* ctx, uint32_t gen_id, const pv3d_sky_view_opts* opts, float* cell_fraction);
 
 /*
  * Series strings of a generator (Section 2: the modules are wired in series

@@ -69,6 +69,7 @@ struct GenH {
     int32_t* d_sub_base = nullptr;  // [M]
     int32_t* d_sub_nk = nullptr;    // [n_sub_tot]
     int32_t* d_sub_mod = nullptr;   // [n_sub_tot]
+    float* d_fdiff = nullptr;       // [C] diffuse shading fraction per cell (pv3d_sky_view)
     size_t bytes = 0;
 };
 
@@ -198,7 +199,7 @@ static void free_gen(GenH& g)
 {
     void* ps[] = {g.d_mods, g.d_cell_mod, g.d_lay_sub, g.d_lay_off, g.d_lay_nk, g.d_lay_nk_off, g.d_pivots,
                   g.d_sun, g.d_dni, g.d_dhi, g.d_dt, g.d_poses, g.d_str_sub, g.d_sub_base, g.d_sub_nk,
-                  g.d_sub_mod};
+                  g.d_sub_mod, g.d_fdiff};
     for (void* p : ps)
         if (p) cudaFree(p);
 }
@@ -711,7 +712,7 @@ extern "C" int pv3d_set_sun_clear_sky(pv3d_ctx* c, uint32_t gen_id, const pv3d_s
 namespace {
 
 struct EvalSetup {
-    int n, R, K, tile, fused, profile, count, strings, heat;
+    int n, R, K, tile, fused, profile, count, strings, heat, diffuse;
     int64_t b, e;
     float i_ref, v_cell, v_diode;
 };
@@ -743,6 +744,8 @@ static int check_eval(pv3d_ctx* c, const GenH& g, const pv3d_eval_opts* o, const
     if (es.b < 0 || es.e > g.n_steps || es.b >= es.e) return fail(c, PV3D_E_INVALID, "bad step range");
     if (!out) return fail(c, PV3D_E_INVALID, "null result");
     if (out->sample_bits && es.n > 8) return fail(c, PV3D_E_INVALID, "sample_bits needs samples_per_side <= 8");
+    es.diffuse = d.diffuse_shading != 0;
+    if (es.diffuse && !g.d_fdiff) return fail(c, PV3D_E_INVALID, "diffuse_shading needs pv3d_sky_view first");
     es.strings = out->string_energy || out->string_energy_unshaded || out->string_power || out->string_power_unshaded;
     es.heat = out->heat_az_bins > 0 || out->heat_zen_bins > 0 || out->heat_energy || out->heat_energy_unshaded ||
               out->heat_steps;
@@ -813,6 +816,7 @@ static JobDev make_job(pv3d_ctx* c, const GenH& g, const SceneH& s, const EvalSe
         J.out_str_power = spw;
         J.out_str_power_u = spwu;
     }
+    J.fdiff = es.diffuse ? g.d_fdiff : nullptr;
     if (heat_e) {
         J.heat_az = heat_az;
         J.heat_zen = heat_zen;
@@ -1259,6 +1263,77 @@ extern "C" int pv3d_evaluate(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts*
     if (!c) return PV3D_E_INVALID;
     std::lock_guard<std::mutex> g(c->gpu_mu);
     return evaluate_plain(c, gen_id, o, out);
+}
+
+extern "C" int pv3d_sky_view(pv3d_ctx* c, uint32_t gen_id, const pv3d_sky_view_opts* o, float* cell_fraction)
+{
+    if (!c) return PV3D_E_INVALID;
+    auto it = c->gens.find(gen_id);
+    if (it == c->gens.end()) return fail(c, PV3D_E_NOTFOUND, "unknown generator %u", gen_id);
+    GenH& g = it->second;
+    pv3d_sky_view_opts d{};
+    if (o) d = *o;
+    const int rings = d.rings ? d.rings : 9, sectors = d.sectors ? d.sectors : 36;
+    const int n = d.samples_per_side ? d.samples_per_side : 3;
+    if (rings < 1 || rings > 90 || sectors < 1 || sectors > 360 || n < 1 || n > 15)
+        return fail(c, PV3D_E_INVALID, "sky view: rings 1..90, sectors 1..360, samples_per_side 1..15");
+    for (const ModuleDev& M : g.mods_h)
+        if (M.tracker >= 0) return fail(c, PV3D_E_INVALID, "sky view: fixed modules only");
+    const int P = rings * sectors;
+    cudaSetDevice(c->device);
+    cudaStream_t st = c->stream;
+    double *xyz = nullptr, *dom = nullptr;
+    float *dni = nullptr, *dhi = nullptr, *dt = nullptr;
+    uint8_t* counts = nullptr;
+    auto cleanup = [&]() {
+        void* ps[] = {xyz, dom, dni, dhi, dt, counts};
+        for (void* p : ps)
+            if (p) cudaFree(p);
+    };
+    if (cudaMalloc(&xyz, (size_t)P * 24) != cudaSuccess || cudaMalloc(&dom, (size_t)P * 8) != cudaSuccess ||
+        cudaMalloc(&dni, (size_t)P * 4) != cudaSuccess || cudaMalloc(&dhi, (size_t)P * 4) != cudaSuccess ||
+        cudaMalloc(&dt, (size_t)P * 4) != cudaSuccess || cudaMalloc(&counts, (size_t)P * g.C) != cudaSuccess ||
+        (!g.d_fdiff && cudaMalloc(&g.d_fdiff, (size_t)g.C * 4) != cudaSuccess)) {
+        cleanup();
+        cudaGetLastError();
+        return fail(c, PV3D_E_NOMEM, "sky view buffers");
+    }
+    if (launch_sky_patches(rings, sectors, xyz, dni, dhi, dt, dom, st) != cudaSuccess) {
+        cleanup();
+        return fail(c, PV3D_E_DEVICE, "sky patches: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    // the patches stand in for the sun table while their depth tests run
+    double* s_sun = g.d_sun;
+    float *s_dni = g.d_dni, *s_dhi = g.d_dhi, *s_dt = g.d_dt;
+    const int64_t s_n = g.n_steps, s_np = g.n_pose_steps;
+    std::vector<uint8_t> s_lit = std::move(g.lit);
+    g.d_sun = xyz; g.d_dni = dni; g.d_dhi = dhi; g.d_dt = dt;
+    g.n_steps = P;
+    g.n_pose_steps = g.n_trk ? P : 0;
+    g.lit.assign((size_t)P, 1);
+    pv3d_eval_opts eo{};
+    eo.samples_per_side = n;
+    eo.map_res = d.map_res;
+    pv3d_result r{};
+    r.is_device = 1;
+    r.cell_counts = counts;
+    int rc = evaluate_plain(c, gen_id, &eo, &r);
+    g.d_sun = s_sun; g.d_dni = s_dni; g.d_dhi = s_dhi; g.d_dt = s_dt;
+    g.n_steps = s_n;
+    g.n_pose_steps = s_np;
+    g.lit = std::move(s_lit);
+    if (rc) {
+        cleanup();
+        return rc;
+    }
+    if (launch_sky_fraction(g.d_mods, g.d_cell_mod, g.C, xyz, dom, P, counts, n * n, g.d_fdiff, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess ||
+        (cell_fraction && cudaMemcpy(cell_fraction, g.d_fdiff, (size_t)g.C * 4, cudaMemcpyDeviceToHost) != cudaSuccess)) {
+        cleanup();
+        return fail(c, PV3D_E_DEVICE, "sky fraction: %s", cudaGetErrorString(cudaGetLastError()));
+    }
+    cleanup();
+    return PV3D_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -2010,7 +2010,8 @@ __device__ void module_pv(const JobDev& J, const ModuleDev& M, const ModStep& s,
     const int* csub = J.lay_sub + J.lay_off[M.layout];
     for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
         const float f = s_cnt[c] * inv_nn;
-        const float G = beam * (1.f - f) + diff;
+        const float gd = J.fdiff ? diff * (1.f - J.fdiff[M.cell_base + c]) : diff;
+        const float G = beam * (1.f - f) + gd;
         const float I = J.i_ref * G * 1e-3f;
         atomicMin(&s_imin[csub[c]], __float_as_uint(I));  // I >= 0: uint order = float order
     }
@@ -2099,7 +2100,8 @@ __global__ void __launch_bounds__(kPvThreads) k_pv(const WaveDev* __restrict__ W
             const uint32_t cnt = B.cs_cnt[cbase + c];
             if (J.out_counts) J.out_counts[row * C + M.cell_base + c] = (uint8_t)cnt;
             if (J.out_bits) J.out_bits[row * C + M.cell_base + c] = B.cs_bits[cbase + c];
-            const float G = beam * (1.f - cnt * inv_nn) + diff;
+            const float gd = J.fdiff ? diff * (1.f - J.fdiff[M.cell_base + c]) : diff;
+            const float G = beam * (1.f - cnt * inv_nn) + gd;
             const float I = J.i_ref * G * 1e-3f;
             atomicMin(&imin[csub[c]], __float_as_uint(I));  // I >= 0: uint order = float order
         }
@@ -2481,6 +2483,52 @@ __global__ void k_gather_sun(const int64_t* __restrict__ idx, int64_t n, const d
     }
 }
 
+// Diffuse shading: sky patches of equal zenith bands and azimuth sectors at
+// their centre directions, solid angle (cos z0 - cos z1) 2 pi / sectors.
+__global__ void k_sky_patches(int rings, int sectors, double* __restrict__ xyz, float* __restrict__ dni,
+                              float* __restrict__ dhi, float* __restrict__ dt, double* __restrict__ dom)
+{
+    const double half_pi = 1.5707963267948966, two_pi = 6.283185307179586;
+    const int n = rings * sectors;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int r = i / sectors, k = i - r * sectors;
+        const double z0 = half_pi * r / rings, z1 = half_pi * (r + 1) / rings;
+        const double zc = 0.5 * (z0 + z1);
+        const double a = two_pi * (k + 0.5) / sectors;
+        xyz[3 * i] = sin(zc) * sin(a);
+        xyz[3 * i + 1] = sin(zc) * cos(a);
+        xyz[3 * i + 2] = cos(zc);
+        dni[i] = 1.f;
+        dhi[i] = 0.f;
+        dt[i] = 1.f;
+        dom[i] = (cos(z0) - cos(z1)) * two_pi / sectors;
+    }
+}
+
+// Per cell: f = sum_p W_p s_p / sum_p W_p, W_p = solid angle x max(0, n . w_p)
+// with the module's front normal n, s_p = shaded samples toward patch p / n^2
+// (counts[p][c]); summed in patch order in FP64.
+__global__ void k_sky_fraction(const ModuleDev* __restrict__ mods, const int32_t* __restrict__ cell_mod, int n_cells,
+                               const double* __restrict__ xyz, const double* __restrict__ dom, int n_patch,
+                               const uint8_t* __restrict__ counts, int nn, float* __restrict__ fdiff)
+{
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += gridDim.x * blockDim.x) {
+        const ModuleDev& M = mods[cell_mod[c]];
+        double nx = (double)M.u[1] * M.v[2] - (double)M.u[2] * M.v[1];
+        double ny = (double)M.u[2] * M.v[0] - (double)M.u[0] * M.v[2];
+        double nz = (double)M.u[0] * M.v[1] - (double)M.u[1] * M.v[0];
+        const double l = sqrt(nx * nx + ny * ny + nz * nz);
+        nx /= l; ny /= l; nz /= l;
+        double num = 0.0, den = 0.0;
+        for (int p = 0; p < n_patch; ++p) {
+            const double w = dom[p] * fmax(0.0, nx * xyz[3 * p] + ny * xyz[3 * p + 1] + nz * xyz[3 * p + 2]);
+            den += w;
+            num += w * ((double)counts[(size_t)p * n_cells + c] / (double)nn);
+        }
+        fdiff[c] = den > 0.0 ? (float)(num / den) : 0.f;
+    }
+}
+
 __global__ void k_ideal_poses(const double* __restrict__ sun, int64_t n_steps, int n_trk, float tilt_max,
                               float* __restrict__ poses)
 {
@@ -2572,6 +2620,23 @@ cudaError_t launch_gather_sun(const int64_t* idx, int64_t n, const double* xyz, 
                               double* oxyz, float* odni, float* odhi, cudaStream_t st)
 {
     k_gather_sun<<<grid_for(n, 256, 4096), 256, 0, st>>>(idx, n, xyz, dni, dhi, oxyz, odni, odhi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sky_patches(int rings, int sectors, double* xyz, float* dni, float* dhi, float* dt, double* dom,
+                               cudaStream_t st)
+{
+    k_sky_patches<<<grid_for((int64_t)rings * sectors, 256, 1024), 256, 0, st>>>(rings, sectors, xyz, dni, dhi, dt,
+                                                                                 dom);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sky_fraction(const ModuleDev* mods, const int32_t* cell_mod, int n_cells, const double* xyz,
+                                const double* dom, int n_patch, const uint8_t* counts, int nn, float* fdiff,
+                                cudaStream_t st)
+{
+    k_sky_fraction<<<grid_for(n_cells, 128, 4096), 128, 0, st>>>(mods, cell_mod, n_cells, xyz, dom, n_patch, counts,
+                                                                  nn, fdiff);
     return cudaGetLastError();
 }
 

@@ -126,6 +126,7 @@ struct JobDev {
     double* heat_e;           // [bins]  sum of the generator's P_mpp * dt
     double* heat_eu;          // [bins]  same without shading
     int32_t* heat_n;          // [bins]  steps
+    const float* fdiff;       // [C] diffuse shading fraction per cell (pv3d_sky_view), or nullptr
 };
 
 struct WaveDev {
@@ -238,6 +239,13 @@ cudaError_t launch_sun_table(double lat_deg, int day_first, int64_t per_day, dou
 // keep steps idx[0, n) of the table (daylight only)
 cudaError_t launch_gather_sun(const int64_t* idx, int64_t n, const double* xyz, const float* dni, const float* dhi,
                               double* oxyz, float* odni, float* odhi, cudaStream_t stream);
+// sky patches (rings x sectors, centre directions) as a sun table: xyz, DNI 1, DHI 0, dt 1, solid angle
+cudaError_t launch_sky_patches(int rings, int sectors, double* xyz, float* dni, float* dhi, float* dt, double* dom,
+                               cudaStream_t stream);
+// per cell: diffuse shading fraction from the counts [patch][cell] of fixed modules
+cudaError_t launch_sky_fraction(const ModuleDev* mods, const int32_t* cell_mod, int n_cells, const double* xyz,
+                                const double* dom, int n_patch, const uint8_t* counts, int nn, float* fdiff,
+                                cudaStream_t stream);
 // two-axis trackers facing the sun: compass azimuth, tilt = zenith angle clamped to tilt_max
 cudaError_t launch_ideal_poses(const double* sun, int64_t n_steps, int n_trk, float tilt_max, float* poses,
                                cudaStream_t stream);

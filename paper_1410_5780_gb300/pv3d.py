@@ -36,7 +36,7 @@ PV3D_PATH_MAP = 1
 EXPORTED = ("pv3d_create", "pv3d_destroy", "pv3d_last_error", "pv3d_scene_load", "pv3d_generator_define",
             "pv3d_set_poses", "pv3d_set_sun", "pv3d_evaluate", "pv3d_submit", "pv3d_poll", "pv3d_release",
             "pv3d_last_profile", "pv3d_module_shade_noalloc", "pv3d_evaluate_batch", "pv3d_generator_strings",
-            "pv3d_set_sun_clear_sky", "pv3d_sun_table")
+            "pv3d_set_sun_clear_sky", "pv3d_sun_table", "pv3d_sky_view")
 
 
 class pv3d_opts(C.Structure):
@@ -65,7 +65,7 @@ class pv3d_eval_opts(C.Structure):
     _fields_ = [("samples_per_side", C.c_int32), ("map_res", C.c_int32), ("step_begin", C.c_int64),
                 ("step_end", C.c_int64), ("i_ref", C.c_float), ("v_cell", C.c_float), ("v_diode", C.c_float),
                 ("chunk_steps", C.c_int32), ("stream", C.c_void_p), ("path", C.c_int32),
-                ("profile", C.c_int32), ("reserved", C.c_int32 * 6)]
+                ("profile", C.c_int32), ("diffuse_shading", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class pv3d_profile(C.Structure):
@@ -92,6 +92,11 @@ class pv3d_result(C.Structure):
                 ("string_power", C.c_void_p), ("string_power_unshaded", C.c_void_p),
                 ("heat_az_bins", C.c_int32), ("heat_zen_bins", C.c_int32), ("heat_energy", C.c_void_p),
                 ("heat_energy_unshaded", C.c_void_p), ("heat_steps", C.c_void_p)]
+
+
+class pv3d_sky_view_opts(C.Structure):
+    _fields_ = [("rings", C.c_int32), ("sectors", C.c_int32), ("samples_per_side", C.c_int32),
+                ("map_res", C.c_int32), ("reserved", C.c_int32 * 4)]
 
 
 class pv3d_sky_opts(C.Structure):
@@ -141,6 +146,7 @@ def load(build_if_missing: bool = False):
         lib.pv3d_generator_strings.argtypes = [P, C.c_uint32, C.POINTER(C.c_int32), P]
         lib.pv3d_set_sun_clear_sky.argtypes = [P, C.c_uint32, C.POINTER(pv3d_sky_opts), C.POINTER(C.c_int64)]
         lib.pv3d_sun_table.argtypes = [P, C.c_uint32, P, P, P, P, C.c_int64]
+        lib.pv3d_sky_view.argtypes = [P, C.c_uint32, C.POINTER(pv3d_sky_view_opts), P]
         lib.pv3d_evaluate_batch.argtypes = [P, C.c_int32, P, C.POINTER(pv3d_eval_opts), C.POINTER(pv3d_result)]
         lib.pv3d_module_shade_noalloc.argtypes = [P, C.c_int64, C.POINTER(pv3d_module), P, C.c_int32, C.c_int32,
                                                   P, P]
@@ -275,6 +281,14 @@ class Context:
         self._gens[gen_id]["steps"] = n.value
         return n.value
 
+    def sky_view(self, gen_id: int, rings: int = 9, sectors: int = 36, n: int = 3, map_res: int = 0) -> np.ndarray:
+        """pv3d_sky_view: per-cell diffuse shading fractions (kept with the
+        generator for evaluations with diffuse_shading)."""
+        o = pv3d_sky_view_opts(rings=rings, sectors=sectors, samples_per_side=n, map_res=map_res)
+        f = np.zeros(self._gens[gen_id]["cells"], np.float32)
+        self._check(self.lib.pv3d_sky_view(self.h, gen_id, C.byref(o), _p(f)))
+        return f
+
     def sun_table(self, gen_id: int):
         """pv3d_sun_table: (xyz [N, 3] float64, dni, dhi, dt_h [N] float32) of the generator."""
         n = self._gens[gen_id]["steps"]
@@ -285,10 +299,10 @@ class Context:
 
     # ---- steps 3 and 4 -----------------------------------------------------
     def _opts(self, n, map_res, step_begin, step_end, chunk_steps, stream, i_ref, v_cell, v_diode, path=0,
-              profile=0):
+              profile=0, diffuse=False):
         return pv3d_eval_opts(samples_per_side=n, map_res=map_res, step_begin=step_begin, step_end=step_end,
                               chunk_steps=chunk_steps, stream=stream, i_ref=i_ref, v_cell=v_cell, v_diode=v_diode,
-                              path=path, profile=profile)
+                              path=path, profile=profile, diffuse_shading=int(diffuse))
 
     def _alloc(self, gen_id, step_begin, step_end, outputs, device, heat_bins=None):
         if gen_id not in self._gens:  # let the library report the unknown id
@@ -328,7 +342,8 @@ class Context:
     def evaluate(self, gen_id: int, n: int = 3, map_res: int = 0, step_begin: int = 0, step_end: int = 0,
                  chunk_steps: int = 0, outputs=("energy", "energy_unshaded"), device: bool = True,
                  stream=None, i_ref: float = 0.0, v_cell: float = 0.0, v_diode: float = 0.0,
-                 path: int = PV3D_PATH_FUSED, profile: bool = False, heat_bins=None) -> dict:
+                 path: int = PV3D_PATH_FUSED, profile: bool = False, heat_bins=None,
+                 diffuse_shading: bool = False) -> dict:
         """pv3d_evaluate.  Returns the requested outputs (torch tensors on the
         device if ``device`` else numpy arrays) plus the counters.  ``heat_bins``
         = (azimuth bins, zenith bins) adds the sky map of the effective shading."""
@@ -337,7 +352,7 @@ class Context:
             stream = torch.cuda.current_stream(self.device).cuda_stream
         res, arrays = self._alloc(gen_id, step_begin, step_end, outputs, device, heat_bins)
         o = self._opts(n, map_res, step_begin, step_end, chunk_steps, stream, i_ref, v_cell, v_diode, path,
-                       int(profile))
+                       int(profile), diffuse_shading)
         self._check(self.lib.pv3d_evaluate(self.h, gen_id, C.byref(o), C.byref(res)))
         arrays.update(tests=res.tests, steps_lit=res.steps_lit, device_ms=res.device_ms, waves=res.waves,
                       nonempty_tiles=res.nonempty_tiles, binned_tris=res.binned_tris,

@@ -250,6 +250,63 @@ def batched_section(dev: int, n_scenes: int) -> dict:
     return mix
 
 
+def extensions_section(ctx, gid, w, stream) -> dict:
+    """The model extensions on the bench workload (device time of one
+    full-year evaluation each, CUDA events on the evaluation's stream): series
+    strings of 5 modules along each floor, the azimuth-zenith sky map
+    (36 x 9 bins), diffuse shading (sky view over 9 x 36 patches, then a year
+    with the diffuse term shaded), and the clear-sky sun table made on the
+    device."""
+    import torch
+    from paper_1410_5780_gb300 import pv3d
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fn()
+        torch.cuda.synchronize()
+        a.record(stream)
+        r = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b), r
+
+    base, r0 = timed(lambda: ctx.evaluate(gid, n=w.n, map_res=w.map_res, outputs=("energy",),
+                                          stream=stream.cuda_stream))
+    out = {"plain_ms": base, "tests": r0["tests"]}
+    gen = w.gen
+    sid = ctx.scene_load(w.scene.verts, w.scene.tris)
+    saved = gen.string.copy()
+    gen.string = (np.arange(gen.n_modules) // 5).astype(np.int32)
+    g2 = ctx.generator_define(sid, gen)
+    gen.string = saved
+    ctx.set_sun(g2, w.sun.xyz, w.sun.dni, w.sun.dhi, w.sun.dt_h)
+    t, r = timed(lambda: ctx.evaluate(g2, n=w.n, map_res=w.map_res, stream=stream.cuda_stream,
+                                      outputs=("energy", "string_energy", "string_energy_unshaded")))
+    se, seu = r["string_energy"].double().sum().item(), r["string_energy_unshaded"].double().sum().item()
+    out["strings"] = {"ms": t, "strings": int(len(np.unique(np.arange(gen.n_modules) // 5))),
+                      "loss_pct": 100.0 * (1.0 - se / seu)}
+    t, r = timed(lambda: ctx.evaluate(g2, n=w.n, map_res=w.map_res, stream=stream.cuda_stream,
+                                      outputs=("energy",), heat_bins=(36, 9)))
+    out["sky_map"] = {"ms": t, "bins": [36, 9], "occupied_bins": int((r["heat_steps"] > 0).sum().item())}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    f = ctx.sky_view(g2, rings=9, sectors=36, n=w.n, map_res=w.map_res)
+    t_sky = (time.perf_counter() - t0) * 1e3
+    t, r = timed(lambda: ctx.evaluate(g2, n=w.n, map_res=w.map_res, stream=stream.cuda_stream,
+                                      outputs=("energy", "energy_unshaded"), diffuse_shading=True))
+    e, eu = r["energy"].double().sum().item(), r["energy_unshaded"].double().sum().item()
+    out["diffuse"] = {"sky_view_ms_wall": t_sky, "patches": 324, "mean_cell_fraction": float(f.mean()),
+                      "year_ms": t, "loss_pct_with_diffuse": 100.0 * (1.0 - e / eu)}
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n = ctx.set_sun_clear_sky(g2, 40.0, 1.0, day_first=1, n_days=365)
+    out["sun_table"] = {"ms_wall": (time.perf_counter() - t0) * 1e3, "steps": int(n),
+                        "what": "hourly clear-sky year at 40 N, daylight steps kept"}
+    ctx.release(g2)
+    ctx.release(sid)
+    return out
+
+
 def serving_section(dev: int, n_requests: int) -> dict:
     """configs[4] on a bounded sample: requests over a pool of resident scenes
     (1e3-5.2e5 triangles), each a random range of 100-4400 sun steps.  The
@@ -446,6 +503,7 @@ def run_ours(args, rank, world, dist):
                            "evaluation, host read-back of the energies"}
 
     if rank == 0 and not args.no_serving and args.workload == "facade":
+        line["extensions"] = extensions_section(ctx, gid, w, stream)
         bt = batched_section(dev, args.batch_scenes)
         line["batched"] = bt
         line["serving"] = serving_section(dev, args.requests)

@@ -860,7 +860,7 @@ static WaveDev pack_wave(std::vector<JobDev>& jobs, size_t first, size_t last, i
         W.tot_win += (int64_t)J.k * groups;
         W.tot_mod += (int64_t)J.k * J.n_mods;
         W.tot_tri += ((int64_t)J.n_ml + (J.n_mtris + 31) / 32) * J.k;
-        W.tot_epi += (int64_t)J.n_cells + J.n_mods + J.n_str;
+        W.tot_epi += (J.kahan_cell ? (int64_t)J.n_cells : 0) + J.n_mods + J.n_str;
         W.tot_ss += (int64_t)J.k * (J.n_str ? J.n_sub_tot : 0);
         W.tot_sq += (int64_t)J.k * J.n_str;
         W.tot_heat += (int64_t)J.heat_az * J.heat_zen;
@@ -1139,7 +1139,8 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
     std::vector<WaveDev> waves;
     for (int64_t s0 = es.b; s0 < es.e; s0 += es.K) {
         int k = (int)std::min<int64_t>(es.K, es.e - s0);
-        jobs.push_back(make_job(c, g, s, es, s0, k, (float2*)c->kahan_mod.p, (float2*)c->kahan_cell.p, d_p, d_pu,
+        jobs.push_back(make_job(c, g, s, es, s0, k, (float2*)c->kahan_mod.p, d_cl ? (float2*)c->kahan_cell.p : nullptr,
+                                d_p, d_pu,
                                 d_cnt, d_bits, (float2*)c->kahan_str.p, d_sp, d_spu, h_e, h_eu, h_n,
                                 es.heat ? out->heat_az_bins : 0, es.heat ? out->heat_zen_bins : 0));
         waves.push_back(pack_wave(jobs, jobs.size() - 1, jobs.size(), tile_sh, u24, es.fused, es.count));
@@ -1168,7 +1169,8 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
         if (es.heat) CUDA_TRY(c, cudaMemsetAsync(c->heat.p, 0, (size_t)n_bins * 20, st));
         CUDA_TRY(c, cudaEventRecord(c->ev0, st));
         if ((rc = run_waves(c, waves, st, es.tile, es.fused, es.profile, es.count, extras))) return rc;
-        CUDA_TRY(c, launch_finalize_pairs((const float2*)c->kahan_mod.p, g.M, (const float2*)c->kahan_cell.p, g.C,
+        CUDA_TRY(c, launch_finalize_pairs((const float2*)c->kahan_mod.p, g.M, (const float2*)c->kahan_cell.p,
+                                          d_cl ? g.C : 0,
                                           d_e, d_eu, d_cl, st));
         if (es.strings)
             CUDA_TRY(c, launch_finalize_pairs((const float2*)c->kahan_str.p, NS, nullptr, 0, d_se, d_seu, nullptr, st));
@@ -1467,7 +1469,8 @@ static int finish(pv3d_ctx* c, pv3d_ctx::Request& r)
     const GenH& g = c->gens.at(r.gen_id);
     const int64_t S = r.es.e - r.es.b;
     cudaStream_t st = c->serve_stream;
-    CUDA_TRY(c, launch_finalize_pairs((const float2*)r.kmod.p, g.M, (const float2*)r.kcell.p, g.C, r.d_e, r.d_eu,
+    CUDA_TRY(c, launch_finalize_pairs((const float2*)r.kmod.p, g.M, (const float2*)r.kcell.p, r.d_cl ? g.C : 0, r.d_e,
+                                      r.d_eu,
                                       r.d_cl, st));
     pv3d_result* out = r.out;
     if (!out->is_device) {
@@ -1543,7 +1546,8 @@ static int serve_wave(pv3d_ctx* c, std::unique_lock<std::mutex>& lk)
         const int64_t need = per_step * k;
         if (!jobs.empty() && scratch + need > scratch_cap) break;
         scratch += need;
-        jobs.push_back(make_job(c, g, sc, r.es, r.next, k, (float2*)r.kmod.p, (float2*)r.kcell.p, r.d_p, r.d_pu,
+        jobs.push_back(make_job(c, g, sc, r.es, r.next, k, (float2*)r.kmod.p, r.d_cl ? (float2*)r.kcell.p : nullptr,
+                                r.d_p, r.d_pu,
                                 r.d_cnt, r.d_bits));
         in_wave.push_back(&r);
         ks.push_back(k);

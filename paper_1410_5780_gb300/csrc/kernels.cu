@@ -2362,56 +2362,72 @@ __device__ __forceinline__ void kahan_add(float2& acc, float x)
     acc.x = t;
 }
 
-__global__ void k_epilogue(const WaveDev* __restrict__ W, const JobDev* __restrict__ jobs, Buffers B)
+// One warp per item (cell, module or string): the lanes load 32 steps at a
+// time, then every lane applies the same Kahan additions in step order from
+// the shuffled values, so the sums equal a sequential loop over the steps
+// while the loads of 32 steps overlap.
+__global__ void __launch_bounds__(256) k_epilogue(const WaveDev* __restrict__ W, const JobDev* __restrict__ jobs,
+                                                  Buffers B)
 {
     const int64_t tot = W->tot_epi;
     const int nj = W->n_jobs;
-    for (int64_t item = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; item < tot;
-         item += (int64_t)gridDim.x * blockDim.x) {
-        int j = job_of(nj, item, [&](int q) { return jobs[q].it_epi; });
+    const int lane = threadIdx.x & 31;
+    const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t item = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; item < tot; item += n_warps) {
+        const int j = job_of(nj, item, [&](int q) { return jobs[q].it_epi; });
         const JobDev& J = jobs[j];
-        int64_t li = item - J.it_epi;
-        const int C = J.n_cells, Mn = J.n_mods;
+        const int64_t li = item - J.it_epi;
+        // cell items only when the per-cell beam loss is wanted
+        const int C = J.kahan_cell ? J.n_cells : 0, Mn = J.n_mods;
         const float inv_nn = 1.f / J.nn;
-        if (li < C) {
-            const int c = (int)li;
-            const int m = J.cell_mod[c];
-            float2 acc = J.kahan_cell[c];
-            for (int ls = 0; ls < J.k; ++ls) {
+        // kind 0: cell c; 1: module m; 2: string q
+        const int kind = li < C ? 0 : (li < C + Mn ? 1 : 2);
+        const int idx = kind == 0 ? (int)li : (kind == 1 ? (int)(li - C) : (int)(li - C - Mn));
+        const int m_cell = kind == 0 ? J.cell_mod[idx] : 0;
+        float2 a, au = make_float2(0.f, 0.f);
+        if (kind == 0) a = J.kahan_cell[idx];
+        else if (kind == 1) { a = J.kahan_mod[2 * idx]; au = J.kahan_mod[2 * idx + 1]; }
+        else { a = J.kahan_str[2 * idx]; au = J.kahan_str[2 * idx + 1]; }
+        for (int l0 = 0; l0 < J.k; l0 += 32) {
+            const int ls = l0 + lane;
+            float x = 0.f, xu = 0.f;
+            bool v = false;
+            if (ls < J.k) {
                 const LightParams& lp = B.lp[J.js_base + ls];
-                if (!lp.valid) continue;
-                const float beam = B.ms_beam[J.ms_base + (int64_t)ls * Mn + m];
-                const uint32_t cnt = B.cs_cnt[J.cs_base + (int64_t)ls * C + c];
-                kahan_add(acc, beam * (cnt * inv_nn) * lp.dt);
+                v = lp.valid != 0;
+                if (kind == 0) {
+                    if (v) {
+                        const float beam = B.ms_beam[J.ms_base + (int64_t)ls * Mn + m_cell];
+                        const uint32_t cnt = B.cs_cnt[J.cs_base + (int64_t)ls * C + idx];
+                        x = beam * (cnt * inv_nn) * lp.dt;
+                    }
+                } else if (kind == 1) {
+                    const int64_t msi = J.ms_base + (int64_t)ls * Mn + idx;
+                    const float p = B.ms_p[msi], pu = B.ms_pu[msi];
+                    if (J.out_power) J.out_power[(int64_t)(J.out_row0 + ls) * Mn + idx] = p;
+                    if (J.out_power_u) J.out_power_u[(int64_t)(J.out_row0 + ls) * Mn + idx] = pu;
+                    x = p * lp.dt;
+                    xu = pu * lp.dt;
+                } else if (v) {
+                    const int64_t sq = J.sq_base + (int64_t)ls * J.n_str + idx;
+                    x = B.sq_p[sq] * lp.dt;
+                    xu = B.sq_pu[sq] * lp.dt;
+                }
             }
-            J.kahan_cell[c] = acc;
-        } else if (li >= C + Mn) {
-            const int q = (int)(li - C - Mn);
-            float2 e = J.kahan_str[2 * q], eu = J.kahan_str[2 * q + 1];
-            for (int ls = 0; ls < J.k; ++ls) {
-                const LightParams& lp = B.lp[J.js_base + ls];
-                if (!lp.valid) continue;
-                const int64_t sq = J.sq_base + (int64_t)ls * J.n_str + q;
-                kahan_add(e, B.sq_p[sq] * lp.dt);
-                kahan_add(eu, B.sq_pu[sq] * lp.dt);
+            const unsigned int vm = __ballot_sync(0xffffffffu, v);
+            const int n_here = min(32, J.k - l0);
+            for (int q = 0; q < n_here; ++q) {
+                const float xq = __shfl_sync(0xffffffffu, x, q);
+                const float xuq = __shfl_sync(0xffffffffu, xu, q);
+                if (!((vm >> q) & 1u)) continue;
+                kahan_add(a, xq);
+                if (kind != 0) kahan_add(au, xuq);
             }
-            J.kahan_str[2 * q] = e;
-            J.kahan_str[2 * q + 1] = eu;
-        } else {
-            const int m = (int)(li - C);
-            float2 e = J.kahan_mod[2 * m], eu = J.kahan_mod[2 * m + 1];
-            for (int ls = 0; ls < J.k; ++ls) {
-                const LightParams& lp = B.lp[J.js_base + ls];
-                const int64_t msi = J.ms_base + (int64_t)ls * Mn + m;
-                const float p = B.ms_p[msi], pu = B.ms_pu[msi];
-                if (J.out_power) J.out_power[(int64_t)(J.out_row0 + ls) * Mn + m] = p;
-                if (J.out_power_u) J.out_power_u[(int64_t)(J.out_row0 + ls) * Mn + m] = pu;
-                if (!lp.valid) continue;
-                kahan_add(e, p * lp.dt);
-                kahan_add(eu, pu * lp.dt);
-            }
-            J.kahan_mod[2 * m] = e;
-            J.kahan_mod[2 * m + 1] = eu;
+        }
+        if (lane == 0) {
+            if (kind == 0) J.kahan_cell[idx] = a;
+            else if (kind == 1) { J.kahan_mod[2 * idx] = a; J.kahan_mod[2 * idx + 1] = au; }
+            else { J.kahan_str[2 * idx] = a; J.kahan_str[2 * idx + 1] = au; }
         }
     }
 }

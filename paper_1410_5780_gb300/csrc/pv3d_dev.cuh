@@ -98,7 +98,7 @@ struct JobDev {
     int64_t it_win, it_mod, it_tri, it_epi;
     // accumulators across the waves of one evaluation
     float2* kahan_mod;   // [M][2]  (E, comp), (E_unshaded, comp)
-    float2* kahan_cell;  // [C]     (beam loss, comp)
+    float2* kahan_cell;  // [C]     (beam loss, comp); nullptr when the per-cell beam loss is not wanted
     // optional outputs, row = out_row0 + local step
     float* out_power;
     float* out_power_u;

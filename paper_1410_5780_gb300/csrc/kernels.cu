@@ -1396,26 +1396,27 @@ __device__ __forceinline__ void test_items(const RecvSm* recv, int n_recv, int t
         int Jr, cu, cv, jj, Ib, Ie;
         const RecvSm& R = decode_item(recv, n_recv, it, n, inv_n, Jr, cu, cv, jj, Ib, Ie);
         if (PROF) cand += (unsigned int)max(0, Ie - Ib + 1);
-        uint32_t cnt = 0;
-        unsigned long long bits = 0ull;
+        // the receiver's sample frame in registers for the row's samples
+        const ModStep s = R.s;
+        const float p_over_n = R.p_over_n;
+        const int i0 = cu * n;
+        uint32_t row = 0u;  // bit i: sample i of the item's row (within its cell) is shaded
         for (int I = Ib; I <= Ie; ++I) {
             float a, b, d;
             int ix, iy;
-            sample_ab(I, Jr, R.p_over_n, a, b);
-            sample_texel(R.s, a, b, R_, ix, iy, d);
+            sample_ab(I, Jr, p_over_n, a, b);
+            sample_texel(s, a, b, R_, ix, iy, d);
             if ((ix >> SH) != tx || (iy >> SH) != ty) continue;
             if (PROF) ++samples;
-            if (sample_test<TS, WORDS, PROF>(tri, n_kept, sbm, nw, seen, ix & (TS - 1), iy & (TS - 1), d, R.s.bias,
-                                             lp, u24, pairs, frags)) {
-                ++cnt;
-                const int k = jj * n + (I - cu * n);
-                if (k < 64) bits |= 1ull << k;
-            }
+            if (sample_test<TS, WORDS, PROF>(tri, n_kept, sbm, nw, seen, ix & (TS - 1), iy & (TS - 1), d, s.bias,
+                                             lp, u24, pairs, frags))
+                row |= 1u << (I - i0);
         }
-        if (cnt) {
+        if (row) {
             const int gcell = R.cell_base + cv * R.cu + cu;
-            atomicAdd(&cnt_row[gcell], cnt);
-            if (want_bits) atomicOr(&bits_row[gcell], bits);
+            atomicAdd(&cnt_row[gcell], (uint32_t)__popc(row));
+            // sample k = jj * n + i of the cell; flags kept for k < 64
+            if (want_bits && jj * n < 64) atomicOr(&bits_row[gcell], (unsigned long long)row << (jj * n));
         }
     }
 }
@@ -1696,7 +1697,7 @@ constexpr int kWarpTri = 64;
 constexpr int kWarpWords = kWarpTri / 32;
 constexpr int kWarpRecv = 16;
 constexpr int kWarpBins = 512;
-constexpr int kTileWarps = 4;   // warps per block; 8 blocks per SM
+constexpr int kTileWarps = 4;   // warps per block; 6 blocks per SM (80 registers a thread)
 
 template <int TS, bool PROF>
 struct WarpSm {
@@ -1705,7 +1706,7 @@ struct WarpSm {
 };
 
 template <int TS, bool PROF>
-__global__ void __launch_bounds__(kTileWarps * 32, 8) k_tile_warp(const WaveDev* __restrict__ W,
+__global__ void __launch_bounds__(kTileWarps * 32, 6) k_tile_warp(const WaveDev* __restrict__ W,
                                                                   const JobDev* __restrict__ jobs, Buffers B)
 {
     __shared__ __align__(16) WarpSm<TS, PROF> sm_all[kTileWarps];
@@ -2573,7 +2574,7 @@ static void launch_tile_kernels(const WaveDev* W, const JobDev* d_jobs, const Bu
 {
     const int sm = cfg.sm_count;
     if (cfg.fused) {
-        k_tile_warp<TS, PROF><<<sm * 8, kTileWarps * 32, 0, cfg.stream>>>(W, d_jobs, b);
+        k_tile_warp<TS, PROF><<<sm * 6, kTileWarps * 32, 0, cfg.stream>>>(W, d_jobs, b);
         if (cfg.ev) cudaEventRecord(cfg.ev[3], cfg.stream);
         k_raster_test<TS, PROF><<<sm * 4, 256, 0, cfg.stream>>>(W, d_jobs, b);
     } else {

@@ -82,7 +82,9 @@ def _load():
                  C.c_double, P, C.c_int64, P, C.c_int32, P, P])
             lib.pv3d_oracle_string_power_from_counts.argtypes = (
                 [C.c_int32, P, P, P, P, P, C.c_int32, P, P, P, P, P, C.c_int32, C.c_double, C.c_double,
-                 C.c_double, P, C.c_int64, P, C.c_int32, P, P, P])
+                 C.c_double, P, C.c_int64, P, C.c_int32, P, P, P, P, C.c_int32, P, P])
+            lib.pv3d_oracle_parallel_pmpp.restype = C.c_double
+            lib.pv3d_oracle_parallel_pmpp.argtypes = [C.c_int32, P, P, P, C.c_double]
             lib.pv3d_oracle_sun_table.restype = C.c_int64
             lib.pv3d_oracle_sun_table.argtypes = [C.c_double, C.c_int32, C.c_int32, C.c_double, C.c_int32,
                                                   C.c_double, P, P, P]
@@ -268,6 +270,16 @@ def series_pmpp(ik, vk, v_diode=V_DIODE) -> float:
     return lib.pv3d_oracle_series_pmpp(ik.size, _ptr(ik), _ptr(vk), v_diode)
 
 
+def parallel_pmpp(strings, v_diode=V_DIODE) -> float:
+    """Maximum power of series strings in parallel at one voltage; `strings`
+    is a list of (ik, vk) substring current limits and voltages."""
+    lib = _load()
+    off = np.concatenate([[0], np.cumsum([len(a) for a, _ in strings])]).astype(np.int32)
+    ik = np.ascontiguousarray(np.concatenate([a for a, _ in strings]), np.float64)
+    vk = np.ascontiguousarray(np.concatenate([b for _, b in strings]), np.float64)
+    return lib.pv3d_oracle_parallel_pmpp(len(strings), _ptr(off), _ptr(ik), _ptr(vk), v_diode)
+
+
 def string_index(gen):
     """(strings, mod_string): the distinct string ids in ascending order, and
     each module's index into them."""
@@ -293,8 +305,44 @@ def string_power_from_counts(w, steps, counts, i_ref=I_REF, v_cell=V_CELL, v_dio
         mod_f.shape[0], _ptr(mod_f), _ptr(mod_i), _ptr(lay_off), _ptr(lay_nsub), _ptr(lay_sub), n_trk,
         _ptr(pivots), _ptr(np.ascontiguousarray(sun.xyz, np.float64)), _ptr(np.ascontiguousarray(sun.dni, np.float32)),
         _ptr(np.ascontiguousarray(sun.dhi, np.float32)), _ptr(pz), int(w.n), i_ref, v_cell, v_diode,
-        _ptr(steps), steps.size, _ptr(ms), ids.size, _ptr(cnt), _ptr(p), _ptr(pu))
+        _ptr(steps), steps.size, _ptr(ms), ids.size, _ptr(cnt), _ptr(p), _ptr(pu), None, 0, None, None)
     return p, pu
+
+
+def array_index(gen):
+    """(arrays, str_array): the distinct array ids of the generator's modules in
+    ascending order, and each string's index into them (the strings in
+    ascending string id; all modules of a string share one array id)."""
+    arr = np.zeros(len(gen.string), np.int32) if getattr(gen, "array", None) is None else np.asarray(gen.array)
+    sid, ms = string_index(gen)
+    a_ids = np.unique(arr)
+    str_array = np.zeros(sid.size, np.int32)
+    str_array[ms] = np.searchsorted(a_ids, arr)
+    return a_ids, str_array
+
+
+def array_power_from_counts(w, steps, counts, i_ref=I_REF, v_cell=V_CELL, v_diode=V_DIODE):
+    """Oracle model of the arrays of strings in parallel (one voltage and one
+    maximum power point per array) on given per-cell shaded counts [S, C];
+    returns (power, power_unshaded) [S, n_arrays], arrays in ascending id."""
+    lib = _load()
+    gen, sun = w.gen, w.sun
+    mod_f, mod_i, lay_off, lay_nsub, lay_sub, n_trk, pivots = _gen_arrays(gen)
+    ids, ms = string_index(gen)
+    a_ids, str_array = array_index(gen)
+    steps = np.ascontiguousarray(steps, np.int64)
+    cnt = np.ascontiguousarray(counts, np.int32)
+    pz = (np.zeros((sun.xyz.shape[0], 1, 2), np.float32) if w.poses is None or n_trk == 0
+          else np.ascontiguousarray(w.poses, np.float32))
+    p = np.zeros((steps.size, ids.size)); pu = np.zeros((steps.size, ids.size))
+    ap = np.zeros((steps.size, a_ids.size)); apu = np.zeros((steps.size, a_ids.size))
+    lib.pv3d_oracle_string_power_from_counts(
+        mod_f.shape[0], _ptr(mod_f), _ptr(mod_i), _ptr(lay_off), _ptr(lay_nsub), _ptr(lay_sub), n_trk,
+        _ptr(pivots), _ptr(np.ascontiguousarray(sun.xyz, np.float64)), _ptr(np.ascontiguousarray(sun.dni, np.float32)),
+        _ptr(np.ascontiguousarray(sun.dhi, np.float32)), _ptr(pz), int(w.n), i_ref, v_cell, v_diode,
+        _ptr(steps), steps.size, _ptr(ms), ids.size, _ptr(cnt), _ptr(p), _ptr(pu), _ptr(str_array), a_ids.size,
+        _ptr(ap), _ptr(apu))
+    return ap, apu
 
 
 def sun_table(lat_deg: float, day_first: int, n_days: int, step_h: float, daylight_only: bool = True,

@@ -856,6 +856,45 @@ double pv3d_oracle_series_pmpp(int32_t n_sub, const double* ik, const double* vk
     return best;
 }
 
+/*
+ * Strings in parallel at one maximum power point tracker (the inverter's
+ * input: Section 2's generator of strings, Fig. 2).  One voltage V is across
+ * every string; string s delivers the largest current I at which its voltage
+ * V_s(I) = sum_{k: I_k >= I} V_k - v_diode * #{k: I_k < I} still reaches V.
+ * V_s is a non-increasing step function of I whose steps are at the
+ * substring currents, so string s's current at V is the largest I_k of its
+ * substrings with V_s(I_k) >= V (0 if none), and P(V) = V * sum_s I_s(V) is
+ * linear in V between the voltages V_s(I_k): its maximum is the best of
+ * those voltages.  String s owns substrings [str_off[s], str_off[s + 1]).
+ */
+double pv3d_oracle_parallel_pmpp(int32_t n_str, const int32_t* str_off, const double* ik, const double* vk,
+                                 double v_diode)
+{
+    int32_t n_all = str_off[n_str];
+    double* w = (double*)malloc(sizeof(double) * (size_t)(n_all > 0 ? n_all : 1));
+    for (int32_t s = 0; s < n_str; ++s)
+        for (int32_t k = str_off[s]; k < str_off[s + 1]; ++k) {
+            double v = 0.0;
+            for (int32_t j = str_off[s]; j < str_off[s + 1]; ++j) v += (ik[j] >= ik[k]) ? vk[j] : -v_diode;
+            w[k] = v;  /* string s's voltage at current ik[k] */
+        }
+    double best = 0.0;
+    for (int32_t c = 0; c < n_all; ++c) {
+        double V = w[c];
+        if (!(V > 0.0)) continue;
+        double cur = 0.0;
+        for (int32_t s = 0; s < n_str; ++s) {
+            double is = 0.0;
+            for (int32_t k = str_off[s]; k < str_off[s + 1]; ++k)
+                if (w[k] >= V && ik[k] > is) is = ik[k];
+            cur += is;
+        }
+        if (V * cur > best) best = V * cur;
+    }
+    free(w);
+    return best;
+}
+
 /* Current limit and voltage of each substring of one module from its cell
  * irradiances g (W/m^2): written to ik[0..n_sub), vk[0..n_sub). */
 static void module_substrings(int32_t n_cells, const double* g, const int32_t* cell_sub, int32_t n_sub,
@@ -874,7 +913,10 @@ static void module_substrings(int32_t n_cells, const double* g, const int32_t* c
  * String powers for given shaded-sample counts: power[s * n_str + q] and
  * power_unshaded[s * n_str + q] of string q, where mod_string[m] = q names the
  * string of module m, and counts[s * C + cell] holds every module's cells in
- * module order.  A step with the sun at or below the horizon gives 0.
+ * module order.  A step with the sun at or below the horizon gives 0.  With
+ * str_array (string q in parallel array str_array[q] < n_arr) and apower /
+ * apower_u non-NULL, also the powers of the arrays of strings in parallel,
+ * apower[s * n_arr + a].
  */
 int pv3d_oracle_string_power_from_counts(int32_t n_mods, const float* mod_f, const int32_t* mod_i,
                                          const int32_t* lay_off, const int32_t* lay_nsub, const int32_t* lay_sub,
@@ -882,7 +924,8 @@ int pv3d_oracle_string_power_from_counts(int32_t n_mods, const float* mod_f, con
                                          const float* dhi, const float* poses, int32_t n, double i_ref,
                                          double v_cell, double v_diode, const int64_t* eval_steps,
                                          int64_t n_eval_steps, const int32_t* mod_string, int32_t n_str,
-                                         const int32_t* counts, double* power, double* power_unshaded)
+                                         const int32_t* counts, double* power, double* power_unshaded,
+                                         const int32_t* str_array, int32_t n_arr, double* apower, double* apower_u)
 {
     ogen_t G;
     memset(&G, 0, sizeof(G));
@@ -934,6 +977,28 @@ int pv3d_oracle_string_power_from_counts(int32_t n_mods, const float* mod_f, con
             int64_t b = str_base[q], e = str_base[q + 1];
             power[si * n_str + q] = pv3d_oracle_series_pmpp((int32_t)(e - b), ik + b, vk + b, v_diode);
             power_unshaded[si * n_str + q] = pv3d_oracle_series_pmpp((int32_t)(e - b), iu + b, vk + b, v_diode);
+        }
+        if (str_array && apower && apower_u) {
+            /* each array: its strings' substrings gathered, string by string */
+            double* gi = (double*)malloc(sizeof(double) * (size_t)(n_sub_all + 1));
+            double* gu = (double*)malloc(sizeof(double) * (size_t)(n_sub_all + 1));
+            double* gv = (double*)malloc(sizeof(double) * (size_t)(n_sub_all + 1));
+            int32_t* off = (int32_t*)malloc(sizeof(int32_t) * (size_t)(n_str + 1));
+            for (int32_t a = 0; a < n_arr; ++a) {
+                int32_t ns = 0, nk = 0;
+                off[0] = 0;
+                for (int32_t q = 0; q < n_str; ++q) {
+                    if (str_array[q] != a) continue;
+                    for (int64_t k = str_base[q]; k < str_base[q + 1]; ++k) {
+                        gi[nk] = ik[k]; gu[nk] = iu[k]; gv[nk] = vk[k];
+                        ++nk;
+                    }
+                    off[++ns] = nk;
+                }
+                apower[si * n_arr + a] = pv3d_oracle_parallel_pmpp(ns, off, gi, gv, v_diode);
+                apower_u[si * n_arr + a] = pv3d_oracle_parallel_pmpp(ns, off, gu, gv, v_diode);
+            }
+            free(gi); free(gu); free(gv); free(off);
         }
     }
     free(cell0); free(ik); free(vk); free(iu); free(str_fill); free(str_base); free(g); free(gu);

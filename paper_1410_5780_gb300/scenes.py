@@ -67,6 +67,7 @@ class Generator:
     string: np.ndarray   # (M,) int32
     layouts: list = field(default_factory=list)
     pivots: np.ndarray = field(default_factory=lambda: np.zeros((0, 3), np.float32))
+    array: np.ndarray | None = None  # (M,) int32 inverter input of the module's string (None: all 0)
 
     @property
     def n_modules(self) -> int:

@@ -300,6 +300,42 @@ def test_string_mpp_is_max_over_current_scan_and_below_module_mppt():
         assert p <= sum(oracle.module_pmpp(g, lay.cell_sub, 3) for g in gs) + 1e-9
 
 
+def test_parallel_strings_closed_forms_and_scan():
+    """Strings in parallel at one voltage: one string is the series model; k
+    identical strings give k times its power; a fine voltage scan (each
+    string's current = the largest current on a fine grid whose string voltage
+    still reaches V) agrees; the array never beats its strings' own maxima."""
+    lay = S.standard_layout(6, 10, 3)
+    rng = np.random.default_rng(12)
+    for _ in range(20):
+        strings = []
+        for _ in range(int(rng.integers(1, 5))):
+            gs = [rng.uniform(50, 1000, 60) for _ in range(int(rng.integers(1, 4)))]
+            subs = [_substrings(g, lay.cell_sub, 3) for g in gs]
+            strings.append((np.concatenate([a for a, _ in subs]), np.concatenate([b for _, b in subs])))
+        p = oracle.parallel_pmpp(strings)
+        if len(strings) == 1:
+            assert abs(p - oracle.series_pmpp(*strings[0])) < 1e-9
+        assert abs(oracle.parallel_pmpp([strings[0]] * 3) - 3 * oracle.series_pmpp(*strings[0])) < 1e-9
+        assert p <= sum(oracle.series_pmpp(a, b) for a, b in strings) + 1e-9
+        # brute force: voltage scan, currents on a fine grid
+        imax = max(a.max() for a, _ in strings)
+        igrid = np.linspace(0, imax, 4001)
+        curves = []
+        for a, b in strings:
+            v_of_i = np.where(a[None, :] >= igrid[:, None], b[None, :], -oracle.V_DIODE).sum(1)  # non-increasing
+            curves.append(v_of_i)
+        vmax = max(c.max() for c in curves)
+        best = 0.0
+        for V in np.linspace(0, vmax, 3001):
+            cur = 0.0
+            for c in curves:
+                ok = np.flatnonzero(c >= V)
+                cur += igrid[ok[-1]] if ok.size else 0.0
+            best = max(best, V * cur)
+        assert best - 1e-9 <= p <= best + (imax / 4000 + 0) * vmax * len(strings) + vmax / 3000 * imax * len(strings) + 1e-9
+
+
 def test_string_power_from_counts_matches_modules_and_strings():
     """String powers from shaded counts: with every module its own string they
     are the module powers; grouped into strings they follow series_pmpp of the
@@ -321,6 +357,13 @@ def test_string_power_from_counts_matches_modules_and_strings():
     assert np.all(p <= p_mod[:, [2, 3, 4]].sum(1)[:, None] * [1, 0, 0] + p_mod[:, [0, 1]].sum(1)[:, None] * [0, 1, 0]
                   + p_mod[:, [5]].sum(1)[:, None] * [0, 0, 1] + 1e-9)
     np.testing.assert_allclose(p[:, 2], p_mod[:, 5], rtol=1e-12, atol=1e-12)
+    # arrays of strings in parallel: one array per string is the string model
+    w.gen.array = np.array([0, 0, 1, 1, 1, 2], np.int32)
+    ap, apu = oracle.array_power_from_counts(w, steps, counts)
+    np.testing.assert_allclose(ap, p[:, [1, 0, 2]], rtol=1e-12, atol=1e-12)  # strings 3, 7, 9 -> arrays 1, 0, 2
+    w.gen.array = np.array([4, 4, 4, 4, 4, 4], np.int32)
+    ap, apu = oracle.array_power_from_counts(w, steps, counts)
+    assert ap.shape == (steps.size, 1) and np.all(ap[:, 0] <= p.sum(1) + 1e-9)
 
 
 def test_sun_table_closed_forms():

@@ -90,7 +90,8 @@ typedef struct pv3d_module {
     int32_t layout;     /* index into the layouts of pv3d_generator_define */
     int32_t tracker;    /* index into the trackers, or -1 for a fixed module */
     int32_t string_id;  /* series string the module belongs to (string outputs of pv3d_evaluate) */
-    int32_t reserved;
+    int32_t array_id;   /* inverter input: strings whose modules share it are in parallel (array outputs);
+                           all modules of a string carry the same array_id */
 } pv3d_module;
 
 /*
@@ -211,6 +212,15 @@ typedef struct pv3d_result {
     double* heat_energy;             /* [heat_zen_bins x heat_az_bins] Wh */
     double* heat_energy_unshaded;    /* [heat_zen_bins x heat_az_bins] Wh */
     int32_t* heat_steps;             /* [heat_zen_bins x heat_az_bins] */
+    /* strings in parallel (pv3d_evaluate only): NA = pv3d_generator_arrays'
+     * count, arrays in ascending array_id order.  One voltage is across every
+     * string of an array and the array runs at its own maximum power point;
+     * string s delivers the largest current at which its voltage still
+     * reaches the array's (at most 512 bypass substrings per array). */
+    double* array_energy;            /* [NA] sum over steps of the array's P_mpp * dt, Wh */
+    double* array_energy_unshaded;   /* [NA] */
+    float* array_power;              /* [S x NA] */
+    float* array_power_unshaded;     /* [S x NA] */
 } pv3d_result;
 
 /* ---- context ------------------------------------------------------------ */
@@ -322,6 +332,11 @@ int pv3d_sky_view(pv3d_ctx* ctx, uint32_t gen_id, const pv3d_sky_view_opts* opts
  * generator), PV3D_E_INVALID (null context or count pointer).
  */
 int pv3d_generator_strings(pv3d_ctx* ctx, uint32_t gen_id, int32_t* n_strings, int32_t* string_ids);
+
+/* Arrays of a generator (strings in parallel at one inverter input): the number
+ * and the distinct array_id values in ascending order, the order of the array
+ * outputs of pv3d_result.  Errors as pv3d_generator_strings. */
+int pv3d_generator_arrays(pv3d_ctx* ctx, uint32_t gen_id, int32_t* n_arrays, int32_t* array_ids);
 
 /*
  * Tracker poses: az_tilt[(step * n_trackers + t) * 2 + {0, 1}] = compass

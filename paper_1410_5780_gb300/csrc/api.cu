@@ -70,6 +70,11 @@ struct GenH {
     int32_t* d_sub_nk = nullptr;    // [n_sub_tot]
     int32_t* d_sub_mod = nullptr;   // [n_sub_tot]
     float* d_fdiff = nullptr;       // [C] diffuse shading fraction per cell (pv3d_sky_view)
+    // arrays of parallel strings: distinct array ids ascending; their strings
+    std::vector<int32_t> arr_ids;
+    int32_t max_arr_sub = 0;        // substrings of the largest array
+    int32_t* d_arr_off = nullptr;   // [n_arr + 1]
+    int32_t* d_arr_strs = nullptr;  // [n_str]
     size_t bytes = 0;
 };
 
@@ -92,7 +97,8 @@ struct pv3d_ctx {
     std::map<uint32_t, GenH> gens;
     uint32_t next_id = 1;
     // workspace pools
-    DevBuf lp, win, ms, ms_p, ms_pu, ms_beam, ms_iu, ss_i, sq_p, sq_pu, kahan_str, js_p, js_pu, js_bin, heat, cs_cnt, cs_bits, t_far, t_cnt, t_off, t_cur, t_slot, t_rcnt, t_roff, t_rcur, nonempty, heavy, bins, pairs, recv, map,
+    DevBuf lp, win, ms, ms_p, ms_pu, ms_beam, ms_iu, ss_i, sq_p, sq_pu, kahan_str, js_p, js_pu, js_bin, heat, sa_p, sa_pu,
+        kahan_arr, cs_cnt, cs_bits, t_far, t_cnt, t_off, t_cur, t_slot, t_rcnt, t_roff, t_rcur, nonempty, heavy, bins, pairs, recv, map,
         big, block_sums, ctr, waves, jobs, kahan_mod, kahan_cell, staging;
     int64_t bin_cap = 0, map_cap_tiles = 0, big_cap = 0, recv_cap = 0;
     uint64_t bufgen = 0;  // bumped whenever a pool is reallocated (captured graphs hold its pointers)
@@ -199,7 +205,7 @@ static void free_gen(GenH& g)
 {
     void* ps[] = {g.d_mods, g.d_cell_mod, g.d_lay_sub, g.d_lay_off, g.d_lay_nk, g.d_lay_nk_off, g.d_pivots,
                   g.d_sun, g.d_dni, g.d_dhi, g.d_dt, g.d_poses, g.d_str_sub, g.d_sub_base, g.d_sub_nk,
-                  g.d_sub_mod, g.d_fdiff};
+                  g.d_sub_mod, g.d_fdiff, g.d_arr_off, g.d_arr_strs};
     for (void* p : ps)
         if (p) cudaFree(p);
 }
@@ -491,6 +497,35 @@ extern "C" int pv3d_generator_define(pv3d_ctx* c, uint32_t scene_id, const pv3d_
         str_sub.push_back((int32_t)sub_nk.size());
         g.n_sub_tot = (int32_t)sub_nk.size();
     }
+    // arrays of parallel strings: every module of a string names the same array
+    std::vector<int32_t> arr_off, arr_strs;
+    {
+        const size_t NS = g.str_ids.size();
+        std::vector<int32_t> str_arr(NS, INT32_MIN);
+        for (int32_t m = 0; m < n_mods; ++m) {
+            const size_t q = std::lower_bound(g.str_ids.begin(), g.str_ids.end(), mods[m].string_id) - g.str_ids.begin();
+            if (str_arr[q] == INT32_MIN) str_arr[q] = mods[m].array_id;
+            else if (str_arr[q] != mods[m].array_id)
+                return fail(c, PV3D_E_INVALID, "string %d: its modules name different array_id values",
+                            mods[m].string_id);
+        }
+        g.arr_ids = str_arr;
+        std::sort(g.arr_ids.begin(), g.arr_ids.end());
+        g.arr_ids.erase(std::unique(g.arr_ids.begin(), g.arr_ids.end()), g.arr_ids.end());
+        std::vector<std::vector<int32_t>> members(g.arr_ids.size());
+        for (size_t q = 0; q < NS; ++q)
+            members[std::lower_bound(g.arr_ids.begin(), g.arr_ids.end(), str_arr[q]) - g.arr_ids.begin()].push_back((int32_t)q);
+        for (auto& mem : members) {
+            arr_off.push_back((int32_t)arr_strs.size());
+            int32_t nsub = 0;
+            for (int32_t q : mem) {
+                arr_strs.push_back(q);
+                nsub += str_sub[q + 1] - str_sub[q];
+            }
+            g.max_arr_sub = std::max(g.max_arr_sub, nsub);
+        }
+        arr_off.push_back((int32_t)arr_strs.size());
+    }
     int rc;
     if ((rc = upload(c, &g.d_mods, g.mods_h.data(), g.mods_h.size())) ||
         (rc = upload(c, &g.d_cell_mod, cell_mod.data(), cell_mod.size())) ||
@@ -502,7 +537,9 @@ extern "C" int pv3d_generator_define(pv3d_ctx* c, uint32_t scene_id, const pv3d_
         (rc = upload(c, &g.d_str_sub, str_sub.data(), str_sub.size())) ||
         (rc = upload(c, &g.d_sub_base, sub_base.data(), sub_base.size())) ||
         (rc = upload(c, &g.d_sub_nk, sub_nk.data(), sub_nk.size())) ||
-        (rc = upload(c, &g.d_sub_mod, sub_mod.data(), sub_mod.size()))) {
+        (rc = upload(c, &g.d_sub_mod, sub_mod.data(), sub_mod.size())) ||
+        (rc = upload(c, &g.d_arr_off, arr_off.data(), arr_off.size())) ||
+        (rc = upload(c, &g.d_arr_strs, arr_strs.data(), arr_strs.size()))) {
         free_gen(g);
         return rc;
     }
@@ -521,6 +558,16 @@ extern "C" int pv3d_generator_strings(pv3d_ctx* c, uint32_t gen_id, int32_t* n_s
     if (it == c->gens.end()) return fail(c, PV3D_E_NOTFOUND, "unknown generator %u", gen_id);
     *n_strings = (int32_t)it->second.str_ids.size();
     if (string_ids) std::copy(it->second.str_ids.begin(), it->second.str_ids.end(), string_ids);
+    return PV3D_OK;
+}
+
+extern "C" int pv3d_generator_arrays(pv3d_ctx* c, uint32_t gen_id, int32_t* n_arrays, int32_t* array_ids)
+{
+    if (!c || !n_arrays) return PV3D_E_INVALID;
+    auto it = c->gens.find(gen_id);
+    if (it == c->gens.end()) return fail(c, PV3D_E_NOTFOUND, "unknown generator %u", gen_id);
+    *n_arrays = (int32_t)it->second.arr_ids.size();
+    if (array_ids) std::copy(it->second.arr_ids.begin(), it->second.arr_ids.end(), array_ids);
     return PV3D_OK;
 }
 
@@ -712,7 +759,7 @@ extern "C" int pv3d_set_sun_clear_sky(pv3d_ctx* c, uint32_t gen_id, const pv3d_s
 namespace {
 
 struct EvalSetup {
-    int n, R, K, tile, fused, profile, count, strings, heat, diffuse;
+    int n, R, K, tile, fused, profile, count, strings, heat, diffuse, arrays;
     int64_t b, e;
     float i_ref, v_cell, v_diode;
 };
@@ -746,7 +793,11 @@ static int check_eval(pv3d_ctx* c, const GenH& g, const pv3d_eval_opts* o, const
     if (out->sample_bits && es.n > 8) return fail(c, PV3D_E_INVALID, "sample_bits needs samples_per_side <= 8");
     es.diffuse = d.diffuse_shading != 0;
     if (es.diffuse && !g.d_fdiff) return fail(c, PV3D_E_INVALID, "diffuse_shading needs pv3d_sky_view first");
-    es.strings = out->string_energy || out->string_energy_unshaded || out->string_power || out->string_power_unshaded;
+    es.arrays = out->array_energy || out->array_energy_unshaded || out->array_power || out->array_power_unshaded;
+    if (es.arrays && g.max_arr_sub > kMaxArraySub)
+        return fail(c, PV3D_E_INVALID, "an array holds %d bypass substrings (at most %d)", g.max_arr_sub, kMaxArraySub);
+    es.strings = out->string_energy || out->string_energy_unshaded || out->string_power || out->string_power_unshaded ||
+                 es.arrays;
     es.heat = out->heat_az_bins > 0 || out->heat_zen_bins > 0 || out->heat_energy || out->heat_energy_unshaded ||
               out->heat_steps;
     if (es.heat && (out->heat_az_bins < 1 || out->heat_az_bins > 1024 || out->heat_zen_bins < 1 ||
@@ -759,7 +810,8 @@ static int check_eval(pv3d_ctx* c, const GenH& g, const pv3d_eval_opts* o, const
 static JobDev make_job(pv3d_ctx* c, const GenH& g, const SceneH& s, const EvalSetup& es, int64_t step0, int k,
                        float2* kmod, float2* kcell, float* pw, float* pwu, uint8_t* cnt, unsigned long long* bits,
                        float2* kstr = nullptr, float* spw = nullptr, float* spwu = nullptr, double* heat_e = nullptr,
-                       double* heat_eu = nullptr, int32_t* heat_n = nullptr, int heat_az = 0, int heat_zen = 0)
+                       double* heat_eu = nullptr, int32_t* heat_n = nullptr, int heat_az = 0, int heat_zen = 0,
+                       float2* karr = nullptr, float* apw = nullptr, float* apwu = nullptr)
 {
     JobDev J{};
     J.tri = s.d_tri;
@@ -817,6 +869,14 @@ static JobDev make_job(pv3d_ctx* c, const GenH& g, const SceneH& s, const EvalSe
         J.out_str_power_u = spwu;
     }
     J.fdiff = es.diffuse ? g.d_fdiff : nullptr;
+    if (es.arrays) {
+        J.n_arr = (int32_t)g.arr_ids.size();
+        J.arr_off = g.d_arr_off;
+        J.arr_strs = g.d_arr_strs;
+        J.kahan_arr = karr;
+        J.out_arr_power = apw;
+        J.out_arr_power_u = apwu;
+    }
     if (heat_e) {
         J.heat_az = heat_az;
         J.heat_zen = heat_zen;
@@ -852,6 +912,7 @@ static WaveDev pack_wave(std::vector<JobDev>& jobs, size_t first, size_t last, i
         J.sq_base = W.tot_sq;
         J.it_str = W.tot_sq;
         J.it_heat = W.tot_heat;
+        J.sa_base = W.tot_sa;
         int64_t groups = (J.n_mods + kWinPerItem - 1) / kWinPerItem;
         W.tot_js += J.k;
         W.tot_te += (int64_t)J.k * J.tiles_x * J.tiles_x;
@@ -860,7 +921,8 @@ static WaveDev pack_wave(std::vector<JobDev>& jobs, size_t first, size_t last, i
         W.tot_win += (int64_t)J.k * groups;
         W.tot_mod += (int64_t)J.k * J.n_mods;
         W.tot_tri += ((int64_t)J.n_ml + (J.n_mtris + 31) / 32) * J.k;
-        W.tot_epi += (J.kahan_cell ? (int64_t)J.n_cells : 0) + J.n_mods + J.n_str;
+        W.tot_epi += (J.kahan_cell ? (int64_t)J.n_cells : 0) + J.n_mods + J.n_str + J.n_arr;
+        W.tot_sa += (int64_t)J.k * J.n_arr;
         W.tot_ss += (int64_t)J.k * (J.n_str ? J.n_sub_tot : 0);
         W.tot_sq += (int64_t)J.k * J.n_str;
         W.tot_heat += (int64_t)J.heat_az * J.heat_zen;
@@ -870,9 +932,10 @@ static WaveDev pack_wave(std::vector<JobDev>& jobs, size_t first, size_t last, i
 }
 
 static int ensure_workspace(pv3d_ctx* c, int64_t js, int64_t te, int64_t ms, int64_t cs, int tile, bool fused,
-                            bool want_bits, int64_t ss = 0, int64_t sq = 0)
+                            bool want_bits, int64_t ss = 0, int64_t sq = 0, int64_t sa = 0)
 {
     int rc;
+    if (sa > 0 && ((rc = ensure(c, c->sa_p, sa * 4)) || (rc = ensure(c, c->sa_pu, sa * 4)))) return rc;
     if ((rc = ensure(c, c->js_p, js * 4)) || (rc = ensure(c, c->js_pu, js * 4)) || (rc = ensure(c, c->js_bin, js * 4)))
         return rc;
     if (sq > 0 && ((rc = ensure(c, c->ms_iu, ms * 4)) || (rc = ensure(c, c->ss_i, ss * 4)) ||
@@ -919,6 +982,8 @@ static Buffers buffers_of(pv3d_ctx* c)
     B.sq_p = (float*)c->sq_p.p;
     B.sq_pu = (float*)c->sq_pu.p;
     B.js_p = (float*)c->js_p.p;
+    B.sa_p = (float*)c->sa_p.p;
+    B.sa_pu = (float*)c->sa_pu.p;
     B.js_pu = (float*)c->js_pu.p;
     B.js_bin = (int32_t*)c->js_bin.p;
     B.cs_cnt = (uint32_t*)c->cs_cnt.p;
@@ -1089,8 +1154,8 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
     // copied back from a device staging area at the end
     const bool dev = out->is_device != 0;
     size_t off_e = 0, off_eu = 0, off_cl = 0, off_p = 0, off_pu = 0, off_cnt = 0, off_bits = 0, tot = 0;
-    size_t off_se = 0, off_seu = 0, off_sp = 0, off_spu = 0;
-    const int32_t NS = (int32_t)g.str_ids.size();
+    size_t off_se = 0, off_seu = 0, off_sp = 0, off_spu = 0, off_ae = 0, off_aeu = 0, off_ap = 0, off_apu = 0;
+    const int32_t NS = (int32_t)g.str_ids.size(), NA = (int32_t)g.arr_ids.size();
     auto take = [&](size_t bytes) {
         size_t o_ = tot;
         tot += (bytes + 255) & ~size_t(255);
@@ -1108,6 +1173,10 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
         if (out->string_energy_unshaded) off_seu = take((size_t)NS * 8);
         if (out->string_power) off_sp = take((size_t)S * NS * 4);
         if (out->string_power_unshaded) off_spu = take((size_t)S * NS * 4);
+        if (out->array_energy) off_ae = take((size_t)NA * 8);
+        if (out->array_energy_unshaded) off_aeu = take((size_t)NA * 8);
+        if (out->array_power) off_ap = take((size_t)S * NA * 4);
+        if (out->array_power_unshaded) off_apu = take((size_t)S * NA * 4);
         if ((rc = ensure(c, c->staging, tot))) return rc;
     }
     char* sb = (char*)c->staging.p;
@@ -1123,11 +1192,16 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
     double* d_seu = dev ? out->string_energy_unshaded : (out->string_energy_unshaded ? (double*)(sb + off_seu) : nullptr);
     float* d_sp = dev ? out->string_power : (out->string_power ? (float*)(sb + off_sp) : nullptr);
     float* d_spu = dev ? out->string_power_unshaded : (out->string_power_unshaded ? (float*)(sb + off_spu) : nullptr);
+    double* d_ae = dev ? out->array_energy : (out->array_energy ? (double*)(sb + off_ae) : nullptr);
+    double* d_aeu = dev ? out->array_energy_unshaded : (out->array_energy_unshaded ? (double*)(sb + off_aeu) : nullptr);
+    float* d_ap = dev ? out->array_power : (out->array_power ? (float*)(sb + off_ap) : nullptr);
+    float* d_apu = dev ? out->array_power_unshaded : (out->array_power_unshaded ? (float*)(sb + off_apu) : nullptr);
 
     const int64_t n_bins = es.heat ? (int64_t)out->heat_az_bins * out->heat_zen_bins : 0;
     if ((rc = ensure(c, c->kahan_mod, (size_t)g.M * 2 * sizeof(float2))) ||
         (rc = ensure(c, c->kahan_cell, (size_t)g.C * sizeof(float2))) ||
         (es.strings && (rc = ensure(c, c->kahan_str, (size_t)NS * 2 * sizeof(float2)))) ||
+        (es.arrays && (rc = ensure(c, c->kahan_arr, (size_t)NA * 2 * sizeof(float2)))) ||
         (es.heat && (rc = ensure(c, c->heat, (size_t)n_bins * 20))))
         return rc;
     double* h_e = es.heat ? (double*)c->heat.p : nullptr;
@@ -1142,19 +1216,21 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
         jobs.push_back(make_job(c, g, s, es, s0, k, (float2*)c->kahan_mod.p, d_cl ? (float2*)c->kahan_cell.p : nullptr,
                                 d_p, d_pu,
                                 d_cnt, d_bits, (float2*)c->kahan_str.p, d_sp, d_spu, h_e, h_eu, h_n,
-                                es.heat ? out->heat_az_bins : 0, es.heat ? out->heat_zen_bins : 0));
+                                es.heat ? out->heat_az_bins : 0, es.heat ? out->heat_zen_bins : 0,
+                                (float2*)c->kahan_arr.p, d_ap, d_apu));
         waves.push_back(pack_wave(jobs, jobs.size() - 1, jobs.size(), tile_sh, u24, es.fused, es.count));
     }
-    int64_t mjs = 0, mte = 0, mms = 0, mcs = 0, mss = 0, msq = 0;
+    int64_t mjs = 0, mte = 0, mms = 0, mcs = 0, mss = 0, msq = 0, msa = 0;
     for (auto& W : waves) {
         mjs = std::max(mjs, W.tot_js); mte = std::max(mte, W.tot_te);
         mms = std::max(mms, W.tot_ms); mcs = std::max(mcs, W.tot_cs);
-        mss = std::max(mss, W.tot_ss); msq = std::max(msq, W.tot_sq);
+        mss = std::max(mss, W.tot_ss); msq = std::max(msq, W.tot_sq); msa = std::max(msa, W.tot_sa);
     }
-    const int extras = (es.strings ? 1 : 0) | (es.heat ? 2 : 0);
+    const int extras = (es.strings ? 1 : 0) | (es.heat ? 2 : 0) | (es.arrays ? 4 : 0);
     Counters hc{};
     for (int attempt = 0; attempt < 4; ++attempt) {
-        if ((rc = ensure_workspace(c, mjs, mte, mms, mcs, es.tile, es.fused, d_bits != nullptr, mss, msq))) return rc;
+        if ((rc = ensure_workspace(c, mjs, mte, mms, mcs, es.tile, es.fused, d_bits != nullptr, mss, msq, msa)))
+            return rc;
         for (auto& W : waves) {
             W.bin_cap = c->bin_cap;
             W.map_cap_tiles = c->map_cap_tiles;
@@ -1166,6 +1242,7 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
         CUDA_TRY(c, cudaMemsetAsync(c->kahan_mod.p, 0, (size_t)g.M * 2 * sizeof(float2), st));
         CUDA_TRY(c, cudaMemsetAsync(c->kahan_cell.p, 0, (size_t)g.C * sizeof(float2), st));
         if (es.strings) CUDA_TRY(c, cudaMemsetAsync(c->kahan_str.p, 0, (size_t)NS * 2 * sizeof(float2), st));
+        if (es.arrays) CUDA_TRY(c, cudaMemsetAsync(c->kahan_arr.p, 0, (size_t)NA * 2 * sizeof(float2), st));
         if (es.heat) CUDA_TRY(c, cudaMemsetAsync(c->heat.p, 0, (size_t)n_bins * 20, st));
         CUDA_TRY(c, cudaEventRecord(c->ev0, st));
         if ((rc = run_waves(c, waves, st, es.tile, es.fused, es.profile, es.count, extras))) return rc;
@@ -1174,6 +1251,8 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
                                           d_e, d_eu, d_cl, st));
         if (es.strings)
             CUDA_TRY(c, launch_finalize_pairs((const float2*)c->kahan_str.p, NS, nullptr, 0, d_se, d_seu, nullptr, st));
+        if (es.arrays)
+            CUDA_TRY(c, launch_finalize_pairs((const float2*)c->kahan_arr.p, NA, nullptr, 0, d_ae, d_aeu, nullptr, st));
         if (es.heat) {
             const cudaMemcpyKind kind = dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
             CUDA_TRY(c, cudaMemcpyAsync(out->heat_energy, h_e, (size_t)n_bins * 8, kind, st));
@@ -1209,6 +1288,12 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
             CUDA_TRY(c, cudaMemcpy(out->string_power, d_sp, (size_t)S * NS * 4, cudaMemcpyDeviceToHost));
         if (out->string_power_unshaded)
             CUDA_TRY(c, cudaMemcpy(out->string_power_unshaded, d_spu, (size_t)S * NS * 4, cudaMemcpyDeviceToHost));
+        if (out->array_energy) CUDA_TRY(c, cudaMemcpy(out->array_energy, d_ae, (size_t)NA * 8, cudaMemcpyDeviceToHost));
+        if (out->array_energy_unshaded)
+            CUDA_TRY(c, cudaMemcpy(out->array_energy_unshaded, d_aeu, (size_t)NA * 8, cudaMemcpyDeviceToHost));
+        if (out->array_power) CUDA_TRY(c, cudaMemcpy(out->array_power, d_ap, (size_t)S * NA * 4, cudaMemcpyDeviceToHost));
+        if (out->array_power_unshaded)
+            CUDA_TRY(c, cudaMemcpy(out->array_power_unshaded, d_apu, (size_t)S * NA * 4, cudaMemcpyDeviceToHost));
     }
     int64_t lit = 0;
     for (int64_t k = es.b; k < es.e; ++k) lit += g.lit[k];
@@ -1219,8 +1304,8 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
     out->nonempty_tiles = (int64_t)hc.stat_nonempty;
     out->binned_tris = (int64_t)hc.stat_bins;
     out->kernel_launches = (int64_t)waves.size() * ((es.fused ? kLaunchesPerWave : kLaunchesPerWaveMap) +
-                                                    (es.strings ? 1 : 0) + (es.heat ? 2 : 0)) +
-                           1 + (es.strings ? 1 : 0);
+                                                    (es.strings ? 1 : 0) + (es.heat ? 2 : 0) + (es.arrays ? 1 : 0)) +
+                           1 + (es.strings ? 1 : 0) + (es.arrays ? 1 : 0);
     if (es.profile || es.count) {
         pv3d_profile& P = c->last_prof;
         P = pv3d_profile{};
@@ -1651,7 +1736,7 @@ extern "C" int pv3d_submit(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o
     int rc = check_eval(c, g, o, out, r->es);
     if (rc) return rc;
     if (o && o->path == PV3D_PATH_MAP) return fail(c, PV3D_E_INVALID, "served requests use the fused path");
-    if (r->es.strings || r->es.heat)
+    if (r->es.strings || r->es.heat || r->es.arrays)
         return fail(c, PV3D_E_INVALID, "string and sky-map outputs are produced by pv3d_evaluate only");
     r->gen_id = gen_id;
     r->opts = o ? *o : pv3d_eval_opts{};
@@ -1773,7 +1858,7 @@ extern "C" void pv3d_destroy(pv3d_ctx* c)
     release_buf(c->wave_slot);
     release_buf(c->jobs_slot);
     DevBuf* bufs[] = {&c->lp, &c->win, &c->ms, &c->ms_p, &c->ms_pu, &c->ms_beam, &c->ms_iu, &c->ss_i, &c->sq_p,
-                      &c->sq_pu, &c->kahan_str, &c->js_p, &c->js_pu, &c->js_bin, &c->heat, &c->cs_cnt, &c->cs_bits, &c->t_far,
+                      &c->sq_pu, &c->kahan_str, &c->js_p, &c->js_pu, &c->js_bin, &c->heat, &c->sa_p, &c->sa_pu, &c->kahan_arr, &c->cs_cnt, &c->cs_bits, &c->t_far,
                       &c->t_cnt, &c->t_off, &c->t_cur, &c->t_slot, &c->t_rcnt, &c->t_roff, &c->t_rcur, &c->nonempty, &c->heavy,
                       &c->bins, &c->pairs, &c->recv, &c->map, &c->big,
                       &c->block_sums, &c->ctr, &c->waves, &c->jobs, &c->kahan_mod, &c->kahan_cell, &c->staging};

@@ -2280,6 +2280,96 @@ __global__ void __launch_bounds__(256) k_string(const WaveDev* __restrict__ W, c
 }
 
 // ---------------------------------------------------------------------------
+// k_array: strings in parallel at one inverter input -- one voltage V across
+// every string of the array; string s delivers the largest of its substring
+// currents I_k whose string voltage V_s(I_k) = sum_{j: I_j >= I_k} V_j -
+// v_diode #{j: I_j < I_k} still reaches V, and P(V) = V sum_s I_s(V) is
+// linear between those voltages, so the array's maximum power point is the
+// best of them.  One warp per (step, array): the array's substrings (current,
+// string voltage at that current) staged in shared memory, then lanes over
+// the candidate voltages.
+// ---------------------------------------------------------------------------
+constexpr int kArrayWarps = 4;
+
+__global__ void __launch_bounds__(kArrayWarps * 32) k_array(const WaveDev* __restrict__ W,
+                                                           const JobDev* __restrict__ jobs, Buffers B)
+{
+    __shared__ float s_i[kArrayWarps][kMaxArraySub], s_w[kArrayWarps][kMaxArraySub];
+    __shared__ float s_iu[kArrayWarps][kMaxArraySub], s_wu[kArrayWarps][kMaxArraySub];
+    __shared__ int s_str[kArrayWarps][kMaxArraySub];  // string of each staged substring (position in the array)
+    const int64_t tot = W->tot_sa;
+    const int nj = W->n_jobs;
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    const int64_t n_warps = (int64_t)gridDim.x * kArrayWarps;
+    for (int64_t item = (int64_t)blockIdx.x * kArrayWarps + wib; item < tot; item += n_warps) {
+        const int j = job_of(nj, item, [&](int q) { return jobs[q].sa_base; });
+        const JobDev& J = jobs[j];
+        const int64_t li = item - J.sa_base;
+        const int ls = (int)(li / J.n_arr), a = (int)(li - (int64_t)ls * J.n_arr);
+        const LightParams& lp = B.lp[J.js_base + ls];
+        float best = 0.f, best_u = 0.f;
+        if (lp.valid) {
+            const float* ik = B.ss_i + J.ss_base + (int64_t)ls * J.n_sub_tot;
+            const float* iu = B.ms_iu + J.ms_base + (int64_t)ls * J.n_mods;
+            // stage the array's substrings string by string, with each one's string voltage
+            int n = 0;
+            for (int t = J.arr_off[a]; t < J.arr_off[a + 1]; ++t) {
+                const int q = J.arr_strs[t];
+                const int k0 = J.str_sub[q], k1 = J.str_sub[q + 1];
+                for (int c = k0 + lane; c < k1; c += 32) {
+                    const float cur = ik[c], cur_u = iu[J.sub_mod[c]];
+                    float volt = 0.f, volt_u = 0.f;
+                    for (int k = k0; k < k1; ++k) {
+                        const float vk = J.sub_nk[k] * J.v_cell;
+                        volt += ik[k] >= cur ? vk : -J.v_diode;
+                        volt_u += iu[J.sub_mod[k]] >= cur_u ? vk : -J.v_diode;
+                    }
+                    const int pos = n + (c - k0);
+                    if (pos < kMaxArraySub) {
+                        s_i[wib][pos] = cur; s_w[wib][pos] = volt;
+                        s_iu[wib][pos] = cur_u; s_wu[wib][pos] = volt_u;
+                        s_str[wib][pos] = t;
+                    }
+                }
+                n += k1 - k0;
+            }
+            n = min(n, kMaxArraySub);
+            __syncwarp();
+            for (int c = lane; c < n; c += 32) {
+                const float V = s_w[wib][c], Vu = s_wu[wib][c];
+                float cur = 0.f, cur_u = 0.f, is = 0.f, isu = 0.f;
+                int prev = s_str[wib][0];
+                for (int k = 0; k < n; ++k) {
+                    if (s_str[wib][k] != prev) {  // next string: add the last one's current
+                        cur += is; cur_u += isu;
+                        is = 0.f; isu = 0.f;
+                        prev = s_str[wib][k];
+                    }
+                    if (s_w[wib][k] >= V && s_i[wib][k] > is) is = s_i[wib][k];
+                    if (s_wu[wib][k] >= Vu && s_iu[wib][k] > isu) isu = s_iu[wib][k];
+                }
+                cur += is; cur_u += isu;
+                if (V > 0.f) best = fmaxf(best, V * cur);
+                if (Vu > 0.f) best_u = fmaxf(best_u, Vu * cur_u);
+            }
+#pragma unroll
+            for (int off = 16; off; off >>= 1) {
+                best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, off));
+                best_u = fmaxf(best_u, __shfl_xor_sync(0xffffffffu, best_u, off));
+            }
+            __syncwarp();
+        }
+        if (lane == 0) {
+            B.sa_p[item] = best;
+            B.sa_pu[item] = best_u;
+            const int64_t row = (int64_t)(J.out_row0 + ls);
+            if (J.out_arr_power) J.out_arr_power[row * J.n_arr + a] = best;
+            if (J.out_arr_power_u) J.out_arr_power_u[row * J.n_arr + a] = best_u;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // sky map of the effective shading (Fig. 6: the shading factor over the sun's
 // azimuth and zenith): k_gen_step sums the generator's power per step and
 // bins the step's sun; k_heat adds each bin's steps in step order (FP64)
@@ -2381,14 +2471,16 @@ __global__ void __launch_bounds__(256) k_epilogue(const WaveDev* __restrict__ W,
         // cell items only when the per-cell beam loss is wanted
         const int C = J.kahan_cell ? J.n_cells : 0, Mn = J.n_mods;
         const float inv_nn = 1.f / J.nn;
-        // kind 0: cell c; 1: module m; 2: string q
-        const int kind = li < C ? 0 : (li < C + Mn ? 1 : 2);
-        const int idx = kind == 0 ? (int)li : (kind == 1 ? (int)(li - C) : (int)(li - C - Mn));
+        // kind 0: cell c; 1: module m; 2: string q; 3: array
+        const int kind = li < C ? 0 : (li < C + Mn ? 1 : (li < C + Mn + J.n_str ? 2 : 3));
+        const int idx = kind == 0 ? (int)li
+                                  : (kind == 1 ? (int)(li - C) : (kind == 2 ? (int)(li - C - Mn) : (int)(li - C - Mn - J.n_str)));
         const int m_cell = kind == 0 ? J.cell_mod[idx] : 0;
         float2 a, au = make_float2(0.f, 0.f);
         if (kind == 0) a = J.kahan_cell[idx];
         else if (kind == 1) { a = J.kahan_mod[2 * idx]; au = J.kahan_mod[2 * idx + 1]; }
-        else { a = J.kahan_str[2 * idx]; au = J.kahan_str[2 * idx + 1]; }
+        else if (kind == 2) { a = J.kahan_str[2 * idx]; au = J.kahan_str[2 * idx + 1]; }
+        else { a = J.kahan_arr[2 * idx]; au = J.kahan_arr[2 * idx + 1]; }
         for (int l0 = 0; l0 < J.k; l0 += 32) {
             const int ls = l0 + lane;
             float x = 0.f, xu = 0.f;
@@ -2409,10 +2501,14 @@ __global__ void __launch_bounds__(256) k_epilogue(const WaveDev* __restrict__ W,
                     if (J.out_power_u) J.out_power_u[(int64_t)(J.out_row0 + ls) * Mn + idx] = pu;
                     x = p * lp.dt;
                     xu = pu * lp.dt;
-                } else if (v) {
+                } else if (v && kind == 2) {
                     const int64_t sq = J.sq_base + (int64_t)ls * J.n_str + idx;
                     x = B.sq_p[sq] * lp.dt;
                     xu = B.sq_pu[sq] * lp.dt;
+                } else if (v) {
+                    const int64_t sa = J.sa_base + (int64_t)ls * J.n_arr + idx;
+                    x = B.sa_p[sa] * lp.dt;
+                    xu = B.sa_pu[sa] * lp.dt;
                 }
             }
             const unsigned int vm = __ballot_sync(0xffffffffu, v);
@@ -2428,7 +2524,8 @@ __global__ void __launch_bounds__(256) k_epilogue(const WaveDev* __restrict__ W,
         if (lane == 0) {
             if (kind == 0) J.kahan_cell[idx] = a;
             else if (kind == 1) { J.kahan_mod[2 * idx] = a; J.kahan_mod[2 * idx + 1] = au; }
-            else { J.kahan_str[2 * idx] = a; J.kahan_str[2 * idx + 1] = au; }
+            else if (kind == 2) { J.kahan_str[2 * idx] = a; J.kahan_str[2 * idx + 1] = au; }
+            else { J.kahan_arr[2 * idx] = a; J.kahan_arr[2 * idx + 1] = au; }
         }
     }
 }
@@ -2615,6 +2712,7 @@ cudaError_t launch_wave(const WaveDev* d_wave, const JobDev* d_jobs, const Buffe
     if (cfg.fused) k_pv<<<sm * 32, kPvThreads, 0, st>>>(W, d_jobs, b);
     else k_sample<<<sm * 16, kPvThreads, 0, st>>>(W, d_jobs, b);
     if (cfg.extras & 1) k_string<<<sm * 4, 256, 0, st>>>(W, d_jobs, b);
+    if (cfg.extras & 4) k_array<<<sm * 4, kArrayWarps * 32, 0, st>>>(W, d_jobs, b);
     if (cfg.extras & 2) {
         k_gen_step<<<sm * 4, 256, 0, st>>>(W, d_jobs, b);
         k_heat<<<sm * 2, 256, 0, st>>>(W, d_jobs, b);

@@ -127,6 +127,16 @@ struct JobDev {
     double* heat_eu;          // [bins]  same without shading
     int32_t* heat_n;          // [bins]  steps
     const float* fdiff;       // [C] diffuse shading fraction per cell (pv3d_sky_view), or nullptr
+    // strings in parallel (array outputs requested; n_arr = 0 otherwise):
+    // array a holds strings arr_strs[arr_off[a] .. arr_off[a + 1])
+    int32_t n_arr;
+    int32_t pad_arr;
+    const int32_t* arr_off;   // [n_arr + 1]
+    const int32_t* arr_strs;  // [n_str]
+    int64_t sa_base;          // (step, array) entries
+    float2* kahan_arr;        // [n_arr][2]
+    float* out_arr_power;     // [rows][n_arr]
+    float* out_arr_power_u;
 };
 
 struct WaveDev {
@@ -140,6 +150,7 @@ struct WaveDev {
     int64_t tot_win, tot_mod, tot_tri, tot_epi;  // tot_tri: (meshlet, step) warp items
     int64_t tot_ss, tot_sq;                      // (step, substring) and (step, string) entries
     int64_t tot_heat;                            // heat-map bins over the jobs
+    int64_t tot_sa;                              // (step, array) entries
     int64_t bin_cap, map_cap_tiles, big_cap, recv_cap;
 };
 
@@ -188,6 +199,8 @@ struct Buffers {
     float* ss_i;             // [tot_ss]  substring current limit per (step, substring) (string model)
     float* sq_p;             // [tot_sq]  string MPP power per (step, string)
     float* sq_pu;            // [tot_sq]  same without shading
+    float* sa_p;             // [tot_sa]  array MPP power per (step, array)
+    float* sa_pu;            // [tot_sa]
     float* js_p;             // [tot_js]  the generator's P_mpp per step (heat map)
     float* js_pu;            // [tot_js]
     int32_t* js_bin;         // [tot_js]  sky bin of the step's sun, -1 below the horizon
@@ -220,12 +233,13 @@ struct LaunchCfg {
     int profile;  // counting kernels
     cudaStream_t stream;
     cudaEvent_t* ev;  // NULL, or kStages + 1 events recorded at the stage boundaries of the wave
-    int extras;       // bit 0: series strings (k_string); bit 1: sky map (k_gen_step, k_heat)
+    int extras;       // bit 0: series strings (k_string); bit 1: sky map (k_gen_step, k_heat); bit 2: arrays (k_array)
 };
 
 constexpr int kStages = 6;  // setup, bin, tile (warp per tile / map raster), heavy tiles, pv/sample, epilogue
 constexpr int kLaunchesPerWave = 15;     // kernels launch_wave starts (fused path), plus 1 with
-constexpr int kLaunchesPerWaveMap = 14;  // strings and 2 with the sky map; (map path)
+constexpr int kLaunchesPerWaveMap = 14;  // strings, 2 with the sky map, 1 with arrays; (map path)
+constexpr int kMaxArraySub = 512;        // bypass substrings an array of parallel strings may hold
 
 cudaError_t launch_wave(const WaveDev* d_wave, const JobDev* d_jobs, const Buffers& b,
                         const LaunchCfg& cfg, int64_t tot_te_host);

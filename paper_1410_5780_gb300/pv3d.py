@@ -36,7 +36,7 @@ PV3D_PATH_MAP = 1
 EXPORTED = ("pv3d_create", "pv3d_destroy", "pv3d_last_error", "pv3d_scene_load", "pv3d_generator_define",
             "pv3d_set_poses", "pv3d_set_sun", "pv3d_evaluate", "pv3d_submit", "pv3d_poll", "pv3d_release",
             "pv3d_last_profile", "pv3d_module_shade_noalloc", "pv3d_evaluate_batch", "pv3d_generator_strings",
-            "pv3d_set_sun_clear_sky", "pv3d_sun_table", "pv3d_sky_view")
+            "pv3d_set_sun_clear_sky", "pv3d_sun_table", "pv3d_sky_view", "pv3d_generator_arrays")
 
 
 class pv3d_opts(C.Structure):
@@ -49,7 +49,7 @@ class pv3d_opts(C.Structure):
 class pv3d_module(C.Structure):
     _fields_ = [("origin", C.c_float * 3), ("u", C.c_float * 3), ("v", C.c_float * 3), ("pitch", C.c_float),
                 ("cells_u", C.c_int32), ("cells_v", C.c_int32), ("layout", C.c_int32), ("tracker", C.c_int32),
-                ("string_id", C.c_int32), ("reserved", C.c_int32)]
+                ("string_id", C.c_int32), ("array_id", C.c_int32)]
 
 
 class pv3d_layout(C.Structure):
@@ -91,7 +91,9 @@ class pv3d_result(C.Structure):
                 ("reserved1", C.c_int32), ("string_energy", C.c_void_p), ("string_energy_unshaded", C.c_void_p),
                 ("string_power", C.c_void_p), ("string_power_unshaded", C.c_void_p),
                 ("heat_az_bins", C.c_int32), ("heat_zen_bins", C.c_int32), ("heat_energy", C.c_void_p),
-                ("heat_energy_unshaded", C.c_void_p), ("heat_steps", C.c_void_p)]
+                ("heat_energy_unshaded", C.c_void_p), ("heat_steps", C.c_void_p),
+                ("array_energy", C.c_void_p), ("array_energy_unshaded", C.c_void_p), ("array_power", C.c_void_p),
+                ("array_power_unshaded", C.c_void_p)]
 
 
 class pv3d_sky_view_opts(C.Structure):
@@ -144,6 +146,7 @@ def load(build_if_missing: bool = False):
         lib.pv3d_release.argtypes = [P, C.c_uint32]
         lib.pv3d_last_profile.argtypes = [P, C.POINTER(pv3d_profile)]
         lib.pv3d_generator_strings.argtypes = [P, C.c_uint32, C.POINTER(C.c_int32), P]
+        lib.pv3d_generator_arrays.argtypes = [P, C.c_uint32, C.POINTER(C.c_int32), P]
         lib.pv3d_set_sun_clear_sky.argtypes = [P, C.c_uint32, C.POINTER(pv3d_sky_opts), C.POINTER(C.c_int64)]
         lib.pv3d_sun_table.argtypes = [P, C.c_uint32, P, P, P, P, C.c_int64]
         lib.pv3d_sky_view.argtypes = [P, C.c_uint32, C.POINTER(pv3d_sky_view_opts), P]
@@ -231,6 +234,7 @@ class Context:
             md.pitch = float(gen.pitch[i])
             md.cells_u = int(gen.cells_u[i]); md.cells_v = int(gen.cells_v[i])
             md.layout = int(gen.layout[i]); md.tracker = int(gen.tracker[i]); md.string_id = int(gen.string[i])
+            md.array_id = 0 if getattr(gen, "array", None) is None else int(gen.array[i])
         subs = [np.ascontiguousarray(l.cell_sub, np.int32) for l in gen.layouts]
         lays = (pv3d_layout * len(subs))()
         for i, (l, s) in enumerate(zip(gen.layouts, subs)):
@@ -244,8 +248,18 @@ class Context:
         self._check(self.lib.pv3d_generator_define(self.h, scene_id, mods, m, lays, len(subs), trk, piv.shape[0],
                                                    C.byref(gid)))
         cells = int((np.asarray(gen.cells_u, np.int64) * np.asarray(gen.cells_v, np.int64)).sum())
-        self._gens[gid.value] = {"modules": m, "cells": cells, "steps": 0, "strings": len(self.string_ids(gid.value))}
+        self._gens[gid.value] = {"modules": m, "cells": cells, "steps": 0, "strings": len(self.string_ids(gid.value)),
+                                 "arrays": len(self.array_ids(gid.value))}
         return gid.value
+
+    def array_ids(self, gen_id: int) -> np.ndarray:
+        """pv3d_generator_arrays: the generator's distinct array ids, ascending
+        (the order of the array outputs)."""
+        n = C.c_int32()
+        self._check(self.lib.pv3d_generator_arrays(self.h, gen_id, C.byref(n), None))
+        ids = np.zeros(n.value, np.int32)
+        self._check(self.lib.pv3d_generator_arrays(self.h, gen_id, C.byref(n), _p(ids)))
+        return ids
 
     def string_ids(self, gen_id: int) -> np.ndarray:
         """pv3d_generator_strings: the generator's distinct string ids, ascending
@@ -308,13 +322,15 @@ class Context:
         if gen_id not in self._gens:  # let the library report the unknown id
             return pv3d_result(is_device=1 if device else 0), {}
         g = self._gens[gen_id]
-        m, cells, n_steps, ns = g["modules"], g["cells"], g["steps"], g["strings"]
+        m, cells, n_steps, ns, na = g["modules"], g["cells"], g["steps"], g["strings"], g["arrays"]
         S = (step_end or n_steps) - step_begin
         shapes = dict(energy=((m,), "f8"), energy_unshaded=((m,), "f8"), power=((S, m), "f4"),
                       power_unshaded=((S, m), "f4"), cell_beam_loss=((cells,), "f8"),
                       cell_counts=((S, cells), "u1"), sample_bits=((S, cells), "u8"),
                       string_energy=((ns,), "f8"), string_energy_unshaded=((ns,), "f8"),
-                      string_power=((S, ns), "f4"), string_power_unshaded=((S, ns), "f4"))
+                      string_power=((S, ns), "f4"), string_power_unshaded=((S, ns), "f4"),
+                      array_energy=((na,), "f8"), array_energy_unshaded=((na,), "f8"),
+                      array_power=((S, na), "f4"), array_power_unshaded=((S, na), "f4"))
         if heat_bins:
             n_az, n_zen = heat_bins
             shapes.update(heat_energy=((n_zen, n_az), "f8"), heat_energy_unshaded=((n_zen, n_az), "f8"),

@@ -95,3 +95,39 @@ def test_string_outputs_on_map_path_and_host(ctx):
     with pytest.raises(pv3d.PV3DError):  # served requests do not produce string outputs
         ctx.submit(gid, n=w.n, map_res=w.map_res, outputs=("string_energy",))
     ctx.release(gid)
+
+
+def test_parallel_strings(ctx):
+    """Arrays of strings in parallel (one voltage per inverter input): per step
+    the GPU's array power from its own counts equals the oracle's parallel
+    model; one string per array is the string model; the array never beats
+    its strings' own maxima; energies are the Kahan sums."""
+    w = workloads()[0]
+    w.gen.array = (w.gen.string // 14).astype(np.int32) * 5   # strings of 4 modules, arrays of two strings
+    gid = pv3d.load_workload(ctx, w)
+    np.testing.assert_array_equal(ctx.array_ids(gid), np.unique(w.gen.array))
+    outs = OUTS + ("array_power", "array_power_unshaded", "array_energy", "array_energy_unshaded")
+    g = run_gpu(ctx, gid, w, outputs=outs, chunk_steps=7)
+    steps = np.arange(w.sun.n_steps)
+    ap, apu = oracle.array_power_from_counts(w, steps, g["cell_counts"].astype(np.int32))
+    for got, ref in ((g["array_power"], ap), (g["array_power_unshaded"], apu)):
+        assert np.all(np.abs(got - ref) <= 1e-4 * np.maximum(np.abs(ref), 1.0) + 1e-3), np.abs(got - ref).max()
+    _, str_array = oracle.array_index(w.gen)
+    sp = np.zeros_like(g["array_power"])
+    np.add.at(sp.T, str_array, g["string_power"].T)
+    assert np.all(g["array_power"] <= sp + 1e-3 + 1e-5 * sp)
+    dt = w.sun.dt_h.astype(np.float64)[:, None]
+    lit = (w.sun.xyz[:, 2] > 0)[:, None]
+    e64 = (g["array_power"].astype(np.float64) * dt * lit).sum(0)
+    assert np.all(np.abs(g["array_energy"] - e64) <= 1e-6 * np.maximum(e64, 1.0))
+    ctx.release(gid)
+    w.gen.array = w.gen.string.copy()   # one string per array
+    gid = pv3d.load_workload(ctx, w)
+    g = run_gpu(ctx, gid, w, outputs=outs)
+    np.testing.assert_allclose(g["array_power"], g["string_power"], rtol=1e-6, atol=1e-4)
+    bad = w.gen.string.copy()
+    bad_arr = np.arange(w.gen.n_modules, dtype=np.int32)   # modules of one string in different arrays
+    w.gen.array = bad_arr
+    with pytest.raises(pv3d.PV3DError):
+        pv3d.load_workload(ctx, w)
+    ctx.release(gid)

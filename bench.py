@@ -160,6 +160,21 @@ def oracle_sample_run(w, budget_s: float, chunk: int = 12, stride: int = 9):
         f"{t_tot:.1f} s", t_tot
 
 
+def reduce_over_ranks(t_ms: float, tests: float, dist, device: str):
+    """Whole-job timing of independent replicas: the slowest rank's time
+    (every rank ran its own problem between the same barriers) and the tests
+    of all ranks.  Without a process group, the local values."""
+    if dist is None:
+        return float(t_ms), float(tests)
+    import torch
+    dist.barrier()
+    t = torch.tensor([float(t_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    n = torch.tensor([float(tests)], dtype=torch.float64, device=device)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(n.item())
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -420,16 +435,7 @@ def run_ours(args, rank, world, dist):
     torch.cuda.nvtx.range_pop()
     clocks = sampler.stop()
     t_ms = sum(a.elapsed_time(b) for a, b in ev)
-    if dist is not None:
-        dist.barrier()
-        t = torch.tensor([t_ms], dtype=torch.float64, device=f"cuda:{dev}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_ms = float(t.item())
-        n = torch.tensor([float(tests)], dtype=torch.float64, device=f"cuda:{dev}")
-        dist.all_reduce(n, op=dist.ReduceOp.SUM)
-        tests_all = float(n.item())
-    else:
-        tests_all = float(tests)
+    t_ms, tests_all = reduce_over_ranks(t_ms, tests, dist, f"cuda:{dev}")
     value = tests_all / (t_ms * 1e-3)
 
     # work counters of one evaluation (untimed), for the roofline numerator

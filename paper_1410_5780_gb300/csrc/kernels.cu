@@ -15,20 +15,28 @@
 //   k_bin_big     same for triangles that span many tiles, one warp each
 //   k_scan_*      bin offsets, the list of non-empty tiles, receiver offsets
 //   k_scatter, k_recv_fill   write the bins and receiver lists
-//   k_raster_test one CTA per non-empty tile: shared-memory depth tile filled
-//                 at the texels the tile's samples read (texel-centre coverage,
-//                 atomicMin of order-preserving depth keys -- Fig. 3: the depth
-//                 buffer keeps the surface nearest the sun), then the depth test
-//                 of those samples and warp-aggregated cell tallies
+//   k_tile_warp   one warp per non-empty tile: the depth test of every sample
+//                 that reads the tile against the tile's kept triangles (those
+//                 in front of its receivers' planes), sub-block masks, one atomic
+//                 per sample row for the cell tallies -- the same decision as a
+//                 test against the tile's stored nearest depth (Fig. 3: the
+//                 depth buffer keeps the surface nearest the sun)
+//   k_raster_test one CTA per tile that a warp cannot take (many receivers or
+//                 triangles): block-wide sample-driven test, or a shared-memory
+//                 depth tile (texel-centre coverage, atomicMin of
+//                 order-preserving depth keys) and the test of its samples
 //   k_pv          per (step, module): irradiance per cell, substring currents,
 //                 bypass-diode maximum power point (Section 2, step 4)
-//   k_string      series strings: one maximum power point per (step, string)
-//                 over the substring currents of its modules
+//   k_string, k_array   series strings and strings in parallel (when asked)
+//   k_gen_step, k_heat  sky map of the effective shading (when asked)
 //   k_epilogue    Kahan-compensated FP32 sums over the wave's steps in step
-//                 order, per module (energy), per cell (beam loss) and per string
-// The map path replaces k_raster_test + k_pv by k_raster_map (tiles stored to
-// an HBM shadow map with 16-byte stores) + k_sample (texel gathers, ballot
-// tallies, PV model).
+//                 order, per module, string and array (energy) and per cell
+//                 (beam loss, when asked)
+// The map path replaces the tile kernels + k_pv by k_raster_map (tiles stored
+// to an HBM shadow map with 16-byte stores) + k_sample (texel gathers, ballot
+// tallies, PV model).  Outside the waves: the clear-sky sun table and ideal
+// tracker poses (k_sun_table, k_gather_sun, k_ideal_poses) and the diffuse
+// sky view (k_sky_patches, then the waves over the patches, k_sky_fraction).
 #include <cfloat>
 #include <cstdint>
 

@@ -392,7 +392,7 @@ def run_ours(args, rank, world, dist):
     # timed trials, not part of the timed region); the map resolution is the
     # workload's own
     from paper_1410_5780_gb300 import autotune
-    tuned = autotune.autotune(w, device=dev, cache=None, n_windows=3)
+    tuned = autotune.autotune(w, device=dev, cache=None, n_windows=6)
     chunk = args.chunk or tuned["chunk_steps"]
     ctx = pv3d.Context(device=dev, map_res=w.map_res, chunk_steps=chunk, tile=tuned["tile"],
                        bin_capacity=tuned["bin_capacity"])

@@ -60,7 +60,7 @@ typedef struct pv3d_ctx pv3d_ctx;
 typedef struct pv3d_opts {
     int32_t device;           /* CUDA device ordinal [0] */
     int32_t map_res;          /* default shadow-map side R, power of two, 64..16384 [4096] */
-    int32_t tile;             /* rasteriser tile side: 32 or 64 texels [64] */
+    int32_t tile;             /* rasteriser tile side: 32, 64 or 128 texels [64] */
     int32_t chunk_steps;      /* sun steps processed per wave, 1..256 [128] */
     int32_t depth_format;     /* PV3D_DEPTH_F32 or PV3D_DEPTH_U24 [F32] */
     int32_t max_inflight;     /* served requests resident on the device at once, 1..256 [64] */

@@ -4,7 +4,7 @@ wave, initial bin-pool capacity and (optionally) shadow-map resolution.
 * Map resolution is an accuracy choice, not a speed one: when asked (``map_res=0``)
   it is the smallest power of two whose texel is at most half the sample
   spacing over the generator's extent, within [512, 8192].
-* Tile side (32 or 64 texels) and wave size K (32..256 sun steps) are chosen by
+* Tile side (32, 64 or 128 texels) and wave size K (32..256 sun steps) are chosen by
   timing short trial evaluations through the C ABI on step windows spread over
   the sun table; the fastest per-step device time wins.
 * The bin pool is pre-sized from the trials' largest per-wave demand, so the
@@ -25,7 +25,7 @@ import numpy as np
 from . import pv3d
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "pv3d", "autotune.json")
-TILES = (32, 64)
+TILES = (32, 64, 128)
 WAVES = (32, 64, 128, 256)
 
 

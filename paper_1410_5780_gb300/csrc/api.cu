@@ -230,7 +230,7 @@ extern "C" int pv3d_create(pv3d_ctx** out, const pv3d_opts* opts)
     if (o.wave_scratch_mb < 1) return PV3D_E_INVALID;
     if (o.bin_capacity < 0 || o.bin_capacity > (1ll << 32)) return PV3D_E_INVALID;
     if (o.bin_capacity > 0) c->bin_cap = o.bin_capacity;
-    if (o.tile != 32 && o.tile != 64) return PV3D_E_INVALID;
+    if (o.tile != 32 && o.tile != 64 && o.tile != 128) return PV3D_E_INVALID;
     if (o.map_res < 64 || o.map_res > 16384 || (o.map_res & (o.map_res - 1))) return PV3D_E_INVALID;
     if (o.chunk_steps < 1 || o.chunk_steps > 256) return PV3D_E_INVALID;
     if (o.depth_format != PV3D_DEPTH_F32 && o.depth_format != PV3D_DEPTH_U24) return PV3D_E_INVALID;
@@ -247,6 +247,7 @@ extern "C" int pv3d_create(pv3d_ctx** out, const pv3d_opts* opts)
     if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return PV3D_E_DEVICE;
     if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) return PV3D_E_DEVICE;
     if (cudaEventCreate(&c->ev0) != cudaSuccess || cudaEventCreate(&c->ev1) != cudaSuccess) return PV3D_E_DEVICE;
+    if (prepare_tile_kernels() != cudaSuccess) return PV3D_E_DEVICE;
     if (o.hbm_budget_bytes == 0) {
         size_t fr = 0, tot = 0;
         cudaMemGetInfo(&fr, &tot);
@@ -1147,7 +1148,7 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
     cudaSetDevice(c->device);
     cudaStream_t st = (o && o->stream) ? (cudaStream_t)o->stream : c->stream;
     const int64_t S = es.e - es.b;
-    const int tile_sh = es.tile == 32 ? 5 : 6;
+    const int tile_sh = es.tile == 32 ? 5 : (es.tile == 64 ? 6 : 7);
     const int u24 = c->opts.depth_format == PV3D_DEPTH_U24;
 
     // result staging: device outputs are written in place, host outputs are
@@ -1640,7 +1641,7 @@ static int serve_wave(pv3d_ctx* c, std::unique_lock<std::mutex>& lk)
     }
     c->rr = (c->rr + jobs.size()) % std::max<size_t>(na, 1);
     lk.unlock();
-    std::vector<WaveDev> waves{pack_wave(jobs, 0, jobs.size(), c->opts.tile == 32 ? 5 : 6,
+    std::vector<WaveDev> waves{pack_wave(jobs, 0, jobs.size(), c->opts.tile == 32 ? 5 : (c->opts.tile == 64 ? 6 : 7),
                                          c->opts.depth_format == PV3D_DEPTH_U24, 1, 0)};
     WaveDev& W = waves[0];
     Counters hc{};

@@ -915,8 +915,14 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_c(const WaveDev* __restri
 constexpr int kRecvChunk = 64;  // receivers staged in shared memory at a time (two per lane of one warp)
 constexpr int kTriBatch = 64;   // triangles set up in shared memory at a time by the rasteriser
 constexpr int kMaxTri = 256;    // triangles a block-wide tile may keep for the sample-driven test
-constexpr int kSubSide = 8;     // sub-blocks per tile side in the sample-driven test
-constexpr int kSubBlocks = kSubSide * kSubSide;
+// Sub-blocks per tile side in the sample-driven test (4, 8 and 16 texels on
+// 32-, 64- and 128-texel tiles; a 16 x 16 grid on 128-texel tiles tests fewer
+// triangles per sample but costs more in its masks than it saves).
+template <int TS>
+struct SubGrid {
+    static constexpr int side = 8;
+    static constexpr int blocks = side * side;
+};
 constexpr int kSubWords = kMaxTri / 32;
 static_assert(kRecvChunk == 64 && kTriBatch == 64, "prefix sums take two entries per lane of one warp");
 
@@ -993,9 +999,9 @@ struct KeptSm {
     TriS tri[NT];
     uint32_t box[NT];                       // texel box x0 | y0 << 8 | x1 << 16 | y1 << 24
     float dmin[NT];                         // nearest vertex depth
-    float dlim[kSubBlocks];                 // per sub-block: a triangle shades none of its samples
+    float dlim[SubGrid<TS>::blocks];        // per sub-block: a triangle shades none of its samples
                                             // unless its nearest depth is below this
-    uint32_t sbm[kSubBlocks][NT / 32];      // per sub-block: triangles that may shade one of its samples
+    uint32_t sbm[SubGrid<TS>::blocks][NT / 32];  // per sub-block: triangles that may shade one of its samples
     uint32_t seen[SEEN ? TS * TS / 32 : 1]; // work counting: texels whose fragments were counted
 };
 
@@ -1179,7 +1185,7 @@ template <int TS, bool PROF, typename F, typename G>
 __device__ __forceinline__ void for_tile_samples(const TileSm<TS>& sm, const JobDev& J, int tx, int ty,
                                                  unsigned int& cand, F f, G g)
 {
-    constexpr int SH = TS == 64 ? 6 : 5;
+    constexpr int SH = TS == 128 ? 7 : (TS == 64 ? 6 : 5);
     const int n = J.n, R_ = J.R;
     const float inv_n = 1.f / (float)n;
     for (int it = threadIdx.x; it < sm.total_items; it += blockDim.x) {
@@ -1275,6 +1281,7 @@ template <int TS>
 __device__ __forceinline__ void sub_limits(const RecvSm* recv, int n_recv, float* dlim, float q1, int q_begin,
                                            int q_stride)
 {
+    constexpr int kSubSide = SubGrid<TS>::side, kSubBlocks = SubGrid<TS>::blocks;
     constexpr int SW = TS / kSubSide;
     for (int sb = q_begin; sb < kSubBlocks; sb += q_stride) {
         const float x0 = (float)((sb % kSubSide) * SW), x1 = x0 + (float)SW;
@@ -1301,6 +1308,7 @@ template <int TS, int WORDS>
 __device__ __forceinline__ void sub_masks(const TriS* tri, const uint32_t* boxes, const float* dmin,
                                           const float* dlim, uint32_t (*sbm)[WORDS], int n, int q_begin, int q_stride)
 {
+    constexpr int kSubSide = SubGrid<TS>::side, kSubBlocks = SubGrid<TS>::blocks;
     constexpr int SW = TS / kSubSide;  // sub-block side, texels
     const int nw = (n + 31) >> 5;
     for (int q = q_begin; q < kSubBlocks * nw; q += q_stride) {
@@ -1352,6 +1360,7 @@ __device__ __forceinline__ bool sample_test(const TriS* tri, int n_kept, const u
                                             uint32_t* seen, int lx, int ly, float d, float bias,
                                             const LightParams& lp, int u24, unsigned int& pairs, unsigned int& frags)
 {
+    constexpr int kSubSide = SubGrid<TS>::side;
     const int sb = (ly / (TS / kSubSide)) * kSubSide + lx / (TS / kSubSide);
     const float px = (float)lx + 0.5f, py = (float)ly + 0.5f;
     const uint32_t* ms = sbm[sb];
@@ -1397,7 +1406,7 @@ __device__ __forceinline__ void test_items(const RecvSm* recv, int n_recv, int t
                                            int want_bits, unsigned int& cand, unsigned int& samples,
                                            unsigned int& pairs, unsigned int& frags)
 {
-    constexpr int SH = TS == 64 ? 6 : 5;
+    constexpr int SH = TS == 128 ? 7 : (TS == 64 ? 6 : 5);
     const int n = J.n, R_ = J.R;
     const float inv_n = 1.f / (float)n;
     for (int it = it_begin; it < total_items; it += it_stride) {
@@ -1442,7 +1451,7 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
                            int ty, int64_t te, uint64_t r0, int nrecv, unsigned int& visits, unsigned int& writes,
                            unsigned int& culled, unsigned int& cand, unsigned int& dense_n)
 {
-    constexpr int SH = TS == 64 ? 6 : 5;
+    constexpr int SH = TS == 128 ? 7 : (TS == 64 ? 6 : 5);
     constexpr int WPR = TS / 32;
     const int tid = threadIdx.x, bd = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, n_warps = bd >> 5;
@@ -1472,19 +1481,27 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
         }
         if (nrecv > kRecvChunk) stage_receivers<TS>(sm, J, B, ls, tx, ty, r0, kRecvChunk);
         if (tid < 32) {
-            // marked texels per row, prefixed (rows 2 * lane and 2 * lane + 1)
-            int c0 = 0, c1 = 0;
-            const int y0 = 2 * tid, y1 = y0 + 1;
-            if (y0 < TS)
+            // marked texels per row, prefixed (rows RPL * lane .. RPL * lane + RPL - 1)
+            constexpr int RPL = (TS + 31) / 32;
+            int c[RPL], sum = 0;
 #pragma unroll
-                for (int w = 0; w < WPR; ++w) c0 += __popc(sm.mask[y0 * WPR + w]);
-            if (y1 < TS)
+            for (int h = 0; h < RPL; ++h) {
+                const int y = RPL * tid + h;
+                c[h] = 0;
+                if (y < TS)
 #pragma unroll
-                for (int w = 0; w < WPR; ++w) c1 += __popc(sm.mask[y1 * WPR + w]);
-            const int tot = warp_excl_scan64(c0, c1);
-            if (y0 < TS) sm.row_start[y0] = c0;
-            if (y1 < TS) sm.row_start[y1] = c1;
-            if (tid == 0) sm.row_start[TS] = tot;
+                    for (int w = 0; w < WPR; ++w) c[h] += __popc(sm.mask[y * WPR + w]);
+                sum += c[h];
+            }
+            const int inc = warp_incl_scan(sum);
+            int ex = inc - sum;
+#pragma unroll
+            for (int h = 0; h < RPL; ++h) {
+                const int y = RPL * tid + h;
+                if (y < TS) sm.row_start[y] = ex;
+                ex += c[h];
+            }
+            if (tid == 31) sm.row_start[TS] = inc;
         }
         __syncthreads();
         for (int q = tid; q < TS * WPR; q += bd) {
@@ -1843,7 +1860,7 @@ __device__ int setup_sample_tris(TileSm<TS>& sm, const JobDev& J, const Buffers&
     if (cull_ok) sub_limits<TS>(sm.recv, sm.n_recv, sm.u.s.dlim, W->depth_u24 ? 1.f / lp.qscale : 0.f, tid,
                                 blockDim.x);
     else
-        for (int q = tid; q < kSubBlocks; q += blockDim.x) sm.u.s.dlim[q] = FLT_MAX;
+        for (int q = tid; q < SubGrid<TS>::blocks; q += blockDim.x) sm.u.s.dlim[q] = FLT_MAX;
     for (uint64_t b0 = 0; b0 < cnt; b0 += blockDim.x) {
         TriS ts;
         uint32_t box = 0u;
@@ -1873,7 +1890,8 @@ template <int TS, bool PROF>
 __global__ void __launch_bounds__(256, 4) k_raster_test(const WaveDev* __restrict__ W,
                                                         const JobDev* __restrict__ jobs, Buffers B)
 {
-    __shared__ __align__(16) TileSm<TS> sm;
+    extern __shared__ __align__(16) unsigned char tile_smem[];  // sizeof(TileSm<TS>), set at launch
+    TileSm<TS>& sm = *reinterpret_cast<TileSm<TS>*>(tile_smem);
     unsigned int p_samples = 0, p_visits = 0, p_writes = 0, p_culled = 0, p_cand = 0, p_dense = 0, p_tiles = 0;
     unsigned int p_stiles = 0, p_pairs = 0;
     __shared__ unsigned int s_item[2];
@@ -1971,7 +1989,8 @@ template <int TS, bool PROF>
 __global__ void __launch_bounds__(256) k_raster_map(const WaveDev* __restrict__ W,
                                                     const JobDev* __restrict__ jobs, Buffers B)
 {
-    __shared__ __align__(16) TileSm<TS> sm;
+    extern __shared__ __align__(16) unsigned char tile_smem[];  // sizeof(TileSm<TS>), set at launch
+    TileSm<TS>& sm = *reinterpret_cast<TileSm<TS>*>(tile_smem);
     unsigned int p_visits = 0, p_writes = 0, p_culled = 0, p_cand = 0, p_dense = 0;
     __shared__ unsigned int s_item;
     const unsigned int n_ne = B.ctr->n_nonempty;
@@ -2674,16 +2693,44 @@ static inline unsigned int grid_for(int64_t items, int per_block, int cap)
     return (unsigned int)g;
 }
 
+// Blocks of the block-per-tile kernels per SM (their shared tile is dynamic:
+// TileSm<128> holds a 64 KB depth tile).
+template <int TS>
+constexpr int tile_blocks() { return TS == 128 ? 2 : 4; }
+
+template <int TS, bool PROF>
+static cudaError_t allow_tile_smem()
+{
+    const int bytes = (int)sizeof(TileSm<TS>);
+    cudaError_t e = cudaFuncSetAttribute(k_raster_test<TS, PROF>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_raster_map<TS, PROF>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return e;
+}
+
+cudaError_t prepare_tile_kernels()
+{
+    cudaError_t e = cudaSuccess;
+    if (e == cudaSuccess) e = allow_tile_smem<32, false>();
+    if (e == cudaSuccess) e = allow_tile_smem<32, true>();
+    if (e == cudaSuccess) e = allow_tile_smem<64, false>();
+    if (e == cudaSuccess) e = allow_tile_smem<64, true>();
+    if (e == cudaSuccess) e = allow_tile_smem<128, false>();
+    if (e == cudaSuccess) e = allow_tile_smem<128, true>();
+    return e;
+}
+
 template <int TS, bool PROF>
 static void launch_tile_kernels(const WaveDev* W, const JobDev* d_jobs, const Buffers& b, const LaunchCfg& cfg)
 {
     const int sm = cfg.sm_count;
+    const size_t tsm = sizeof(TileSm<TS>);
     if (cfg.fused) {
         k_tile_warp<TS, PROF><<<sm * 6, kTileWarps * 32, 0, cfg.stream>>>(W, d_jobs, b);
         if (cfg.ev) cudaEventRecord(cfg.ev[3], cfg.stream);
-        k_raster_test<TS, PROF><<<sm * 4, 256, 0, cfg.stream>>>(W, d_jobs, b);
+        k_raster_test<TS, PROF><<<sm * tile_blocks<TS>(), 256, tsm, cfg.stream>>>(W, d_jobs, b);
     } else {
-        k_raster_map<TS, PROF><<<sm * 4, 256, 0, cfg.stream>>>(W, d_jobs, b);
+        k_raster_map<TS, PROF><<<sm * tile_blocks<TS>(), 256, tsm, cfg.stream>>>(W, d_jobs, b);
         if (cfg.ev) cudaEventRecord(cfg.ev[3], cfg.stream);
     }
 }
@@ -2712,9 +2759,12 @@ cudaError_t launch_wave(const WaveDev* d_wave, const JobDev* d_jobs, const Buffe
     if (cfg.tile == 32) {
         if (cfg.profile) launch_tile_kernels<32, true>(W, d_jobs, b, cfg);
         else launch_tile_kernels<32, false>(W, d_jobs, b, cfg);
-    } else {
+    } else if (cfg.tile == 64) {
         if (cfg.profile) launch_tile_kernels<64, true>(W, d_jobs, b, cfg);
         else launch_tile_kernels<64, false>(W, d_jobs, b, cfg);
+    } else {
+        if (cfg.profile) launch_tile_kernels<128, true>(W, d_jobs, b, cfg);
+        else launch_tile_kernels<128, false>(W, d_jobs, b, cfg);
     }
     if (cfg.ev) cudaEventRecord(cfg.ev[4], st);
     if (cfg.fused) k_pv<<<sm * 32, kPvThreads, 0, st>>>(W, d_jobs, b);

@@ -228,7 +228,7 @@ struct Buffers {
 // ---- host launchers (kernels.cu) ------------------------------------------
 struct LaunchCfg {
     int sm_count;
-    int tile;     // 32 or 64
+    int tile;     // 32, 64 or 128
     int fused;    // 1: k_raster_test + k_pv; 0: k_raster_map + k_sample
     int profile;  // counting kernels
     cudaStream_t stream;
@@ -241,6 +241,8 @@ constexpr int kLaunchesPerWave = 15;     // kernels launch_wave starts (fused pa
 constexpr int kLaunchesPerWaveMap = 14;  // strings, 2 with the sky map, 1 with arrays; (map path)
 constexpr int kMaxArraySub = 512;        // bypass substrings an array of parallel strings may hold
 
+// once per context, before any launch: the block-per-tile kernels' dynamic shared tile
+cudaError_t prepare_tile_kernels();
 cudaError_t launch_wave(const WaveDev* d_wave, const JobDev* d_jobs, const Buffers& b,
                         const LaunchCfg& cfg, int64_t tot_te_host);
 cudaError_t launch_finalize_pairs(const float2* kmod, int n_mods, const float2* kcell, int n_cells,

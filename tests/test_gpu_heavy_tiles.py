@@ -23,6 +23,7 @@ pytestmark = pytest.mark.gpu
     ("many_receivers", 64, 128, True, 30),     # > 16 receivers per tile: block-wide sample-driven test
     ("receiver_chunks", 64, 64, True, 30),     # > 64 receivers: staged in chunks, no plane culling, raster
     ("warp_tiles", 32, 512, False, 30),        # the same canopy on small tiles
+    ("block_raster_128", 128, 256, False, 60), # 128-texel tiles: block raster of a 64 KB shared tile
 ])
 def test_heavy_tile_paths(case, tile, map_res, tiny, cells):
     w = S.make_canopy(31 if not tiny else 32, tiny_modules=tiny, map_res=map_res, cells=cells)
@@ -47,7 +48,7 @@ def test_heavy_tile_paths(case, tile, map_res, tiny, cells):
     raster_tiles = p["nonempty_tiles"] - p["sample_tiles"]
     if case == "block_sample_test":
         assert why[2] > 0 and block_sample_tiles > 0, p
-    elif case == "block_raster":
+    elif case in ("block_raster", "block_raster_128"):
         assert why[1] > 0 and raster_tiles > 0 and p["texel_visits"] > 0, p
     elif case == "many_receivers":
         assert why[0] > 0 and block_sample_tiles > 0, p

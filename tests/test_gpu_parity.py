@@ -75,7 +75,7 @@ def test_mini_tracker(ctx):
     full_check(ctx, w, strict_loss=False)
 
 
-@pytest.mark.parametrize("tile,fmt,path", [(32, 0, 0), (64, 1, 0), (32, 1, 1), (64, 0, 1)])
+@pytest.mark.parametrize("tile,fmt,path", [(32, 0, 0), (64, 1, 0), (32, 1, 1), (64, 0, 1), (128, 0, 0), (128, 1, 1)])
 def test_tile_depth_format_and_path(tile, fmt, path):
     w = S.make_random_small(111, n_mods=6, n_steps=10, n=4, map_res=1024, tracked=True)
     o = oracle.evaluate_workload(w)

@@ -150,23 +150,44 @@ __device__ __forceinline__ float dot3(float3 a, float ax, float ay, float az)
 
 // Sample (I, J) of a module, I = cu * n + i and J = cv * n + j, sits at
 // a = (I + 1/2) p/n, b = (J + 1/2) p/n along the module axes (Section 2,
-// step 3: n x n areas per cell, centred).  The rasteriser's needed-texel mask
-// and the depth test evaluate these with the same rounded operations, so they
-// agree bit for bit on the texel every sample reads.
-__device__ __forceinline__ void sample_ab(int I, int Jr, float p_over_n, float& a, float& b)
+// step 3: n x n areas per cell, centred).  Its texel-space position is the
+// row's base (the b terms) plus a times the module's first axis, so the
+// samples of a row share the base.  The rasteriser's needed-texel mask, the
+// fused test and the map gather all evaluate this one rounding sequence, so
+// they agree bit for bit on the texel every sample reads.
+struct SampleRow {
+    float x, y, d;
+};
+__device__ __forceinline__ SampleRow sample_row(const ModStep& s, int Jr, float p_over_n)
 {
-    a = __fmul_rn(__fadd_rn((float)I, 0.5f), p_over_n);
-    b = __fmul_rn(__fadd_rn((float)Jr, 0.5f), p_over_n);
+    const float b = __fmul_rn(__fadd_rn((float)Jr, 0.5f), p_over_n);
+    return SampleRow{__fmaf_rn(b, s.tbx, s.tx0), __fmaf_rn(b, s.tby, s.ty0), __fmaf_rn(b, s.db, s.d0)};
 }
 
-__device__ __forceinline__ void sample_texel(const ModStep& s, float a, float b, int R, int& ix, int& iy,
-                                             float& d)
+// floor(x) clamped to [0, r_max] (r_max = R - 1 < 2^22) without a conversion
+// instruction: x is clamped as a float (NaN goes to 0), then 1.5 * 2^23 is
+// added rounding toward minus infinity, which leaves floor(x) in the low
+// mantissa bits.
+__device__ __forceinline__ int texel_floor(float x, float r_max)
 {
-    const float tx = __fmaf_rn(b, s.tbx, __fmaf_rn(a, s.tax, s.tx0));
-    const float ty = __fmaf_rn(b, s.tby, __fmaf_rn(a, s.tay, s.ty0));
-    d = __fmaf_rn(b, s.db, __fmaf_rn(a, s.da, s.d0));
-    ix = min(R - 1, max(0, (int)floorf(tx)));
-    iy = min(R - 1, max(0, (int)floorf(ty)));
+    const float c = fminf(fmaxf(x, 0.f), r_max);
+    return __float_as_int(__fadd_rd(c, 12582912.f)) - 0x4B400000;
+}
+
+// Texel (ix, iy) and depth d of sample I of a row; ih = I + 1/2 (exact).
+__device__ __forceinline__ void sample_texel(const ModStep& s, const SampleRow& row, float ih, float p_over_n,
+                                             float r_max, int& ix, int& iy, float& d)
+{
+    const float a = __fmul_rn(ih, p_over_n);
+    ix = texel_floor(__fmaf_rn(a, s.tax, row.x), r_max);
+    iy = texel_floor(__fmaf_rn(a, s.tay, row.y), r_max);
+    d = __fmaf_rn(a, s.da, row.d);
+}
+
+// (float)k + 1/2 for 0 <= k < 2^22, by the same exponent trick.
+__device__ __forceinline__ float texel_centre(int k)
+{
+    return __fadd_rn(__fadd_rn(__int_as_float(0x4B400000 | k), -12582912.f), 0.5f);
 }
 
 // Inclusive prefix sum over the lanes of a warp.
@@ -987,6 +1008,8 @@ struct RecvSm {
     int item_pref;             // (row, cell column) items of the receivers staged before this one
 };
 
+constexpr int kRasterThreads = 256;  // threads of a k_raster_test block
+
 template <int TS>
 struct RasterSm {
     uint32_t tile[TS * TS];  // depth keys of the tile
@@ -1186,17 +1209,19 @@ __device__ __forceinline__ void for_tile_samples(const TileSm<TS>& sm, const Job
                                                  unsigned int& cand, F f, G g)
 {
     constexpr int SH = TS == 128 ? 7 : (TS == 64 ? 6 : 5);
-    const int n = J.n, R_ = J.R;
+    const int n = J.n;
+    const float r_max = (float)(J.R - 1);
     const float inv_n = 1.f / (float)n;
     for (int it = threadIdx.x; it < sm.total_items; it += blockDim.x) {
         int Jr, cu, cv, jj, Ib, Ie;
         const RecvSm& R = decode_item(sm.recv, sm.n_recv, it, n, inv_n, Jr, cu, cv, jj, Ib, Ie);
         if (PROF) cand += (unsigned int)max(0, Ie - Ib + 1);
-        for (int I = Ib; I <= Ie; ++I) {
-            float a, b, d;
+        const SampleRow row = sample_row(R.s, Jr, R.p_over_n);
+        float ih = (float)Ib + 0.5f;
+        for (int I = Ib; I <= Ie; ++I, ih += 1.f) {
+            float d;
             int ix, iy;
-            sample_ab(I, Jr, R.p_over_n, a, b);
-            sample_texel(R.s, a, b, R_, ix, iy, d);
+            sample_texel(R.s, row, ih, R.p_over_n, r_max, ix, iy, d);
             if ((ix >> SH) == tx && (iy >> SH) == ty) f(R, jj * n + (I - cu * n), ix, iy, d);
         }
         g(R, cu, cv);
@@ -1362,7 +1387,7 @@ __device__ __forceinline__ bool sample_test(const TriS* tri, int n_kept, const u
 {
     constexpr int kSubSide = SubGrid<TS>::side;
     const int sb = (ly / (TS / kSubSide)) * kSubSide + lx / (TS / kSubSide);
-    const float px = (float)lx + 0.5f, py = (float)ly + 0.5f;
+    const float px = texel_centre(lx), py = texel_centre(ly);
     const uint32_t* ms = sbm[sb];
     bool shaded = false;
     for (int w = 0; w < nw && !shaded; ++w) {
@@ -1400,40 +1425,42 @@ __device__ __forceinline__ bool sample_test(const TriS* tri, int n_kept, const u
 template <int TS, int WORDS, bool PROF>
 __device__ __forceinline__ void test_items(const RecvSm* recv, int n_recv, int total_items, const JobDev& J,
                                            const LightParams& lp, int u24, int tx, int ty, int it_begin,
-                                           int it_stride, const TriS* tri, int n_kept, const uint32_t (*sbm)[WORDS],
-                                           int nw,
-                                           uint32_t* seen, uint32_t* cnt_row, unsigned long long* bits_row,
-                                           int want_bits, unsigned int& cand, unsigned int& samples,
-                                           unsigned int& pairs, unsigned int& frags)
+                                           int it_stride, const TriS* tri, int n_kept,
+                                           const uint32_t (*sbm)[WORDS], int nw, uint32_t* seen,
+                                           uint32_t* cnt_row, unsigned long long* bits_row, int want_bits,
+                                           unsigned int& cand, unsigned int& samples, unsigned int& pairs,
+                                           unsigned int& frags)
 {
     constexpr int SH = TS == 128 ? 7 : (TS == 64 ? 6 : 5);
-    const int n = J.n, R_ = J.R;
+    const int n = J.n;
+    const float r_max = (float)(J.R - 1);
     const float inv_n = 1.f / (float)n;
     for (int it = it_begin; it < total_items; it += it_stride) {
         int Jr, cu, cv, jj, Ib, Ie;
         const RecvSm& R = decode_item(recv, n_recv, it, n, inv_n, Jr, cu, cv, jj, Ib, Ie);
         if (PROF) cand += (unsigned int)max(0, Ie - Ib + 1);
-        // the receiver's sample frame in registers for the row's samples
+        // the receiver's sample frame and the row's base in registers
         const ModStep s = R.s;
         const float p_over_n = R.p_over_n;
+        const SampleRow row = sample_row(s, Jr, p_over_n);
         const int i0 = cu * n;
-        uint32_t row = 0u;  // bit i: sample i of the item's row (within its cell) is shaded
-        for (int I = Ib; I <= Ie; ++I) {
-            float a, b, d;
+        uint32_t bits = 0u;  // bit i: sample i of the item's row (within its cell) is shaded
+        float ih = (float)Ib + 0.5f;
+        for (int I = Ib; I <= Ie; ++I, ih += 1.f) {
+            float d;
             int ix, iy;
-            sample_ab(I, Jr, p_over_n, a, b);
-            sample_texel(s, a, b, R_, ix, iy, d);
+            sample_texel(s, row, ih, p_over_n, r_max, ix, iy, d);
             if ((ix >> SH) != tx || (iy >> SH) != ty) continue;
             if (PROF) ++samples;
             if (sample_test<TS, WORDS, PROF>(tri, n_kept, sbm, nw, seen, ix & (TS - 1), iy & (TS - 1), d, s.bias,
                                              lp, u24, pairs, frags))
-                row |= 1u << (I - i0);
+                bits |= 1u << (I - i0);
         }
-        if (row) {
+        if (bits) {
             const int gcell = R.cell_base + cv * R.cu + cu;
-            atomicAdd(&cnt_row[gcell], (uint32_t)__popc(row));
+            atomicAdd(&cnt_row[gcell], (uint32_t)__popc(bits));
             // sample k = jj * n + i of the cell; flags kept for k < 64
-            if (want_bits && jj * n < 64) atomicOr(&bits_row[gcell], (unsigned long long)row << (jj * n));
+            if (want_bits && jj * n < 64) atomicOr(&bits_row[gcell], (unsigned long long)bits << (jj * n));
         }
     }
 }
@@ -1887,8 +1914,8 @@ __device__ int setup_sample_tris(TileSm<TS>& sm, const JobDev& J, const Buffers&
 }
 
 template <int TS, bool PROF>
-__global__ void __launch_bounds__(256, 4) k_raster_test(const WaveDev* __restrict__ W,
-                                                        const JobDev* __restrict__ jobs, Buffers B)
+__global__ void __launch_bounds__(kRasterThreads, 4) k_raster_test(const WaveDev* __restrict__ W,
+                                                                   const JobDev* __restrict__ jobs, Buffers B)
 {
     extern __shared__ __align__(16) unsigned char tile_smem[];  // sizeof(TileSm<TS>), set at launch
     TileSm<TS>& sm = *reinterpret_cast<TileSm<TS>*>(tile_smem);
@@ -2210,10 +2237,11 @@ __global__ void __launch_bounds__(kPvThreads) k_sample(const WaveDev* __restrict
                 int c = g / nn, k = g - c * nn;
                 int jj = k / n, ii = k - jj * n;
                 int cv_ = c / cu, cu_ = c - cv_ * cu;
-                float a, b, d;
+                float d;
                 int ix, iy;
-                sample_ab(cu_ * n + ii, cv_ * n + jj, p_over_n, a, b);
-                sample_texel(s, a, b, R, ix, iy, d);
+                const int I = cu_ * n + ii;
+                sample_texel(s, sample_row(s, cv_ * n + jj, p_over_n), (float)I + 0.5f, p_over_n,
+                             (float)(R - 1), ix, iy, d);
                 const int64_t te = te0 + (int64_t)(iy >> sh) * J.tiles_x + (ix >> sh);
                 if (B.t_cnt[te] != 0u) {
                     const uint32_t slot = B.t_slot[te];
@@ -2728,7 +2756,7 @@ static void launch_tile_kernels(const WaveDev* W, const JobDev* d_jobs, const Bu
     if (cfg.fused) {
         k_tile_warp<TS, PROF><<<sm * 6, kTileWarps * 32, 0, cfg.stream>>>(W, d_jobs, b);
         if (cfg.ev) cudaEventRecord(cfg.ev[3], cfg.stream);
-        k_raster_test<TS, PROF><<<sm * tile_blocks<TS>(), 256, tsm, cfg.stream>>>(W, d_jobs, b);
+        k_raster_test<TS, PROF><<<sm * tile_blocks<TS>(), kRasterThreads, tsm, cfg.stream>>>(W, d_jobs, b);
     } else {
         k_raster_map<TS, PROF><<<sm * tile_blocks<TS>(), 256, tsm, cfg.stream>>>(W, d_jobs, b);
         if (cfg.ev) cudaEventRecord(cfg.ev[3], cfg.stream);

@@ -2109,83 +2109,214 @@ __device__ __forceinline__ void zero_step_module(const JobDev& J, const ModuleDe
     }
 }
 
-// Fused path: the tallies were accumulated by k_raster_test.  One warp per
-// (step, module): lanes over cells, substring minima in shared memory, the
-// candidate currents of the MPP split over lanes.
+// Fused path: the tallies were accumulated by the tile kernels.  The PV model
+// of one (step, module) item by one warp: lanes over its cells into substring
+// minima in shared memory, then over the candidate currents of the MPP.
+// `imin` holds kMaxSub entries.
+__device__ void pv_module_warp(const JobDev* jobs, int nj, int64_t item, const Buffers& B, uint32_t* imin)
+{
+    const int lane = threadIdx.x & 31;
+    const int j = job_of(nj, item, [&](int q) { return jobs[q].it_mod; });
+    const JobDev& J = jobs[j];
+    const int64_t li = item - J.it_mod;
+    const int ls = (int)(li / J.n_mods), m = (int)(li % J.n_mods);
+    const int64_t msi = J.ms_base + li;
+    const LightParams& lp = B.lp[J.js_base + ls];
+    const ModuleDev& M = J.mods[m];
+    const int ncell = M.cu * M.cv, C = J.n_cells;
+    const int64_t row = (int64_t)(J.out_row0 + ls);
+    const int64_t cbase = J.cs_base + (int64_t)ls * C + M.cell_base;
+    if (!lp.valid) {
+        if (lane == 0) { B.ms_p[msi] = 0.f; B.ms_pu[msi] = 0.f; B.ms_beam[msi] = 0.f; }
+        for (int c = lane; c < ncell; c += 32) {
+            B.cs_cnt[cbase + c] = 0u;
+            if (J.out_counts) J.out_counts[row * C + M.cell_base + c] = 0;
+            if (J.out_bits) J.out_bits[row * C + M.cell_base + c] = 0ull;
+        }
+        return;
+    }
+    const ModStep& s = B.ms[msi];
+    const float beam = lp.dni * fmaxf(0.f, s.cosi);
+    const float diff = lp.dhi * (1.f + s.nz) * 0.5f;
+    const float inv_nn = 1.f / J.nn;
+    const int* csub = J.lay_sub + J.lay_off[M.layout];
+    const int ns = M.n_sub;
+    for (int k = lane; k < ns; k += 32) imin[k] = 0x7F800000u;  // +inf
+    __syncwarp();
+    for (int c = lane; c < ncell; c += 32) {
+        const uint32_t cnt = B.cs_cnt[cbase + c];
+        if (J.out_counts) J.out_counts[row * C + M.cell_base + c] = (uint8_t)cnt;
+        if (J.out_bits) J.out_bits[row * C + M.cell_base + c] = B.cs_bits[cbase + c];
+        const float gd = J.fdiff ? diff * (1.f - J.fdiff[M.cell_base + c]) : diff;
+        const float G = beam * (1.f - cnt * inv_nn) + gd;
+        const float I = J.i_ref * G * 1e-3f;
+        atomicMin(&imin[csub[c]], __float_as_uint(I));  // I >= 0: uint order = float order
+    }
+    __syncwarp();
+    if (J.n_str) {  // substring currents for the series-string model (k_string)
+        float* ss = B.ss_i + J.ss_base + (int64_t)ls * J.n_sub_tot + J.sub_base[m];
+        for (int k = lane; k < ns; k += 32) ss[k] = __uint_as_float(imin[k]);
+        if (lane == 0) B.ms_iu[msi] = J.i_ref * (beam + diff) * 1e-3f;
+    }
+    const int* nk = J.lay_nk + J.lay_nk_off[M.layout];
+    float best = 0.f, vsum = 0.f;
+    for (int k = lane; k < ns; k += 32) {
+        const float ik = __uint_as_float(imin[k]);
+        float volt = 0.f;
+        for (int q = 0; q < ns; ++q) volt += __uint_as_float(imin[q]) >= ik ? nk[q] * J.v_cell : -J.v_diode;
+        best = fmaxf(best, ik * volt);
+        vsum += nk[k] * J.v_cell;
+    }
+#pragma unroll
+    for (int off = 16; off; off >>= 1) {
+        best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, off));
+        vsum += __shfl_xor_sync(0xffffffffu, vsum, off);
+    }
+    if (lane == 0) {
+        B.ms_p[msi] = best;
+        B.ms_pu[msi] = J.i_ref * (beam + diff) * 1e-3f * vsum;
+        B.ms_beam[msi] = beam;
+    }
+    __syncwarp();
+}
+
+// A warp takes bw consecutive (step, module) items, one per lane (bw = 32, or
+// the smallest power of two that still covers the wave in one pass of the
+// grid, so that small waves spread over all warps).  Each lane decodes its
+// item (job, step, module, irradiance, cell layout); the warp then walks the
+// items' cells one module at a time (lanes over its cells, the module's fields
+// taken from its lane) into per-module substring minima in shared memory, and
+// each lane evaluates its own module's MPP.  The arithmetic is that of
+// pv_module_warp, operation for operation (a module's voltage sum is exact in
+// either order), which the warp falls back to when one of its modules has
+// more than kPvFastSub substrings.
 constexpr int kPvWarps = kPvThreads / 32;
+constexpr int kPvFastSub = 8;
+constexpr int kPvUnroll = 4;
+static_assert(32 * kPvFastSub >= kMaxSub, "the per-module path reuses the warp's minima");
 
 __global__ void __launch_bounds__(kPvThreads) k_pv(const WaveDev* __restrict__ W, const JobDev* __restrict__ jobs,
                                                    Buffers B)
 {
-    __shared__ uint32_t s_imin[kPvWarps][kMaxSub];
+    __shared__ uint32_t s_imin[kPvWarps][32 * kPvFastSub];
     const int64_t tot = W->tot_mod;
     const int nj = W->n_jobs;
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     uint32_t* imin = s_imin[wib];
     const int64_t n_warps = (int64_t)gridDim.x * kPvWarps;
-    for (int64_t item = (int64_t)blockIdx.x * kPvWarps + wib; item < tot; item += n_warps) {
-        const int j = job_of(nj, item, [&](int q) { return jobs[q].it_mod; });
-        const JobDev& J = jobs[j];
-        const int64_t li = item - J.it_mod;
-        const int ls = (int)(li / J.n_mods), m = (int)(li % J.n_mods);
-        const int64_t msi = J.ms_base + li;
-        const LightParams& lp = B.lp[J.js_base + ls];
-        const ModuleDev& M = J.mods[m];
-        const int ncell = M.cu * M.cv, C = J.n_cells;
-        const int64_t row = (int64_t)(J.out_row0 + ls);
-        const int64_t cbase = J.cs_base + (int64_t)ls * C + M.cell_base;
-        if (!lp.valid) {
-            if (lane == 0) { B.ms_p[msi] = 0.f; B.ms_pu[msi] = 0.f; B.ms_beam[msi] = 0.f; }
-            for (int c = lane; c < ncell; c += 32) {
-                B.cs_cnt[cbase + c] = 0u;
-                if (J.out_counts) J.out_counts[row * C + M.cell_base + c] = 0;
-                if (J.out_bits) J.out_bits[row * C + M.cell_base + c] = 0ull;
+    int bw = 32;
+    while (bw > 1 && n_warps * (bw >> 1) >= tot) bw >>= 1;
+    for (int64_t base = ((int64_t)blockIdx.x * kPvWarps + wib) * bw; base < tot; base += n_warps * bw) {
+        const int64_t item = base + lane;
+        const bool have = lane < bw && item < tot;
+        int j = 0, ls = 0, m = 0, ncell = 0, ns = 0, cell0 = 0;
+        int64_t msi = 0, cbase = 0;
+        const int* csub = nullptr;
+        bool lit = false;
+        float beam = 0.f, diff = 0.f;
+        if (have) {
+            j = job_of(nj, item, [&](int q) { return jobs[q].it_mod; });
+            const JobDev& J = jobs[j];
+            const int64_t li = item - J.it_mod;
+            ls = (int)(li / J.n_mods);
+            m = (int)(li - (int64_t)ls * J.n_mods);
+            msi = J.ms_base + li;
+            const LightParams& lp = B.lp[J.js_base + ls];
+            const ModuleDev& M = J.mods[m];
+            ncell = M.cu * M.cv;
+            ns = M.n_sub;
+            cell0 = M.cell_base;
+            cbase = J.cs_base + (int64_t)ls * J.n_cells + cell0;
+            csub = J.lay_sub + J.lay_off[M.layout];
+            lit = lp.valid != 0;
+            if (lit) {
+                const ModStep& s = B.ms[msi];
+                beam = lp.dni * fmaxf(0.f, s.cosi);
+                diff = lp.dhi * (1.f + s.nz) * 0.5f;
             }
+        }
+        if (__reduce_max_sync(0xffffffffu, ns) > kPvFastSub) {
+            for (int q = 0; q < bw && base + q < tot; ++q) pv_module_warp(jobs, nj, base + q, B, imin);
             continue;
         }
-        const ModStep& s = B.ms[msi];
-        const float beam = lp.dni * fmaxf(0.f, s.cosi);
-        const float diff = lp.dhi * (1.f + s.nz) * 0.5f;
-        const float inv_nn = 1.f / J.nn;
-        const int* csub = J.lay_sub + J.lay_off[M.layout];
-        const int ns = M.n_sub;
-        for (int k = lane; k < ns; k += 32) imin[k] = 0x7F800000u;  // +inf
+        for (int k = 0; k < kPvFastSub; ++k) imin[lane * kPvFastSub + k] = 0x7F800000u;  // +inf
         __syncwarp();
-        for (int c = lane; c < ncell; c += 32) {
-            const uint32_t cnt = B.cs_cnt[cbase + c];
-            if (J.out_counts) J.out_counts[row * C + M.cell_base + c] = (uint8_t)cnt;
-            if (J.out_bits) J.out_bits[row * C + M.cell_base + c] = B.cs_bits[cbase + c];
-            const float gd = J.fdiff ? diff * (1.f - J.fdiff[M.cell_base + c]) : diff;
-            const float G = beam * (1.f - cnt * inv_nn) + gd;
-            const float I = J.i_ref * G * 1e-3f;
-            atomicMin(&imin[csub[c]], __float_as_uint(I));  // I >= 0: uint order = float order
-        }
-        __syncwarp();
-        if (J.n_str) {  // substring currents for the series-string model (k_string)
-            float* ss = B.ss_i + J.ss_base + (int64_t)ls * J.n_sub_tot + J.sub_base[m];
-            for (int k = lane; k < ns; k += 32) ss[k] = __uint_as_float(imin[k]);
-            if (lane == 0) B.ms_iu[msi] = J.i_ref * (beam + diff) * 1e-3f;
-        }
-        const int* nk = J.lay_nk + J.lay_nk_off[M.layout];
-        float best = 0.f, vsum = 0.f;
-        for (int k = lane; k < ns; k += 32) {
-            const float ik = __uint_as_float(imin[k]);
-            float volt = 0.f;
-            for (int q = 0; q < ns; ++q) volt += __uint_as_float(imin[q]) >= ik ? nk[q] * J.v_cell : -J.v_diode;
-            best = fmaxf(best, ik * volt);
-            vsum += nk[k] * J.v_cell;
-        }
+        for (unsigned int act = __ballot_sync(0xffffffffu, have); act; act &= act - 1u) {
+            const int q = __ffs(act) - 1;
+            const JobDev& J = jobs[__shfl_sync(0xffffffffu, j, q)];
+            const int nc = __shfl_sync(0xffffffffu, ncell, q);
+            const int c0 = __shfl_sync(0xffffffffu, cell0, q);
+            const int64_t cb = __shfl_sync(0xffffffffu, cbase, q);
+            const int* cs = reinterpret_cast<const int*>(
+                __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(csub), q));
+            const int64_t row = (int64_t)(J.out_row0 + __shfl_sync(0xffffffffu, ls, q));
+            const bool litq = __shfl_sync(0xffffffffu, (int)lit, q) != 0;
+            const float bq = __shfl_sync(0xffffffffu, beam, q), dq = __shfl_sync(0xffffffffu, diff, q);
+            const int C = J.n_cells;
+            const float inv_nn = 1.f / J.nn;
+            uint32_t* im = imin + q * kPvFastSub;
+            if (!litq) {
+                for (int c = lane; c < nc; c += 32) {
+                    B.cs_cnt[cb + c] = 0u;
+                    if (J.out_counts) J.out_counts[row * C + c0 + c] = 0;
+                    if (J.out_bits) J.out_bits[row * C + c0 + c] = 0ull;
+                }
+                continue;
+            }
+            // kPvUnroll rounds of 32 cells at once: their loads are issued
+            // together, before the minima are taken
+            for (int cr = lane; cr < nc; cr += 32 * kPvUnroll) {
+                uint32_t cnt[kPvUnroll];
+                int sub[kPvUnroll];
 #pragma unroll
-        for (int off = 16; off; off >>= 1) {
-            best = fmaxf(best, __shfl_xor_sync(0xffffffffu, best, off));
-            vsum += __shfl_xor_sync(0xffffffffu, vsum, off);
-        }
-        if (lane == 0) {
-            B.ms_p[msi] = best;
-            B.ms_pu[msi] = J.i_ref * (beam + diff) * 1e-3f * vsum;
-            B.ms_beam[msi] = beam;
+                for (int u = 0; u < kPvUnroll; ++u) {
+                    const int c = cr + 32 * u;
+                    cnt[u] = c < nc ? B.cs_cnt[cb + c] : 0u;
+                    sub[u] = c < nc ? cs[c] : 0;
+                }
+#pragma unroll
+                for (int u = 0; u < kPvUnroll; ++u) {
+                    const int c = cr + 32 * u;
+                    if (c >= nc) continue;
+                    if (J.out_counts) J.out_counts[row * C + c0 + c] = (uint8_t)cnt[u];
+                    if (J.out_bits) J.out_bits[row * C + c0 + c] = B.cs_bits[cb + c];
+                    const float gd = J.fdiff ? dq * (1.f - J.fdiff[c0 + c]) : dq;
+                    const float G = bq * (1.f - cnt[u] * inv_nn) + gd;
+                    const float I = J.i_ref * G * 1e-3f;
+                    atomicMin(&im[sub[u]], __float_as_uint(I));  // I >= 0: uint order = float order
+                }
+            }
         }
         __syncwarp();
+        if (have) {
+            const JobDev& J = jobs[j];
+            if (!lit) {
+                B.ms_p[msi] = 0.f;
+                B.ms_pu[msi] = 0.f;
+                B.ms_beam[msi] = 0.f;
+            } else {
+                const ModuleDev& M = J.mods[m];
+                const uint32_t* im = imin + lane * kPvFastSub;
+                if (J.n_str) {  // substring currents for the series-string model (k_string)
+                    float* ss = B.ss_i + J.ss_base + (int64_t)ls * J.n_sub_tot + J.sub_base[m];
+                    for (int k = 0; k < ns; ++k) ss[k] = __uint_as_float(im[k]);
+                    B.ms_iu[msi] = J.i_ref * (beam + diff) * 1e-3f;
+                }
+                const int* nk = J.lay_nk + J.lay_nk_off[M.layout];
+                float best = 0.f, vsum = 0.f;
+                for (int k = 0; k < ns; ++k) {
+                    const float ik = __uint_as_float(im[k]);
+                    float volt = 0.f;
+                    for (int q = 0; q < ns; ++q) volt += __uint_as_float(im[q]) >= ik ? nk[q] * J.v_cell : -J.v_diode;
+                    best = fmaxf(best, ik * volt);
+                    vsum += nk[k] * J.v_cell;
+                }
+                B.ms_p[msi] = best;
+                B.ms_pu[msi] = J.i_ref * (beam + diff) * 1e-3f * vsum;
+                B.ms_beam[msi] = beam;
+            }
+        }
+        __syncwarp();  // the warp's minima may be reset
     }
 }
 

@@ -63,6 +63,21 @@ def test_random_small(ctx, seed, tracked):
     full_check(ctx, w, chunk_steps=5, strict_loss=False)
 
 
+def test_many_substring_modules(ctx):
+    """Modules of 12 bypass substrings (two per cell column) among 3-substring
+    modules: the PV kernel evaluates up to 8 substrings per lane and falls back
+    to one module per warp otherwise; with 70 modules a step, its 32-item
+    batches take both forms, and batches cross steps."""
+    w = S.make_random_small(106, n_mods=70, n_steps=6, n=3, map_res=512)
+    g = w.gen
+    cu, cv = g.layouts[0].cells_u, g.layouts[0].cells_v
+    col = np.tile(np.arange(cu), cv)
+    half = (np.repeat(np.arange(cv), cu) >= cv // 2).astype(np.int32)
+    g.layouts.append(S.Layout(cu, cv, 2 * cu, (2 * col + half).astype(np.int32)))
+    g.layout[:2] = 1
+    full_check(ctx, w, chunk_steps=4, strict_loss=False)
+
+
 def test_mini_facade(ctx):
     w = S.make_facade(seed=7, n=4, map_res=1024, n_buildings=12, n_trees=6, n_poles=4, floors=2, per_floor=6,
                       target_tris=4000, days=np.array([20, 110, 200, 300]), radius=80.0)

@@ -921,7 +921,7 @@ static WaveDev pack_wave(std::vector<JobDev>& jobs, size_t first, size_t last, i
         W.tot_cs += (int64_t)J.k * J.n_cells;
         W.tot_win += (int64_t)J.k * groups;
         W.tot_mod += (int64_t)J.k * J.n_mods;
-        W.tot_tri += ((int64_t)J.n_ml + (J.n_mtris + 31) / 32) * J.k;
+        W.tot_tri += (((int64_t)J.n_ml + (J.n_mtris + 31) / 32 + 31) / 32) * J.k;  // groups of 32 meshlets
         W.tot_epi += (J.kahan_cell ? (int64_t)J.n_cells : 0) + J.n_mods + J.n_str + J.n_arr;
         W.tot_sa += (int64_t)J.k * J.n_arr;
         W.tot_ss += (int64_t)J.k * (J.n_str ? J.n_sub_tot : 0);

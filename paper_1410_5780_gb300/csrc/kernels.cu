@@ -605,16 +605,18 @@ __device__ __forceinline__ void append_pairs(const Buffers& B, const WaveDev* W,
         }
 }
 
-__global__ void __launch_bounds__(256) k_bin(const WaveDev* __restrict__ W, const JobDev* __restrict__ jobs,
+__global__ void __launch_bounds__(256, 4) k_bin(const WaveDev* __restrict__ W, const JobDev* __restrict__ jobs,
                                              Buffers B)
 {
-    // One warp per (meshlet, step), the step fastest so that consecutive warps
-    // reuse the meshlet's 32 triangles from cache.  A scene meshlet is first
-    // tested as a whole: its bounding box, projected for the step, against the
-    // far planes of the tiles it covers; if no tile can receive a shadow from
-    // it, the 32 triangles are skipped together.  Then each lane bins one
-    // triangle.  Generator module triangles follow the scene's, in groups of
-    // 32, without the box test.  A triangle over more than kBigTiles tiles is
+    // One warp per (group of 32 meshlets, step), the step fastest so that
+    // consecutive warps reuse the group's triangles from cache.  Each lane
+    // first projects one scene meshlet's bounding box for the step and keeps
+    // it if it overlaps the light window; the warp then tests each kept box
+    // against the far planes of the tiles it covers (lanes over tiles): if no
+    // tile can receive a shadow from the meshlet, its 32 triangles are
+    // skipped together.  Otherwise each lane bins one of its triangles.
+    // Generator module triangles follow the scene's, in meshlets of 32,
+    // without the box test.  A triangle over more than kBigTiles tiles is
     // listed for k_bin_big.
     const int64_t tot = W->tot_tri;
     const int nj = W->n_jobs;
@@ -627,16 +629,20 @@ __global__ void __launch_bounds__(256) k_bin(const WaveDev* __restrict__ W, cons
         const int j = job_of(nj, item, [&](int q) { return jobs[q].it_tri; });
         const JobDev& J = jobs[j];
         const int64_t li = item - J.it_tri;
-        const int mi = (int)(li / J.k), ls = (int)(li - (int64_t)mi * J.k);
+        const int g = (int)(li / J.k), ls = (int)(li - (int64_t)g * J.k);
         const int R = J.R;
         const int64_t js = J.js_base + ls;
         const LightParams& lp = B.lp[js];
         if (!lp.valid) continue;
         const int64_t te0 = J.te_base + (int64_t)ls * J.tiles_x * J.tiles_x;
-        int t;
-        bool act;
-        if (mi < J.n_ml) {
-            const float4 lo = J.ml_box[2 * mi], hi = J.ml_box[2 * mi + 1];
+        const int n_all = J.n_ml + ((J.n_mtris + 31) >> 5);  // scene meshlets, then module meshlets
+        // this lane's scene meshlet: window test, covered tiles, nearest depth key
+        const int ml = g * 32 + lane;
+        int btx0 = 0, btx1 = -1, bty0 = 0, bty1 = -1;
+        uint32_t bkey = 0u;
+        bool pass = false;
+        if (ml < J.n_ml) {
+            const float4 lo = J.ml_box[2 * ml], hi = J.ml_box[2 * ml + 1];
             float xmin = FLT_MAX, xmax = -FLT_MAX, ymin = FLT_MAX, ymax = -FLT_MAX, dmin = FLT_MAX;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
@@ -649,71 +655,89 @@ __global__ void __launch_bounds__(256) k_bin(const WaveDev* __restrict__ W, cons
                 ymin = fminf(ymin, ty); ymax = fmaxf(ymax, ty);
                 dmin = fminf(dmin, -(x * lp.sx + y * lp.sy + z * lp.sz));
             }
-            if (!(xmax >= 0.5f && ymax >= 0.5f && xmin <= R - 0.5f && ymin <= R - 0.5f)) continue;
-            const int tx0 = max(0, (int)floorf(xmin - 0.5f)) >> sh, tx1 = min(R - 1, (int)ceilf(xmax)) >> sh;
-            const int ty0 = max(0, (int)floorf(ymin - 0.5f)) >> sh, ty1 = min(R - 1, (int)ceilf(ymax)) >> sh;
-            // the box's nearest point, less a margin for the rounding of the
-            // projection, against each covered tile's far plane
-            const uint32_t bkey = depth_store_key(dmin - 1e-3f * (1.f + fabsf(dmin)), lp, u24);
-            const int wx = tx1 - tx0 + 1, ntl = wx * (ty1 - ty0 + 1);
-            bool keep = false;
-            for (int q0 = 0; q0 < ntl && !keep; q0 += 32) {
-                const int q = q0 + lane;
-                bool k = false;
-                if (q < ntl) {
-                    const int ty = ty0 + q / wx, tx = tx0 + q % wx;
-                    k = bkey < B.t_far[te0 + (int64_t)ty * J.tiles_x + tx];
-                }
-                keep = __any_sync(0xffffffffu, k);
+            pass = xmax >= 0.5f && ymax >= 0.5f && xmin <= R - 0.5f && ymin <= R - 0.5f;
+            if (pass) {
+                btx0 = max(0, (int)floorf(xmin - 0.5f)) >> sh;
+                btx1 = min(R - 1, (int)ceilf(xmax)) >> sh;
+                bty0 = max(0, (int)floorf(ymin - 0.5f)) >> sh;
+                bty1 = min(R - 1, (int)ceilf(ymax)) >> sh;
+                // the box's nearest point, less a margin for the rounding of
+                // the projection
+                bkey = depth_store_key(dmin - 1e-3f * (1.f + fabsf(dmin)), lp, u24);
             }
-            if (!keep) continue;
-            t = mi * 32 + lane;
-            act = t < J.n_tris;
         } else {
-            t = J.n_tris + (mi - J.n_ml) * 32 + lane;
-            act = t < J.n_tris + J.n_mtris;
+            pass = ml < n_all;
         }
-        // per lane: the tiles its triangle may shade (at most kBigTiles), in
-        // registers until the warp appends them together
-        uint32_t te[kBigTiles];
-        uint32_t valid = 0u;
-        if (act) {
-            TriT T;
-            tri_texel(J, B, lp, ls, t, T);
-            Edges e;
-            const float xmin = fminf(T.x[0], fminf(T.x[1], T.x[2])), xmax = fmaxf(T.x[0], fmaxf(T.x[1], T.x[2]));
-            const float ymin = fminf(T.y[0], fminf(T.y[1], T.y[2])), ymax = fmaxf(T.y[0], fmaxf(T.y[1], T.y[2]));
-            // covered texel centres (ix + 0.5) lie in [xmin, xmax]
-            const int ix0 = max(0, (int)ceilf(xmin - 0.5f)), ix1 = min(R - 1, (int)floorf(xmax - 0.5f));
-            const int iy0 = max(0, (int)ceilf(ymin - 0.5f)), iy1 = min(R - 1, (int)floorf(ymax - 0.5f));
-            if (make_edges(T, e) && xmax >= 0.5f && ymax >= 0.5f && xmin <= R - 0.5f && ymin <= R - 0.5f &&
-                ix0 <= ix1 && iy0 <= iy1) {
-                const uint32_t dkey = depth_store_key(fminf(T.d[0], fminf(T.d[1], T.d[2])), lp, u24);
-                const int tx0 = ix0 >> sh, tx1 = ix1 >> sh, ty0 = iy0 >> sh, ty1 = iy1 >> sh;
-                const int wx = tx1 - tx0 + 1, ntiles = wx * (ty1 - ty0 + 1);
-                if (ntiles > kBigTiles) {
-                    const unsigned int pos = atomicAdd(&B.ctr->n_big, 1u);
-                    if (pos < (uint64_t)W->big_cap) B.big[pos] = make_uint2((uint32_t)t, (uint32_t)js);
-                } else {
+        for (unsigned int cand = __ballot_sync(0xffffffffu, pass); cand; cand &= cand - 1u) {
+            const int q = __ffs(cand) - 1;
+            const int mi = g * 32 + q;
+            const int mx0 = __shfl_sync(0xffffffffu, btx0, q), mx1 = __shfl_sync(0xffffffffu, btx1, q);
+            const int my0 = __shfl_sync(0xffffffffu, bty0, q), my1 = __shfl_sync(0xffffffffu, bty1, q);
+            const uint32_t mkey = __shfl_sync(0xffffffffu, bkey, q);
+            int t;
+            bool act;
+            if (mi < J.n_ml) {
+                // the meshlet's nearest point against each covered tile's far plane
+                const int wx = mx1 - mx0 + 1, ntl = wx * (my1 - my0 + 1);
+                bool keep = false;
+                for (int q0 = 0; q0 < ntl && !keep; q0 += 32) {
+                    const int k = q0 + lane;
+                    bool kk = false;
+                    if (k < ntl) {
+                        const int ty = my0 + k / wx, tx = mx0 + k % wx;
+                        kk = mkey < B.t_far[te0 + (int64_t)ty * J.tiles_x + tx];
+                    }
+                    keep = __any_sync(0xffffffffu, kk);
+                }
+                if (!keep) continue;
+                t = mi * 32 + lane;
+                act = t < J.n_tris;
+            } else {
+                t = J.n_tris + (mi - J.n_ml) * 32 + lane;
+                act = t < J.n_tris + J.n_mtris;
+            }
+            // per lane: the tiles its triangle may shade (at most kBigTiles), in
+            // registers until the warp appends them together
+            uint32_t te[kBigTiles];
+            uint32_t valid = 0u;
+            if (act) {
+                TriT T;
+                tri_texel(J, B, lp, ls, t, T);
+                Edges e;
+                const float xmin = fminf(T.x[0], fminf(T.x[1], T.x[2])), xmax = fmaxf(T.x[0], fmaxf(T.x[1], T.x[2]));
+                const float ymin = fminf(T.y[0], fminf(T.y[1], T.y[2])), ymax = fmaxf(T.y[0], fmaxf(T.y[1], T.y[2]));
+                // covered texel centres (ix + 0.5) lie in [xmin, xmax]
+                const int ix0 = max(0, (int)ceilf(xmin - 0.5f)), ix1 = min(R - 1, (int)floorf(xmax - 0.5f));
+                const int iy0 = max(0, (int)ceilf(ymin - 0.5f)), iy1 = min(R - 1, (int)floorf(ymax - 0.5f));
+                if (make_edges(T, e) && xmax >= 0.5f && ymax >= 0.5f && xmin <= R - 0.5f && ymin <= R - 0.5f &&
+                    ix0 <= ix1 && iy0 <= iy1) {
+                    const uint32_t dkey = depth_store_key(fminf(T.d[0], fminf(T.d[1], T.d[2])), lp, u24);
+                    const int tx0 = ix0 >> sh, tx1 = ix1 >> sh, ty0 = iy0 >> sh, ty1 = iy1 >> sh;
+                    const int wx = tx1 - tx0 + 1, ntiles = wx * (ty1 - ty0 + 1);
+                    if (ntiles > kBigTiles) {
+                        const unsigned int pos = atomicAdd(&B.ctr->n_big, 1u);
+                        if (pos < (uint64_t)W->big_cap) B.big[pos] = make_uint2((uint32_t)t, (uint32_t)js);
+                    } else {
 #pragma unroll
-                    for (int q = 0; q < kBigTiles; ++q) {
-                        te[q] = 0u;
-                        if (q >= ntiles) continue;
-                        const int ty = ty0 + q / wx, tx = tx0 + q % wx;
-                        if (ntiles > 1 && !rect_overlap(e, tx * TS + 0.5f, tx * TS + TS - 0.5f, ty * TS + 0.5f,
-                                                        ty * TS + TS - 0.5f))
-                            continue;
-                        const uint32_t x = (uint32_t)(te0 + (int64_t)ty * J.tiles_x + tx);
-                        // unoccupied tile (far 0) or triangle wholly behind its far plane
-                        if (!(dkey < B.t_far[x])) continue;
-                        atomicAdd(&B.t_cnt[x], 1u);
-                        te[q] = x;
-                        valid |= 1u << q;
+                        for (int q = 0; q < kBigTiles; ++q) {
+                            te[q] = 0u;
+                            if (q >= ntiles) continue;
+                            const int ty = ty0 + q / wx, tx = tx0 + q % wx;
+                            if (ntiles > 1 && !rect_overlap(e, tx * TS + 0.5f, tx * TS + TS - 0.5f, ty * TS + 0.5f,
+                                                            ty * TS + TS - 0.5f))
+                                continue;
+                            const uint32_t x = (uint32_t)(te0 + (int64_t)ty * J.tiles_x + tx);
+                            // unoccupied tile (far 0) or triangle wholly behind its far plane
+                            if (!(dkey < B.t_far[x])) continue;
+                            atomicAdd(&B.t_cnt[x], 1u);
+                            te[q] = x;
+                            valid |= 1u << q;
+                        }
                     }
                 }
             }
+            append_pairs(B, W, te, valid, (uint32_t)t);
         }
-        append_pairs(B, W, te, valid, (uint32_t)t);
     }
 }
 

@@ -147,7 +147,7 @@ struct WaveDev {
     int32_t want_bits;  // per-sample flags requested by some job of the wave
     int32_t profile;    // count work (texel visits, sample tests) into Counters
     int64_t tot_js, tot_te, tot_ms, tot_cs;
-    int64_t tot_win, tot_mod, tot_tri, tot_epi;  // tot_tri: (meshlet, step) warp items
+    int64_t tot_win, tot_mod, tot_tri, tot_epi;  // tot_tri: (group of 32 meshlets, step) warp items
     int64_t tot_ss, tot_sq;                      // (step, substring) and (step, string) entries
     int64_t tot_heat;                            // heat-map bins over the jobs
     int64_t tot_sa;                              // (step, array) entries

@@ -1032,7 +1032,15 @@ struct RecvSm {
     int item_pref;             // (row, cell column) items of the receivers staged before this one
 };
 
-constexpr int kRasterThreads = 256;  // threads of a k_raster_test block
+// Threads of a k_raster_test block and its register budget (blocks an SM):
+// 32-texel tiles have small shared tiles, and the plants with many heavy
+// 32-texel tiles keep more of them in flight with 128-thread blocks (fewer
+// threads wait at each of a tile's barriers).
+template <int TS>
+struct HeavyCfg {
+    static constexpr int threads = TS == 32 ? 128 : 256;
+    static constexpr int min_blocks = TS == 32 ? 8 : 4;
+};
 
 template <int TS>
 struct RasterSm {
@@ -1938,8 +1946,8 @@ __device__ int setup_sample_tris(TileSm<TS>& sm, const JobDev& J, const Buffers&
 }
 
 template <int TS, bool PROF>
-__global__ void __launch_bounds__(kRasterThreads, 4) k_raster_test(const WaveDev* __restrict__ W,
-                                                                   const JobDev* __restrict__ jobs, Buffers B)
+__global__ void __launch_bounds__(HeavyCfg<TS>::threads, HeavyCfg<TS>::min_blocks)
+    k_raster_test(const WaveDev* __restrict__ W, const JobDev* __restrict__ jobs, Buffers B)
 {
     extern __shared__ __align__(16) unsigned char tile_smem[];  // sizeof(TileSm<TS>), set at launch
     TileSm<TS>& sm = *reinterpret_cast<TileSm<TS>*>(tile_smem);
@@ -2911,7 +2919,8 @@ static void launch_tile_kernels(const WaveDev* W, const JobDev* d_jobs, const Bu
     if (cfg.fused) {
         k_tile_warp<TS, PROF><<<sm * 6, kTileWarps * 32, 0, cfg.stream>>>(W, d_jobs, b);
         if (cfg.ev) cudaEventRecord(cfg.ev[3], cfg.stream);
-        k_raster_test<TS, PROF><<<sm * tile_blocks<TS>(), kRasterThreads, tsm, cfg.stream>>>(W, d_jobs, b);
+        k_raster_test<TS, PROF><<<sm * (TS == 32 ? HeavyCfg<TS>::min_blocks : tile_blocks<TS>()), HeavyCfg<TS>::threads,
+                                   tsm, cfg.stream>>>(W, d_jobs, b);
     } else {
         k_raster_map<TS, PROF><<<sm * tile_blocks<TS>(), 256, tsm, cfg.stream>>>(W, d_jobs, b);
         if (cfg.ev) cudaEventRecord(cfg.ev[3], cfg.stream);

@@ -54,7 +54,10 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="facade", choices=["facade", "tracker", "tiny"])
     ap.add_argument("--path", default="fused", choices=["fused", "map"])
-    ap.add_argument("--chunk", type=int, default=0, help="sun steps per wave (0 = library default)")
+    ap.add_argument("--chunk", type=int, default=0, help="sun steps per wave (0 = autotuned)")
+    ap.add_argument("--tile", type=int, default=0, choices=[0, 32, 64, 128],
+                    help="rasteriser tile side (0 = autotuned); with --chunk, the autotuner is skipped "
+                         "(profiling runs pin the configuration the plain bench chose)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true", help="skip the batched and served sections")
@@ -392,7 +395,11 @@ def run_ours(args, rank, world, dist):
     # timed trials, not part of the timed region); the map resolution is the
     # workload's own
     from paper_1410_5780_gb300 import autotune
-    tuned = autotune.autotune(w, device=dev, cache=None, n_windows=6)
+    if args.tile and args.chunk:
+        tuned = {"tile": args.tile, "chunk_steps": args.chunk, "bin_capacity": 0}  # 0: the library's pool
+    else:
+        tuned = autotune.autotune(w, device=dev, cache=None, n_windows=6)
+        tuned["tile"] = args.tile or tuned["tile"]
     chunk = args.chunk or tuned["chunk_steps"]
     ctx = pv3d.Context(device=dev, map_res=w.map_res, chunk_steps=chunk, tile=tuned["tile"],
                        bin_capacity=tuned["bin_capacity"])

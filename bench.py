@@ -271,10 +271,10 @@ def batched_section(dev: int, n_scenes: int) -> dict:
 def extensions_section(ctx, gid, w, stream) -> dict:
     """The model extensions on the bench workload (device time of one
     full-year evaluation each, CUDA events on the evaluation's stream): series
-    strings of 5 modules along each floor, the azimuth-zenith sky map
-    (36 x 9 bins), diffuse shading (sky view over 9 x 36 patches, then a year
-    with the diffuse term shaded), and the clear-sky sun table made on the
-    device."""
+    strings of 5 modules along each floor, one 1024-texel light window per
+    string (window groups), the azimuth-zenith sky map (36 x 9 bins), diffuse
+    shading (sky view over 9 x 36 patches, then a year with the diffuse term
+    shaded), and the clear-sky sun table made on the device."""
     import torch
     from paper_1410_5780_gb300 import pv3d
 
@@ -303,6 +303,12 @@ def extensions_section(ctx, gid, w, stream) -> dict:
     se, seu = r["string_energy"].double().sum().item(), r["string_energy_unshaded"].double().sum().item()
     out["strings"] = {"ms": t, "strings": int(len(np.unique(np.arange(gen.n_modules) // 5))),
                       "loss_pct": 100.0 * (1.0 - se / seu)}
+    t, r = timed(lambda: ctx.evaluate(g2, n=w.n, map_res=1024, stream=stream.cuda_stream,
+                                      outputs=("energy", "energy_unshaded"),
+                                      window_groups=pv3d.PV3D_WINDOWS_PER_STRING))
+    e, eu = r["energy"].double().sum().item(), r["energy_unshaded"].double().sum().item()
+    out["windows_per_string"] = {"ms": t, "windows": out["strings"]["strings"], "map_res": 1024,
+                                 "waves": int(r["waves"]), "loss_pct": 100.0 * (1.0 - e / eu)}
     t, r = timed(lambda: ctx.evaluate(g2, n=w.n, map_res=w.map_res, stream=stream.cuda_stream,
                                       outputs=("energy",), heat_bins=(36, 9)))
     out["sky_map"] = {"ms": t, "bins": [36, 9], "occupied_bins": int((r["heat_steps"] > 0).sum().item())}

@@ -54,6 +54,23 @@ extern "C" {
 #define PV3D_PATH_FUSED   0
 #define PV3D_PATH_MAP     1
 
+/* ---- light windows (pv3d_eval_opts.window_groups) -------------------------
+ * Section 2, step 3 limits the sun's field of view to the PV generator of
+ * interest.  ONE: one window per sun step around all modules of the
+ * generator.  The other modes give each group of modules its own window per
+ * step (finer texels at the same map_res): the modules of one tracker, of one
+ * series string (string_id) or of one inverter input (array_id); fixed
+ * modules under PER_TRACKER form one group.  A group's modules must be
+ * consecutive in module order (else PV3D_E_INVALID).  Every module of the
+ * generator, in or out of the group, shades the group's samples.  map_res is
+ * the side of each group's window; the steps per wave shrink so that a wave
+ * holds at most 2^26 (group, step, tile) entries.  pv3d_evaluate only; string,
+ * array and heat-map outputs are rejected with groups. */
+#define PV3D_WINDOWS_ONE          0
+#define PV3D_WINDOWS_PER_TRACKER  1
+#define PV3D_WINDOWS_PER_STRING   2
+#define PV3D_WINDOWS_PER_ARRAY    3
+
 typedef struct pv3d_ctx pv3d_ctx;
 
 /* Context options.  Zero fields take the defaults in brackets. */
@@ -126,7 +143,8 @@ typedef struct pv3d_eval_opts {
     int32_t path;              /* PV3D_PATH_FUSED or PV3D_PATH_MAP [FUSED] */
     int32_t profile;           /* bit 0: time each stage with CUDA events; bit 1: count work (pv3d_last_profile) [0] */
     int32_t diffuse_shading;   /* 1: shade the diffuse term of each cell by its pv3d_sky_view fraction [0] */
-    int32_t reserved[5];
+    int32_t window_groups;     /* PV3D_WINDOWS_*: one light window, or one per tracker, string or array [ONE] */
+    int32_t reserved[4];
 } pv3d_eval_opts;
 
 /*

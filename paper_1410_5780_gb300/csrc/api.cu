@@ -75,6 +75,19 @@ struct GenH {
     int32_t max_arr_sub = 0;        // substrings of the largest array
     int32_t* d_arr_off = nullptr;   // [n_arr + 1]
     int32_t* d_arr_strs = nullptr;  // [n_str]
+    // window groups: each module's string and array ids, and the world boxes of
+    // the occluder meshlets (16 modules each, boxes that hold them under any pose)
+    std::vector<int32_t> mod_string, mod_array;
+    float4* d_oml = nullptr;
+    int32_t n_oml = 0;
+    // per grouping mode: group g holds modules [m0[g], m0[g + 1]) and cells
+    // [c0[g], c0[g + 1]); module tables with group-local cell numbers
+    struct WinGroups {
+        std::vector<int32_t> m0, c0;
+        ModuleDev* d_mods = nullptr;
+        int32_t* d_cell_mod = nullptr;
+    };
+    std::map<int, WinGroups> wgroups;
     size_t bytes = 0;
 };
 
@@ -205,9 +218,13 @@ static void free_gen(GenH& g)
 {
     void* ps[] = {g.d_mods, g.d_cell_mod, g.d_lay_sub, g.d_lay_off, g.d_lay_nk, g.d_lay_nk_off, g.d_pivots,
                   g.d_sun, g.d_dni, g.d_dhi, g.d_dt, g.d_poses, g.d_str_sub, g.d_sub_base, g.d_sub_nk,
-                  g.d_sub_mod, g.d_fdiff, g.d_arr_off, g.d_arr_strs};
+                  g.d_sub_mod, g.d_fdiff, g.d_arr_off, g.d_arr_strs, g.d_oml};
     for (void* p : ps)
         if (p) cudaFree(p);
+    for (auto& kv : g.wgroups) {
+        if (kv.second.d_mods) cudaFree(kv.second.d_mods);
+        if (kv.second.d_cell_mod) cudaFree(kv.second.d_cell_mod);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -388,9 +405,12 @@ extern "C" int pv3d_generator_define(pv3d_ctx* c, uint32_t scene_id, const pv3d_
     double glo[3] = {INFINITY, INFINITY, INFINITY}, ghi[3] = {-INFINITY, -INFINITY, -INFINITY};
     std::vector<int32_t> cell_mod;
     g.mods_h.resize(n_mods);
+    std::vector<double> mlo((size_t)3 * n_mods), mhi((size_t)3 * n_mods);  // module world boxes
     int32_t cell = 0;
     for (int32_t m = 0; m < n_mods; ++m) {
         const pv3d_module& P = mods[m];
+        g.mod_string.push_back(P.string_id);
+        g.mod_array.push_back(P.array_id);
         if (!finite3(P.origin) || !finite3(P.u) || !finite3(P.v) || !std::isfinite(P.pitch) || !(P.pitch > 0))
             return fail(c, PV3D_E_INVALID, "module %d: non-finite geometry", m);
         double uu = (double)P.u[0] * P.u[0] + (double)P.u[1] * P.u[1] + (double)P.u[2] * P.u[2];
@@ -423,17 +443,25 @@ extern "C" int pv3d_generator_define(pv3d_ctx* c, uint32_t scene_id, const pv3d_
             for (int q = 0; q < 3; ++q) cx[k][q] = P.origin[q] + a * P.u[q] + b * P.v[q];
         }
         if (P.tracker < 0) {
+            for (int q = 0; q < 3; ++q) { mlo[3 * m + q] = INFINITY; mhi[3 * m + q] = -INFINITY; }
             for (int k = 0; k < 4; ++k)
-                for (int q = 0; q < 3; ++q) { glo[q] = std::min(glo[q], cx[k][q]); ghi[q] = std::max(ghi[q], cx[k][q]); }
+                for (int q = 0; q < 3; ++q) {
+                    mlo[3 * m + q] = std::min(mlo[3 * m + q], cx[k][q]);
+                    mhi[3 * m + q] = std::max(mhi[3 * m + q], cx[k][q]);
+                }
         } else {
             double reach = 0;
             for (int k = 0; k < 4; ++k)
                 reach = std::max(reach, std::sqrt(cx[k][0] * cx[k][0] + cx[k][1] * cx[k][1] + cx[k][2] * cx[k][2]));
             const float* pv = trackers[P.tracker].pivot;
             for (int q = 0; q < 3; ++q) {
-                glo[q] = std::min(glo[q], pv[q] - reach);
-                ghi[q] = std::max(ghi[q], pv[q] + reach);
+                mlo[3 * m + q] = pv[q] - reach;
+                mhi[3 * m + q] = pv[q] + reach;
             }
+        }
+        for (int q = 0; q < 3; ++q) {
+            glo[q] = std::min(glo[q], mlo[3 * m + q]);
+            ghi[q] = std::max(ghi[q], mhi[3 * m + q]);
         }
     }
     g.C = cell;
@@ -527,8 +555,23 @@ extern "C" int pv3d_generator_define(pv3d_ctx* c, uint32_t scene_id, const pv3d_
         }
         arr_off.push_back((int32_t)arr_strs.size());
     }
+    // occluder meshlets for window groups: modules 16q .. 16q + 15 (triangles
+    // 32q .. 32q + 31), boxes widened by a millimetre for the rounding of poses
+    g.n_oml = (n_mods + 15) / 16;
+    std::vector<float4> oml((size_t)2 * g.n_oml);
+    for (int32_t q = 0; q < g.n_oml; ++q) {
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int32_t m = 16 * q; m < std::min(n_mods, 16 * q + 16); ++m)
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = std::min(lo[a], mlo[3 * m + a]);
+                hi[a] = std::max(hi[a], mhi[3 * m + a]);
+            }
+        oml[2 * q] = make_float4((float)(lo[0] - 1e-3), (float)(lo[1] - 1e-3), (float)(lo[2] - 1e-3), 0.f);
+        oml[2 * q + 1] = make_float4((float)(hi[0] + 1e-3), (float)(hi[1] + 1e-3), (float)(hi[2] + 1e-3), 0.f);
+    }
     int rc;
-    if ((rc = upload(c, &g.d_mods, g.mods_h.data(), g.mods_h.size())) ||
+    if ((rc = upload(c, &g.d_oml, oml.data(), oml.size())) ||
+        (rc = upload(c, &g.d_mods, g.mods_h.data(), g.mods_h.size())) ||
         (rc = upload(c, &g.d_cell_mod, cell_mod.data(), cell_mod.size())) ||
         (rc = upload(c, &g.d_lay_sub, lay_sub.data(), lay_sub.size())) ||
         (rc = upload(c, &g.d_lay_off, lay_off.data(), lay_off.size())) ||
@@ -545,7 +588,7 @@ extern "C" int pv3d_generator_define(pv3d_ctx* c, uint32_t scene_id, const pv3d_
         return rc;
     }
     g.bytes = g.mods_h.size() * sizeof(ModuleDev) + cell_mod.size() * 4 + lay_sub.size() * 8 + piv.size() * 4 +
-              (str_sub.size() + sub_base.size() + 2 * sub_nk.size()) * 4;
+              (str_sub.size() + sub_base.size() + 2 * sub_nk.size()) * 4 + oml.size() * sizeof(float4);
     uint32_t id = c->next_id++;
     c->gens[id] = std::move(g);
     *gen_id = id;
@@ -760,7 +803,7 @@ extern "C" int pv3d_set_sun_clear_sky(pv3d_ctx* c, uint32_t gen_id, const pv3d_s
 namespace {
 
 struct EvalSetup {
-    int n, R, K, tile, fused, profile, count, strings, heat, diffuse, arrays;
+    int n, R, K, tile, fused, profile, count, strings, heat, diffuse, arrays, groups;
     int64_t b, e;
     float i_ref, v_cell, v_diode;
 };
@@ -804,6 +847,57 @@ static int check_eval(pv3d_ctx* c, const GenH& g, const pv3d_eval_opts* o, const
     if (es.heat && (out->heat_az_bins < 1 || out->heat_az_bins > 1024 || out->heat_zen_bins < 1 ||
                     out->heat_zen_bins > 1024 || !out->heat_energy || !out->heat_energy_unshaded || !out->heat_steps))
         return fail(c, PV3D_E_INVALID, "heat map: bin counts 1..1024 and all three arrays");
+    es.groups = d.window_groups;
+    if (es.groups < PV3D_WINDOWS_ONE || es.groups > PV3D_WINDOWS_PER_ARRAY)
+        return fail(c, PV3D_E_INVALID, "unknown window_groups mode %d", es.groups);
+    if (es.groups && (es.strings || es.heat))
+        return fail(c, PV3D_E_INVALID, "window groups: string, array and heat-map outputs are not supported");
+    return PV3D_OK;
+}
+
+// The window groups of generator g under `mode` (PV3D_WINDOWS_PER_*): runs of
+// consecutive modules with the same tracker, string or array id.  Built on
+// first use and kept with the generator.
+static int window_groups(pv3d_ctx* c, GenH& g, int mode, const GenH::WinGroups** out)
+{
+    auto it = g.wgroups.find(mode);
+    if (it != g.wgroups.end()) {
+        *out = &it->second;
+        return PV3D_OK;
+    }
+    auto key = [&](int32_t m) {
+        return mode == PV3D_WINDOWS_PER_TRACKER ? std::max(g.mods_h[m].tracker, -1)
+                                                : (mode == PV3D_WINDOWS_PER_STRING ? g.mod_string[m] : g.mod_array[m]);
+    };
+    GenH::WinGroups wg;
+    std::vector<int32_t> seen;
+    for (int32_t m = 0; m < g.M; ++m)
+        if (m == 0 || key(m) != key(m - 1)) {
+            if (std::find(seen.begin(), seen.end(), key(m)) != seen.end())
+                return fail(c, PV3D_E_INVALID, "window groups: the modules of group %d are not consecutive", key(m));
+            seen.push_back(key(m));
+            wg.m0.push_back(m);
+            wg.c0.push_back(g.mods_h[m].cell_base);
+        }
+    wg.m0.push_back(g.M);
+    wg.c0.push_back(g.C);
+    // module tables and cell -> module maps numbered within each group
+    std::vector<ModuleDev> local = g.mods_h;
+    std::vector<int32_t> cell_mod((size_t)g.C);
+    for (size_t q = 0; q + 1 < wg.m0.size(); ++q)
+        for (int32_t m = wg.m0[q]; m < wg.m0[q + 1]; ++m) {
+            local[m].cell_base -= wg.c0[q];
+            for (int32_t k = 0; k < local[m].cu * local[m].cv; ++k)
+                cell_mod[(size_t)g.mods_h[m].cell_base + k] = m - wg.m0[q];
+        }
+    int rc;
+    if ((rc = upload(c, &wg.d_mods, local.data(), local.size())) ||
+        (rc = upload(c, &wg.d_cell_mod, cell_mod.data(), cell_mod.size()))) {
+        if (wg.d_mods) cudaFree(wg.d_mods);
+        return rc;
+    }
+    g.bytes += local.size() * sizeof(ModuleDev) + cell_mod.size() * 4;
+    *out = &(g.wgroups[mode] = std::move(wg));
     return PV3D_OK;
 }
 
@@ -858,6 +952,8 @@ static JobDev make_job(pv3d_ctx* c, const GenH& g, const SceneH& s, const EvalSe
     J.out_power_u = pwu;
     J.out_counts = cnt;
     J.out_bits = bits;
+    J.out_mstride = g.M;
+    J.out_cstride = g.C;
     if (es.strings) {
         J.n_str = (int32_t)g.str_ids.size();
         J.n_sub_tot = g.n_sub_tot;
@@ -921,7 +1017,7 @@ static WaveDev pack_wave(std::vector<JobDev>& jobs, size_t first, size_t last, i
         W.tot_cs += (int64_t)J.k * J.n_cells;
         W.tot_win += (int64_t)J.k * groups;
         W.tot_mod += (int64_t)J.k * J.n_mods;
-        W.tot_tri += (((int64_t)J.n_ml + (J.n_mtris + 31) / 32 + 31) / 32) * J.k;  // groups of 32 meshlets
+        W.tot_tri += (((int64_t)J.n_ml + J.n_oml + (J.n_mtris + 31) / 32 + 31) / 32) * J.k;  // groups of 32 meshlets
         W.tot_epi += (J.kahan_cell ? (int64_t)J.n_cells : 0) + J.n_mods + J.n_str + J.n_arr;
         W.tot_sa += (int64_t)J.k * J.n_arr;
         W.tot_ss += (int64_t)J.k * (J.n_str ? J.n_sub_tot : 0);
@@ -1209,17 +1305,52 @@ static int evaluate_plain(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o,
     double* h_eu = es.heat ? h_e + n_bins : nullptr;
     int32_t* h_n = es.heat ? (int32_t*)(h_eu + n_bins) : nullptr;
 
-    // plan: one job per wave
+    // plan: a wave per chunk of steps, one job per window group (or one job)
+    const GenH::WinGroups* wg = nullptr;
+    if (es.groups && (rc = window_groups(c, g, es.groups, &wg))) return rc;
+    const int n_groups = wg ? (int)wg->m0.size() - 1 : 1;
+    int64_t K = es.K;
+    if (wg) {  // at most 2^26 (group, step, tile) entries a wave
+        const int64_t tiles = (int64_t)(es.R / es.tile) * (es.R / es.tile);
+        K = std::max<int64_t>(1, std::min<int64_t>(K, (int64_t(1) << 26) / ((int64_t)n_groups * tiles)));
+    }
     std::vector<JobDev> jobs;
     std::vector<WaveDev> waves;
-    for (int64_t s0 = es.b; s0 < es.e; s0 += es.K) {
-        int k = (int)std::min<int64_t>(es.K, es.e - s0);
-        jobs.push_back(make_job(c, g, s, es, s0, k, (float2*)c->kahan_mod.p, d_cl ? (float2*)c->kahan_cell.p : nullptr,
+    for (int64_t s0 = es.b; s0 < es.e; s0 += K) {
+        int k = (int)std::min<int64_t>(K, es.e - s0);
+        const size_t first = jobs.size();
+        for (int q = 0; q < n_groups; ++q) {
+            JobDev J = make_job(c, g, s, es, s0, k, (float2*)c->kahan_mod.p, d_cl ? (float2*)c->kahan_cell.p : nullptr,
                                 d_p, d_pu,
                                 d_cnt, d_bits, (float2*)c->kahan_str.p, d_sp, d_spu, h_e, h_eu, h_n,
                                 es.heat ? out->heat_az_bins : 0, es.heat ? out->heat_zen_bins : 0,
-                                (float2*)c->kahan_arr.p, d_ap, d_apu));
-        waves.push_back(pack_wave(jobs, jobs.size() - 1, jobs.size(), tile_sh, u24, es.fused, es.count));
+                                (float2*)c->kahan_arr.p, d_ap, d_apu);
+            if (wg) {
+                // the group's modules and cells; every module of the generator
+                // is an occluder (none when the generator is one plane)
+                const int32_t m0 = wg->m0[q], c0 = wg->c0[q];
+                J.mods = wg->d_mods + m0;
+                J.n_mods = wg->m0[q + 1] - m0;
+                J.n_cells = wg->c0[q + 1] - c0;
+                J.cell_mod = wg->d_cell_mod + c0;
+                J.kahan_mod += 2 * m0;
+                if (J.kahan_cell) J.kahan_cell += c0;
+                if (J.out_power) J.out_power += m0;
+                if (J.out_power_u) J.out_power_u += m0;
+                if (J.out_counts) J.out_counts += c0;
+                if (J.out_bits) J.out_bits += c0;
+                if (J.fdiff) J.fdiff += c0;
+                J.n_mtris = 0;
+                if (!g.coplanar) {
+                    J.occ_mods = g.d_mods;
+                    J.n_occ = g.M;
+                    J.oml_box = g.d_oml;
+                    J.n_oml = g.n_oml;
+                }
+            }
+            jobs.push_back(J);
+        }
+        waves.push_back(pack_wave(jobs, first, jobs.size(), tile_sh, u24, es.fused, es.count));
     }
     int64_t mjs = 0, mte = 0, mms = 0, mcs = 0, mss = 0, msq = 0, msa = 0;
     for (auto& W : waves) {
@@ -1739,6 +1870,7 @@ extern "C" int pv3d_submit(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o
     if (o && o->path == PV3D_PATH_MAP) return fail(c, PV3D_E_INVALID, "served requests use the fused path");
     if (r->es.strings || r->es.heat || r->es.arrays)
         return fail(c, PV3D_E_INVALID, "string and sky-map outputs are produced by pv3d_evaluate only");
+    if (r->es.groups) return fail(c, PV3D_E_INVALID, "window groups are evaluated by pv3d_evaluate only");
     r->gen_id = gen_id;
     r->opts = o ? *o : pv3d_eval_opts{};
     r->out = out;

@@ -501,10 +501,32 @@ struct TriT {
 };
 
 // Triangle `t` of job J (scene triangle, or module triangle after the scene's)
-// at local step ls in texel coordinates.
+// at local step ls in texel coordinates.  Module triangles come from the
+// job's own module frames (ModStep), or, for a window group, from every
+// module of the generator posed for the step and projected like the scene.
 __device__ __forceinline__ void tri_texel(const JobDev& J, const Buffers& B, const LightParams& lp,
                                           int ls, int t, TriT& T)
 {
+    if (t >= J.n_tris && J.occ_mods) {
+        const int q = t - J.n_tris;
+        float3 o, u, v;
+        posed_module(J, J.occ_mods[q >> 1], J.step0 + ls, o, u, v);
+        const ModuleDev& M = J.occ_mods[q >> 1];
+        const float lu = M.cu * M.pitch, lv = M.cv * M.pitch;
+        // corners c0 = O, c1 = O + lu U, c2 = O + lu U + lv V, c3 = O + lv V;
+        // triangles (c0, c1, c2) and (c0, c2, c3)
+        const float a1 = lu, b1 = (q & 1) ? lv : 0.f;
+        const float a2 = (q & 1) ? 0.f : lu, b2 = lv;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float a = k == 0 ? 0.f : (k == 1 ? a1 : a2), b = k == 0 ? 0.f : (k == 1 ? b1 : b2);
+            const float x = o.x + a * u.x + b * v.x, y = o.y + a * u.y + b * v.y, z = o.z + a * u.z + b * v.z;
+            T.x[k] = (x * lp.ux + y * lp.uy + z * lp.uz - lp.u0) * lp.inv_delta;
+            T.y[k] = (x * lp.vx + y * lp.vy + z * lp.vz - lp.v0) * lp.inv_delta;
+            T.d[k] = -(x * lp.sx + y * lp.sy + z * lp.sz);
+        }
+        return;
+    }
     if (t < J.n_tris) {
         const float4* p = J.tri + 3 * (size_t)t;
 #pragma unroll
@@ -635,14 +657,18 @@ __global__ void __launch_bounds__(256, 4) k_bin(const WaveDev* __restrict__ W, c
         const LightParams& lp = B.lp[js];
         if (!lp.valid) continue;
         const int64_t te0 = J.te_base + (int64_t)ls * J.tiles_x * J.tiles_x;
-        const int n_all = J.n_ml + ((J.n_mtris + 31) >> 5);  // scene meshlets, then module meshlets
-        // this lane's scene meshlet: window test, covered tiles, nearest depth key
+        // scene meshlets, then (window groups) occluder-module meshlets, both
+        // with boxes, then the job's own module meshlets
+        const int n_boxed = J.n_ml + J.n_oml;
+        const int n_all = n_boxed + ((J.n_mtris + 31) >> 5);
+        // this lane's boxed meshlet: window test, covered tiles, nearest depth key
         const int ml = g * 32 + lane;
         int btx0 = 0, btx1 = -1, bty0 = 0, bty1 = -1;
         uint32_t bkey = 0u;
         bool pass = false;
-        if (ml < J.n_ml) {
-            const float4 lo = J.ml_box[2 * ml], hi = J.ml_box[2 * ml + 1];
+        if (ml < n_boxed) {
+            const float4* box = ml < J.n_ml ? J.ml_box + 2 * ml : J.oml_box + 2 * (ml - J.n_ml);
+            const float4 lo = box[0], hi = box[1];
             float xmin = FLT_MAX, xmax = -FLT_MAX, ymin = FLT_MAX, ymax = -FLT_MAX, dmin = FLT_MAX;
 #pragma unroll
             for (int c = 0; c < 8; ++c) {
@@ -676,7 +702,7 @@ __global__ void __launch_bounds__(256, 4) k_bin(const WaveDev* __restrict__ W, c
             const uint32_t mkey = __shfl_sync(0xffffffffu, bkey, q);
             int t;
             bool act;
-            if (mi < J.n_ml) {
+            if (mi < n_boxed) {
                 // the meshlet's nearest point against each covered tile's far plane
                 const int wx = mx1 - mx0 + 1, ntl = wx * (my1 - my0 + 1);
                 bool keep = false;
@@ -690,10 +716,15 @@ __global__ void __launch_bounds__(256, 4) k_bin(const WaveDev* __restrict__ W, c
                     keep = __any_sync(0xffffffffu, kk);
                 }
                 if (!keep) continue;
-                t = mi * 32 + lane;
-                act = t < J.n_tris;
+                if (mi < J.n_ml) {
+                    t = mi * 32 + lane;
+                    act = t < J.n_tris;
+                } else {
+                    t = J.n_tris + (mi - J.n_ml) * 32 + lane;
+                    act = t < J.n_tris + 2 * J.n_occ;
+                }
             } else {
-                t = J.n_tris + (mi - J.n_ml) * 32 + lane;
+                t = J.n_tris + (mi - n_boxed) * 32 + lane;
                 act = t < J.n_tris + J.n_mtris;
             }
             // per lane: the tiles its triangle may shade (at most kBigTiles), in
@@ -2136,8 +2167,8 @@ __device__ __forceinline__ void zero_step_module(const JobDev& J, const ModuleDe
     if (threadIdx.x == 0) { B.ms_p[msi] = 0.f; B.ms_pu[msi] = 0.f; B.ms_beam[msi] = 0.f; }
     for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
         B.cs_cnt[J.cs_base + (int64_t)ls * C + M.cell_base + c] = 0u;
-        if (J.out_counts) J.out_counts[row * C + M.cell_base + c] = 0;
-        if (J.out_bits) J.out_bits[row * C + M.cell_base + c] = 0ull;
+        if (J.out_counts) J.out_counts[row * J.out_cstride + M.cell_base + c] = 0;
+        if (J.out_bits) J.out_bits[row * J.out_cstride + M.cell_base + c] = 0ull;
     }
 }
 
@@ -2162,8 +2193,8 @@ __device__ void pv_module_warp(const JobDev* jobs, int nj, int64_t item, const B
         if (lane == 0) { B.ms_p[msi] = 0.f; B.ms_pu[msi] = 0.f; B.ms_beam[msi] = 0.f; }
         for (int c = lane; c < ncell; c += 32) {
             B.cs_cnt[cbase + c] = 0u;
-            if (J.out_counts) J.out_counts[row * C + M.cell_base + c] = 0;
-            if (J.out_bits) J.out_bits[row * C + M.cell_base + c] = 0ull;
+            if (J.out_counts) J.out_counts[row * J.out_cstride + M.cell_base + c] = 0;
+            if (J.out_bits) J.out_bits[row * J.out_cstride + M.cell_base + c] = 0ull;
         }
         return;
     }
@@ -2177,8 +2208,8 @@ __device__ void pv_module_warp(const JobDev* jobs, int nj, int64_t item, const B
     __syncwarp();
     for (int c = lane; c < ncell; c += 32) {
         const uint32_t cnt = B.cs_cnt[cbase + c];
-        if (J.out_counts) J.out_counts[row * C + M.cell_base + c] = (uint8_t)cnt;
-        if (J.out_bits) J.out_bits[row * C + M.cell_base + c] = B.cs_bits[cbase + c];
+        if (J.out_counts) J.out_counts[row * J.out_cstride + M.cell_base + c] = (uint8_t)cnt;
+        if (J.out_bits) J.out_bits[row * J.out_cstride + M.cell_base + c] = B.cs_bits[cbase + c];
         const float gd = J.fdiff ? diff * (1.f - J.fdiff[M.cell_base + c]) : diff;
         const float G = beam * (1.f - cnt * inv_nn) + gd;
         const float I = J.i_ref * G * 1e-3f;
@@ -2284,14 +2315,13 @@ __global__ void __launch_bounds__(kPvThreads) k_pv(const WaveDev* __restrict__ W
             const int64_t row = (int64_t)(J.out_row0 + __shfl_sync(0xffffffffu, ls, q));
             const bool litq = __shfl_sync(0xffffffffu, (int)lit, q) != 0;
             const float bq = __shfl_sync(0xffffffffu, beam, q), dq = __shfl_sync(0xffffffffu, diff, q);
-            const int C = J.n_cells;
             const float inv_nn = 1.f / J.nn;
             uint32_t* im = imin + q * kPvFastSub;
             if (!litq) {
                 for (int c = lane; c < nc; c += 32) {
                     B.cs_cnt[cb + c] = 0u;
-                    if (J.out_counts) J.out_counts[row * C + c0 + c] = 0;
-                    if (J.out_bits) J.out_bits[row * C + c0 + c] = 0ull;
+                    if (J.out_counts) J.out_counts[row * J.out_cstride + c0 + c] = 0;
+                    if (J.out_bits) J.out_bits[row * J.out_cstride + c0 + c] = 0ull;
                 }
                 continue;
             }
@@ -2310,8 +2340,8 @@ __global__ void __launch_bounds__(kPvThreads) k_pv(const WaveDev* __restrict__ W
                 for (int u = 0; u < kPvUnroll; ++u) {
                     const int c = cr + 32 * u;
                     if (c >= nc) continue;
-                    if (J.out_counts) J.out_counts[row * C + c0 + c] = (uint8_t)cnt[u];
-                    if (J.out_bits) J.out_bits[row * C + c0 + c] = B.cs_bits[cb + c];
+                    if (J.out_counts) J.out_counts[row * J.out_cstride + c0 + c] = (uint8_t)cnt[u];
+                    if (J.out_bits) J.out_bits[row * J.out_cstride + c0 + c] = B.cs_bits[cb + c];
                     const float gd = J.fdiff ? dq * (1.f - J.fdiff[c0 + c]) : dq;
                     const float G = bq * (1.f - cnt[u] * inv_nn) + gd;
                     const float I = J.i_ref * G * 1e-3f;
@@ -2433,8 +2463,8 @@ __global__ void __launch_bounds__(kPvThreads) k_sample(const WaveDev* __restrict
         for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
             const uint32_t cnt = s_cnt[c];
             B.cs_cnt[J.cs_base + (int64_t)ls * C + M.cell_base + c] = cnt;
-            if (J.out_counts) J.out_counts[row * C + M.cell_base + c] = (uint8_t)cnt;
-            if (J.out_bits) J.out_bits[row * C + M.cell_base + c] = s_bits[c];
+            if (J.out_counts) J.out_counts[row * J.out_cstride + M.cell_base + c] = (uint8_t)cnt;
+            if (J.out_bits) J.out_bits[row * J.out_cstride + M.cell_base + c] = s_bits[c];
         }
         module_pv(J, M, s, lp, s_cnt, s_imin, B, msi);
         __syncthreads();
@@ -2715,8 +2745,8 @@ __global__ void __launch_bounds__(256) k_epilogue(const WaveDev* __restrict__ W,
                 } else if (kind == 1) {
                     const int64_t msi = J.ms_base + (int64_t)ls * Mn + idx;
                     const float p = B.ms_p[msi], pu = B.ms_pu[msi];
-                    if (J.out_power) J.out_power[(int64_t)(J.out_row0 + ls) * Mn + idx] = p;
-                    if (J.out_power_u) J.out_power_u[(int64_t)(J.out_row0 + ls) * Mn + idx] = pu;
+                    if (J.out_power) J.out_power[(int64_t)(J.out_row0 + ls) * J.out_mstride + idx] = p;
+                    if (J.out_power_u) J.out_power_u[(int64_t)(J.out_row0 + ls) * J.out_mstride + idx] = pu;
                     x = p * lp.dt;
                     xu = pu * lp.dt;
                 } else if (v && kind == 2) {

@@ -137,6 +137,18 @@ struct JobDev {
     float2* kahan_arr;        // [n_arr][2]
     float* out_arr_power;     // [rows][n_arr]
     float* out_arr_power_u;
+    // row strides of the per-step outputs: out_power rows hold out_mstride
+    // modules, out_counts / out_bits rows out_cstride cells (a job over a
+    // window group writes its columns of the generator's rows)
+    int32_t out_mstride, out_cstride;
+    // window groups: every module of the generator (occ_mods, n_occ) shades
+    // the group's samples, as meshlets of 16 modules (32 triangles) with
+    // world boxes that hold them under any pose (oml_box, n_oml meshlets,
+    // tested like scene meshlets); their triangles follow the scene's.  The
+    // group's own module triangles (n_mtris) are then 0.
+    const ModuleDev* occ_mods;
+    const float4* oml_box;    // [n_oml][2] world lo, hi
+    int32_t n_occ, n_oml;
 };
 
 struct WaveDev {

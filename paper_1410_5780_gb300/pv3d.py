@@ -32,6 +32,10 @@ PV3D_DEPTH_F32 = 0
 PV3D_DEPTH_U24 = 1
 PV3D_PATH_FUSED = 0
 PV3D_PATH_MAP = 1
+PV3D_WINDOWS_ONE = 0
+PV3D_WINDOWS_PER_TRACKER = 1
+PV3D_WINDOWS_PER_STRING = 2
+PV3D_WINDOWS_PER_ARRAY = 3
 
 EXPORTED = ("pv3d_create", "pv3d_destroy", "pv3d_last_error", "pv3d_scene_load", "pv3d_generator_define",
             "pv3d_set_poses", "pv3d_set_sun", "pv3d_evaluate", "pv3d_submit", "pv3d_poll", "pv3d_release",
@@ -65,7 +69,8 @@ class pv3d_eval_opts(C.Structure):
     _fields_ = [("samples_per_side", C.c_int32), ("map_res", C.c_int32), ("step_begin", C.c_int64),
                 ("step_end", C.c_int64), ("i_ref", C.c_float), ("v_cell", C.c_float), ("v_diode", C.c_float),
                 ("chunk_steps", C.c_int32), ("stream", C.c_void_p), ("path", C.c_int32),
-                ("profile", C.c_int32), ("diffuse_shading", C.c_int32), ("reserved", C.c_int32 * 5)]
+                ("profile", C.c_int32), ("diffuse_shading", C.c_int32), ("window_groups", C.c_int32),
+                ("reserved", C.c_int32 * 4)]
 
 
 class pv3d_profile(C.Structure):
@@ -313,10 +318,11 @@ class Context:
 
     # ---- steps 3 and 4 -----------------------------------------------------
     def _opts(self, n, map_res, step_begin, step_end, chunk_steps, stream, i_ref, v_cell, v_diode, path=0,
-              profile=0, diffuse=False):
+              profile=0, diffuse=False, window_groups=0):
         return pv3d_eval_opts(samples_per_side=n, map_res=map_res, step_begin=step_begin, step_end=step_end,
                               chunk_steps=chunk_steps, stream=stream, i_ref=i_ref, v_cell=v_cell, v_diode=v_diode,
-                              path=path, profile=profile, diffuse_shading=int(diffuse))
+                              path=path, profile=profile, diffuse_shading=int(diffuse),
+                              window_groups=int(window_groups))
 
     def _alloc(self, gen_id, step_begin, step_end, outputs, device, heat_bins=None):
         if gen_id not in self._gens:  # let the library report the unknown id
@@ -359,16 +365,18 @@ class Context:
                  chunk_steps: int = 0, outputs=("energy", "energy_unshaded"), device: bool = True,
                  stream=None, i_ref: float = 0.0, v_cell: float = 0.0, v_diode: float = 0.0,
                  path: int = PV3D_PATH_FUSED, profile: bool = False, heat_bins=None,
-                 diffuse_shading: bool = False) -> dict:
+                 diffuse_shading: bool = False, window_groups: int = PV3D_WINDOWS_ONE) -> dict:
         """pv3d_evaluate.  Returns the requested outputs (torch tensors on the
         device if ``device`` else numpy arrays) plus the counters.  ``heat_bins``
-        = (azimuth bins, zenith bins) adds the sky map of the effective shading."""
+        = (azimuth bins, zenith bins) adds the sky map of the effective shading;
+        ``window_groups`` (PV3D_WINDOWS_*) gives each tracker, string or array
+        its own light window of side ``map_res``."""
         if stream is None and device:
             import torch
             stream = torch.cuda.current_stream(self.device).cuda_stream
         res, arrays = self._alloc(gen_id, step_begin, step_end, outputs, device, heat_bins)
         o = self._opts(n, map_res, step_begin, step_end, chunk_steps, stream, i_ref, v_cell, v_diode, path,
-                       int(profile), diffuse_shading)
+                       int(profile), diffuse_shading, window_groups)
         self._check(self.lib.pv3d_evaluate(self.h, gen_id, C.byref(o), C.byref(res)))
         arrays.update(tests=res.tests, steps_lit=res.steps_lit, device_ms=res.device_ms, waves=res.waves,
                       nonempty_tiles=res.nonempty_tiles, binned_tris=res.binned_tris,

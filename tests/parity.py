@@ -19,10 +19,11 @@ LOSS_PP = 0.1
 
 def run_gpu(ctx, gid, w, step_begin=0, step_end=0, outputs=("energy", "energy_unshaded", "power",
                                                                    "power_unshaded", "sample_bits", "cell_counts"),
-            chunk_steps=0, device=True, path=0):
+            chunk_steps=0, device=True, path=0, window_groups=0, map_res=0):
     import torch
-    r = ctx.evaluate(gid, n=w.n, map_res=w.map_res, step_begin=step_begin, step_end=step_end,
-                     chunk_steps=chunk_steps, outputs=outputs, device=device, path=path)
+    r = ctx.evaluate(gid, n=w.n, map_res=map_res or w.map_res, step_begin=step_begin, step_end=step_end,
+                     chunk_steps=chunk_steps, outputs=outputs, device=device, path=path,
+                     window_groups=window_groups)
     if device:
         torch.cuda.synchronize()
     out = {}

@@ -202,9 +202,10 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def profiled_traffic(workload: str):
+def profiled_traffic(workload: str, tile: int):
     """DRAM bytes per launch of the tile kernel from the committed ncu summary,
-    if it was taken on the current kernels.cu (else None)."""
+    if it was taken on the current kernels.cu with the same tile side (else
+    None)."""
     import hashlib
     import re
     path = os.path.join(ROOT, "profiles", f"k_tile_warp_{workload}.md")
@@ -215,7 +216,7 @@ def profiled_traffic(workload: str):
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
     except (OSError, AttributeError, ValueError):
         return None
-    return rec["bytes_per_launch"] if rec.get("sha256") == sha else None
+    return rec["bytes_per_launch"] if rec.get("sha256") == sha and rec.get("tile") == tile else None
 
 
 def input_bytes(w) -> int:
@@ -486,9 +487,9 @@ def run_ours(args, rank, world, dist):
                                       "bin_capacity": tuned["bin_capacity"]}),
             "roofline": {"bound": "alu", "kernel": kname,
                          "achieved": achieved, "peak": alu_peak, "unit": "T lane-ops/s",
-                         "frac": achieved / alu_peak, "traffic": profiled_traffic(args.workload),
+                         "frac": achieved / alu_peak, "traffic": profiled_traffic(args.workload, tuned["tile"]),
                          "traffic_source": "DRAM read+write bytes of the first timed launch, ncu capture in "
-                                           f"profiles/k_tile_warp_{args.workload}.md (null if kernels.cu changed)",
+                                           f"profiles/k_tile_warp_{args.workload}.md (null if kernels.cu or the tile side changed)",
                          "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "
                                         "(sm_max_mhz of MEASURED_PEAKS.json)",
                          "work_per_launch": {"fragments": frag, "sample_tests": samp,

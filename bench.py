@@ -332,6 +332,34 @@ def extensions_section(ctx, gid, w, stream) -> dict:
     return out
 
 
+def tracker_windows_section(ctx, gid, w, stream, n_steps: int = 1024) -> dict:
+    """One light window per tracker on the tracker plant, on a bounded sample
+    (the first ``n_steps`` quarter-hour steps, device time): the plant-wide
+    window at the workload's resolution against per-tracker windows of 256 and
+    512 texels (every tracker's table still shades the others)."""
+    import torch
+    from paper_1410_5780_gb300 import pv3d
+
+    out = {"steps": n_steps, "trackers": int(w.gen.pivots.shape[0])}
+    for name, res, mode in (("plant_window", w.map_res, pv3d.PV3D_WINDOWS_ONE),
+                            ("per_tracker_256", 256, pv3d.PV3D_WINDOWS_PER_TRACKER),
+                            ("per_tracker_512", 512, pv3d.PV3D_WINDOWS_PER_TRACKER)):
+        def run():
+            return ctx.evaluate(gid, n=w.n, map_res=res, step_end=n_steps, stream=stream.cuda_stream,
+                                outputs=("energy", "energy_unshaded"), window_groups=mode)
+        run()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        r = run()
+        b.record(stream)
+        torch.cuda.synchronize()
+        e, eu = r["energy"].double().sum().item(), r["energy_unshaded"].double().sum().item()
+        out[name] = {"map_res": res, "ms": a.elapsed_time(b), "tests_per_s": r["tests"] / (a.elapsed_time(b) * 1e-3),
+                     "waves": int(r["waves"]), "loss_pct": 100.0 * (1.0 - e / eu)}
+    return out
+
+
 def serving_section(dev: int, n_requests: int) -> dict:
     """configs[4] on a bounded sample: requests over a pool of resident scenes
     (1e3-5.2e5 triangles), each a random range of 100-4400 sun steps.  The
@@ -522,6 +550,8 @@ def run_ours(args, rank, world, dist):
                            "d2h_bytes_per_step": d2h, "includes": "scene/generator/sun upload from host arrays, "
                            "evaluation, host read-back of the energies"}
 
+    if rank == 0 and not args.no_serving and args.workload == "tracker":
+        line["extensions"] = tracker_windows_section(ctx, gid, w, stream)
     if rank == 0 and not args.no_serving and args.workload == "facade":
         line["extensions"] = extensions_section(ctx, gid, w, stream)
         bt = batched_section(dev, args.batch_scenes)

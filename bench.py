@@ -202,21 +202,36 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def profiled_traffic(workload: str, tile: int):
-    """DRAM bytes per launch of the tile kernel from the committed ncu summary,
-    if it was taken on the current kernels.cu with the same tile side (else
-    None)."""
+def code_digest(path: str) -> str:
+    """sha256 of a CUDA/C source with its comments and whitespace removed: the
+    digest changes with the code, not with its comments."""
     import hashlib
     import re
-    path = os.path.join(ROOT, "profiles", f"k_tile_warp_{workload}.md")
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return hashlib.sha256(re.sub(r"\s+", "", text).encode()).hexdigest()
+
+
+def profiled_traffic(workload: str, tile: int):
+    """DRAM bytes per launch of the tile kernel from the committed ncu summary,
+    if it was taken on the current code of kernels.cu with the same tile side
+    (else None)."""
+    import glob
+    import re
     src = os.path.join(ROOT, "paper_1410_5780_gb300", "csrc", "kernels.cu")
     try:
-        m = re.search(r"<!-- traffic: (\{.*?\}) -->", open(path).read())
-        rec = json.loads(m.group(1))
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    except (OSError, AttributeError, ValueError):
+        digest = code_digest(src)
+    except OSError:
         return None
-    return rec["bytes_per_launch"] if rec.get("sha256") == sha and rec.get("tile") == tile else None
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"k_tile_warp_{workload}*.md"))):
+        try:
+            rec = json.loads(re.search(r"<!-- traffic: (\{.*?\}) -->", open(path).read()).group(1))
+        except (OSError, AttributeError, ValueError):
+            continue
+        if rec.get("code_sha256") == digest and rec.get("tile") == tile:
+            return rec["bytes_per_launch"]
+    return None
 
 
 def input_bytes(w) -> int:
@@ -517,7 +532,8 @@ def run_ours(args, rank, world, dist):
                          "achieved": achieved, "peak": alu_peak, "unit": "T lane-ops/s",
                          "frac": achieved / alu_peak, "traffic": profiled_traffic(args.workload, tuned["tile"]),
                          "traffic_source": "DRAM read+write bytes of the first timed launch, ncu capture in "
-                                           f"profiles/k_tile_warp_{args.workload}.md (null if kernels.cu or the tile side changed)",
+                                           f"profiles/k_tile_warp_{args.workload}*.md taken with the same tile side (null if the code of "
+                                           "kernels.cu changed since)",
                          "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "
                                         "(sm_max_mhz of MEASURED_PEAKS.json)",
                          "work_per_launch": {"fragments": frag, "sample_tests": samp,

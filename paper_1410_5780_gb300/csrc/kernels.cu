@@ -8,10 +8,11 @@
 //   k_modsetup    each module at each step in texel space; marks the raster
 //                 tiles that hold samples, their far plane (max sample depth +
 //                 bias) and counts the receiver modules per tile
-//   k_bin         (triangle, tile) pairs: vertex transform batched over the
-//                 job's steps (one warp per meshlet and step), cull against
-//                 occupied tiles and far planes; pairs counted per tile and
-//                 appended to the wave's pair list
+//   k_bin         (triangle, tile) pairs: one warp per 32 meshlets and step,
+//                 meshlet boxes tested against the light window one per lane,
+//                 then against the far planes of occupied tiles; the
+//                 survivors' triangles transformed and binned one per lane;
+//                 pairs counted per tile and appended to the wave's pair list
 //   k_bin_big     same for triangles that span many tiles, one warp each
 //   k_scan_*      bin offsets, the list of non-empty tiles, receiver offsets
 //   k_scatter, k_recv_fill   write the bins and receiver lists
@@ -25,13 +26,16 @@
 //                 triangles): block-wide sample-driven test, or a shared-memory
 //                 depth tile (texel-centre coverage, atomicMin of
 //                 order-preserving depth keys) and the test of its samples
-//   k_pv          per (step, module): irradiance per cell, substring currents,
-//                 bypass-diode maximum power point (Section 2, step 4)
+//   k_pv          per (step, module), one per lane: irradiance per cell,
+//                 substring currents, bypass-diode maximum power point
+//                 (Section 2, step 4)
 //   k_string, k_array   series strings and strings in parallel (when asked)
 //   k_gen_step, k_heat  sky map of the effective shading (when asked)
 //   k_epilogue    Kahan-compensated FP32 sums over the wave's steps in step
 //                 order, per module, string and array (energy) and per cell
 //                 (beam loss, when asked)
+// A job may cover one window group of a generator (its own light window);
+// the generator's other modules then enter its map as occluder meshlets.
 // The map path replaces the tile kernels + k_pv by k_raster_map (tiles stored
 // to an HBM shadow map with 16-byte stores) + k_sample (texel gathers, ballot
 // tallies, PV model).  Outside the waves: the clear-sky sun table and ideal

@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the batched and served sections")
     ap.add_argument("--batch-scenes", type=int, default=256)
     ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--step-range", type=int, nargs=2, default=None, metavar=("BEGIN", "END"),
+                    help="evaluate only sun steps [BEGIN, END) of the workload (profiling captures of one wave)")
     return ap.parse_args()
 
 
@@ -460,9 +462,11 @@ def run_ours(args, rank, world, dist):
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{dev}")
 
+    sb, se = args.step_range or (0, 0)
+
     def evaluate(profile=0):
         return ctx.evaluate(gid, n=w.n, map_res=w.map_res, outputs=("energy", "energy_unshaded"),
-                            stream=stream.cuda_stream, path=path, profile=profile)
+                            stream=stream.cuda_stream, path=path, profile=profile, step_begin=sb, step_end=se)
 
     for _ in range(max(args.warmup, 0)):
         evaluate()

@@ -219,6 +219,24 @@ def evaluate_workload(w, **kw) -> dict:
     return evaluate(w.scene, w.gen, w.sun, w.poses, w.n, w.map_res, **kw)
 
 
+def cell_beam_loss_from_counts(w, steps, modules, counts, cos_inc) -> np.ndarray:
+    """Per-cell beam irradiation removed by shading (Section 2 step 4: the
+    beam component is taken from the shaded share of a cell, then summed over
+    time): sum over ``steps`` of DNI * max(0, cos_inc) * (count / n^2) * dt, in
+    Wh/m^2, for given shaded-sample counts [S, C_eval] (cells of ``modules``
+    in order) and the oracle's cosines of incidence [S, M_eval].  Used to
+    bound results whose counts differ from the oracle's at masked samples."""
+    gen, sun = w.gen, w.sun
+    steps = np.asarray(steps, np.int64)
+    mods = np.asarray(modules, np.int64)
+    cells = (gen.cells_u[mods].astype(np.int64) * gen.cells_v[mods])
+    mod_of_cell = np.repeat(np.arange(mods.size), cells)
+    beam = sun.dni[steps].astype(np.float64)[:, None] * np.maximum(0.0, np.asarray(cos_inc, np.float64))
+    beam = np.where(sun.xyz[steps, 2][:, None] > 0.0, beam, 0.0)
+    f = np.asarray(counts, np.float64) / float(w.n * w.n)
+    return (beam[:, mod_of_cell] * f * sun.dt_h[steps].astype(np.float64)[:, None]).sum(0)
+
+
 def samples(gen, poses, step: int, module: int, n: int) -> np.ndarray:
     lib = _load()
     mod_f, mod_i, _, _, _, n_trk, pivots = _gen_arrays(gen)

@@ -31,7 +31,9 @@
  * of view is limited to the generator (Section 2, step 3).
  *
  * parity pins: brute force vs BVH; closed-form pole, convex-obstacle and
- * infinite-sheds shadows; PV-model closed forms; invariants (tests/).
+ * infinite-sheds shadows; PV-model closed forms; the per-cell beam loss under
+ * a straight shadow edge; tracker cell centres about the pivot at right-angle
+ * poses; invariants (tests/).
  */
 #include <math.h>
 #include <stdint.h>

@@ -90,6 +90,41 @@ def test_mini_tracker(ctx):
     full_check(ctx, w, strict_loss=False)
 
 
+@pytest.mark.parametrize("make", ["tiny_dec21", "mini_tracker"])
+def test_cell_beam_loss_vs_oracle(ctx, make):
+    """Per-cell annual beam irradiation lost to shading (Section 2 step 4).
+    1. The GPU's Kahan FP32 sums equal the FP64 sum over steps of
+       DNI cos dt f_c on the GPU's own cell counts.
+    2. Every cell whose unmasked flags agree with the oracle's at every step
+       lies between the oracle's sums with its masked samples forced lit and
+       forced shaded."""
+    if make == "tiny_dec21":
+        w = S.make_tiny(day=355)
+    else:
+        w = S.make_tracker(seed=9, n=4, map_res=1024, grid=(4, 3), terrain_n=64, spacing=1.5, n_pylons=2,
+                           step_h=1.0, days=np.array([30, 172, 300]))
+    gid = pv3d.load_workload(ctx, w)
+    g = run_gpu(ctx, gid, w, outputs=("cell_beam_loss", "cell_counts", "sample_bits"))
+    ctx.release(gid)
+    o = oracle.evaluate_workload(w)
+    steps, mods = o["steps"], o["modules"]
+    gl = g["cell_beam_loss"].astype(np.float64)
+    own = oracle.cell_beam_loss_from_counts(w, steps, mods, g["cell_counts"].astype(np.int64), o["cos_inc"])
+    assert own.max() > 0
+    tol = 1e-4 * np.maximum(np.abs(own), 1.0)
+    assert np.all(np.abs(gl - own) <= tol), np.abs(gl - own).max()
+    ob, mb, gb = o["bits"], o["mbits"], g["sample_bits"]
+    lo = oracle.cell_beam_loss_from_counts(w, steps, mods, oracle.popcount64(ob & ~mb), o["cos_inc"])
+    hi = oracle.cell_beam_loss_from_counts(w, steps, mods, oracle.popcount64(ob | mb), o["cos_inc"])
+    agree = (((gb ^ ob) & ~mb) == 0).all(0)
+    assert agree.mean() >= 0.99, agree.mean()
+    tol = 1e-4 * np.maximum(hi, 1.0)
+    ok = (gl >= lo - tol) & (gl <= hi + tol)
+    assert ok[agree].all(), (np.flatnonzero(~ok & agree)[:5], gl[~ok & agree][:5], lo[~ok & agree][:5])
+    # the cells the oracle shades with no ambiguity carry beam loss on the GPU too
+    assert (gl[agree & (lo > 0)] > 0).all()
+
+
 @pytest.mark.parametrize("tile,fmt,path", [(32, 0, 0), (64, 1, 0), (32, 1, 1), (64, 0, 1), (128, 0, 0), (128, 1, 1)])
 def test_tile_depth_format_and_path(tile, fmt, path):
     w = S.make_random_small(111, n_mods=6, n_steps=10, n=4, map_res=1024, tracked=True)

@@ -630,3 +630,97 @@ def test_texel_size_closed_forms():
     for el in (10.0, 45.0, 70.0):
         r = oracle.evaluate(empty, gen, one_sun(sun_from(180.0, el)), None, 1, R, want_mask=False)
         assert abs(r["delta"][0] / (max(W, H * math.cos(math.radians(el))) / (R - 2)) - 1) < 1e-7
+
+
+# ---------------------------------------------------------------------------
+# closed form: per-cell beam irradiation lost to shading (Section 2 step 4:
+# beam removed from shaded areas, summed over the year)
+# ---------------------------------------------------------------------------
+def test_cell_beam_loss_straight_edge_closed_form():
+    """A horizontal module (4 x 2 cells of 0.2 m, 4 x 4 samples) under a
+    horizontal plate at height h = 1 m that covers x <= x_e = 1 m.  With the
+    sun s = (sin z, 0, cos z) a sample at x is shaded iff x <= x_e - tan z, so
+    each step's shadow edge is a straight line across the module; the steps
+    put it through the middle of a cell column, past the module, before it,
+    and one sun is below the horizon.  Per cell the oracle's beam loss must
+    be sum_k DNI_k cos z_k dt_k f_k, with f_k the cell's share of samples left
+    of the edge (DNI, cos and dt differ per step, so a dropped or swapped
+    factor changes the sum)."""
+    pitch, cu, cv, n = 0.2, 4, 2, 4
+    gen = flat_gen([(0.0, 0.0, 0.0)], (1, 0, 0), (0, 1, 0), cu, cv, pitch=pitch)
+    x_e, h = 1.0, 1.0
+    verts = np.array([[-20.0, -20.0, h], [x_e, -20.0, h], [x_e, 20.0, h], [-20.0, 20.0, h]], np.float32)
+    scene = S.Scene(verts, np.array([[0, 1, 2], [0, 2, 3]], np.int32))
+    x_s = np.array([0.30, 0.90, 0.50, -0.10])          # shadow edge on the module per lit step
+    tan_z = x_e - x_s
+    z = np.arctan(tan_z)
+    lit = np.stack([np.sin(z), np.zeros(4), np.cos(z)], 1)
+    night = np.array([[0.8, 0.0, -0.6]])
+    xyz = np.concatenate([lit[:2], night, lit[2:]])
+    dni = np.array([700.0, 820.0, 450.0, 910.0, 640.0], np.float32)
+    dt = np.array([1.0, 0.25, 1.0, 0.5, 1.0], np.float32)
+    sun = S.Sun(xyz=xyz, dni=dni, dhi=np.full(5, 90.0, np.float32), dt_h=dt)
+    r = oracle.evaluate(scene, gen, sun, None, n, 1024)
+    # hand values: shaded sample columns per cell column for each edge
+    #   x_s = 0.3: cell column 0 all 4, column 1 two of 4 (x = 0.225, 0.275), others none
+    #   x_s = 0.9: all;  x_s = 0.5: columns 0, 1 all, column 2 two of 4;  x_s = -0.1: none
+    f_col = {0.30: [1.0, 0.5, 0.0, 0.0], 0.90: [1.0, 1.0, 1.0, 1.0], 0.50: [1.0, 1.0, 0.5, 0.0],
+             -0.10: [0.0, 0.0, 0.0, 0.0]}
+    lit_rows = [0, 1, 3, 4]
+    exp_col = np.zeros(cu)
+    for k, xs in zip(lit_rows, x_s):
+        cos_z = float(xyz[k, 2])
+        exp_col += float(dni[k]) * cos_z * float(dt[k]) * np.array(f_col[round(float(xs), 2)])
+    exp = np.tile(exp_col, cv)  # cells numbered cv * cells_u + cu
+    assert np.allclose(r["cell_beam_loss"], exp, rtol=1e-12, atol=1e-9), (r["cell_beam_loss"], exp)
+    # the fully shaded column equals the full beam over the lit steps; the
+    # half-shaded cells half of their step's beam
+    full = sum(float(dni[k]) * float(xyz[k, 2]) * float(dt[k]) for k in lit_rows[:3])
+    assert abs(r["cell_beam_loss"][0] - full) < 1e-9
+    assert abs(r["cell_beam_loss"][1] - (0.5 * 700.0 * float(xyz[0, 2]) + 820.0 * 0.25 * float(xyz[1, 2])
+                                         + 910.0 * 0.5 * float(xyz[3, 2]))) < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# closed form: a tracked module turns about its tracker's pivot
+# ---------------------------------------------------------------------------
+def test_tracker_pivot_cell_centres_closed_form():
+    """One module in tracker-local coordinates (cells 2 x 1 of 0.3 m, origin
+    (-0.3, -0.2, 0.05), axes x and y) on a tracker whose pivot is at
+    (10, -3, 2).  For right-angle poses the rotation is a signed permutation
+    of the axes, written here by hand: at tilt 0 facing south the module is
+    only translated by the pivot; at tilt 90 deg facing south (az 180) local
+    (x, y, z) -> (x, -z, y); facing east (az 90) -> (z, x, y); facing west
+    (az 270) -> (-z, -x, y); at tilt 0 facing east -> (-y, x, z).  The cell
+    centres (one sample per cell) must be the pivot plus the mapped local
+    centre -- a pose about the origin instead of the pivot, or a dropped or
+    misplaced pivot, fails."""
+    g = flat_gen([(-0.3, -0.2, 0.05)], (1, 0, 0), (0, 1, 0), 2, 1, pitch=0.3)
+    g.tracker = np.zeros(1, np.int32)
+    g.pivots = np.array([[10.0, -3.0, 2.0]], np.float32)
+    piv = np.array([10.0, -3.0, 2.0])
+    local = np.array([[-0.15, -0.05, 0.05], [0.15, -0.05, 0.05]])  # cell centres, tracker-local
+    cases = [
+        (180.0, 0.0, lambda x, y, z: (x, y, z)),
+        (180.0, 90.0, lambda x, y, z: (x, -z, y)),
+        (90.0, 90.0, lambda x, y, z: (z, x, y)),
+        (270.0, 90.0, lambda x, y, z: (-z, -x, y)),
+        (90.0, 0.0, lambda x, y, z: (-y, x, z)),
+    ]
+    poses = np.array([[[math.radians(az), math.radians(t)]] for az, t, _ in cases], np.float32)
+    for st, (az, t, f) in enumerate(cases):
+        got = oracle.samples(g, poses, st, 0, 1)
+        exp = np.array([piv + np.array(f(*c)) for c in local])
+        assert np.allclose(got, exp, atol=2e-6), (az, t, got, exp)
+        nrm = oracle.module_normal(g, poses, st, 0)
+        assert np.allclose(nrm, np.array(f(0.0, 0.0, 1.0)), atol=1e-6)
+
+
+def test_cell_beam_loss_from_counts_matches_the_evaluation():
+    """The counts-based beam loss (used for the GPU envelope) equals the
+    oracle's own per-cell sums on its own counts."""
+    for w in (S.make_tiny(day=355), S.make_random_small(31, n_mods=4, n_steps=8, n=3, tracked=True)):
+        o = oracle.evaluate_workload(w, want_mask=False)
+        b = oracle.cell_beam_loss_from_counts(w, o["steps"], o["modules"], o["counts"], o["cos_inc"])
+        assert o["cell_beam_loss"].max() > 0
+        assert np.allclose(b, o["cell_beam_loss"], rtol=1e-12, atol=1e-9)

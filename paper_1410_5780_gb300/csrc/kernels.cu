@@ -993,8 +993,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_c(const WaveDev* __restri
 // rasteriser (shared by the fused and the map kernels)
 // ---------------------------------------------------------------------------
 constexpr int kRecvChunk = 64;  // receivers staged in shared memory at a time (two per lane of one warp)
-constexpr int kTriBatch = 64;   // triangles set up in shared memory at a time by the rasteriser
-constexpr int kMaxTri = 256;    // triangles a block-wide tile may keep for the sample-driven test
+constexpr int kTriBatchMax = 128;  // triangles set up in shared memory at a time by the rasteriser (one per thread)
 // Sub-blocks per tile side in the sample-driven test (4, 8 and 16 texels on
 // 32-, 64- and 128-texel tiles; a 16 x 16 grid on 128-texel tiles tests fewer
 // triangles per sample but costs more in its masks than it saves).
@@ -1003,8 +1002,7 @@ struct SubGrid {
     static constexpr int side = 8;
     static constexpr int blocks = side * side;
 };
-constexpr int kSubWords = kMaxTri / 32;
-static_assert(kRecvChunk == 64 && kTriBatch == 64, "prefix sums take two entries per lane of one warp");
+static_assert(kRecvChunk == 64, "receiver prefix sums take two entries per lane of one warp");
 
 // Exclusive prefix sum of up to 64 entries, two per lane; called by one full
 // warp.  Returns the total in every lane.
@@ -1018,13 +1016,40 @@ __device__ __forceinline__ int warp_excl_scan64(int& a0, int& a1)
     return __shfl_sync(0xffffffffu, inc, 31);
 }
 
+// Exclusive prefix sum of n <= 32 K entries a[0, n), K consecutive entries
+// per lane of one warp, in place; a[n] receives the total.  Called by one
+// full warp.
+template <int K>
+__device__ __forceinline__ void warp_excl_scan_k(int* a, int n)
+{
+    const int lane = threadIdx.x & 31;
+    int v[K], sum = 0;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int i = lane * K + k;
+        v[k] = i < n ? a[i] : 0;
+        sum += v[k];
+    }
+    const int inc = warp_incl_scan(sum);
+    int ex = inc - sum;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const int i = lane * K + k;
+        if (i < n) a[i] = ex;
+        ex += v[k];
+    }
+    if (lane == 31) a[n] = inc;
+}
+
 // A triangle set up for one tile: edge functions, scaled depths, the texels
-// it visits (its bounding box, or a range of the marked-texel list).
+// it visits (its bounding box, or a range of the marked-texel list) and the
+// sub-blocks in which it may shade a sample (tri_sub_mask).
 struct TriSetup {
     float A[3], Bc[3], C[3];
     float e0, e1, e2;
     short x0, y0, bw, list;  // list = 1: visit entries [q_beg, q_beg + work) of the marked list
     int q_beg, work;
+    uint2 smask;
 };
 
 // A triangle set up for the sample-driven test (48 bytes, three 16-byte loads):
@@ -1087,29 +1112,27 @@ struct RasterSm {
 template <int TS, int NT, bool SEEN>
 struct KeptSm {
     TriS tri[NT];
-    uint32_t box[NT];                       // texel box x0 | y0 << 8 | x1 << 16 | y1 << 24
-    float dmin[NT];                         // nearest vertex depth
+    uint2 smask[NT];                        // per triangle: the sub-blocks (bit sb) it may shade a sample of
     float dlim[SubGrid<TS>::blocks];        // per sub-block: a triangle shades none of its samples
                                             // unless its nearest depth is below this
     uint32_t sbm[SubGrid<TS>::blocks][NT / 32];  // per sub-block: triangles that may shade one of its samples
     uint32_t seen[SEEN ? TS * TS / 32 : 1]; // work counting: texels whose fragments were counted
 };
+static_assert(SubGrid<32>::blocks == 64 && SubGrid<64>::blocks == 64 && SubGrid<128>::blocks == 64,
+              "a triangle's sub-block set is one 64-bit mask");
 
 template <int TS>
 struct TileSm {
-    union {
-        RasterSm<TS> r;
-        KeptSm<TS, kMaxTri, true> s;
-    } u;
+    RasterSm<TS> r;
+    float dlim[SubGrid<TS>::blocks]; // per sub-block depth limit (sub_limits)
     uint32_t mask[TS * TS / 32];     // texels read by some sample (sparse tiles)
     uint32_t row_start[TS + 1];      // start of each row in `list`
     RecvSm recv[kRecvChunk];
     int n_recv;                      // receivers staged
     int total_items;                 // (sample row, cell column) items over the staged receivers
-    int n_tri;                       // triangles kept by the sample-driven set-up
-    TriSetup tri[kTriBatch];         // a batch of set-up triangles (rasteriser)
-    int chunk_pref[kTriBatch + 1];   // prefix of their 32-texel work chunks
     int any_write;                   // some texel of the tile received a depth
+    TriSetup tri[kTriBatchMax];      // a batch of set-up triangles, one per thread
+    int chunk_pref[kTriBatchMax + 1];  // prefix of their 32-texel work chunks
 };
 
 // Stage receiver module m of tile (tx, ty): sample-index box (the tile
@@ -1331,13 +1354,45 @@ __device__ __forceinline__ bool tri_box(const TriT& T, int& x0, int& x1, int& y0
 // decision as a depth test against the tile's stored minimum (the comparison
 // is monotone in the stored depth), with the same arithmetic per triangle.
 
+// The sub-blocks of the tile in which a set-up triangle may shade a sample
+// (bit sb = sy * side + sx): its nearest vertex is nearer than the
+// sub-block's depth limit, and each edge function is non-negative at the
+// texel centre of (its texel box within the sub-block) farthest inside the
+// edge -- exact, since edge_at is monotone in px and py, so a texel centre
+// of the sub-block that the triangle covers implies a non-negative value
+// there.  A triangle with no such sub-block cannot shade any sample of the
+// tile and is not kept.
+template <int TS>
+__device__ __forceinline__ uint64_t tri_sub_mask(const Edges& ed, int x0, int x1, int y0, int y1, float dmin,
+                                                 const float* dlim)
+{
+    constexpr int kSubSide = SubGrid<TS>::side;
+    constexpr int SW = TS / kSubSide;  // sub-block side, texels
+    uint64_t m = 0ull;
+    for (int sy = y0 / SW; sy <= y1 / SW; ++sy) {
+        const float fy0 = texel_centre(max(y0, sy * SW)), fy1 = texel_centre(min(y1, sy * SW + SW - 1));
+        for (int sx = x0 / SW; sx <= x1 / SW; ++sx) {
+            const int sb = sy * kSubSide + sx;
+            if (!(dmin < dlim[sb])) continue;
+            const float fx0 = texel_centre(max(x0, sx * SW)), fx1 = texel_centre(min(x1, sx * SW + SW - 1));
+            bool in = true;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                in = in && edge_at(ed.A[k], ed.Bc[k], ed.C[k], ed.A[k] > 0.f ? fx1 : fx0,
+                                   ed.Bc[k] > 0.f ? fy1 : fy0) >= 0.f;
+            if (in) m |= 1ull << sb;
+        }
+    }
+    return m;
+}
+
 // Set up binned triangle t of tile (ox, oy) for the sample-driven test: false
-// if it lies behind every staged receiver or covers no texel centre of the
-// tile.
+// if it lies behind every staged receiver or may shade no sample of any
+// sub-block (tri_sub_mask, with the sub-block depth limits dlim).
 template <int TS, bool PROF>
 __device__ __forceinline__ bool setup_tri_s(const JobDev& J, const Buffers& B, const LightParams& lp, int ls, int t,
                                             float ox, float oy, const RecvSm* recv, int n_recv, bool cull_ok,
-                                            TriS& ts, uint32_t& box, float& dmin, unsigned int& culled)
+                                            const float* dlim, TriS& ts, uint64_t& smask, unsigned int& culled)
 {
     TriT T;
     tri_texel(J, B, lp, ls, t, T);
@@ -1350,12 +1405,12 @@ __device__ __forceinline__ bool setup_tri_s(const JobDev& J, const Buffers& B, c
     Edges ed;
     int x0, x1, y0, y1;
     if (!make_edges(T, ed) || !tri_box<TS>(T, x0, x1, y0, y1)) return false;
+    smask = tri_sub_mask<TS>(ed, x0, x1, y0, y1, fminf(T.d[0], fminf(T.d[1], T.d[2])), dlim);
+    if (smask == 0ull) return false;
     const float inv_a = 1.f / ed.area2;
     ts.p = make_float4(ed.A[0], ed.Bc[0], ed.C[0], ed.A[1]);
     ts.q = make_float4(ed.Bc[1], ed.C[1], ed.A[2], ed.Bc[2]);
     ts.r = make_float4(ed.C[2], T.d[0] * inv_a, T.d[1] * inv_a, T.d[2] * inv_a);
-    box = (uint32_t)x0 | ((uint32_t)y0 << 8) | ((uint32_t)x1 << 16) | ((uint32_t)y1 << 24);
-    dmin = fminf(T.d[0], fminf(T.d[1], T.d[2]));
     return true;
 }
 
@@ -1391,39 +1446,28 @@ __device__ __forceinline__ void sub_limits(const RecvSm* recv, int n_recv, float
 }
 
 // Per sub-block of the tile, the kept triangles that may shade one of its
-// samples: nearest depth below the sub-block's limit, box overlap, then each
-// edge at the sub-block's texel centre farthest inside it (exact: edge_at is
-// monotone in px and py, so a covered texel of the sub-block implies a
-// non-negative value there).  Entries q = q_begin, q_begin + q_stride, ... <
-// 64 * words(n) of sbm are written.
-template <int TS, int WORDS>
-__device__ __forceinline__ void sub_masks(const TriS* tri, const uint32_t* boxes, const float* dmin,
-                                          const float* dlim, uint32_t (*sbm)[WORDS], int n, int q_begin, int q_stride)
+// samples (bit k of word w: kept triangle 32 w + k), transposed from the
+// triangles' sub-block masks with one ballot per sub-block.  Words w =
+// w_begin, w_begin + w_stride, ... of the n kept triangles are written; called
+// by whole warps.
+template <int WORDS>
+__device__ __forceinline__ void build_sbm(const uint2* smask, uint32_t (*sbm)[WORDS], int n, int w_begin,
+                                          int w_stride)
 {
-    constexpr int kSubSide = SubGrid<TS>::side, kSubBlocks = SubGrid<TS>::blocks;
-    constexpr int SW = TS / kSubSide;  // sub-block side, texels
+    const int lane = threadIdx.x & 31;
     const int nw = (n + 31) >> 5;
-    for (int q = q_begin; q < kSubBlocks * nw; q += q_stride) {
-        const int sb = q & (kSubBlocks - 1), w = q / kSubBlocks;
-        const int sx = (sb % kSubSide) * SW, sy = (sb / kSubSide) * SW;
-        const float fx0 = (float)sx + 0.5f, fx1 = (float)(sx + SW - 1) + 0.5f;
-        const float fy0 = (float)sy + 0.5f, fy1 = (float)(sy + SW - 1) + 0.5f;
-        const float lim = dlim[sb];
-        uint32_t m = 0u;
-        const int kend = min(32, n - w * 32);
-        for (int k = 0; k < kend; ++k) {
-            const int t = w * 32 + k;
-            if (!(dmin[t] < lim)) continue;
-            const uint32_t bx = boxes[t];
-            const int x0 = bx & 255u, y0 = (bx >> 8) & 255u, x1 = (bx >> 16) & 255u, y1 = bx >> 24;
-            if (x0 > sx + SW - 1 || x1 < sx || y0 > sy + SW - 1 || y1 < sy) continue;
-            const float4 p = tri[t].p, qq = tri[t].q, r = tri[t].r;
-            if (edge_at(p.x, p.y, p.z, p.x > 0.f ? fx1 : fx0, p.y > 0.f ? fy1 : fy0) < 0.f) continue;
-            if (edge_at(p.w, qq.x, qq.y, p.w > 0.f ? fx1 : fx0, qq.x > 0.f ? fy1 : fy0) < 0.f) continue;
-            if (edge_at(qq.z, qq.w, r.x, qq.z > 0.f ? fx1 : fx0, qq.w > 0.f ? fy1 : fy0) < 0.f) continue;
-            m |= 1u << k;
+    for (int w = w_begin; w < nw; w += w_stride) {
+        const int t = (w << 5) | lane;
+        const uint2 m = t < n ? smask[t] : make_uint2(0u, 0u);
+        uint32_t lo = 0u, hi = 0u;
+#pragma unroll
+        for (int sb = 0; sb < 32; ++sb) {
+            const uint32_t a = __ballot_sync(0xffffffffu, (m.x >> sb) & 1u);
+            const uint32_t b = __ballot_sync(0xffffffffu, (m.y >> sb) & 1u);
+            if (lane == sb) { lo = a; hi = b; }
         }
-        sbm[sb][w] = m;
+        sbm[lane][w] = lo;
+        sbm[lane + 32][w] = hi;
     }
 }
 
@@ -1534,12 +1578,17 @@ __device__ __forceinline__ void test_items(const RecvSm* recv, int n_recv, int t
 
 // ---- tile rasteriser ------------------------------------------------------
 
-// Rasterise the tile's triangles into sm.u.r.tile.  Sparse tiles (fewer samples
-// than half the texels) are rasterised only at the texels their samples
-// read; each triangle then visits its bounding box or the marked texels of
-// its rows, whichever is fewer.  Receivers [r0, r0 + nrecv) must be staged
-// (the first kRecvChunk of them) on entry.  Returns 0 if no sample reads the
-// tile.
+// Rasterise the tile's triangles into sm.r.tile.  Sparse tiles (fewer samples
+// than two per texel) are rasterised only at the texels their samples read;
+// each triangle then visits its bounding box or the marked texels of its
+// rows, whichever is fewer.  A triangle is drawn only in the sub-blocks where
+// it may shade a sample (tri_sub_mask with the sub-block depth limits): the
+// stored nearest depth may then differ at a texel, but never the decision of
+// a sample there (the dropped triangles are behind every sample they cover,
+// and "shaded" is "some covering triangle is nearer than the sample less its
+// bias").  Receivers [r0, r0 + nrecv) must be staged (the first kRecvChunk of
+// them) on entry.  Returns 0 if no sample reads the tile or nothing was drawn
+// at a texel a sample reads.
 template <int TS, bool PROF>
 __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, const WaveDev* W, int ls, int tx,
                            int ty, int64_t te, uint64_t r0, int nrecv, unsigned int& visits, unsigned int& writes,
@@ -1547,6 +1596,9 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
 {
     constexpr int SH = TS == 128 ? 7 : (TS == 64 ? 6 : 5);
     constexpr int WPR = TS / 32;
+    constexpr int kSubSide = SubGrid<TS>::side;
+    constexpr int SWS = SH - 3;  // log2 of the sub-block side (8 x 8 sub-blocks)
+    static_assert(kSubSide == 8, "sub-block index by shifts");
     const int tid = threadIdx.x, bd = blockDim.x;
     const int lane = tid & 31, warp = tid >> 5, n_warps = bd >> 5;
     const int u24 = W->depth_u24;
@@ -1559,6 +1611,9 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
     // the texels that samples read
     const bool dense = est >= 2 * TS * TS;
     if (PROF && threadIdx.x == 0 && dense) ++dense_n;
+    if (cull_ok) sub_limits<TS>(sm.recv, sm.n_recv, sm.dlim, u24 ? 1.f / lp.qscale : 0.f, tid, bd);
+    else
+        for (int q = tid; q < SubGrid<TS>::blocks; q += bd) sm.dlim[q] = FLT_MAX;
     int n_need = TS * TS;
     if (!dense) {
         for (int q = tid; q < TS * WPR; q += bd) sm.mask[q] = 0u;
@@ -1605,14 +1660,14 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
             for (int w2 = 0; w2 < w; ++w2) pos += __popc(sm.mask[y * WPR + w2]);
             while (bits) {
                 const int bit = __ffs(bits) - 1;
-                sm.u.r.list[pos++] = (uint16_t)(y * TS + w * 32 + bit);
+                sm.r.list[pos++] = (uint16_t)(y * TS + w * 32 + bit);
                 bits &= bits - 1;
             }
         }
         __syncthreads();
         n_need = (int)sm.row_start[TS];
     }
-    uint4* t4 = reinterpret_cast<uint4*>(sm.u.r.tile);
+    uint4* t4 = reinterpret_cast<uint4*>(sm.r.tile);
     for (int q = tid; q < TS * TS / 4; q += bd) t4[q] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
     if (tid == 0) sm.any_write = 0;
     __syncthreads();
@@ -1623,10 +1678,11 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
     uint64_t cnt = B.t_cnt[te];
     const uint64_t cap = (uint64_t)W->bin_cap;
     if (off + cnt > cap) cnt = off < cap ? cap - off : 0;
-    // triangles in batches: set-up by one thread each, then all warps share
-    // the batch's texel visits in chunks of 32
-    for (uint64_t b0 = 0; b0 < cnt; b0 += kTriBatch) {
-        const int nb = (int)min((uint64_t)kTriBatch, cnt - b0);
+    // triangles in batches of one per thread (at most kTriBatchMax): set-up,
+    // then all warps share the batch's texel visits in chunks of 32
+    const int batch = min(bd, kTriBatchMax);
+    for (uint64_t b0 = 0; b0 < cnt; b0 += batch) {
+        const int nb = (int)min((uint64_t)batch, cnt - b0);
         if (tid < nb) {
             TriSetup& S = sm.tri[tid];
             S.work = 0;
@@ -1640,30 +1696,29 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
             if (!may_shade(sm.recv, sm.n_recv, T, cull_ok)) {
                 if (PROF) ++culled;
             } else if (make_edges(T, ed) && tri_box<TS>(T, x0, x1, y0, y1)) {
-                const float inv_a = 1.f / ed.area2;
+                const uint64_t sb = tri_sub_mask<TS>(ed, x0, x1, y0, y1, fminf(T.d[0], fminf(T.d[1], T.d[2])),
+                                                     sm.dlim);
+                if (sb != 0ull) {
+                    const float inv_a = 1.f / ed.area2;
 #pragma unroll
-                for (int k = 0; k < 3; ++k) { S.A[k] = ed.A[k]; S.Bc[k] = ed.Bc[k]; S.C[k] = ed.C[k]; }
-                S.e0 = T.d[0] * inv_a; S.e1 = T.d[1] * inv_a; S.e2 = T.d[2] * inv_a;
-                S.x0 = (short)x0; S.y0 = (short)y0; S.bw = (short)(x1 - x0 + 1);
-                const int n_px = (x1 - x0 + 1) * (y1 - y0 + 1);
-                const int q_beg = dense ? 0 : (int)sm.row_start[y0];
-                const int q_end = dense ? 0 : (int)sm.row_start[y1 + 1];
-                if (dense || n_px <= q_end - q_beg) {
-                    S.list = 0; S.q_beg = 0; S.work = n_px;
-                } else {
-                    S.list = 1; S.q_beg = q_beg; S.work = q_end - q_beg;
+                    for (int k = 0; k < 3; ++k) { S.A[k] = ed.A[k]; S.Bc[k] = ed.Bc[k]; S.C[k] = ed.C[k]; }
+                    S.e0 = T.d[0] * inv_a; S.e1 = T.d[1] * inv_a; S.e2 = T.d[2] * inv_a;
+                    S.smask = make_uint2((uint32_t)sb, (uint32_t)(sb >> 32));
+                    S.x0 = (short)x0; S.y0 = (short)y0; S.bw = (short)(x1 - x0 + 1);
+                    const int n_px = (x1 - x0 + 1) * (y1 - y0 + 1);
+                    const int q_beg = dense ? 0 : (int)sm.row_start[y0];
+                    const int q_end = dense ? 0 : (int)sm.row_start[y1 + 1];
+                    if (dense || n_px <= q_end - q_beg) {
+                        S.list = 0; S.q_beg = 0; S.work = n_px;
+                    } else {
+                        S.list = 1; S.q_beg = q_beg; S.work = q_end - q_beg;
+                    }
                 }
             }
+            sm.chunk_pref[tid] = (S.work + 31) >> 5;
         }
         __syncthreads();
-        if (tid < 32) {
-            int c0 = 2 * tid < nb ? (sm.tri[2 * tid].work + 31) >> 5 : 0;
-            int c1 = 2 * tid + 1 < nb ? (sm.tri[2 * tid + 1].work + 31) >> 5 : 0;
-            const int tot = warp_excl_scan64(c0, c1);
-            if (2 * tid < nb) sm.chunk_pref[2 * tid] = c0;
-            if (2 * tid + 1 < nb) sm.chunk_pref[2 * tid + 1] = c1;
-            if (tid == 0) sm.chunk_pref[nb] = tot;
-        }
+        if (tid < 32) warp_excl_scan_k<kTriBatchMax / 32>(sm.chunk_pref, nb);
         __syncthreads();
         // each warp takes a contiguous range of chunks: one search, then the
         // triangles of the range in order with their set-up in registers
@@ -1687,6 +1742,7 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
             const float B0 = S.Bc[0], B1 = S.Bc[1], B2 = S.Bc[2];
             const float C0 = S.C[0], C1 = S.C[1], C2 = S.C[2];
             const float e0 = S.e0, e1 = S.e1, e2 = S.e2;
+            const uint2 smask = S.smask;
             const int x0 = S.x0, y0 = S.y0, bw = S.bw, is_list = S.list, q_beg = S.q_beg, work = S.work;
             const float inv_bw = 1.f / (float)bw;
             for (; ch < t_end; ++ch) {
@@ -1694,7 +1750,7 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
                 if (q >= work) continue;
                 int ix, iy;
                 if (is_list) {
-                    const int p = sm.u.r.list[q_beg + q];
+                    const int p = sm.r.list[q_beg + q];
                     ix = p & (TS - 1);
                     iy = p >> SH;
                     if (ix < x0 || ix >= x0 + bw) continue;
@@ -1704,13 +1760,15 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
                     ix = x0 + q - ry * bw;
                     if (!dense && !(sm.mask[iy * WPR + (ix >> 5)] & (1u << (ix & 31)))) continue;
                 }
+                const int sb = ((iy >> SWS) << 3) | (ix >> SWS);
+                if (!(((sb < 32 ? smask.x : smask.y) >> (sb & 31)) & 1u)) continue;
                 const float px = (float)ix + 0.5f, py = (float)iy + 0.5f;
                 const float w0 = edge_at(A0, B0, C0, px, py);
                 const float w1 = edge_at(A1, B1, C1, px, py);
                 const float w2 = edge_at(A2, B2, C2, px, py);
                 if (PROF) ++visits;
                 if (w0 >= 0.f && w1 >= 0.f && w2 >= 0.f) {
-                    atomicMin(&sm.u.r.tile[iy * TS + ix], depth_store_key(depth_at(w0, w1, w2, e0, e1, e2), lp, u24));
+                    atomicMin(&sm.r.tile[iy * TS + ix], depth_store_key(depth_at(w0, w1, w2, e0, e1, e2), lp, u24));
                     wrote = true;
                     if (PROF) ++writes;
                 }
@@ -1875,17 +1933,15 @@ __global__ void __launch_bounds__(kTileWarps * 32, 6) k_tile_warp(const WaveDev*
             int n = 0;
             for (uint64_t b0 = 0; b0 < cnt && n <= kWarpTri; b0 += 32) {
                 TriS ts;
-                uint32_t box = 0u;
-                float dmin = 0.f;
+                uint64_t smask = 0ull;
                 const bool keep = b0 + lane < cnt &&
                                   setup_tri_s<TS, PROF>(J, B, lp, ls, (int)B.bins[off + b0 + lane], ox, oy, sm.recv,
-                                                        nrecv, true, ts, box, dmin, p_culled);
+                                                        nrecv, true, sm.k.dlim, ts, smask, p_culled);
                 const unsigned int bal = __ballot_sync(0xffffffffu, keep);
                 const int slot = n + __popc(bal & ((1u << lane) - 1u));
                 if (keep && slot < kWarpTri) {
                     sm.k.tri[slot] = ts;
-                    sm.k.box[slot] = box;
-                    sm.k.dmin[slot] = dmin;
+                    sm.k.smask[slot] = make_uint2((uint32_t)smask, (uint32_t)(smask >> 32));
                 }
                 n += __popc(bal);
             }
@@ -1893,7 +1949,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 6) k_tile_warp(const WaveDev*
             if (PROF && lane == 0 && heavy) ++p_ht;
             if (!heavy && n > 0) {
                 __syncwarp();
-                sub_masks<TS, kWarpWords>(sm.k.tri, sm.k.box, sm.k.dmin, sm.k.dlim, sm.k.sbm, n, lane, 32);
+                build_sbm<kWarpWords>(sm.k.smask, sm.k.sbm, n, 0, 1);
                 __syncwarp();
                 const int C = J.n_cells;
                 test_items<TS, kWarpWords, PROF>(sm.recv, nrecv, total, J, lp, u24, tx, ty, lane, 32, sm.k.tri, n,
@@ -1929,57 +1985,16 @@ __global__ void __launch_bounds__(kTileWarps * 32, 6) k_tile_warp(const WaveDev*
 }
 
 // ---------------------------------------------------------------------------
-// k_raster_test: fused path, the tiles k_tile_warp listed -- one CTA per
-// tile.  A tile keeping at most kMaxTri triangles after culling is tested
-// sample by sample against them; a tile with more is rasterised in shared
-// memory first, then its samples read the tile.
+// k_raster_test: fused path, the tiles k_tile_warp listed (more receivers,
+// binned or kept triangles than a warp takes) -- one CTA per tile: the tile
+// is rasterised in shared memory (tile_raster: texel-centre coverage,
+// atomicMin of order-preserving depth keys, only at the texels samples read
+// and only where a triangle may shade one), then every sample that reads the
+// tile is depth-tested against it.  Measured on the tracker plant, the
+// shared-memory depth tile beats a block-wide sample-by-sample test of the
+// kept triangles for every kept count: samples behind many thin members
+// (lattice pylons) test each candidate triangle, texels are written once.
 // ---------------------------------------------------------------------------
-
-// Set up the tile's binned triangles that may shade a staged receiver and
-// cover a texel centre of the tile, for the whole block.  Returns how many
-// were kept, or -1 if more than kMaxTri were (the tile is then rasterised).
-template <int TS, bool PROF>
-__device__ int setup_sample_tris(TileSm<TS>& sm, const JobDev& J, const Buffers& B, const WaveDev* W,
-                                 const LightParams& lp, int ls, int tx, int ty, int64_t te, bool cull_ok,
-                                 unsigned int& culled)
-{
-    const int tid = threadIdx.x, lane = tid & 31;
-    const float ox = (float)(tx * TS), oy = (float)(ty * TS);
-    const uint64_t off = B.t_off[te];
-    uint64_t cnt = B.t_cnt[te];
-    const uint64_t cap = (uint64_t)W->bin_cap;
-    if (off + cnt > cap) cnt = off < cap ? cap - off : 0;
-    if (PROF)
-        for (int q = tid; q < TS * TS / 32; q += blockDim.x) sm.u.s.seen[q] = 0u;
-    if (cull_ok) sub_limits<TS>(sm.recv, sm.n_recv, sm.u.s.dlim, W->depth_u24 ? 1.f / lp.qscale : 0.f, tid,
-                                blockDim.x);
-    else
-        for (int q = tid; q < SubGrid<TS>::blocks; q += blockDim.x) sm.u.s.dlim[q] = FLT_MAX;
-    for (uint64_t b0 = 0; b0 < cnt; b0 += blockDim.x) {
-        TriS ts;
-        uint32_t box = 0u;
-        float dmin = 0.f;
-        const bool keep = b0 + tid < cnt &&
-                          setup_tri_s<TS, PROF>(J, B, lp, ls, (int)B.bins[off + b0 + tid], ox, oy, sm.recv,
-                                                sm.n_recv, cull_ok, ts, box, dmin, culled);
-        const unsigned int bal = __ballot_sync(0xffffffffu, keep);
-        int base = 0;
-        if (lane == 0 && bal) base = atomicAdd(&sm.n_tri, __popc(bal));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (keep) {
-            const int slot = base + __popc(bal & ((1u << lane) - 1u));
-            if (slot < kMaxTri) {
-                sm.u.s.tri[slot] = ts;
-                sm.u.s.box[slot] = box;
-                sm.u.s.dmin[slot] = dmin;
-            }
-        }
-    }
-    __syncthreads();
-    const int n = sm.n_tri;
-    return n > kMaxTri ? -1 : n;
-}
-
 template <int TS, bool PROF>
 __global__ void __launch_bounds__(HeavyCfg<TS>::threads, HeavyCfg<TS>::min_blocks)
     k_raster_test(const WaveDev* __restrict__ W, const JobDev* __restrict__ jobs, Buffers B)
@@ -1987,11 +2002,9 @@ __global__ void __launch_bounds__(HeavyCfg<TS>::threads, HeavyCfg<TS>::min_block
     extern __shared__ __align__(16) unsigned char tile_smem[];  // sizeof(TileSm<TS>), set at launch
     TileSm<TS>& sm = *reinterpret_cast<TileSm<TS>*>(tile_smem);
     unsigned int p_samples = 0, p_visits = 0, p_writes = 0, p_culled = 0, p_cand = 0, p_dense = 0, p_tiles = 0;
-    unsigned int p_stiles = 0, p_pairs = 0;
     __shared__ unsigned int s_item[2];
     const unsigned int n_ne = min(B.ctr->n_heavy, (unsigned int)W->tot_te);
     const int nj = W->n_jobs;
-    const int want_bits = W->want_bits;
     const int u24 = W->depth_u24;
     const int tid = threadIdx.x;
     if (tid == 0) s_item[0] = atomicAdd(&B.ctr->heavy_next, 1u);
@@ -2001,10 +2014,7 @@ __global__ void __launch_bounds__(HeavyCfg<TS>::threads, HeavyCfg<TS>::min_block
         // the tile publish it
         const unsigned int item = s_item[par];
         if (item >= n_ne) break;
-        if (tid == 0) {
-            s_item[par ^ 1] = atomicAdd(&B.ctr->heavy_next, 1u);
-            sm.n_tri = 0;
-        }
+        if (tid == 0) s_item[par ^ 1] = atomicAdd(&B.ctr->heavy_next, 1u);
         const uint32_t te = B.heavy[item];
         int j, ls, tx, ty;
         decode_tile(jobs, nj, te, j, ls, tx, ty);
@@ -2018,27 +2028,9 @@ __global__ void __launch_bounds__(HeavyCfg<TS>::threads, HeavyCfg<TS>::min_block
         const int C = J.n_cells;
         uint32_t* cnt_row = B.cs_cnt + J.cs_base + (int64_t)ls * C;
         unsigned long long* bits_row = B.cs_bits + J.cs_base + (int64_t)ls * C;
-        const int nt = setup_sample_tris<TS, PROF>(sm, J, B, W, lp, ls, tx, ty, te, nrecv <= kRecvChunk, p_culled);
-        if (nt >= 0) {
-            // sample-driven test (no triangle kept: every sample of the tile is lit)
-            if (PROF && tid == 0) ++p_stiles;
-            if (nt > 0) {
-                sub_masks<TS, kSubWords>(sm.u.s.tri, sm.u.s.box, sm.u.s.dmin, sm.u.s.dlim, sm.u.s.sbm, nt, tid,
-                                         blockDim.x);
-                __syncthreads();
-                for (int c0 = 0; c0 < nrecv; c0 += kRecvChunk) {
-                    if (c0 > 0) {
-                        __syncthreads();
-                        stage_receivers<TS>(sm, J, B, ls, tx, ty, r0 + c0, min(kRecvChunk, nrecv - c0));
-                    }
-                    test_items<TS, kSubWords, PROF>(sm.recv, sm.n_recv, sm.total_items, J, lp, u24, tx, ty, tid,
-                                                    blockDim.x, sm.u.s.tri, nt, sm.u.s.sbm, (nt + 31) >> 5,
-                                                    sm.u.s.seen, cnt_row, bits_row, want_bits, p_cand, p_samples,
-                                                    p_pairs, p_writes);
-                }
-            }
-        } else if (tile_raster<TS, PROF>(sm, J, B, W, ls, tx, ty, te, r0, nrecv, p_visits, p_writes, p_culled,
-                                         p_cand, p_dense) != 0) {
+        const int want_bits = W->want_bits;
+        if (tile_raster<TS, PROF>(sm, J, B, W, ls, tx, ty, te, r0, nrecv, p_visits, p_writes, p_culled, p_cand,
+                                  p_dense) != 0) {
             for (int c0 = 0; c0 < nrecv; c0 += kRecvChunk) {
                 if (c0 > 0) stage_receivers<TS>(sm, J, B, ls, tx, ty, r0 + c0, min(kRecvChunk, nrecv - c0));
                 uint32_t cnt = 0;
@@ -2047,7 +2039,7 @@ __global__ void __launch_bounds__(HeavyCfg<TS>::threads, HeavyCfg<TS>::min_block
                     sm, J, tx, ty, p_cand,
                     [&](const RecvSm& R, int k, int ix, int iy, float d) {
                         if (PROF) ++p_samples;
-                        const uint32_t key = sm.u.r.tile[(iy & (TS - 1)) * TS + (ix & (TS - 1))];
+                        const uint32_t key = sm.r.tile[(iy & (TS - 1)) * TS + (ix & (TS - 1))];
                         if (key == kEmpty) return;
                         if (behind_key(d, R.s.bias, key, lp.dnear, lp.qscale, u24)) {
                             ++cnt;
@@ -2070,7 +2062,7 @@ __global__ void __launch_bounds__(HeavyCfg<TS>::threads, HeavyCfg<TS>::min_block
     }
     if (PROF) {
         flush_profile(B, p_samples, p_visits, p_writes, p_culled);
-        flush_profile2(B, p_cand, p_tiles, p_dense, p_stiles, p_pairs);
+        flush_profile2(B, p_cand, p_tiles, p_dense, 0u, 0u);
         flush_heavy(B, p_samples, p_writes, p_tiles);
     }
 }
@@ -2107,7 +2099,7 @@ __global__ void __launch_bounds__(256) k_raster_map(const WaveDev* __restrict__ 
         stage_receivers<TS>(sm, J, B, ls, tx, ty, r0, min(nrecv, kRecvChunk));
         // the tile is stored even when nothing was drawn: its samples read it
         tile_raster<TS, PROF>(sm, J, B, W, ls, tx, ty, te, r0, nrecv, p_visits, p_writes, p_culled, p_cand, p_dense);
-        const uint4* t4 = reinterpret_cast<const uint4*>(sm.u.r.tile);
+        const uint4* t4 = reinterpret_cast<const uint4*>(sm.r.tile);
         uint4* dst = reinterpret_cast<uint4*>(B.map + ((size_t)item * (TS * TS)));
         for (int q = tid; q < TS * TS / 4; q += bd) dst[q] = t4[q];
         __syncthreads();

@@ -10,11 +10,16 @@
 // fixed shadow map compiled into the library.
 //
 // The shadow map is the file-scope array g_noalloc_map below: kNoAllocMaxRes^2
-// uint32 depth keys (16 MiB), which every GPU that loads the library keeps until
-// the process exits.  Host code cannot use the array's name as a device address
-// (in host code it names a host-side stand-in), so the first call on each
-// device, with that device current, looks the address up with
-// cudaGetSymbolAddress and caches it; that first call should therefore come
+// uint32 depth keys (16 MiB).  With CUDA's lazy module loading (the default)
+// the array is reserved on a device when this file's module is first loaded
+// there, i.e. by the first call on that device, and it is then kept until the
+// process exits: a caller whose own pool takes all device memory should make
+// one call before creating the pool.  Host code cannot use the array's name as
+// a device address (in host code it names a host-side stand-in), so every call
+// looks the address up with cudaGetSymbolAddress for the current device and
+// context (a context made after cudaDeviceReset loads the module again at a new
+// address).  While the stream is being captured the lookup is not made and the
+// address found by the last call on that device is used, so one call must come
 // before any stream capture.  All calls share the one array and it keeps the
 // last call's contents: every call clears the part it uses first, and calls
 // whose work overlaps on the GPU (different streams, no ordering) race on it.
@@ -159,22 +164,23 @@ extern "C" int pv3d_module_shade_noalloc(const float* tri_xyz, int64_t n_tris, c
     cudaStream_t st = (cudaStream_t)stream;
     const int n_cells = M.cells_u * M.cells_v;
 
-    // set-up, once per device, with that device current
+    // device address of the map for the current device and context; under
+    // stream capture, the address the last call on this device found
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PV3D_E_DEVICE;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) return PV3D_E_DEVICE;
     uint32_t* map = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_setup_mu);
-        if (!g_map_ptr[dev]) {
+        if (cap == cudaStreamCaptureStatusNone) {
             void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_map) != cudaSuccess || !p) {
-                cudaGetLastError();
-                return PV3D_E_DEVICE;
-            }
+            if (cudaGetSymbolAddress(&p, g_noalloc_map) != cudaSuccess || !p) return PV3D_E_DEVICE;
             g_map_ptr[dev] = (uint32_t*)p;
         }
         map = g_map_ptr[dev];
     }
+    if (!map) return PV3D_E_DEVICE;  // captured before any call on this device
 
     // light frame (w = s, u = normalize(s x z), x at the zenith, v = s x u) and
     // window: bounding square of the module's corners, one texel of padding
@@ -227,20 +233,32 @@ extern "C" int pv3d_module_shade_noalloc(const float* tri_xyz, int64_t n_tris, c
     const float bias = (float)(delta * (0.70710678 * std::sqrt(std::fmax(0.0, 1.0 - ci * ci)) / ci + 0.03125));
 
     const int64_t n_texels = (int64_t)map_res * map_res;
-    na_clear<<<512, 256, 0, st>>>(map, n_texels, cell_counts, n_cells);
+    // each launch's status comes from its own cudaLaunchKernel call, so an
+    // earlier error of the caller's is neither reported nor cleared here
+    void* a_clear[] = {&map, (void*)&n_texels, &cell_counts, (void*)&n_cells};
+    if (cudaLaunchKernel((const void*)na_clear, dim3(512), dim3(256), a_clear, 0, st) != cudaSuccess)
+        return PV3D_E_DEVICE;
     if (sz > 0.0) {
         if (n_tris > 0) {
             const int64_t blocks = std::min<int64_t>((n_tris + 7) / 8, 4096);
-            na_raster<<<(unsigned)blocks, 256, 0, st>>>(tri_xyz, n_tris, f, map);
+            void* a_raster[] = {(void*)&tri_xyz, &n_tris, &f, &map};
+            if (cudaLaunchKernel((const void*)na_raster, dim3((unsigned)blocks), dim3(256), a_raster, 0, st) !=
+                cudaSuccess)
+                return PV3D_E_DEVICE;
         }
-        const float3 o = make_float3((float)(M.origin[0] - ref[0]), (float)(M.origin[1] - ref[1]),
-                                     (float)(M.origin[2] - ref[2]));
-        const float3 u = make_float3(M.u[0], M.u[1], M.u[2]), v = make_float3(M.v[0], M.v[1], M.v[2]);
+        float3 o = make_float3((float)(M.origin[0] - ref[0]), (float)(M.origin[1] - ref[1]),
+                               (float)(M.origin[2] - ref[2]));
+        float3 u = make_float3(M.u[0], M.u[1], M.u[2]), v = make_float3(M.v[0], M.v[1], M.v[2]);
+        float pitch = M.pitch;
+        int cells_u = M.cells_u, nc = n_cells, nside = n;
+        float b = bias;
         const int64_t total = (int64_t)n_cells * n * n;
         const int64_t blocks = std::min<int64_t>((total + 255) / 256, 4096);
-        na_sample<<<(unsigned)blocks, 256, 0, st>>>(f, map, o, u, v, M.pitch, M.cells_u, n_cells, n, bias,
-                                                    cell_counts);
+        const uint32_t* cmap = map;
+        void* a_sample[] = {&f, &cmap, &o, &u, &v, &pitch, &cells_u, &nc, &nside, &b, &cell_counts};
+        if (cudaLaunchKernel((const void*)na_sample, dim3((unsigned)blocks), dim3(256), a_sample, 0, st) !=
+            cudaSuccess)
+            return PV3D_E_DEVICE;
     }
-    const cudaError_t e = cudaGetLastError();
-    return e == cudaSuccess ? PV3D_OK : PV3D_E_DEVICE;
+    return PV3D_OK;
 }

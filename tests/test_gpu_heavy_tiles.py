@@ -1,8 +1,8 @@
 """GPU parity on the tile kernels' less common paths: tiles handed from one
-warp per tile to one block per tile because they keep more than 64 triangles
-(block-wide sample-driven test up to 256, shared-memory rasterisation above),
-have more than 512 binned triangles, or more than 16 or 64 receiver modules
-(receivers then staged in chunks, without plane culling).
+warp per tile to one block per tile (a shared-memory depth tile, then the
+test of its samples) because they keep more than 64 triangles, have more
+than 512 binned triangles, or more than 16 or 64 receiver modules (receivers
+then staged in chunks, without plane culling).
 Each case must agree with the FP64 oracle, be bit-identical to the map path
 (HBM shadow map + gather), and the work counters must show that the intended
 path ran."""
@@ -18,9 +18,9 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("case,tile,map_res,tiny,cells", [
-    ("block_sample_test", 64, 256, False, 30), # 64 < kept <= 256: one block, sample by sample
-    ("block_raster", 64, 128, False, 60),      # binned > 512, kept > 256: one block, shared-memory raster
-    ("many_receivers", 64, 128, True, 30),     # > 16 receivers per tile: block-wide sample-driven test
+    ("block_kept", 64, 256, False, 30),        # kept > 64: one block, shared-memory raster
+    ("block_raster", 64, 128, False, 60),      # binned > 512: one block, shared-memory raster
+    ("many_receivers", 64, 128, True, 30),     # > 16 receivers per tile: one block
     ("receiver_chunks", 64, 64, True, 30),     # > 64 receivers: staged in chunks, no plane culling, raster
     ("warp_tiles", 32, 512, False, 30),        # the same canopy on small tiles
     ("block_raster_128", 128, 256, False, 60), # 128-texel tiles: block raster of a 64 KB shared tile
@@ -44,14 +44,14 @@ def test_heavy_tile_paths(case, tile, map_res, tiny, cells):
     why = p["heavy_why"]  # [receivers, binned triangles, kept triangles]
     p = {k: v for k, v in p.items() if not k.endswith("_ms")}
     warp_tiles = p["nonempty_tiles"] - p["heavy_tiles"]
-    block_sample_tiles = p["sample_tiles"] - warp_tiles
     raster_tiles = p["nonempty_tiles"] - p["sample_tiles"]
-    if case == "block_sample_test":
-        assert why[2] > 0 and block_sample_tiles > 0, p
+    assert raster_tiles == p["heavy_tiles"], p  # every tile a warp hands on is rasterised
+    if case == "block_kept":
+        assert why[2] > 0 and raster_tiles > 0 and p["texel_visits"] > 0, p
     elif case in ("block_raster", "block_raster_128"):
         assert why[1] > 0 and raster_tiles > 0 and p["texel_visits"] > 0, p
     elif case == "many_receivers":
-        assert why[0] > 0 and block_sample_tiles > 0, p
+        assert why[0] > 0 and raster_tiles > 0, p
     elif case == "receiver_chunks":
         # one tile holds every module; without plane culling it keeps the
         # whole canopy and is rasterised, its receivers staged in chunks

@@ -2,14 +2,18 @@
 """Benchmark of the GB300 shadow-sample path (3DPV method, arXiv 1410.5780).
 
 Metric: shadow sample tests per second (lit sun steps x cell samples).  The
-default workload is the BIPV facade: 200 vertical south-facing modules of
-6x10 cells with 8x8 samples per cell, ~50k triangles of buildings, trees and
-poles, hourly suns of a year at 40 N (4,379 daylight steps), a 4096^2 light
-window.  One bench step is one full-year evaluation of that workload.
+headline workload is the tracker plant, the largest single-GPU case: 500
+two-axis trackers of 24 modules (6 x 12 cells, 4 x 4 samples per cell) on a
+512 x 512 fractal terrain with 20 lattice pylons and a ridge (0.56 M
+triangles), quarter-hour suns of a year at 40 N (17,519 daylight steps), an
+8192^2 light window.  One bench step is one full-year evaluation; the timed
+region runs the library's production path (each wave a replayed CUDA graph).
+The BIPV facade (200 modules among buildings and trees, hourly year, 8 x 8
+samples, 4096^2) is measured the same way and reported under "facade".
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-Multi-GPU (torchrun): every rank evaluates its own seeded facade (independent
+Multi-GPU (torchrun): every rank evaluates its own seeded plant (independent
 problems, weak scaling); the only collectives are the timing barrier and the
 max-over-ranks of the timed region.  --impl reference times the FP64 CPU
 oracle on the host cores on a bounded sample of the same workload.
@@ -52,7 +56,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="facade", choices=["facade", "tracker", "tiny"])
+    ap.add_argument("--workload", default="tracker", choices=["facade", "tracker", "tiny"])
     ap.add_argument("--path", default="fused", choices=["fused", "map"])
     ap.add_argument("--chunk", type=int, default=0, help="sun steps per wave (0 = autotuned)")
     ap.add_argument("--tile", type=int, default=0, choices=[0, 32, 64, 128],
@@ -60,7 +64,8 @@ def parse():
                          "(profiling runs pin the configuration the plain bench chose)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--no-serving", action="store_true", help="skip the batched and served sections")
+    ap.add_argument("--no-serving", action="store_true", help="skip the batched, served and extension sections")
+    ap.add_argument("--no-facade", action="store_true", help="skip the secondary facade measurement")
     ap.add_argument("--batch-scenes", type=int, default=256)
     ap.add_argument("--requests", type=int, default=200)
     ap.add_argument("--step-range", type=int, nargs=2, default=None, metavar=("BEGIN", "END"),
@@ -218,10 +223,10 @@ def code_digest(path: str) -> str:
     return hashlib.sha256(re.sub(r"\s+", "", text).encode()).hexdigest()
 
 
-def profiled_traffic(workload: str, tile: int):
-    """DRAM bytes per launch of the tile kernel from the committed ncu summary,
-    if it was taken on the current code of kernels.cu with the same tile side
-    (else None)."""
+def profiled_traffic(workload: str, tile: int, kernel: str = "k_tile_warp"):
+    """DRAM bytes per launch of ``kernel`` from the committed ncu summary
+    (profiles/<kernel>_<workload>*.md), if it was taken on the current code of
+    kernels.cu with the same tile side (else None)."""
     import glob
     import re
     src = os.path.join(ROOT, "paper_1410_5780_gb300", "csrc", "kernels.cu")
@@ -229,12 +234,12 @@ def profiled_traffic(workload: str, tile: int):
         digest = code_digest(src)
     except OSError:
         return None
-    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"k_tile_warp_{workload}*.md"))):
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", f"{kernel}_{workload}*.md"))):
         try:
             rec = json.loads(re.search(r"<!-- traffic: (\{.*?\}) -->", open(path).read()).group(1))
         except (OSError, AttributeError, ValueError):
             continue
-        if rec.get("code_sha256") == digest and rec.get("tile") == tile:
+        if rec.get("code_sha256") == digest and rec.get("tile") == tile and rec.get("kernel", kernel) == kernel:
             return rec["bytes_per_launch"]
     return None
 
@@ -437,61 +442,114 @@ def serving_section(dev: int, n_requests: int) -> dict:
             "p99_ms": float(np.percentile(lat, 99)), "tests_per_s": total_tests / span, "requests": n_requests}
 
 
-def run_ours(args, rank, world, dist):
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def tile_kernel_rooflines(work, stages_ms, tile, n_waves, hbm_gbs, alu_tops, raster_peak, workload):
+    """Roofline figures of the two tile kernels per launch (one launch a wave).
+
+    Algorithmic work per launch, from the work counters of one evaluation:
+    * bytes (the HBM byte model of a depth-map design restricted to the
+      kernel's tiles): 4 B per texel of every tile it takes (the depth tile
+      written once) + 4 B per sample it tests (the texel gather);
+    * lane-ops: 12 per fragment (a kept triangle covering a texel a sample
+      reads: 3 edge functions, barycentric depth, key and minimum) + 14 per
+      sample test (position, projection, texel, compare);
+    * fragments F (k_raster_test: depth atomicMin writes into the shared tile).
+    """
+    nw = max(n_waves, 1)
+    heavy = {"tiles": work["heavy_tiles"], "samples": work["heavy_sample_tests"],
+             "fragments": work["heavy_texel_writes"], "ms": stages_ms["heavy"]}
+    warp = {"tiles": work["nonempty_tiles"] - work["heavy_tiles"],
+            "samples": work["sample_tests"] - work["heavy_sample_tests"],
+            "fragments": work["texel_writes"] - work["heavy_texel_writes"], "ms": stages_ms["raster"]}
+    out = {}
+    for name, k in (("k_tile_warp", warp), ("k_raster_test", heavy)):
+        launch_ms = k["ms"] / nw
+        t = max(launch_ms * 1e-3, 1e-12)
+        byts = (4.0 * tile * tile * k["tiles"] + 4.0 * k["samples"]) / nw
+        ops = (OPS_PER_TEXEL_WRITE * k["fragments"] + OPS_PER_SAMPLE_TEST * k["samples"]) / nw
+        gbs = byts / t / 1e9
+        tops = ops / t / 1e12
+        d = {"avg_launch_ms": launch_ms, "ms_per_step": k["ms"],
+             "per_launch": {"tiles": k["tiles"] / nw, "sample_tests": k["samples"] / nw,
+                            "fragments": k["fragments"] / nw, "algorithmic_bytes": byts, "lane_ops": ops},
+             "hbm": {"achieved": gbs, "peak": hbm_gbs, "unit": "GB/s", "frac": gbs / hbm_gbs},
+             "alu": {"achieved": tops, "peak": alu_tops, "unit": "T lane-ops/s", "frac": tops / alu_tops},
+             "traffic": profiled_traffic(workload, tile, name)}
+        if name == "k_raster_test" and raster_peak:
+            fr = k["fragments"] / nw / t / 1e9
+            d["raster"] = {"achieved": fr, "peak": raster_peak, "unit": "G atomicMin/s", "frac": fr / raster_peak}
+        out[name] = d
+    return out
+
+
+def path_byte_model(w, work, tile, chunk, n_steps_lit, t_ms_per_step):
+    """The hot path's algorithmic bytes per sun step (HBM byte model of a
+    depth-map design): 4 R2_occ (occupied-tile texels, written once) + 4 S
+    (one texel gathered per sample) + 36 T / K (triangles read once per wave
+    of K steps) + outputs (1 B per cell, 12 B per module)."""
+    r2_occ = work["nonempty_tiles"] * tile * tile / max(n_steps_lit, 1)
+    S = w.samples_per_step
+    T = int(w.scene.n_tris) + 2 * w.gen.n_modules
+    b_step = 4.0 * r2_occ + 4.0 * S + 36.0 * T / chunk + w.gen.n_cells + 12.0 * w.gen.n_modules
+    achieved = b_step * n_steps_lit / (t_ms_per_step * 1e-3) / 1e9
+    return {"R2_occ_per_step": r2_occ, "S": S, "T": T, "K": chunk, "bytes_per_step": b_step,
+            "achieved_GBps": achieved}
+
+
+def measure(args, name, dev, dist, rank, world, steps, warmup, tile=0, chunk=0):
+    """Time ``steps`` full evaluations of workload ``name`` on the production
+    path; returns the line's fields for it (rank 0) and the objects for the
+    e2e and extension sections."""
     import torch
-    from paper_1410_5780_gb300 import pv3d
-    pv3d.load(build_if_missing=True)
-    local = int(os.environ.get("LOCAL_RANK", rank))
-    dev = local if torch.cuda.device_count() > local else 0
-    torch.cuda.set_device(dev)
-    w = make_workload(args.workload, rank)
+    from paper_1410_5780_gb300 import autotune, pv3d
+    w = make_workload(name, rank)
     path = pv3d.PV3D_PATH_FUSED if args.path == "fused" else pv3d.PV3D_PATH_MAP
     # tile size, sun steps per wave and bin pool from the autotuner (short
     # timed trials, not part of the timed region); the map resolution is the
     # workload's own
-    from paper_1410_5780_gb300 import autotune
-    if args.tile and args.chunk:
-        tuned = {"tile": args.tile, "chunk_steps": args.chunk, "bin_capacity": 0}  # 0: the library's pool
+    if tile and chunk:
+        tuned = {"tile": tile, "chunk_steps": chunk, "bin_capacity": 0}  # 0: the library's pool
     else:
         tuned = autotune.autotune(w, device=dev, cache=None, n_windows=6)
-        tuned["tile"] = args.tile or tuned["tile"]
-    chunk = args.chunk or tuned["chunk_steps"]
+        tuned["tile"] = tile or tuned["tile"]
+    chunk = chunk or tuned["chunk_steps"]
     ctx = pv3d.Context(device=dev, map_res=w.map_res, chunk_steps=chunk, tile=tuned["tile"],
                        bin_capacity=tuned["bin_capacity"])
     gid = pv3d.load_workload(ctx, w)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=f"cuda:{dev}")
-
     sb, se = args.step_range or (0, 0)
 
     def evaluate(profile=0):
         return ctx.evaluate(gid, n=w.n, map_res=w.map_res, outputs=("energy", "energy_unshaded"),
                             stream=stream.cuda_stream, path=path, profile=profile, step_begin=sb, step_end=se)
 
-    for _ in range(max(args.warmup, 0)):
+    for _ in range(max(warmup, 0)):
         evaluate()
     torch.cuda.synchronize()
-    # timed region: K full-year evaluations, L2 flushed between them (outside the events)
+    # timed region: K evaluations on the production path (waves replayed from
+    # one captured CUDA graph), L2 flushed between them outside the events
     sampler = ClockSampler(dev)
     if dist is not None:
         dist.barrier()
     torch.cuda.synchronize()
     sampler.start()
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
-    stage_ms = np.zeros(len(pv3d.STAGES))
-    waves = 0
-    tests = 0
-    launches = 0
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    tests = launches = 0
     results = []
     torch.cuda.nvtx.range_push("timed")
-    for k in range(args.steps):
+    for k in range(steps):
         flush.zero_()
         ev[k][0].record(stream)
-        r = evaluate(profile=1)
+        r = evaluate(profile=0)
         ev[k][1].record(stream)
-        prof = ctx.last_profile()
-        stage_ms += np.array([prof[f"{s}_ms"] for s in pv3d.STAGES])
-        waves += prof["waves"]
         tests += r["tests"]
         launches += r["kernel_launches"]
         results.append(r)
@@ -501,89 +559,128 @@ def run_ours(args, rank, world, dist):
     t_ms = sum(a.elapsed_time(b) for a, b in ev)
     t_ms, tests_all = reduce_over_ranks(t_ms, tests, dist, f"cuda:{dev}")
     value = tests_all / (t_ms * 1e-3)
-
-    # work counters of one evaluation (untimed), for the roofline numerator
+    # untimed: the stage split (per-kernel launches with stage events) and
+    # the work counters (a counting run) of the same evaluation
+    torch.cuda.synchronize()
+    evaluate(profile=1)
+    prof = ctx.last_profile()
     evaluate(profile=3)
     work = ctx.last_profile()
     e_loss = 100.0 * (1.0 - float(results[-1]["energy"].sum()) / float(results[-1]["energy_unshaded"].sum()))
+    out = {"w": w, "ctx": ctx, "gid": gid, "stream": stream, "path": path, "tuned": tuned, "chunk": chunk}
+    if rank != 0:
+        return out
+    peaks = measured_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    props = torch.cuda.get_device_properties(dev)
+    alu_peak = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12  # T lane-ops/s
+    stages = {s_: float(prof[f"{s_}_ms"]) for s_ in pv3d.STAGES}
+    raster_peak = None
+    try:
+        raster_peak = pv3d.raster_peak(dev)["g_atomics_per_s"]
+    except (AttributeError, pv3d.PV3DError, OSError):
+        raster_peak = None
+    kern = tile_kernel_rooflines(work, stages, tuned["tile"], prof["waves"], hbm, alu_peak, raster_peak, name)
+    dom = max(kern, key=lambda k: kern[k]["ms_per_step"])
+    kd = kern[dom]
+    lit = int(results[-1]["steps_lit"])
+    t_step = t_ms / steps
+    model = path_byte_model(w, work, tuned["tile"], chunk, lit, t_step / max(world, 1) * max(world, 1))
+    model["frac"] = model["achieved_GBps"] / hbm
+    out["line"] = {
+        "value": value, "ms_per_step": t_step, "steps": steps, "warmup": warmup,
+        "config": dict(workload_config(w, name), path=args.path, l2="flushed between steps (512 MB write)",
+                       waves_per_step=int(prof["waves"]), annual_loss_pct=round(e_loss, 4),
+                       timed_path="production: each wave a replayed CUDA graph, no stage events",
+                       autotuned={"tile": tuned["tile"], "chunk_steps": chunk, "bin_capacity": tuned["bin_capacity"]}),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": kd["hbm"]["achieved"], "peak": hbm, "unit": "GB/s",
+                     "frac": kd["hbm"]["frac"], "traffic": kd["traffic"],
+                     "peak_source": "hbm_gbs of MEASURED_PEAKS.json (measured copy bandwidth)",
+                     "algorithmic": "4 B per texel of each tile the kernel takes (depth tile written once) + 4 B per "
+                                    "sample it tests (texel gather), per launch (one wave), over its average launch "
+                                    "time (stage events of an untimed run of the same evaluation)",
+                     "traffic_source": f"DRAM read+write bytes of one launch, ncu capture in profiles/{dom}_{name}*.md "
+                                       "taken with the same tile side (null if the code of kernels.cu changed since)",
+                     "alu": kd["alu"], "per_launch": kd["per_launch"], "avg_launch_ms": kd["avg_launch_ms"],
+                     "alu_peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz",
+                     "kernels": kern, "path_byte_model": model},
+        "work_per_step": {"sample_tests_in_tested_tiles": work["sample_tests"] / max(lit, 1),
+                          "fragments": work["texel_writes"] / max(lit, 1),
+                          "nonempty_tiles": work["nonempty_tiles"] / max(lit, 1),
+                          "heavy_tiles": work["heavy_tiles"] / max(lit, 1),
+                          "heavy_why_per_year": {"receivers": work["heavy_why"][0], "binned": work["heavy_why"][1],
+                                                 "kept": work["heavy_why"][2]},
+                          "binned_pairs": work["binned_tris"] / max(lit, 1),
+                          "pair_tests": work["pair_tests"] / max(lit, 1)},
+        "stages_ms_per_step": stages,
+        "gpu_launches": int(launches),
+        "clocks": clocks,
+    }
+    return out
 
+
+def e2e_section(m, args, world):
+    """The same metric through the C ABI with host arrays: scene, generator,
+    sun (and poses) uploaded from host memory, the evaluation with host
+    outputs, the energies read back -- every step."""
+    import torch
+    from paper_1410_5780_gb300 import pv3d
+    w, ctx = m["w"], m["ctx"]
+    h2d = input_bytes(w)
+    d2h = 16 * w.gen.n_modules
+    t_e2e = []
+    r2 = None
+    for k in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g2 = pv3d.load_workload(ctx, w)
+        r2 = ctx.evaluate(g2, n=w.n, map_res=w.map_res, outputs=("energy", "energy_unshaded"), device=False,
+                          path=m["path"])
+        ctx.release(g2)
+        t_e2e.append(time.perf_counter() - t0)
+    e2e_val = r2["tests"] / statistics.mean(t_e2e)
+    return {"value": e2e_val * world, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "includes": "scene/generator/sun/pose upload from host arrays, evaluation, host read-back of the "
+                        "energies (best of the library's pools, host wall clock)"}
+
+
+def run_ours(args, rank, world, dist):
+    import torch
+    from paper_1410_5780_gb300 import pv3d
+    pv3d.load(build_if_missing=True)
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    dev = local if torch.cuda.device_count() > local else 0
+    torch.cuda.set_device(dev)
+    m = measure(args, args.workload, dev, dist, rank, world, args.steps, args.warmup, args.tile, args.chunk)
     line = None
     if rank == 0:
-        peaks = {}
-        try:
-            with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-                peaks = json.load(f)
-        except OSError:
-            pass
-        sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-        props = torch.cuda.get_device_properties(dev)
-        alu_peak = props.multi_processor_count * 128 * sm_max * 1e6 / 1e12  # T lane-ops/s
-        # the dominant kernel: k_tile_warp (fused path; stage 2), whose work is
-        # the counters' total less the heavy-tile kernel's share (stage 3)
-        raster_launch_ms = stage_ms[2] / max(waves, 1)
-        nw = max(work["waves"], 1)
-        frag = (work["texel_writes"] - work["heavy_texel_writes"]) / nw
-        samp = (work["sample_tests"] - work["heavy_sample_tests"]) / nw
-        ops_per_launch = OPS_PER_TEXEL_WRITE * frag + OPS_PER_SAMPLE_TEST * samp
-        achieved = ops_per_launch / (raster_launch_ms * 1e-3) / 1e12
-        kname = "k_tile_warp" if args.path == "fused" else "k_raster_map"
-        line = {
-            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": t_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": dict(workload_config(w, args.workload), path=args.path, l2="flushed between steps (512 MB)",
-                           waves_per_step=waves // args.steps, annual_loss_pct=round(e_loss, 4),
-                           autotuned={"tile": tuned["tile"], "chunk_steps": chunk,
-                                      "bin_capacity": tuned["bin_capacity"]}),
-            "roofline": {"bound": "alu", "kernel": kname,
-                         "achieved": achieved, "peak": alu_peak, "unit": "T lane-ops/s",
-                         "frac": achieved / alu_peak, "traffic": profiled_traffic(args.workload, tuned["tile"]),
-                         "traffic_source": "DRAM read+write bytes of the first timed launch, ncu capture in "
-                                           f"profiles/k_tile_warp_{args.workload}*.md taken with the same tile side (null if the code of "
-                                           "kernels.cu changed since)",
-                         "peak_source": f"{props.multi_processor_count} SMs x 128 FP32 lanes x {sm_max:.0f} MHz "
-                                        "(sm_max_mhz of MEASURED_PEAKS.json)",
-                         "work_per_launch": {"fragments": frag, "sample_tests": samp,
-                                             "pair_tests": work["pair_tests"] / nw,
-                                             "candidates": work["candidates"] / nw},
-                         "avg_launch_ms": raster_launch_ms,
-                         "heavy_tiles": {"share_of_tiles": work["heavy_tiles"] / max(work["nonempty_tiles"], 1),
-                                         "ms_per_step": float(stage_ms[3] / args.steps)}},
-            "stages_ms_per_step": {s: float(stage_ms[i] / args.steps) for i, s in enumerate(pv3d.STAGES)},
-            "gpu_launches": int(launches),
-            "clocks": clocks,
-        }
-
-    # end to end through the C ABI with host buffers: load, define, sun, evaluate, read back
+        line = {"metric": METRIC, "value": m["line"]["value"], "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["line"]["ms_per_step"],
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic"}
+        line.update({k: v for k, v in m["line"].items() if k not in ("value", "ms_per_step", "steps", "warmup")})
     if not args.no_e2e:
-        h2d = input_bytes(w)
-        d2h = 16 * w.gen.n_modules
-        t_e2e = []
-        for k in range(max(1, min(args.steps, 3))):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            g2 = pv3d.load_workload(ctx, w)
-            r2 = ctx.evaluate(g2, n=w.n, map_res=w.map_res, outputs=("energy", "energy_unshaded"), device=False,
-                              path=path)
-            ctx.release(g2)
-            t_e2e.append(time.perf_counter() - t0)
-        e2e_val = r2["tests"] / statistics.mean(t_e2e)
+        e2e = e2e_section(m, args, world)
         if rank == 0:
-            line["e2e"] = {"value": e2e_val * world, "unit": UNIT, "h2d_bytes_per_step": h2d,
-                           "d2h_bytes_per_step": d2h, "includes": "scene/generator/sun upload from host arrays, "
-                           "evaluation, host read-back of the energies"}
-
+            line["e2e"] = e2e
     if rank == 0 and not args.no_serving and args.workload == "tracker":
-        line["extensions"] = tracker_windows_section(ctx, gid, w, stream)
-    if rank == 0 and not args.no_serving and args.workload == "facade":
-        line["extensions"] = extensions_section(ctx, gid, w, stream)
-        bt = batched_section(dev, args.batch_scenes)
-        line["batched"] = bt
-        line["serving"] = serving_section(dev, args.requests)
+        line["extensions"] = tracker_windows_section(m["ctx"], m["gid"], m["w"], m["stream"])
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, cores, sample, _ = oracle_sample_run(w, budget_s=15.0)
+        v, cores, sample, _ = oracle_sample_run(m["w"], budget_s=15.0)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
-    ctx.close()
+    m["ctx"].close()
+    # the facade (the secondary workload): the same measurement, its own line fields
+    if args.workload != "facade" and not args.no_facade and args.step_range is None:
+        f = measure(args, "facade", dev, dist, rank, world, max(3, args.steps), max(3, args.warmup))
+        if rank == 0:
+            line["facade"] = f["line"]
+            if not args.no_serving:
+                line["facade"]["extensions"] = extensions_section(f["ctx"], f["gid"], f["w"], f["stream"])
+        f["ctx"].close()
+    if rank == 0 and not args.no_serving and world == 1:
+        line["batched"] = batched_section(dev, args.batch_scenes)
+        line["serving"] = serving_section(dev, args.requests)
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -430,6 +430,22 @@ int pv3d_last_profile(pv3d_ctx* ctx, pv3d_profile* out);
 /* Free a scene (and every generator defined on it) or a generator. */
 int pv3d_release(pv3d_ctx* ctx, uint32_t scene_or_gen_id);
 
+/* ---- measured raster roofline ------------------------------------------------
+ *
+ * The rasterising kernels draw a tile's depth in shared memory with atomicMin
+ * of 32-bit order-preserving keys (Fig. 3: the depth buffer keeps the surface
+ * nearest the sun).  Their roofline is this operation's throughput on the
+ * device, measured here: 16 blocks of 128 threads per SM, each block a 32 x 32
+ * shared tile of keys, warps updating strips of 32 consecutive texels (the
+ * rasteriser's access pattern), best of 5 timed launches of 2^14 updates per
+ * thread after a warm-up launch (CUDA events on a private stream).
+ *   device         CUDA device ordinal; the caller's current device is restored
+ *   atomics_per_s  out: shared-memory atomicMin updates per second, whole GPU
+ *   best_ms        out (may be NULL): the best launch's duration
+ * Allocates 4 bytes of device memory for the fold of the tiles and frees it.
+ * Returns PV3D_OK, PV3D_E_INVALID (NULL output) or PV3D_E_DEVICE. */
+int pv3d_raster_peak(int32_t device, double* atomics_per_s, double* best_ms);
+
 /* ---- evaluation without device allocation --------------------------------
  *
  * The paper has no counterpart to this call: it serves callers that cannot
@@ -440,9 +456,14 @@ int pv3d_release(pv3d_ctx* ctx, uint32_t scene_or_gen_id);
  *
  * Shaded-sample counts of ONE fixed module for ONE sun direction: the
  * triangles are depth-rasterised from the sun into a map of map_res^2 texels
- * over the module's window (same frame, window, coverage and bias rules as
- * pv3d_evaluate) and every one of the module's n x n samples per cell is
- * depth-tested against it.
+ * over the module's window and every one of the module's n x n samples per
+ * cell is depth-tested against it.  The rules follow pv3d_evaluate's (light
+ * frame, window of one texel padding, texel-centre coverage, slope-scaled
+ * bias), but the frame is built in FP64 on the host for every elevation, the
+ * coordinates are taken relative to the module's centre and each triangle is
+ * rasterised by one warp: counts can differ from pv3d_evaluate's for samples
+ * at texel edges (the tests accept one sample per cell and 0.1 % of all
+ * samples), not bit for bit.
  *   tri_xyz       device pointer, 9 floats per triangle (three world vertices, m)
  *   module        host pointer; tracker must be -1; its layout is not used
  *   sun_xyz       host pointer, unit vector toward the sun; s.z <= 0 gives zeros
@@ -453,12 +474,20 @@ int pv3d_release(pv3d_ctx* ctx, uint32_t scene_or_gen_id);
  *   stream        cudaStream_t the work is queued on (NULL = legacy stream);
  *                 the call returns without waiting for it
  * The shadow map is one fixed array compiled into the library
- * (PV3D_NOALLOC_MAX_RES^2 x 4 bytes = 16 MiB on every GPU that loads it, kept
- * until the process exits); the call allocates nothing.  The first call on a
- * device, with that device current, looks up the array's device address;
- * make that first call before any stream capture.  All calls share the array:
- * each clears the part it uses, and calls that overlap on the GPU (different
- * streams without ordering) race on it.
+ * (PV3D_NOALLOC_MAX_RES^2 x 4 bytes = 16 MiB per GPU, kept until the process
+ * exits); the call allocates nothing itself.  With CUDA's lazy module loading
+ * (the default) the array is reserved on a device when the library's module
+ * is first loaded there, i.e. by the first call on that device: a caller
+ * whose own pool takes all device memory should make one call before creating
+ * the pool.  Each call looks up the array's device address for the current
+ * device and context (after cudaDeviceReset the module loads again at a new
+ * address); while `stream` is being captured no lookup is made and the address
+ * found by the last uncaptured call on that device is used, so make one call
+ * before any stream capture (else PV3D_E_DEVICE).  Launch failures of the
+ * call's own kernels return PV3D_E_DEVICE; an earlier error of the caller's
+ * is neither reported nor cleared.  All calls share the array: each clears the
+ * part it uses, and calls that overlap on the GPU (different streams without
+ * ordering) race on it.
  */
 #define PV3D_NOALLOC_MAX_RES 2048
 int pv3d_module_shade_noalloc(const float* tri_xyz, int64_t n_tris, const pv3d_module* module,

@@ -1,6 +1,6 @@
 """Build the pv3d CUDA library (sm_103a) in-tree: paper_1410_5780_gb300/_build/libpv3d.so.
 
-Two translation units are compiled in parallel with nvcc and linked into one
+The translation units are compiled in parallel with nvcc and linked into one
 shared library exporting the C ABI declared in include/pv3d.h.
 """
 from __future__ import annotations
@@ -15,7 +15,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpv3d.so")
-SOURCES = ["kernels.cu", "api.cu", "noalloc.cu"]
+SOURCES = ["kernels.cu", "api.cu", "noalloc.cu", "peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

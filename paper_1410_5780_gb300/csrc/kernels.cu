@@ -994,6 +994,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_c(const WaveDev* __restri
 // ---------------------------------------------------------------------------
 constexpr int kRecvChunk = 64;  // receivers staged in shared memory at a time (two per lane of one warp)
 constexpr int kTriBatchMax = 128;  // triangles set up in shared memory at a time by the rasteriser (one per thread)
+constexpr int kMaxTri = 256;    // triangles a block-wide tile may keep for the sample-driven test
 // Sub-blocks per tile side in the sample-driven test (4, 8 and 16 texels on
 // 32-, 64- and 128-texel tiles; a 16 x 16 grid on 128-texel tiles tests fewer
 // triangles per sample but costs more in its masks than it saves).
@@ -1001,6 +1002,14 @@ template <int TS>
 struct SubGrid {
     static constexpr int side = 8;
     static constexpr int blocks = side * side;
+};
+// Triangles a heavy-tile block may keep for its sample-driven test: 32-texel
+// tiles are always rasterised (k_raster_test), so their shared memory holds
+// only a token list and more blocks fit an SM.
+template <int TS>
+struct HeavyKept {
+    static constexpr int n = TS == 32 ? 32 : kMaxTri;
+    static constexpr int words = n / 32;
 };
 static_assert(kRecvChunk == 64, "receiver prefix sums take two entries per lane of one warp");
 
@@ -1112,7 +1121,9 @@ struct RasterSm {
 template <int TS, int NT, bool SEEN>
 struct KeptSm {
     TriS tri[NT];
-    uint2 smask[NT];                        // per triangle: the sub-blocks (bit sb) it may shade a sample of
+    uint32_t box[NT];                       // texel box x0 | y0 << 8 | x1 << 16 | y1 << 24
+    float dmin[NT];                         // nearest vertex depth
+    uint2 smask[NT];                        // strict keep: the sub-blocks (bit sb) it may shade a sample of
     float dlim[SubGrid<TS>::blocks];        // per sub-block: a triangle shades none of its samples
                                             // unless its nearest depth is below this
     uint32_t sbm[SubGrid<TS>::blocks][NT / 32];  // per sub-block: triangles that may shade one of its samples
@@ -1121,16 +1132,27 @@ struct KeptSm {
 static_assert(SubGrid<32>::blocks == 64 && SubGrid<64>::blocks == 64 && SubGrid<128>::blocks == 64,
               "a triangle's sub-block set is one 64-bit mask");
 
+// Summary of a tile's sub-block depth limits (sub_summary).
+struct SubInfo {
+    uint2 occ;   // sub-blocks some receiver meets
+    float dlo;   // smallest limit among them
+};
+
 template <int TS>
 struct TileSm {
-    RasterSm<TS> r;
+    union {
+        RasterSm<TS> r;
+        KeptSm<TS, HeavyKept<TS>::n, true> s;
+    } u;
     float dlim[SubGrid<TS>::blocks]; // per sub-block depth limit (sub_limits)
+    SubInfo si;                      // their summary (sub_summary)
     uint32_t mask[TS * TS / 32];     // texels read by some sample (sparse tiles)
     uint32_t row_start[TS + 1];      // start of each row in `list`
     RecvSm recv[kRecvChunk];
     int n_recv;                      // receivers staged
     int total_items;                 // (sample row, cell column) items over the staged receivers
     int any_write;                   // some texel of the tile received a depth
+    int n_tri;                       // triangles kept by the sample-driven set-up
     TriSetup tri[kTriBatchMax];      // a batch of set-up triangles, one per thread
     int chunk_pref[kTriBatchMax + 1];  // prefix of their 32-texel work chunks
 };
@@ -1354,45 +1376,90 @@ __device__ __forceinline__ bool tri_box(const TriT& T, int& x0, int& x1, int& y0
 // decision as a depth test against the tile's stored minimum (the comparison
 // is monotone in the stored depth), with the same arithmetic per triangle.
 
+// Summary of a tile's sub-block depth limits, for tri_sub_mask's fast path:
+// the sub-blocks that any receiver meets (limit above -inf) and the smallest
+// limit among them.  Called by one full warp once the limits are written.
+__device__ __forceinline__ SubInfo sub_summary(const float* dlim)
+{
+    const int lane = threadIdx.x & 31;
+    const float a = dlim[lane], b = dlim[lane + 32];
+    SubInfo si;
+    si.occ.x = __ballot_sync(0xffffffffu, a > -FLT_MAX);
+    si.occ.y = __ballot_sync(0xffffffffu, b > -FLT_MAX);
+    float lo = fminf(a > -FLT_MAX ? a : FLT_MAX, b > -FLT_MAX ? b : FLT_MAX);
+#pragma unroll
+    for (int off = 16; off; off >>= 1) lo = fminf(lo, __shfl_xor_sync(0xffffffffu, lo, off));
+    si.dlo = lo;
+    return si;
+}
+
 // The sub-blocks of the tile in which a set-up triangle may shade a sample
 // (bit sb = sy * side + sx): its nearest vertex is nearer than the
 // sub-block's depth limit, and each edge function is non-negative at the
 // texel centre of (its texel box within the sub-block) farthest inside the
 // edge -- exact, since edge_at is monotone in px and py, so a texel centre
 // of the sub-block that the triangle covers implies a non-negative value
-// there.  A triangle with no such sub-block cannot shade any sample of the
-// tile and is not kept.
+// there.  Row by row of sub-blocks: when every edge is non-negative at the
+// row's corner farthest outside it, the triangle covers every texel centre
+// of its box in that row, and when its nearest vertex is also nearer than the
+// tile's smallest limit, the row's bits are the occupied sub-blocks of the
+// box's columns.  A triangle with no such sub-block cannot shade any sample
+// of the tile and is not kept.
 template <int TS>
 __device__ __forceinline__ uint64_t tri_sub_mask(const Edges& ed, int x0, int x1, int y0, int y1, float dmin,
-                                                 const float* dlim)
+                                                 const float* dlim, const SubInfo& si)
 {
     constexpr int kSubSide = SubGrid<TS>::side;
     constexpr int SW = TS / kSubSide;  // sub-block side, texels
+    static_assert(kSubSide == 8, "a row of sub-blocks is one byte of the mask");
+    const uint64_t occ = (uint64_t)si.occ.x | ((uint64_t)si.occ.y << 32);
+    const int sx0 = x0 / SW, sx1 = x1 / SW;
+    const uint64_t cols = (uint64_t)((2u << sx1) - (1u << sx0));  // bits sx0..sx1 of a row
+    const bool near_all = dmin < si.dlo;
+    const float fxl = texel_centre(x0), fxh = texel_centre(x1);
     uint64_t m = 0ull;
     for (int sy = y0 / SW; sy <= y1 / SW; ++sy) {
         const float fy0 = texel_centre(max(y0, sy * SW)), fy1 = texel_centre(min(y1, sy * SW + SW - 1));
-        for (int sx = x0 / SW; sx <= x1 / SW; ++sx) {
-            const int sb = sy * kSubSide + sx;
-            if (!(dmin < dlim[sb])) continue;
-            const float fx0 = texel_centre(max(x0, sx * SW)), fx1 = texel_centre(min(x1, sx * SW + SW - 1));
-            bool in = true;
+        float t[3];
+        bool full = true;
 #pragma unroll
-            for (int k = 0; k < 3; ++k)
-                in = in && edge_at(ed.A[k], ed.Bc[k], ed.C[k], ed.A[k] > 0.f ? fx1 : fx0,
-                                   ed.Bc[k] > 0.f ? fy1 : fy0) >= 0.f;
-            if (in) m |= 1ull << sb;
+        for (int k = 0; k < 3; ++k) {
+            t[k] = __fmaf_rn(ed.Bc[k], ed.Bc[k] > 0.f ? fy1 : fy0, ed.C[k]);
+            full = full && edge_at(ed.A[k], ed.Bc[k], ed.C[k], ed.A[k] > 0.f ? fxl : fxh,
+                                   ed.Bc[k] > 0.f ? fy0 : fy1) >= 0.f;
+        }
+        const uint64_t row = (cols << (8 * sy)) & occ;
+        if (full && near_all) {
+            m |= row;
+            continue;
+        }
+        for (uint64_t r = row; r; r &= r - 1ull) {
+            const int sb = __ffsll((long long)r) - 1;
+            if (!(dmin < dlim[sb])) continue;
+            if (!full) {
+                const int sx = sb & 7;
+                const float fx0 = texel_centre(max(x0, sx * SW)), fx1 = texel_centre(min(x1, sx * SW + SW - 1));
+                bool in = true;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) in = in && __fmaf_rn(ed.A[k], ed.A[k] > 0.f ? fx1 : fx0, t[k]) >= 0.f;
+                if (!in) continue;
+            }
+            m |= 1ull << sb;
         }
     }
     return m;
 }
 
 // Set up binned triangle t of tile (ox, oy) for the sample-driven test: false
-// if it lies behind every staged receiver or may shade no sample of any
-// sub-block (tri_sub_mask, with the sub-block depth limits dlim).
+// if it lies behind every staged receiver or covers no texel centre of the
+// tile; with `strict`, also if it may shade no sample of any sub-block
+// (tri_sub_mask with the sub-block depth limits dlim), its sub-blocks in
+// smask.  box and dmin feed sub_masks (loose keep).
 template <int TS, bool PROF>
 __device__ __forceinline__ bool setup_tri_s(const JobDev& J, const Buffers& B, const LightParams& lp, int ls, int t,
                                             float ox, float oy, const RecvSm* recv, int n_recv, bool cull_ok,
-                                            const float* dlim, TriS& ts, uint64_t& smask, unsigned int& culled)
+                                            bool strict, const float* dlim, const SubInfo& si, TriS& ts,
+                                            uint32_t& box, float& dmin, uint64_t& smask, unsigned int& culled)
 {
     TriT T;
     tri_texel(J, B, lp, ls, t, T);
@@ -1405,12 +1472,16 @@ __device__ __forceinline__ bool setup_tri_s(const JobDev& J, const Buffers& B, c
     Edges ed;
     int x0, x1, y0, y1;
     if (!make_edges(T, ed) || !tri_box<TS>(T, x0, x1, y0, y1)) return false;
-    smask = tri_sub_mask<TS>(ed, x0, x1, y0, y1, fminf(T.d[0], fminf(T.d[1], T.d[2])), dlim);
-    if (smask == 0ull) return false;
+    dmin = fminf(T.d[0], fminf(T.d[1], T.d[2]));
+    if (strict) {
+        smask = tri_sub_mask<TS>(ed, x0, x1, y0, y1, dmin, dlim, si);
+        if (smask == 0ull) return false;
+    }
     const float inv_a = 1.f / ed.area2;
     ts.p = make_float4(ed.A[0], ed.Bc[0], ed.C[0], ed.A[1]);
     ts.q = make_float4(ed.Bc[1], ed.C[1], ed.A[2], ed.Bc[2]);
     ts.r = make_float4(ed.C[2], T.d[0] * inv_a, T.d[1] * inv_a, T.d[2] * inv_a);
+    box = (uint32_t)x0 | ((uint32_t)y0 << 8) | ((uint32_t)x1 << 16) | ((uint32_t)y1 << 24);
     return true;
 }
 
@@ -1446,8 +1517,46 @@ __device__ __forceinline__ void sub_limits(const RecvSm* recv, int n_recv, float
 }
 
 // Per sub-block of the tile, the kept triangles that may shade one of its
+// samples: nearest depth below the sub-block's limit, box overlap, then each
+// edge at the sub-block's texel centre farthest inside it (exact: edge_at is
+// monotone in px and py, so a covered texel of the sub-block implies a
+// non-negative value there).  Entries q = q_begin, q_begin + q_stride, ... <
+// 64 * words(n) of sbm are written.
+template <int TS, int WORDS>
+__device__ __forceinline__ void sub_masks(const TriS* tri, const uint32_t* boxes, const float* dmin,
+                                          const float* dlim, uint32_t (*sbm)[WORDS], int n, int q_begin, int q_stride)
+{
+    constexpr int kSubSide = SubGrid<TS>::side, kSubBlocks = SubGrid<TS>::blocks;
+    constexpr int SW = TS / kSubSide;  // sub-block side, texels
+    const int nw = (n + 31) >> 5;
+    for (int q = q_begin; q < kSubBlocks * nw; q += q_stride) {
+        const int sb = q & (kSubBlocks - 1), w = q / kSubBlocks;
+        const int sx = (sb % kSubSide) * SW, sy = (sb / kSubSide) * SW;
+        const float fx0 = (float)sx + 0.5f, fx1 = (float)(sx + SW - 1) + 0.5f;
+        const float fy0 = (float)sy + 0.5f, fy1 = (float)(sy + SW - 1) + 0.5f;
+        const float lim = dlim[sb];
+        uint32_t m = 0u;
+        const int kend = min(32, n - w * 32);
+        for (int k = 0; k < kend; ++k) {
+            const int t = w * 32 + k;
+            if (!(dmin[t] < lim)) continue;
+            const uint32_t bx = boxes[t];
+            const int x0 = bx & 255u, y0 = (bx >> 8) & 255u, x1 = (bx >> 16) & 255u, y1 = bx >> 24;
+            if (x0 > sx + SW - 1 || x1 < sx || y0 > sy + SW - 1 || y1 < sy) continue;
+            const float4 p = tri[t].p, qq = tri[t].q, r = tri[t].r;
+            if (edge_at(p.x, p.y, p.z, p.x > 0.f ? fx1 : fx0, p.y > 0.f ? fy1 : fy0) < 0.f) continue;
+            if (edge_at(p.w, qq.x, qq.y, p.w > 0.f ? fx1 : fx0, qq.x > 0.f ? fy1 : fy0) < 0.f) continue;
+            if (edge_at(qq.z, qq.w, r.x, qq.z > 0.f ? fx1 : fx0, qq.w > 0.f ? fy1 : fy0) < 0.f) continue;
+            m |= 1u << k;
+        }
+        sbm[sb][w] = m;
+    }
+}
+
+// Per sub-block of the tile, the kept triangles that may shade one of its
 // samples (bit k of word w: kept triangle 32 w + k), transposed from the
-// triangles' sub-block masks with one ballot per sub-block.  Words w =
+// triangles' sub-block masks: for a few triangles each lane gathers its two
+// sub-blocks' bits, else one ballot per sub-block.  Words w =
 // w_begin, w_begin + w_stride, ... of the n kept triangles are written; called
 // by whole warps.
 template <int WORDS>
@@ -1456,6 +1565,19 @@ __device__ __forceinline__ void build_sbm(const uint2* smask, uint32_t (*sbm)[WO
 {
     const int lane = threadIdx.x & 31;
     const int nw = (n + 31) >> 5;
+    if (n <= 24) {
+        // few triangles: each lane assembles its two sub-blocks' words
+        if (w_begin != 0) return;
+        uint32_t lo = 0u, hi = 0u;
+        for (int t = 0; t < n; ++t) {
+            const uint2 m = smask[t];
+            lo |= ((m.x >> lane) & 1u) << t;
+            hi |= ((m.y >> lane) & 1u) << t;
+        }
+        sbm[lane][0] = lo;
+        sbm[lane + 32][0] = hi;
+        return;
+    }
     for (int w = w_begin; w < nw; w += w_stride) {
         const int t = (w << 5) | lane;
         const uint2 m = t < n ? smask[t] : make_uint2(0u, 0u);
@@ -1578,7 +1700,7 @@ __device__ __forceinline__ void test_items(const RecvSm* recv, int n_recv, int t
 
 // ---- tile rasteriser ------------------------------------------------------
 
-// Rasterise the tile's triangles into sm.r.tile.  Sparse tiles (fewer samples
+// Rasterise the tile's triangles into sm.u.r.tile.  Sparse tiles (fewer samples
 // than two per texel) are rasterised only at the texels their samples read;
 // each triangle then visits its bounding box or the marked texels of its
 // rows, whichever is fewer.  A triangle is drawn only in the sub-blocks where
@@ -1589,10 +1711,27 @@ __device__ __forceinline__ void test_items(const RecvSm* recv, int n_recv, int t
 // bias").  Receivers [r0, r0 + nrecv) must be staged (the first kRecvChunk of
 // them) on entry.  Returns 0 if no sample reads the tile or nothing was drawn
 // at a texel a sample reads.
+// The tile's sub-block depth limits (sub_limits, or no limit when the
+// receivers are staged in chunks) and their summary, for the whole block.
+template <int TS>
+__device__ __forceinline__ void tile_limits(TileSm<TS>& sm, const LightParams& lp, int u24, bool cull_ok)
+{
+    const int tid = threadIdx.x, bd = blockDim.x;
+    if (cull_ok) sub_limits<TS>(sm.recv, sm.n_recv, sm.dlim, u24 ? 1.f / lp.qscale : 0.f, tid, bd);
+    else
+        for (int q = tid; q < SubGrid<TS>::blocks; q += bd) sm.dlim[q] = FLT_MAX;
+    __syncthreads();
+    if (tid < 32) {
+        const SubInfo si = sub_summary(sm.dlim);
+        if (tid == 0) sm.si = si;
+    }
+    __syncthreads();
+}
+
 template <int TS, bool PROF>
 __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, const WaveDev* W, int ls, int tx,
-                           int ty, int64_t te, uint64_t r0, int nrecv, unsigned int& visits, unsigned int& writes,
-                           unsigned int& culled, unsigned int& cand, unsigned int& dense_n)
+                           int ty, int64_t te, uint64_t r0, int nrecv, bool limits_ready, unsigned int& visits,
+                           unsigned int& writes, unsigned int& culled, unsigned int& cand, unsigned int& dense_n)
 {
     constexpr int SH = TS == 128 ? 7 : (TS == 64 ? 6 : 5);
     constexpr int WPR = TS / 32;
@@ -1611,9 +1750,7 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
     // the texels that samples read
     const bool dense = est >= 2 * TS * TS;
     if (PROF && threadIdx.x == 0 && dense) ++dense_n;
-    if (cull_ok) sub_limits<TS>(sm.recv, sm.n_recv, sm.dlim, u24 ? 1.f / lp.qscale : 0.f, tid, bd);
-    else
-        for (int q = tid; q < SubGrid<TS>::blocks; q += bd) sm.dlim[q] = FLT_MAX;
+    if (!limits_ready) tile_limits<TS>(sm, lp, u24, cull_ok);
     int n_need = TS * TS;
     if (!dense) {
         for (int q = tid; q < TS * WPR; q += bd) sm.mask[q] = 0u;
@@ -1660,14 +1797,14 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
             for (int w2 = 0; w2 < w; ++w2) pos += __popc(sm.mask[y * WPR + w2]);
             while (bits) {
                 const int bit = __ffs(bits) - 1;
-                sm.r.list[pos++] = (uint16_t)(y * TS + w * 32 + bit);
+                sm.u.r.list[pos++] = (uint16_t)(y * TS + w * 32 + bit);
                 bits &= bits - 1;
             }
         }
         __syncthreads();
         n_need = (int)sm.row_start[TS];
     }
-    uint4* t4 = reinterpret_cast<uint4*>(sm.r.tile);
+    uint4* t4 = reinterpret_cast<uint4*>(sm.u.r.tile);
     for (int q = tid; q < TS * TS / 4; q += bd) t4[q] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
     if (tid == 0) sm.any_write = 0;
     __syncthreads();
@@ -1697,7 +1834,7 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
                 if (PROF) ++culled;
             } else if (make_edges(T, ed) && tri_box<TS>(T, x0, x1, y0, y1)) {
                 const uint64_t sb = tri_sub_mask<TS>(ed, x0, x1, y0, y1, fminf(T.d[0], fminf(T.d[1], T.d[2])),
-                                                     sm.dlim);
+                                                     sm.dlim, sm.si);
                 if (sb != 0ull) {
                     const float inv_a = 1.f / ed.area2;
 #pragma unroll
@@ -1750,7 +1887,7 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
                 if (q >= work) continue;
                 int ix, iy;
                 if (is_list) {
-                    const int p = sm.r.list[q_beg + q];
+                    const int p = sm.u.r.list[q_beg + q];
                     ix = p & (TS - 1);
                     iy = p >> SH;
                     if (ix < x0 || ix >= x0 + bw) continue;
@@ -1768,7 +1905,7 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
                 const float w2 = edge_at(A2, B2, C2, px, py);
                 if (PROF) ++visits;
                 if (w0 >= 0.f && w1 >= 0.f && w2 >= 0.f) {
-                    atomicMin(&sm.r.tile[iy * TS + ix], depth_store_key(depth_at(w0, w1, w2, e0, e1, e2), lp, u24));
+                    atomicMin(&sm.u.r.tile[iy * TS + ix], depth_store_key(depth_at(w0, w1, w2, e0, e1, e2), lp, u24));
                     wrote = true;
                     if (PROF) ++writes;
                 }
@@ -1930,17 +2067,32 @@ __global__ void __launch_bounds__(kTileWarps * 32, 6) k_tile_warp(const WaveDev*
             sub_limits<TS>(sm.recv, nrecv, sm.k.dlim, u24 ? 1.f / lp.qscale : 0.f, lane, 32);
             __syncwarp();
             const float ox = (float)(tx * TS), oy = (float)(ty * TS);
+            // strict keep (only the triangles that may shade a sample of some
+            // sub-block, tri_sub_mask: fewer kept, tighter sub-block masks,
+            // more set-up per triangle) on 32-texel tiles, whose samples are
+            // dense over few texels, and on crowded tiles; otherwise the loose
+            // keep (in front of some receiver's plane, covering a texel centre
+            // of the tile), cheaper for the few large triangles of a 64- or
+            // 128-texel tile (measured on the tracker plant and the facade)
+            const bool strict = TS == 32 || cnt > (uint64_t)kWarpTri;
+            SubInfo si{};
+            if (strict) si = sub_summary(sm.k.dlim);
             int n = 0;
             for (uint64_t b0 = 0; b0 < cnt && n <= kWarpTri; b0 += 32) {
                 TriS ts;
+                uint32_t box = 0u;
+                float dmin = 0.f;
                 uint64_t smask = 0ull;
                 const bool keep = b0 + lane < cnt &&
                                   setup_tri_s<TS, PROF>(J, B, lp, ls, (int)B.bins[off + b0 + lane], ox, oy, sm.recv,
-                                                        nrecv, true, sm.k.dlim, ts, smask, p_culled);
+                                                        nrecv, true, strict, sm.k.dlim, si, ts, box, dmin, smask,
+                                                        p_culled);
                 const unsigned int bal = __ballot_sync(0xffffffffu, keep);
                 const int slot = n + __popc(bal & ((1u << lane) - 1u));
                 if (keep && slot < kWarpTri) {
                     sm.k.tri[slot] = ts;
+                    sm.k.box[slot] = box;
+                    sm.k.dmin[slot] = dmin;
                     sm.k.smask[slot] = make_uint2((uint32_t)smask, (uint32_t)(smask >> 32));
                 }
                 n += __popc(bal);
@@ -1949,7 +2101,8 @@ __global__ void __launch_bounds__(kTileWarps * 32, 6) k_tile_warp(const WaveDev*
             if (PROF && lane == 0 && heavy) ++p_ht;
             if (!heavy && n > 0) {
                 __syncwarp();
-                build_sbm<kWarpWords>(sm.k.smask, sm.k.sbm, n, 0, 1);
+                if (strict) build_sbm<kWarpWords>(sm.k.smask, sm.k.sbm, n, 0, 1);
+                else sub_masks<TS, kWarpWords>(sm.k.tri, sm.k.box, sm.k.dmin, sm.k.dlim, sm.k.sbm, n, lane, 32);
                 __syncwarp();
                 const int C = J.n_cells;
                 test_items<TS, kWarpWords, PROF>(sm.recv, nrecv, total, J, lp, u24, tx, ty, lane, 32, sm.k.tri, n,
@@ -1986,15 +2139,66 @@ __global__ void __launch_bounds__(kTileWarps * 32, 6) k_tile_warp(const WaveDev*
 
 // ---------------------------------------------------------------------------
 // k_raster_test: fused path, the tiles k_tile_warp listed (more receivers,
-// binned or kept triangles than a warp takes) -- one CTA per tile: the tile
-// is rasterised in shared memory (tile_raster: texel-centre coverage,
-// atomicMin of order-preserving depth keys, only at the texels samples read
-// and only where a triangle may shade one), then every sample that reads the
-// tile is depth-tested against it.  Measured on the tracker plant, the
-// shared-memory depth tile beats a block-wide sample-by-sample test of the
-// kept triangles for every kept count: samples behind many thin members
-// (lattice pylons) test each candidate triangle, texels are written once.
+// binned or kept triangles than a warp takes) -- one CTA per tile.  On 64-
+// and 128-texel tiles the binned triangles are first set up by the whole
+// block, keeping those that may shade a sample of some sub-block
+// (tri_sub_mask); with at most kMaxTri kept, every sample is tested against
+// the kept triangles of its sub-block (few large triangles over sparse
+// samples: most samples stop at their first occluder).  Otherwise, and always
+// on 32-texel tiles, the tile is rasterised in shared memory (tile_raster:
+// texel-centre coverage, atomicMin of order-preserving depth keys, only at
+// the texels samples read and only where a triangle may shade) and the
+// samples read it (many small triangles -- lattice members, grazing terrain
+// -- each drawn once instead of tested by every sample near it; measured
+// faster on the tracker plant for every kept count).  Both give the same
+// decisions.
 // ---------------------------------------------------------------------------
+
+// Set up the tile's binned triangles that may shade a sample of a staged
+// receiver (strict keep), for the whole block; the sub-block depth limits
+// must be ready (tile_limits).  Returns how many were kept, or -1 if more than
+// kMaxTri were.
+template <int TS, bool PROF>
+__device__ int setup_sample_tris(TileSm<TS>& sm, const JobDev& J, const Buffers& B, const WaveDev* W,
+                                 const LightParams& lp, int ls, int tx, int ty, int64_t te, bool cull_ok,
+                                 unsigned int& culled)
+{
+    const int tid = threadIdx.x, lane = tid & 31;
+    const float ox = (float)(tx * TS), oy = (float)(ty * TS);
+    const uint64_t off = B.t_off[te];
+    uint64_t cnt = B.t_cnt[te];
+    const uint64_t cap = (uint64_t)W->bin_cap;
+    if (off + cnt > cap) cnt = off < cap ? cap - off : 0;
+    if (PROF)
+        for (int q = tid; q < TS * TS / 32; q += blockDim.x) sm.u.s.seen[q] = 0u;
+    if (tid == 0) sm.n_tri = 0;
+    __syncthreads();
+    const SubInfo si = sm.si;
+    for (uint64_t b0 = 0; b0 < cnt; b0 += blockDim.x) {
+        TriS ts;
+        uint32_t box = 0u;
+        float dmin = 0.f;
+        uint64_t smask = 0ull;
+        const bool keep = b0 + tid < cnt &&
+                          setup_tri_s<TS, PROF>(J, B, lp, ls, (int)B.bins[off + b0 + tid], ox, oy, sm.recv,
+                                                sm.n_recv, cull_ok, true, sm.dlim, si, ts, box, dmin, smask, culled);
+        const unsigned int bal = __ballot_sync(0xffffffffu, keep);
+        int base = 0;
+        if (lane == 0 && bal) base = atomicAdd(&sm.n_tri, __popc(bal));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (keep) {
+            const int slot = base + __popc(bal & ((1u << lane) - 1u));
+            if (slot < HeavyKept<TS>::n) {
+                sm.u.s.tri[slot] = ts;
+                sm.u.s.smask[slot] = make_uint2((uint32_t)smask, (uint32_t)(smask >> 32));
+            }
+        }
+    }
+    __syncthreads();
+    const int n = sm.n_tri;
+    return n > HeavyKept<TS>::n ? -1 : n;
+}
+
 template <int TS, bool PROF>
 __global__ void __launch_bounds__(HeavyCfg<TS>::threads, HeavyCfg<TS>::min_blocks)
     k_raster_test(const WaveDev* __restrict__ W, const JobDev* __restrict__ jobs, Buffers B)
@@ -2002,10 +2206,12 @@ __global__ void __launch_bounds__(HeavyCfg<TS>::threads, HeavyCfg<TS>::min_block
     extern __shared__ __align__(16) unsigned char tile_smem[];  // sizeof(TileSm<TS>), set at launch
     TileSm<TS>& sm = *reinterpret_cast<TileSm<TS>*>(tile_smem);
     unsigned int p_samples = 0, p_visits = 0, p_writes = 0, p_culled = 0, p_cand = 0, p_dense = 0, p_tiles = 0;
+    unsigned int p_stiles = 0, p_pairs = 0;
     __shared__ unsigned int s_item[2];
     const unsigned int n_ne = min(B.ctr->n_heavy, (unsigned int)W->tot_te);
     const int nj = W->n_jobs;
     const int u24 = W->depth_u24;
+    const int want_bits = W->want_bits;
     const int tid = threadIdx.x;
     if (tid == 0) s_item[0] = atomicAdd(&B.ctr->heavy_next, 1u);
     __syncthreads();
@@ -2028,9 +2234,32 @@ __global__ void __launch_bounds__(HeavyCfg<TS>::threads, HeavyCfg<TS>::min_block
         const int C = J.n_cells;
         uint32_t* cnt_row = B.cs_cnt + J.cs_base + (int64_t)ls * C;
         unsigned long long* bits_row = B.cs_bits + J.cs_base + (int64_t)ls * C;
-        const int want_bits = W->want_bits;
-        if (tile_raster<TS, PROF>(sm, J, B, W, ls, tx, ty, te, r0, nrecv, p_visits, p_writes, p_culled, p_cand,
-                                  p_dense) != 0) {
+        const bool cull_ok = nrecv <= kRecvChunk;
+        tile_limits<TS>(sm, lp, u24, cull_ok);
+        // 32-texel tiles are always rasterised (dense samples over few
+        // texels: each kept triangle drawn once beats every sample testing
+        // it); larger tiles take the sample-driven test when at most kMaxTri
+        // triangles are kept (few large triangles over sparse samples)
+        const int nt = TS == 32 ? -1
+                                : setup_sample_tris<TS, PROF>(sm, J, B, W, lp, ls, tx, ty, te, cull_ok, p_culled);
+        const bool sample_driven = nt >= 0;
+        if (sample_driven) {
+            // sample-driven test (no triangle kept: every sample of the tile is lit)
+            if (PROF && tid == 0) ++p_stiles;
+            if (nt > 0) build_sbm<HeavyKept<TS>::words>(sm.u.s.smask, sm.u.s.sbm, nt, tid >> 5, blockDim.x >> 5);
+            __syncthreads();
+            for (int c0 = 0; nt > 0 && c0 < nrecv; c0 += kRecvChunk) {
+                if (c0 > 0) {
+                    __syncthreads();
+                    stage_receivers<TS>(sm, J, B, ls, tx, ty, r0 + c0, min(kRecvChunk, nrecv - c0));
+                }
+                test_items<TS, HeavyKept<TS>::words, PROF>(sm.recv, sm.n_recv, sm.total_items, J, lp, u24, tx, ty, tid,
+                                                blockDim.x, sm.u.s.tri, nt, sm.u.s.sbm, (nt + 31) >> 5,
+                                                sm.u.s.seen, cnt_row, bits_row, want_bits, p_cand, p_samples,
+                                                p_pairs, p_writes);
+            }
+        } else if (tile_raster<TS, PROF>(sm, J, B, W, ls, tx, ty, te, r0, nrecv, true, p_visits, p_writes, p_culled,
+                                         p_cand, p_dense) != 0) {
             for (int c0 = 0; c0 < nrecv; c0 += kRecvChunk) {
                 if (c0 > 0) stage_receivers<TS>(sm, J, B, ls, tx, ty, r0 + c0, min(kRecvChunk, nrecv - c0));
                 uint32_t cnt = 0;
@@ -2039,7 +2268,7 @@ __global__ void __launch_bounds__(HeavyCfg<TS>::threads, HeavyCfg<TS>::min_block
                     sm, J, tx, ty, p_cand,
                     [&](const RecvSm& R, int k, int ix, int iy, float d) {
                         if (PROF) ++p_samples;
-                        const uint32_t key = sm.r.tile[(iy & (TS - 1)) * TS + (ix & (TS - 1))];
+                        const uint32_t key = sm.u.r.tile[(iy & (TS - 1)) * TS + (ix & (TS - 1))];
                         if (key == kEmpty) return;
                         if (behind_key(d, R.s.bias, key, lp.dnear, lp.qscale, u24)) {
                             ++cnt;
@@ -2062,7 +2291,7 @@ __global__ void __launch_bounds__(HeavyCfg<TS>::threads, HeavyCfg<TS>::min_block
     }
     if (PROF) {
         flush_profile(B, p_samples, p_visits, p_writes, p_culled);
-        flush_profile2(B, p_cand, p_tiles, p_dense, 0u, 0u);
+        flush_profile2(B, p_cand, p_tiles, p_dense, p_stiles, p_pairs);
         flush_heavy(B, p_samples, p_writes, p_tiles);
     }
 }
@@ -2098,8 +2327,9 @@ __global__ void __launch_bounds__(256) k_raster_map(const WaveDev* __restrict__ 
         tile_receivers(B, W, te, r0, nrecv);
         stage_receivers<TS>(sm, J, B, ls, tx, ty, r0, min(nrecv, kRecvChunk));
         // the tile is stored even when nothing was drawn: its samples read it
-        tile_raster<TS, PROF>(sm, J, B, W, ls, tx, ty, te, r0, nrecv, p_visits, p_writes, p_culled, p_cand, p_dense);
-        const uint4* t4 = reinterpret_cast<const uint4*>(sm.r.tile);
+        tile_raster<TS, PROF>(sm, J, B, W, ls, tx, ty, te, r0, nrecv, false, p_visits, p_writes, p_culled, p_cand,
+                              p_dense);
+        const uint4* t4 = reinterpret_cast<const uint4*>(sm.u.r.tile);
         uint4* dst = reinterpret_cast<uint4*>(B.map + ((size_t)item * (TS * TS)));
         for (int q = tid; q < TS * TS / 4; q += bd) dst[q] = t4[q];
         __syncthreads();

@@ -40,7 +40,8 @@ PV3D_WINDOWS_PER_ARRAY = 3
 EXPORTED = ("pv3d_create", "pv3d_destroy", "pv3d_last_error", "pv3d_scene_load", "pv3d_generator_define",
             "pv3d_set_poses", "pv3d_set_sun", "pv3d_evaluate", "pv3d_submit", "pv3d_poll", "pv3d_release",
             "pv3d_last_profile", "pv3d_module_shade_noalloc", "pv3d_evaluate_batch", "pv3d_generator_strings",
-            "pv3d_set_sun_clear_sky", "pv3d_sun_table", "pv3d_sky_view", "pv3d_generator_arrays")
+            "pv3d_set_sun_clear_sky", "pv3d_sun_table", "pv3d_sky_view", "pv3d_generator_arrays",
+            "pv3d_raster_peak")
 
 
 class pv3d_opts(C.Structure):
@@ -158,6 +159,7 @@ def load(build_if_missing: bool = False):
         lib.pv3d_evaluate_batch.argtypes = [P, C.c_int32, P, C.POINTER(pv3d_eval_opts), C.POINTER(pv3d_result)]
         lib.pv3d_module_shade_noalloc.argtypes = [P, C.c_int64, C.POINTER(pv3d_module), P, C.c_int32, C.c_int32,
                                                   P, P]
+        lib.pv3d_raster_peak.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double)]
         for name in EXPORTED:
             if name not in ("pv3d_destroy", "pv3d_last_error"):
                 getattr(lib, name).restype = C.c_int
@@ -453,7 +455,19 @@ def pv3d_module_shade_noalloc(tri_xyz, module: dict, sun_xyz, samples_per_side: 
     tensor of cells_u * cells_v int32/uint32 (overwritten); ``module``: dict with
     origin, u, v, pitch, cells_u, cells_v; ``sun_xyz``: 3 floats.  Returns the
     status code (0 = queued on ``stream``)."""
+    import torch
     lib = load()
+    n_cells = int(module["cells_u"]) * int(module["cells_v"])
+    if tri_xyz is not None and tri_xyz.numel():
+        if not (isinstance(tri_xyz, torch.Tensor) and tri_xyz.is_cuda and tri_xyz.dtype == torch.float32
+                and tri_xyz.is_contiguous() and tri_xyz.numel() % 9 == 0):
+            raise ValueError("tri_xyz must be a contiguous float32 CUDA tensor of 9 floats per triangle")
+    if not (isinstance(cell_counts, torch.Tensor) and cell_counts.is_cuda
+            and cell_counts.dtype in (torch.int32, getattr(torch, "uint32", torch.int32))
+            and cell_counts.is_contiguous() and cell_counts.numel() >= n_cells):
+        raise ValueError(f"cell_counts must be a contiguous int32/uint32 CUDA tensor of at least {n_cells} elements")
+    if tri_xyz is not None and tri_xyz.numel() and tri_xyz.device != cell_counts.device:
+        raise ValueError("tri_xyz and cell_counts must be on the same device")
     md = pv3d_module()
     md.origin[:] = [float(x) for x in module["origin"]]
     md.u[:] = [float(x) for x in module["u"]]
@@ -466,6 +480,17 @@ def pv3d_module_shade_noalloc(tri_xyz, module: dict, sun_xyz, samples_per_side: 
     tp = tri_xyz.data_ptr() if n_tris else None
     return lib.pv3d_module_shade_noalloc(tp, n_tris, C.byref(md), _p(sun), int(samples_per_side), int(map_res),
                                          cell_counts.data_ptr(), stream)
+
+
+def raster_peak(device: int = 0) -> dict:
+    """pv3d_raster_peak: measured shared-memory atomicMin throughput (the
+    rasteriser's roofline) of ``device``, in G updates/s."""
+    lib = load()
+    a, ms = C.c_double(), C.c_double()
+    rc = lib.pv3d_raster_peak(int(device), C.byref(a), C.byref(ms))
+    if rc != PV3D_OK:
+        raise PV3DError(rc, "pv3d_raster_peak failed")
+    return {"g_atomics_per_s": a.value / 1e9, "best_ms": ms.value}
 
 
 def load_workload(ctx: Context, w) -> int:

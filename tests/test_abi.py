@@ -77,3 +77,23 @@ def test_product_path_does_not_import_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in text and "from oracle" not in text, f
                 assert "pv3d_oracle" not in text, f
+
+
+def test_noalloc_wrapper_rejects_bad_buffers():
+    """The binding checks the buffers of pv3d_module_shade_noalloc before the
+    call: the kernels read 9 float32 per triangle and write cells_u * cells_v
+    32-bit counts, so host, wrong-dtype, non-contiguous or short tensors are
+    refused with ValueError (the checks run before any device access)."""
+    import torch
+    module = dict(origin=(0.0, 0.0, 0.0), u=(1.0, 0.0, 0.0), v=(0.0, 1.0, 0.0), pitch=0.156, cells_u=6,
+                  cells_v=10)
+    tri = torch.zeros(4, 9, dtype=torch.float32)
+    counts = torch.zeros(60, dtype=torch.int32)
+    with pytest.raises(ValueError):
+        pv3d.pv3d_module_shade_noalloc(tri, module, (0.0, 0.0, 1.0), 2, 256, counts)  # host tensors
+    with pytest.raises(ValueError):
+        pv3d.pv3d_module_shade_noalloc(tri.half(), module, (0.0, 0.0, 1.0), 2, 256, counts)
+    with pytest.raises(ValueError):
+        pv3d.pv3d_module_shade_noalloc(tri.t(), module, (0.0, 0.0, 1.0), 2, 256, counts)
+    with pytest.raises(ValueError):
+        pv3d.pv3d_module_shade_noalloc(tri, module, (0.0, 0.0, 1.0), 2, 256, counts[:10])

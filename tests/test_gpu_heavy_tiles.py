@@ -1,8 +1,9 @@
 """GPU parity on the tile kernels' less common paths: tiles handed from one
-warp per tile to one block per tile (a shared-memory depth tile, then the
-test of its samples) because they keep more than 64 triangles, have more
-than 512 binned triangles, or more than 16 or 64 receiver modules (receivers
-then staged in chunks, without plane culling).
+warp per tile to one block per tile (a block-wide sample-driven test, or a
+shared-memory depth tile and the test of its samples, whichever is estimated
+cheaper) because they keep more than 64 triangles, have more than 512 binned
+triangles, or more than 16 or 64 receiver modules (receivers then staged in
+chunks, without plane culling).
 Each case must agree with the FP64 oracle, be bit-identical to the map path
 (HBM shadow map + gather), and the work counters must show that the intended
 path ran."""
@@ -45,9 +46,8 @@ def test_heavy_tile_paths(case, tile, map_res, tiny, cells):
     p = {k: v for k, v in p.items() if not k.endswith("_ms")}
     warp_tiles = p["nonempty_tiles"] - p["heavy_tiles"]
     raster_tiles = p["nonempty_tiles"] - p["sample_tiles"]
-    assert raster_tiles == p["heavy_tiles"], p  # every tile a warp hands on is rasterised
     if case == "block_kept":
-        assert why[2] > 0 and raster_tiles > 0 and p["texel_visits"] > 0, p
+        assert why[2] > 0 and p["heavy_tiles"] > 0, p
     elif case in ("block_raster", "block_raster_128"):
         assert why[1] > 0 and raster_tiles > 0 and p["texel_visits"] > 0, p
     elif case == "many_receivers":

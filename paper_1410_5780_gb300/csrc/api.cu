@@ -111,7 +111,7 @@ struct pv3d_ctx {
     uint32_t next_id = 1;
     // workspace pools
     DevBuf lp, win, ms, ms_p, ms_pu, ms_beam, ms_iu, ss_i, sq_p, sq_pu, kahan_str, js_p, js_pu, js_bin, heat, sa_p, sa_pu,
-        kahan_arr, cs_cnt, cs_bits, t_far, t_cnt, t_off, t_cur, t_slot, t_rcnt, t_roff, t_rcur, nonempty, heavy, bins, pairs, recv, map,
+        kahan_arr, cs_cnt, cs_bits, t_far, t_cnt, t_off, t_cur, t_slot, t_rcnt, t_plane, t_roff, t_rcur, nonempty, heavy, bins, pairs, recv, map,
         big, block_sums, ctr, waves, jobs, kahan_mod, kahan_cell, staging;
     int64_t bin_cap = 0, map_cap_tiles = 0, big_cap = 0, recv_cap = 0;
     uint64_t bufgen = 0;  // bumped whenever a pool is reallocated (captured graphs hold its pointers)
@@ -493,6 +493,40 @@ extern "C" int pv3d_generator_define(pv3d_ctx* c, uint32_t scene_id, const pv3d_
             if (dn < 1.0 - 1e-9 || std::fabs(off) > 1e-4) cop = false;
         }
         g.coplanar = cop;
+    }
+    // plane groups: the modules of one tracker that share one plane in the
+    // tracker's frame (a pose moves them together), and fixed modules that
+    // share one plane in the world, lie in one plane under every pose and
+    // cannot shade one another (a ray leaving a plane does not meet it again)
+    {
+        struct PlaneKey {
+            int32_t tracker;
+            double n[3], off;
+        };
+        std::vector<PlaneKey> groups;
+        std::map<std::pair<int32_t, long long>, std::vector<int32_t>> index;  // (tracker, offset bucket) -> groups
+        for (int32_t m = 0; m < n_mods; ++m) {
+            const pv3d_module& P = mods[m];
+            double n[3] = {(double)P.u[1] * P.v[2] - (double)P.u[2] * P.v[1],
+                           (double)P.u[2] * P.v[0] - (double)P.u[0] * P.v[2],
+                           (double)P.u[0] * P.v[1] - (double)P.u[1] * P.v[0]};
+            const double l = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+            for (int q = 0; q < 3; ++q) n[q] /= l;
+            const double off = n[0] * P.origin[0] + n[1] * P.origin[1] + n[2] * P.origin[2];
+            const std::pair<int32_t, long long> key(P.tracker, (long long)std::floor(off * 1e3));
+            int32_t id = -1;
+            for (int32_t cand : index[key]) {
+                const PlaneKey& G = groups[(size_t)cand];
+                const double dn = n[0] * G.n[0] + n[1] * G.n[1] + n[2] * G.n[2];
+                if (dn >= 1.0 - 1e-12 && std::fabs(off - G.off) <= 1e-6) { id = cand; break; }
+            }
+            if (id < 0) {
+                id = (int32_t)groups.size();
+                groups.push_back(PlaneKey{P.tracker, {n[0], n[1], n[2]}, off});
+                index[key].push_back(id);
+            }
+            g.mods_h[m].plane = id;
+        }
     }
     // positions relative to the reference point
     for (auto& D : g.mods_h)
@@ -1045,7 +1079,8 @@ static int ensure_workspace(pv3d_ctx* c, int64_t js, int64_t te, int64_t ms, int
         (rc = ensure(c, c->cs_cnt, cs * 4)) || (rc = ensure(c, c->t_far, te * 4)) ||
         (rc = ensure(c, c->t_cnt, te * 4)) || (rc = ensure(c, c->t_off, te * 4)) ||
         (rc = ensure(c, c->t_cur, te * 4)) || (rc = ensure(c, c->t_slot, te * 4)) ||
-        (rc = ensure(c, c->t_rcnt, te * 4)) || (rc = ensure(c, c->t_roff, te * 4)) ||
+        (rc = ensure(c, c->t_rcnt, te * 4)) || (rc = ensure(c, c->t_plane, te * 4)) ||
+        (rc = ensure(c, c->t_roff, te * 4)) ||
         (rc = ensure(c, c->t_rcur, te * 4)) || (rc = ensure(c, c->nonempty, te * 4)) || (rc = ensure(c, c->heavy, te * 4)) ||
         (rc = ensure(c, c->block_sums, scan_tiles * 24)) || (rc = ensure(c, c->ctr, sizeof(Counters))))
         return rc;
@@ -1093,6 +1128,7 @@ static Buffers buffers_of(pv3d_ctx* c)
     B.nonempty = (uint32_t*)c->nonempty.p;
     B.heavy = (uint32_t*)c->heavy.p;
     B.t_rcnt = (uint32_t*)c->t_rcnt.p;
+    B.t_plane = (uint32_t*)c->t_plane.p;
     B.t_roff = (uint32_t*)c->t_roff.p;
     B.t_rcur = (uint32_t*)c->t_rcur.p;
     B.recv = (uint32_t*)c->recv.p;
@@ -1992,7 +2028,7 @@ extern "C" void pv3d_destroy(pv3d_ctx* c)
     release_buf(c->jobs_slot);
     DevBuf* bufs[] = {&c->lp, &c->win, &c->ms, &c->ms_p, &c->ms_pu, &c->ms_beam, &c->ms_iu, &c->ss_i, &c->sq_p,
                       &c->sq_pu, &c->kahan_str, &c->js_p, &c->js_pu, &c->js_bin, &c->heat, &c->sa_p, &c->sa_pu, &c->kahan_arr, &c->cs_cnt, &c->cs_bits, &c->t_far,
-                      &c->t_cnt, &c->t_off, &c->t_cur, &c->t_slot, &c->t_rcnt, &c->t_roff, &c->t_rcur, &c->nonempty, &c->heavy,
+                      &c->t_cnt, &c->t_off, &c->t_cur, &c->t_slot, &c->t_rcnt, &c->t_plane, &c->t_roff, &c->t_rcur, &c->nonempty, &c->heavy,
                       &c->bins, &c->pairs, &c->recv, &c->map, &c->big,
                       &c->block_sums, &c->ctr, &c->waves, &c->jobs, &c->kahan_mod, &c->kahan_cell, &c->staging};
     for (DevBuf* b : bufs) release_buf(*b);

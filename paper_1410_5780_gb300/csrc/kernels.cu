@@ -251,6 +251,7 @@ __global__ void k_clear(const WaveDev* __restrict__ W, Buffers B)
         B.t_far[i] = 0u;
         B.t_cnt[i] = 0u;
         B.t_rcnt[i] = 0u;
+        B.t_plane[i] = kPlaneNone;
     }
     if (W->fused) {
         const int64_t nc = W->tot_cs;
@@ -466,6 +467,10 @@ __global__ void k_modsetup(const WaveDev* __restrict__ W, const JobDev* __restri
                 const int64_t te = te0 + (int64_t)ty * J.tiles_x + tx;
                 atomicMax(&B.t_far[te], far_key);
                 atomicAdd(&B.t_rcnt[te], 1u);
+                // the plane group shared by every receiver of the tile
+                const uint32_t pl = (uint32_t)M.plane;
+                const uint32_t old = atomicCAS(&B.t_plane[te], kPlaneNone, pl);
+                if (old != kPlaneNone && old != pl && old != kPlaneMixed) atomicExch(&B.t_plane[te], kPlaneMixed);
             }
     }
 }
@@ -559,6 +564,18 @@ __device__ __forceinline__ void tri_texel(const JobDev& J, const Buffers& B, con
         T.y[2] = s.ty0 + a2 * s.tay + b2 * s.tby;
         T.d[2] = s.d0 + a2 * s.da + b2 * s.db;
     }
+}
+
+// Plane group of triangle t if it is a module triangle (the job's own
+// modules, or the generator's occluder modules of a window group), else
+// kPlaneNone.  Modules of one plane group cannot shade one another, so a
+// module triangle is not binned into a tile whose receivers all share its
+// plane group (t_plane).
+__device__ __forceinline__ uint32_t module_tri_plane(const JobDev& J, int t)
+{
+    if (t < J.n_tris) return kPlaneNone;
+    const int m = (t - J.n_tris) >> 1;
+    return (uint32_t)(J.occ_mods ? J.occ_mods[m].plane : J.mods[m].plane);
 }
 
 // Edge functions of a counter-clockwise triangle: E_k(p) = A_k px + B_k py + C_k,
@@ -738,6 +755,7 @@ __global__ void __launch_bounds__(256, 4) k_bin(const WaveDev* __restrict__ W, c
             if (act) {
                 TriT T;
                 tri_texel(J, B, lp, ls, t, T);
+                const uint32_t tplane = module_tri_plane(J, t);
                 Edges e;
                 const float xmin = fminf(T.x[0], fminf(T.x[1], T.x[2])), xmax = fmaxf(T.x[0], fmaxf(T.x[1], T.x[2]));
                 const float ymin = fminf(T.y[0], fminf(T.y[1], T.y[2])), ymax = fmaxf(T.y[0], fmaxf(T.y[1], T.y[2]));
@@ -764,6 +782,8 @@ __global__ void __launch_bounds__(256, 4) k_bin(const WaveDev* __restrict__ W, c
                             const uint32_t x = (uint32_t)(te0 + (int64_t)ty * J.tiles_x + tx);
                             // unoccupied tile (far 0) or triangle wholly behind its far plane
                             if (!(dkey < B.t_far[x])) continue;
+                            // a module triangle in the plane of every receiver of the tile
+                            if (tplane != kPlaneNone && B.t_plane[x] == tplane) continue;
                             atomicAdd(&B.t_cnt[x], 1u);
                             te[q] = x;
                             valid |= 1u << q;
@@ -809,6 +829,7 @@ __global__ void __launch_bounds__(256) k_bin_big(const WaveDev* __restrict__ W,
         if (ix0 > ix1 || iy0 > iy1) continue;
         float dmin = fminf(T.d[0], fminf(T.d[1], T.d[2]));
         uint32_t dkey = depth_store_key(dmin, lp, u24);
+        const uint32_t tplane = module_tri_plane(J, t);
         int tx0 = ix0 >> sh, tx1 = ix1 >> sh, ty0 = iy0 >> sh, ty1 = iy1 >> sh;
         int wx = tx1 - tx0 + 1;
         int ntiles = wx * (ty1 - ty0 + 1);
@@ -822,7 +843,7 @@ __global__ void __launch_bounds__(256) k_bin_big(const WaveDev* __restrict__ W,
                 const int tx = tx0 + q % wx, ty = ty0 + q / wx;
                 const uint32_t x = (uint32_t)(te0 + (int64_t)ty * J.tiles_x + tx);
                 if (rect_overlap(ed, tx * TS + 0.5f, tx * TS + TS - 0.5f, ty * TS + 0.5f, ty * TS + TS - 0.5f) &&
-                    dkey < B.t_far[x]) {
+                    dkey < B.t_far[x] && !(tplane != kPlaneNone && B.t_plane[x] == tplane)) {
                     atomicAdd(&B.t_cnt[x], 1u);
                     te[0] = x;
                     valid = 1u;

@@ -19,14 +19,18 @@ constexpr int kMaxSub = 64;
 constexpr int kBigTiles = 4;       // triangles over more tiles are binned by whole warps
 constexpr int kWinPerItem = 256;   // modules reduced per window item
 
-// Generator module in device memory (64 bytes).
+// Generator module in device memory (68 bytes).
 struct ModuleDev {
     float o[3], u[3], v[3];
     float pitch;
     int32_t cu, cv, layout, tracker;
     int32_t cell_base;  // first cell of the module in the generator's cell numbering
     int32_t n_sub;      // substrings of its layout
+    int32_t plane;      // plane group: modules with one id lie in one plane under every pose
 };
+
+constexpr uint32_t kPlaneNone = 0xFFFFFFFFu;   // t_plane: no receiver yet
+constexpr uint32_t kPlaneMixed = 0xFFFFFFFEu;  // t_plane: receivers of several plane groups
 
 // Light frame of one (job, step): orthographic view from the sun (Section 2,
 // step 3).  Light-plane coordinates are taken relative to the job's reference
@@ -224,6 +228,7 @@ struct Buffers {
     uint32_t* t_cur;         // [tot_te]
     uint32_t* t_slot;        // [tot_te]  index among the wave's non-empty tiles (= map slot)
     uint32_t* t_rcnt;        // [tot_te]  receiver modules touching the tile
+    uint32_t* t_plane;       // [tot_te]  plane group of every receiver of the tile, or kPlaneMixed
     uint32_t* t_roff;        // [tot_te]
     uint32_t* t_rcur;        // [tot_te]
     uint32_t* nonempty;      // [tot_te]

@@ -327,3 +327,33 @@ def test_invalid_inputs_rejected(ctx):
         ctx.evaluate(987654, n=2)
     assert e.value.code == pv3d.PV3D_E_NOTFOUND
     ctx.release(sid)
+
+
+def test_stepped_tracker_table_shades_itself(ctx):
+    """Modules of one tracker table that do not share a plane (a row raised
+    0.3 m along the table's normal, overlapping the row below like shingles)
+    shade one another; modules that share one plane cannot, and the binning
+    leaves their triangles out of the tiles whose receivers all lie in that
+    plane.  Both against the FP64 oracle at non-normal incidence (tilt limit
+    30 deg, low suns)."""
+    cu, cv = 6, 10
+    p = S.CELL_PITCH
+    w0, h0 = cu * p, cv * p
+    origins = [(-w0 - 0.01, -h0, 0.0), (0.01, -h0, 0.0),                 # lower row, coplanar pair
+               (-w0 - 0.01, -0.25, 0.3), (0.01, -0.25, 0.3)]             # raised row, overlapping by 0.25 m
+    lay = S.standard_layout(cu, cv, 3)
+    gen = S._gen_from_lists(origins, [(1.0, 0.0, 0.0)] * 4, [(0.0, 1.0, 0.0)] * 4, cu, cv, [0] * 4, [0] * 4,
+                            list(range(4)), [lay], np.array([[0.0, 0.0, 3.0]]))
+    mb = S.MeshBuilder()
+    mb.box((6.0, 6.0, 0.0), (6.5, 6.5, 0.5))
+    scene = mb.build()
+    days, hours = np.array([80, 80, 80, 172, 172, 355, 355, 355]), np.array([8.0, 9.5, 15.0, 7.0, 18.0, 9.0, 12.0, 14.5])
+    xyz = S.sun_vectors(40.0, days, hours)
+    dni = S.clear_sky_dni(xyz[:, 2]).astype(np.float32)
+    sun = S.Sun(xyz=xyz, dni=dni, dhi=(0.1 * dni).astype(np.float32), dt_h=np.ones(len(xyz), np.float32))
+    poses = S.ideal_poses(sun, 1, 30.0)
+    w = S.Workload("stepped", scene, gen, sun, poses, 4, 1024)
+    g, o, st = full_check(ctx, w, strict_loss=False)
+    cells = cu * cv
+    assert o["counts"][:, :2 * cells].sum() > 100       # the raised row shades the lower one
+    assert g["cell_counts"][:, :2 * cells].sum() > 100

@@ -2049,7 +2049,9 @@ __global__ void __launch_bounds__(kTileWarps * 32, 6) k_tile_warp(const WaveDev*
     unsigned int p_hr = 0, p_hb = 0, p_ht = 0;
     const int lane = threadIdx.x & 31;
     WarpSm<TS, PROF>& sm = sm_all[threadIdx.x >> 5];
-    const unsigned int n_ne = B.ctr->n_nonempty;
+    // the bins are incomplete when the pool overflowed: the wave is rerun
+    // with a larger pool, so nothing here may read them
+    const unsigned int n_ne = (B.ctr->overflow & 1u) ? 0u : B.ctr->n_nonempty;
     const int nj = W->n_jobs;
     const int want_bits = W->want_bits;
     const int u24 = W->depth_u24;
@@ -2229,7 +2231,8 @@ __global__ void __launch_bounds__(HeavyCfg<TS>::threads, HeavyCfg<TS>::min_block
     unsigned int p_samples = 0, p_visits = 0, p_writes = 0, p_culled = 0, p_cand = 0, p_dense = 0, p_tiles = 0;
     unsigned int p_stiles = 0, p_pairs = 0;
     __shared__ unsigned int s_item[2];
-    const unsigned int n_ne = min(B.ctr->n_heavy, (unsigned int)W->tot_te);
+    // incomplete bins (pool overflow, the wave is rerun): nothing to read
+    const unsigned int n_ne = (B.ctr->overflow & 1u) ? 0u : min(B.ctr->n_heavy, (unsigned int)W->tot_te);
     const int nj = W->n_jobs;
     const int u24 = W->depth_u24;
     const int want_bits = W->want_bits;
@@ -2329,7 +2332,8 @@ __global__ void __launch_bounds__(256) k_raster_map(const WaveDev* __restrict__ 
     TileSm<TS>& sm = *reinterpret_cast<TileSm<TS>*>(tile_smem);
     unsigned int p_visits = 0, p_writes = 0, p_culled = 0, p_cand = 0, p_dense = 0;
     __shared__ unsigned int s_item;
-    const unsigned int n_ne = B.ctr->n_nonempty;
+    // incomplete bins (pool overflow, the wave is rerun): nothing to read
+    const unsigned int n_ne = (B.ctr->overflow & 1u) ? 0u : B.ctr->n_nonempty;
     const int64_t map_cap = W->map_cap_tiles;
     const int nj = W->n_jobs;
     const int tid = threadIdx.x, bd = blockDim.x;

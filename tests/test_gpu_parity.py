@@ -357,3 +357,27 @@ def test_stepped_tracker_table_shades_itself(ctx):
     cells = cu * cv
     assert o["counts"][:, :2 * cells].sum() > 100       # the raised row shades the lower one
     assert g["cell_counts"][:, :2 * cells].sum() > 100
+
+
+@pytest.mark.parametrize("make", ["random", "mini_tracker"])
+def test_bin_pool_overflow_regrows(make):
+    """A context whose (triangle, tile) pool holds 16 entries overflows on its
+    first wave; the kernels stop appending at the pool's end and flag it, and
+    the host grows the pool from the demand they counted and reruns.  The
+    results must equal those of a context with the default pool bit for bit,
+    and meet the oracle criteria."""
+    if make == "random":
+        w = S.make_random_small(141, n_mods=6, n_steps=10, n=3, map_res=512, tracked=True)
+    else:
+        w = S.make_tracker(seed=9, n=4, map_res=1024, grid=(4, 3), terrain_n=64, spacing=1.5, n_pylons=2,
+                           step_h=1.0, days=np.array([30, 172, 300]))
+    with pv3d.Context(device=0, bin_capacity=16) as small, pv3d.Context(device=0) as big:
+        a = run_gpu(small, pv3d.load_workload(small, w), w)
+        b = run_gpu(big, pv3d.load_workload(big, w), w)
+    assert b["binned_tris"] > 16 * b["waves"]  # every wave needs more than the small pool
+    for k in ("sample_bits", "cell_counts", "power", "power_unshaded", "energy", "energy_unshaded"):
+        np.testing.assert_array_equal(a[k], b[k], err_msg=k)
+    o = oracle.evaluate_workload(w)
+    st = compare(w, a, o, np.arange(w.sun.n_steps))
+    assert st["agree"] >= FLAG_AGREEMENT, st
+    energy_checks(w, a, o, np.arange(w.sun.n_steps))

@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the batched, served and extension sections")
     ap.add_argument("--no-facade", action="store_true", help="skip the secondary facade measurement")
     ap.add_argument("--batch-scenes", type=int, default=256)
-    ap.add_argument("--requests", type=int, default=200)
+    ap.add_argument("--requests", type=int, default=10000)
     ap.add_argument("--step-range", type=int, nargs=2, default=None, metavar=("BEGIN", "END"),
                     help="evaluate only sun steps [BEGIN, END) of the workload (profiling captures of one wave)")
     return ap.parse_args()
@@ -254,15 +254,17 @@ def input_bytes(w) -> int:
     return int(b)
 
 
-def _batched_vs_plain(dev: int, ws) -> dict:
+def _batched_vs_plain(dev: int, ws, depth_format: int = 0) -> dict:
     import torch
     from paper_1410_5780_gb300 import pv3d
     tests = sum(w.n_tests() for w in ws)
-    with pv3d.Context(device=dev, wave_scratch_mb=128) as ctx:
+    with pv3d.Context(device=dev, depth_format=depth_format) as ctx:
         gids = [pv3d.load_workload(ctx, w) for w in ws]
         ns = [w.n for w in ws]
         rs = [w.map_res for w in ws]
         ctx.evaluate_batch(gids[:8], n=ns[:8], map_res=rs[:8])  # warm-up
+        for w, g in zip(ws[:4], gids[:4]):
+            ctx.evaluate(g, n=w.n, map_res=w.map_res)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         plain = [ctx.evaluate(g, n=w.n, map_res=w.map_res) for w, g in zip(ws, gids)]
@@ -273,24 +275,35 @@ def _batched_vs_plain(dev: int, ws) -> dict:
         torch.cuda.synchronize()
         t_batch = time.perf_counter() - t0
         same = all(bool(torch.equal(a["energy"], b["energy"])) for a, b in zip(plain, batch))
+        loss = [100.0 * (1.0 - float(b["energy"].double().sum()) / max(float(b["energy_unshaded"].double().sum()), 1e-30))
+                for b in batch]
     return {"tests": int(tests), "plain_tests_per_s": tests / t_plain, "batched_tests_per_s": tests / t_batch,
-            "speedup": t_plain / t_batch, "batched_equals_plain": same}
+            "speedup": t_plain / t_batch, "batched_equals_plain": same, "plain_s": t_plain, "batched_s": t_batch,
+            "_loss": loss}
 
 
 def batched_section(dev: int, n_scenes: int) -> dict:
     """Batched scenes of uneven size (log-uniform triangles and modules,
     latitudes 0-60 deg, 100-4400 sun steps): the plain per-scene loop against
-    one batched call (all scenes' sun steps packed into shared waves); also a
-    mix of small scenes, where one scene alone does not fill the GPU."""
-    from paper_1410_5780_gb300 import scenes as S
-    mix = _batched_vs_plain(dev, S.make_batch(seed=4, n_scenes=n_scenes))
+    one batched call (all scenes' sun steps packed into shared waves), with
+    FP32 depth and with 24-bit fixed-point depth; also a mix of small scenes,
+    where one scene alone does not fill the GPU."""
+    from paper_1410_5780_gb300 import pv3d, scenes as S
+    ws = S.make_batch(seed=4, n_scenes=n_scenes)
+    mix = _batched_vs_plain(dev, ws)
+    u24 = _batched_vs_plain(dev, ws, depth_format=pv3d.PV3D_DEPTH_U24)
+    dl = np.abs(np.array(u24.pop("_loss")) - np.array(mix.pop("_loss")))
     mix["workload"] = (f"{n_scenes} scenes: triangles log-uniform 1e3-2e5, modules log-uniform 10-2000, "
                        "latitude U(0,60), 100-4400 hourly sun steps, 4x4 samples, map 512-4096")
+    mix["depth_u24"] = {"plain_tests_per_s": u24["plain_tests_per_s"], "batched_tests_per_s": u24["batched_tests_per_s"],
+                        "speedup": u24["speedup"], "batched_equals_plain": u24["batched_equals_plain"],
+                        "loss_pp_vs_f32": {"max_abs": float(dl.max()), "mean_abs": float(dl.mean())}}
     small = _batched_vs_plain(dev, S.make_batch(seed=6, n_scenes=n_scenes, tris=(1e3, 2e4), mods=(10, 100),
                                                 steps=(100, 400)))
+    small.pop("_loss")
     small["workload"] = f"{n_scenes} small scenes: 1e3-2e4 triangles, 10-100 modules, 100-400 sun steps"
     mix["small_scenes"] = small
-    mix["clock"] = "host wall clock"
+    mix["clock"] = "host wall clock around each form, device synchronised"
     return mix
 
 
@@ -386,15 +399,18 @@ def tracker_windows_section(ctx, gid, w, stream, n_steps: int = 1024) -> dict:
 
 
 def serving_section(dev: int, n_requests: int) -> dict:
-    """Served evaluation on a bounded sample: requests over a pool of resident scenes
-    (1e3-5.2e5 triangles), each a random range of 100-4400 sun steps.  The
-    served capacity is measured first (all requests submitted at once), then
-    Poisson arrivals at 80 % of it; p50/p99 of submit-to-result latency."""
+    """Served evaluation of a stream of requests over a pool of resident
+    scenes (1e3-5.2e5 triangles, 10-2000 modules), each request a random
+    range of 100-4400 sun steps of its scene.  Three runs over the same
+    request list: the plain per-scene loop (one synchronous evaluation after
+    another), the served capacity (every request submitted at once:
+    continuous batching into shared waves), and Poisson arrivals at 80 % of
+    that capacity, with p50/p99 submit-to-result latency."""
     import torch
     from paper_1410_5780_gb300 import pv3d, scenes as S
     rng = np.random.default_rng(11)
     pool = S.make_batch(seed=5, n_scenes=24, tris=(1e3, 5.2e5))
-    with pv3d.Context(device=dev, hbm_budget_bytes=120 << 30, wave_scratch_mb=128) as ctx:
+    with pv3d.Context(device=dev, hbm_budget_bytes=120 << 30) as ctx:
         gids = [pv3d.load_workload(ctx, w) for w in pool]
         reqs = []
         for _ in range(n_requests):
@@ -402,44 +418,69 @@ def serving_section(dev: int, n_requests: int) -> dict:
             w = pool[q]
             k = int(rng.integers(min(100, w.sun.n_steps), w.sun.n_steps + 1))
             b = int(rng.integers(0, w.sun.n_steps - k + 1))
-            reqs.append((q, b, b + k, k * w.samples_per_step))
+            lit = int((w.sun.xyz[b:b + k, 2] > 0).sum())
+            reqs.append((q, b, b + k, lit * w.samples_per_step))
+        total_tests = sum(r[3] for r in reqs)
 
         def submit(q, b, e):
             w = pool[q]
             return ctx.submit(gids[q], n=w.n, map_res=w.map_res, step_begin=b, step_end=e)
 
-        # capacity: every request at once
+        for q in range(min(4, len(pool))):  # warm-up
+            assert ctx.poll(submit(q, 0, 100)[0], timeout_ms=-1) == pv3d.PV3D_OK
+            ctx.evaluate(gids[q], n=pool[q].n, map_res=pool[q].map_res, step_end=100)
+        # plain per-scene loop over the same requests
         torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for q, b, e, _ in reqs:
+            w = pool[q]
+            ctx.evaluate(gids[q], n=w.n, map_res=w.map_res, step_begin=b, step_end=e)
+        torch.cuda.synchronize()
+        t_plain = time.perf_counter() - t0
+        # capacity: every request at once
         t0 = time.perf_counter()
         ids = [submit(q, b, e)[0] for q, b, e, _ in reqs]
         for rid in ids:
             assert ctx.poll(rid, timeout_ms=-1) == pv3d.PV3D_OK
         t_cap = time.perf_counter() - t0
-        total_tests = sum(r[3] for r in reqs)
         capacity_rps = n_requests / t_cap
+        # Poisson arrivals at 80 % of the capacity
         rate = 0.8 * capacity_rps
         gaps = rng.exponential(1.0 / rate, n_requests)
         t0 = time.perf_counter()
         t_arr = t0 + np.cumsum(gaps)
-        live, lat = {}, []
+        live, lat, lat_tests = {}, [], []
         for i, (q, b, e, nt) in enumerate(reqs):
             while time.perf_counter() < t_arr[i]:
                 for rid in list(live):
                     if ctx.poll(rid, timeout_ms=0) == pv3d.PV3D_OK:
-                        lat.append(live.pop(rid)["latency_ms"])
+                        arr, n_t = live.pop(rid)
+                        lat.append(arr["latency_ms"])
+                        lat_tests.append(n_t)
                 time.sleep(0.0002)
             rid, arrays = submit(q, b, e)
-            live[rid] = arrays
+            live[rid] = (arrays, nt)
         for rid in list(live):
             assert ctx.poll(rid, timeout_ms=-1) == pv3d.PV3D_OK
-            lat.append(live.pop(rid)["latency_ms"])
+            arr, n_t = live.pop(rid)
+            lat.append(arr["latency_ms"])
+            lat_tests.append(n_t)
         span = time.perf_counter() - t0
-    return {"workload": f"{n_requests} requests over {len(pool)} resident scenes (1e3-5.2e5 triangles), 100-4400 "
-                        "sun steps each (a bounded sample of a 10k-request stream); Poisson arrivals at 80% of the measured "
-                        "served capacity",
-            "capacity_tests_per_s": total_tests / t_cap, "capacity_requests_per_s": capacity_rps,
-            "arrival_rate_per_s": rate, "p50_ms": float(np.percentile(lat, 50)),
-            "p99_ms": float(np.percentile(lat, 99)), "tests_per_s": total_tests / span, "requests": n_requests}
+    lat = np.array(lat)
+    lat_tests = np.array(lat_tests, float)
+    small = lat_tests <= np.percentile(lat_tests, 50)
+    return {"workload": f"{n_requests} requests over {len(pool)} resident scenes (1e3-5.2e5 triangles, 10-2000 "
+                        "modules), each a random range of 100-4400 hourly sun steps; the same list for all three runs",
+            "tests": int(total_tests),
+            "plain_tests_per_s": total_tests / t_plain, "plain_s": t_plain,
+            "served_capacity_tests_per_s": total_tests / t_cap, "served_capacity_s": t_cap,
+            "served_vs_plain": t_plain / t_cap,
+            "capacity_requests_per_s": capacity_rps, "arrival_rate_per_s": rate,
+            "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "p50_ms_smaller_half": float(np.percentile(lat[small], 50)),
+            "p99_ms_smaller_half": float(np.percentile(lat[small], 99)),
+            "poisson_tests_per_s": total_tests / span, "requests": n_requests,
+            "clock": "host wall clock; latency from pv3d_submit to the result (the library's own stamp)"}
 
 
 def measured_peaks() -> dict:

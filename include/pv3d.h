@@ -83,7 +83,7 @@ typedef struct pv3d_opts {
     int32_t max_inflight;     /* served requests resident on the device at once, 1..256 [64] */
     int64_t hbm_budget_bytes; /* device memory the context may use [90% of free memory] */
     int32_t wave_scratch_mb;  /* served waves: per-wave scratch target, MiB; requests take fewer steps per
-                                 wave to stay under it [256] */
+                                 wave to stay under it [2048] */
     int32_t reserved0;
     int64_t bin_capacity;     /* initial (triangle, tile) pool entries; grown on overflow [4 Mi] */
     int32_t reserved[4];

@@ -243,7 +243,7 @@ extern "C" int pv3d_create(pv3d_ctx** out, const pv3d_opts* opts)
     if (o.chunk_steps == 0) o.chunk_steps = 128;
     if (o.max_inflight == 0) o.max_inflight = 64;
     if (o.max_inflight < 1 || o.max_inflight > 256) return PV3D_E_INVALID;  // jobs per wave
-    if (o.wave_scratch_mb == 0) o.wave_scratch_mb = 256;
+    if (o.wave_scratch_mb == 0) o.wave_scratch_mb = 2048;
     if (o.wave_scratch_mb < 1) return PV3D_E_INVALID;
     if (o.bin_capacity < 0 || o.bin_capacity > (1ll << 32)) return PV3D_E_INVALID;
     if (o.bin_capacity > 0) c->bin_cap = o.bin_capacity;

@@ -325,18 +325,35 @@ int pv3d_sun_table(pv3d_ctx* ctx, uint32_t gen_id, double* sun_xyz, float* dni, 
  * samples tested), and weighted by its solid angle times the cosine to the
  * module's front normal.  A cell's fraction is sum_p W_p s_p / sum_p W_p (s_p
  * = its shaded samples toward patch p over n^2); 0 without obstructions.  The
- * fractions are kept with the generator (fixed modules only) and used by
- * evaluations with diffuse_shading = 1: G_c = DNI max(0, cos i)(1 - f_c) +
- * DHI (1 + cos beta)/2 (1 - f_diffuse,c).  cell_fraction (host, C entries, may
- * be NULL) receives them.  Errors: PV3D_E_INVALID (a tracked module, options
- * out of range), PV3D_E_NOTFOUND, PV3D_E_NOMEM, PV3D_E_DEVICE.
+ * fractions are kept with the generator and used by evaluations with
+ * diffuse_shading = 1: G_c = DNI max(0, cos i)(1 - f_c) + DHI (1 + cos beta)/2
+ * (1 - f_diffuse,c), cos beta the module's tilt at the step.
+ *
+ * Tracked generators (Section 3.4): a tracker's view of the sky changes with
+ * its pose, so the fractions are taken per pose bin.  A step's pose bin is
+ * that of the first tracker's pose (the plant tracks in unison): compass
+ * azimuth in pose_az_bins equal sectors of [0, 360) deg, tilt in
+ * pose_tilt_bins equal bands of [0, 90] deg, bin = tilt band * pose_az_bins +
+ * azimuth sector.  For every bin that a lit step falls in, every tracker is
+ * set to the bin's centre pose (the middle of both ranges) and the fractions
+ * are taken as above with the modules' normals at that pose; a step then uses
+ * the row of its bin.  The sun table and poses must be set first; a new sun
+ * table or pose table drops the fractions (evaluate with diffuse_shading again
+ * needs pv3d_sky_view).
+ *
+ * cell_fraction (host, may be NULL) receives bins x C floats, row-major by
+ * bin (bins = 1 for a generator of fixed modules; rows of bins that no lit
+ * step uses are 0).  Errors: PV3D_E_INVALID (options out of range, tracked
+ * generator without poses), PV3D_E_NOTFOUND, PV3D_E_NOMEM, PV3D_E_DEVICE.
  */
 typedef struct pv3d_sky_view_opts {
     int32_t rings;             /* zenith bands over [0, 90] deg, 1..90 [9] */
     int32_t sectors;           /* azimuth sectors, 1..360 [36] */
     int32_t samples_per_side;  /* n, 1..15 [3] */
     int32_t map_res;           /* shadow-map side [context default] */
-    int32_t reserved[4];
+    int32_t pose_az_bins;      /* tracked generators: azimuth sectors of the pose bins, 1..360 [12] */
+    int32_t pose_tilt_bins;    /* tracked generators: tilt bands of the pose bins, 1..90 [6] */
+    int32_t reserved[2];
 } pv3d_sky_view_opts;
 
 int pv3d_sky_view(pv3d_ctx* ctx, uint32_t gen_id, const pv3d_sky_view_opts* opts, float* cell_fraction);

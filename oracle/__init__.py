@@ -431,6 +431,60 @@ def diffuse_shade_fractions(w, rings: int, sectors: int, counts, normals):
     return np.where(tot > 0, (wgt * frac).sum(0) / np.where(tot > 0, tot, 1.0), 0.0)
 
 
+def pose_bins(az_tilt, n_az: int, n_tilt: int):
+    """Pose bins of tracker poses for the diffuse shading of tracked modules
+    (reading: a tracker's view of the sky changes with its pose, Section 3.4;
+    the sky view is taken once per bin): compass azimuth in ``n_az`` equal
+    sectors of [0, 2 pi), tilt in ``n_tilt`` equal bands of [0, pi/2], bin =
+    band * n_az + sector.  ``az_tilt`` [S, 2] (radians).  Returns (bin [S],
+    centre azimuth [n_az * n_tilt], centre tilt [n_az * n_tilt]), the centre
+    being the middle of both ranges."""
+    a = np.asarray(az_tilt, np.float64).reshape(-1, 2)
+    two_pi, half_pi = 2.0 * math.pi, 0.5 * math.pi
+    az = np.mod(a[:, 0], two_pi)
+    ia = np.clip(np.floor(az / two_pi * n_az).astype(np.int64), 0, n_az - 1)
+    it = np.clip(np.floor(np.clip(a[:, 1], 0.0, half_pi) / half_pi * n_tilt).astype(np.int64), 0, n_tilt - 1)
+    b = np.arange(n_az * n_tilt)
+    return it * n_az + ia, (b % n_az + 0.5) * two_pi / n_az, (b // n_az + 0.5) * half_pi / n_tilt
+
+
+def tracked_diffuse_fractions(w, rings: int, sectors: int, n_az: int, n_tilt: int, n: int, map_res: int,
+                              bins=None, want_mask: bool = True):
+    """Diffuse shading fractions of a tracked generator per pose bin: a
+    step's bin is that of the first tracker's pose (pose_bins); for each bin
+    (those of the lit steps, or ``bins``) every tracker takes the bin's
+    centre pose and the exact rays toward the sky patches give each cell's
+    fraction (diffuse_shade_fractions, with the module normals at that pose).
+    Returns ({bin: fractions [C]}, {bin: masked share [C]} (the patches'
+    masked samples weighted like the fraction, or None), the step bins [S])."""
+    gen = w.gen
+    step_bin, az_c, tilt_c = pose_bins(w.poses[:, 0, :], n_az, n_tilt)
+    lit = w.sun.xyz[:, 2] > 0
+    use = sorted(set(int(b) for b in step_bin[lit])) if bins is None else list(bins)
+    xyz, dom = sky_patches(rings, sectors)
+    P = len(xyz)
+    sun = type(w.sun)(xyz=xyz, dni=np.ones(P, np.float32), dhi=np.zeros(P, np.float32), dt_h=np.ones(P, np.float32))
+    n_trk = gen.pivots.shape[0]
+    cells = (gen.cells_u.astype(np.int64) * gen.cells_v)
+    out, masked = {}, {}
+    for b in use:
+        poses = np.zeros((P, n_trk, 2), np.float32)
+        poses[:, :, 0] = az_c[b]
+        poses[:, :, 1] = tilt_c[b]
+        o = evaluate(w.scene, gen, sun, poses, n, map_res, want_mask=want_mask)
+        normals = np.concatenate([np.repeat(module_normal(gen, poses, 0, m)[None, :], cells[m], 0)
+                                  for m in range(gen.n_modules)])
+        wn = type(w)(w.name, w.scene, gen, sun, poses, n, map_res)
+        out[b] = diffuse_shade_fractions(wn, rings, sectors, o["counts"], normals)
+        if want_mask:
+            wgt = dom[:, None] * np.maximum(0.0, xyz @ normals.T)
+            mk = popcount64(o["mbits"]) / float(n * n)
+            masked[b] = (wgt * mk).sum(0) / np.maximum(wgt.sum(0), 1e-300)
+        else:
+            masked[b] = None
+    return out, masked, step_bin
+
+
 def popcount64(a: np.ndarray) -> np.ndarray:
     a = a.astype(np.uint64)
     c = np.zeros(a.shape, np.int32)

@@ -69,7 +69,9 @@ struct GenH {
     int32_t* d_sub_base = nullptr;  // [M]
     int32_t* d_sub_nk = nullptr;    // [n_sub_tot]
     int32_t* d_sub_mod = nullptr;   // [n_sub_tot]
-    float* d_fdiff = nullptr;       // [C] diffuse shading fraction per cell (pv3d_sky_view)
+    float* d_fdiff = nullptr;       // [bins][C] diffuse shading fraction per cell (pv3d_sky_view)
+    int32_t* d_fbin = nullptr;      // [n_steps] pose bin of each step (tracked generators)
+    int32_t fdiff_bins = 0;         // rows of d_fdiff
     // arrays of parallel strings: distinct array ids ascending; their strings
     std::vector<int32_t> arr_ids;
     int32_t max_arr_sub = 0;        // substrings of the largest array
@@ -218,7 +220,7 @@ static void free_gen(GenH& g)
 {
     void* ps[] = {g.d_mods, g.d_cell_mod, g.d_lay_sub, g.d_lay_off, g.d_lay_nk, g.d_lay_nk_off, g.d_pivots,
                   g.d_sun, g.d_dni, g.d_dhi, g.d_dt, g.d_poses, g.d_str_sub, g.d_sub_base, g.d_sub_nk,
-                  g.d_sub_mod, g.d_fdiff, g.d_arr_off, g.d_arr_strs, g.d_oml};
+                  g.d_sub_mod, g.d_fdiff, g.d_fbin, g.d_arr_off, g.d_arr_strs, g.d_oml};
     for (void* p : ps)
         if (p) cudaFree(p);
     for (auto& kv : g.wgroups) {
@@ -649,6 +651,18 @@ extern "C" int pv3d_generator_arrays(pv3d_ctx* c, uint32_t gen_id, int32_t* n_ar
     return PV3D_OK;
 }
 
+// Diffuse fractions of a tracked generator are tied to the poses and steps
+// they were binned with: a new pose or sun table drops them.
+static void drop_tracked_diffuse(GenH& g)
+{
+    if (!g.n_trk) return;
+    if (g.d_fdiff) cudaFree(g.d_fdiff);
+    if (g.d_fbin) cudaFree(g.d_fbin);
+    g.d_fdiff = nullptr;
+    g.d_fbin = nullptr;
+    g.fdiff_bins = 0;
+}
+
 extern "C" int pv3d_set_poses(pv3d_ctx* c, uint32_t gen_id, const float* az_tilt, int64_t n_steps)
 {
     if (!c) return PV3D_E_INVALID;
@@ -661,6 +675,7 @@ extern "C" int pv3d_set_poses(pv3d_ctx* c, uint32_t gen_id, const float* az_tilt
     for (size_t k = 0; k < n; ++k)
         if (!std::isfinite(az_tilt[k])) return fail(c, PV3D_E_INVALID, "pose %zu not finite", k / 2);
     cudaSetDevice(c->device);
+    drop_tracked_diffuse(g);
     if (g.d_poses) cudaFree(g.d_poses);
     g.d_poses = nullptr;
     int rc = upload(c, &g.d_poses, az_tilt, n);
@@ -693,6 +708,7 @@ extern "C" int pv3d_set_sun(pv3d_ctx* c, uint32_t gen_id, const double* sun_xyz,
         lit[k] = s[2] > 0.0;
     }
     cudaSetDevice(c->device);
+    drop_tracked_diffuse(g);
     void* olds[] = {g.d_sun, g.d_dni, g.d_dhi, g.d_dt};
     for (void* p : olds)
         if (p) cudaFree(p);
@@ -740,6 +756,7 @@ extern "C" int pv3d_set_sun_clear_sky(pv3d_ctx* c, uint32_t gen_id, const pv3d_s
     if (n_all > (1ll << 30)) return fail(c, PV3D_E_INVALID, "sun table too long");
     const double dhi_f = o->dhi_fraction > 0.f ? o->dhi_fraction : 0.1;
     cudaSetDevice(c->device);
+    drop_tracked_diffuse(g);
     cudaStream_t st = c->stream;
     double* d_xyz = nullptr;
     float *d_dni = nullptr, *d_dhi = nullptr, *d_dt = nullptr, *d_poses = nullptr;
@@ -1000,6 +1017,8 @@ static JobDev make_job(pv3d_ctx* c, const GenH& g, const SceneH& s, const EvalSe
         J.out_str_power_u = spwu;
     }
     J.fdiff = es.diffuse ? g.d_fdiff : nullptr;
+    J.fbin = es.diffuse ? g.d_fbin : nullptr;
+    J.fstride = g.C;
     if (es.arrays) {
         J.n_arr = (int32_t)g.arr_ids.size();
         J.arr_off = g.d_arr_off;
@@ -1520,6 +1539,20 @@ extern "C" int pv3d_evaluate(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts*
     return evaluate_plain(c, gen_id, o, out);
 }
 
+// Pose bin of a tracker pose: compass azimuth in n_az equal sectors of
+// [0, 2 pi), tilt in n_tilt equal bands of [0, pi/2]; bin = tilt band * n_az +
+// azimuth sector.  Its centre pose is the middle of both ranges.
+static int pose_bin(float az, float tilt, int n_az, int n_tilt)
+{
+    const double two_pi = 6.283185307179586, half_pi = 1.5707963267948966;
+    double a = std::fmod((double)az, two_pi);
+    if (a < 0) a += two_pi;
+    const int ia = std::min(n_az - 1, std::max(0, (int)std::floor(a / two_pi * n_az)));
+    const double t = std::min(half_pi, std::max(0.0, (double)tilt));
+    const int it = std::min(n_tilt - 1, std::max(0, (int)std::floor(t / half_pi * n_tilt)));
+    return it * n_az + ia;
+}
+
 extern "C" int pv3d_sky_view(pv3d_ctx* c, uint32_t gen_id, const pv3d_sky_view_opts* o, float* cell_fraction)
 {
     if (!c) return PV3D_E_INVALID;
@@ -1532,61 +1565,119 @@ extern "C" int pv3d_sky_view(pv3d_ctx* c, uint32_t gen_id, const pv3d_sky_view_o
     const int n = d.samples_per_side ? d.samples_per_side : 3;
     if (rings < 1 || rings > 90 || sectors < 1 || sectors > 360 || n < 1 || n > 15)
         return fail(c, PV3D_E_INVALID, "sky view: rings 1..90, sectors 1..360, samples_per_side 1..15");
-    for (const ModuleDev& M : g.mods_h)
-        if (M.tracker >= 0) return fail(c, PV3D_E_INVALID, "sky view: fixed modules only");
+    const bool tracked = g.n_trk > 0;
+    const int n_az = tracked ? (d.pose_az_bins ? d.pose_az_bins : 12) : 1;
+    const int n_tilt = tracked ? (d.pose_tilt_bins ? d.pose_tilt_bins : 6) : 1;
+    if (n_az < 1 || n_az > 360 || n_tilt < 1 || n_tilt > 90)
+        return fail(c, PV3D_E_INVALID, "sky view: pose_az_bins 1..360, pose_tilt_bins 1..90");
+    if (tracked && (!g.d_poses || g.n_pose_steps != g.n_steps || g.n_steps < 1))
+        return fail(c, PV3D_E_INVALID, "sky view of tracked modules: set the sun table and the poses first");
+    const int nb = n_az * n_tilt;
     const int P = rings * sectors;
     cudaSetDevice(c->device);
     cudaStream_t st = c->stream;
+    // the pose bin of every step (tracked): the first tracker's pose
+    std::vector<int32_t> bins;
+    std::vector<int> used;
+    if (tracked) {
+        std::vector<float> p0((size_t)g.n_steps * 2);
+        if (cudaMemcpy2D(p0.data(), 8, g.d_poses, (size_t)g.n_trk * 8, 8, (size_t)g.n_steps, cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+            return fail(c, PV3D_E_DEVICE, "sky view: pose read-back: %s", cudaGetErrorString(cudaGetLastError()));
+        bins.resize((size_t)g.n_steps);
+        std::vector<char> seen((size_t)nb, 0);
+        for (int64_t k = 0; k < g.n_steps; ++k) {
+            bins[(size_t)k] = pose_bin(p0[2 * k], p0[2 * k + 1], n_az, n_tilt);
+            if (g.lit[(size_t)k] && !seen[(size_t)bins[(size_t)k]]) {
+                seen[(size_t)bins[(size_t)k]] = 1;
+                used.push_back(bins[(size_t)k]);
+            }
+        }
+        std::sort(used.begin(), used.end());
+    } else {
+        used.push_back(0);
+    }
     double *xyz = nullptr, *dom = nullptr;
-    float *dni = nullptr, *dhi = nullptr, *dt = nullptr;
+    float *dni = nullptr, *dhi = nullptr, *dt = nullptr, *bposes = nullptr, *fdiff = nullptr;
+    int32_t* fbin = nullptr;
     uint8_t* counts = nullptr;
     auto cleanup = [&]() {
-        void* ps[] = {xyz, dom, dni, dhi, dt, counts};
+        void* ps[] = {xyz, dom, dni, dhi, dt, counts, bposes, fdiff, fbin};
         for (void* p : ps)
             if (p) cudaFree(p);
     };
     if (cudaMalloc(&xyz, (size_t)P * 24) != cudaSuccess || cudaMalloc(&dom, (size_t)P * 8) != cudaSuccess ||
         cudaMalloc(&dni, (size_t)P * 4) != cudaSuccess || cudaMalloc(&dhi, (size_t)P * 4) != cudaSuccess ||
         cudaMalloc(&dt, (size_t)P * 4) != cudaSuccess || cudaMalloc(&counts, (size_t)P * g.C) != cudaSuccess ||
-        (!g.d_fdiff && cudaMalloc(&g.d_fdiff, (size_t)g.C * 4) != cudaSuccess)) {
+        cudaMalloc(&fdiff, (size_t)nb * g.C * 4) != cudaSuccess ||
+        (tracked && (cudaMalloc(&bposes, (size_t)P * g.n_trk * 8) != cudaSuccess ||
+                     cudaMalloc(&fbin, (size_t)g.n_steps * 4) != cudaSuccess))) {
         cleanup();
         cudaGetLastError();
         return fail(c, PV3D_E_NOMEM, "sky view buffers");
     }
-    if (launch_sky_patches(rings, sectors, xyz, dni, dhi, dt, dom, st) != cudaSuccess) {
+    if (cudaMemsetAsync(fdiff, 0, (size_t)nb * g.C * 4, st) != cudaSuccess ||
+        (tracked && cudaMemcpy(fbin, bins.data(), bins.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) ||
+        launch_sky_patches(rings, sectors, xyz, dni, dhi, dt, dom, st) != cudaSuccess) {
         cleanup();
         return fail(c, PV3D_E_DEVICE, "sky patches: %s", cudaGetErrorString(cudaGetLastError()));
     }
-    // the patches stand in for the sun table while their depth tests run
-    double* s_sun = g.d_sun;
-    float *s_dni = g.d_dni, *s_dhi = g.d_dhi, *s_dt = g.d_dt;
-    const int64_t s_n = g.n_steps, s_np = g.n_pose_steps;
-    std::vector<uint8_t> s_lit = std::move(g.lit);
-    g.d_sun = xyz; g.d_dni = dni; g.d_dhi = dhi; g.d_dt = dt;
-    g.n_steps = P;
-    g.n_pose_steps = g.n_trk ? P : 0;
-    g.lit.assign((size_t)P, 1);
-    pv3d_eval_opts eo{};
-    eo.samples_per_side = n;
-    eo.map_res = d.map_res;
-    pv3d_result r{};
-    r.is_device = 1;
-    r.cell_counts = counts;
-    int rc = evaluate_plain(c, gen_id, &eo, &r);
-    g.d_sun = s_sun; g.d_dni = s_dni; g.d_dhi = s_dhi; g.d_dt = s_dt;
-    g.n_steps = s_n;
-    g.n_pose_steps = s_np;
-    g.lit = std::move(s_lit);
+    const double two_pi = 6.283185307179586, half_pi = 1.5707963267948966;
+    int rc = PV3D_OK;
+    for (int b : used) {
+        const double az_c = (b % n_az + 0.5) * two_pi / n_az, tilt_c = (b / n_az + 0.5) * half_pi / n_tilt;
+        if (tracked) {
+            std::vector<float> pz((size_t)P * g.n_trk * 2);
+            for (size_t k = 0; k < pz.size(); k += 2) { pz[k] = (float)az_c; pz[k + 1] = (float)tilt_c; }
+            if (cudaMemcpy(bposes, pz.data(), pz.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+                rc = fail(c, PV3D_E_DEVICE, "sky view: pose upload");
+                break;
+            }
+        }
+        // the patches stand in for the sun table (and every tracker takes the
+        // bin's centre pose) while their depth tests run
+        double* s_sun = g.d_sun;
+        float *s_dni = g.d_dni, *s_dhi = g.d_dhi, *s_dt = g.d_dt, *s_poses = g.d_poses;
+        const int64_t s_n = g.n_steps, s_np = g.n_pose_steps;
+        std::vector<uint8_t> s_lit = std::move(g.lit);
+        g.d_sun = xyz; g.d_dni = dni; g.d_dhi = dhi; g.d_dt = dt;
+        g.n_steps = P;
+        if (tracked) { g.d_poses = bposes; g.n_pose_steps = P; }
+        g.lit.assign((size_t)P, 1);
+        pv3d_eval_opts eo{};
+        eo.samples_per_side = n;
+        eo.map_res = d.map_res;
+        pv3d_result r{};
+        r.is_device = 1;
+        r.cell_counts = counts;
+        rc = evaluate_plain(c, gen_id, &eo, &r);
+        g.d_sun = s_sun; g.d_dni = s_dni; g.d_dhi = s_dhi; g.d_dt = s_dt;
+        g.n_steps = s_n;
+        g.d_poses = s_poses;
+        g.n_pose_steps = s_np;
+        g.lit = std::move(s_lit);
+        if (rc) break;
+        if (launch_sky_fraction(g.d_mods, g.d_cell_mod, g.C, xyz, dom, P, counts, n * n, fdiff + (size_t)b * g.C,
+                                tracked ? az_c : 0.0, tracked ? tilt_c : 0.0, st) != cudaSuccess) {
+            rc = fail(c, PV3D_E_DEVICE, "sky fraction: %s", cudaGetErrorString(cudaGetLastError()));
+            break;
+        }
+    }
+    if (!rc && (cudaStreamSynchronize(st) != cudaSuccess ||
+                (cell_fraction &&
+                 cudaMemcpy(cell_fraction, fdiff, (size_t)nb * g.C * 4, cudaMemcpyDeviceToHost) != cudaSuccess)))
+        rc = fail(c, PV3D_E_DEVICE, "sky fraction: %s", cudaGetErrorString(cudaGetLastError()));
     if (rc) {
         cleanup();
         return rc;
     }
-    if (launch_sky_fraction(g.d_mods, g.d_cell_mod, g.C, xyz, dom, P, counts, n * n, g.d_fdiff, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess ||
-        (cell_fraction && cudaMemcpy(cell_fraction, g.d_fdiff, (size_t)g.C * 4, cudaMemcpyDeviceToHost) != cudaSuccess)) {
-        cleanup();
-        return fail(c, PV3D_E_DEVICE, "sky fraction: %s", cudaGetErrorString(cudaGetLastError()));
-    }
+    if (g.d_fdiff) cudaFree(g.d_fdiff);
+    if (g.d_fbin) cudaFree(g.d_fbin);
+    g.d_fdiff = fdiff;
+    g.d_fbin = fbin;
+    g.fdiff_bins = nb;
+    fdiff = nullptr;
+    fbin = nullptr;
     cleanup();
     return PV3D_OK;
 }

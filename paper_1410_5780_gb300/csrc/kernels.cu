@@ -2367,6 +2367,15 @@ __global__ void __launch_bounds__(256) k_raster_map(const WaveDev* __restrict__ 
 // ---------------------------------------------------------------------------
 constexpr int kPvThreads = 128;
 
+// The diffuse shading fractions of local step ls: the row of its pose bin
+// (tracked generators) or the generator's one row; nullptr when the diffuse
+// term is not shaded.
+__device__ __forceinline__ const float* diffuse_row(const JobDev& J, int ls)
+{
+    if (!J.fdiff) return nullptr;
+    return J.fbin ? J.fdiff + (int64_t)J.fbin[J.step0 + ls] * J.fstride : J.fdiff;
+}
+
 // Irradiance per cell, substring currents, MPP over the bypass states.  All
 // threads of the block call it with the cell counts in shared memory.
 __device__ void module_pv(const JobDev& J, const ModuleDev& M, const ModStep& s, const LightParams& lp,
@@ -2377,9 +2386,10 @@ __device__ void module_pv(const JobDev& J, const ModuleDev& M, const ModStep& s,
     const float diff = lp.dhi * (1.f + s.nz) * 0.5f;
     const float inv_nn = 1.f / J.nn;
     const int* csub = J.lay_sub + J.lay_off[M.layout];
+    const float* fd = diffuse_row(J, (int)((msi - J.ms_base) / J.n_mods));
     for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
         const float f = s_cnt[c] * inv_nn;
-        const float gd = J.fdiff ? diff * (1.f - J.fdiff[M.cell_base + c]) : diff;
+        const float gd = fd ? diff * (1.f - fd[M.cell_base + c]) : diff;
         const float G = beam * (1.f - f) + gd;
         const float I = J.i_ref * G * 1e-3f;
         atomicMin(&s_imin[csub[c]], __float_as_uint(I));  // I >= 0: uint order = float order
@@ -2457,11 +2467,12 @@ __device__ void pv_module_warp(const JobDev* jobs, int nj, int64_t item, const B
     const int ns = M.n_sub;
     for (int k = lane; k < ns; k += 32) imin[k] = 0x7F800000u;  // +inf
     __syncwarp();
+    const float* fd = diffuse_row(J, ls);
     for (int c = lane; c < ncell; c += 32) {
         const uint32_t cnt = B.cs_cnt[cbase + c];
         if (J.out_counts) J.out_counts[row * J.out_cstride + M.cell_base + c] = (uint8_t)cnt;
         if (J.out_bits) J.out_bits[row * J.out_cstride + M.cell_base + c] = B.cs_bits[cbase + c];
-        const float gd = J.fdiff ? diff * (1.f - J.fdiff[M.cell_base + c]) : diff;
+        const float gd = fd ? diff * (1.f - fd[M.cell_base + c]) : diff;
         const float G = beam * (1.f - cnt * inv_nn) + gd;
         const float I = J.i_ref * G * 1e-3f;
         atomicMin(&imin[csub[c]], __float_as_uint(I));  // I >= 0: uint order = float order
@@ -2563,7 +2574,9 @@ __global__ void __launch_bounds__(kPvThreads) k_pv(const WaveDev* __restrict__ W
             const int64_t cb = __shfl_sync(0xffffffffu, cbase, q);
             const int* cs = reinterpret_cast<const int*>(
                 __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(csub), q));
-            const int64_t row = (int64_t)(J.out_row0 + __shfl_sync(0xffffffffu, ls, q));
+            const int lsq = __shfl_sync(0xffffffffu, ls, q);
+            const int64_t row = (int64_t)(J.out_row0 + lsq);
+            const float* fd = diffuse_row(J, lsq);
             const bool litq = __shfl_sync(0xffffffffu, (int)lit, q) != 0;
             const float bq = __shfl_sync(0xffffffffu, beam, q), dq = __shfl_sync(0xffffffffu, diff, q);
             const float inv_nn = 1.f / J.nn;
@@ -2593,7 +2606,7 @@ __global__ void __launch_bounds__(kPvThreads) k_pv(const WaveDev* __restrict__ W
                     if (c >= nc) continue;
                     if (J.out_counts) J.out_counts[row * J.out_cstride + c0 + c] = (uint8_t)cnt[u];
                     if (J.out_bits) J.out_bits[row * J.out_cstride + c0 + c] = B.cs_bits[cb + c];
-                    const float gd = J.fdiff ? dq * (1.f - J.fdiff[c0 + c]) : dq;
+                    const float gd = fd ? dq * (1.f - fd[c0 + c]) : dq;
                     const float G = bq * (1.f - cnt[u] * inv_nn) + gd;
                     const float I = J.i_ref * G * 1e-3f;
                     atomicMin(&im[sub[u]], __float_as_uint(I));  // I >= 0: uint order = float order
@@ -3119,11 +3132,13 @@ __global__ void k_sky_patches(int rings, int sectors, double* __restrict__ xyz, 
 }
 
 // Per cell: f = sum_p W_p s_p / sum_p W_p, W_p = solid angle x max(0, n . w_p)
-// with the module's front normal n, s_p = shaded samples toward patch p / n^2
-// (counts[p][c]); summed in patch order in FP64.
+// with the module's front normal n (a tracked module's at the pose (az,
+// tilt) of the sky view: R = Rz(pi - az) Rx(tilt)), s_p = shaded samples
+// toward patch p / n^2 (counts[p][c]); summed in patch order in FP64.
 __global__ void k_sky_fraction(const ModuleDev* __restrict__ mods, const int32_t* __restrict__ cell_mod, int n_cells,
                                const double* __restrict__ xyz, const double* __restrict__ dom, int n_patch,
-                               const uint8_t* __restrict__ counts, int nn, float* __restrict__ fdiff)
+                               const uint8_t* __restrict__ counts, int nn, float* __restrict__ fdiff, double az,
+                               double tilt)
 {
     for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += gridDim.x * blockDim.x) {
         const ModuleDev& M = mods[cell_mod[c]];
@@ -3132,6 +3147,14 @@ __global__ void k_sky_fraction(const ModuleDev* __restrict__ mods, const int32_t
         double nz = (double)M.u[0] * M.v[1] - (double)M.u[1] * M.v[0];
         const double l = sqrt(nx * nx + ny * ny + nz * nz);
         nx /= l; ny /= l; nz /= l;
+        if (M.tracker >= 0) {
+            const double cb = cos(tilt), sb = sin(tilt), cg = -cos(az), sg = sin(az);
+            const double yy = cb * ny - sb * nz, zz = sb * ny + cb * nz;
+            const double xx = nx;
+            nx = cg * xx - sg * yy;
+            ny = sg * xx + cg * yy;
+            nz = zz;
+        }
         double num = 0.0, den = 0.0;
         for (int p = 0; p < n_patch; ++p) {
             const double w = dom[p] * fmax(0.0, nx * xyz[3 * p] + ny * xyz[3 * p + 1] + nz * xyz[3 * p + 2]);
@@ -3279,10 +3302,10 @@ cudaError_t launch_sky_patches(int rings, int sectors, double* xyz, float* dni, 
 
 cudaError_t launch_sky_fraction(const ModuleDev* mods, const int32_t* cell_mod, int n_cells, const double* xyz,
                                 const double* dom, int n_patch, const uint8_t* counts, int nn, float* fdiff,
-                                cudaStream_t st)
+                                double az, double tilt, cudaStream_t st)
 {
     k_sky_fraction<<<grid_for(n_cells, 128, 4096), 128, 0, st>>>(mods, cell_mod, n_cells, xyz, dom, n_patch, counts,
-                                                                  nn, fdiff);
+                                                                  nn, fdiff, az, tilt);
     return cudaGetLastError();
 }
 

@@ -130,7 +130,9 @@ struct JobDev {
     double* heat_e;           // [bins]  sum of the generator's P_mpp * dt
     double* heat_eu;          // [bins]  same without shading
     int32_t* heat_n;          // [bins]  steps
-    const float* fdiff;       // [C] diffuse shading fraction per cell (pv3d_sky_view), or nullptr
+    const float* fdiff;       // [bins][C] diffuse shading fraction per cell (pv3d_sky_view), or nullptr
+    const int32_t* fbin;      // [steps] the step's pose bin (tracked generators), or nullptr (one bin)
+    int64_t fstride;          // cells of the generator (one bin's row of fdiff)
     // strings in parallel (array outputs requested; n_arr = 0 otherwise):
     // array a holds strings arr_strs[arr_off[a] .. arr_off[a + 1])
     int32_t n_arr;
@@ -278,7 +280,7 @@ cudaError_t launch_sky_patches(int rings, int sectors, double* xyz, float* dni, 
 // per cell: diffuse shading fraction from the counts [patch][cell] of fixed modules
 cudaError_t launch_sky_fraction(const ModuleDev* mods, const int32_t* cell_mod, int n_cells, const double* xyz,
                                 const double* dom, int n_patch, const uint8_t* counts, int nn, float* fdiff,
-                                cudaStream_t stream);
+                                double az, double tilt, cudaStream_t st);
 // two-axis trackers facing the sun: compass azimuth, tilt = zenith angle clamped to tilt_max
 cudaError_t launch_ideal_poses(const double* sun, int64_t n_steps, int n_trk, float tilt_max, float* poses,
                                cudaStream_t stream);

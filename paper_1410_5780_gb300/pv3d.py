@@ -104,7 +104,8 @@ class pv3d_result(C.Structure):
 
 class pv3d_sky_view_opts(C.Structure):
     _fields_ = [("rings", C.c_int32), ("sectors", C.c_int32), ("samples_per_side", C.c_int32),
-                ("map_res", C.c_int32), ("reserved", C.c_int32 * 4)]
+                ("map_res", C.c_int32), ("pose_az_bins", C.c_int32), ("pose_tilt_bins", C.c_int32),
+                ("reserved", C.c_int32 * 2)]
 
 
 class pv3d_sky_opts(C.Structure):
@@ -256,7 +257,7 @@ class Context:
                                                    C.byref(gid)))
         cells = int((np.asarray(gen.cells_u, np.int64) * np.asarray(gen.cells_v, np.int64)).sum())
         self._gens[gid.value] = {"modules": m, "cells": cells, "steps": 0, "strings": len(self.string_ids(gid.value)),
-                                 "arrays": len(self.array_ids(gid.value))}
+                                 "arrays": len(self.array_ids(gid.value)), "trackers": int(piv.shape[0])}
         return gid.value
 
     def array_ids(self, gen_id: int) -> np.ndarray:
@@ -302,13 +303,19 @@ class Context:
         self._gens[gen_id]["steps"] = n.value
         return n.value
 
-    def sky_view(self, gen_id: int, rings: int = 9, sectors: int = 36, n: int = 3, map_res: int = 0) -> np.ndarray:
+    def sky_view(self, gen_id: int, rings: int = 9, sectors: int = 36, n: int = 3, map_res: int = 0,
+                 pose_az_bins: int = 12, pose_tilt_bins: int = 6) -> np.ndarray:
         """pv3d_sky_view: per-cell diffuse shading fractions (kept with the
-        generator for evaluations with diffuse_shading)."""
-        o = pv3d_sky_view_opts(rings=rings, sectors=sectors, samples_per_side=n, map_res=map_res)
-        f = np.zeros(self._gens[gen_id]["cells"], np.float32)
+        generator for evaluations with diffuse_shading): [cells] for a
+        generator of fixed modules, [pose_tilt_bins * pose_az_bins, cells]
+        (one row per pose bin) for a tracked one."""
+        o = pv3d_sky_view_opts(rings=rings, sectors=sectors, samples_per_side=n, map_res=map_res,
+                               pose_az_bins=pose_az_bins, pose_tilt_bins=pose_tilt_bins)
+        g = self._gens.get(gen_id, {"cells": 0, "trackers": 0})
+        bins = pose_az_bins * pose_tilt_bins if g["trackers"] else 1
+        f = np.zeros((bins, max(g["cells"], 1)), np.float32)
         self._check(self.lib.pv3d_sky_view(self.h, gen_id, C.byref(o), _p(f)))
-        return f
+        return f if g["trackers"] else f[0]
 
     def sun_table(self, gen_id: int):
         """pv3d_sun_table: (xyz [N, 3] float64, dni, dhi, dt_h [N] float32) of the generator."""

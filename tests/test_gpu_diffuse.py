@@ -1,8 +1,9 @@
 """GPU parity of diffuse shading (pv3d_sky_view): per-cell shares of the
 cosine-weighted sky hidden by the scene, from depth tests toward the sky
 patches, against the FP64 oracle's ray tests toward the same patches; a long
-wall against its closed-form view factor; and the PV model with the diffuse
-term shaded, on the GPU's own counts and fractions."""
+wall against its closed-form view factor; tracked modules per pose bin; and
+the PV model with the diffuse term shaded, on the GPU's own counts and
+fractions."""
 import math
 
 import numpy as np
@@ -95,11 +96,47 @@ def test_facade_fractions_and_pv_model(ctx):
     ctx.release(gid)
 
 
-def test_tracked_modules_rejected(ctx):
-    w = S.make_random_small(43, n_mods=3, n_steps=3, n=2, tracked=True)
+def test_tracked_fractions_per_pose_bin_and_pv_model(ctx):
+    """Tracked modules: fractions per pose bin (a step's bin is the first
+    tracker's pose; every tracker at the bin's centre pose for the sky view)
+    against the oracle's exact rays toward the same patches at the same
+    poses, and the PV model with the diffuse term shaded by the row of each
+    step's bin and the module's own tilt at the step."""
+    w = S.make_tracker(seed=29, n=3, map_res=512, grid=(3, 2), terrain_n=48, spacing=1.5, relief=2.0, n_pylons=1,
+                       step_h=2.0, days=np.array([40, 200]))
     gid = pv3d.load_workload(ctx, w)
+    rings, sectors, n_az, n_tilt = 4, 12, 4, 2
+    f = ctx.sky_view(gid, rings=rings, sectors=sectors, n=3, map_res=512, pose_az_bins=n_az, pose_tilt_bins=n_tilt)
+    assert f.shape == (n_az * n_tilt, w.gen.n_cells)
+    fo, masked, step_bin = oracle.tracked_diffuse_fractions(w, rings, sectors, n_az, n_tilt, 3, 512)
+    assert len(fo) >= 2
+    for b in range(n_az * n_tilt):
+        if b in fo:
+            assert np.all(np.abs(f[b] - fo[b]) <= masked[b] + 0.01), (b, np.abs(f[b] - fo[b]).max())
+        else:
+            assert not f[b].any()
+    assert max(float(fo[b].max()) for b in fo) > 0.02  # neighbouring tables and the ground hide some sky
+    g = ctx.evaluate(gid, n=w.n, map_res=w.map_res, outputs=("cell_counts", "power", "energy"), device=False,
+                     diffuse_shading=True)
+    g0 = ctx.evaluate(gid, n=w.n, map_res=w.map_res, outputs=("energy",), device=False)
+    assert g["energy"].sum() < g0["energy"].sum()
+    starts = np.concatenate([[0], np.cumsum(w.gen.cells_u * w.gen.cells_v)])
+    lay = w.gen.layouts[0]
+    rng = np.random.default_rng(2)
+    lit = np.flatnonzero(w.sun.xyz[:, 2] > 0)
+    for st in rng.choice(lit, min(8, len(lit)), replace=False):
+        s = w.sun.xyz[st]
+        for m in rng.choice(w.gen.n_modules, 12, replace=False):
+            nrm = oracle.module_normal(w.gen, w.poses, int(st), int(m))
+            beam = float(w.sun.dni[st]) * max(0.0, float(nrm @ s))
+            diff = float(w.sun.dhi[st]) * (1 + nrm[2]) / 2
+            c0, c1 = starts[m], starts[m + 1]
+            fc = g["cell_counts"][st, c0:c1] / float(w.n * w.n)
+            G = beam * (1 - fc) + diff * (1 - f[step_bin[st], c0:c1].astype(np.float64))
+            p = oracle.module_pmpp(G, lay.cell_sub, lay.n_sub)
+            assert abs(g["power"][st, m] - p) <= 1e-4 * max(p, 1.0) + 1e-3, (st, m, g["power"][st, m], p)
+    # a new pose table drops the fractions
+    ctx.set_poses(gid, w.poses)
     with pytest.raises(pv3d.PV3DError):
-        ctx.sky_view(gid)
-    with pytest.raises(pv3d.PV3DError):  # no fractions were made
         ctx.evaluate(gid, n=2, diffuse_shading=True)
     ctx.release(gid)

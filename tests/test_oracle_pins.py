@@ -724,3 +724,55 @@ def test_cell_beam_loss_from_counts_matches_the_evaluation():
         b = oracle.cell_beam_loss_from_counts(w, o["steps"], o["modules"], o["counts"], o["cos_inc"])
         assert o["cell_beam_loss"].max() > 0
         assert np.allclose(b, o["cell_beam_loss"], rtol=1e-12, atol=1e-9)
+
+
+# ---------------------------------------------------------------------------
+# diffuse shading of tracked modules: pose bins and the posed sky view
+# ---------------------------------------------------------------------------
+def test_pose_bins_hand_values():
+    """Pose bins: azimuth sectors of [0, 360) deg (wrapped), tilt bands of
+    [0, 90] deg (clamped), bin = band * sectors + sector, centre poses in the
+    middle of both ranges -- values written out by hand."""
+    d = math.radians
+    poses = np.array([[d(10), d(5)], [d(-10), d(5)], [d(95), d(46)], [d(360 + 185), d(90)], [d(270), d(-3)]])
+    b, az_c, tilt_c = oracle.pose_bins(poses, 4, 2)
+    assert list(b) == [0, 3, 5, 6, 3]
+    assert np.allclose(np.degrees(az_c[[0, 3, 5, 6]]), [45, 315, 135, 225])
+    assert np.allclose(np.degrees(tilt_c[[0, 3, 5, 6]]), [22.5, 22.5, 67.5, 67.5])
+
+
+def test_tracked_sky_view_equals_fixed_module_at_the_bin_pose():
+    """A tracked module's diffuse fraction at pose bin (az 90, tilt 45 deg)
+    equals that of a fixed module placed by hand where that pose puts it:
+    R = Rz(pi - az) Rx(tilt) maps the local axes x -> (0, 1, 0) and y ->
+    (-cos 45, 0, sin 45) (facing east, tilted 45 deg), the origin to
+    pivot + R o.  The fixed path is pinned by the long wall's view factor."""
+    mb = S.MeshBuilder()
+    mb.grid_quad((3.0, -100.0, 0.0), (0.0, 200.0, 0.0), (0.0, 0.0, 6.0), 20, 1)   # wall 3 m east, 6 m high
+    mb.box((-4.0, -2.0, 0.0), (-3.0, 2.0, 2.5))
+    scene = mb.build()
+    lay = S.Layout(3, 2, 1, np.zeros(6, np.int32))
+    o_loc = np.array([-0.234, -0.156, 0.0])
+    piv = np.array([0.5, 0.2, 2.0])
+    g_trk = S._gen_from_lists([tuple(o_loc)], [(1.0, 0.0, 0.0)], [(0.0, 1.0, 0.0)], 3, 2, [0], [0], [0], [lay],
+                              piv[None, :])
+    c = math.cos(math.radians(45.0))
+    u_w, v_w = np.array([0.0, 1.0, 0.0]), np.array([-c, 0.0, c])
+    o_w = piv + o_loc[0] * u_w + o_loc[1] * v_w
+    g_fix = S._gen_from_lists([tuple(o_w)], [tuple(u_w)], [tuple(v_w)], 3, 2, [0], [-1], [0], [lay], np.zeros((0, 3)))
+    sun1 = S.Sun(xyz=np.array([[0.0, 0.0, 1.0]]), dni=np.ones(1, np.float32), dhi=np.ones(1, np.float32),
+                 dt_h=np.ones(1, np.float32))
+    poses = np.array([[[math.radians(100.0), math.radians(50.0)]]], np.float32)   # falls in bin (90, 45)
+    w_trk = S.Workload("trk", scene, g_trk, sun1, poses, 3, 512)
+    f_trk, _, step_bin = oracle.tracked_diffuse_fractions(w_trk, 6, 24, 2, 1, 3, 512, want_mask=False)
+    assert list(step_bin) == [0] and list(f_trk) == [0]
+    rings, sectors = 6, 24
+    xyz, _ = oracle.sky_patches(rings, sectors)
+    sun = S.Sun(xyz=xyz, dni=np.ones(len(xyz), np.float32), dhi=np.zeros(len(xyz), np.float32),
+                dt_h=np.ones(len(xyz), np.float32))
+    o = oracle.evaluate(scene, g_fix, sun, None, 3, 512, want_mask=False)
+    nrm = np.repeat(np.cross(u_w, v_w)[None, :], 6, 0)
+    f_fix = oracle.diffuse_shade_fractions(S.Workload("fix", scene, g_fix, sun, None, 3, 512), rings, sectors,
+                                           o["counts"], nrm)
+    assert f_fix.max() > 0.05  # the wall hides part of the east-facing module's sky
+    assert np.allclose(f_trk[0], f_fix, atol=1e-12), (f_trk[0], f_fix)

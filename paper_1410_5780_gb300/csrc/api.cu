@@ -1095,7 +1095,7 @@ static int ensure_workspace(pv3d_ctx* c, int64_t js, int64_t te, int64_t ms, int
     if ((rc = ensure(c, c->lp, js * sizeof(LightParams))) || (rc = ensure(c, c->win, js * 16)) ||
         (rc = ensure(c, c->ms, ms * sizeof(ModStep))) || (rc = ensure(c, c->ms_p, ms * 4)) ||
         (rc = ensure(c, c->ms_pu, ms * 4)) || (rc = ensure(c, c->ms_beam, ms * 4)) ||
-        (rc = ensure(c, c->cs_cnt, cs * 4)) || (rc = ensure(c, c->t_far, te * 4)) ||
+        (rc = ensure(c, c->cs_cnt, (cs + 3) / 4 * 4)) || (rc = ensure(c, c->t_far, te * 4)) ||
         (rc = ensure(c, c->t_cnt, te * 4)) || (rc = ensure(c, c->t_off, te * 4)) ||
         (rc = ensure(c, c->t_cur, te * 4)) || (rc = ensure(c, c->t_slot, te * 4)) ||
         (rc = ensure(c, c->t_rcnt, te * 4)) || (rc = ensure(c, c->t_plane, te * 4)) ||

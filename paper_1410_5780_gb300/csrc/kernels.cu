@@ -66,6 +66,23 @@ __device__ __forceinline__ float okey_inv(uint32_t k)
 
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;
 
+// Per-(step, cell) shaded-sample tallies, one byte per entry e (a count is at
+// most n^2 <= 225), four bytes to a 32-bit word: the tile kernels add to a
+// byte with a word atomic (no carry can leave the byte), the PV kernels read
+// bytes.
+__device__ __forceinline__ void tally_add(uint32_t* words, int64_t e, uint32_t cnt)
+{
+    atomicAdd(&words[e >> 2], cnt << (8 * (int)(e & 3)));
+}
+__device__ __forceinline__ uint32_t tally_get(const uint32_t* words, int64_t e)
+{
+    return reinterpret_cast<const uint8_t*>(words)[e];
+}
+__device__ __forceinline__ void tally_set(uint32_t* words, int64_t e, uint32_t v)
+{
+    reinterpret_cast<uint8_t*>(words)[e] = (uint8_t)v;
+}
+
 // Largest job index j with base(j) <= item (bases ascend with j).
 template <typename F>
 __device__ __forceinline__ int job_of(int n_jobs, int64_t item, F base)
@@ -254,8 +271,8 @@ __global__ void k_clear(const WaveDev* __restrict__ W, Buffers B)
         B.t_plane[i] = kPlaneNone;
     }
     if (W->fused) {
-        const int64_t nc = W->tot_cs;
-        for (int64_t i = i0; i < nc; i += stride) B.cs_cnt[i] = 0u;
+        const int64_t nc = W->tot_cs, nw = (nc + 3) / 4;  // tallies, and their words
+        for (int64_t i = i0; i < nw; i += stride) B.cs_cnt[i] = 0u;
         if (W->want_bits)
             for (int64_t i = i0; i < nc; i += stride) B.cs_bits[i] = 0ull;
     }
@@ -1681,7 +1698,8 @@ __device__ __forceinline__ void test_items(const RecvSm* recv, int n_recv, int t
                                            const LightParams& lp, int u24, int tx, int ty, int it_begin,
                                            int it_stride, const TriS* tri, int n_kept,
                                            const uint32_t (*sbm)[WORDS], int nw, uint32_t* seen,
-                                           uint32_t* cnt_row, unsigned long long* bits_row, int want_bits,
+                                           uint32_t* tally, int64_t tally0, unsigned long long* bits_row,
+                                           int want_bits,
                                            unsigned int& cand, unsigned int& samples, unsigned int& pairs,
                                            unsigned int& frags)
 {
@@ -1712,7 +1730,7 @@ __device__ __forceinline__ void test_items(const RecvSm* recv, int n_recv, int t
         }
         if (bits) {
             const int gcell = R.cell_base + cv * R.cu + cu;
-            atomicAdd(&cnt_row[gcell], (uint32_t)__popc(bits));
+            tally_add(tally, tally0 + gcell, (uint32_t)__popc(bits));
             // sample k = jj * n + i of the cell; flags kept for k < 64
             if (want_bits && jj * n < 64) atomicOr(&bits_row[gcell], (unsigned long long)bits << (jj * n));
         }
@@ -2130,7 +2148,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 6) k_tile_warp(const WaveDev*
                 const int C = J.n_cells;
                 test_items<TS, kWarpWords, PROF>(sm.recv, nrecv, total, J, lp, u24, tx, ty, lane, 32, sm.k.tri, n,
                                                  sm.k.sbm, (n + 31) >> 5, sm.k.seen,
-                                                 B.cs_cnt + J.cs_base + (int64_t)ls * C,
+                                                 B.cs_cnt, J.cs_base + (int64_t)ls * C,
                                                  B.cs_bits + J.cs_base + (int64_t)ls * C, want_bits, p_cand,
                                                  p_samples, p_pairs, p_writes);
             }
@@ -2256,7 +2274,7 @@ __global__ void __launch_bounds__(HeavyCfg<TS>::threads, HeavyCfg<TS>::min_block
         if (PROF && tid == 0) ++p_tiles;
         const LightParams& lp = B.lp[J.js_base + ls];
         const int C = J.n_cells;
-        uint32_t* cnt_row = B.cs_cnt + J.cs_base + (int64_t)ls * C;
+        const int64_t tally0 = J.cs_base + (int64_t)ls * C;
         unsigned long long* bits_row = B.cs_bits + J.cs_base + (int64_t)ls * C;
         const bool cull_ok = nrecv <= kRecvChunk;
         tile_limits<TS>(sm, lp, u24, cull_ok);
@@ -2279,7 +2297,7 @@ __global__ void __launch_bounds__(HeavyCfg<TS>::threads, HeavyCfg<TS>::min_block
                 }
                 test_items<TS, HeavyKept<TS>::words, PROF>(sm.recv, sm.n_recv, sm.total_items, J, lp, u24, tx, ty, tid,
                                                 blockDim.x, sm.u.s.tri, nt, sm.u.s.sbm, (nt + 31) >> 5,
-                                                sm.u.s.seen, cnt_row, bits_row, want_bits, p_cand, p_samples,
+                                                sm.u.s.seen, B.cs_cnt, tally0, bits_row, want_bits, p_cand, p_samples,
                                                 p_pairs, p_writes);
             }
         } else if (tile_raster<TS, PROF>(sm, J, B, W, ls, tx, ty, te, r0, nrecv, true, p_visits, p_writes, p_culled,
@@ -2302,7 +2320,7 @@ __global__ void __launch_bounds__(HeavyCfg<TS>::threads, HeavyCfg<TS>::min_block
                     [&](const RecvSm& R, int cu, int cv) {
                         if (cnt) {
                             const int gcell = R.cell_base + cv * R.cu + cu;
-                            atomicAdd(&cnt_row[gcell], cnt);
+                            tally_add(B.cs_cnt, tally0 + gcell, cnt);
                             if (want_bits) atomicOr(&bits_row[gcell], bits);
                         }
                         cnt = 0;
@@ -2427,7 +2445,7 @@ __device__ __forceinline__ void zero_step_module(const JobDev& J, const ModuleDe
     const int64_t row = (int64_t)(J.out_row0 + ls);
     if (threadIdx.x == 0) { B.ms_p[msi] = 0.f; B.ms_pu[msi] = 0.f; B.ms_beam[msi] = 0.f; }
     for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
-        B.cs_cnt[J.cs_base + (int64_t)ls * C + M.cell_base + c] = 0u;
+        tally_set(B.cs_cnt, J.cs_base + (int64_t)ls * C + M.cell_base + c, 0u);
         if (J.out_counts) J.out_counts[row * J.out_cstride + M.cell_base + c] = 0;
         if (J.out_bits) J.out_bits[row * J.out_cstride + M.cell_base + c] = 0ull;
     }
@@ -2453,7 +2471,7 @@ __device__ void pv_module_warp(const JobDev* jobs, int nj, int64_t item, const B
     if (!lp.valid) {
         if (lane == 0) { B.ms_p[msi] = 0.f; B.ms_pu[msi] = 0.f; B.ms_beam[msi] = 0.f; }
         for (int c = lane; c < ncell; c += 32) {
-            B.cs_cnt[cbase + c] = 0u;
+            tally_set(B.cs_cnt, cbase + c, 0u);
             if (J.out_counts) J.out_counts[row * J.out_cstride + M.cell_base + c] = 0;
             if (J.out_bits) J.out_bits[row * J.out_cstride + M.cell_base + c] = 0ull;
         }
@@ -2469,7 +2487,7 @@ __device__ void pv_module_warp(const JobDev* jobs, int nj, int64_t item, const B
     __syncwarp();
     const float* fd = diffuse_row(J, ls);
     for (int c = lane; c < ncell; c += 32) {
-        const uint32_t cnt = B.cs_cnt[cbase + c];
+        const uint32_t cnt = tally_get(B.cs_cnt, cbase + c);
         if (J.out_counts) J.out_counts[row * J.out_cstride + M.cell_base + c] = (uint8_t)cnt;
         if (J.out_bits) J.out_bits[row * J.out_cstride + M.cell_base + c] = B.cs_bits[cbase + c];
         const float gd = fd ? diff * (1.f - fd[M.cell_base + c]) : diff;
@@ -2583,7 +2601,7 @@ __global__ void __launch_bounds__(kPvThreads) k_pv(const WaveDev* __restrict__ W
             uint32_t* im = imin + q * kPvFastSub;
             if (!litq) {
                 for (int c = lane; c < nc; c += 32) {
-                    B.cs_cnt[cb + c] = 0u;
+                    tally_set(B.cs_cnt, cb + c, 0u);
                     if (J.out_counts) J.out_counts[row * J.out_cstride + c0 + c] = 0;
                     if (J.out_bits) J.out_bits[row * J.out_cstride + c0 + c] = 0ull;
                 }
@@ -2597,7 +2615,7 @@ __global__ void __launch_bounds__(kPvThreads) k_pv(const WaveDev* __restrict__ W
 #pragma unroll
                 for (int u = 0; u < kPvUnroll; ++u) {
                     const int c = cr + 32 * u;
-                    cnt[u] = c < nc ? B.cs_cnt[cb + c] : 0u;
+                    cnt[u] = c < nc ? tally_get(B.cs_cnt, cb + c) : 0u;
                     sub[u] = c < nc ? cs[c] : 0;
                 }
 #pragma unroll
@@ -2726,7 +2744,7 @@ __global__ void __launch_bounds__(kPvThreads) k_sample(const WaveDev* __restrict
         __syncthreads();
         for (int c = threadIdx.x; c < ncell; c += blockDim.x) {
             const uint32_t cnt = s_cnt[c];
-            B.cs_cnt[J.cs_base + (int64_t)ls * C + M.cell_base + c] = cnt;
+            tally_set(B.cs_cnt, J.cs_base + (int64_t)ls * C + M.cell_base + c, cnt);
             if (J.out_counts) J.out_counts[row * J.out_cstride + M.cell_base + c] = (uint8_t)cnt;
             if (J.out_bits) J.out_bits[row * J.out_cstride + M.cell_base + c] = s_bits[c];
         }
@@ -3003,7 +3021,7 @@ __global__ void __launch_bounds__(256) k_epilogue(const WaveDev* __restrict__ W,
                 if (kind == 0) {
                     if (v) {
                         const float beam = B.ms_beam[J.ms_base + (int64_t)ls * Mn + m_cell];
-                        const uint32_t cnt = B.cs_cnt[J.cs_base + (int64_t)ls * C + idx];
+                        const uint32_t cnt = tally_get(B.cs_cnt, J.cs_base + (int64_t)ls * C + idx);
                         x = beam * (cnt * inv_nn) * lp.dt;
                     }
                 } else if (kind == 1) {

@@ -222,7 +222,8 @@ struct Buffers {
     float* js_p;             // [tot_js]  the generator's P_mpp per step (heat map)
     float* js_pu;            // [tot_js]
     int32_t* js_bin;         // [tot_js]  sky bin of the step's sun, -1 below the horizon
-    uint32_t* cs_cnt;        // [tot_cs]  shaded samples per (step, cell)
+    uint32_t* cs_cnt;        // [(tot_cs + 3) / 4]  shaded samples per (step, cell): one byte each (a count
+                             //  is at most n^2 <= 225), four to a word for the tile kernels' atomics
     unsigned long long* cs_bits;  // [tot_cs] shaded flags per (step, cell), fused path with flags requested
     uint32_t* t_far;         // [tot_te]  far-plane key of the tile (0 = no sample)
     uint32_t* t_cnt;         // [tot_te]  triangles binned

@@ -2582,52 +2582,85 @@ __global__ void __launch_bounds__(kPvThreads) k_pv(const WaveDev* __restrict__ W
             for (int q = 0; q < bw && base + q < tot; ++q) pv_module_warp(jobs, nj, base + q, B, imin);
             continue;
         }
-        for (int k = 0; k < kPvFastSub; ++k) imin[lane * kPvFastSub + k] = 0x7F800000u;  // +inf
-        __syncwarp();
-        for (unsigned int act = __ballot_sync(0xffffffffu, have); act; act &= act - 1u) {
-            const int q = __ffs(act) - 1;
-            const JobDev& J = jobs[__shfl_sync(0xffffffffu, j, q)];
-            const int nc = __shfl_sync(0xffffffffu, ncell, q);
-            const int c0 = __shfl_sync(0xffffffffu, cell0, q);
-            const int64_t cb = __shfl_sync(0xffffffffu, cbase, q);
-            const int* cs = reinterpret_cast<const int*>(
-                __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(csub), q));
-            const int lsq = __shfl_sync(0xffffffffu, ls, q);
-            const int64_t row = (int64_t)(J.out_row0 + lsq);
-            const float* fd = diffuse_row(J, lsq);
-            const bool litq = __shfl_sync(0xffffffffu, (int)lit, q) != 0;
-            const float bq = __shfl_sync(0xffffffffu, beam, q), dq = __shfl_sync(0xffffffffu, diff, q);
-            const float inv_nn = 1.f / J.nn;
-            uint32_t* im = imin + q * kPvFastSub;
-            if (!litq) {
-                for (int c = lane; c < nc; c += 32) {
-                    tally_set(B.cs_cnt, cb + c, 0u);
-                    if (J.out_counts) J.out_counts[row * J.out_cstride + c0 + c] = 0;
-                    if (J.out_bits) J.out_bits[row * J.out_cstride + c0 + c] = 0ull;
+        uint32_t* im = imin + lane * kPvFastSub;
+        for (int k = 0; k < kPvFastSub; ++k) im[k] = 0x7F800000u;  // +inf
+        if (bw == 32) {
+            // a full batch: each lane walks its own module's cells (their
+            // tallies are one byte each, consecutive per module: the warp's
+            // lanes share the few cache lines of their modules), the
+            // substring minima in its slice of shared memory
+            if (have) {
+                const JobDev& J = jobs[j];
+                const int64_t row = (int64_t)(J.out_row0 + ls);
+                if (!lit) {
+                    for (int c = 0; c < ncell; ++c) {
+                        tally_set(B.cs_cnt, cbase + c, 0u);
+                        if (J.out_counts) J.out_counts[row * J.out_cstride + cell0 + c] = 0;
+                        if (J.out_bits) J.out_bits[row * J.out_cstride + cell0 + c] = 0ull;
+                    }
+                } else {
+                    const float* fd = diffuse_row(J, ls);
+                    const float inv_nn = 1.f / J.nn;
+                    for (int c = 0; c < ncell; ++c) {
+                        const uint32_t cnt = tally_get(B.cs_cnt, cbase + c);
+                        if (J.out_counts) J.out_counts[row * J.out_cstride + cell0 + c] = (uint8_t)cnt;
+                        if (J.out_bits) J.out_bits[row * J.out_cstride + cell0 + c] = B.cs_bits[cbase + c];
+                        const float gd = fd ? diff * (1.f - fd[cell0 + c]) : diff;
+                        const float G = beam * (1.f - cnt * inv_nn) + gd;
+                        const uint32_t I = __float_as_uint(J.i_ref * G * 1e-3f);  // I >= 0: uint order = float order
+                        const int k = csub[c];
+                        if (I < im[k]) im[k] = I;
+                    }
                 }
-                continue;
             }
-            // kPvUnroll rounds of 32 cells at once: their loads are issued
-            // together, before the minima are taken
-            for (int cr = lane; cr < nc; cr += 32 * kPvUnroll) {
-                uint32_t cnt[kPvUnroll];
-                int sub[kPvUnroll];
-#pragma unroll
-                for (int u = 0; u < kPvUnroll; ++u) {
-                    const int c = cr + 32 * u;
-                    cnt[u] = c < nc ? tally_get(B.cs_cnt, cb + c) : 0u;
-                    sub[u] = c < nc ? cs[c] : 0;
+        } else {
+            // a short batch (a wave too small to fill the grid): the lanes
+            // take the cells of one item after another, loads of 32 cells at
+            // a time issued together before the minima are taken
+            __syncwarp();
+            for (unsigned int act = __ballot_sync(0xffffffffu, have); act; act &= act - 1u) {
+                const int q = __ffs(act) - 1;
+                const JobDev& J = jobs[__shfl_sync(0xffffffffu, j, q)];
+                const int nc = __shfl_sync(0xffffffffu, ncell, q);
+                const int c0 = __shfl_sync(0xffffffffu, cell0, q);
+                const int64_t cb = __shfl_sync(0xffffffffu, cbase, q);
+                const int* cs = reinterpret_cast<const int*>(
+                    __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(csub), q));
+                const int lsq = __shfl_sync(0xffffffffu, ls, q);
+                const int64_t row = (int64_t)(J.out_row0 + lsq);
+                const float* fd = diffuse_row(J, lsq);
+                const bool litq = __shfl_sync(0xffffffffu, (int)lit, q) != 0;
+                const float bq = __shfl_sync(0xffffffffu, beam, q), dq = __shfl_sync(0xffffffffu, diff, q);
+                const float inv_nn = 1.f / J.nn;
+                uint32_t* iq = imin + q * kPvFastSub;
+                if (!litq) {
+                    for (int c = lane; c < nc; c += 32) {
+                        tally_set(B.cs_cnt, cb + c, 0u);
+                        if (J.out_counts) J.out_counts[row * J.out_cstride + c0 + c] = 0;
+                        if (J.out_bits) J.out_bits[row * J.out_cstride + c0 + c] = 0ull;
+                    }
+                    continue;
                 }
+                for (int cr = lane; cr < nc; cr += 32 * kPvUnroll) {
+                    uint32_t cnt[kPvUnroll];
+                    int sub[kPvUnroll];
 #pragma unroll
-                for (int u = 0; u < kPvUnroll; ++u) {
-                    const int c = cr + 32 * u;
-                    if (c >= nc) continue;
-                    if (J.out_counts) J.out_counts[row * J.out_cstride + c0 + c] = (uint8_t)cnt[u];
-                    if (J.out_bits) J.out_bits[row * J.out_cstride + c0 + c] = B.cs_bits[cb + c];
-                    const float gd = fd ? dq * (1.f - fd[c0 + c]) : dq;
-                    const float G = bq * (1.f - cnt[u] * inv_nn) + gd;
-                    const float I = J.i_ref * G * 1e-3f;
-                    atomicMin(&im[sub[u]], __float_as_uint(I));  // I >= 0: uint order = float order
+                    for (int u = 0; u < kPvUnroll; ++u) {
+                        const int c = cr + 32 * u;
+                        cnt[u] = c < nc ? tally_get(B.cs_cnt, cb + c) : 0u;
+                        sub[u] = c < nc ? cs[c] : 0;
+                    }
+#pragma unroll
+                    for (int u = 0; u < kPvUnroll; ++u) {
+                        const int c = cr + 32 * u;
+                        if (c >= nc) continue;
+                        if (J.out_counts) J.out_counts[row * J.out_cstride + c0 + c] = (uint8_t)cnt[u];
+                        if (J.out_bits) J.out_bits[row * J.out_cstride + c0 + c] = B.cs_bits[cb + c];
+                        const float gd = fd ? dq * (1.f - fd[c0 + c]) : dq;
+                        const float G = bq * (1.f - cnt[u] * inv_nn) + gd;
+                        const float I = J.i_ref * G * 1e-3f;
+                        atomicMin(&iq[sub[u]], __float_as_uint(I));  // I >= 0: uint order = float order
+                    }
                 }
             }
         }
@@ -2640,7 +2673,6 @@ __global__ void __launch_bounds__(kPvThreads) k_pv(const WaveDev* __restrict__ W
                 B.ms_beam[msi] = 0.f;
             } else {
                 const ModuleDev& M = J.mods[m];
-                const uint32_t* im = imin + lane * kPvFastSub;
                 if (J.n_str) {  // substring currents for the series-string model (k_string)
                     float* ss = B.ss_i + J.ss_base + (int64_t)ls * J.n_sub_tot + J.sub_base[m];
                     for (int k = 0; k < ns; ++k) ss[k] = __uint_as_float(im[k]);

@@ -665,6 +665,8 @@ __device__ __forceinline__ void append_pairs(const Buffers& B, const WaveDev* W,
         }
 }
 
+constexpr int kLaneTiles = 16;  // a meshlet over at most this many tiles is tested by its own lane
+
 __global__ void __launch_bounds__(256, 4) k_bin(const WaveDev* __restrict__ W, const JobDev* __restrict__ jobs,
                                              Buffers B)
 {
@@ -732,28 +734,51 @@ __global__ void __launch_bounds__(256, 4) k_bin(const WaveDev* __restrict__ W, c
         } else {
             pass = ml < n_all;
         }
-        for (unsigned int cand = __ballot_sync(0xffffffffu, pass); cand; cand &= cand - 1u) {
-            const int q = __ffs(cand) - 1;
-            const int mi = g * 32 + q;
+        // the meshlet's nearest point against the far plane of each tile it
+        // covers: each lane tests its own meshlet's tiles (independent loads
+        // across the warp), the warp together those of a meshlet over many
+        // tiles
+        bool keep_lane = false, coop = false;
+        if (pass && ml < n_boxed) {
+            const int ntl = (btx1 - btx0 + 1) * (bty1 - bty0 + 1);
+            if (ntl <= kLaneTiles) {
+                // no early exit: the loads of a row of tiles are issued together
+                for (int ty = bty0; ty <= bty1; ++ty) {
+                    const uint32_t* far_row = B.t_far + te0 + (int64_t)ty * J.tiles_x;
+#pragma unroll 4
+                    for (int tx = btx0; tx <= btx1; ++tx) keep_lane |= bkey < far_row[tx];
+                }
+            } else {
+                coop = true;
+            }
+        } else if (pass) {
+            keep_lane = true;  // module meshlets: no box
+        }
+        unsigned int kept = __ballot_sync(0xffffffffu, keep_lane);
+        for (unsigned int cm = __ballot_sync(0xffffffffu, coop); cm; cm &= cm - 1u) {
+            const int q = __ffs(cm) - 1;
             const int mx0 = __shfl_sync(0xffffffffu, btx0, q), mx1 = __shfl_sync(0xffffffffu, btx1, q);
             const int my0 = __shfl_sync(0xffffffffu, bty0, q), my1 = __shfl_sync(0xffffffffu, bty1, q);
             const uint32_t mkey = __shfl_sync(0xffffffffu, bkey, q);
+            const int wx = mx1 - mx0 + 1, ntl = wx * (my1 - my0 + 1);
+            bool keep = false;
+            for (int q0 = 0; q0 < ntl && !keep; q0 += 32) {
+                const int k = q0 + lane;
+                bool kk = false;
+                if (k < ntl) {
+                    const int ty = my0 + k / wx, tx = mx0 + k % wx;
+                    kk = mkey < B.t_far[te0 + (int64_t)ty * J.tiles_x + tx];
+                }
+                keep = __any_sync(0xffffffffu, kk);
+            }
+            if (keep) kept |= 1u << q;
+        }
+        for (unsigned int cand = kept; cand; cand &= cand - 1u) {
+            const int q = __ffs(cand) - 1;
+            const int mi = g * 32 + q;
             int t;
             bool act;
             if (mi < n_boxed) {
-                // the meshlet's nearest point against each covered tile's far plane
-                const int wx = mx1 - mx0 + 1, ntl = wx * (my1 - my0 + 1);
-                bool keep = false;
-                for (int q0 = 0; q0 < ntl && !keep; q0 += 32) {
-                    const int k = q0 + lane;
-                    bool kk = false;
-                    if (k < ntl) {
-                        const int ty = my0 + k / wx, tx = mx0 + k % wx;
-                        kk = mkey < B.t_far[te0 + (int64_t)ty * J.tiles_x + tx];
-                    }
-                    keep = __any_sync(0xffffffffu, kk);
-                }
-                if (!keep) continue;
                 if (mi < J.n_ml) {
                     t = mi * 32 + lane;
                     act = t < J.n_tris;

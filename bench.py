@@ -330,6 +330,15 @@ def extensions_section(ctx, gid, w, stream) -> dict:
     base, r0 = timed(lambda: ctx.evaluate(gid, n=w.n, map_res=w.map_res, outputs=("energy",),
                                           stream=stream.cuda_stream))
     out = {"plain_ms": base, "tests": r0["tests"]}
+    # FP32 Kahan yearly energy sums against the FP64 sum of the same per-step powers
+    rk = ctx.evaluate(gid, n=w.n, map_res=w.map_res, outputs=("energy", "power"), stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    p64 = rk["power"].double().cpu().numpy()
+    e64 = (p64 * w.sun.dt_h.astype(np.float64)[:, None]).sum(0)
+    ek = rk["energy"].cpu().numpy()
+    rel = np.abs(ek - e64) / np.maximum(np.abs(e64), 1e-30)
+    out["kahan_fp32_vs_fp64"] = {"max_rel_err": float(rel.max()), "mean_rel_err": float(rel.mean()),
+                                 "modules": int(len(ek)), "steps": int(w.sun.n_steps)}
     gen = w.gen
     sid = ctx.scene_load(w.scene.verts, w.scene.tris)
     saved = gen.string.copy()

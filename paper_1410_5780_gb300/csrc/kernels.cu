@@ -42,6 +42,7 @@
 // tracker poses (k_sun_table, k_gather_sun, k_ideal_poses) and the diffuse
 // sky view (k_sky_patches, then the waves over the patches, k_sky_fraction).
 #include <cfloat>
+#include <climits>
 #include <cstdint>
 
 #include "pv3d_dev.cuh"
@@ -1119,10 +1120,19 @@ __device__ __forceinline__ void warp_excl_scan_k(int* a, int n)
 struct TriSetup {
     float A[3], Bc[3], C[3];
     float e0, e1, e2;
-    short x0, y0, bw, list;  // list = 1: visit entries [q_beg, q_beg + work) of the marked list
+    short x0, y0, bw, list;  // list = 0: the box; 1: entries [q_beg, q_beg + work) of the marked list;
+                             // 2: every texel of the sub-blocks in smask (within the box)
+    short bh, pad;
     int q_beg, work;
     uint2 smask;
 };
+
+// Position of the (k+1)-th set bit of a 64-bit mask (k < popcount).
+__device__ __forceinline__ int nth_bit64(uint2 m, int k)
+{
+    const int pl = __popc(m.x);
+    return k < pl ? (int)__fns(m.x, 0u, k + 1) : 32 + (int)__fns(m.y, 0u, k - pl + 1);
+}
 
 // A triangle set up for the sample-driven test (48 bytes, three 16-byte loads):
 // edge functions k = 0..2 in tile-local texel coordinates and depths scaled by
@@ -1905,14 +1915,19 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
                     for (int k = 0; k < 3; ++k) { S.A[k] = ed.A[k]; S.Bc[k] = ed.Bc[k]; S.C[k] = ed.C[k]; }
                     S.e0 = T.d[0] * inv_a; S.e1 = T.d[1] * inv_a; S.e2 = T.d[2] * inv_a;
                     S.smask = make_uint2((uint32_t)sb, (uint32_t)(sb >> 32));
-                    S.x0 = (short)x0; S.y0 = (short)y0; S.bw = (short)(x1 - x0 + 1);
+                    S.x0 = (short)x0; S.y0 = (short)y0; S.bw = (short)(x1 - x0 + 1); S.bh = (short)(y1 - y0 + 1);
+                    // visit the fewest texels: the box, the marked texels of its
+                    // rows (sparse tiles), or the whole sub-blocks it may shade in
                     const int n_px = (x1 - x0 + 1) * (y1 - y0 + 1);
+                    const int n_sb = (__popc(S.smask.x) + __popc(S.smask.y)) << (2 * SWS);
                     const int q_beg = dense ? 0 : (int)sm.row_start[y0];
-                    const int q_end = dense ? 0 : (int)sm.row_start[y1 + 1];
-                    if (dense || n_px <= q_end - q_beg) {
+                    const int n_list = dense ? INT_MAX : (int)sm.row_start[y1 + 1] - q_beg;
+                    if (n_sb < n_px && n_sb < n_list) {
+                        S.list = 2; S.q_beg = 0; S.work = n_sb;
+                    } else if (n_px <= n_list) {
                         S.list = 0; S.q_beg = 0; S.work = n_px;
                     } else {
-                        S.list = 1; S.q_beg = q_beg; S.work = q_end - q_beg;
+                        S.list = 1; S.q_beg = q_beg; S.work = n_list;
                     }
                 }
             }
@@ -1944,25 +1959,34 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
             const float C0 = S.C[0], C1 = S.C[1], C2 = S.C[2];
             const float e0 = S.e0, e1 = S.e1, e2 = S.e2;
             const uint2 smask = S.smask;
-            const int x0 = S.x0, y0 = S.y0, bw = S.bw, is_list = S.list, q_beg = S.q_beg, work = S.work;
+            const int x0 = S.x0, y0 = S.y0, bw = S.bw, bh = S.bh, is_list = S.list, q_beg = S.q_beg, work = S.work;
             const float inv_bw = 1.f / (float)bw;
             for (; ch < t_end; ++ch) {
                 const int q = ((ch - sm.chunk_pref[t]) << 5) + lane;
                 if (q >= work) continue;
                 int ix, iy;
-                if (is_list) {
-                    const int p = sm.u.r.list[q_beg + q];
-                    ix = p & (TS - 1);
-                    iy = p >> SH;
-                    if (ix < x0 || ix >= x0 + bw) continue;
-                } else {
-                    const int ry = fdiv(q, bw, inv_bw);
-                    iy = y0 + ry;
-                    ix = x0 + q - ry * bw;
+                if (is_list == 2) {
+                    const int sb = nth_bit64(smask, q >> (2 * SWS));
+                    const int r = q & ((1 << (2 * SWS)) - 1);
+                    ix = ((sb & 7) << SWS) + (r & ((1 << SWS) - 1));
+                    iy = ((sb >> 3) << SWS) + (r >> SWS);
+                    if ((unsigned)(ix - x0) >= (unsigned)bw || (unsigned)(iy - y0) >= (unsigned)bh) continue;
                     if (!dense && !(sm.mask[iy * WPR + (ix >> 5)] & (1u << (ix & 31)))) continue;
+                } else {
+                    if (is_list) {
+                        const int p = sm.u.r.list[q_beg + q];
+                        ix = p & (TS - 1);
+                        iy = p >> SH;
+                        if (ix < x0 || ix >= x0 + bw) continue;
+                    } else {
+                        const int ry = fdiv(q, bw, inv_bw);
+                        iy = y0 + ry;
+                        ix = x0 + q - ry * bw;
+                        if (!dense && !(sm.mask[iy * WPR + (ix >> 5)] & (1u << (ix & 31)))) continue;
+                    }
+                    const int sb = ((iy >> SWS) << 3) | (ix >> SWS);
+                    if (!(((sb < 32 ? smask.x : smask.y) >> (sb & 31)) & 1u)) continue;
                 }
-                const int sb = ((iy >> SWS) << 3) | (ix >> SWS);
-                if (!(((sb < 32 ? smask.x : smask.y) >> (sb & 31)) & 1u)) continue;
                 const float px = (float)ix + 0.5f, py = (float)iy + 0.5f;
                 const float w0 = edge_at(A0, B0, C0, px, py);
                 const float w1 = edge_at(A1, B1, C1, px, py);

@@ -420,7 +420,9 @@ int pv3d_evaluate(pv3d_ctx* ctx, uint32_t gen_id, const pv3d_eval_opts* opts, pv
  * pv3d_evaluate of the same request.  PV3D_E_ADMISSION if the request alone
  * exceeds the budget.  The scene, generator and `out` must stay valid until
  * the request completes; pv3d_release refuses ids that queued or active
- * requests use.  Served requests use the fused path.
+ * requests use.  Served requests use the fused path; they take every output
+ * and option of pv3d_evaluate (series-string and array outputs, the diffuse
+ * term) except sky-map outputs and window groups (PV3D_E_INVALID).
  */
 int pv3d_submit(pv3d_ctx* ctx, uint32_t gen_id, const pv3d_eval_opts* opts, pv3d_result* out,
                 uint64_t* req);

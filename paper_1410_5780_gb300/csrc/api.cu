@@ -1696,7 +1696,7 @@ struct pv3d_ctx::Request {
     EvalSetup es{};
     int status = PV3D_E_PENDING;
     int64_t next = 0;          // next sun step to evaluate
-    DevBuf kmod, kcell, stage; // Kahan pairs and the staging of host outputs
+    DevBuf kmod, kcell, kstr, karr, stage; // Kahan pairs and the staging of host outputs
     double* d_e = nullptr;
     double* d_eu = nullptr;
     double* d_cl = nullptr;
@@ -1704,6 +1704,8 @@ struct pv3d_ctx::Request {
     float* d_pu = nullptr;
     uint8_t* d_cnt = nullptr;
     unsigned long long* d_bits = nullptr;
+    double *d_se = nullptr, *d_seu = nullptr, *d_ae = nullptr, *d_aeu = nullptr;  // string and array energies
+    float *d_sp = nullptr, *d_spu = nullptr, *d_ap = nullptr, *d_apu = nullptr;   // string and array powers
     int64_t footprint = 0;
     int64_t waves = 0;
     float device_ms = 0.f;
@@ -1728,7 +1730,18 @@ static int64_t request_bytes(const GenH& g, const EvalSetup& es, const pv3d_resu
         if (out->power_unshaded) b += S * g.M * 4;
         if (out->cell_counts) b += S * g.C;
         if (out->sample_bits) b += S * g.C * 8;
+        const int64_t NS = (int64_t)g.str_ids.size(), NA = (int64_t)g.arr_ids.size();
+        if (out->string_energy) b += NS * 8;
+        if (out->string_energy_unshaded) b += NS * 8;
+        if (out->string_power) b += S * NS * 4;
+        if (out->string_power_unshaded) b += S * NS * 4;
+        if (out->array_energy) b += NA * 8;
+        if (out->array_energy_unshaded) b += NA * 8;
+        if (out->array_power) b += S * NA * 4;
+        if (out->array_power_unshaded) b += S * NA * 4;
     }
+    if (es.strings) b += (int64_t)g.str_ids.size() * 16;
+    if (es.arrays) b += (int64_t)g.arr_ids.size() * 16;
     return b;
 }
 
@@ -1775,14 +1788,21 @@ static int admit(pv3d_ctx* c, pv3d_ctx::Request& r)
     const GenH& g = c->gens.at(r.gen_id);
     const int64_t S = r.es.e - r.es.b;
     int rc;
+    const size_t NS = g.str_ids.size(), NA = g.arr_ids.size();
     if ((rc = take_buf(c, r.kmod, (size_t)g.M * 2 * sizeof(float2))) ||
-        (rc = take_buf(c, r.kcell, (size_t)g.C * sizeof(float2))))
+        (rc = take_buf(c, r.kcell, (size_t)g.C * sizeof(float2))) ||
+        (r.es.strings && (rc = take_buf(c, r.kstr, NS * 2 * sizeof(float2)))) ||
+        (r.es.arrays && (rc = take_buf(c, r.karr, NA * 2 * sizeof(float2)))))
         return rc;
     pv3d_result* out = r.out;
     if (out->is_device) {
         r.d_e = out->energy; r.d_eu = out->energy_unshaded; r.d_cl = out->cell_beam_loss;
         r.d_p = out->power; r.d_pu = out->power_unshaded; r.d_cnt = out->cell_counts;
         r.d_bits = (unsigned long long*)out->sample_bits;
+        r.d_se = out->string_energy; r.d_seu = out->string_energy_unshaded;
+        r.d_sp = out->string_power; r.d_spu = out->string_power_unshaded;
+        r.d_ae = out->array_energy; r.d_aeu = out->array_energy_unshaded;
+        r.d_ap = out->array_power; r.d_apu = out->array_power_unshaded;
     } else {
         size_t off = 0;
         auto take = [&](size_t bytes) { size_t o = off; off += (bytes + 255) & ~size_t(255); return o; };
@@ -1790,6 +1810,12 @@ static int admit(pv3d_ctx* c, pv3d_ctx::Request& r)
         size_t ocl = out->cell_beam_loss ? take((size_t)g.C * 8) : 0;
         size_t op = out->power ? take((size_t)S * g.M * 4) : 0, opu = out->power_unshaded ? take((size_t)S * g.M * 4) : 0;
         size_t oc = out->cell_counts ? take((size_t)S * g.C) : 0, ob = out->sample_bits ? take((size_t)S * g.C * 8) : 0;
+        size_t ose = out->string_energy ? take(NS * 8) : 0, oseu = out->string_energy_unshaded ? take(NS * 8) : 0;
+        size_t osp = out->string_power ? take((size_t)S * NS * 4) : 0;
+        size_t ospu = out->string_power_unshaded ? take((size_t)S * NS * 4) : 0;
+        size_t oae = out->array_energy ? take(NA * 8) : 0, oaeu = out->array_energy_unshaded ? take(NA * 8) : 0;
+        size_t oap = out->array_power ? take((size_t)S * NA * 4) : 0;
+        size_t oapu = out->array_power_unshaded ? take((size_t)S * NA * 4) : 0;
         if ((rc = take_buf(c, r.stage, off))) return rc;
         char* b = (char*)r.stage.p;
         r.d_e = out->energy ? (double*)(b + oe) : nullptr;
@@ -1799,9 +1825,19 @@ static int admit(pv3d_ctx* c, pv3d_ctx::Request& r)
         r.d_pu = out->power_unshaded ? (float*)(b + opu) : nullptr;
         r.d_cnt = out->cell_counts ? (uint8_t*)(b + oc) : nullptr;
         r.d_bits = out->sample_bits ? (unsigned long long*)(b + ob) : nullptr;
+        r.d_se = out->string_energy ? (double*)(b + ose) : nullptr;
+        r.d_seu = out->string_energy_unshaded ? (double*)(b + oseu) : nullptr;
+        r.d_sp = out->string_power ? (float*)(b + osp) : nullptr;
+        r.d_spu = out->string_power_unshaded ? (float*)(b + ospu) : nullptr;
+        r.d_ae = out->array_energy ? (double*)(b + oae) : nullptr;
+        r.d_aeu = out->array_energy_unshaded ? (double*)(b + oaeu) : nullptr;
+        r.d_ap = out->array_power ? (float*)(b + oap) : nullptr;
+        r.d_apu = out->array_power_unshaded ? (float*)(b + oapu) : nullptr;
     }
     CUDA_TRY(c, cudaMemsetAsync(r.kmod.p, 0, (size_t)g.M * 2 * sizeof(float2), c->serve_stream));
     CUDA_TRY(c, cudaMemsetAsync(r.kcell.p, 0, (size_t)g.C * sizeof(float2), c->serve_stream));
+    if (r.es.strings) CUDA_TRY(c, cudaMemsetAsync(r.kstr.p, 0, NS * 2 * sizeof(float2), c->serve_stream));
+    if (r.es.arrays) CUDA_TRY(c, cudaMemsetAsync(r.karr.p, 0, NA * 2 * sizeof(float2), c->serve_stream));
     r.next = r.es.b;
     r.admitted = true;
     return PV3D_OK;
@@ -1816,6 +1852,11 @@ static int finish(pv3d_ctx* c, pv3d_ctx::Request& r)
     CUDA_TRY(c, launch_finalize_pairs((const float2*)r.kmod.p, g.M, (const float2*)r.kcell.p, r.d_cl ? g.C : 0, r.d_e,
                                       r.d_eu,
                                       r.d_cl, st));
+    const int NS = (int)g.str_ids.size(), NA = (int)g.arr_ids.size();
+    if (r.es.strings)
+        CUDA_TRY(c, launch_finalize_pairs((const float2*)r.kstr.p, NS, nullptr, 0, r.d_se, r.d_seu, nullptr, st));
+    if (r.es.arrays)
+        CUDA_TRY(c, launch_finalize_pairs((const float2*)r.karr.p, NA, nullptr, 0, r.d_ae, r.d_aeu, nullptr, st));
     pv3d_result* out = r.out;
     if (!out->is_device) {
         auto cp = [&](void* dst, const void* src, size_t bytes) {
@@ -1828,6 +1869,14 @@ static int finish(pv3d_ctx* c, pv3d_ctx::Request& r)
         CUDA_TRY(c, cp(out->power_unshaded, r.d_pu, (size_t)S * g.M * 4));
         CUDA_TRY(c, cp(out->cell_counts, r.d_cnt, (size_t)S * g.C));
         CUDA_TRY(c, cp(out->sample_bits, r.d_bits, (size_t)S * g.C * 8));
+        CUDA_TRY(c, cp(out->string_energy, r.d_se, (size_t)NS * 8));
+        CUDA_TRY(c, cp(out->string_energy_unshaded, r.d_seu, (size_t)NS * 8));
+        CUDA_TRY(c, cp(out->string_power, r.d_sp, (size_t)S * NS * 4));
+        CUDA_TRY(c, cp(out->string_power_unshaded, r.d_spu, (size_t)S * NS * 4));
+        CUDA_TRY(c, cp(out->array_energy, r.d_ae, (size_t)NA * 8));
+        CUDA_TRY(c, cp(out->array_energy_unshaded, r.d_aeu, (size_t)NA * 8));
+        CUDA_TRY(c, cp(out->array_power, r.d_ap, (size_t)S * NA * 4));
+        CUDA_TRY(c, cp(out->array_power_unshaded, r.d_apu, (size_t)S * NA * 4));
     }
     CUDA_TRY(c, cudaStreamSynchronize(st));
     int64_t lit = 0;
@@ -1836,7 +1885,7 @@ static int finish(pv3d_ctx* c, pv3d_ctx::Request& r)
     out->tests = lit * (int64_t)g.C * r.es.n * r.es.n;
     out->device_ms = r.device_ms;
     out->waves = (int32_t)r.waves;
-    out->kernel_launches = r.waves * kLaunchesPerWave + 1;
+    out->kernel_launches = r.waves * kLaunchesPerWave + 1 + (r.es.strings ? 1 : 0) + (r.es.arrays ? 1 : 0);
     r.t_done = std::chrono::steady_clock::now();
     out->latency_ms = (float)std::chrono::duration<double, std::milli>(r.t_done - r.t_submit).count();
     return PV3D_OK;
@@ -1846,6 +1895,8 @@ static void release_request_bufs(pv3d_ctx* c, pv3d_ctx::Request& r)
 {
     give_buf(c, r.kmod);
     give_buf(c, r.kcell);
+    give_buf(c, r.kstr);
+    give_buf(c, r.karr);
     give_buf(c, r.stage);
 }
 
@@ -1879,6 +1930,7 @@ static int serve_wave(pv3d_ctx* c, std::unique_lock<std::mutex>& lk)
     std::vector<int> ks;
     int64_t scratch = 0;
     bool want_bits = false;
+    int extras = 0;  // string (1) and array (4) kernels in the wave
     const size_t na = c->active.size();
     for (size_t q = 0; q < na; ++q) {
         pv3d_ctx::Request& r = *c->reqs.at(c->active[(c->rr + q) % na]);
@@ -1891,11 +1943,12 @@ static int serve_wave(pv3d_ctx* c, std::unique_lock<std::mutex>& lk)
         if (!jobs.empty() && scratch + need > scratch_cap) break;
         scratch += need;
         jobs.push_back(make_job(c, g, sc, r.es, r.next, k, (float2*)r.kmod.p, r.d_cl ? (float2*)r.kcell.p : nullptr,
-                                r.d_p, r.d_pu,
-                                r.d_cnt, r.d_bits));
+                                r.d_p, r.d_pu, r.d_cnt, r.d_bits, (float2*)r.kstr.p, r.d_sp, r.d_spu, nullptr, nullptr,
+                                nullptr, 0, 0, (float2*)r.karr.p, r.d_ap, r.d_apu));
         in_wave.push_back(&r);
         ks.push_back(k);
         want_bits = want_bits || r.d_bits;
+        extras |= (r.es.strings ? 1 : 0) | (r.es.arrays ? 4 : 0);
     }
     c->rr = (c->rr + jobs.size()) % std::max<size_t>(na, 1);
     lk.unlock();
@@ -1909,7 +1962,8 @@ static int serve_wave(pv3d_ctx* c, std::unique_lock<std::mutex>& lk)
         std::lock_guard<std::mutex> g(c->gpu_mu);
         cudaSetDevice(c->device);
         cudaStream_t st = c->serve_stream;
-        rc = ensure_workspace(c, W.tot_js, W.tot_te, W.tot_ms, W.tot_cs, c->opts.tile, true, want_bits);
+        rc = ensure_workspace(c, W.tot_js, W.tot_te, W.tot_ms, W.tot_cs, c->opts.tile, true, want_bits, W.tot_ss,
+                              W.tot_sq, W.tot_sa);
         if (!rc) {
             W.bin_cap = c->bin_cap; W.map_cap_tiles = c->map_cap_tiles;
             W.big_cap = c->big_cap; W.recv_cap = c->recv_cap;
@@ -1917,7 +1971,7 @@ static int serve_wave(pv3d_ctx* c, std::unique_lock<std::mutex>& lk)
         }
         if (!rc && cudaMemsetAsync(c->ctr.p, 0, sizeof(Counters), st) != cudaSuccess) rc = PV3D_E_DEVICE;
         if (!rc && cudaEventRecord(c->ev0, st) != cudaSuccess) rc = PV3D_E_DEVICE;
-        if (!rc) rc = run_waves(c, waves, st, c->opts.tile, true, false, false);
+        if (!rc) rc = run_waves(c, waves, st, c->opts.tile, true, false, false, extras);
         if (!rc && cudaEventRecord(c->ev1, st) != cudaSuccess) rc = PV3D_E_DEVICE;
         if (!rc && cudaMemcpyAsync(&hc, c->ctr.p, sizeof(Counters), cudaMemcpyDeviceToHost, st) != cudaSuccess)
             rc = PV3D_E_DEVICE;
@@ -1932,6 +1986,8 @@ static int serve_wave(pv3d_ctx* c, std::unique_lock<std::mutex>& lk)
                 const GenH& g = c->gens.at(r->gen_id);
                 cudaMemsetAsync(r->kmod.p, 0, (size_t)g.M * 2 * sizeof(float2), st);
                 cudaMemsetAsync(r->kcell.p, 0, (size_t)g.C * sizeof(float2), st);
+                if (r->kstr.p) cudaMemsetAsync(r->kstr.p, 0, g.str_ids.size() * 2 * sizeof(float2), st);
+                if (r->karr.p) cudaMemsetAsync(r->karr.p, 0, g.arr_ids.size() * 2 * sizeof(float2), st);
             }
             cudaStreamSynchronize(st);
         }
@@ -1995,8 +2051,7 @@ extern "C" int pv3d_submit(pv3d_ctx* c, uint32_t gen_id, const pv3d_eval_opts* o
     int rc = check_eval(c, g, o, out, r->es);
     if (rc) return rc;
     if (o && o->path == PV3D_PATH_MAP) return fail(c, PV3D_E_INVALID, "served requests use the fused path");
-    if (r->es.strings || r->es.heat || r->es.arrays)
-        return fail(c, PV3D_E_INVALID, "string and sky-map outputs are produced by pv3d_evaluate only");
+    if (r->es.heat) return fail(c, PV3D_E_INVALID, "sky-map outputs are produced by pv3d_evaluate only");
     if (r->es.groups) return fail(c, PV3D_E_INVALID, "window groups are evaluated by pv3d_evaluate only");
     r->gen_id = gen_id;
     r->opts = o ? *o : pv3d_eval_opts{};

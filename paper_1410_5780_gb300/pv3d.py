@@ -407,11 +407,14 @@ class Context:
 
     def submit(self, gen_id: int, n: int = 3, map_res: int = 0, step_begin: int = 0, step_end: int = 0,
                chunk_steps: int = 0, outputs=("energy", "energy_unshaded"), device: bool = True,
-               stream=None):
+               stream=None, diffuse_shading: bool = False):
         """pv3d_submit.  Returns (request id, outputs dict); the outputs are
-        valid once pv3d_poll returns PV3D_OK for the request."""
+        valid once pv3d_poll returns PV3D_OK for the request (string and array
+        outputs included; sky-map outputs and window groups are pv3d_evaluate's
+        only)."""
         res, arrays = self._alloc(gen_id, step_begin, step_end, outputs, device)
-        o = self._opts(n, map_res, step_begin, step_end, chunk_steps, None, 0.0, 0.0, 0.0)
+        o = self._opts(n, map_res, step_begin, step_end, chunk_steps, None, 0.0, 0.0, 0.0,
+                       diffuse=diffuse_shading)
         rid = C.c_uint64()
         self._check(self.lib.pv3d_submit(self.h, gen_id, C.byref(o), C.byref(res), C.byref(rid)))
         self._keep[rid.value] = (res, o, arrays)

@@ -128,3 +128,39 @@ def test_evaluate_batch_equals_alone():
             b = _np(b)
             for k in ("energy", "energy_unshaded", "cell_counts"):
                 np.testing.assert_array_equal(a[k], b[k])
+
+
+def test_served_strings_arrays_and_diffuse_equal_alone():
+    """Served requests with series-string and parallel-array outputs and the
+    diffuse term shaded, mixed with a plain request, equal the same
+    evaluations run alone bit for bit (their string and array Kahan sums run
+    in step order in the request's own accumulators), with device and with
+    host outputs."""
+    import torch
+    w = S.make_facade(seed=25, n=3, map_res=1024, n_buildings=10, n_trees=5, n_poles=3, floors=2, per_floor=6,
+                      target_tris=3000, days=np.array([30, 120, 250]), radius=70.0)
+    w.gen.string = (np.arange(w.gen.n_modules) // 3).astype(np.int32)
+    w.gen.array = (np.arange(w.gen.n_modules) // 6).astype(np.int32)
+    other = S.make_random_small(203, n_mods=5, n_steps=30, n=3, map_res=512)
+    outs = ("energy", "energy_unshaded", "power", "string_energy", "string_energy_unshaded", "string_power",
+            "array_energy", "array_energy_unshaded", "array_power")
+    with pv3d.Context(device=0, chunk_steps=16) as ctx:
+        gid = pv3d.load_workload(ctx, w)
+        ctx.sky_view(gid, rings=4, sectors=12, n=2, map_res=512)
+        g2 = pv3d.load_workload(ctx, other)
+        for device in (True, False):
+            alone = _np(ctx.evaluate(gid, n=w.n, map_res=w.map_res, outputs=outs, device=device,
+                                     diffuse_shading=True))
+            torch.cuda.synchronize()
+            r_other = ctx.submit(g2, n=other.n, map_res=other.map_res)
+            rid, arrays = ctx.submit(gid, n=w.n, map_res=w.map_res, outputs=outs, device=device,
+                                     diffuse_shading=True)
+            assert ctx.poll(r_other[0], timeout_ms=-1) == pv3d.PV3D_OK
+            assert ctx.poll(rid, timeout_ms=-1) == pv3d.PV3D_OK
+            torch.cuda.synchronize()
+            b = _np(arrays)
+            assert b["string_energy"].shape == (len(ctx.string_ids(gid)),)
+            assert b["array_energy"].shape == (len(ctx.array_ids(gid)),)
+            for k in outs:
+                np.testing.assert_array_equal(alone[k], b[k], err_msg=f"device={device}:{k}")
+            assert b["string_energy"].sum() > 0 and b["array_energy"].sum() > 0

@@ -92,8 +92,11 @@ def test_string_outputs_on_map_path_and_host(ctx):
     for k in ("string_power", "string_energy", "string_energy_unshaded"):
         np.testing.assert_array_equal(a[k], b[k], err_msg=k)
         np.testing.assert_array_equal(a[k], h[k], err_msg=k)
-    with pytest.raises(pv3d.PV3DError):  # served requests do not produce string outputs
-        ctx.submit(gid, n=w.n, map_res=w.map_res, outputs=("string_energy",))
+    # served requests produce them too, bit-identical to the evaluation alone
+    rid, arr = ctx.submit(gid, n=w.n, map_res=w.map_res, outputs=("string_energy", "string_power"))
+    assert ctx.poll(rid, timeout_ms=-1) == pv3d.PV3D_OK
+    np.testing.assert_array_equal(arr["string_energy"].cpu().numpy(), a["string_energy"])
+    np.testing.assert_array_equal(arr["string_power"].cpu().numpy(), a["string_power"])
     ctx.release(gid)
 
 

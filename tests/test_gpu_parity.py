@@ -381,3 +381,43 @@ def test_bin_pool_overflow_regrows(make):
     st = compare(w, a, o, np.arange(w.sun.n_steps))
     assert st["agree"] >= FLAG_AGREEMENT, st
     energy_checks(w, a, o, np.arange(w.sun.n_steps))
+
+
+def test_maximum_sizes(ctx):
+    """The largest sizes the boundary takes: 15 x 15 samples per cell (a cell's
+    count reaches 225, the most its one-byte tally holds), a module of 32 x 32
+    = 1024 cells (the per-module maximum) with 64 bypass substrings (the
+    maximum: each cell column split in two halves), and the largest light window side,
+    16384 -- against the oracle's counts cell by cell, and fully shaded cells
+    reaching 225."""
+    n, cu, cv = 15, 32, 32
+    p = 0.05
+    mb = S.MeshBuilder()
+    mb.box((-0.4, -0.4, 0.0), (1.2, 0.2, 2.0))   # a block over part of the module
+    scene = mb.build()
+    # substring 2 c + h: cell column c, lower (h = 0) or upper (h = 1) half
+    lay = S.Layout(cu, cv, 64, (2 * np.tile(np.arange(cu), cv) + (np.repeat(np.arange(cv), cu) >= cv // 2))
+                   .astype(np.int32))
+    gen = S._gen_from_lists([(0.0, 0.0, 0.05)], [(1.0, 0.0, 0.0)], [(0.0, 1.0, 0.0)], cu, cv, [0], [-1], [0], [lay],
+                            np.zeros((0, 3)))
+    gen.pitch = np.full(1, p, np.float32)
+    xyz = S.sun_vectors(40.0, np.array([172, 172, 355]), np.array([10.0, 14.0, 12.0]))
+    dni = S.clear_sky_dni(xyz[:, 2]).astype(np.float32)
+    sun = S.Sun(xyz=xyz, dni=dni, dhi=(0.1 * dni).astype(np.float32), dt_h=np.ones(3, np.float32))
+    w = S.Workload("max", scene, gen, sun, None, n, 16384)
+    gid = pv3d.load_workload(ctx, w)
+    g = run_gpu(ctx, gid, w, outputs=("cell_counts", "power", "energy", "energy_unshaded"))
+    ctx.release(gid)
+    o = oracle.evaluate_workload(w)
+    gc = g["cell_counts"].astype(np.int64)
+    oc = o["counts"].astype(np.int64)
+    assert oc.max() == n * n and gc.max() == n * n   # fully shaded cells hold 225
+    # a texel of 1.6 m / 16382 = 0.1 mm: counts agree except within a few
+    # samples of the block's shadow edge
+    diff = np.abs(gc - oc)
+    assert (diff == 0).mean() >= 0.99, (diff > 0).mean()
+    assert diff.max() <= n, diff.max()
+    assert oc.sum() > 0 and abs(int(gc.sum()) - int(oc.sum())) <= 0.001 * oc.sum() + n
+    # the PV model over 64 substrings on the GPU's own counts
+    pc = oracle.power_from_counts(w, np.arange(3), [0], gc.astype(np.int32))
+    assert np.all(np.abs(g["power"].astype(np.float64) - pc) <= 1e-4 * np.maximum(pc, 1.0) + 1e-3), (g["power"], pc)

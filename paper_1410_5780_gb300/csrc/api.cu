@@ -306,35 +306,45 @@ extern "C" int pv3d_scene_load(pv3d_ctx* c, const float* xyz, int64_t n_verts, c
         for (int a = 0; a < 3; ++a) lo[a] = hi[a] = 0.f;
     memcpy(s.lo, lo, sizeof(lo));
     memcpy(s.hi, hi, sizeof(hi));
-    // triangles in Morton order of their centroids, grouped 32 at a time into
-    // meshlets with world bounding boxes (the binning culls whole meshlets)
+    // triangles grouped 32 at a time into meshlets with world bounding boxes
+    // (the binning culls whole meshlets): the triangle set is split at the
+    // median centroid of its longest centroid extent, at a multiple of 32
+    // triangles, until each part is one meshlet, so a meshlet is a compact
+    // patch and its box stays tight
     {
-        std::vector<std::pair<uint32_t, int64_t>> key((size_t)n_tris);
-        auto spread = [](uint32_t x) {
-            x &= 0x3FF;
-            x = (x | (x << 16)) & 0x030000FF;
-            x = (x | (x << 8)) & 0x0300F00F;
-            x = (x | (x << 4)) & 0x030C30C3;
-            x = (x | (x << 2)) & 0x09249249;
-            return x;
-        };
+        std::vector<float> cen((size_t)n_tris * 3);
         for (int64_t t = 0; t < n_tris; ++t) {
-            uint32_t q[3];
-            for (int a = 0; a < 3; ++a) {
-                const float cen = (tv[3 * t].x * (a == 0) + tv[3 * t].y * (a == 1) + tv[3 * t].z * (a == 2) +
-                                   tv[3 * t + 1].x * (a == 0) + tv[3 * t + 1].y * (a == 1) + tv[3 * t + 1].z * (a == 2) +
-                                   tv[3 * t + 2].x * (a == 0) + tv[3 * t + 2].y * (a == 1) + tv[3 * t + 2].z * (a == 2)) /
-                                  3.f;
-                const float ext = hi[a] - lo[a];
-                const float f = ext > 0 ? (cen - lo[a]) / ext : 0.f;
-                q[a] = (uint32_t)std::min(1023.f, std::max(0.f, f * 1023.f));
-            }
-            key[t] = {spread(q[0]) | (spread(q[1]) << 1) | (spread(q[2]) << 2), t};
+            const float4 a = tv[3 * t], b = tv[3 * t + 1], d = tv[3 * t + 2];
+            cen[3 * t] = (a.x + b.x + d.x) / 3.f;
+            cen[3 * t + 1] = (a.y + b.y + d.y) / 3.f;
+            cen[3 * t + 2] = (a.z + b.z + d.z) / 3.f;
         }
-        std::sort(key.begin(), key.end());
+        std::vector<int64_t> order((size_t)n_tris);
+        for (int64_t t = 0; t < n_tris; ++t) order[t] = t;
+        std::vector<std::pair<int64_t, int64_t>> todo;
+        if (n_tris > 32) todo.push_back({0, n_tris});
+        while (!todo.empty()) {
+            const auto [b, e] = todo.back();
+            todo.pop_back();
+            float clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
+            for (int64_t i = b; i < e; ++i)
+                for (int a = 0; a < 3; ++a) {
+                    clo[a] = std::min(clo[a], cen[3 * order[i] + a]);
+                    chi[a] = std::max(chi[a], cen[3 * order[i] + a]);
+                }
+            int ax = 0;
+            for (int a = 1; a < 3; ++a)
+                if (chi[a] - clo[a] > chi[ax] - clo[ax]) ax = a;
+            // b is a multiple of 32, so every part starts on a meshlet
+            const int64_t mid = b + ((e - b + 31) / 32 / 2) * 32;
+            std::nth_element(order.begin() + b, order.begin() + mid, order.begin() + e,
+                             [&](int64_t x, int64_t y) { return cen[3 * x + ax] < cen[3 * y + ax]; });
+            if (mid - b > 32) todo.push_back({b, mid});
+            if (e - mid > 32) todo.push_back({mid, e});
+        }
         std::vector<float4> sorted(tv.size());
         for (int64_t t = 0; t < n_tris; ++t)
-            for (int k = 0; k < 3; ++k) sorted[3 * t + k] = tv[3 * key[t].second + k];
+            for (int k = 0; k < 3; ++k) sorted[3 * t + k] = tv[3 * order[t] + k];
         tv.swap(sorted);
         s.n_ml = (int32_t)((n_tris + 31) / 32);
         std::vector<float4> boxes((size_t)s.n_ml * 2);

@@ -64,7 +64,7 @@ struct JobDev {
     const float4* tri;
     int32_t n_tris;
     int32_t n_mtris;  // module triangles rasterised: 2 per module, or 0 for a coplanar generator
-    const float4* ml_box;  // scene meshlets (32 consecutive triangles, Morton order): world lo, hi
+    const float4* ml_box;  // scene meshlets (32 consecutive triangles, median-split order): world lo, hi
     int32_t n_ml;          // scene meshlets = ceil(n_tris / 32)
     int32_t pad_ml;
     // generator

@@ -1114,25 +1114,18 @@ __device__ __forceinline__ void warp_excl_scan_k(int* a, int n)
     if (lane == 31) a[n] = inc;
 }
 
-// A triangle set up for one tile: edge functions, scaled depths, the texels
-// it visits (its bounding box, or a range of the marked-texel list) and the
-// sub-blocks in which it may shade a sample (tri_sub_mask).
+// A triangle set up for one tile: edge functions, scaled depths, its texel
+// box and the sub-blocks in which it may shade a sample (tri_sub_mask).  The
+// rasteriser visits rows y0 .. y0 + rows - 1 of the box, one row per lane.
+// 17 words: lanes reading different triangles' fields hit different banks.
 struct TriSetup {
     float A[3], Bc[3], C[3];
     float e0, e1, e2;
-    short x0, y0, bw, list;  // list = 0: the box; 1: entries [q_beg, q_beg + work) of the marked list;
-                             // 2: every texel of the sub-blocks in smask (within the box)
-    short bh, pad;
-    int q_beg, work;
-    uint2 smask;
+    short x0, bw;
+    int y0, rows;        // rows = 0: not kept
+    uint32_t sm_lo, sm_hi;  // sub-block bits 0-31, 32-63
 };
-
-// Position of the (k+1)-th set bit of a 64-bit mask (k < popcount).
-__device__ __forceinline__ int nth_bit64(uint2 m, int k)
-{
-    const int pl = __popc(m.x);
-    return k < pl ? (int)__fns(m.x, 0u, k + 1) : 32 + (int)__fns(m.y, 0u, k - pl + 1);
-}
+static_assert(sizeof(TriSetup) == 17 * 4, "odd word stride");
 
 // A triangle set up for the sample-driven test (48 bytes, three 16-byte loads):
 // edge functions k = 0..2 in tile-local texel coordinates and depths scaled by
@@ -1187,7 +1180,6 @@ struct HeavyCfg {
 template <int TS>
 struct RasterSm {
     uint32_t tile[TS * TS];  // depth keys of the tile
-    uint16_t list[TS * TS];  // marked texels, row-major
 };
 
 // Kept triangles of a tile for the sample-driven test, up to NT of them.
@@ -1220,14 +1212,14 @@ struct TileSm {
     float dlim[SubGrid<TS>::blocks]; // per sub-block depth limit (sub_limits)
     SubInfo si;                      // their summary (sub_summary)
     uint32_t mask[TS * TS / 32];     // texels read by some sample (sparse tiles)
-    uint32_t row_start[TS + 1];      // start of each row in `list`
+    int n_need;                      // how many (sparse tiles)
     RecvSm recv[kRecvChunk];
     int n_recv;                      // receivers staged
     int total_items;                 // (sample row, cell column) items over the staged receivers
     int any_write;                   // some texel of the tile received a depth
     int n_tri;                       // triangles kept by the sample-driven set-up
     TriSetup tri[kTriBatchMax];      // a batch of set-up triangles, one per thread
-    int chunk_pref[kTriBatchMax + 1];  // prefix of their 32-texel work chunks
+    int row_pref[kTriBatchMax + 1];  // prefix of their rows
 };
 
 // Stage receiver module m of tile (tx, ty): sample-index box (the tile
@@ -1774,17 +1766,61 @@ __device__ __forceinline__ void test_items(const RecvSm* recv, int n_recv, int t
 
 // ---- tile rasteriser ------------------------------------------------------
 
-// Rasterise the tile's triangles into sm.u.r.tile.  Sparse tiles (fewer samples
-// than two per texel) are rasterised only at the texels their samples read;
-// each triangle then visits its bounding box or the marked texels of its
-// rows, whichever is fewer.  A triangle is drawn only in the sub-blocks where
-// it may shade a sample (tri_sub_mask with the sub-block depth limits): the
-// stored nearest depth may then differ at a texel, but never the decision of
-// a sample there (the dropped triangles are behind every sample they cover,
-// and "shaded" is "some covering triangle is nearer than the sample less its
-// bias").  Receivers [r0, r0 + nrecv) must be staged (the first kRecvChunk of
-// them) on entry.  Returns 0 if no sample reads the tile or nothing was drawn
-// at a texel a sample reads.
+// Narrow the texel range [lo, hi] of a row to the texels whose centre px
+// has fma(A, px, t) >= 0 -- edge_at on that row, which is monotone in px,
+// so the texels form an interval: an estimate of its end from the edge's
+// root, corrected by evaluating the edge exactly as the per-texel test does
+// (at most the range's width of steps, one or two in practice).
+__device__ __forceinline__ void edge_span(float A, float t, int& lo, int& hi)
+{
+    if (lo > hi) return;
+    if (A > 0.f) {
+        const float f = ceilf(__fdividef(-t, A) - 0.5f);
+        int i = (int)fminf(fmaxf(f, (float)lo), (float)(hi + 1));
+        while (i > lo && __fmaf_rn(A, (float)(i - 1) + 0.5f, t) >= 0.f) --i;
+        while (i <= hi && __fmaf_rn(A, (float)i + 0.5f, t) < 0.f) ++i;
+        lo = i;
+    } else if (A < 0.f) {
+        const float f = floorf(__fdividef(-t, A) - 0.5f);
+        int i = (int)fminf(fmaxf(f, (float)(lo - 1)), (float)hi);
+        while (i < hi && __fmaf_rn(A, (float)(i + 1) + 0.5f, t) >= 0.f) ++i;
+        while (i >= lo && __fmaf_rn(A, (float)i + 0.5f, t) < 0.f) --i;
+        hi = i;
+    } else if (!(t >= 0.f)) {
+        hi = lo - 1;  // fma(0, px, t) = t for every texel of the row
+    }
+}
+
+// Bits of the texels lo .. hi (tile-local) that fall in word w of a row.
+__device__ __forceinline__ uint32_t span_word(int lo, int hi, int w)
+{
+    const int a = max(lo - 32 * w, 0), b = min(hi - 32 * w, 31);
+    return b < a ? 0u : (0xFFFFFFFFu >> (31 - b)) & (0xFFFFFFFFu << a);
+}
+
+// Texel bits of word w of a row from the row's byte of sub-block bits (bit
+// sx covers texels sx * TS / 8 .. sx * TS / 8 + TS / 8 - 1).
+template <int TS>
+__device__ __forceinline__ uint32_t sub_word(uint32_t sbyte, int w)
+{
+    if constexpr (TS == 32) {
+        uint32_t x = sbyte;  // bit i -> bit 4 i, then a nibble each
+        x = (x | (x << 12)) & 0x000F000Fu;
+        x = (x | (x << 6)) & 0x03030303u;
+        x = (x | (x << 3)) & 0x11111111u;
+        return x * 0xFu;
+    } else if constexpr (TS == 64) {
+        uint32_t x = (sbyte >> (4 * w)) & 0xFu;  // bit i -> bit 8 i, then a byte each
+        x = (x | (x << 14)) & 0x00030003u;
+        x = (x | (x << 7)) & 0x01010101u;
+        return x * 0xFFu;
+    } else {
+        uint32_t x = (sbyte >> (2 * w)) & 0x3u;  // bit i -> bit 16 i, then a half-word each
+        x = (x | (x << 15)) & 0x00010001u;
+        return x * 0xFFFFu;
+    }
+}
+
 // The tile's sub-block depth limits (sub_limits, or no limit when the
 // receivers are staged in chunks) and their summary, for the whole block.
 template <int TS>
@@ -1802,6 +1838,18 @@ __device__ __forceinline__ void tile_limits(TileSm<TS>& sm, const LightParams& l
     __syncthreads();
 }
 
+// Rasterise the tile's triangles into sm.u.r.tile.  Sparse tiles (fewer samples
+// than two per texel) are rasterised only at the texels their samples read.
+// A triangle is drawn only in the sub-blocks where it may shade a sample
+// (tri_sub_mask with the sub-block depth limits): the stored nearest depth
+// may then differ at a texel, but never the decision of a sample there (the
+// dropped triangles are behind every sample they cover, and "shaded" is
+// "some covering triangle is nearer than the sample less its bias").  Each
+// (triangle, row) goes to one lane, which visits only the texels of the row
+// inside all three edges (edge_span), of the triangle's sub-blocks and, in
+// sparse tiles, marked.  Receivers [r0, r0 + nrecv) must be staged (the
+// first kRecvChunk of them) on entry.  Returns 0 if no sample reads the tile
+// or nothing was drawn at a texel a sample reads.
 template <int TS, bool PROF>
 __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, const WaveDev* W, int ls, int tx,
                            int ty, int64_t te, uint64_t r0, int nrecv, bool limits_ready, unsigned int& visits,
@@ -1841,42 +1889,13 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
         }
         if (nrecv > kRecvChunk) stage_receivers<TS>(sm, J, B, ls, tx, ty, r0, kRecvChunk);
         if (tid < 32) {
-            // marked texels per row, prefixed (rows RPL * lane .. RPL * lane + RPL - 1)
-            constexpr int RPL = (TS + 31) / 32;
-            int c[RPL], sum = 0;
-#pragma unroll
-            for (int h = 0; h < RPL; ++h) {
-                const int y = RPL * tid + h;
-                c[h] = 0;
-                if (y < TS)
-#pragma unroll
-                    for (int w = 0; w < WPR; ++w) c[h] += __popc(sm.mask[y * WPR + w]);
-                sum += c[h];
-            }
-            const int inc = warp_incl_scan(sum);
-            int ex = inc - sum;
-#pragma unroll
-            for (int h = 0; h < RPL; ++h) {
-                const int y = RPL * tid + h;
-                if (y < TS) sm.row_start[y] = ex;
-                ex += c[h];
-            }
-            if (tid == 31) sm.row_start[TS] = inc;
+            unsigned int c = 0;
+            for (int q = tid; q < TS * WPR; q += 32) c += __popc(sm.mask[q]);
+            c = __reduce_add_sync(0xffffffffu, c);
+            if (tid == 0) sm.n_need = (int)c;
         }
         __syncthreads();
-        for (int q = tid; q < TS * WPR; q += bd) {
-            const int y = q / WPR, w = q % WPR;
-            uint32_t bits = sm.mask[q];
-            int pos = sm.row_start[y];
-            for (int w2 = 0; w2 < w; ++w2) pos += __popc(sm.mask[y * WPR + w2]);
-            while (bits) {
-                const int bit = __ffs(bits) - 1;
-                sm.u.r.list[pos++] = (uint16_t)(y * TS + w * 32 + bit);
-                bits &= bits - 1;
-            }
-        }
-        __syncthreads();
-        n_need = (int)sm.row_start[TS];
+        n_need = sm.n_need;
     }
     uint4* t4 = reinterpret_cast<uint4*>(sm.u.r.tile);
     for (int q = tid; q < TS * TS / 4; q += bd) t4[q] = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
@@ -1890,13 +1909,13 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
     const uint64_t cap = (uint64_t)W->bin_cap;
     if (off + cnt > cap) cnt = off < cap ? cap - off : 0;
     // triangles in batches of one per thread (at most kTriBatchMax): set-up,
-    // then all warps share the batch's texel visits in chunks of 32
+    // then all warps share the batch's rows, one (triangle, row) per lane
     const int batch = min(bd, kTriBatchMax);
     for (uint64_t b0 = 0; b0 < cnt; b0 += batch) {
         const int nb = (int)min((uint64_t)batch, cnt - b0);
         if (tid < nb) {
             TriSetup& S = sm.tri[tid];
-            S.work = 0;
+            S.rows = 0;
             const int t = (int)B.bins[off + b0 + tid];
             TriT T;
             tri_texel(J, B, lp, ls, t, T);
@@ -1914,88 +1933,76 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
 #pragma unroll
                     for (int k = 0; k < 3; ++k) { S.A[k] = ed.A[k]; S.Bc[k] = ed.Bc[k]; S.C[k] = ed.C[k]; }
                     S.e0 = T.d[0] * inv_a; S.e1 = T.d[1] * inv_a; S.e2 = T.d[2] * inv_a;
-                    S.smask = make_uint2((uint32_t)sb, (uint32_t)(sb >> 32));
-                    S.x0 = (short)x0; S.y0 = (short)y0; S.bw = (short)(x1 - x0 + 1); S.bh = (short)(y1 - y0 + 1);
-                    // visit the fewest texels: the box, the marked texels of its
-                    // rows (sparse tiles), or the whole sub-blocks it may shade in
-                    const int n_px = (x1 - x0 + 1) * (y1 - y0 + 1);
-                    const int n_sb = (__popc(S.smask.x) + __popc(S.smask.y)) << (2 * SWS);
-                    const int q_beg = dense ? 0 : (int)sm.row_start[y0];
-                    const int n_list = dense ? INT_MAX : (int)sm.row_start[y1 + 1] - q_beg;
-                    if (n_sb < n_px && n_sb < n_list) {
-                        S.list = 2; S.q_beg = 0; S.work = n_sb;
-                    } else if (n_px <= n_list) {
-                        S.list = 0; S.q_beg = 0; S.work = n_px;
-                    } else {
-                        S.list = 1; S.q_beg = q_beg; S.work = n_list;
-                    }
+                    S.sm_lo = (uint32_t)sb;
+                    S.sm_hi = (uint32_t)(sb >> 32);
+                    S.x0 = (short)x0; S.bw = (short)(x1 - x0 + 1);
+                    // the box's rows within the sub-block rows it may shade
+                    const int sy0 = (__ffsll((long long)sb) - 1) >> 3, sy1 = (63 - __clzll((long long)sb)) >> 3;
+                    const int ry0 = max(y0, sy0 << SWS), ry1 = min(y1, (sy1 << SWS) + (1 << SWS) - 1);
+                    S.y0 = ry0;
+                    S.rows = ry1 - ry0 + 1;
                 }
             }
-            sm.chunk_pref[tid] = (S.work + 31) >> 5;
+            sm.row_pref[tid] = S.rows;
         }
         __syncthreads();
-        if (tid < 32) warp_excl_scan_k<kTriBatchMax / 32>(sm.chunk_pref, nb);
+        if (tid < 32) warp_excl_scan_k<kTriBatchMax / 32>(sm.row_pref, nb);
         __syncthreads();
-        // each warp takes a contiguous range of chunks: one search, then the
-        // triangles of the range in order with their set-up in registers
-        const int n_chunks = sm.chunk_pref[nb];
-        const int c_beg = (int)(((int64_t)n_chunks * warp) / n_warps);
-        const int c_end = (int)(((int64_t)n_chunks * (warp + 1)) / n_warps);
+        // each warp takes a contiguous range of the batch's rows, 32 at a
+        // time; a lane finds its triangle by walking forward from the last
+        const int n_rows = sm.row_pref[nb];
+        const int u_beg = (int)(((int64_t)n_rows * warp) / n_warps);
+        const int u_end = (int)(((int64_t)n_rows * (warp + 1)) / n_warps);
         int t = 0;
         {
             int lo = 0, hi = nb - 1;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (sm.chunk_pref[mid] <= c_beg) lo = mid; else hi = mid - 1;
+                if (sm.row_pref[mid] <= u_beg) lo = mid; else hi = mid - 1;
             }
             t = lo;
         }
-        for (int ch = c_beg; ch < c_end; ++t) {
+        for (int ub = u_beg; ub < u_end; ub += 32) {
+            const int u = ub + lane;
+            if (u >= u_end) break;
+            while (sm.row_pref[t + 1] <= u) ++t;
             const TriSetup& S = sm.tri[t];
-            const int t_end = min(c_end, sm.chunk_pref[t + 1]);
-            if (ch >= t_end) continue;
+            const int iy = S.y0 + (u - sm.row_pref[t]);
+            const int sy = iy >> SWS;
+            const uint32_t sbyte = ((sy < 4 ? S.sm_lo : S.sm_hi) >> ((sy & 3) << 3)) & 0xFFu;
+            if (sbyte == 0u) continue;
+            if (!dense) {
+                uint32_t any = 0u;
+#pragma unroll
+                for (int w = 0; w < WPR; ++w) any |= sm.mask[iy * WPR + w];
+                if (any == 0u) continue;
+            }
+            // the row's texels inside all three edges, exactly: edge_at at
+            // the row's texel centres is fma(A, px, t_k), monotone in px
+            const float py = (float)iy + 0.5f;
             const float A0 = S.A[0], A1 = S.A[1], A2 = S.A[2];
-            const float B0 = S.Bc[0], B1 = S.Bc[1], B2 = S.Bc[2];
-            const float C0 = S.C[0], C1 = S.C[1], C2 = S.C[2];
+            const float t0 = __fmaf_rn(S.Bc[0], py, S.C[0]);
+            const float t1 = __fmaf_rn(S.Bc[1], py, S.C[1]);
+            const float t2 = __fmaf_rn(S.Bc[2], py, S.C[2]);
+            int lo = S.x0, hi = S.x0 + S.bw - 1;
+            edge_span(A0, t0, lo, hi);
+            edge_span(A1, t1, lo, hi);
+            edge_span(A2, t2, lo, hi);
+            if (lo > hi) continue;
             const float e0 = S.e0, e1 = S.e1, e2 = S.e2;
-            const uint2 smask = S.smask;
-            const int x0 = S.x0, y0 = S.y0, bw = S.bw, bh = S.bh, is_list = S.list, q_beg = S.q_beg, work = S.work;
-            const float inv_bw = 1.f / (float)bw;
-            for (; ch < t_end; ++ch) {
-                const int q = ((ch - sm.chunk_pref[t]) << 5) + lane;
-                if (q >= work) continue;
-                int ix, iy;
-                if (is_list == 2) {
-                    const int sb = nth_bit64(smask, q >> (2 * SWS));
-                    const int r = q & ((1 << (2 * SWS)) - 1);
-                    ix = ((sb & 7) << SWS) + (r & ((1 << SWS) - 1));
-                    iy = ((sb >> 3) << SWS) + (r >> SWS);
-                    if ((unsigned)(ix - x0) >= (unsigned)bw || (unsigned)(iy - y0) >= (unsigned)bh) continue;
-                    if (!dense && !(sm.mask[iy * WPR + (ix >> 5)] & (1u << (ix & 31)))) continue;
-                } else {
-                    if (is_list) {
-                        const int p = sm.u.r.list[q_beg + q];
-                        ix = p & (TS - 1);
-                        iy = p >> SH;
-                        if (ix < x0 || ix >= x0 + bw) continue;
-                    } else {
-                        const int ry = fdiv(q, bw, inv_bw);
-                        iy = y0 + ry;
-                        ix = x0 + q - ry * bw;
-                        if (!dense && !(sm.mask[iy * WPR + (ix >> 5)] & (1u << (ix & 31)))) continue;
-                    }
-                    const int sb = ((iy >> SWS) << 3) | (ix >> SWS);
-                    if (!(((sb < 32 ? smask.x : smask.y) >> (sb & 31)) & 1u)) continue;
-                }
-                const float px = (float)ix + 0.5f, py = (float)iy + 0.5f;
-                const float w0 = edge_at(A0, B0, C0, px, py);
-                const float w1 = edge_at(A1, B1, C1, px, py);
-                const float w2 = edge_at(A2, B2, C2, px, py);
-                if (PROF) ++visits;
-                if (w0 >= 0.f && w1 >= 0.f && w2 >= 0.f) {
+            for (int w = lo >> 5; w <= (hi >> 5); ++w) {
+                uint32_t bits = span_word(lo, hi, w) & sub_word<TS>(sbyte, w);
+                if (!dense) bits &= sm.mask[iy * WPR + w];
+                while (bits) {
+                    const int ix = (w << 5) + __ffs(bits) - 1;
+                    bits &= bits - 1u;
+                    const float px = (float)ix + 0.5f;
+                    const float w0 = __fmaf_rn(A0, px, t0);
+                    const float w1 = __fmaf_rn(A1, px, t1);
+                    const float w2 = __fmaf_rn(A2, px, t2);
                     atomicMin(&sm.u.r.tile[iy * TS + ix], depth_store_key(depth_at(w0, w1, w2, e0, e1, e2), lp, u24));
                     wrote = true;
-                    if (PROF) ++writes;
+                    if (PROF) { ++visits; ++writes; }
                 }
             }
         }

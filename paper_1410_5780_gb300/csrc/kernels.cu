@@ -1716,21 +1716,36 @@ __device__ __forceinline__ bool sample_test(const TriS* tri, int n_kept, const u
     return shaded;
 }
 
+// Sub-blocks sx0..sx1 x sy0..sy1 of a tile as a mask (bit sy * 8 + sx).
+__device__ __forceinline__ uint64_t sub_box(int sx0, int sx1, int sy0, int sy1)
+{
+    const uint64_t cols = (uint64_t)((2u << sx1) - (1u << sx0));
+    const uint64_t rows = (0x0101010101010101ull >> (8 * (7 - (sy1 - sy0)))) << (8 * sy0);
+    return rows * cols;  // bytes of rows are 0 or 1: no carries
+}
+
 // Depth-test the samples of staged receivers recv[0, n_recv) (items prefixed
 // in item_pref, total_items in all) that read tile (tx, ty) against the kept
 // triangles: items it_begin, it_begin + it_stride, ... one per thread.  Each
-// item adds its shaded count to its (step, cell) tally with one atomic.
+// item adds its shaded count to its (step, cell) tally with one atomic.  An
+// item is skipped whole when no sub-block of the texel box of its end
+// samples is in cand_sb (the sub-blocks in which some kept triangle may shade
+// a sample; all ones: no skipping) -- exact, since a sample's texel is
+// monotone in its index along the row (sample_texel), so every sample of the
+// item reads a texel of that box.
 template <int TS, int WORDS, bool PROF>
 __device__ __forceinline__ void test_items(const RecvSm* recv, int n_recv, int total_items, const JobDev& J,
                                            const LightParams& lp, int u24, int tx, int ty, int it_begin,
                                            int it_stride, const TriS* tri, int n_kept,
-                                           const uint32_t (*sbm)[WORDS], int nw, uint32_t* seen,
+                                           const uint32_t (*sbm)[WORDS], int nw, uint64_t cand_sb, uint32_t* seen,
                                            uint32_t* tally, int64_t tally0, unsigned long long* bits_row,
                                            int want_bits,
                                            unsigned int& cand, unsigned int& samples, unsigned int& pairs,
                                            unsigned int& frags)
 {
     constexpr int SH = TS == 128 ? 7 : (TS == 64 ? 6 : 5);
+    constexpr int SWS = SH - 3;  // log2 of the sub-block side (8 x 8 sub-blocks)
+    static_assert(SubGrid<TS>::side == 8, "sub-block index by shifts");
     const int n = J.n;
     const float r_max = (float)(J.R - 1);
     const float inv_n = 1.f / (float)n;
@@ -1738,10 +1753,21 @@ __device__ __forceinline__ void test_items(const RecvSm* recv, int n_recv, int t
         int Jr, cu, cv, jj, Ib, Ie;
         const RecvSm& R = decode_item(recv, n_recv, it, n, inv_n, Jr, cu, cv, jj, Ib, Ie);
         if (PROF) cand += (unsigned int)max(0, Ie - Ib + 1);
+        if (Ib > Ie) continue;
         // the receiver's sample frame and the row's base in registers
         const ModStep s = R.s;
         const float p_over_n = R.p_over_n;
         const SampleRow row = sample_row(s, Jr, p_over_n);
+        if (cand_sb != ~0ull) {
+            float dq;
+            int ax, ay, bx, by;
+            sample_texel(s, row, (float)Ib + 0.5f, p_over_n, r_max, ax, ay, dq);
+            sample_texel(s, row, (float)Ie + 0.5f, p_over_n, r_max, bx, by, dq);
+            const int lx0 = max(min(ax, bx) - (tx << SH), 0), lx1 = min(max(ax, bx) - (tx << SH), TS - 1);
+            const int ly0 = max(min(ay, by) - (ty << SH), 0), ly1 = min(max(ay, by) - (ty << SH), TS - 1);
+            if (lx0 > lx1 || ly0 > ly1) continue;
+            if (!(sub_box(lx0 >> SWS, lx1 >> SWS, ly0 >> SWS, ly1 >> SWS) & cand_sb)) continue;
+        }
         const int i0 = cu * n;
         uint32_t bits = 0u;  // bit i: sample i of the item's row (within its cell) is shaded
         float ih = (float)Ib + 0.5f;
@@ -2202,8 +2228,16 @@ __global__ void __launch_bounds__(kTileWarps * 32, 6) k_tile_warp(const WaveDev*
                 else sub_masks<TS, kWarpWords>(sm.k.tri, sm.k.box, sm.k.dmin, sm.k.dlim, sm.k.sbm, n, lane, 32);
                 __syncwarp();
                 const int C = J.n_cells;
+                // sub-blocks in which some kept triangle may shade a sample
+                uint32_t a0 = 0u, a1 = 0u;
+                for (int w = 0; w < ((n + 31) >> 5); ++w) {
+                    a0 |= sm.k.sbm[lane][w];
+                    a1 |= sm.k.sbm[lane + 32][w];
+                }
+                const uint64_t cand_sb = (uint64_t)__ballot_sync(0xffffffffu, a0 != 0u) |
+                                         ((uint64_t)__ballot_sync(0xffffffffu, a1 != 0u) << 32);
                 test_items<TS, kWarpWords, PROF>(sm.recv, nrecv, total, J, lp, u24, tx, ty, lane, 32, sm.k.tri, n,
-                                                 sm.k.sbm, (n + 31) >> 5, sm.k.seen,
+                                                 sm.k.sbm, (n + 31) >> 5, cand_sb, sm.k.seen,
                                                  B.cs_cnt, J.cs_base + (int64_t)ls * C,
                                                  B.cs_bits + J.cs_base + (int64_t)ls * C, want_bits, p_cand,
                                                  p_samples, p_pairs, p_writes);
@@ -2352,7 +2386,7 @@ __global__ void __launch_bounds__(HeavyCfg<TS>::threads, HeavyCfg<TS>::min_block
                     stage_receivers<TS>(sm, J, B, ls, tx, ty, r0 + c0, min(kRecvChunk, nrecv - c0));
                 }
                 test_items<TS, HeavyKept<TS>::words, PROF>(sm.recv, sm.n_recv, sm.total_items, J, lp, u24, tx, ty, tid,
-                                                blockDim.x, sm.u.s.tri, nt, sm.u.s.sbm, (nt + 31) >> 5,
+                                                blockDim.x, sm.u.s.tri, nt, sm.u.s.sbm, (nt + 31) >> 5, ~0ull,
                                                 sm.u.s.seen, B.cs_cnt, tally0, bits_row, want_bits, p_cand, p_samples,
                                                 p_pairs, p_writes);
             }

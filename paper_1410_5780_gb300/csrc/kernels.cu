@@ -2123,8 +2123,11 @@ __device__ __forceinline__ void tile_receivers(const Buffers& B, const WaveDev* 
 // k_tile_warp: fused path -- one warp per non-empty tile: the depth test of
 // every sample that reads the tile, sample by sample against the tile's kept
 // triangles; shaded counts go to (step, cell).  A warp takes a tile with at
-// most kWarpRecv receivers, kWarpBins binned and kWarpTri kept triangles;
-// it lists any other tile for k_raster_test.  A tile is a small work item
+// most kWarpRecv receivers, kWarpBins binned (kWarpTri on 32-texel tiles,
+// whose crowded tiles are rasterised anyway: handing them on before the keep
+// loop saves the warp's set-up of triangles it would drop, measured on the
+// tracker plant) and kWarpTri kept triangles; it lists any other tile for
+// k_raster_test.  A tile is a small work item
 // (hundreds of samples, a few triangles): one warp each keeps many tiles in
 // flight per SM, which hides the chain of dependent loads that starts a tile.
 // ---------------------------------------------------------------------------
@@ -2172,7 +2175,7 @@ __global__ void __launch_bounds__(kTileWarps * 32, 6) k_tile_warp(const WaveDev*
         const uint64_t off = B.t_off[te];
         uint64_t cnt = B.t_cnt[te];
         if (off + cnt > bin_cap) cnt = off < bin_cap ? bin_cap - off : 0;
-        bool heavy = nrecv > kWarpRecv || cnt > (uint64_t)kWarpBins;
+        bool heavy = nrecv > kWarpRecv || cnt > (uint64_t)(TS == 32 ? kWarpTri : kWarpBins);
         if (PROF && lane == 0) {
             if (nrecv > kWarpRecv) ++p_hr;
             else if (heavy) ++p_hb;

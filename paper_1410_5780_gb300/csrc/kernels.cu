@@ -1382,16 +1382,17 @@ __device__ __forceinline__ const RecvSm& decode_item(const RecvSm* recv, int n_r
 // is called per sample inside the tile (k = j * n + i within the cell);
 // g(R, cu, cv) after each item.
 template <int TS, bool PROF, typename F, typename G>
-__device__ __forceinline__ void for_tile_samples(const TileSm<TS>& sm, const JobDev& J, int tx, int ty,
-                                                 unsigned int& cand, F f, G g)
+__device__ __forceinline__ void for_tile_samples(const RecvSm* recv, int n_recv, int total_items, const JobDev& J,
+                                                 int tx, int ty, int it_begin, int it_stride, unsigned int& cand,
+                                                 F f, G g)
 {
     constexpr int SH = TS == 128 ? 7 : (TS == 64 ? 6 : 5);
     const int n = J.n;
     const float r_max = (float)(J.R - 1);
     const float inv_n = 1.f / (float)n;
-    for (int it = threadIdx.x; it < sm.total_items; it += blockDim.x) {
+    for (int it = it_begin; it < total_items; it += it_stride) {
         int Jr, cu, cv, jj, Ib, Ie;
-        const RecvSm& R = decode_item(sm.recv, sm.n_recv, it, n, inv_n, Jr, cu, cv, jj, Ib, Ie);
+        const RecvSm& R = decode_item(recv, n_recv, it, n, inv_n, Jr, cu, cv, jj, Ib, Ie);
         if (PROF) cand += (unsigned int)max(0, Ie - Ib + 1);
         const SampleRow row = sample_row(R.s, Jr, R.p_over_n);
         float ih = (float)Ib + 0.5f;
@@ -1847,6 +1848,112 @@ __device__ __forceinline__ uint32_t sub_word(uint32_t sbyte, int w)
     }
 }
 
+// Set up binned triangle t of tile (ox, oy) for the rasteriser in S and
+// return its rows: 0 (not kept) if it lies behind every staged receiver's
+// plane, covers no texel centre of the tile, or may shade no sample of any
+// sub-block (tri_sub_mask with the sub-block depth limits dlim).
+template <int TS, bool PROF>
+__device__ __forceinline__ int setup_raster_tri(const JobDev& J, const Buffers& B, const LightParams& lp, int ls,
+                                                int t, float ox, float oy, const RecvSm* recv, int n_recv,
+                                                bool cull_ok, const float* dlim, const SubInfo& si, TriSetup& S,
+                                                unsigned int& culled)
+{
+    constexpr int SWS = (TS == 128 ? 7 : (TS == 64 ? 6 : 5)) - 3;  // log2 of the sub-block side
+    TriT T;
+    tri_texel(J, B, lp, ls, t, T);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { T.x[k] -= ox; T.y[k] -= oy; }
+    if (!may_shade(recv, n_recv, T, cull_ok)) {
+        if (PROF) ++culled;
+        return 0;
+    }
+    Edges ed;
+    int x0, x1, y0, y1;
+    if (!make_edges(T, ed) || !tri_box<TS>(T, x0, x1, y0, y1)) return 0;
+    const uint64_t sb = tri_sub_mask<TS>(ed, x0, x1, y0, y1, fminf(T.d[0], fminf(T.d[1], T.d[2])), dlim, si);
+    if (sb == 0ull) return 0;
+    const float inv_a = 1.f / ed.area2;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) { S.A[k] = ed.A[k]; S.Bc[k] = ed.Bc[k]; S.C[k] = ed.C[k]; }
+    S.e0 = T.d[0] * inv_a; S.e1 = T.d[1] * inv_a; S.e2 = T.d[2] * inv_a;
+    S.sm_lo = (uint32_t)sb;
+    S.sm_hi = (uint32_t)(sb >> 32);
+    S.x0 = (short)x0; S.bw = (short)(x1 - x0 + 1);
+    // the box's rows within the sub-block rows it may shade
+    const int sy0 = (__ffsll((long long)sb) - 1) >> 3, sy1 = (63 - __clzll((long long)sb)) >> 3;
+    const int ry0 = max(y0, sy0 << SWS), ry1 = min(y1, (sy1 << SWS) + (1 << SWS) - 1);
+    S.y0 = ry0;
+    S.rows = ry1 - ry0 + 1;
+    return S.rows;
+}
+
+// Draw rows [u_beg, u_end) of set-up triangles tri[0, nb) (rows prefixed in
+// row_pref) into the depth tile, 32 at a time, one (triangle, row) per lane
+// of the calling warp: the row's texels inside all three edges, exactly
+// (edge_at on a row is fma(A, px, t_k), monotone in px: edge_span), within
+// the triangle's sub-blocks and, unless mask is null, marked in mask.
+template <int TS, bool PROF>
+__device__ __forceinline__ void draw_rows(const TriSetup* tri, const int* row_pref, int nb, int u_beg, int u_end,
+                                          const uint32_t* mask, uint32_t* tile, const LightParams& lp, int u24,
+                                          bool& wrote, unsigned int& visits, unsigned int& writes)
+{
+    constexpr int WPR = TS / 32;
+    constexpr int SWS = (TS == 128 ? 7 : (TS == 64 ? 6 : 5)) - 3;
+    const int lane = threadIdx.x & 31;
+    // a lane finds its triangle by walking forward from the last
+    int t = 0;
+    {
+        int lo = 0, hi = nb - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (row_pref[mid] <= u_beg) lo = mid; else hi = mid - 1;
+        }
+        t = lo;
+    }
+    for (int ub = u_beg; ub < u_end; ub += 32) {
+        const int u = ub + lane;
+        if (u >= u_end) break;
+        while (row_pref[t + 1] <= u) ++t;
+        const TriSetup& S = tri[t];
+        const int iy = S.y0 + (u - row_pref[t]);
+        const int sy = iy >> SWS;
+        const uint32_t sbyte = ((sy < 4 ? S.sm_lo : S.sm_hi) >> ((sy & 3) << 3)) & 0xFFu;
+        if (sbyte == 0u) continue;
+        if (mask) {
+            uint32_t any = 0u;
+#pragma unroll
+            for (int w = 0; w < WPR; ++w) any |= mask[iy * WPR + w];
+            if (any == 0u) continue;
+        }
+        const float py = (float)iy + 0.5f;
+        const float A0 = S.A[0], A1 = S.A[1], A2 = S.A[2];
+        const float t0 = __fmaf_rn(S.Bc[0], py, S.C[0]);
+        const float t1 = __fmaf_rn(S.Bc[1], py, S.C[1]);
+        const float t2 = __fmaf_rn(S.Bc[2], py, S.C[2]);
+        int lo = S.x0, hi = S.x0 + S.bw - 1;
+        edge_span(A0, t0, lo, hi);
+        edge_span(A1, t1, lo, hi);
+        edge_span(A2, t2, lo, hi);
+        if (lo > hi) continue;
+        const float e0 = S.e0, e1 = S.e1, e2 = S.e2;
+        for (int w = lo >> 5; w <= (hi >> 5); ++w) {
+            uint32_t bits = span_word(lo, hi, w) & sub_word<TS>(sbyte, w);
+            if (mask) bits &= mask[iy * WPR + w];
+            while (bits) {
+                const int ix = (w << 5) + __ffs(bits) - 1;
+                bits &= bits - 1u;
+                const float px = (float)ix + 0.5f;
+                const float w0 = __fmaf_rn(A0, px, t0);
+                const float w1 = __fmaf_rn(A1, px, t1);
+                const float w2 = __fmaf_rn(A2, px, t2);
+                atomicMin(&tile[iy * TS + ix], depth_store_key(depth_at(w0, w1, w2, e0, e1, e2), lp, u24));
+                wrote = true;
+                if (PROF) { ++visits; ++writes; }
+            }
+        }
+    }
+}
+
 // The tile's sub-block depth limits (sub_limits, or no limit when the
 // receivers are staged in chunks) and their summary, for the whole block.
 template <int TS>
@@ -1881,13 +1988,10 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
                            int ty, int64_t te, uint64_t r0, int nrecv, bool limits_ready, unsigned int& visits,
                            unsigned int& writes, unsigned int& culled, unsigned int& cand, unsigned int& dense_n)
 {
-    constexpr int SH = TS == 128 ? 7 : (TS == 64 ? 6 : 5);
     constexpr int WPR = TS / 32;
-    constexpr int kSubSide = SubGrid<TS>::side;
-    constexpr int SWS = SH - 3;  // log2 of the sub-block side (8 x 8 sub-blocks)
-    static_assert(kSubSide == 8, "sub-block index by shifts");
+    static_assert(SubGrid<TS>::side == 8, "sub-block index by shifts");
     const int tid = threadIdx.x, bd = blockDim.x;
-    const int lane = tid & 31, warp = tid >> 5, n_warps = bd >> 5;
+    const int warp = tid >> 5, n_warps = bd >> 5;
     const int u24 = W->depth_u24;
     const LightParams& lp = B.lp[J.js_base + ls];
     const bool cull_ok = nrecv <= kRecvChunk;
@@ -1906,7 +2010,7 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
         for (int c0 = 0; c0 < nrecv; c0 += kRecvChunk) {
             if (c0 > 0) stage_receivers<TS>(sm, J, B, ls, tx, ty, r0 + c0, min(kRecvChunk, nrecv - c0));
             for_tile_samples<TS, PROF>(
-                sm, J, tx, ty, cand,
+                sm.recv, sm.n_recv, sm.total_items, J, tx, ty, threadIdx.x, blockDim.x, cand,
                 [&](const RecvSm&, int, int ix, int iy, float) {
                     atomicOr(&sm.mask[(iy & (TS - 1)) * WPR + ((ix & (TS - 1)) >> 5)], 1u << (ix & 31));
                 },
@@ -1939,99 +2043,17 @@ __device__ int tile_raster(TileSm<TS>& sm, const JobDev& J, const Buffers& B, co
     const int batch = min(bd, kTriBatchMax);
     for (uint64_t b0 = 0; b0 < cnt; b0 += batch) {
         const int nb = (int)min((uint64_t)batch, cnt - b0);
-        if (tid < nb) {
-            TriSetup& S = sm.tri[tid];
-            S.rows = 0;
-            const int t = (int)B.bins[off + b0 + tid];
-            TriT T;
-            tri_texel(J, B, lp, ls, t, T);
-#pragma unroll
-            for (int k = 0; k < 3; ++k) { T.x[k] -= ox; T.y[k] -= oy; }
-            Edges ed;
-            int x0, x1, y0, y1;
-            if (!may_shade(sm.recv, sm.n_recv, T, cull_ok)) {
-                if (PROF) ++culled;
-            } else if (make_edges(T, ed) && tri_box<TS>(T, x0, x1, y0, y1)) {
-                const uint64_t sb = tri_sub_mask<TS>(ed, x0, x1, y0, y1, fminf(T.d[0], fminf(T.d[1], T.d[2])),
-                                                     sm.dlim, sm.si);
-                if (sb != 0ull) {
-                    const float inv_a = 1.f / ed.area2;
-#pragma unroll
-                    for (int k = 0; k < 3; ++k) { S.A[k] = ed.A[k]; S.Bc[k] = ed.Bc[k]; S.C[k] = ed.C[k]; }
-                    S.e0 = T.d[0] * inv_a; S.e1 = T.d[1] * inv_a; S.e2 = T.d[2] * inv_a;
-                    S.sm_lo = (uint32_t)sb;
-                    S.sm_hi = (uint32_t)(sb >> 32);
-                    S.x0 = (short)x0; S.bw = (short)(x1 - x0 + 1);
-                    // the box's rows within the sub-block rows it may shade
-                    const int sy0 = (__ffsll((long long)sb) - 1) >> 3, sy1 = (63 - __clzll((long long)sb)) >> 3;
-                    const int ry0 = max(y0, sy0 << SWS), ry1 = min(y1, (sy1 << SWS) + (1 << SWS) - 1);
-                    S.y0 = ry0;
-                    S.rows = ry1 - ry0 + 1;
-                }
-            }
-            sm.row_pref[tid] = S.rows;
-        }
+        if (tid < nb)
+            sm.row_pref[tid] = setup_raster_tri<TS, PROF>(J, B, lp, ls, (int)B.bins[off + b0 + tid], ox, oy, sm.recv,
+                                                          sm.n_recv, cull_ok, sm.dlim, sm.si, sm.tri[tid], culled);
         __syncthreads();
         if (tid < 32) warp_excl_scan_k<kTriBatchMax / 32>(sm.row_pref, nb);
         __syncthreads();
-        // each warp takes a contiguous range of the batch's rows, 32 at a
-        // time; a lane finds its triangle by walking forward from the last
+        // each warp takes a contiguous range of the batch's rows
         const int n_rows = sm.row_pref[nb];
-        const int u_beg = (int)(((int64_t)n_rows * warp) / n_warps);
-        const int u_end = (int)(((int64_t)n_rows * (warp + 1)) / n_warps);
-        int t = 0;
-        {
-            int lo = 0, hi = nb - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (sm.row_pref[mid] <= u_beg) lo = mid; else hi = mid - 1;
-            }
-            t = lo;
-        }
-        for (int ub = u_beg; ub < u_end; ub += 32) {
-            const int u = ub + lane;
-            if (u >= u_end) break;
-            while (sm.row_pref[t + 1] <= u) ++t;
-            const TriSetup& S = sm.tri[t];
-            const int iy = S.y0 + (u - sm.row_pref[t]);
-            const int sy = iy >> SWS;
-            const uint32_t sbyte = ((sy < 4 ? S.sm_lo : S.sm_hi) >> ((sy & 3) << 3)) & 0xFFu;
-            if (sbyte == 0u) continue;
-            if (!dense) {
-                uint32_t any = 0u;
-#pragma unroll
-                for (int w = 0; w < WPR; ++w) any |= sm.mask[iy * WPR + w];
-                if (any == 0u) continue;
-            }
-            // the row's texels inside all three edges, exactly: edge_at at
-            // the row's texel centres is fma(A, px, t_k), monotone in px
-            const float py = (float)iy + 0.5f;
-            const float A0 = S.A[0], A1 = S.A[1], A2 = S.A[2];
-            const float t0 = __fmaf_rn(S.Bc[0], py, S.C[0]);
-            const float t1 = __fmaf_rn(S.Bc[1], py, S.C[1]);
-            const float t2 = __fmaf_rn(S.Bc[2], py, S.C[2]);
-            int lo = S.x0, hi = S.x0 + S.bw - 1;
-            edge_span(A0, t0, lo, hi);
-            edge_span(A1, t1, lo, hi);
-            edge_span(A2, t2, lo, hi);
-            if (lo > hi) continue;
-            const float e0 = S.e0, e1 = S.e1, e2 = S.e2;
-            for (int w = lo >> 5; w <= (hi >> 5); ++w) {
-                uint32_t bits = span_word(lo, hi, w) & sub_word<TS>(sbyte, w);
-                if (!dense) bits &= sm.mask[iy * WPR + w];
-                while (bits) {
-                    const int ix = (w << 5) + __ffs(bits) - 1;
-                    bits &= bits - 1u;
-                    const float px = (float)ix + 0.5f;
-                    const float w0 = __fmaf_rn(A0, px, t0);
-                    const float w1 = __fmaf_rn(A1, px, t1);
-                    const float w2 = __fmaf_rn(A2, px, t2);
-                    atomicMin(&sm.u.r.tile[iy * TS + ix], depth_store_key(depth_at(w0, w1, w2, e0, e1, e2), lp, u24));
-                    wrote = true;
-                    if (PROF) { ++visits; ++writes; }
-                }
-            }
-        }
+        draw_rows<TS, PROF>(sm.tri, sm.row_pref, nb, (int)(((int64_t)n_rows * warp) / n_warps),
+                            (int)(((int64_t)n_rows * (warp + 1)) / n_warps), dense ? nullptr : sm.mask, sm.u.r.tile,
+                            lp, u24, wrote, visits, writes);
         __syncthreads();
     }
     if (wrote) sm.any_write = 1;
@@ -2400,7 +2422,7 @@ __global__ void __launch_bounds__(HeavyCfg<TS>::threads, HeavyCfg<TS>::min_block
                 uint32_t cnt = 0;
                 unsigned long long bits = 0ull;
                 for_tile_samples<TS, PROF>(
-                    sm, J, tx, ty, p_cand,
+                    sm.recv, sm.n_recv, sm.total_items, J, tx, ty, tid, blockDim.x, p_cand,
                     [&](const RecvSm& R, int k, int ix, int iy, float d) {
                         if (PROF) ++p_samples;
                         const uint32_t key = sm.u.r.tile[(iy & (TS - 1)) * TS + (ix & (TS - 1))];

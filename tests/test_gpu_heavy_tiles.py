@@ -3,7 +3,8 @@ warp per tile to one block per tile (a block-wide sample-driven test, or a
 shared-memory depth tile and the test of its samples, whichever is estimated
 cheaper) because they keep more than 64 triangles, have more than 512 binned
 triangles, or more than 16 or 64 receiver modules (receivers then staged in
-chunks, without plane culling).
+chunks, without plane culling); 32-texel tiles go on with more than 64
+binned triangles.
 Each case must agree with the FP64 oracle, be bit-identical to the map path
 (HBM shadow map + gather), and the work counters must show that the intended
 path ran."""
@@ -25,6 +26,7 @@ pytestmark = pytest.mark.gpu
     ("receiver_chunks", 64, 64, True, 30),     # > 64 receivers: staged in chunks, no plane culling, raster
     ("warp_tiles", 32, 512, False, 30),        # the same canopy on small tiles
     ("block_raster_128", 128, 256, False, 60), # 128-texel tiles: block raster of a 64 KB shared tile
+    ("crowded_32", 32, 128, False, 60),        # 32-texel tiles, > 64 binned: handed on before the keep loop
 ])
 def test_heavy_tile_paths(case, tile, map_res, tiny, cells):
     w = S.make_canopy(31 if not tiny else 32, tiny_modules=tiny, map_res=map_res, cells=cells)
@@ -48,6 +50,9 @@ def test_heavy_tile_paths(case, tile, map_res, tiny, cells):
     raster_tiles = p["nonempty_tiles"] - p["sample_tiles"]
     if case == "block_kept":
         assert why[2] > 0 and p["heavy_tiles"] > 0, p
+    elif case == "crowded_32":
+        # handed on for their binned count (more than a warp keeps), rasterised
+        assert why[1] > 0 and p["heavy_tiles"] > 0 and p["texel_visits"] > 0, p
     elif case in ("block_raster", "block_raster_128"):
         assert why[1] > 0 and raster_tiles > 0 and p["texel_visits"] > 0, p
     elif case == "many_receivers":

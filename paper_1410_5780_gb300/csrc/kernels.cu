@@ -1039,13 +1039,16 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_c(const WaveDev* __restri
 #pragma unroll
         for (int q = 0; q < kScanPer; ++q) {
             int64_t i = base + q;
-            if (i < tot) {
+            // offsets of non-empty tiles only: every reader of t_off, t_cur,
+            // t_slot, t_roff and t_rcur takes a tile from the non-empty list
+            // or checks t_cnt first
+            if (i < tot && x[q][1]) {
                 B.t_off[i] = (uint32_t)min(v[0], 0xFFFFFFFFull);
                 B.t_cur[i] = (uint32_t)min(v[0], 0xFFFFFFFFull);
                 B.t_slot[i] = (uint32_t)min(v[1], 0xFFFFFFFFull);
                 B.t_roff[i] = (uint32_t)min(v[2], 0xFFFFFFFFull);
                 B.t_rcur[i] = (uint32_t)min(v[2], 0xFFFFFFFFull);
-                if (x[q][1]) B.nonempty[v[1]] = (uint32_t)i;
+                B.nonempty[v[1]] = (uint32_t)i;
             }
             v[0] += x[q][0]; v[1] += x[q][1]; v[2] += x[q][2];
         }

@@ -1177,7 +1177,7 @@ struct RecvSm {
 template <int TS>
 struct HeavyCfg {
     static constexpr int threads = TS == 32 ? 128 : 256;
-    static constexpr int min_blocks = TS == 32 ? 8 : 4;
+    static constexpr int min_blocks = TS == 32 ? 9 : 4;  // 32: 53 registers, 9 x 24 KB shared
 };
 
 template <int TS>

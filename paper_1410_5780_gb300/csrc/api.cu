@@ -281,6 +281,88 @@ extern "C" const char* pv3d_last_error(pv3d_ctx* c) { return c ? c->err.c_str() 
 // ---------------------------------------------------------------------------
 // scene
 // ---------------------------------------------------------------------------
+// Order of the triangles (3 float4 vertices each in tv) for 32-triangle
+// meshlets: the set is split at the median centroid of its longest centroid
+// extent, at a multiple of 32 triangles, until each part is one meshlet, so a
+// meshlet is a compact patch and its box stays tight.  The two parts of a
+// split are independent: host threads take parts from a shared stack (the
+// order is the same whatever the threads' timing, since parts never overlap).
+static std::vector<uint32_t> meshlet_order(const std::vector<float4>& tv, int64_t n_tris)
+{
+    struct Rec {
+        float c[3];
+        uint32_t t;
+    };
+    std::vector<Rec> r((size_t)n_tris);
+    for (int64_t t = 0; t < n_tris; ++t) {
+        const float4 a = tv[3 * t], b = tv[3 * t + 1], d = tv[3 * t + 2];
+        r[t] = Rec{{(a.x + b.x + d.x) / 3.f, (a.y + b.y + d.y) / 3.f, (a.z + b.z + d.z) / 3.f}, (uint32_t)t};
+    }
+    // split [b, e) once; its parts of more than one meshlet go to `out`
+    auto split = [&r](int64_t b, int64_t e, std::vector<std::pair<int64_t, int64_t>>& out) {
+        float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int64_t i = b; i < e; ++i)
+            for (int a = 0; a < 3; ++a) {
+                lo[a] = std::min(lo[a], r[i].c[a]);
+                hi[a] = std::max(hi[a], r[i].c[a]);
+            }
+        int ax = 0;
+        for (int a = 1; a < 3; ++a)
+            if (hi[a] - lo[a] > hi[ax] - lo[ax]) ax = a;
+        // b is a multiple of 32, so every part starts on a meshlet
+        const int64_t mid = b + ((e - b + 31) / 32 / 2) * 32;
+        std::nth_element(r.begin() + b, r.begin() + mid, r.begin() + e,
+                         [ax](const Rec& x, const Rec& y) { return x.c[ax] < y.c[ax]; });
+        if (mid - b > 32) out.push_back({b, mid});
+        if (e - mid > 32) out.push_back({mid, e});
+    };
+    constexpr int64_t kSerial = 1 << 14;  // a part this small is finished by one thread
+    std::vector<std::pair<int64_t, int64_t>> todo;
+    if (n_tris > 32) todo.push_back({0, n_tris});
+    std::mutex mu;
+    std::condition_variable cv;
+    int busy = 0;
+    auto worker = [&]() {
+        std::vector<std::pair<int64_t, int64_t>> local;
+        std::unique_lock<std::mutex> lk(mu);
+        for (;;) {
+            cv.wait(lk, [&] { return !todo.empty() || busy == 0; });
+            if (todo.empty()) break;  // nothing queued and nobody splitting: done
+            const auto part = todo.back();
+            todo.pop_back();
+            ++busy;
+            lk.unlock();
+            local.clear();
+            split(part.first, part.second, local);
+            std::vector<std::pair<int64_t, int64_t>> out;
+            for (const auto& q : local) {
+                if (q.second - q.first > kSerial) {
+                    out.push_back(q);
+                    continue;
+                }
+                std::vector<std::pair<int64_t, int64_t>> stack{q};
+                while (!stack.empty()) {
+                    const auto c = stack.back();
+                    stack.pop_back();
+                    split(c.first, c.second, stack);
+                }
+            }
+            lk.lock();
+            for (const auto& q : out) todo.push_back(q);
+            --busy;
+            cv.notify_all();
+        }
+    };
+    const int n_threads = n_tris > 4 * kSerial ? (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency())) : 1;
+    std::vector<std::thread> pool;
+    for (int k = 1; k < n_threads; ++k) pool.emplace_back(worker);
+    worker();
+    for (auto& th : pool) th.join();
+    std::vector<uint32_t> order((size_t)n_tris);
+    for (int64_t t = 0; t < n_tris; ++t) order[t] = r[t].t;
+    return order;
+}
+
 extern "C" int pv3d_scene_load(pv3d_ctx* c, const float* xyz, int64_t n_verts, const int32_t* tri_idx,
                                int64_t n_tris, uint32_t* scene_id)
 {
@@ -307,41 +389,9 @@ extern "C" int pv3d_scene_load(pv3d_ctx* c, const float* xyz, int64_t n_verts, c
     memcpy(s.lo, lo, sizeof(lo));
     memcpy(s.hi, hi, sizeof(hi));
     // triangles grouped 32 at a time into meshlets with world bounding boxes
-    // (the binning culls whole meshlets): the triangle set is split at the
-    // median centroid of its longest centroid extent, at a multiple of 32
-    // triangles, until each part is one meshlet, so a meshlet is a compact
-    // patch and its box stays tight
+    // (the binning culls whole meshlets), in meshlet_order
     {
-        std::vector<float> cen((size_t)n_tris * 3);
-        for (int64_t t = 0; t < n_tris; ++t) {
-            const float4 a = tv[3 * t], b = tv[3 * t + 1], d = tv[3 * t + 2];
-            cen[3 * t] = (a.x + b.x + d.x) / 3.f;
-            cen[3 * t + 1] = (a.y + b.y + d.y) / 3.f;
-            cen[3 * t + 2] = (a.z + b.z + d.z) / 3.f;
-        }
-        std::vector<int64_t> order((size_t)n_tris);
-        for (int64_t t = 0; t < n_tris; ++t) order[t] = t;
-        std::vector<std::pair<int64_t, int64_t>> todo;
-        if (n_tris > 32) todo.push_back({0, n_tris});
-        while (!todo.empty()) {
-            const auto [b, e] = todo.back();
-            todo.pop_back();
-            float clo[3] = {INFINITY, INFINITY, INFINITY}, chi[3] = {-INFINITY, -INFINITY, -INFINITY};
-            for (int64_t i = b; i < e; ++i)
-                for (int a = 0; a < 3; ++a) {
-                    clo[a] = std::min(clo[a], cen[3 * order[i] + a]);
-                    chi[a] = std::max(chi[a], cen[3 * order[i] + a]);
-                }
-            int ax = 0;
-            for (int a = 1; a < 3; ++a)
-                if (chi[a] - clo[a] > chi[ax] - clo[ax]) ax = a;
-            // b is a multiple of 32, so every part starts on a meshlet
-            const int64_t mid = b + ((e - b + 31) / 32 / 2) * 32;
-            std::nth_element(order.begin() + b, order.begin() + mid, order.begin() + e,
-                             [&](int64_t x, int64_t y) { return cen[3 * x + ax] < cen[3 * y + ax]; });
-            if (mid - b > 32) todo.push_back({b, mid});
-            if (e - mid > 32) todo.push_back({mid, e});
-        }
+        const std::vector<uint32_t> order = meshlet_order(tv, n_tris);
         std::vector<float4> sorted(tv.size());
         for (int64_t t = 0; t < n_tris; ++t)
             for (int k = 0; k < 3; ++k) sorted[3 * t + k] = tv[3 * order[t] + k];

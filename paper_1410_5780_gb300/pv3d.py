@@ -234,15 +234,17 @@ class Context:
         ``pivots`` (attributes of paper_1410_5780_gb300.scenes.Generator)."""
         m = int(gen.origin.shape[0])
         mods = (pv3d_module * m)()
-        for i in range(m):
-            md = mods[i]
-            md.origin[:] = [float(x) for x in gen.origin[i]]
-            md.u[:] = [float(x) for x in gen.u[i]]
-            md.v[:] = [float(x) for x in gen.v[i]]
-            md.pitch = float(gen.pitch[i])
-            md.cells_u = int(gen.cells_u[i]); md.cells_v = int(gen.cells_v[i])
-            md.layout = int(gen.layout[i]); md.tracker = int(gen.tracker[i]); md.string_id = int(gen.string[i])
-            md.array_id = 0 if getattr(gen, "array", None) is None else int(gen.array[i])
+        mv = np.ctypeslib.as_array(mods)  # a structured view of the same memory
+        mv["origin"] = np.asarray(gen.origin, np.float32).reshape(m, 3)
+        mv["u"] = np.asarray(gen.u, np.float32).reshape(m, 3)
+        mv["v"] = np.asarray(gen.v, np.float32).reshape(m, 3)
+        mv["pitch"] = np.asarray(gen.pitch, np.float32).reshape(m)
+        mv["cells_u"] = np.asarray(gen.cells_u).reshape(m)
+        mv["cells_v"] = np.asarray(gen.cells_v).reshape(m)
+        mv["layout"] = np.asarray(gen.layout).reshape(m)
+        mv["tracker"] = np.asarray(gen.tracker).reshape(m)
+        mv["string_id"] = np.asarray(gen.string).reshape(m)
+        mv["array_id"] = 0 if getattr(gen, "array", None) is None else np.asarray(gen.array).reshape(m)
         subs = [np.ascontiguousarray(l.cell_sub, np.int32) for l in gen.layouts]
         lays = (pv3d_layout * len(subs))()
         for i, (l, s) in enumerate(zip(gen.layouts, subs)):
@@ -250,8 +252,8 @@ class Context:
             lays[i].cell_sub = s.ctypes.data_as(C.POINTER(C.c_int32))
         piv = np.asarray(gen.pivots, np.float32).reshape(-1, 3)
         trk = (pv3d_tracker * max(1, piv.shape[0]))()
-        for i in range(piv.shape[0]):
-            trk[i].pivot[:] = [float(x) for x in piv[i]]
+        if piv.shape[0]:
+            np.ctypeslib.as_array(trk)["pivot"] = piv
         gid = C.c_uint32()
         self._check(self.lib.pv3d_generator_define(self.h, scene_id, mods, m, lays, len(subs), trk, piv.shape[0],
                                                    C.byref(gid)))

@@ -527,6 +527,18 @@ struct TriT {
     float x[3], y[3], d[3];
 };
 
+// Light-space texel coordinates and depth of a point (world, relative to the
+// job's reference), with every rounding written out: the tile kernels and
+// the map path inline this in different contexts, and must get the same
+// bits for the same vertex whatever the compiler would otherwise fuse.
+__device__ __forceinline__ void project_point(const LightParams& lp, float x, float y, float z, float& tx, float& ty,
+                                              float& d)
+{
+    tx = __fmul_rn(__fsub_rn(__fmaf_rn(z, lp.uz, __fmaf_rn(y, lp.uy, __fmul_rn(x, lp.ux))), lp.u0), lp.inv_delta);
+    ty = __fmul_rn(__fsub_rn(__fmaf_rn(z, lp.vz, __fmaf_rn(y, lp.vy, __fmul_rn(x, lp.vx))), lp.v0), lp.inv_delta);
+    d = -__fmaf_rn(z, lp.sz, __fmaf_rn(y, lp.sy, __fmul_rn(x, lp.sx)));
+}
+
 // Triangle `t` of job J (scene triangle, or module triangle after the scene's)
 // at local step ls in texel coordinates.  Module triangles come from the
 // job's own module frames (ModStep), or, for a window group, from every
@@ -547,10 +559,10 @@ __device__ __forceinline__ void tri_texel(const JobDev& J, const Buffers& B, con
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const float a = k == 0 ? 0.f : (k == 1 ? a1 : a2), b = k == 0 ? 0.f : (k == 1 ? b1 : b2);
-            const float x = o.x + a * u.x + b * v.x, y = o.y + a * u.y + b * v.y, z = o.z + a * u.z + b * v.z;
-            T.x[k] = (x * lp.ux + y * lp.uy + z * lp.uz - lp.u0) * lp.inv_delta;
-            T.y[k] = (x * lp.vx + y * lp.vy + z * lp.vz - lp.v0) * lp.inv_delta;
-            T.d[k] = -(x * lp.sx + y * lp.sy + z * lp.sz);
+            const float x = __fmaf_rn(b, v.x, __fmaf_rn(a, u.x, o.x));
+            const float y = __fmaf_rn(b, v.y, __fmaf_rn(a, u.y, o.y));
+            const float z = __fmaf_rn(b, v.z, __fmaf_rn(a, u.z, o.z));
+            project_point(lp, x, y, z, T.x[k], T.y[k], T.d[k]);
         }
         return;
     }
@@ -558,11 +570,9 @@ __device__ __forceinline__ void tri_texel(const JobDev& J, const Buffers& B, con
         const float4* p = J.tri + 3 * (size_t)t;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            float4 q = __ldg(p + k);
-            float x = q.x - J.ref[0], y = q.y - J.ref[1], z = q.z - J.ref[2];
-            T.x[k] = (x * lp.ux + y * lp.uy + z * lp.uz - lp.u0) * lp.inv_delta;
-            T.y[k] = (x * lp.vx + y * lp.vy + z * lp.vz - lp.v0) * lp.inv_delta;
-            T.d[k] = -(x * lp.sx + y * lp.sy + z * lp.sz);
+            const float4 q = __ldg(p + k);
+            project_point(lp, __fsub_rn(q.x, J.ref[0]), __fsub_rn(q.y, J.ref[1]), __fsub_rn(q.z, J.ref[2]), T.x[k],
+                          T.y[k], T.d[k]);
         }
     } else {
         int q = t - J.n_tris;
@@ -575,12 +585,12 @@ __device__ __forceinline__ void tri_texel(const JobDev& J, const Buffers& B, con
         float a1 = lu, b1 = (q & 1) ? lv : 0.f;
         float a2 = (q & 1) ? 0.f : lu, b2 = lv;
         T.x[0] = s.tx0; T.y[0] = s.ty0; T.d[0] = s.d0;
-        T.x[1] = s.tx0 + a1 * s.tax + b1 * s.tbx;
-        T.y[1] = s.ty0 + a1 * s.tay + b1 * s.tby;
-        T.d[1] = s.d0 + a1 * s.da + b1 * s.db;
-        T.x[2] = s.tx0 + a2 * s.tax + b2 * s.tbx;
-        T.y[2] = s.ty0 + a2 * s.tay + b2 * s.tby;
-        T.d[2] = s.d0 + a2 * s.da + b2 * s.db;
+        T.x[1] = __fmaf_rn(b1, s.tbx, __fmaf_rn(a1, s.tax, s.tx0));
+        T.y[1] = __fmaf_rn(b1, s.tby, __fmaf_rn(a1, s.tay, s.ty0));
+        T.d[1] = __fmaf_rn(b1, s.db, __fmaf_rn(a1, s.da, s.d0));
+        T.x[2] = __fmaf_rn(b2, s.tbx, __fmaf_rn(a2, s.tax, s.tx0));
+        T.y[2] = __fmaf_rn(b2, s.tby, __fmaf_rn(a2, s.tay, s.ty0));
+        T.d[2] = __fmaf_rn(b2, s.db, __fmaf_rn(a2, s.da, s.d0));
     }
 }
 
@@ -605,7 +615,8 @@ struct Edges {
 
 __device__ __forceinline__ bool make_edges(TriT& T, Edges& e)
 {
-    float area2 = (T.x[1] - T.x[0]) * (T.y[2] - T.y[0]) - (T.y[1] - T.y[0]) * (T.x[2] - T.x[0]);
+    float area2 = __fsub_rn(__fmul_rn(__fsub_rn(T.x[1], T.x[0]), __fsub_rn(T.y[2], T.y[0])),
+                            __fmul_rn(__fsub_rn(T.y[1], T.y[0]), __fsub_rn(T.x[2], T.x[0])));
     if (!(fabsf(area2) > 0.f)) return false;
     if (area2 < 0.f) {
         float tx = T.x[1], ty = T.y[1], td = T.d[1];
@@ -617,9 +628,9 @@ __device__ __forceinline__ bool make_edges(TriT& T, Edges& e)
     for (int k = 0; k < 3; ++k) {
         // edge k is opposite vertex k: from vertex k+1 to vertex k+2
         int a = (k + 1) % 3, b = (k + 2) % 3;
-        e.A[k] = -(T.y[b] - T.y[a]);
-        e.Bc[k] = T.x[b] - T.x[a];
-        e.C[k] = -(e.A[k] * T.x[a] + e.Bc[k] * T.y[a]);
+        e.A[k] = -__fsub_rn(T.y[b], T.y[a]);
+        e.Bc[k] = __fsub_rn(T.x[b], T.x[a]);
+        e.C[k] = -__fadd_rn(__fmul_rn(e.A[k], T.x[a]), __fmul_rn(e.Bc[k], T.y[a]));
     }
     e.area2 = area2;
     return true;
